@@ -1,0 +1,669 @@
+/*
+ * dg_oracle.c -- plain CPU oracle for dyGRASS (Yuan, Aghdaei, Feng,
+ * "dyGRASS: Dynamic Spectral Graph Sparsification via Localized Random Walks
+ * on GPUs", arXiv:2505.02741).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, single-threaded,
+ * obviously-correct statement of what the method computes.  Only the test
+ * suite, the smoke check and the benchmark's CPU-baseline / reference arm load
+ * it.  It shares no code, header, table or helper with the CUDA library.
+ *
+ * What it follows (section / equation / algorithm of the paper):
+ *   - Section II-A:   weighted undirected graph, r_e = 1 / w_e.
+ *   - Section III-B:  non-backtracking random walk (NBRW) from p toward q; the
+ *                     walker accumulates the resistance of the edges it crosses;
+ *                     estimate R~_pq = min over the s walkers that reach q
+ *                     (Eq. 12); distortion threshold w_pq * R_cum > K stops an
+ *                     insertion walker; step limit T; a leaf stops the walker.
+ *                     An insertion is kept (added to H) iff no walker reaches q.
+ *   - Section III-C:  deletion of an edge of H: remove it, walk on the updated
+ *                     G up to T steps, recover the edges of the minimum-
+ *                     resistance path that reaches q; if none reaches q,
+ *                     recover a few local edges near p and q.
+ *   - Algorithm 1:    the stream loop (insertion / deletion branches).
+ *   - Section III-F:  the GPU version defers sparsifier updates to the end of
+ *                     a batch (one snapshot per batch).
+ *
+ * Readings where the paper is silent (each is listed in the design notes):
+ *   R1  neighbour lists are ordered by ascending neighbour id;
+ *   R2  random numbers: Philox4x32-10 (Salmon et al., SC'11), counter
+ *       (step, walker, lo32(update id), hi32(update id)), key (lo32(seed),
+ *       hi32(seed)), output word 0;
+ *   R3  the step picks uniformly among the neighbours other than the previous
+ *       vertex: j = floor(x * n_eff / 2^32), take the j-th such neighbour in
+ *       ascending id order;
+ *   R4  a walker that reaches q with w_pq * R <= K has hit (stop only on > K);
+ *   R5  reaching q on step T counts as a hit;
+ *   R6  deletion walks use no K;  R7 deletion walks start at the update's u;
+ *   R8  insertion early exit: all walkers of one update advance in lock-step;
+ *       at the first step index k* where any walker hits, every walker stops
+ *       (its path is cut at min(own stop, k*));
+ *   R9  the argmin walker is the lowest walker id among exact FP64 ties;
+ *   R10 recovered edges are the distinct edges of the argmin walker's walk
+ *       that are not already in H';
+ *   R11 fallback (no walker reached q): for x in (u, v), the incident G edge of
+ *       minimum resistance (ties: smaller neighbour id) not already in H';
+ *   R12 batch snapshot: validate in update order against a batch-local view of
+ *       G; G_b = G with all valid changes; H' = H minus every deleted edge that
+ *       was in H at batch start; insertion walks run on H', deletion walks on
+ *       G_b; H_b = H' U {kept insertions whose edge is in G_b} U recovered U
+ *       fallback, weights taken from G_b.
+ *
+ * Floating point: FP64 only, each operation rounded on its own (build with
+ * -ffp-contract=off); 1/w is computed once per edge.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* update status and walker stop reasons                                     */
+/* ------------------------------------------------------------------------ */
+enum {
+    ORC_OK = 0,
+    ORC_SELF_LOOP = 1,
+    ORC_BAD_VERTEX = 2,
+    ORC_DUP_INSERT = 3,
+    ORC_MISSING_DELETE = 4,
+    ORC_BAD_WEIGHT = 5,
+    ORC_BAD_OP = 6
+};
+enum { STOP_NONE = 0, STOP_HIT = 1, STOP_OVER_K = 2, STOP_AT_T = 3, STOP_LEAF = 4, STOP_CUT = 5 };
+enum { OP_INS = 0, OP_DEL = 1 };
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11, "Parallel random        */
+/* numbers: as easy as 1, 2, 3"): 10 rounds of the 4x32 S-box with           */
+/* multipliers 0xD2511F53 / 0xCD9E8D57 and Weyl key increments               */
+/* 0x9E3779B9 / 0xBB67AE85 applied between rounds.                           */
+/* ------------------------------------------------------------------------ */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; round++) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)x0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)x2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t y0 = hi1 ^ x1 ^ k0;
+        uint32_t y1 = lo1;
+        uint32_t y2 = hi0 ^ x3 ^ k1;
+        uint32_t y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* The random word a walker uses at one step (reading R2). */
+static uint32_t step_random(uint64_t seed, uint64_t upd_id, uint32_t walker, uint32_t step)
+{
+    uint32_t ctr[4] = {step, walker, (uint32_t)upd_id, (uint32_t)(upd_id >> 32)};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    return out[0];
+}
+
+/* ------------------------------------------------------------------------ */
+/* graph: per-vertex adjacency arrays sorted by neighbour id (reading R1)    */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t nbr;
+    double w;
+    double r; /* 1.0 / w, computed once when the edge is created */
+} orc_adj;
+
+typedef struct {
+    int32_t n;
+    int32_t *deg;
+    int32_t *cap;
+    orc_adj **adj;
+} orc_graph;
+
+static int graph_init(orc_graph *g, int32_t n)
+{
+    g->n = n;
+    g->deg = (int32_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
+    g->cap = (int32_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
+    g->adj = (orc_adj **)calloc((size_t)(n > 0 ? n : 1), sizeof(orc_adj *));
+    return (g->deg && g->cap && g->adj) ? 0 : -1;
+}
+
+static void graph_free(orc_graph *g)
+{
+    if (g->adj)
+        for (int32_t x = 0; x < g->n; x++) free(g->adj[x]);
+    free(g->adj);
+    free(g->deg);
+    free(g->cap);
+    memset(g, 0, sizeof(*g));
+}
+
+/* position of y in x's list, or -1 (binary search over the sorted list) */
+static int32_t graph_find(const orc_graph *g, int32_t x, int32_t y)
+{
+    int32_t lo = 0, hi = g->deg[x] - 1;
+    const orc_adj *L = g->adj[x];
+    while (lo <= hi) {
+        int32_t mid = lo + (hi - lo) / 2;
+        if (L[mid].nbr == y) return mid;
+        if (L[mid].nbr < y) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+static int graph_has(const orc_graph *g, int32_t a, int32_t b)
+{
+    return graph_find(g, a, b) >= 0;
+}
+
+/* insert the half edge x->y keeping the list sorted; the caller checked absence */
+static int half_insert(orc_graph *g, int32_t x, int32_t y, double w, double r)
+{
+    if (g->deg[x] == g->cap[x]) {
+        int32_t nc = g->cap[x] ? 2 * g->cap[x] : 4;
+        orc_adj *p = (orc_adj *)realloc(g->adj[x], (size_t)nc * sizeof(orc_adj));
+        if (!p) return -1;
+        g->adj[x] = p;
+        g->cap[x] = nc;
+    }
+    orc_adj *L = g->adj[x];
+    int32_t k = 0;
+    while (k < g->deg[x] && L[k].nbr < y) k++;
+    memmove(L + k + 1, L + k, (size_t)(g->deg[x] - k) * sizeof(orc_adj));
+    L[k].nbr = y;
+    L[k].w = w;
+    L[k].r = r;
+    g->deg[x]++;
+    return 0;
+}
+
+static void half_remove(orc_graph *g, int32_t x, int32_t y)
+{
+    int32_t k = graph_find(g, x, y);
+    if (k < 0) return;
+    orc_adj *L = g->adj[x];
+    memmove(L + k, L + k + 1, (size_t)(g->deg[x] - k - 1) * sizeof(orc_adj));
+    g->deg[x]--;
+}
+
+static int edge_insert(orc_graph *g, int32_t a, int32_t b, double w, double r)
+{
+    if (half_insert(g, a, b, w, r)) return -1;
+    if (half_insert(g, b, a, w, r)) return -1;
+    return 0;
+}
+
+static void edge_remove(orc_graph *g, int32_t a, int32_t b)
+{
+    half_remove(g, a, b);
+    half_remove(g, b, a);
+}
+
+/* weight and resistance stored for edge (a, b); the edge must exist */
+static void edge_wr(const orc_graph *g, int32_t a, int32_t b, double *w, double *r)
+{
+    int32_t k = graph_find(g, a, b);
+    *w = g->adj[a][k].w;
+    *r = g->adj[a][k].r;
+}
+
+/* ------------------------------------------------------------------------ */
+/* state of one dynamic graph                                                */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    orc_graph G;
+    orc_graph H;
+    uint64_t next_id; /* sequence number of the next submitted update */
+    uint64_t seed;
+    double K;
+    int32_t T;
+    int32_t s;
+    int32_t early_exit; /* reading R8 on (1) or off (0) */
+} orc_state;
+
+static int weight_ok(double w)
+{
+    return isfinite(w) && w > 0.0;
+}
+
+/* G(0): n vertices, m undirected edges; simple, 0 <= ids < n, w > 0 finite. */
+orc_state *orc_create(int32_t n, int64_t m, const int32_t *u, const int32_t *v, const double *w,
+                      uint64_t seed, double K, int32_t T, int32_t s, int32_t early_exit)
+{
+    if (n < 0 || m < 0 || T < 1 || s < 1 || !(K >= 0.0)) return NULL;
+    orc_state *st = (orc_state *)calloc(1, sizeof(orc_state));
+    if (!st) return NULL;
+    if (graph_init(&st->G, n) || graph_init(&st->H, n)) goto fail;
+    for (int64_t i = 0; i < m; i++) {
+        int32_t a = u[i], b = v[i];
+        if (a < 0 || a >= n || b < 0 || b >= n || a == b || !weight_ok(w[i])) goto fail;
+        if (graph_has(&st->G, a, b)) goto fail;
+        double r = 1.0 / w[i];
+        if (edge_insert(&st->G, a, b, w[i], r)) goto fail;
+    }
+    st->seed = seed;
+    st->K = K;
+    st->T = T;
+    st->s = s;
+    st->early_exit = early_exit;
+    return st;
+fail:
+    graph_free(&st->G);
+    graph_free(&st->H);
+    free(st);
+    return NULL;
+}
+
+void orc_destroy(orc_state *st)
+{
+    if (!st) return;
+    graph_free(&st->G);
+    graph_free(&st->H);
+    free(st);
+}
+
+/* H(0) = the listed edges of G (weights taken from G). Replaces any previous H. */
+int orc_init_sparsifier(orc_state *st, int64_t mh, const int32_t *u, const int32_t *v)
+{
+    int32_t n = st->G.n;
+    for (int64_t i = 0; i < mh; i++) {
+        if (u[i] < 0 || u[i] >= n || v[i] < 0 || v[i] >= n || u[i] == v[i]) return -1;
+        if (!graph_has(&st->G, u[i], v[i])) return -1;
+    }
+    graph_free(&st->H);
+    if (graph_init(&st->H, n)) return -2;
+    for (int64_t i = 0; i < mh; i++) {
+        if (graph_has(&st->H, u[i], v[i])) continue; /* repeated entry: set semantics */
+        double w, r;
+        edge_wr(&st->G, u[i], v[i], &w, &r);
+        if (edge_insert(&st->H, u[i], v[i], w, r)) return -2;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* one non-backtracking walker (Section III-B, III-C)                        */
+/* ------------------------------------------------------------------------ */
+/* Walks from p toward q on g.  Returns the stop reason; *steps_out = steps
+ * taken, *R_out = accumulated resistance.  path (nullable, room for T+1
+ * entries) receives the visited vertices, path[0] = p. */
+static int walk_one(const orc_graph *g, int32_t p, int32_t q, double wpq, int deletion, double K,
+                    int32_t T, uint64_t seed, uint64_t upd_id, uint32_t walker, int32_t *steps_out,
+                    double *R_out, int32_t *path)
+{
+    int32_t c = p;     /* current vertex */
+    int32_t prev = -1; /* previous vertex, none at the start */
+    int32_t steps = 0;
+    double R = 0.0;
+    int reason = STOP_NONE;
+    if (path) path[0] = p;
+    for (;;) {
+        const orc_adj *L = g->adj[c];
+        int32_t d = g->deg[c];
+        int32_t n_eff = (prev < 0) ? d : d - 1; /* neighbours other than prev */
+        if (n_eff <= 0) {
+            reason = STOP_LEAF;
+            break;
+        }
+        uint32_t x = step_random(seed, upd_id, walker, (uint32_t)steps);
+        uint32_t j = (uint32_t)(((uint64_t)x * (uint64_t)(uint32_t)n_eff) >> 32);
+        /* the j-th neighbour (ascending id) that is not prev */
+        int32_t pick = -1;
+        uint32_t seen = 0;
+        for (int32_t k = 0; k < d; k++) {
+            if (L[k].nbr == prev) continue;
+            if (seen == j) {
+                pick = k;
+                break;
+            }
+            seen++;
+        }
+        R = R + L[pick].r;
+        steps = steps + 1;
+        prev = c;
+        c = L[pick].nbr;
+        if (path) path[steps] = c;
+        if (c == q && (deletion || wpq * R <= K)) {
+            reason = STOP_HIT;
+            break;
+        }
+        if (!deletion && wpq * R > K) {
+            reason = STOP_OVER_K;
+            break;
+        }
+        if (steps == T) {
+            reason = STOP_AT_T;
+            break;
+        }
+    }
+    *steps_out = steps;
+    *R_out = R;
+    return reason;
+}
+
+/* exported single-walk entry (used by the sampler pins) */
+int orc_walk(const orc_state *st, int use_h, int32_t p, int32_t q, double wpq, int deletion,
+             uint64_t upd_id, uint32_t walker, int32_t *steps_out, double *R_out, int32_t *path)
+{
+    const orc_graph *g = use_h ? &st->H : &st->G;
+    if (p < 0 || p >= g->n || q < 0 || q >= g->n) return -1;
+    return walk_one(g, p, q, wpq, deletion, st->K, st->T, st->seed, upd_id, walker, steps_out, R_out,
+                    path);
+}
+
+/* ------------------------------------------------------------------------ */
+/* batch application (Algorithm 1 with the deferred-batch reading R12)       */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t a, b; /* a < b */
+} orc_pair;
+
+typedef struct {
+    orc_pair *e;
+    int64_t n, cap;
+} orc_pairs;
+
+static int pairs_push(orc_pairs *P, int32_t x, int32_t y)
+{
+    if (P->n == P->cap) {
+        int64_t nc = P->cap ? 2 * P->cap : 64;
+        orc_pair *q = (orc_pair *)realloc(P->e, (size_t)nc * sizeof(orc_pair));
+        if (!q) return -1;
+        P->e = q;
+        P->cap = nc;
+    }
+    P->e[P->n].a = x < y ? x : y;
+    P->e[P->n].b = x < y ? y : x;
+    P->n++;
+    return 0;
+}
+
+/* Per-walker debug record (optional output). */
+typedef struct {
+    int32_t reason; /* after the early-exit cut */
+    int32_t steps;  /* after the early-exit cut */
+    double R;       /* accumulated resistance, meaningful for hitting walkers */
+} orc_walker_out;
+
+/*
+ * Apply one batch of nu updates.  Per-update outputs (each an array of nu):
+ *   status, walked, hit, accepted, fallback, nhits, best, nrec, steps, rest.
+ * Optional: wout (nu*s records) and paths (nu*s*(T+1) vertices, -1 padded).
+ * Returns 0, or -2 on allocation failure.
+ */
+int orc_apply_batch(orc_state *st, int64_t nu, const int32_t *u, const int32_t *v, const double *w,
+                    const int32_t *op, int32_t *status, uint8_t *walked, uint8_t *hit,
+                    uint8_t *accepted, uint8_t *fallback, int32_t *nhits, int32_t *best,
+                    int32_t *nrec, int32_t *steps, double *rest, orc_walker_out *wout,
+                    int32_t *paths)
+{
+    orc_graph *G = &st->G, *H = &st->H;
+    const int32_t n = G->n, s = st->s, T = st->T;
+    const uint64_t id0 = st->next_id;
+    int rc = 0;
+    orc_pairs commit = {0}, hdel = {0};
+    int32_t *wsteps = (int32_t *)malloc((size_t)s * sizeof(int32_t));
+    int32_t *wreason = (int32_t *)malloc((size_t)s * sizeof(int32_t));
+    double *wR = (double *)malloc((size_t)s * sizeof(double));
+    int32_t *path = (int32_t *)malloc((size_t)(T + 1) * sizeof(int32_t));
+    int32_t *best_path = (int32_t *)malloc((size_t)(T + 1) * sizeof(int32_t));
+    if (!wsteps || !wreason || !wR || !path || !best_path) {
+        rc = -2;
+        goto done;
+    }
+
+    /* (i) validation in update order against a batch-local view of G.  The
+     * view is G itself, changed in order; H is not touched here, so the
+     * membership test below sees H at batch start. */
+    for (int64_t i = 0; i < nu; i++) {
+        walked[i] = hit[i] = accepted[i] = fallback[i] = 0;
+        nhits[i] = 0;
+        best[i] = -1;
+        nrec[i] = 0;
+        steps[i] = 0;
+        rest[i] = INFINITY;
+        int32_t a = u[i], b = v[i];
+        if (op[i] != OP_INS && op[i] != OP_DEL) {
+            status[i] = ORC_BAD_OP;
+            continue;
+        }
+        if (a < 0 || a >= n || b < 0 || b >= n) {
+            status[i] = ORC_BAD_VERTEX;
+            continue;
+        }
+        if (a == b) {
+            status[i] = ORC_SELF_LOOP;
+            continue;
+        }
+        if (op[i] == OP_INS) {
+            if (!weight_ok(w[i])) {
+                status[i] = ORC_BAD_WEIGHT;
+                continue;
+            }
+            if (graph_has(G, a, b)) {
+                status[i] = ORC_DUP_INSERT;
+                continue;
+            }
+            if (edge_insert(G, a, b, w[i], 1.0 / w[i])) {
+                rc = -2;
+                goto done;
+            }
+            status[i] = ORC_OK;
+            walked[i] = 1; /* every valid insertion is tested by walks on H' */
+        } else {
+            if (!graph_has(G, a, b)) {
+                status[i] = ORC_MISSING_DELETE;
+                continue;
+            }
+            edge_remove(G, a, b);
+            status[i] = ORC_OK;
+            if (graph_has(H, a, b)) { /* in H at batch start: Algorithm 1, deletion branch */
+                walked[i] = 1;
+                if (pairs_push(&hdel, a, b)) {
+                    rc = -2;
+                    goto done;
+                }
+            }
+        }
+    }
+
+    /* (ii) H' = H minus the deleted sparsifier edges (G is now G_b). */
+    for (int64_t k = 0; k < hdel.n; k++) edge_remove(H, hdel.e[k].a, hdel.e[k].b);
+
+    /* (iii) walks from the snapshot (H' for insertions, G_b for deletions). */
+    for (int64_t i = 0; i < nu; i++) {
+        if (!walked[i]) continue;
+        const int deletion = (op[i] == OP_DEL);
+        const orc_graph *g = deletion ? G : H;
+        const uint64_t upd_id = id0 + (uint64_t)i;
+        const double wpq = deletion ? 0.0 : w[i];
+        int32_t first_hit = -1; /* smallest step at which some walker hit */
+        for (int32_t k = 0; k < s; k++) {
+            wreason[k] = walk_one(g, u[i], v[i], wpq, deletion, st->K, T, st->seed, upd_id,
+                                  (uint32_t)k, &wsteps[k], &wR[k],
+                                  paths ? paths + ((size_t)i * s + k) * (size_t)(T + 1) : NULL);
+            if (paths) /* pad the unused tail of the path with -1 */
+                for (int32_t t = wsteps[k] + 1; t <= T; t++)
+                    paths[((size_t)i * s + k) * (size_t)(T + 1) + t] = -1;
+            if (wreason[k] == STOP_HIT && (first_hit < 0 || wsteps[k] < first_hit))
+                first_hit = wsteps[k];
+        }
+        /* reading R8: insertion walkers are cut at the first hitting step */
+        if (!deletion && st->early_exit && first_hit >= 0) {
+            for (int32_t k = 0; k < s; k++) {
+                if (wsteps[k] > first_hit) {
+                    wsteps[k] = first_hit;
+                    wreason[k] = STOP_CUT;
+                } else if (wsteps[k] == first_hit && wreason[k] != STOP_HIT) {
+                    /* stopped exactly at k* for another reason: keeps its reason */
+                }
+            }
+        }
+        /* Eq. 12: minimum over the walkers that reached q; ties -> lowest id (R9) */
+        int32_t nh = 0, bw = -1, tot = 0;
+        double Rmin = INFINITY;
+        for (int32_t k = 0; k < s; k++) {
+            tot += wsteps[k];
+            if (wreason[k] != STOP_HIT) continue;
+            nh++;
+            if (wR[k] < Rmin) {
+                Rmin = wR[k];
+                bw = k;
+            }
+        }
+        nhits[i] = nh;
+        best[i] = bw;
+        steps[i] = tot;
+        rest[i] = Rmin;
+        hit[i] = (uint8_t)(nh > 0);
+        if (paths && !deletion && st->early_exit && first_hit >= 0)
+            for (int32_t k = 0; k < s; k++)
+                for (int32_t t = wsteps[k] + 1; t <= T; t++)
+                    paths[((size_t)i * s + k) * (size_t)(T + 1) + t] = -1;
+        if (wout)
+            for (int32_t k = 0; k < s; k++) {
+                wout[(size_t)i * s + k].reason = wreason[k];
+                wout[(size_t)i * s + k].steps = wsteps[k];
+                wout[(size_t)i * s + k].R = wR[k];
+            }
+
+        if (!deletion) {
+            /* Section III-B: kept iff q was not reached by any walker. */
+            accepted[i] = (uint8_t)(nh == 0);
+            if (accepted[i] && graph_has(G, u[i], v[i]))
+                if (pairs_push(&commit, u[i], v[i])) {
+                    rc = -2;
+                    goto done;
+                }
+            continue;
+        }
+
+        /* Section III-C: deletion of a sparsifier edge. */
+        int32_t emitted = 0;
+        if (nh > 0) {
+            /* re-run the argmin walker to get its walk (same counters -> same path) */
+            int32_t ts;
+            double tR;
+            walk_one(g, u[i], v[i], 0.0, 1, st->K, T, st->seed, upd_id, (uint32_t)bw, &ts, &tR,
+                     best_path);
+            /* R10: distinct edges of the walk that are not in H' */
+            for (int32_t t = 0; t < ts; t++) {
+                int32_t x = best_path[t], y = best_path[t + 1];
+                int dup = 0;
+                for (int32_t t2 = 0; t2 < t; t2++) {
+                    int32_t x2 = best_path[t2], y2 = best_path[t2 + 1];
+                    if ((x2 == x && y2 == y) || (x2 == y && y2 == x)) {
+                        dup = 1;
+                        break;
+                    }
+                }
+                if (dup || graph_has(H, x, y)) continue;
+                if (pairs_push(&commit, x, y)) {
+                    rc = -2;
+                    goto done;
+                }
+                emitted++;
+            }
+        } else {
+            /* R11: fallback -- for each endpoint, its minimum-resistance G_b edge not in H' */
+            fallback[i] = 1;
+            int32_t pick_x[2] = {-1, -1}, pick_y[2] = {-1, -1};
+            const int32_t ends[2] = {u[i], v[i]};
+            for (int e = 0; e < 2; e++) {
+                int32_t x = ends[e];
+                double rmin = INFINITY;
+                for (int32_t k = 0; k < G->deg[x]; k++) {
+                    const orc_adj *A = &G->adj[x][k];
+                    if (graph_has(H, x, A->nbr)) continue;
+                    if (A->r < rmin) { /* ascending ids: first minimum = smaller id */
+                        rmin = A->r;
+                        pick_x[e] = x;
+                        pick_y[e] = A->nbr;
+                    }
+                }
+            }
+            for (int e = 0; e < 2; e++) {
+                if (pick_x[e] < 0) continue;
+                if (e == 1 && pick_x[0] >= 0 &&
+                    ((pick_x[0] == pick_x[1] && pick_y[0] == pick_y[1]) ||
+                     (pick_x[0] == pick_y[1] && pick_y[0] == pick_x[1])))
+                    continue;
+                if (pairs_push(&commit, pick_x[e], pick_y[e])) {
+                    rc = -2;
+                    goto done;
+                }
+                emitted++;
+            }
+        }
+        nrec[i] = emitted;
+    }
+
+    /* (iv) H_b = H' U committed edges (set union; weights from G_b). */
+    for (int64_t k = 0; k < commit.n; k++) {
+        int32_t a = commit.e[k].a, b = commit.e[k].b;
+        if (graph_has(H, a, b)) continue;
+        double ww, rr;
+        edge_wr(G, a, b, &ww, &rr);
+        if (edge_insert(H, a, b, ww, rr)) {
+            rc = -2;
+            goto done;
+        }
+    }
+    st->next_id = id0 + (uint64_t)nu;
+
+done:
+    free(commit.e);
+    free(hdel.e);
+    free(wsteps);
+    free(wreason);
+    free(wR);
+    free(path);
+    free(best_path);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* queries                                                                   */
+/* ------------------------------------------------------------------------ */
+/* Edges (a < b) of H (which = 1) or G (which = 0) in lexicographic order.
+ * Writes at most cap entries; returns the total count. */
+int64_t orc_query(const orc_state *st, int which, int64_t cap, int32_t *a, int32_t *b, double *w)
+{
+    const orc_graph *g = which ? &st->H : &st->G;
+    int64_t cnt = 0;
+    for (int32_t x = 0; x < g->n; x++)
+        for (int32_t k = 0; k < g->deg[x]; k++) {
+            if (g->adj[x][k].nbr <= x) continue;
+            if (cnt < cap) {
+                a[cnt] = x;
+                b[cnt] = g->adj[x][k].nbr;
+                w[cnt] = g->adj[x][k].w;
+            }
+            cnt++;
+        }
+    return cnt;
+}
+
+/* Degree of x in H (which = 1) or G (which = 0). */
+int32_t orc_degree(const orc_state *st, int which, int32_t x)
+{
+    const orc_graph *g = which ? &st->H : &st->G;
+    return (x >= 0 && x < g->n) ? g->deg[x] : -1;
+}
+
+uint64_t orc_next_id(const orc_state *st)
+{
+    return st->next_id;
+}
+
+void orc_set_next_id(orc_state *st, uint64_t id)
+{
+    st->next_id = id;
+}

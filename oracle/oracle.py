@@ -1,0 +1,172 @@
+"""ctypes shim over the plain C oracle (dg_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by the test suite, the smoke check and the
+benchmark's CPU-baseline / reference arm; the product path never loads it.
+
+``build()`` compiles ``dg_oracle.c`` with ``gcc -O2 -ffp-contract=off`` so that
+every FP64 add and multiply is rounded on its own, as the paper's estimator is
+written (Eq. 12: sums of r_e in walk order; threshold w_pq * R > K).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "dg_oracle.c")
+LIB = os.path.join(HERE, "libdg_oracle.so")
+
+# walker stop reasons (dg_oracle.c)
+STOP_HIT, STOP_OVER_K, STOP_AT_T, STOP_LEAF, STOP_CUT = 1, 2, 3, 4, 5
+
+WALKER_DTYPE = np.dtype([("reason", "<i4"), ("steps", "<i4"), ("R", "<f8")])
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into a shared library next to its source."""
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+               "-Wall", "-o", LIB + ".tmp", SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(LIB + ".tmp", LIB)
+    return LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(build())
+        P = C.c_void_p
+        i32p = np.ctypeslib.ndpointer(np.int32, flags="C")
+        f64p = np.ctypeslib.ndpointer(np.float64, flags="C")
+        u8p = np.ctypeslib.ndpointer(np.uint8, flags="C")
+        u32p = np.ctypeslib.ndpointer(np.uint32, flags="C")
+        L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        L.orc_philox4x32_10.restype = None
+        L.orc_create.argtypes = [C.c_int32, C.c_int64, i32p, i32p, f64p, C.c_uint64, C.c_double,
+                                 C.c_int32, C.c_int32, C.c_int32]
+        L.orc_create.restype = P
+        L.orc_destroy.argtypes = [P]
+        L.orc_destroy.restype = None
+        L.orc_init_sparsifier.argtypes = [P, C.c_int64, i32p, i32p]
+        L.orc_init_sparsifier.restype = C.c_int
+        L.orc_walk.argtypes = [P, C.c_int, C.c_int32, C.c_int32, C.c_double, C.c_int, C.c_uint64,
+                               C.c_uint32, C.POINTER(C.c_int32), C.POINTER(C.c_double), P]
+        L.orc_walk.restype = C.c_int
+        L.orc_apply_batch.argtypes = [P, C.c_int64, i32p, i32p, f64p, i32p, i32p, u8p, u8p, u8p, u8p,
+                                      i32p, i32p, i32p, i32p, f64p, P, P]
+        L.orc_apply_batch.restype = C.c_int
+        L.orc_query.argtypes = [P, C.c_int, C.c_int64, i32p, i32p, f64p]
+        L.orc_query.restype = C.c_int64
+        L.orc_degree.argtypes = [P, C.c_int, C.c_int32]
+        L.orc_degree.restype = C.c_int32
+        L.orc_next_id.argtypes = [P]
+        L.orc_next_id.restype = C.c_uint64
+        L.orc_set_next_id.argtypes = [P, C.c_uint64]
+        L.orc_set_next_id.restype = None
+        _lib = L
+    return _lib
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    """Philox4x32-10 block for one 128-bit counter and 64-bit key."""
+    out = np.zeros(4, np.uint32)
+    lib().orc_philox4x32_10(np.ascontiguousarray(ctr, np.uint32), np.ascontiguousarray(key, np.uint32),
+                            out)
+    return out
+
+
+class OracleGraph:
+    """One dynamic graph G with its sparsifier H, driven update by update."""
+
+    def __init__(self, n, u, v, w, *, seed=0, K=100.0, T=100, s=32, early_exit=True):
+        self.n, self.T, self.s = int(n), int(T), int(s)
+        u = np.ascontiguousarray(u, np.int32)
+        v = np.ascontiguousarray(v, np.int32)
+        w = np.ascontiguousarray(w, np.float64)
+        self._h = lib().orc_create(self.n, u.size, u, v, w, int(seed), float(K), self.T, self.s,
+                                   1 if early_exit else 0)
+        if not self._h:
+            raise ValueError("oracle rejected the graph (not simple, ids out of range or bad weight)")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().orc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def init_sparsifier(self, hu, hv):
+        rc = lib().orc_init_sparsifier(self._h, len(hu), np.ascontiguousarray(hu, np.int32),
+                                       np.ascontiguousarray(hv, np.int32))
+        if rc != 0:
+            raise ValueError("oracle rejected the sparsifier (edge not in G)")
+
+    @property
+    def next_id(self) -> int:
+        return int(lib().orc_next_id(self._h))
+
+    @next_id.setter
+    def next_id(self, value: int):
+        lib().orc_set_next_id(self._h, int(value))
+
+    def walk(self, p, q, wpq, deletion, upd_id, walker, on_h=True):
+        """One walker; returns (reason, steps, R, path)."""
+        steps = C.c_int32()
+        R = C.c_double()
+        path = np.full(self.T + 1, -1, np.int32)
+        reason = lib().orc_walk(self._h, 1 if on_h else 0, int(p), int(q), float(wpq),
+                                1 if deletion else 0, int(upd_id), int(walker), C.byref(steps),
+                                C.byref(R), path.ctypes.data)
+        if reason < 0:
+            raise ValueError("vertex out of range")
+        return reason, steps.value, R.value, path[: steps.value + 1].copy()
+
+    def apply(self, u, v, w, op, *, walkers=False, paths=False):
+        """Apply one batch; returns a dict of per-update arrays (and walker records)."""
+        nu = len(u)
+        u = np.ascontiguousarray(u, np.int32)
+        v = np.ascontiguousarray(v, np.int32)
+        w = np.ascontiguousarray(w, np.float64)
+        op = np.ascontiguousarray(op, np.int32)
+        out = dict(status=np.zeros(nu, np.int32), walked=np.zeros(nu, np.uint8),
+                   hit=np.zeros(nu, np.uint8), accepted=np.zeros(nu, np.uint8),
+                   fallback=np.zeros(nu, np.uint8), nhits=np.zeros(nu, np.int32),
+                   best_walker=np.zeros(nu, np.int32), nrecovered=np.zeros(nu, np.int32),
+                   steps=np.zeros(nu, np.int32), r_est=np.zeros(nu, np.float64))
+        wout = np.zeros(nu * self.s, WALKER_DTYPE) if walkers else None
+        pbuf = np.full(nu * self.s * (self.T + 1), -1, np.int32) if paths else None
+        rc = lib().orc_apply_batch(self._h, nu, u, v, w, op, out["status"], out["walked"], out["hit"],
+                                   out["accepted"], out["fallback"], out["nhits"], out["best_walker"],
+                                   out["nrecovered"], out["steps"], out["r_est"],
+                                   None if wout is None else wout.ctypes.data,
+                                   None if pbuf is None else pbuf.ctypes.data)
+        if rc != 0:
+            raise MemoryError("oracle batch failed")
+        if walkers:
+            out["walkers"] = wout.reshape(nu, self.s)
+        if paths:
+            out["paths"] = pbuf.reshape(nu, self.s, self.T + 1)
+        return out
+
+    def edges(self, which="H"):
+        """(a, b, w) of H or G, a < b, lexicographic."""
+        wh = 1 if which == "H" else 0
+        dummy_i = np.zeros(1, np.int32)
+        dummy_f = np.zeros(1, np.float64)
+        cnt = lib().orc_query(self._h, wh, 0, dummy_i, dummy_i, dummy_f)
+        a = np.zeros(max(cnt, 1), np.int32)
+        b = np.zeros(max(cnt, 1), np.int32)
+        w = np.zeros(max(cnt, 1), np.float64)
+        lib().orc_query(self._h, wh, cnt, a, b, w)
+        return a[:cnt], b[:cnt], w[:cnt]
+
+    def degree(self, x, which="H"):
+        return int(lib().orc_degree(self._h, 1 if which == "H" else 0, int(x)))

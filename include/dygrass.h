@@ -1,0 +1,269 @@
+/*
+ * dygrass.h -- C ABI of libdygrass.so: batched localized non-backtracking
+ * random walks that keep a spectral sparsifier H of a dynamic graph G up to
+ * date, after dyGRASS (Yuan, Aghdaei, Feng, arXiv:2505.02741).
+ *
+ * What each call computes, in the paper's terms:
+ *   dg_load_graph        -- G(0), the original graph (Section II-A: weighted,
+ *                           undirected; r_e = 1 / w_e).
+ *   dg_init_sparsifier   -- H(0), the initial sparsifier (Section III-A; the
+ *                           paper takes it from GRASS, here the caller passes it).
+ *   dg_apply_updates     -- one batch of the EdgeStream of Algorithm 1, with the
+ *                           batch-deferred semantics of Section III-F:
+ *                           insertions run s NBRW walkers from u toward v on H
+ *                           with distortion threshold K and step limit T, and
+ *                           the edge is added to H iff no walker reaches v
+ *                           (Section III-B, Eq. 12); deletions of an H edge run
+ *                           s walkers on the updated G up to T steps and recover
+ *                           the edges of the minimum-resistance path that
+ *                           reaches v, or a few local edges when none does
+ *                           (Section III-C).
+ *   dg_query_sparsifier  -- H(t), the output of Algorithm 1.
+ *
+ * Batch semantics (the paper defers GPU updates to the end of a batch,
+ * Section III-F; the order of phases inside a batch is this library's reading):
+ *   1. updates are validated in order against a batch-local view of G;
+ *   2. G_b = G with every valid change; H' = H minus every deleted edge that
+ *      was in H at batch start;
+ *   3. insertion walks run on H', deletion walks on G_b, all on that snapshot;
+ *   4. H_b = H' U {kept insertions whose edge is in G_b} U recovered edges,
+ *      with weights from G_b.  A batch of one update is Algorithm 1 exactly.
+ *
+ * Randomness: Philox4x32-10 with counter (step, walker, lo32(id), hi32(id))
+ * and key (lo32(seed), hi32(seed)); id is the graph's 0-based sequence number
+ * of the update over all updates ever submitted to that graph (rejected ones
+ * included).  Results therefore do not depend on how a stream is cut into
+ * batches of walks, on launch shapes, or on other graphs sharing the device.
+ *
+ * Conventions for every call:
+ *   - Return value: DG_OK (0) or a negative dg_status; no exception crosses
+ *     the ABI.  dg_last_error() describes the last failure on this thread.
+ *   - Host arrays are owned by the caller and only read (or written) during the
+ *     call.  All device memory is owned by the library (allocated through the
+ *     caller's hooks in dg_config when given).
+ *   - A dg_ctx is bound to one CUDA device; calls on one context must not be
+ *     made concurrently from several threads, except dg_submit_updates /
+ *     dg_wait, which are thread-safe.
+ */
+#ifndef DYGRASS_H
+#define DYGRASS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dg_ctx dg_ctx;
+typedef int32_t dg_status;
+
+#define DG_OK 0
+#define DG_E_INVALID (-1) /* bad argument or input (see dg_last_error) */
+#define DG_E_NOMEM (-2)   /* device allocation failed or HBM budget exceeded */
+#define DG_E_CUDA (-3)    /* CUDA runtime error */
+#define DG_E_TIMEOUT (-4) /* device work did not finish within timeout_ms */
+#define DG_E_STATE (-5)   /* call not valid in this state (e.g. no sparsifier yet) */
+#define DG_E_BUSY (-6)    /* serving queue full */
+
+/* per-update status codes (dg_update_result.status) */
+#define DG_UPD_OK 0
+#define DG_UPD_SELF_LOOP 1      /* u == v */
+#define DG_UPD_BAD_VERTEX 2     /* u or v outside [0, n) */
+#define DG_UPD_DUP_INSERT 3     /* insertion of an edge present in the batch-local view of G */
+#define DG_UPD_MISSING_DELETE 4 /* deletion of an edge absent from the batch-local view of G */
+#define DG_UPD_BAD_WEIGHT 5     /* insertion weight not finite or not > 0 */
+#define DG_UPD_BAD_OP 6         /* op not DG_OP_INSERT / DG_OP_DELETE */
+/* Checks run in this order: op, vertex range, self-loop, weight, presence. */
+
+#define DG_OP_INSERT 0
+#define DG_OP_DELETE 1
+
+/* walk execution forms (dg_config.walk_mode) */
+#define DG_WALK_BATCHED 0    /* one persistent launch runs every walker of the batch */
+#define DG_WALK_PER_UPDATE 1 /* one launch per walked update, one block of s threads (the paper's GPU scheme) */
+
+typedef struct {
+    uint64_t seed;          /* Philox key */
+    double K;               /* distortion threshold (Section III-B); >= 0 */
+    int32_t T;              /* step limit per walker (Section III-B; the paper fixes 100); 1..65535 */
+    int32_t s;              /* walkers per update (Section III-B); 1..1024 */
+    int32_t ins_early_exit; /* 1: an insertion's walkers stop at the first step index at which
+                               any of them reaches v (decisions unchanged; R~ and step counts
+                               refer to the truncated walks); 0: every walker runs to its own stop */
+    int32_t walk_mode;      /* DG_WALK_BATCHED or DG_WALK_PER_UPDATE */
+    double slack;           /* per-vertex capacity = deg + max(2, ceil(deg*(slack-1))); >= 1 */
+    double overflow_frac;   /* pool headroom for relocated lists, fraction of the initial pool */
+    uint64_t hbm_budget_bytes; /* serving admission budget in bytes; 0 = no limit */
+    int32_t autotune;       /* 1: tune walk launch shape per graph on its first large batch */
+    int32_t timeout_ms;     /* bound on every host wait for device work; <= 0 means 60000 */
+    int32_t use_cuda_graphs;/* 1: capture each batch step as a CUDA graph, replayed per batch size class */
+    int32_t record_walkers; /* debug: keep per-walker records (and paths if T <= 256) of the last batch */
+    int32_t device;         /* CUDA device ordinal */
+    /* optional device allocator (NULL = cudaMallocAsync / cudaFreeAsync on the library stream) */
+    void* (*alloc)(size_t bytes, void* cuda_stream, void* user);
+    void (*free)(void* ptr, size_t bytes, void* cuda_stream, void* user);
+    void* alloc_user;
+} dg_config;
+
+/* one streamed edge update, 24 bytes */
+typedef struct {
+    int32_t u, v;   /* endpoints; walks run from u toward v */
+    double w;       /* weight of an insertion (> 0, finite); ignored for a deletion */
+    int32_t op;     /* DG_OP_INSERT or DG_OP_DELETE */
+    int32_t reserved;
+} dg_update;
+
+/* per-update result, 32 bytes */
+typedef struct {
+    int32_t status;      /* DG_UPD_* */
+    uint8_t walked;      /* walkers ran (valid insertion, or deletion of an edge in H) */
+    uint8_t hit;         /* some walker reached v (within K for insertions) */
+    uint8_t accepted;    /* insertion kept for H (no walker reached v); committed if the edge is in G_b */
+    uint8_t fallback;    /* deletion walked but no walker reached v: local fallback edges recovered */
+    int32_t nhits;       /* walkers that reached v (after the early-exit cut for insertions) */
+    int32_t best_walker; /* walker index of R~ (lowest index among equal resistances), -1 if none */
+    int32_t nrecovered;  /* distinct edges this deletion returned to H (path or fallback) */
+    int32_t steps;       /* walk steps taken by this update's walkers (after the cut) */
+    double r_est;        /* R~ = minimum path resistance over hitting walkers (Eq. 12); +inf if none */
+} dg_update_result;
+
+/* statistics of the last completed batch on a graph */
+typedef struct {
+    int64_t updates;         /* updates in the batch */
+    int64_t valid;           /* updates with status DG_UPD_OK */
+    int64_t walked;          /* walked updates */
+    int64_t steps;           /* useful walk steps (sum of dg_update_result.steps) */
+    int64_t accepted;        /* kept insertions */
+    int64_t recovered;       /* edges returned to H by deletions */
+    int64_t h_edges;         /* |E(H)| after the batch */
+    int64_t g_edges;         /* |E(G)| after the batch */
+    double walk_ms;          /* device time of the walk phase (CUDA events on the batch stream) */
+    double batch_ms;         /* device time of the whole batch step */
+    int64_t walk_launches;   /* kernel launches in the walk phase */
+    int64_t launches;        /* kernel launches of the batch step */
+    int64_t retries;         /* pool growth / scratch growth retries */
+    int32_t walk_block;      /* launch shape used by the walk phase */
+    int32_t walk_ilp;
+    int32_t walk_blocks_per_sm;
+    int32_t graph_replayed;  /* 1 if the step ran as a replayed CUDA graph */
+} dg_batch_stats;
+
+/* default configuration: seed 0, K 100, T 100, s 32, early exit on, batched walks,
+   slack 1.25, overflow 0.5, no budget, autotune on, timeout 60 s, CUDA graphs on */
+void dg_config_default(dg_config* cfg);
+
+/* Create a context on cfg->device (cfg may be NULL for defaults). */
+dg_status dg_create(const dg_config* cfg, dg_ctx** out);
+
+/* Destroy a context and free all its device memory. NULL is ignored. */
+dg_status dg_destroy(dg_ctx* ctx);
+
+/* Text for a status code (static storage). */
+const char* dg_status_str(dg_status st);
+
+/* Description of the last error raised on the calling thread (static storage). */
+const char* dg_last_error(void);
+
+/*
+ * G(0) (Section II-A).  n vertices, m undirected edges (u[i], v[i], w[i]),
+ * host arrays of length m.  The graph must be simple: 0 <= u, v < n, u != v,
+ * no pair listed twice (in either orientation), w finite and > 0.  Violations
+ * return DG_E_INVALID and load nothing.  The graph starts with an empty
+ * sparsifier and update sequence number 0.  *graph_id_out receives the id.
+ */
+dg_status dg_load_graph(dg_ctx* ctx, int32_t n, int64_t m, const int32_t* u, const int32_t* v,
+                        const double* w, int32_t* graph_id_out);
+
+/* Free a graph and its sparsifier. */
+dg_status dg_unload_graph(dg_ctx* ctx, int32_t graph_id);
+
+/*
+ * H(0) (Section III-A: an input of Algorithm 1).  mh edges (u[i], v[i]) that
+ * must be edges of the current G (DG_E_INVALID otherwise); weights are taken
+ * from G; repeated pairs are kept once.  Replaces the current sparsifier.
+ */
+dg_status dg_init_sparsifier(dg_ctx* ctx, int32_t graph_id, int64_t mh, const int32_t* u,
+                             const int32_t* v);
+
+/*
+ * One batch of nu updates (Algorithm 1, batch semantics above).  ups: host
+ * array of nu records; res: host array of nu results, or NULL.  cuda_stream:
+ * stream to run on (NULL = the context's stream); the call returns after the
+ * results are on the host, waiting at most timeout_ms.  nu == 0 is a no-op.
+ * Per-update problems are reported in res[i].status; the batch still applies.
+ */
+dg_status dg_apply_updates(dg_ctx* ctx, int32_t graph_id, int64_t nu, const dg_update* ups,
+                           dg_update_result* res, void* cuda_stream);
+
+/*
+ * Same as dg_apply_updates with device-resident inputs and outputs: d_ups and
+ * d_res are device pointers (d_res may be NULL).  Returns once the batch is
+ * complete on the device.
+ */
+dg_status dg_apply_updates_device(dg_ctx* ctx, int32_t graph_id, int64_t nu, const dg_update* d_ups,
+                                  dg_update_result* d_res, void* cuda_stream);
+
+/*
+ * Edges of H: u[i] < v[i], lexicographic order, weights from G.  Writes at most
+ * cap entries; *count_out receives |E(H)|.  cap < |E(H)| returns DG_E_INVALID
+ * with *count_out set (call with cap = 0 to size the arrays).
+ */
+dg_status dg_query_sparsifier(dg_ctx* ctx, int32_t graph_id, int64_t cap, int32_t* u, int32_t* v,
+                              double* w, int64_t* count_out);
+
+/* Edges of the current G, same conventions as dg_query_sparsifier. */
+dg_status dg_query_graph(dg_ctx* ctx, int32_t graph_id, int64_t cap, int32_t* u, int32_t* v,
+                         double* w, int64_t* count_out);
+
+/* Statistics of the graph's last batch. */
+dg_status dg_get_batch_stats(dg_ctx* ctx, int32_t graph_id, dg_batch_stats* out);
+
+/*
+ * Debug records of the last batch (needs cfg.record_walkers = 1): for every
+ * update i and walker k, row i*s+k of reason (1 hit, 2 over K, 3 step limit,
+ * 4 leaf, 5 cut by the early exit; 0 if the update was not walked) and steps;
+ * paths (nullable, rows of T+1 vertex ids, -1 padded) when T <= 256.
+ * cap = number of rows the arrays hold (must be >= nu of that batch).
+ */
+dg_status dg_get_walker_records(dg_ctx* ctx, int32_t graph_id, int64_t cap, int32_t* reason,
+                                int32_t* steps, int32_t* paths);
+
+/* Force a compaction of G's and H's slack-slot pools (normally automatic). */
+dg_status dg_compact(dg_ctx* ctx, int32_t graph_id);
+
+/* Device bytes held by a graph (both pools and their vertex arrays). */
+dg_status dg_graph_bytes(dg_ctx* ctx, int32_t graph_id, uint64_t* bytes_out);
+
+/* Kernel launches issued by this context so far (all graphs). */
+uint64_t dg_launch_count(dg_ctx* ctx);
+
+/* Set / get a graph's next update sequence number (checkpoint / resume). */
+dg_status dg_set_next_update_id(dg_ctx* ctx, int32_t graph_id, uint64_t next_id);
+dg_status dg_get_next_update_id(dg_ctx* ctx, int32_t graph_id, uint64_t* next_id);
+
+/* Walk launch shape for a graph (threads per block, walkers per thread, blocks per SM);
+   0 fields keep the current value.  Outputs never depend on the shape. */
+dg_status dg_set_walk_shape(dg_ctx* ctx, int32_t graph_id, int32_t block, int32_t ilp,
+                            int32_t blocks_per_sm);
+
+/*
+ * Serving (continuous batching over resident graphs).  dg_submit_updates
+ * copies the request and queues it; requests on one graph run in submission
+ * order, one at a time; requests on different graphs run concurrently on
+ * separate streams when the HBM budget (cfg.hbm_budget_bytes) admits their
+ * working set.  res (nullable) must stay valid until dg_wait returns for the
+ * ticket.  Each request is one batch: its results equal those of
+ * dg_apply_updates on the same graph state.  Thread-safe.
+ */
+dg_status dg_submit_updates(dg_ctx* ctx, int32_t graph_id, int64_t nu, const dg_update* ups,
+                            dg_update_result* res, uint64_t* ticket_out);
+
+/* Wait for a ticket (timeout_ms < 0: the context timeout).  Returns the request's status;
+   *latency_ms (nullable) receives submit-to-completion time. */
+dg_status dg_wait(dg_ctx* ctx, uint64_t ticket, int32_t timeout_ms, double* latency_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DYGRASS_H */

@@ -1,0 +1,1043 @@
+// dg_batch.cu -- graph load / sparsifier init / the batch step of Algorithm 1.
+//
+// Batch step (one snapshot per batch, the deferral of Section III-F):
+//   pre:    validate updates in order (runs of equal edge keys after a stable
+//           sort), net G changes, H removals (Algorithm 1 deletion branch),
+//           plan + execute both mutations, walks (Section III-B/C), reduction
+//           (Eq. 12, accept rule);
+//   commit: kept insertions + recovered / fallback edges (Section III-C) as
+//           sorted unique half-edges not already in H', merged into H.
+// All kernels read their counts from device memory, so the whole step can be
+// captured once per batch-size class and replayed as a CUDA graph.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <thread>
+
+#include "dg_ctx.h"
+
+namespace dg {
+
+constexpr int BT = 256;  // threads per block of the small batch kernels
+
+__device__ __forceinline__ bool batch_aborted(const uint32_t* d_err) { return (*d_err & ABORT_MASK) != 0u; }
+
+static int grid_for(uint64_t items) {
+    uint64_t g = (items + BT - 1) / BT;
+    const uint64_t cap = (uint64_t)device_sms() * 16;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+// ---------------------------------------------------------------------------
+// load / init kernels
+// ---------------------------------------------------------------------------
+__global__ void k_load_keys(const int32_t* __restrict__ u, const int32_t* __restrict__ v,
+                            const double* __restrict__ w, uint32_t m, uint32_t n, uint64_t* __restrict__ keys,
+                            uint32_t* __restrict__ vals, uint32_t* d_err) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        const int32_t a = u[i], b = v[i];
+        const double ww = w[i];
+        const bool ok = a >= 0 && b >= 0 && (uint32_t)a < n && (uint32_t)b < n && a != b && isfinite(ww) && ww > 0.0;
+        if (!ok) {
+            atomicOr(d_err, (uint32_t)ERR_BAD_INPUT);
+            keys[2 * i] = 0;
+            keys[2 * i + 1] = 0;
+        } else {
+            keys[2 * i] = (uint64_t)a * n + (uint32_t)b;
+            keys[2 * i + 1] = (uint64_t)b * n + (uint32_t)a;
+        }
+        vals[2 * i] = i;
+        vals[2 * i + 1] = i;
+    }
+}
+
+// H(0) half-edges with weights looked up in G
+__global__ void k_inith_keys(const int32_t* __restrict__ u, const int32_t* __restrict__ v, uint32_t m, CSRView G,
+                             uint64_t* __restrict__ keys, uint32_t* __restrict__ vals, double* __restrict__ ws,
+                             uint32_t* d_err) {
+    const uint32_t n = (uint32_t)G.n;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        const int32_t a = u[i], b = v[i];
+        double w = 0.0;
+        const bool ok = a >= 0 && b >= 0 && (uint32_t)a < n && (uint32_t)b < n && a != b &&
+                        has_edge(G, (uint32_t)a, (uint32_t)b, &w);
+        if (!ok) {
+            atomicOr(d_err, (uint32_t)ERR_NOT_IN_G);
+            keys[2 * i] = 0;
+            keys[2 * i + 1] = 0;
+        } else {
+            keys[2 * i] = (uint64_t)a * n + (uint32_t)b;
+            keys[2 * i + 1] = (uint64_t)b * n + (uint32_t)a;
+        }
+        vals[2 * i] = 2 * i;
+        vals[2 * i + 1] = 2 * i + 1;
+        ws[2 * i] = w;
+        ws[2 * i + 1] = w;
+    }
+}
+
+// keep the first of each run of equal keys
+__global__ void k_first_of_run(const uint64_t* __restrict__ keys, const uint32_t* d_n, uint32_t n_max,
+                               uint32_t* __restrict__ flag) {
+    const uint32_t n = d_n ? min(*d_n, n_max) : n_max;
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
+        flag[c] = (c == 0 || keys[c - 1] != keys[c]) ? 1u : 0u;
+}
+
+__global__ void k_compact_kv(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                             const uint32_t* __restrict__ flag, const uint32_t* __restrict__ pos,
+                             const uint32_t* d_n, uint32_t n_max, uint64_t* __restrict__ okeys,
+                             uint32_t* __restrict__ ovals) {
+    const uint32_t n = d_n ? min(*d_n, n_max) : n_max;
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
+        if (flag[c]) {
+            okeys[pos[c]] = keys[c];
+            ovals[pos[c]] = vals[c];
+        }
+}
+
+// ---------------------------------------------------------------------------
+// batch kernels
+// ---------------------------------------------------------------------------
+// per update: basic checks (op, range, self-loop, weight); sort key of its edge
+__global__ void k_val_prep(const dg_update* __restrict__ ups, const BatchHdr* hdr, uint32_t n, uint32_t b_max,
+                           dg_update_result* __restrict__ res, uint64_t* __restrict__ keys,
+                           uint32_t* __restrict__ vals, uint8_t* __restrict__ wkind, double* __restrict__ fin_w) {
+    const uint32_t nu = min(hdr->nu, b_max);
+    const uint64_t sent = (uint64_t)n * n;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nu; i += gridDim.x * blockDim.x) {
+        const dg_update up = ups[i];
+        int32_t st = ST_OK;
+        if (up.op != DG_OP_INSERT && up.op != DG_OP_DELETE) st = ST_BAD_OP;
+        else if (up.u < 0 || up.v < 0 || (uint32_t)up.u >= n || (uint32_t)up.v >= n) st = ST_BAD_VERTEX;
+        else if (up.u == up.v) st = ST_SELF_LOOP;
+        else if (up.op == DG_OP_INSERT && !(isfinite(up.w) && up.w > 0.0)) st = ST_BAD_WEIGHT;
+        dg_update_result r;
+        r.status = st;
+        r.walked = r.hit = r.accepted = r.fallback = 0;
+        r.nhits = 0;
+        r.best_walker = -1;
+        r.nrecovered = 0;
+        r.steps = 0;
+        r.r_est = INFINITY;
+        res[i] = r;
+        if (st == ST_OK) {
+            const uint32_t a = (uint32_t)min(up.u, up.v), b = (uint32_t)max(up.u, up.v);
+            keys[i] = (uint64_t)a * n + b;
+        } else {
+            keys[i] = sent;
+        }
+        vals[i] = i;
+        wkind[i] = WALK_NONE;
+        fin_w[i] = __longlong_as_double(0x7ff8000000000000ll);  // NaN: edge absent at batch end
+    }
+}
+
+struct RunArgs {
+    const uint64_t* keys;
+    const uint32_t* vals;
+    const dg_update* ups;
+    const BatchHdr* hdr;
+    uint32_t n, b_max;
+    CSRView G, H;
+    dg_update_result* res;
+    uint8_t* wkind;
+    double* fin_w;
+    // net G changes (half-edges), appended
+    uint64_t* gkeys;
+    uint32_t* gvals;
+    uint8_t* gkind;
+    uint8_t* ghrem;
+    double* gw;
+    uint32_t* gcount;
+    BatchCounters* ctr;
+};
+
+// one thread per run of equal edges: replay the run in update order against
+// the batch-local view (presence, weight) of that edge
+__global__ void k_val_runs(RunArgs a) {
+    const uint32_t nu = min(a.hdr->nu, a.b_max);
+    const uint64_t sent = (uint64_t)a.n * a.n;
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nu; c += gridDim.x * blockDim.x) {
+        const uint64_t key = a.keys[c];
+        if (key == sent) continue;
+        if (c > 0 && a.keys[c - 1] == key) continue;
+        const uint32_t x = (uint32_t)(key / a.n), y = (uint32_t)(key % a.n);
+        double w0 = 0.0;
+        const bool present0 = has_edge(a.G, x, y, &w0);
+        const bool in_h = present0 && has_edge(a.H, x, y);
+        bool state = present0, any_valid = false, hrem = false;
+        double wcur = w0;
+        uint32_t valid = 0;
+        uint32_t e = c;
+        for (; e < nu && a.keys[e] == key; ++e) {
+            const uint32_t i = a.vals[e];
+            const dg_update up = a.ups[i];
+            if (up.op == DG_OP_INSERT) {
+                if (state) {
+                    a.res[i].status = ST_DUP_INSERT;
+                } else {
+                    state = true;
+                    wcur = up.w;
+                    any_valid = true;
+                    ++valid;
+                    a.wkind[i] = WALK_INS;
+                    a.res[i].walked = 1;
+                }
+            } else {
+                if (!state) {
+                    a.res[i].status = ST_MISSING_DELETE;
+                } else {
+                    state = false;
+                    any_valid = true;
+                    ++valid;
+                    if (in_h) {
+                        hrem = true;
+                        a.wkind[i] = WALK_DEL;
+                        a.res[i].walked = 1;
+                    }
+                }
+            }
+        }
+        // final presence / weight of the edge, needed by kept insertions
+        if (state)
+            for (uint32_t e2 = c; e2 < e; ++e2) {
+                const uint32_t i = a.vals[e2];
+                if (a.wkind[i] == WALK_INS) a.fin_w[i] = wcur;
+            }
+        atomicAdd(&a.ctr->valid, (unsigned long long)valid);
+        uint8_t kind = 255;
+        if (present0 && !state) kind = CHG_DEL;
+        else if (!present0 && state) kind = CHG_INS;
+        else if (present0 && state && any_valid) kind = CHG_SETW;
+        if (kind == 255) continue;
+        const uint32_t pos = atomicAdd(a.gcount, 2u);
+        a.gkeys[pos] = key;
+        a.gkeys[pos + 1] = (uint64_t)y * a.n + x;
+        a.gvals[pos] = pos;
+        a.gvals[pos + 1] = pos + 1;
+        a.gkind[pos] = a.gkind[pos + 1] = kind;
+        a.ghrem[pos] = a.ghrem[pos + 1] = hrem ? 1 : 0;
+        a.gw[pos] = a.gw[pos + 1] = wcur;
+    }
+}
+
+__global__ void k_walk_flags(const uint8_t* __restrict__ wkind, const BatchHdr* hdr, uint32_t b_max,
+                             uint32_t* __restrict__ flag) {
+    const uint32_t nu = min(hdr->nu, b_max);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nu; i += gridDim.x * blockDim.x)
+        flag[i] = wkind[i] != WALK_NONE;
+}
+
+__global__ void k_make_tasks(const dg_update* __restrict__ ups, const uint8_t* __restrict__ wkind,
+                             const uint32_t* __restrict__ pos, const BatchHdr* hdr, uint32_t b_max, WalkTasks t) {
+    const uint32_t nu = min(hdr->nu, b_max);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nu; i += gridDim.x * blockDim.x) {
+        const uint8_t k = wkind[i];
+        if (k == WALK_NONE) continue;
+        const uint32_t j = pos[i];
+        const dg_update up = ups[i];
+        t.u[j] = (uint32_t)up.u;
+        t.v[j] = (uint32_t)up.v;
+        t.idx[j] = i;
+        t.wpq[j] = k == WALK_INS ? up.w : 0.0;
+        t.kind[j] = k;
+    }
+}
+
+__global__ void k_flag_hrem(const uint32_t* __restrict__ gvals, const uint8_t* __restrict__ ghrem,
+                            const uint32_t* d_n, uint32_t n_max, uint32_t* __restrict__ flag) {
+    const uint32_t n = min(*d_n, n_max);
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
+        flag[c] = ghrem[gvals[c]];
+}
+
+// commit candidates: first of each equal-key run and not already in H'
+__global__ void k_commit_flags(const uint64_t* __restrict__ keys, const uint32_t* d_n, uint32_t n_max, CSRView H,
+                               uint32_t* __restrict__ flag, const uint32_t* d_err) {
+    if (batch_aborted(d_err)) return;
+    const uint32_t n = min(*d_n, n_max);
+    const uint32_t nv = (uint32_t)H.n;
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        const uint64_t k = keys[c];
+        bool keep = (c == 0 || keys[c - 1] != k);
+        if (keep) keep = find_nbr(H, (uint32_t)(k / nv), (uint32_t)(k % nv)) == 0xFFFFFFFFu;
+        flag[c] = keep ? 1u : 0u;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// workspace
+// ---------------------------------------------------------------------------
+uint64_t BatchWS::bytes() const {
+    uint64_t b = 0;
+    b += ups.bytes() + res.bytes() + hdr.bytes() + err.bytes() + ctr.bytes() + next.bytes();
+    b += vkeys.bytes() + vkeys_alt.bytes() + vvals.bytes() + vvals_alt.bytes() + vhist.bytes() + vscan.bytes();
+    b += wkind.bytes() + fin_w.bytes() + wflag.bytes() + wpos.bytes();
+    b += gkeys.bytes() + gkeys_alt.bytes() + hkeys.bytes() + gvals.bytes() + gvals_alt.bytes() + ghist.bytes();
+    b += gscan.bytes() + gcount.bytes() + hflag.bytes() + hpos.bytes() + hvals.bytes() + hcount.bytes();
+    b += gkind.bytes() + ghrem.bytes() + kind_del.bytes() + gw.bytes();
+    b += t_u.bytes() + t_v.bytes() + t_idx.bytes() + t_kstar.bytes() + t_count.bytes() + meta.bytes();
+    b += t_wpq.bytes() + recR.bytes() + t_kind.bytes() + best.bytes();
+    b += ckeys.bytes() + ckeys_alt.bytes() + ck2.bytes() + cvals.bytes() + cvals_alt.bytes() + chist.bytes();
+    b += cscan.bytes() + ccount.bytes() + cflag.bytes() + cpos.bytes() + cv2.bytes() + ccount2.bytes();
+    b += cw.bytes() + kind_ins.bytes() + path_buf.bytes();
+    b += dbg_reason.bytes() + dbg_steps.bytes() + dbg_paths.bytes();
+    b += apG.bytes() + apH.bytes() + apC.bytes();
+    return b;
+}
+
+static void ensure_cands(Ctx& c, DGraph& g, uint32_t cap, cudaStream_t st) {
+    BatchWS& w = g.ws;
+    if (cap <= w.cand_cap && w.ckeys.p) return;
+    DevAlloc& a = c.alloc;
+    w.ckeys.ensure(a, cap, st);
+    w.ckeys_alt.ensure(a, cap, st);
+    w.ck2.ensure(a, cap, st);
+    w.cvals.ensure(a, cap, st);
+    w.cvals_alt.ensure(a, cap, st);
+    w.cflag.ensure(a, cap, st);
+    w.cpos.ensure(a, cap, st);
+    w.cv2.ensure(a, cap, st);
+    w.cw.ensure(a, cap, st);
+    w.kind_ins.ensure(a, cap, st);
+    DG_CUDA(cudaMemsetAsync(w.kind_ins.p, CHG_INS, w.kind_ins.bytes(), st));
+    w.chist.ensure(a, sort_hist_words(cap), st);
+    w.cscan.ensure(a, std::max(sort_scan_tmp_words(cap), scan_tmp_words(cap + 1)), st);
+    w.apC.ensure(a, cap, (uint64_t)cap * 8, st);
+    w.cand_cap = cap;
+    ++g.layout_gen;
+}
+
+static void ensure_ws(Ctx& c, DGraph& g, uint32_t b_max, cudaStream_t st) {
+    BatchWS& w = g.ws;
+    const uint32_t s = (uint32_t)c.cfg.s, T = (uint32_t)c.cfg.T;
+    const bool need_dbg = c.cfg.record && !w.dbg_reason.p;
+    if (b_max <= w.b_max && !need_dbg) return;
+    if (b_max < w.b_max) b_max = w.b_max;
+    DevAlloc& a = c.alloc;
+    const uint32_t B = b_max, B2 = 2 * b_max;
+    w.ups.ensure(a, B, st);
+    w.res.ensure(a, B, st);
+    w.hdr.ensure(a, 1, st);
+    w.err.ensure(a, 4, st);
+    w.ctr.ensure(a, 1, st);
+    w.next.ensure(a, 1, st);
+    w.vkeys.ensure(a, B, st);
+    w.vkeys_alt.ensure(a, B, st);
+    w.vvals.ensure(a, B, st);
+    w.vvals_alt.ensure(a, B, st);
+    w.vhist.ensure(a, sort_hist_words(B), st);
+    w.vscan.ensure(a, std::max(sort_scan_tmp_words(B), scan_tmp_words(B + 1)), st);
+    w.wkind.ensure(a, B, st);
+    w.fin_w.ensure(a, B, st);
+    w.wflag.ensure(a, B, st);
+    w.wpos.ensure(a, B, st);
+    w.gkeys.ensure(a, B2, st);
+    w.gkeys_alt.ensure(a, B2, st);
+    w.hkeys.ensure(a, B2, st);
+    w.gvals.ensure(a, B2, st);
+    w.gvals_alt.ensure(a, B2, st);
+    w.ghist.ensure(a, sort_hist_words(B2), st);
+    w.gscan.ensure(a, std::max(sort_scan_tmp_words(B2), scan_tmp_words(B2 + 1)), st);
+    w.gcount.ensure(a, 1, st);
+    w.hflag.ensure(a, B2, st);
+    w.hpos.ensure(a, B2, st);
+    w.hvals.ensure(a, B2, st);
+    w.hcount.ensure(a, 1, st);
+    w.gkind.ensure(a, B2, st);
+    w.ghrem.ensure(a, B2, st);
+    w.kind_del.ensure(a, B2, st);
+    DG_CUDA(cudaMemsetAsync(w.kind_del.p, CHG_DEL, w.kind_del.bytes(), st));
+    w.gw.ensure(a, B2, st);
+    w.t_u.ensure(a, B, st);
+    w.t_v.ensure(a, B, st);
+    w.t_idx.ensure(a, B, st);
+    w.t_kstar.ensure(a, B, st);
+    w.t_count.ensure(a, 2, st);
+    w.t_wpq.ensure(a, B, st);
+    w.t_kind.ensure(a, B, st);
+    w.best.ensure(a, B, st);
+    w.meta.ensure(a, (size_t)B * s, st);
+    w.recR.ensure(a, (size_t)B * s, st);
+    w.ccount.ensure(a, 1, st);
+    w.ccount2.ensure(a, 1, st);
+    w.path_buf.ensure(a, (size_t)B * (T + 1), st);
+    if (c.cfg.record) {
+        w.dbg_reason.ensure(a, (size_t)B * s, st);
+        w.dbg_steps.ensure(a, (size_t)B * s, st);
+        if (T <= 256) w.dbg_paths.ensure(a, (size_t)B * s * (T + 1), st);
+    }
+    w.apG.ensure(a, B2, (uint64_t)B2 * 16, st);
+    w.apH.ensure(a, B2, (uint64_t)B2 * 16, st);
+    w.b_max = b_max;
+    ensure_cands(c, g, std::max<uint32_t>(B2 * 4, w.cand_cap), st);
+    // pinned staging
+    if (g.hs.cap < b_max) {
+        if (g.hs.ups) {
+            cudaFreeHost(g.hs.ups);
+            cudaFreeHost(g.hs.res);
+        }
+        DG_CUDA(cudaMallocHost(&g.hs.ups, sizeof(dg_update) * b_max));
+        DG_CUDA(cudaMallocHost(&g.hs.res, sizeof(dg_update_result) * b_max));
+        g.hs.cap = b_max;
+    }
+    if (!g.hs.hdr) {
+        DG_CUDA(cudaMallocHost(&g.hs.hdr, sizeof(BatchHdr)));
+        DG_CUDA(cudaMallocHost(&g.hs.err, sizeof(uint32_t) * 4));
+        DG_CUDA(cudaMallocHost(&g.hs.ctr, sizeof(BatchCounters)));
+        DG_CUDA(cudaMallocHost(&g.hs.tops, sizeof(unsigned long long) * 2));
+        DG_CUDA(cudaMallocHost(&g.hs.counts, sizeof(uint32_t) * 4));
+    }
+    ++g.layout_gen;
+}
+
+static uint32_t bucket_of(uint64_t nu) {
+    uint32_t b = 1024;
+    while (b < nu) b <<= 1;
+    return b;
+}
+
+// ---------------------------------------------------------------------------
+// load / init / export
+// ---------------------------------------------------------------------------
+static void wait_stream(Ctx& c, cudaStream_t st) {
+    cudaEvent_t ev;
+    DG_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    DG_CUDA(cudaEventRecord(ev, st));
+    const int tmo = c.cfg.timeout_ms > 0 ? c.cfg.timeout_ms : 60000;
+    const double t0 = now_ms();
+    for (;;) {
+        cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) {
+            cudaEventDestroy(ev);
+            throw Error(DG_E_CUDA, std::string("device error: ") + cudaGetErrorString(e));
+        }
+        if (now_ms() - t0 > tmo) {
+            cudaEventDestroy(ev);
+            throw Error(DG_E_TIMEOUT, "device work did not finish within timeout_ms");
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    cudaEventDestroy(ev);
+}
+
+void graph_load(Ctx& c, DGraph& g, int32_t n, int64_t m, const int32_t* u, const int32_t* v, const double* w) {
+    cudaStream_t st = c.stream;
+    DevAlloc& a = c.alloc;
+    if (n < 0 || m < 0) throw Error(DG_E_INVALID, "negative size");
+    if ((uint64_t)n * (uint64_t)n >= (1ull << 62)) throw Error(DG_E_INVALID, "too many vertices");
+    if (2 * (uint64_t)m >= 0xFFFFFFF0ull) throw Error(DG_E_INVALID, "too many edges");
+    g.n = n;
+    g.G.slack = g.H.slack = (float)c.cfg.slack;
+    g.G.overflow = g.H.overflow = c.cfg.overflow;
+    csr_alloc_vertices(g.G, a, n, st);
+    csr_alloc_vertices(g.H, a, n, st);
+    g.touched.ensure(a, (size_t)n + 1, st);
+    DG_CUDA(cudaMemsetAsync(g.touched.p, 0, g.touched.bytes(), st));
+    const uint32_t M = (uint32_t)m, M2 = 2 * (uint32_t)m;
+    DBuf<int32_t> du, dv;
+    DBuf<double> dw;
+    DBuf<uint64_t> k0, k1;
+    DBuf<uint32_t> v0, v1, hist, stmp, err;
+    du.ensure(a, M + 1, st);
+    dv.ensure(a, M + 1, st);
+    dw.ensure(a, M + 1, st);
+    k0.ensure(a, M2 + 1, st);
+    k1.ensure(a, M2 + 1, st);
+    v0.ensure(a, M2 + 1, st);
+    v1.ensure(a, M2 + 1, st);
+    hist.ensure(a, sort_hist_words(M2 + 1), st);
+    stmp.ensure(a, sort_scan_tmp_words(M2 + 1), st);
+    err.ensure(a, 1, st);
+    DG_CUDA(cudaMemsetAsync(err.p, 0, 4, st));
+    if (M) {
+        DG_CUDA(cudaMemcpyAsync(du.p, u, 4ull * M, cudaMemcpyHostToDevice, st));
+        DG_CUDA(cudaMemcpyAsync(dv.p, v, 4ull * M, cudaMemcpyHostToDevice, st));
+        DG_CUDA(cudaMemcpyAsync(dw.p, w, 8ull * M, cudaMemcpyHostToDevice, st));
+        k_load_keys<<<grid_for(M), BT, 0, st>>>(du.p, dv.p, dw.p, M, (uint32_t)n, k0.p, v0.p, err.p);
+        ++g_launches;
+    }
+    uint32_t herr = 0;
+    DG_CUDA(cudaMemcpyAsync(&herr, err.p, 4, cudaMemcpyDeviceToHost, st));
+    wait_stream(c, st);
+    auto cleanup = [&]() {
+        du.release(a, st); dv.release(a, st); k0.release(a, st); k1.release(a, st);
+        v0.release(a, st); v1.release(a, st); hist.release(a, st); stmp.release(a, st); err.release(a, st);
+        dw.release(a, st);
+    };
+    if (herr) {
+        cleanup();
+        throw Error(DG_E_INVALID, "graph edge with a vertex out of range, a self-loop or a weight not finite > 0");
+    }
+    const uint64_t* keys = k0.p;
+    const uint32_t* vals = v0.p;
+    if (M2) {
+        SortBufs sb{k0.p, v0.p, k1.p, v1.p, hist.p, stmp.p};
+        const int nbits = bit_length((uint64_t)n * n - 1);
+        if (radix_sort_pairs(sb, nullptr, M2, nbits, st)) {
+            keys = k1.p;
+            vals = v1.p;
+        }
+    }
+    csr_build(g.G, a, keys, vals, dw.p, M2, err.p, st);
+    DG_CUDA(cudaMemcpyAsync(&herr, err.p, 4, cudaMemcpyDeviceToHost, st));
+    wait_stream(c, st);
+    cleanup();
+    if (herr & ERR_DUP_EDGE) throw Error(DG_E_INVALID, "graph lists an edge twice");
+    if (herr) throw Error(DG_E_CUDA, "internal error while building the graph");
+    csr_build(g.H, a, nullptr, nullptr, nullptr, 0, nullptr, st);
+    g.has_h = true;  // empty sparsifier
+    g.next_id = 0;
+    for (int i = 0; i < 4; ++i) DG_CUDA(cudaEventCreate(&g.ev[i]));
+    wait_stream(c, st);
+}
+
+void graph_init_h(Ctx& c, DGraph& g, int64_t mh, const int32_t* u, const int32_t* v) {
+    cudaStream_t st = c.stream;
+    DevAlloc& a = c.alloc;
+    if (mh < 0 || 2 * (uint64_t)mh >= 0xFFFFFFF0ull) throw Error(DG_E_INVALID, "bad sparsifier size");
+    const uint32_t M = (uint32_t)mh, M2 = 2 * M;
+    DBuf<int32_t> du, dv;
+    DBuf<double> dw;
+    DBuf<uint64_t> k0, k1, k2;
+    DBuf<uint32_t> v0, v1, v2, hist, stmp, err, flag, pos, cnt;
+    du.ensure(a, M + 1, st);
+    dv.ensure(a, M + 1, st);
+    dw.ensure(a, M2 + 1, st);
+    k0.ensure(a, M2 + 1, st);
+    k1.ensure(a, M2 + 1, st);
+    k2.ensure(a, M2 + 1, st);
+    v0.ensure(a, M2 + 1, st);
+    v1.ensure(a, M2 + 1, st);
+    v2.ensure(a, M2 + 1, st);
+    flag.ensure(a, M2 + 1, st);
+    pos.ensure(a, M2 + 1, st);
+    cnt.ensure(a, 2, st);
+    hist.ensure(a, sort_hist_words(M2 + 1), st);
+    stmp.ensure(a, std::max(sort_scan_tmp_words(M2 + 1), scan_tmp_words(M2 + 1)), st);
+    err.ensure(a, 1, st);
+    DG_CUDA(cudaMemsetAsync(err.p, 0, 4, st));
+    DG_CUDA(cudaMemsetAsync(cnt.p, 0, 8, st));
+    if (M) {
+        DG_CUDA(cudaMemcpyAsync(du.p, u, 4ull * M, cudaMemcpyHostToDevice, st));
+        DG_CUDA(cudaMemcpyAsync(dv.p, v, 4ull * M, cudaMemcpyHostToDevice, st));
+        k_inith_keys<<<grid_for(M), BT, 0, st>>>(du.p, dv.p, M, g.G.view(), k0.p, v0.p, dw.p, err.p);
+        ++g_launches;
+    }
+    uint32_t herr = 0;
+    DG_CUDA(cudaMemcpyAsync(&herr, err.p, 4, cudaMemcpyDeviceToHost, st));
+    wait_stream(c, st);
+    auto cleanup = [&]() {
+        DBuf<int32_t>* i32s[] = {&du, &dv};
+        for (auto* b : i32s) b->release(a, st);
+        DBuf<uint64_t>* u64s[] = {&k0, &k1, &k2};
+        for (auto* b : u64s) b->release(a, st);
+        DBuf<uint32_t>* u32s[] = {&v0, &v1, &v2, &hist, &stmp, &err, &flag, &pos, &cnt};
+        for (auto* b : u32s) b->release(a, st);
+        dw.release(a, st);
+    };
+    if (herr) {
+        cleanup();
+        throw Error(DG_E_INVALID, "sparsifier edge that is not an edge of G");
+    }
+    const uint64_t* keys = k0.p;
+    const uint32_t* vals = v0.p;
+    uint32_t uniq = 0;
+    if (M2) {
+        SortBufs sb{k0.p, v0.p, k1.p, v1.p, hist.p, stmp.p};
+        const int nbits = bit_length((uint64_t)g.n * g.n - 1);
+        if (radix_sort_pairs(sb, nullptr, M2, nbits, st)) {
+            keys = k1.p;
+            vals = v1.p;
+        }
+        k_first_of_run<<<grid_for(M2), BT, 0, st>>>(keys, nullptr, M2, flag.p);
+        ScanJob j;
+        j.in[0] = flag.p;
+        j.out[0] = pos.p;
+        j.total[0] = cnt.p;
+        j.k = 1;
+        scan_exclusive(j, nullptr, M2, stmp.p, st);
+        k_compact_kv<<<grid_for(M2), BT, 0, st>>>(keys, vals, flag.p, pos.p, nullptr, M2, k2.p, v2.p);
+        g_launches += 2;
+        DG_CUDA(cudaMemcpyAsync(&uniq, cnt.p, 4, cudaMemcpyDeviceToHost, st));
+        wait_stream(c, st);
+    }
+    csr_release(g.H, a, st);
+    g.H.slack = (float)c.cfg.slack;
+    g.H.overflow = c.cfg.overflow;
+    csr_alloc_vertices(g.H, a, g.n, st);
+    csr_build(g.H, a, k2.p, v2.p, dw.p, uniq, err.p, st);
+    DG_CUDA(cudaMemcpyAsync(&herr, err.p, 4, cudaMemcpyDeviceToHost, st));
+    wait_stream(c, st);
+    cleanup();
+    if (herr) throw Error(DG_E_CUDA, "internal error while building the sparsifier");
+    g.has_h = true;
+    ++g.layout_gen;
+}
+
+void graph_export(Ctx& c, DGraph& g, bool which_h, int64_t cap, int32_t* u, int32_t* v, double* w,
+                  int64_t* count, cudaStream_t st) {
+    CSR& s = which_h ? g.H : g.G;
+    DevAlloc& a = c.alloc;
+    const uint64_t cnt = csr_edge_count(s, a, st);
+    if (count) *count = (int64_t)cnt;
+    if ((int64_t)cnt > cap) throw Error(DG_E_INVALID, "output arrays too small (count_out holds the size)");
+    if (cnt == 0) return;
+    DBuf<int32_t> da, db;
+    DBuf<double> dw;
+    da.ensure(a, cnt, st);
+    db.ensure(a, cnt, st);
+    dw.ensure(a, cnt, st);
+    csr_export(s, a, da.p, db.p, dw.p, st);
+    if (u) DG_CUDA(cudaMemcpyAsync(u, da.p, 4 * cnt, cudaMemcpyDeviceToHost, st));
+    if (v) DG_CUDA(cudaMemcpyAsync(v, db.p, 4 * cnt, cudaMemcpyDeviceToHost, st));
+    if (w) DG_CUDA(cudaMemcpyAsync(w, dw.p, 8 * cnt, cudaMemcpyDeviceToHost, st));
+    wait_stream(c, st);
+    da.release(a, st);
+    db.release(a, st);
+    dw.release(a, st);
+}
+
+void graph_compact(Ctx& c, DGraph& g, cudaStream_t st) {
+    csr_compact(g.G, c.alloc, 0, st);
+    csr_compact(g.H, c.alloc, 0, st);
+    ++g.layout_gen;
+}
+
+void graph_release(Ctx& c, DGraph& g) {
+    cudaStream_t st = c.stream;
+    cudaStreamSynchronize(st);
+    if (g.stream) cudaStreamSynchronize(g.stream);
+    for (auto& kv : g.steps)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    g.steps.clear();
+    csr_release(g.G, c.alloc, st);
+    csr_release(g.H, c.alloc, st);
+    g.touched.release(c.alloc, st);
+    BatchWS& w = g.ws;
+    w.apG.release(c.alloc, st);
+    w.apH.release(c.alloc, st);
+    w.apC.release(c.alloc, st);
+#define REL(b) w.b.release(c.alloc, st)
+    REL(ups); REL(res); REL(hdr); REL(err); REL(ctr); REL(next); REL(vkeys); REL(vkeys_alt); REL(vvals);
+    REL(vvals_alt); REL(vhist); REL(vscan); REL(wkind); REL(fin_w); REL(wflag); REL(wpos); REL(gkeys);
+    REL(gkeys_alt); REL(hkeys); REL(gvals); REL(gvals_alt); REL(ghist); REL(gscan); REL(gcount); REL(hflag);
+    REL(hpos); REL(hvals); REL(hcount); REL(gkind); REL(ghrem); REL(kind_del); REL(gw); REL(t_u); REL(t_v);
+    REL(t_idx); REL(t_kstar); REL(t_count); REL(meta); REL(t_wpq); REL(recR); REL(t_kind); REL(best);
+    REL(ckeys); REL(ckeys_alt); REL(ck2); REL(cvals); REL(cvals_alt); REL(chist); REL(cscan); REL(ccount);
+    REL(cflag); REL(cpos); REL(cv2); REL(ccount2); REL(cw); REL(kind_ins); REL(path_buf); REL(dbg_reason);
+    REL(dbg_steps); REL(dbg_paths);
+#undef REL
+    w.b_max = 0;
+    w.cand_cap = 0;
+    if (g.hs.ups) cudaFreeHost(g.hs.ups);
+    if (g.hs.res) cudaFreeHost(g.hs.res);
+    if (g.hs.hdr) cudaFreeHost(g.hs.hdr);
+    if (g.hs.err) cudaFreeHost(g.hs.err);
+    if (g.hs.ctr) cudaFreeHost(g.hs.ctr);
+    if (g.hs.tops) cudaFreeHost(g.hs.tops);
+    if (g.hs.counts) cudaFreeHost(g.hs.counts);
+    g.hs = HostStage{};
+    for (int i = 0; i < 4; ++i)
+        if (g.ev[i]) cudaEventDestroy(g.ev[i]);
+    if (g.stream) cudaStreamDestroy(g.stream);
+    g.stream = nullptr;
+    cudaStreamSynchronize(st);
+}
+
+// ---------------------------------------------------------------------------
+// the batch step
+// ---------------------------------------------------------------------------
+struct StepIO {
+    bool host_io;                   // ups/res through the pinned staging buffers
+    const dg_update* d_ups_src;     // device-io: caller's updates (copied outside the graph)
+    bool per_update;                // paper's one-launch-per-update walk form
+};
+
+static WalkTasks tasks_of(BatchWS& w) {
+    WalkTasks t;
+    t.u = w.t_u.p;
+    t.v = w.t_v.p;
+    t.idx = w.t_idx.p;
+    t.wpq = w.t_wpq.p;
+    t.kind = w.t_kind.p;
+    t.kstar = w.t_kstar.p;
+    t.count = w.t_count.p;
+    return t;
+}
+
+static WalkParams params_of(const Config& cfg) {
+    WalkParams p;
+    p.K = cfg.K;
+    p.T = (uint32_t)cfg.T;
+    p.s = (uint32_t)cfg.s;
+    p.early_exit = cfg.early_exit ? 1u : 0u;
+    p.key0 = (uint32_t)cfg.seed;
+    p.key1 = (uint32_t)(cfg.seed >> 32);
+    return p;
+}
+
+static WalkRecs recs_of(Ctx& c, BatchWS& w) {
+    WalkRecs r;
+    r.meta = w.meta.p;
+    r.R = w.recR.p;
+    r.paths = (c.cfg.record && w.dbg_paths.p) ? w.dbg_paths.p : nullptr;
+    return r;
+}
+
+// validation and both mutations (G -> G_b, H -> H'); nothing is written to G
+// or H unless both plans found enough space
+static void enqueue_mutate(Ctx& c, DGraph& g, cudaStream_t st) {
+    BatchWS& w = g.ws;
+    const uint32_t B = w.b_max, B2 = 2 * w.b_max, n = (uint32_t)g.n;
+    DG_CUDA(cudaMemsetAsync(w.err.p, 0, 16, st));
+    DG_CUDA(cudaMemsetAsync(w.ctr.p, 0, sizeof(BatchCounters), st));
+    DG_CUDA(cudaMemsetAsync(w.gcount.p, 0, 4, st));
+    DG_CUDA(cudaMemsetAsync(w.t_kstar.p, 0xFF, 4ull * B, st));
+    const uint32_t* d_nu = &w.hdr.p->nu;
+    k_val_prep<<<grid_for(B), BT, 0, st>>>(w.ups.p, w.hdr.p, n, B, w.res.p, w.vkeys.p, w.vvals.p, w.wkind.p,
+                                          w.fin_w.p);
+    ++g_launches;
+    SortBufs vs{w.vkeys.p, w.vvals.p, w.vkeys_alt.p, w.vvals_alt.p, w.vhist.p, w.vscan.p};
+    const bool valt = radix_sort_pairs(vs, d_nu, B, bit_length((uint64_t)n * n), st);
+    RunArgs ra;
+    ra.keys = valt ? w.vkeys_alt.p : w.vkeys.p;
+    ra.vals = valt ? w.vvals_alt.p : w.vvals.p;
+    ra.ups = w.ups.p;
+    ra.hdr = w.hdr.p;
+    ra.n = n;
+    ra.b_max = B;
+    ra.G = g.G.view();
+    ra.H = g.H.view();
+    ra.res = w.res.p;
+    ra.wkind = w.wkind.p;
+    ra.fin_w = w.fin_w.p;
+    ra.gkeys = w.gkeys.p;
+    ra.gvals = w.gvals.p;
+    ra.gkind = w.gkind.p;
+    ra.ghrem = w.ghrem.p;
+    ra.gw = w.gw.p;
+    ra.gcount = w.gcount.p;
+    ra.ctr = w.ctr.p;
+    k_val_runs<<<grid_for(B), BT, 0, st>>>(ra);
+    k_walk_flags<<<grid_for(B), BT, 0, st>>>(w.wkind.p, w.hdr.p, B, w.wflag.p);
+    g_launches += 2;
+    {
+        ScanJob j;
+        j.in[0] = w.wflag.p;
+        j.out[0] = w.wpos.p;
+        j.total[0] = w.t_count.p;
+        j.k = 1;
+        scan_exclusive(j, d_nu, B, w.vscan.p, st);
+    }
+    WalkTasks tasks = tasks_of(w);
+    k_make_tasks<<<grid_for(B), BT, 0, st>>>(w.ups.p, w.wkind.p, w.wpos.p, w.hdr.p, B, tasks);
+    ++g_launches;
+    // net G changes, sorted by (vertex, neighbour)
+    SortBufs gs{w.gkeys.p, w.gvals.p, w.gkeys_alt.p, w.gvals_alt.p, w.ghist.p, w.gscan.p};
+    const bool galt = radix_sort_pairs(gs, w.gcount.p, B2, bit_length((uint64_t)n * n - 1), st);
+    const uint64_t* gk = galt ? w.gkeys_alt.p : w.gkeys.p;
+    const uint32_t* gv = galt ? w.gvals_alt.p : w.gvals.p;
+    k_flag_hrem<<<grid_for(B2), BT, 0, st>>>(gv, w.ghrem.p, w.gcount.p, B2, w.hflag.p);
+    ++g_launches;
+    {
+        ScanJob j;
+        j.in[0] = w.hflag.p;
+        j.out[0] = w.hpos.p;
+        j.total[0] = w.hcount.p;
+        j.k = 1;
+        scan_exclusive(j, w.gcount.p, B2, w.gscan.p, st);
+    }
+    k_compact_kv<<<grid_for(B2), BT, 0, st>>>(gk, gv, w.hflag.p, w.hpos.p, w.gcount.p, B2, w.hkeys.p, w.hvals.p);
+    ++g_launches;
+    ChangeList clG;
+    clG.keys = gk;
+    clG.vals = gv;
+    clG.kinds = w.gkind.p;
+    clG.ws = w.gw.p;
+    clG.d_count = w.gcount.p;
+    clG.max_count = B2;
+    ChangeList clH;
+    clH.keys = w.hkeys.p;
+    clH.vals = w.hvals.p;
+    clH.kinds = w.kind_del.p;
+    clH.ws = w.gw.p;
+    clH.d_count = w.hcount.p;
+    clH.max_count = B2;
+    // both plans before either execution: an abort leaves G and H untouched
+    csr_plan(g.G, clG, w.apG, w.err.p, ERR_POOL_G, ERR_CAP_PRE, st);
+    csr_plan(g.H, clH, w.apH, w.err.p, ERR_POOL_G, ERR_CAP_PRE, st);
+    csr_exec(g.G, clG, w.apG, g.touched.p, w.err.p, st);
+    csr_exec(g.H, clH, w.apH, g.touched.p, w.err.p, st);
+}
+
+// walks on the snapshot (H' for insertions, G_b for deletions) and the
+// per-update reduction; per_update_W >= 0 selects the one-launch-per-update form
+static void enqueue_walks(Ctx& c, DGraph& g, cudaStream_t st, int64_t per_update_W) {
+    BatchWS& w = g.ws;
+    const WalkParams wp = params_of(c.cfg);
+    const WalkRecs wr = recs_of(c, w);
+    const WalkTasks tasks = tasks_of(w);
+    DG_CUDA(cudaEventRecordWithFlags(g.ev[0], st, cudaEventRecordExternal));
+    if (per_update_W < 0) {
+        launch_walk_batched(g.H.view(), g.G.view(), tasks, wp, wr, w.hdr.p, w.next.p, 0, w.b_max, g.shape,
+                            w.err.p, st);
+    } else {
+        for (int64_t j = 0; j < per_update_W; ++j)
+            launch_walk_one(g.H.view(), g.G.view(), tasks, wp, wr, w.hdr.p, (uint32_t)j, w.err.p, st);
+    }
+    DG_CUDA(cudaEventRecordWithFlags(g.ev[1], st, cudaEventRecordExternal));
+    launch_walk_reduce(tasks, wp, wr, w.res.p, w.best.p, w.ctr.p, c.cfg.record ? w.dbg_reason.p : nullptr,
+                       c.cfg.record ? w.dbg_steps.p : nullptr, w.b_max, w.err.p, st);
+}
+
+// kept insertions, recovered and fallback edges -> H (re-runnable)
+static void enqueue_commit(Ctx& c, DGraph& g, cudaStream_t st) {
+    BatchWS& w = g.ws;
+    const uint32_t B = w.b_max, n = (uint32_t)g.n, CC = w.cand_cap;
+    DG_CUDA(cudaMemsetAsync(w.ccount.p, 0, 4, st));
+    Cands cd;
+    cd.keys = w.ckeys.p;
+    cd.vals = w.cvals.p;
+    cd.w = w.cw.p;
+    cd.count = w.ccount.p;
+    cd.cap = CC;
+    launch_emit(g.H.view(), g.G.view(), tasks_of(w), params_of(c.cfg), recs_of(c, w), w.hdr.p, w.best.p, w.fin_w.p,
+                w.res.p, w.ctr.p, cd, w.path_buf.p, B, w.err.p, st);
+    SortBufs cs{w.ckeys.p, w.cvals.p, w.ckeys_alt.p, w.cvals_alt.p, w.chist.p, w.cscan.p};
+    const bool calt = radix_sort_pairs(cs, w.ccount.p, CC, bit_length((uint64_t)n * n - 1), st);
+    const uint64_t* ck = calt ? w.ckeys_alt.p : w.ckeys.p;
+    const uint32_t* cv = calt ? w.cvals_alt.p : w.cvals.p;
+    k_commit_flags<<<grid_for(CC), BT, 0, st>>>(ck, w.ccount.p, CC, g.H.view(), w.cflag.p, w.err.p);
+    ++g_launches;
+    {
+        ScanJob j;
+        j.in[0] = w.cflag.p;
+        j.out[0] = w.cpos.p;
+        j.total[0] = w.ccount2.p;
+        j.k = 1;
+        scan_exclusive(j, w.ccount.p, CC, w.cscan.p, st);
+    }
+    k_compact_kv<<<grid_for(CC), BT, 0, st>>>(ck, cv, w.cflag.p, w.cpos.p, w.ccount.p, CC, w.ck2.p, w.cv2.p);
+    ++g_launches;
+    ChangeList clC;
+    clC.keys = w.ck2.p;
+    clC.vals = w.cv2.p;
+    clC.kinds = w.kind_ins.p;
+    clC.ws = w.cw.p;
+    clC.d_count = w.ccount2.p;
+    clC.max_count = CC;
+    csr_plan(g.H, clC, w.apC, w.err.p, ERR_POOL_H, ERR_CAP_COMMIT, st);
+    csr_exec(g.H, clC, w.apC, g.touched.p, w.err.p, st);
+}
+
+static void enqueue_readback(DGraph& g, cudaStream_t st) {
+    BatchWS& w = g.ws;
+    DG_CUDA(cudaMemcpyAsync(g.hs.err, w.err.p, 16, cudaMemcpyDeviceToHost, st));
+    DG_CUDA(cudaMemcpyAsync(g.hs.ctr, w.ctr.p, sizeof(BatchCounters), cudaMemcpyDeviceToHost, st));
+    DG_CUDA(cudaMemcpyAsync(g.hs.tops, g.G.top.p, 8, cudaMemcpyDeviceToHost, st));
+    DG_CUDA(cudaMemcpyAsync(g.hs.tops + 1, g.H.top.p, 8, cudaMemcpyDeviceToHost, st));
+    DG_CUDA(cudaMemcpyAsync(g.hs.counts, w.t_count.p, 4, cudaMemcpyDeviceToHost, st));
+    DG_CUDA(cudaMemcpyAsync(g.hs.counts + 1, w.ccount.p, 4, cudaMemcpyDeviceToHost, st));
+}
+
+static uint32_t read_total(ApplyScratch& s, int which, cudaStream_t st) {
+    uint32_t v = 0;
+    DG_CUDA(cudaMemcpyAsync(&v, s.totals.p + which, 4, cudaMemcpyDeviceToHost, st));
+    DG_CUDA(cudaStreamSynchronize(st));
+    return v;
+}
+
+// grow what an abort asked for; returns true when the whole batch must re-run
+static bool handle_abort(Ctx& c, DGraph& g, uint32_t err, cudaStream_t st) {
+    BatchWS& w = g.ws;
+    DevAlloc& a = c.alloc;
+    if (err & (ERR_POOL_G | ERR_CAP_PRE)) {
+        if (err & ERR_POOL_G) {
+            const uint32_t R = read_total(w.apG, TOT_R, st);
+            csr_compact(g.G, a, (uint64_t)R * 2 + 4096, st);
+        }
+        if (err & ERR_CAP_PRE) {
+            const uint64_t s1 = read_total(w.apG, TOT_S, st), s2 = read_total(w.apH, TOT_S, st);
+            w.apG.ensure(a, w.apG.c_max, std::max<uint64_t>(s1 * 2, w.apG.s_cap), st);
+            w.apH.ensure(a, w.apH.c_max, std::max<uint64_t>(s2 * 2, w.apH.s_cap), st);
+        }
+        ++g.layout_gen;
+        return true;
+    }
+    if (err & ERR_POOL_H) {
+        const uint32_t R = read_total(w.apC, TOT_R, st);
+        csr_compact(g.H, a, (uint64_t)R * 2 + 4096, st);
+    }
+    if (err & ERR_CAP_COMMIT) {
+        const uint32_t need = g.hs.counts[1];
+        if (need > w.cand_cap) ensure_cands(c, g, need * 2, st);
+        const uint64_t s3 = read_total(w.apC, TOT_S, st);
+        if (s3 > w.apC.s_cap) w.apC.ensure(a, w.apC.c_max, s3 * 2, st);
+    }
+    ++g.layout_gen;
+    return false;
+}
+
+
+// proactive growth so that most batches never abort
+static void ensure_headroom(Ctx& c, DGraph& g, uint32_t nu, cudaStream_t st) {
+    const uint64_t want = (uint64_t)nu * 64 + 65536;
+    if (g.G.pool_cap - g.G.host_top < want) {
+        csr_compact(g.G, c.alloc, want * 2, st);
+        ++g.layout_gen;
+    }
+    if (g.H.pool_cap - g.H.host_top < want) {
+        csr_compact(g.H, c.alloc, want * 2, st);
+        ++g.layout_gen;
+    }
+}
+
+void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_update_result* res, bool device_io,
+                 cudaStream_t st) {
+    if (!g.has_h) throw Error(DG_E_STATE, "no sparsifier");
+    if (nu64 < 0 || nu64 > (1ll << 26)) throw Error(DG_E_INVALID, "batch size out of range");
+    if (nu64 == 0) return;
+    const uint32_t nu = (uint32_t)nu64;
+    const uint64_t l0 = g_launches;
+    const uint32_t bucket = bucket_of(nu);
+    ensure_ws(c, g, bucket, st);
+    ensure_headroom(c, g, nu, st);
+    BatchWS& w = g.ws;
+    const bool per_update = c.cfg.walk_mode == DG_WALK_PER_UPDATE;
+    g.hs.hdr->nu = nu;
+    g.hs.hdr->pad = 0;
+    g.hs.hdr->id0 = g.next_id;
+    if (!device_io) std::memcpy(g.hs.ups, ups, sizeof(dg_update) * nu);
+
+    auto stage_inputs = [&]() {
+        DG_CUDA(cudaMemcpyAsync(w.hdr.p, g.hs.hdr, sizeof(BatchHdr), cudaMemcpyHostToDevice, st));
+        if (!device_io)
+            DG_CUDA(cudaMemcpyAsync(w.ups.p, g.hs.ups, sizeof(dg_update) * nu, cudaMemcpyHostToDevice, st));
+        else
+            DG_CUDA(cudaMemcpyAsync(w.ups.p, ups, sizeof(dg_update) * nu, cudaMemcpyDeviceToDevice, st));
+    };
+    // eager form of the pre-commit part (validation, mutation, walks, reduction)
+    auto run_pre = [&]() {
+        enqueue_mutate(c, g, st);
+        int64_t W = -1;
+        if (per_update) {  // the per-update form needs the walked count on the host to issue its launches
+            DG_CUDA(cudaMemcpyAsync(g.hs.counts, w.t_count.p, 4, cudaMemcpyDeviceToHost, st));
+            DG_CUDA(cudaMemcpyAsync(g.hs.err, w.err.p, 4, cudaMemcpyDeviceToHost, st));
+            wait_stream(c, st);
+            W = (g.hs.err[0] & ABORT_MASK) ? 0 : g.hs.counts[0];
+            if (g.hs.counts[0] > w.b_max) W = 0;
+        }
+        enqueue_walks(c, g, st, W);
+    };
+    auto finish_eager = [&]() {
+        enqueue_commit(c, g, st);
+        if (!device_io)
+            DG_CUDA(cudaMemcpyAsync(g.hs.res, w.res.p, sizeof(dg_update_result) * nu, cudaMemcpyDeviceToHost, st));
+        enqueue_readback(g, st);
+        DG_CUDA(cudaEventRecordWithFlags(g.ev[3], st, cudaEventRecordExternal));
+        wait_stream(c, st);
+    };
+
+    const bool use_graph = c.cfg.use_graphs && !per_update && !c.cfg.record;
+    bool replayed = false;
+    DG_CUDA(cudaEventRecordWithFlags(g.ev[2], st, cudaEventRecordExternal));
+    if (use_graph) {
+        if (device_io) DG_CUDA(cudaMemcpyAsync(w.ups.p, ups, sizeof(dg_update) * nu, cudaMemcpyDeviceToDevice, st));
+        CapturedStep& cs = g.steps[bucket];
+        if (!cs.exec || cs.layout_gen != g.layout_gen || cs.device_io != device_io) {
+            if (cs.exec) cudaGraphExecDestroy(cs.exec);
+            cs.exec = nullptr;
+            cudaGraph_t graph = nullptr;
+            const uint64_t k0 = g_launches;
+            DG_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            try {
+                DG_CUDA(cudaMemcpyAsync(w.hdr.p, g.hs.hdr, sizeof(BatchHdr), cudaMemcpyHostToDevice, st));
+                if (!device_io)
+                    DG_CUDA(cudaMemcpyAsync(w.ups.p, g.hs.ups, sizeof(dg_update) * bucket, cudaMemcpyHostToDevice, st));
+                enqueue_mutate(c, g, st);
+                enqueue_walks(c, g, st, -1);
+                enqueue_commit(c, g, st);
+                if (!device_io)
+                    DG_CUDA(cudaMemcpyAsync(g.hs.res, w.res.p, sizeof(dg_update_result) * bucket,
+                                            cudaMemcpyDeviceToHost, st));
+                enqueue_readback(g, st);
+            } catch (...) {
+                cudaStreamEndCapture(st, &graph);
+                if (graph) cudaGraphDestroy(graph);
+                throw;
+            }
+            DG_CUDA(cudaStreamEndCapture(st, &graph));
+            DG_CUDA(cudaGraphInstantiate(&cs.exec, graph, 0));
+            cudaGraphDestroy(graph);
+            cs.layout_gen = g.layout_gen;
+            cs.device_io = device_io;
+            cs.kernels = g_launches - k0;
+            g_launches = k0;  // counted per replay below
+        }
+        DG_CUDA(cudaGraphLaunch(cs.exec, st));
+        g_launches += cs.kernels;
+        DG_CUDA(cudaEventRecordWithFlags(g.ev[3], st, cudaEventRecordExternal));
+        wait_stream(c, st);
+        replayed = true;
+    } else {
+        stage_inputs();
+        run_pre();
+        finish_eager();
+    }
+    int64_t retries = 0;
+    for (;;) {
+        const uint32_t err = g.hs.err[0];
+        if (err & ERR_INTERNAL) throw Error(DG_E_CUDA, "internal consistency check failed on the device");
+        if (!(err & ABORT_MASK)) break;
+        if (++retries > 8) throw Error(DG_E_NOMEM, "batch could not get enough device memory");
+        const bool whole = handle_abort(c, g, err, st);
+        DG_CUDA(cudaEventRecordWithFlags(g.ev[2], st, cudaEventRecordExternal));
+        if (whole) {
+            stage_inputs();
+            run_pre();
+        } else {  // only the commit re-runs; walks and their results are kept
+            DG_CUDA(cudaMemsetAsync(w.err.p, 0, 16, st));
+            DG_CUDA(cudaMemsetAsync(&w.ctr.p->recovered, 0, sizeof(unsigned long long), st));
+        }
+        finish_eager();
+        replayed = false;
+    }
+    if (res) {
+        if (device_io) {
+            DG_CUDA(cudaMemcpyAsync(res, w.res.p, sizeof(dg_update_result) * nu, cudaMemcpyDeviceToDevice, st));
+            wait_stream(c, st);
+        } else {
+            std::memcpy(res, g.hs.res, sizeof(dg_update_result) * nu);
+        }
+    }
+    g.G.host_top = g.hs.tops[0];
+    g.H.host_top = g.hs.tops[1];
+    g.next_id += nu;
+    dg_batch_stats& s = g.stats;
+    s.updates = nu;
+    s.valid = (int64_t)g.hs.ctr->valid;
+    s.walked = (int64_t)g.hs.ctr->walked;
+    s.steps = (int64_t)g.hs.ctr->steps;
+    s.accepted = (int64_t)g.hs.ctr->accepted;
+    s.recovered = (int64_t)g.hs.ctr->recovered;
+    float ms = 0.f;
+    s.walk_ms = (cudaEventElapsedTime(&ms, g.ev[0], g.ev[1]) == cudaSuccess) ? ms : -1.0;
+    s.batch_ms = (cudaEventElapsedTime(&ms, g.ev[2], g.ev[3]) == cudaSuccess) ? ms : -1.0;
+    cudaGetLastError();
+    s.retries = retries;
+    s.graph_replayed = replayed ? 1 : 0;
+    s.walk_block = g.shape.block;
+    s.walk_ilp = g.shape.ilp;
+    s.walk_blocks_per_sm = g.shape.blocks_per_sm;
+    s.walk_launches = per_update ? (int64_t)g.hs.counts[0] : 1;
+    const uint64_t dl = g_launches - l0;
+    s.launches = (int64_t)dl;
+    c.launches += dl;
+}
+
+}  // namespace dg

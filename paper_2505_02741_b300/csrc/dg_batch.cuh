@@ -1,0 +1,117 @@
+// dg_batch.cuh -- one resident dynamic graph (G, H in slack-slot CSRs) and
+// the batch step of Algorithm 1 under the batch-snapshot semantics.
+#pragma once
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "dg_csr.cuh"
+#include "dg_walk.cuh"
+
+namespace dg {
+
+struct Config {
+    uint64_t seed = 0;
+    double K = 100.0;
+    int32_t T = 100;
+    int32_t s = 32;
+    int32_t early_exit = 1;
+    int32_t walk_mode = DG_WALK_BATCHED;
+    double slack = 1.25;
+    double overflow = 0.5;
+    uint64_t budget = 0;
+    int32_t autotune = 1;
+    int32_t timeout_ms = 60000;
+    int32_t use_graphs = 1;
+    int32_t record = 0;
+};
+
+// device workspace for batches of at most b_max updates
+struct BatchWS {
+    uint32_t b_max = 0;
+    uint32_t cand_cap = 0;
+    DBuf<dg_update> ups;
+    DBuf<dg_update_result> res;
+    DBuf<BatchHdr> hdr;
+    DBuf<uint32_t> err;
+    DBuf<BatchCounters> ctr;
+    DBuf<unsigned long long> next;
+    // validation
+    DBuf<uint64_t> vkeys, vkeys_alt;
+    DBuf<uint32_t> vvals, vvals_alt, vhist, vscan;
+    DBuf<uint8_t> wkind;
+    DBuf<double> fin_w;
+    DBuf<uint32_t> wflag, wpos;
+    // G changes (and the H removals among them)
+    DBuf<uint64_t> gkeys, gkeys_alt, hkeys;
+    DBuf<uint32_t> gvals, gvals_alt, ghist, gscan, gcount, hflag, hpos, hvals, hcount;
+    DBuf<uint8_t> gkind, ghrem, kind_del;
+    DBuf<double> gw;
+    // walks
+    DBuf<uint32_t> t_u, t_v, t_idx, t_kstar, t_count, meta;
+    DBuf<double> t_wpq, recR;
+    DBuf<uint8_t> t_kind;
+    DBuf<int32_t> best;
+    // commit
+    DBuf<uint64_t> ckeys, ckeys_alt, ck2;
+    DBuf<uint32_t> cvals, cvals_alt, chist, cscan, ccount, cflag, cpos, cv2, ccount2;
+    DBuf<double> cw;
+    DBuf<uint8_t> kind_ins;
+    DBuf<uint32_t> path_buf;
+    // debug
+    DBuf<int32_t> dbg_reason, dbg_steps, dbg_paths;
+    ApplyScratch apG, apH, apC;
+    uint64_t bytes() const;
+};
+
+struct HostStage {  // pinned staging for host-API batches
+    dg_update* ups = nullptr;
+    dg_update_result* res = nullptr;
+    BatchHdr* hdr = nullptr;
+    uint32_t* err = nullptr;
+    BatchCounters* ctr = nullptr;
+    unsigned long long* tops = nullptr;  // [G top, H top]
+    uint32_t* counts = nullptr;          // [W, ccount]
+    size_t cap = 0;
+};
+
+struct CapturedStep {
+    cudaGraphExec_t exec = nullptr;
+    uint64_t layout_gen = 0;
+    bool device_io = false;
+    uint64_t kernels = 0;  // kernel nodes in the captured step
+};
+
+struct DGraph {
+    int32_t id = 0;
+    int32_t n = 0;
+    CSR G, H;
+    bool has_h = false;
+    uint64_t next_id = 0;
+    DBuf<uint8_t> touched;
+    BatchWS ws;
+    HostStage hs;
+    WalkShape shape;
+    bool tuned = false;
+    uint64_t layout_gen = 1;  // bumped whenever a buffer baked into a captured step moves
+    std::map<uint32_t, CapturedStep> steps;  // by batch-size class
+    cudaStream_t stream = nullptr;           // private stream (serving)
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    dg_batch_stats stats{};
+    std::mutex mu;
+    uint64_t bytes() const { return G.bytes() + H.bytes() + touched.bytes() + ws.bytes(); }
+};
+
+struct Ctx;  // context (dg_api.cu)
+
+// batch entry points (stream = caller stream or the context stream)
+void graph_load(Ctx& c, DGraph& g, int32_t n, int64_t m, const int32_t* u, const int32_t* v, const double* w);
+void graph_init_h(Ctx& c, DGraph& g, int64_t mh, const int32_t* u, const int32_t* v);
+void graph_apply(Ctx& c, DGraph& g, int64_t nu, const dg_update* ups, dg_update_result* res, bool device_io,
+                 cudaStream_t st);
+void graph_release(Ctx& c, DGraph& g);
+void graph_compact(Ctx& c, DGraph& g, cudaStream_t st);
+void graph_export(Ctx& c, DGraph& g, bool which_h, int64_t cap, int32_t* u, int32_t* v, double* w,
+                  int64_t* count, cudaStream_t st);
+
+}  // namespace dg

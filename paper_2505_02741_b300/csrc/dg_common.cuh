@@ -1,0 +1,146 @@
+// dg_common.cuh -- device types and helpers shared by the dyGRASS CUDA kernels.
+//
+// Slack-slot CSR (generalises the dynamic CSR of Section III-F, Fig. 4):
+//   per vertex x:  off[x]  first entry of x's adjacency list in the pool
+//                  deg[x]  number of neighbours
+//                  cap[x]  slots reserved at off[x] (deg <= cap)
+//   pool:          32-byte entries, each list sorted by ascending neighbour id.
+// Each entry caches the neighbour's (off, deg) and the position of x inside the
+// neighbour's list, so one walk step is one dependent 32-byte load: the entry
+// just read names the next list and where the previous vertex sits in it,
+// which is all the non-backtracking pick (Section III-B) needs.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dg {
+
+struct __align__(32) Ent {
+    uint32_t nbr;   // neighbour id
+    uint32_t noff;  // off[nbr] (cached)
+    uint32_t ndeg;  // deg[nbr] (cached)
+    uint32_t rev;   // position of this list's owner inside nbr's list
+    double r;       // resistance 1 / w (Section II-A, computed once, IEEE RN)
+    double w;       // weight
+};
+static_assert(sizeof(Ent) == 32, "entry must be one 32-byte sector");
+
+// device view of one slack-slot CSR
+struct CSRView {
+    uint32_t* off;
+    uint32_t* deg;
+    uint32_t* cap;
+    Ent* pool;
+    unsigned long long* top;  // entries in use (bump pointer)
+    uint64_t pool_cap;        // entries allocated
+    int32_t n;
+};
+
+// change kinds applied to a CSR
+enum : uint8_t { CHG_INS = 0, CHG_DEL = 1, CHG_SETW = 2 };
+
+// per-update status codes (mirror of the C ABI)
+enum : int32_t {
+    ST_OK = 0, ST_SELF_LOOP = 1, ST_BAD_VERTEX = 2, ST_DUP_INSERT = 3,
+    ST_MISSING_DELETE = 4, ST_BAD_WEIGHT = 5, ST_BAD_OP = 6
+};
+enum : uint8_t { WALK_NONE = 0, WALK_INS = 1, WALK_DEL = 2 };
+
+// abort / error bits raised on the device and read back by the host
+enum : uint32_t {
+    ERR_POOL_G = 1u << 0,       // G pool short before any write (batch retried after growth)
+    ERR_POOL_H = 1u << 1,       // H pool short at commit (commit retried after growth)
+    ERR_BAD_INPUT = 1u << 2,    // load/init input invalid
+    ERR_DUP_EDGE = 1u << 3,     // load input has a repeated edge
+    ERR_NOT_IN_G = 1u << 4,     // init-sparsifier edge missing from G
+    ERR_CAP_PRE = 1u << 5,      // staging space short before the walks (batch retried)
+    ERR_CAP_COMMIT = 1u << 6,   // candidate / staging space short at commit (commit retried)
+    ERR_INTERNAL = 1u << 7,     // consistency check failed (lookup of an edge that must exist)
+};
+constexpr uint32_t ABORT_MASK = ERR_POOL_G | ERR_POOL_H | ERR_CAP_PRE | ERR_CAP_COMMIT;
+
+__host__ __device__ inline uint32_t cap_for(uint32_t d, float slack) {
+    if (d == 0) return 0;
+    uint32_t extra = (uint32_t)((double)d * (double)(slack - 1.0f) + 0.999999);
+    if (extra < 2) extra = 2;
+    return d + extra;
+}
+
+// -------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Counter words
+// (c0, c1, c2, c3), key (k0, k1); returns output word 0.
+// -------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t philox_word0(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                 uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int rnd = 0; rnd < 10; ++rnd) {
+        const uint32_t m0lo = 0xD2511F53u * c0;
+        const uint32_t m0hi = __umulhi(0xD2511F53u, c0);
+        const uint32_t m1lo = 0xCD9E8D57u * c2;
+        const uint32_t m1hi = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t t0 = m1hi ^ c1 ^ k0;
+        const uint32_t t2 = m0hi ^ c3 ^ k1;
+        c0 = t0;
+        c1 = m1lo;
+        c2 = t2;
+        c3 = m0lo;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c0;
+}
+
+// 128-bit loads of an entry (two halves of the sector)
+__device__ __forceinline__ void load_ent(const Ent* p, uint4& head, double2& tail) {
+    const uint4* q = reinterpret_cast<const uint4*>(p);
+    head = __ldg(q);
+    tail = __ldg(reinterpret_cast<const double2*>(q + 1));
+}
+
+// first position in list L[0..d) whose neighbour id >= y
+__device__ __forceinline__ uint32_t lower_bound_nbr(const Ent* L, uint32_t d, uint32_t y) {
+    uint32_t lo = 0, hi = d;
+    while (lo < hi) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (L[mid].nbr < y) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// position of y in x's list or 0xFFFFFFFF
+__device__ __forceinline__ uint32_t find_nbr(const CSRView& g, uint32_t x, uint32_t y) {
+    const Ent* L = g.pool + g.off[x];
+    const uint32_t d = g.deg[x];
+    const uint32_t p = lower_bound_nbr(L, d, y);
+    return (p < d && L[p].nbr == y) ? p : 0xFFFFFFFFu;
+}
+
+// edge membership using the shorter of the two lists
+__device__ __forceinline__ bool has_edge(const CSRView& g, uint32_t a, uint32_t b, double* w = nullptr) {
+    uint32_t x = a, y = b;
+    if (g.deg[b] < g.deg[a]) { x = b; y = a; }
+    const uint32_t p = find_nbr(g, x, y);
+    if (p == 0xFFFFFFFFu) return false;
+    if (w) *w = g.pool[g.off[x] + p].w;
+    return true;
+}
+
+// first index i in [lo, hi) of a sorted array with a[i] > key (upper bound)
+template <typename T>
+__device__ __forceinline__ uint32_t upper_bound_arr(const T* a, uint32_t lo, uint32_t hi, T key) {
+    while (lo < hi) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (a[mid] <= key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+template <typename T>
+__device__ __forceinline__ uint32_t lower_bound_arr(const T* a, uint32_t lo, uint32_t hi, T key) {
+    while (lo < hi) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (a[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+}  // namespace dg

@@ -1,0 +1,581 @@
+// dg_csr.cu -- slack-slot CSR kernels (see dg_csr.cuh).
+#include "dg_csr.cuh"
+
+namespace dg {
+
+static int g_num_sms = 0;
+
+int flat_grid() {
+    if (g_num_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 148;
+    }
+    return g_num_sms * 8;
+}
+
+constexpr int FLAT_THREADS = 256;
+
+__device__ __forceinline__ bool aborted(const uint32_t* d_err) { return (*d_err & ABORT_MASK) != 0u; }
+
+__device__ __forceinline__ uint32_t count_of(const uint32_t* d_count, uint32_t max_count) {
+    return min(*d_count, max_count);
+}
+
+__device__ __forceinline__ uint64_t ent_key_u64(uint32_t x, uint32_t y, uint32_t n) {
+    return (uint64_t)x * (uint64_t)n + (uint64_t)y;
+}
+
+// ---------------------------------------------------------------------------
+// scratch management
+// ---------------------------------------------------------------------------
+void ApplyScratch::ensure(DevAlloc& a, uint32_t changes, uint64_t stage_entries, cudaStream_t st) {
+    if (changes > c_max || !f_head.p) {
+        uint32_t c = changes < 1024 ? 1024 : changes;
+        DBuf<uint32_t>* bufs[] = {&f_head, &f_ins, &f_del, &p_head, &p_ins, &p_del, &tv, &tstart, &tend,
+                                  &odeg, &ndeg, &ooff, &ncap, &rsz, &work, &r_off, &s_off, &w_off};
+        for (auto* b : bufs) b->ensure(a, (size_t)c + 1, st);
+        scan_tmp.ensure(a, scan_tmp_words(c + 1), st);
+        c_max = c;
+    }
+    totals.ensure(a, 2 * TOT_WORDS, st);
+    if (stage_entries > s_cap || !stage.p) {
+        uint64_t e = stage_entries < 4096 ? 4096 : stage_entries;
+        stage.ensure(a, e, st);
+        s_cap = e;
+    }
+}
+
+void ApplyScratch::release(DevAlloc& a, cudaStream_t st) {
+    DBuf<uint32_t>* bufs[] = {&f_head, &f_ins, &f_del, &p_head, &p_ins, &p_del, &tv, &tstart, &tend,
+                              &odeg, &ndeg, &ooff, &ncap, &rsz, &work, &r_off, &s_off, &w_off,
+                              &scan_tmp, &totals};
+    for (auto* b : bufs) b->release(a, st);
+    stage.release(a, st);
+    c_max = 0;
+    s_cap = 0;
+}
+
+uint64_t ApplyScratch::bytes() const {
+    return 18ull * (c_max + 1) * 4 + scan_tmp.bytes() + totals.bytes() + stage.bytes();
+}
+
+void csr_alloc_vertices(CSR& g, DevAlloc& a, int32_t n, cudaStream_t st) {
+    g.n = n;
+    g.off.ensure(a, (size_t)n + 1, st);
+    g.deg.ensure(a, (size_t)n + 1, st);
+    g.cap.ensure(a, (size_t)n + 1, st);
+    g.top.ensure(a, 1, st);
+    DG_CUDA(cudaMemsetAsync(g.off.p, 0, g.off.bytes(), st));
+    DG_CUDA(cudaMemsetAsync(g.deg.p, 0, g.deg.bytes(), st));
+    DG_CUDA(cudaMemsetAsync(g.cap.p, 0, g.cap.bytes(), st));
+    DG_CUDA(cudaMemsetAsync(g.top.p, 0, g.top.bytes(), st));
+}
+
+void csr_release(CSR& g, DevAlloc& a, cudaStream_t st) {
+    g.off.release(a, st);
+    g.deg.release(a, st);
+    g.cap.release(a, st);
+    g.pool.release(a, st);
+    g.top.release(a, st);
+    g.pool_cap = 0;
+    g.n = 0;
+}
+
+// ---------------------------------------------------------------------------
+// build from sorted unique half-edges
+// ---------------------------------------------------------------------------
+__global__ void k_build_deg(const uint64_t* __restrict__ keys, uint32_t count, uint32_t n,
+                            uint32_t* __restrict__ deg, uint32_t* d_err) {
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < count; c += gridDim.x * blockDim.x) {
+        const uint64_t k = keys[c];
+        const uint32_t x = (uint32_t)(k / n);
+        if (c > 0 && keys[c - 1] == k) atomicOr(d_err, (uint32_t)ERR_DUP_EDGE);
+        if (c == 0 || (uint32_t)(keys[c - 1] / n) != x) {
+            const uint32_t e = lower_bound_arr<uint64_t>(keys, c, count, (uint64_t)(x + 1) * n);
+            deg[x] = e - c;
+        }
+    }
+}
+
+__global__ void k_caps(const uint32_t* __restrict__ deg, uint32_t n, float slack, uint32_t* __restrict__ cap) {
+    for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x)
+        cap[x] = cap_for(deg[x], slack);
+}
+
+__global__ void k_build_fill(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                             const double* __restrict__ ws, uint32_t count, uint32_t n,
+                             const uint32_t* __restrict__ off, Ent* __restrict__ pool) {
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < count; c += gridDim.x * blockDim.x) {
+        const uint64_t k = keys[c];
+        const uint32_t x = (uint32_t)(k / n), y = (uint32_t)(k % n);
+        const uint32_t s0 = lower_bound_arr<uint64_t>(keys, 0, c, (uint64_t)x * n);
+        const double w = ws[vals[c]];
+        Ent e;
+        e.nbr = y;
+        e.noff = 0;
+        e.ndeg = 0;
+        e.rev = 0;
+        e.w = w;
+        e.r = __ddiv_rn(1.0, w);
+        pool[off[x] + (c - s0)] = e;
+    }
+}
+
+// refresh (noff, ndeg, rev) of every entry listed by the sorted key array
+__global__ void k_build_fix(const uint64_t* __restrict__ keys, uint32_t count, uint32_t n, CSRView g,
+                            uint32_t* d_err) {
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < count; c += gridDim.x * blockDim.x) {
+        const uint64_t k = keys[c];
+        const uint32_t x = (uint32_t)(k / n), y = (uint32_t)(k % n);
+        const uint32_t s0 = lower_bound_arr<uint64_t>(keys, 0, c, (uint64_t)x * n);
+        const uint32_t ly = g.off[y], dy = g.deg[y];
+        const uint32_t p = lower_bound_nbr(g.pool + ly, dy, x);
+        if (p >= dy || g.pool[ly + p].nbr != x) {
+            atomicOr(d_err, (uint32_t)ERR_INTERNAL);
+            continue;
+        }
+        uint4 h = make_uint4(y, ly, dy, p);
+        *reinterpret_cast<uint4*>(g.pool + g.off[x] + (c - s0)) = h;
+    }
+}
+
+void csr_build(CSR& g, DevAlloc& a, const uint64_t* keys, const uint32_t* vals, const double* ws,
+               uint32_t count, uint32_t* d_err, cudaStream_t st) {
+    const uint32_t n = (uint32_t)g.n;
+    const int grid = flat_grid();
+    DG_CUDA(cudaMemsetAsync(g.deg.p, 0, g.deg.bytes(), st));
+    if (count > 0) {
+        k_build_deg<<<grid, FLAT_THREADS, 0, st>>>(keys, count, n, g.deg.p, d_err);
+        ++g_launches;
+    }
+    k_caps<<<grid, FLAT_THREADS, 0, st>>>(g.deg.p, n, g.slack, g.cap.p);
+    ++g_launches;
+    DBuf<uint32_t> tmp, total;
+    tmp.ensure(a, scan_tmp_words(n + 1), st);
+    total.ensure(a, 2, st);
+    ScanJob job;
+    job.in[0] = g.cap.p;
+    job.out[0] = g.off.p;
+    job.total[0] = total.p;
+    job.k = 1;
+    scan_exclusive(job, nullptr, n, tmp.p, st);
+    uint32_t h_total = 0;
+    DG_CUDA(cudaMemcpyAsync(&h_total, total.p, 4, cudaMemcpyDeviceToHost, st));
+    DG_CUDA(cudaStreamSynchronize(st));
+    tmp.release(a, st);
+    total.release(a, st);
+    const uint64_t want = (uint64_t)h_total + (uint64_t)((double)h_total * g.overflow) + 4096;
+    if (want >= 0xFFFFFFF0ull) throw Error(DG_E_NOMEM, "graph too large for 32-bit pool offsets");
+    g.pool.release(a, st);
+    g.pool.ensure(a, want, st);
+    g.pool_cap = want;
+    unsigned long long t = h_total;
+    DG_CUDA(cudaMemcpyAsync(g.top.p, &t, sizeof(t), cudaMemcpyHostToDevice, st));
+    g.host_top = h_total;
+    if (count > 0) {
+        k_build_fill<<<grid, FLAT_THREADS, 0, st>>>(keys, vals, ws, count, n, g.off.p, g.pool.p);
+        k_build_fix<<<grid, FLAT_THREADS, 0, st>>>(keys, count, n, g.view(), d_err);
+        g_launches += 2;
+    }
+    DG_CHECK_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------
+// plan
+// ---------------------------------------------------------------------------
+__global__ void k_plan_flags(ChangeList cl, uint32_t n, uint32_t* __restrict__ f_head,
+                             uint32_t* __restrict__ f_ins, uint32_t* __restrict__ f_del, const uint32_t* d_err) {
+    if (aborted(d_err)) return;
+    const uint32_t count = count_of(cl.d_count, cl.max_count);
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < count; c += gridDim.x * blockDim.x) {
+        const uint32_t x = (uint32_t)(cl.keys[c] / n);
+        f_head[c] = (c == 0 || (uint32_t)(cl.keys[c - 1] / n) != x) ? 1u : 0u;
+        const uint8_t kd = cl.kinds[cl.vals[c]];
+        f_ins[c] = kd == CHG_INS;
+        f_del[c] = kd == CHG_DEL;
+    }
+}
+
+struct PlanArgs {
+    ChangeList cl;
+    CSRView g;
+    uint32_t n;
+    float slack;
+    const uint32_t *p_head, *p_ins, *p_del, *totals;
+    uint32_t *tv, *tstart, *tend, *odeg, *ndeg, *ooff, *ncap, *rsz, *work;
+};
+
+__device__ __forceinline__ uint32_t pre_at(const uint32_t* p, uint32_t c, uint32_t count, uint32_t total) {
+    return c < count ? p[c] : total;
+}
+
+__global__ void k_plan_touch(PlanArgs a, const uint32_t* d_err) {
+    if (aborted(d_err)) return;
+    const uint32_t count = count_of(a.cl.d_count, a.cl.max_count);
+    const uint32_t NI = a.totals[TOT_NI], ND = a.totals[TOT_ND];
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < count; c += gridDim.x * blockDim.x) {
+        const uint32_t x = (uint32_t)(a.cl.keys[c] / a.n);
+        if (!(c == 0 || (uint32_t)(a.cl.keys[c - 1] / a.n) != x)) continue;
+        const uint32_t t = a.p_head[c];
+        const uint32_t e = lower_bound_arr<uint64_t>(a.cl.keys, c, count, (uint64_t)(x + 1) * a.n);
+        const uint32_t ins = pre_at(a.p_ins, e, count, NI) - a.p_ins[c];
+        const uint32_t del = pre_at(a.p_del, e, count, ND) - a.p_del[c];
+        const uint32_t od = a.g.deg[x];
+        const uint32_t nd = od + ins - del;
+        const uint32_t oc = a.g.cap[x];
+        const bool reloc = nd > oc;
+        const uint32_t nc = reloc ? cap_for(nd, a.slack) : oc;
+        a.tv[t] = x;
+        a.tstart[t] = c;
+        a.tend[t] = e;
+        a.odeg[t] = od;
+        a.ndeg[t] = nd;
+        a.ooff[t] = a.g.off[x];
+        a.ncap[t] = nc;
+        a.rsz[t] = reloc ? nc : 0u;
+        a.work[t] = od + (e - c);
+    }
+}
+
+__global__ void k_plan_alloc(CSRView g, uint32_t* totals, uint64_t stage_cap, uint32_t* d_err,
+                             uint32_t pool_bit, uint32_t cap_bit) {
+    if (aborted(d_err)) return;
+    const unsigned long long base = *g.top;
+    const uint64_t R = totals[TOT_R];
+    const uint64_t S = totals[TOT_S];
+    totals[TOT_BASE_LO] = (uint32_t)base;
+    totals[TOT_BASE_HI] = (uint32_t)(base >> 32);
+    if (base + R > g.pool_cap) atomicOr(d_err, pool_bit);
+    else if (S > stage_cap) atomicOr(d_err, cap_bit);
+}
+
+void csr_plan(CSR& g, const ChangeList& cl, ApplyScratch& s, uint32_t* d_err, uint32_t pool_bit,
+              uint32_t cap_bit, cudaStream_t st) {
+    const int grid = flat_grid();
+    const uint32_t C = cl.max_count;
+    uint32_t* tot = s.totals.p;
+    k_plan_flags<<<grid, FLAT_THREADS, 0, st>>>(cl, (uint32_t)g.n, s.f_head.p, s.f_ins.p, s.f_del.p, d_err);
+    ++g_launches;
+    ScanJob j1;
+    j1.in[0] = s.f_head.p; j1.out[0] = s.p_head.p; j1.total[0] = tot + TOT_X;
+    j1.in[1] = s.f_ins.p;  j1.out[1] = s.p_ins.p;  j1.total[1] = tot + TOT_NI;
+    j1.in[2] = s.f_del.p;  j1.out[2] = s.p_del.p;  j1.total[2] = tot + TOT_ND;
+    j1.k = 3;
+    scan_exclusive(j1, cl.d_count, C, s.scan_tmp.p, st);
+    PlanArgs pa;
+    pa.cl = cl;
+    pa.g = g.view();
+    pa.n = (uint32_t)g.n;
+    pa.slack = g.slack;
+    pa.p_head = s.p_head.p; pa.p_ins = s.p_ins.p; pa.p_del = s.p_del.p; pa.totals = tot;
+    pa.tv = s.tv.p; pa.tstart = s.tstart.p; pa.tend = s.tend.p; pa.odeg = s.odeg.p; pa.ndeg = s.ndeg.p;
+    pa.ooff = s.ooff.p; pa.ncap = s.ncap.p; pa.rsz = s.rsz.p; pa.work = s.work.p;
+    k_plan_touch<<<grid, FLAT_THREADS, 0, st>>>(pa, d_err);
+    ++g_launches;
+    ScanJob j2;
+    j2.in[0] = s.rsz.p;  j2.out[0] = s.r_off.p; j2.total[0] = tot + TOT_R;
+    j2.in[1] = s.ndeg.p; j2.out[1] = s.s_off.p; j2.total[1] = tot + TOT_S;
+    j2.in[2] = s.work.p; j2.out[2] = s.w_off.p; j2.total[2] = tot + TOT_WK;
+    j2.k = 3;
+    scan_exclusive(j2, tot + TOT_X, C, s.scan_tmp.p, st);
+    k_plan_alloc<<<1, 1, 0, st>>>(g.view(), tot, s.s_cap, d_err, pool_bit, cap_bit);
+    ++g_launches;
+    DG_CHECK_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------
+// execute
+// ---------------------------------------------------------------------------
+struct ExecArgs {
+    ChangeList cl;
+    CSRView g;
+    uint32_t n;
+    const uint32_t *p_ins, *p_del, *totals;
+    const uint32_t *tv, *tstart, *tend, *odeg, *ndeg, *ooff, *ncap, *rsz, *r_off, *s_off, *w_off;
+    Ent* stage;
+    uint8_t* touched;
+};
+
+__device__ __forceinline__ uint64_t base_of(const uint32_t* totals) {
+    return (uint64_t)totals[TOT_BASE_LO] | ((uint64_t)totals[TOT_BASE_HI] << 32);
+}
+
+__device__ __forceinline__ uint32_t dst_off(const ExecArgs& a, uint32_t t) {
+    return a.rsz[t] ? (uint32_t)(base_of(a.totals) + a.r_off[t]) : a.ooff[t];
+}
+
+__global__ void k_exec_meta(ExecArgs a, const uint32_t* d_err) {
+    if (aborted(d_err)) return;
+    const uint32_t X = a.totals[TOT_X];
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        *a.g.top = (unsigned long long)(base_of(a.totals) + a.totals[TOT_R]);
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < X; t += gridDim.x * blockDim.x) {
+        const uint32_t x = a.tv[t];
+        a.g.off[x] = dst_off(a, t);
+        a.g.deg[x] = a.ndeg[t];
+        a.g.cap[x] = a.ncap[t];
+        a.touched[x] = 1;
+    }
+}
+
+// merge: one thread per (old entry | change) of every touched vertex
+__global__ void k_exec_merge(ExecArgs a, uint32_t* d_err) {
+    if (aborted(d_err)) return;
+    const uint32_t X = a.totals[TOT_X];
+    const uint32_t WK = a.totals[TOT_WK];
+    const uint32_t count = count_of(a.cl.d_count, a.cl.max_count);
+    const uint32_t NI = a.totals[TOT_NI], ND = a.totals[TOT_ND];
+    for (uint32_t item = blockIdx.x * blockDim.x + threadIdx.x; item < WK; item += gridDim.x * blockDim.x) {
+        const uint32_t t = upper_bound_arr<uint32_t>(a.w_off, 0, X, item) - 1;
+        const uint32_t local = item - a.w_off[t];
+        const uint32_t x = a.tv[t];
+        const uint32_t s0 = a.tstart[t], s1 = a.tend[t];
+        const uint32_t od = a.odeg[t];
+        const Ent* L = a.g.pool + a.ooff[t];
+        uint32_t outpos;
+        Ent out;
+        if (local < od) {
+            out = L[local];
+            const uint64_t key = ent_key_u64(x, out.nbr, a.n);
+            const uint32_t c0 = lower_bound_arr<uint64_t>(a.cl.keys, s0, s1, key);
+            const bool found = c0 < s1 && a.cl.keys[c0] == key;
+            uint8_t kd = 255;
+            if (found) kd = a.cl.kinds[a.cl.vals[c0]];
+            if (kd == CHG_DEL) continue;
+            if (kd == CHG_INS) {  // insertion of a present edge: inconsistent input
+                atomicOr(d_err, (uint32_t)ERR_INTERNAL);
+                continue;
+            }
+            const uint32_t ib = pre_at(a.p_ins, c0, count, NI) - a.p_ins[s0];
+            const uint32_t db = pre_at(a.p_del, c0, count, ND) - a.p_del[s0];
+            outpos = local + ib - db;
+            if (kd == CHG_SETW) {
+                const double w = a.cl.ws[a.cl.vals[c0]];
+                out.w = w;
+                out.r = __ddiv_rn(1.0, w);
+            }
+        } else {
+            const uint32_t c = s0 + (local - od);
+            if (a.cl.kinds[a.cl.vals[c]] != CHG_INS) continue;
+            const uint32_t y = (uint32_t)(a.cl.keys[c] - (uint64_t)x * a.n);
+            const uint32_t lb = lower_bound_nbr(L, od, y);
+            if (lb < od && L[lb].nbr == y) {
+                atomicOr(d_err, (uint32_t)ERR_INTERNAL);
+                continue;
+            }
+            const uint32_t ib = a.p_ins[c] - a.p_ins[s0];
+            const uint32_t db = a.p_del[c] - a.p_del[s0];
+            outpos = lb + ib - db;
+            const double w = a.cl.ws[a.cl.vals[c]];
+            out.nbr = y;
+            out.noff = 0;
+            out.ndeg = 0;
+            out.rev = 0;
+            out.w = w;
+            out.r = __ddiv_rn(1.0, w);
+        }
+        if (outpos >= a.ndeg[t]) {
+            atomicOr(d_err, (uint32_t)ERR_INTERNAL);
+            continue;
+        }
+        a.stage[a.s_off[t] + outpos] = out;
+    }
+}
+
+__global__ void k_exec_place(ExecArgs a, const uint32_t* d_err) {
+    if (aborted(d_err)) return;
+    const uint32_t X = a.totals[TOT_X];
+    const uint32_t S = a.totals[TOT_S];
+    for (uint32_t item = blockIdx.x * blockDim.x + threadIdx.x; item < S; item += gridDim.x * blockDim.x) {
+        const uint32_t t = upper_bound_arr<uint32_t>(a.s_off, 0, X, item) - 1;
+        const uint32_t local = item - a.s_off[t];
+        a.g.pool[dst_off(a, t) + local] = a.stage[item];
+    }
+}
+
+__global__ void k_exec_fix(ExecArgs a, uint32_t* d_err) {
+    if (aborted(d_err)) return;
+    const uint32_t X = a.totals[TOT_X];
+    const uint32_t S = a.totals[TOT_S];
+    for (uint32_t item = blockIdx.x * blockDim.x + threadIdx.x; item < S; item += gridDim.x * blockDim.x) {
+        const uint32_t t = upper_bound_arr<uint32_t>(a.s_off, 0, X, item) - 1;
+        const uint32_t local = item - a.s_off[t];
+        const uint32_t x = a.tv[t];
+        const uint32_t lx = a.g.off[x];
+        const uint32_t y = a.g.pool[lx + local].nbr;
+        if (y >= a.n) {
+            atomicOr(d_err, (uint32_t)ERR_INTERNAL);
+            continue;
+        }
+        const uint32_t ly = a.g.off[y], dy = a.g.deg[y];
+        const uint32_t p = lower_bound_nbr(a.g.pool + ly, dy, x);
+        if (p >= dy || a.g.pool[ly + p].nbr != x) {
+            atomicOr(d_err, (uint32_t)ERR_INTERNAL);
+            continue;
+        }
+        *reinterpret_cast<uint4*>(a.g.pool + lx + local) = make_uint4(y, ly, dy, p);
+        if (!a.touched[y])
+            *reinterpret_cast<uint4*>(a.g.pool + ly + p) = make_uint4(x, lx, a.g.deg[x], local);
+    }
+}
+
+__global__ void k_exec_untouch(ExecArgs a, const uint32_t* d_err) {
+    if (aborted(d_err)) return;
+    const uint32_t X = a.totals[TOT_X];
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < X; t += gridDim.x * blockDim.x)
+        a.touched[a.tv[t]] = 0;
+}
+
+void csr_exec(CSR& g, const ChangeList& cl, ApplyScratch& s, uint8_t* touched, uint32_t* d_err,
+              cudaStream_t st) {
+    const int grid = flat_grid();
+    ExecArgs a;
+    a.cl = cl;
+    a.g = g.view();
+    a.n = (uint32_t)g.n;
+    a.p_ins = s.p_ins.p; a.p_del = s.p_del.p; a.totals = s.totals.p;
+    a.tv = s.tv.p; a.tstart = s.tstart.p; a.tend = s.tend.p; a.odeg = s.odeg.p; a.ndeg = s.ndeg.p;
+    a.ooff = s.ooff.p; a.ncap = s.ncap.p; a.rsz = s.rsz.p; a.r_off = s.r_off.p; a.s_off = s.s_off.p;
+    a.w_off = s.w_off.p;
+    a.stage = s.stage.p;
+    a.touched = touched;
+    // merge reads the old lists; meta then points every touched vertex at its
+    // final slots; place copies the staged lists there; fix refreshes caches.
+    k_exec_merge<<<grid, FLAT_THREADS, 0, st>>>(a, d_err);
+    k_exec_meta<<<grid, FLAT_THREADS, 0, st>>>(a, d_err);
+    k_exec_place<<<grid, FLAT_THREADS, 0, st>>>(a, d_err);
+    k_exec_fix<<<grid, FLAT_THREADS, 0, st>>>(a, d_err);
+    k_exec_untouch<<<grid, FLAT_THREADS, 0, st>>>(a, d_err);
+    g_launches += 5;
+    DG_CHECK_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------
+// compaction
+// ---------------------------------------------------------------------------
+__global__ void k_compact_copy(CSRView g, const uint32_t* __restrict__ noff, uint32_t total,
+                               Ent* __restrict__ np) {
+    for (uint32_t item = blockIdx.x * blockDim.x + threadIdx.x; item < total; item += gridDim.x * blockDim.x) {
+        const uint32_t x = upper_bound_arr<uint32_t>(noff, 0, (uint32_t)g.n, item) - 1;
+        const uint32_t local = item - noff[x];
+        if (local >= g.deg[x]) continue;
+        Ent e = g.pool[g.off[x] + local];
+        e.noff = noff[e.nbr];
+        np[item] = e;
+    }
+}
+
+void csr_compact(CSR& g, DevAlloc& a, uint64_t min_free, cudaStream_t st) {
+    const uint32_t n = (uint32_t)g.n;
+    const int grid = flat_grid();
+    DBuf<uint32_t> ncap, noff, tmp, total;
+    ncap.ensure(a, (size_t)n + 1, st);
+    noff.ensure(a, (size_t)n + 1, st);
+    tmp.ensure(a, scan_tmp_words(n + 1), st);
+    total.ensure(a, 2, st);
+    k_caps<<<grid, FLAT_THREADS, 0, st>>>(g.deg.p, n, g.slack, ncap.p);
+    ++g_launches;
+    ScanJob job;
+    job.in[0] = ncap.p;
+    job.out[0] = noff.p;
+    job.total[0] = total.p;
+    job.k = 1;
+    scan_exclusive(job, nullptr, n, tmp.p, st);
+    uint32_t h_total = 0;
+    DG_CUDA(cudaMemcpyAsync(&h_total, total.p, 4, cudaMemcpyDeviceToHost, st));
+    DG_CUDA(cudaStreamSynchronize(st));
+    uint64_t want = (uint64_t)h_total + (uint64_t)((double)h_total * g.overflow) + 4096;
+    if (want < (uint64_t)h_total + min_free) want = (uint64_t)h_total + min_free;
+    if (want >= 0xFFFFFFF0ull) throw Error(DG_E_NOMEM, "graph too large for 32-bit pool offsets");
+    DBuf<Ent> np;
+    np.ensure(a, want, st);
+    if (h_total > 0) {
+        k_compact_copy<<<grid, FLAT_THREADS, 0, st>>>(g.view(), noff.p, h_total, np.p);
+        ++g_launches;
+    }
+    DG_CHECK_LAUNCH();
+    g.pool.release(a, st);
+    g.pool = np;
+    g.pool_cap = want;
+    std::swap(g.off, noff);
+    std::swap(g.cap, ncap);
+    noff.release(a, st);
+    ncap.release(a, st);
+    tmp.release(a, st);
+    total.release(a, st);
+    unsigned long long t = h_total;
+    DG_CUDA(cudaMemcpyAsync(g.top.p, &t, sizeof(t), cudaMemcpyHostToDevice, st));
+    g.host_top = h_total;
+    DG_CUDA(cudaStreamSynchronize(st));
+}
+
+// ---------------------------------------------------------------------------
+// export
+// ---------------------------------------------------------------------------
+__global__ void k_count_upper(CSRView g, uint32_t* __restrict__ cnt) {
+    for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < (uint32_t)g.n; x += gridDim.x * blockDim.x) {
+        const uint32_t d = g.deg[x];
+        cnt[x] = d - lower_bound_nbr(g.pool + g.off[x], d, x + 1);
+    }
+}
+
+__global__ void k_export(CSRView g, const uint32_t* __restrict__ pos, int32_t* __restrict__ A,
+                         int32_t* __restrict__ B, double* __restrict__ W) {
+    for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < (uint32_t)g.n; x += gridDim.x * blockDim.x) {
+        const uint32_t d = g.deg[x];
+        const Ent* L = g.pool + g.off[x];
+        uint32_t k = lower_bound_nbr(L, d, x + 1);
+        uint32_t p = pos[x];
+        for (; k < d; ++k, ++p) {
+            A[p] = (int32_t)x;
+            B[p] = (int32_t)L[k].nbr;
+            if (W) W[p] = L[k].w;
+        }
+    }
+}
+
+static uint32_t export_prepare(CSR& g, DevAlloc& a, DBuf<uint32_t>& cnt, DBuf<uint32_t>& pos, cudaStream_t st) {
+    const uint32_t n = (uint32_t)g.n;
+    const int grid = flat_grid();
+    DBuf<uint32_t> tmp, total;
+    cnt.ensure(a, (size_t)n + 1, st);
+    pos.ensure(a, (size_t)n + 1, st);
+    tmp.ensure(a, scan_tmp_words(n + 1), st);
+    total.ensure(a, 2, st);
+    k_count_upper<<<grid, FLAT_THREADS, 0, st>>>(g.view(), cnt.p);
+    ++g_launches;
+    ScanJob job;
+    job.in[0] = cnt.p;
+    job.out[0] = pos.p;
+    job.total[0] = total.p;
+    job.k = 1;
+    scan_exclusive(job, nullptr, n, tmp.p, st);
+    uint32_t h = 0;
+    DG_CUDA(cudaMemcpyAsync(&h, total.p, 4, cudaMemcpyDeviceToHost, st));
+    DG_CUDA(cudaStreamSynchronize(st));
+    tmp.release(a, st);
+    total.release(a, st);
+    return h;
+}
+
+uint64_t csr_edge_count(CSR& g, DevAlloc& a, cudaStream_t st) {
+    DBuf<uint32_t> cnt, pos;
+    uint32_t h = export_prepare(g, a, cnt, pos, st);
+    cnt.release(a, st);
+    pos.release(a, st);
+    return h;
+}
+
+void csr_export(CSR& g, DevAlloc& a, int32_t* d_a, int32_t* d_b, double* d_w, cudaStream_t st) {
+    DBuf<uint32_t> cnt, pos;
+    export_prepare(g, a, cnt, pos, st);
+    k_export<<<flat_grid(), FLAT_THREADS, 0, st>>>(g.view(), pos.p, d_a, d_b, d_w);
+    ++g_launches;
+    DG_CHECK_LAUNCH();
+    cnt.release(a, st);
+    pos.release(a, st);
+}
+
+}  // namespace dg

@@ -1,0 +1,95 @@
+// dg_csr.cuh -- slack-slot CSR on the device: build, batched in-place mutation
+// (plan / execute), compaction and export.
+//
+// Mutation follows the dynamic CSR idea of Section III-F (lists that outgrow
+// their slots move into spare pool space; deletions stay in place), made
+// parallel and deterministic: a batch's half-edge changes arrive sorted by
+// (vertex, neighbour); every touched vertex's new list is the sorted merge of
+// its old list and its changes, computed with one thread per output position
+// (load-balanced over all touched vertices, so hubs cost no more than their
+// degree), then placed in its slots or in freshly bumped pool space, after
+// which the cached (off, deg, rev) fields of the entries that point at moved
+// or resized lists are refreshed.
+#pragma once
+#include "dg_common.cuh"
+#include "dg_host.h"
+#include "dg_prims.cuh"
+
+namespace dg {
+
+struct CSR {
+    int32_t n = 0;
+    uint64_t pool_cap = 0;  // entries
+    float slack = 1.25f;
+    double overflow = 0.5;
+    DBuf<uint32_t> off, deg, cap;
+    DBuf<Ent> pool;
+    DBuf<unsigned long long> top;
+    uint64_t host_top = 0;  // last value read back
+
+    CSRView view() const {
+        CSRView v;
+        v.off = off.p;
+        v.deg = deg.p;
+        v.cap = cap.p;
+        v.pool = pool.p;
+        v.top = top.p;
+        v.pool_cap = pool_cap;
+        v.n = n;
+        return v;
+    }
+    uint64_t bytes() const { return off.bytes() + deg.bytes() + cap.bytes() + pool.bytes() + top.bytes(); }
+};
+
+// sorted, unique half-edge changes: keys[c] = x * n + y ascending; vals[c]
+// indexes the payload arrays kinds[] (CHG_*) and ws[] (new weight).
+struct ChangeList {
+    const uint64_t* keys = nullptr;
+    const uint32_t* vals = nullptr;
+    const uint8_t* kinds = nullptr;
+    const double* ws = nullptr;
+    const uint32_t* d_count = nullptr;
+    uint32_t max_count = 0;
+};
+
+enum { TOT_X = 0, TOT_NI, TOT_ND, TOT_R, TOT_S, TOT_WK, TOT_BASE_LO, TOT_BASE_HI, TOT_WORDS = 8 };
+
+struct ApplyScratch {
+    uint32_t c_max = 0;
+    uint64_t s_cap = 0;  // entries of staging space
+    DBuf<uint32_t> f_head, f_ins, f_del, p_head, p_ins, p_del;
+    DBuf<uint32_t> tv, tstart, tend, odeg, ndeg, ooff, ncap, rsz, work, r_off, s_off, w_off;
+    DBuf<uint32_t> scan_tmp, totals;
+    DBuf<Ent> stage;
+    void ensure(DevAlloc& a, uint32_t changes, uint64_t stage_entries, cudaStream_t st);
+    void release(DevAlloc& a, cudaStream_t st);
+    uint64_t bytes() const;
+};
+
+void csr_alloc_vertices(CSR& g, DevAlloc& a, int32_t n, cudaStream_t st);
+void csr_release(CSR& g, DevAlloc& a, cudaStream_t st);
+
+// Build g (fresh) from sorted unique half-edge keys with weights ws[vals[c]].
+// Sets ERR_DUP_EDGE in *d_err when two keys are equal.  count is host-known.
+void csr_build(CSR& g, DevAlloc& a, const uint64_t* keys, const uint32_t* vals, const double* ws,
+               uint32_t count, uint32_t* d_err, cudaStream_t st);
+
+// plan: sizes, relocation space and staging checks; raises pool_err_bit or
+// cap_err_bit in *d_err instead of writing anything when space is short.
+void csr_plan(CSR& g, const ChangeList& cl, ApplyScratch& s, uint32_t* d_err, uint32_t pool_err_bit,
+              uint32_t cap_err_bit, cudaStream_t st);
+// execute: merge, place, refresh cached fields (no-op when *d_err has an abort bit)
+void csr_exec(CSR& g, const ChangeList& cl, ApplyScratch& s, uint8_t* touched, uint32_t* d_err,
+              cudaStream_t st);
+
+// rebuild every list with fresh slack into a new pool with at least min_free spare entries
+void csr_compact(CSR& g, DevAlloc& a, uint64_t min_free, cudaStream_t st);
+
+// number of undirected edges (host, synchronous)
+uint64_t csr_edge_count(CSR& g, DevAlloc& a, cudaStream_t st);
+// export edges (x < nbr) in lexicographic order into device arrays of size >= count
+void csr_export(CSR& g, DevAlloc& a, int32_t* d_a, int32_t* d_b, double* d_w, cudaStream_t st);
+
+int flat_grid();  // grid size of the grid-stride flattened kernels
+
+}  // namespace dg

@@ -1,0 +1,48 @@
+// dg_prims.cuh -- scan and radix-sort primitives used by the slack-CSR mutation
+// and batch-validation steps.  Every primitive reads its element count from
+// device memory (with a host-side upper bound that fixes grid sizes), so the
+// launches can be captured once into a CUDA graph and replayed for any count.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dg {
+
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr uint32_t SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+// Exclusive prefix sums of up to three uint32 arrays of the same length n.
+// n = *d_n (or n_max when d_n is null).  total[a] (nullable) receives the sum.
+struct ScanJob {
+    const uint32_t* in[3] = {nullptr, nullptr, nullptr};
+    uint32_t* out[3] = {nullptr, nullptr, nullptr};
+    uint32_t* total[3] = {nullptr, nullptr, nullptr};
+    int k = 0;
+};
+size_t scan_tmp_words(uint32_t n_max);  // uint32 words of scratch for one ScanJob
+void scan_exclusive(const ScanJob& job, const uint32_t* d_n, uint32_t n_max, uint32_t* tmp,
+                    cudaStream_t st);
+
+// Stable LSD radix sort of (uint64 key, uint32 value) pairs on the low nbits of
+// the key.  The count is *d_n <= n_max.  Returns true when the sorted data ends
+// in the *_alt buffers.
+struct SortBufs {
+    uint64_t* keys;
+    uint32_t* vals;
+    uint64_t* keys_alt;
+    uint32_t* vals_alt;
+    uint32_t* hist;      // sort_hist_words(n_max)
+    uint32_t* scan_tmp;  // scan_tmp_words(256 * tiles)
+};
+size_t sort_hist_words(uint32_t n_max);
+size_t sort_scan_tmp_words(uint32_t n_max);
+bool radix_sort_pairs(const SortBufs& b, const uint32_t* d_n, uint32_t n_max, int nbits,
+                      cudaStream_t st);
+
+int bit_length(uint64_t x);
+
+// one extra kernel launch counter for the benchmark's launch tally
+extern thread_local uint64_t g_launches;
+
+}  // namespace dg

@@ -1,0 +1,503 @@
+// dg_walk.cu -- NBRW walkers (Section III-B/C), per-update reduction (Eq. 12),
+// path replay and fallback edges for deletions (Section III-C).
+//
+// Walker step (counter-based, so every walker's path is a pure function of
+// (seed, update id, walker, graph snapshot)):
+//   n_eff = deg(c) - [a previous vertex exists]; n_eff == 0 -> leaf stop
+//   x     = Philox4x32-10((step, walker, lo32(id), hi32(id)), seed)[0]
+//   j     = floor(x * n_eff / 2^32)                  (j-th allowed neighbour)
+//   idx   = j + (j >= pos(prev))                     (skip the previous vertex;
+//                                                    lists are sorted by id)
+//   R    += r(c, L[idx]); step += 1
+//   stop on: reaching v with (deletion or w_pq*R <= K) -> hit;
+//            insertion and w_pq*R > K;  step == T.
+// The entry read at idx carries the next list's offset/degree and pos(prev)
+// for the next step, so each step is one dependent 32-byte load.
+#include <cmath>
+
+#include "dg_prims.cuh"
+#include "dg_walk.cuh"
+
+namespace dg {
+
+static int g_sms = 0;
+int device_sms() {
+    if (g_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_sms <= 0) g_sms = 148;
+    }
+    return g_sms;
+}
+
+constexpr uint32_t NONE = 0xFFFFFFFFu;
+
+__device__ __forceinline__ bool walk_aborted(const uint32_t* d_err) { return (*d_err & ABORT_MASK) != 0u; }
+
+struct Walker {
+    const Ent* pool;
+    uint32_t pcap;   // entries in that pool (bounds guard)
+    uint32_t wid;    // absolute walker index j*s + k
+    uint32_t j, k;
+    uint32_t q;      // target
+    uint32_t c, off, deg, prev;
+    uint32_t steps;
+    uint32_t ulo, uhi;
+    double R, wpq;
+    bool ins;
+    bool active;
+};
+
+struct WalkKernelArgs {
+    CSRView H, G;
+    WalkTasks t;
+    WalkParams p;
+    WalkRecs r;
+    const BatchHdr* hdr;
+    unsigned long long* next;
+    uint32_t j_lo, j_hi;
+    uint32_t* d_err;
+};
+
+// a cached (off, deg) that points outside the pool or a neighbour id >= n can
+// only come from a broken mutation; the walker stops and the batch reports it
+__device__ __forceinline__ bool step_in_bounds(const Walker& w, uint32_t idx, const WalkKernelArgs& a) {
+    if ((uint64_t)w.off + idx < w.pcap) return true;
+    atomicOr(a.d_err, (uint32_t)ERR_INTERNAL);
+    return false;
+}
+
+__device__ __forceinline__ void walker_start(Walker& w, const WalkKernelArgs& a, uint32_t wid, uint64_t id0) {
+    w.wid = wid;
+    w.j = wid / a.p.s;
+    w.k = wid - w.j * a.p.s;
+    const uint32_t u = a.t.u[w.j];
+    w.q = a.t.v[w.j];
+    w.ins = a.t.kind[w.j] == WALK_INS;
+    w.wpq = a.t.wpq[w.j];
+    const uint64_t id = id0 + a.t.idx[w.j];
+    w.ulo = (uint32_t)id;
+    w.uhi = (uint32_t)(id >> 32);
+    const CSRView& g = w.ins ? a.H : a.G;
+    w.pool = g.pool;
+    w.pcap = (uint32_t)g.pool_cap;
+    w.off = g.off[u];
+    w.deg = g.deg[u];
+    w.c = u;
+    w.prev = NONE;
+    w.steps = 0;
+    w.R = 0.0;
+    w.active = true;
+    if (a.r.paths) a.r.paths[(size_t)wid * (a.p.T + 1)] = (int32_t)u;
+}
+
+__device__ __forceinline__ void walker_finish(Walker& w, const WalkKernelArgs& a, uint32_t reason) {
+    a.r.meta[w.wid] = w.steps | (reason << 16);
+    a.r.R[w.wid] = w.R;
+    w.active = false;
+}
+
+// consume one loaded entry: advance and test the stop rules
+__device__ __forceinline__ void walker_advance(Walker& w, const WalkKernelArgs& a, const uint4& h, double r) {
+    w.R = __dadd_rn(w.R, r);
+    w.steps += 1;
+    w.c = h.x;
+    w.off = h.y;
+    w.deg = h.z;
+    w.prev = h.w;
+    if (a.r.paths) a.r.paths[(size_t)w.wid * (a.p.T + 1) + w.steps] = (int32_t)w.c;
+    if (w.c == w.q) {
+        if (!w.ins || __dmul_rn(w.wpq, w.R) <= a.p.K) {
+            if (w.ins && a.p.early_exit) atomicMin(&a.t.kstar[w.j], w.steps);
+            walker_finish(w, a, R_HIT);
+            return;
+        }
+    }
+    if (w.ins && __dmul_rn(w.wpq, w.R) > a.p.K) {
+        walker_finish(w, a, R_OVER_K);
+        return;
+    }
+    if (w.steps == a.p.T) walker_finish(w, a, R_AT_T);
+}
+
+template <int ILP>
+__global__ void __launch_bounds__(256) k_walk_batched(WalkKernelArgs a) {
+    if (walk_aborted(a.d_err)) return;
+    const uint32_t W = min(*a.t.count, a.j_hi);
+    if (W <= a.j_lo) return;
+    const uint32_t total = (W - a.j_lo) * a.p.s;
+    const uint32_t wbase = a.j_lo * a.p.s;
+    const uint64_t id0 = a.hdr->id0;
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    Walker w[ILP];
+#pragma unroll
+    for (int i = 0; i < ILP; ++i) w[i].active = false;
+    bool exhausted = false;
+    for (;;) {
+        // refill empty slots, one atomic per warp and slot
+#pragma unroll
+        for (int i = 0; i < ILP; ++i) {
+            const bool need = !w[i].active && !exhausted;
+            const uint32_t m = __ballot_sync(0xffffffffu, need);
+            if (m) {
+                const int leader = __ffs(m) - 1;
+                unsigned long long b = 0;
+                if (lane == leader) b = atomicAdd(a.next, (unsigned long long)__popc(m));
+                b = __shfl_sync(0xffffffffu, b, leader);
+                if (need) {
+                    const unsigned long long id = b + __popc(m & lt);
+                    if (id < total) walker_start(w[i], a, wbase + (uint32_t)id, id0);
+                    else exhausted = true;
+                }
+            }
+        }
+        bool any = false;
+#pragma unroll
+        for (int i = 0; i < ILP; ++i) any |= w[i].active;
+        if (!__any_sync(0xffffffffu, any)) break;
+        // issue: leaf / early-exit checks and the entry loads of every slot
+        uint4 h[ILP];
+        double2 tl[ILP];
+        uint32_t ks[ILP];
+        bool go[ILP];
+#pragma unroll
+        for (int i = 0; i < ILP; ++i) {
+            go[i] = false;
+            ks[i] = NONE;
+            if (!w[i].active) continue;
+            const uint32_t neff = w[i].deg - (w[i].prev != NONE ? 1u : 0u);
+            if (neff == 0) {
+                walker_finish(w[i], a, R_LEAF);
+                continue;
+            }
+            if (w[i].ins && a.p.early_exit) ks[i] = __ldcg(&a.t.kstar[w[i].j]);
+            const uint32_t x = philox_word0(w[i].steps, w[i].k, w[i].ulo, w[i].uhi, a.p.key0, a.p.key1);
+            const uint32_t jj = __umulhi(x, neff);
+            const uint32_t idx = jj + (jj >= w[i].prev ? 1u : 0u);
+            if (!step_in_bounds(w[i], idx, a)) {
+                walker_finish(w[i], a, R_LEAF);
+                continue;
+            }
+            load_ent(w[i].pool + w[i].off + idx, h[i], tl[i]);
+            go[i] = true;
+        }
+        // consume
+#pragma unroll
+        for (int i = 0; i < ILP; ++i) {
+            if (!go[i]) continue;
+            if (ks[i] <= w[i].steps) {  // a walker of this update hit at a step <= ours: cut
+                walker_finish(w[i], a, R_CUT);
+                continue;
+            }
+            walker_advance(w[i], a, h[i], tl[i].x);
+        }
+    }
+}
+
+// the paper's scheme: one block per walked update, one thread per walker
+__global__ void k_walk_one(WalkKernelArgs a, uint32_t j) {
+    if (walk_aborted(a.d_err)) return;
+    if (j >= *a.t.count) return;
+    __shared__ uint32_t ks;
+    if (threadIdx.x == 0) ks = NONE;
+    __syncthreads();
+    for (uint32_t k = threadIdx.x; k < a.p.s; k += blockDim.x) {
+        Walker w;
+        walker_start(w, a, j * a.p.s + k, a.hdr->id0);
+        while (w.active) {
+            const uint32_t neff = w.deg - (w.prev != NONE ? 1u : 0u);
+            if (neff == 0) {
+                walker_finish(w, a, R_LEAF);
+                break;
+            }
+            if (w.ins && a.p.early_exit && *(volatile uint32_t*)&ks <= w.steps) {
+                walker_finish(w, a, R_CUT);
+                break;
+            }
+            const uint32_t x = philox_word0(w.steps, w.k, w.ulo, w.uhi, a.p.key0, a.p.key1);
+            const uint32_t jj = __umulhi(x, neff);
+            const uint32_t idx = jj + (jj >= w.prev ? 1u : 0u);
+            if (!step_in_bounds(w, idx, a)) {
+                walker_finish(w, a, R_LEAF);
+                break;
+            }
+            uint4 h;
+            double2 tl;
+            load_ent(w.pool + w.off + idx, h, tl);
+            const uint32_t before = w.steps;
+            walker_advance(w, a, h, tl.x);
+            if (!w.active && w.ins && a.p.early_exit && (a.r.meta[w.wid] >> 16) == R_HIT)
+                atomicMin(&ks, before + 1);
+        }
+    }
+}
+
+static WalkKernelArgs make_args(const CSRView& H, const CSRView& G, const WalkTasks& t, const WalkParams& p,
+                                const WalkRecs& r, const BatchHdr* d_hdr, unsigned long long* d_next,
+                                uint32_t j_lo, uint32_t j_hi, const uint32_t* d_err) {
+    WalkKernelArgs a;
+    a.H = H;
+    a.G = G;
+    a.t = t;
+    a.p = p;
+    a.r = r;
+    a.hdr = d_hdr;
+    a.next = d_next;
+    a.j_lo = j_lo;
+    a.j_hi = j_hi;
+    a.d_err = const_cast<uint32_t*>(d_err);
+    return a;
+}
+
+template <int ILP>
+static void launch_ilp(const WalkKernelArgs& a, const WalkShape& shape, cudaStream_t st) {
+    int bps = shape.blocks_per_sm;
+    if (bps <= 0) {
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_walk_batched<ILP>, shape.block, 0);
+        bps = occ > 0 ? occ : 1;
+    }
+    const int grid = device_sms() * bps;
+    k_walk_batched<ILP><<<grid, shape.block, 0, st>>>(a);
+}
+
+void launch_walk_batched(const CSRView& H, const CSRView& G, const WalkTasks& t, const WalkParams& p,
+                         const WalkRecs& r, const BatchHdr* d_hdr, unsigned long long* d_next,
+                         uint32_t j_lo, uint32_t j_hi, const WalkShape& shape, const uint32_t* d_err,
+                         cudaStream_t st) {
+    WalkKernelArgs a = make_args(H, G, t, p, r, d_hdr, d_next, j_lo, j_hi, d_err);
+    DG_CUDA(cudaMemsetAsync(d_next, 0, sizeof(unsigned long long), st));
+    switch (shape.ilp) {
+        case 1: launch_ilp<1>(a, shape, st); break;
+        case 4: launch_ilp<4>(a, shape, st); break;
+        default: launch_ilp<2>(a, shape, st); break;
+    }
+    ++g_launches;
+    DG_CHECK_LAUNCH();
+}
+
+void launch_walk_one(const CSRView& H, const CSRView& G, const WalkTasks& t, const WalkParams& p,
+                     const WalkRecs& r, const BatchHdr* d_hdr, uint32_t j, const uint32_t* d_err,
+                     cudaStream_t st) {
+    WalkKernelArgs a = make_args(H, G, t, p, r, d_hdr, nullptr, 0, 0, d_err);
+    int threads = (int)p.s;
+    if (threads > 1024) threads = 1024;
+    threads = (threads + 31) / 32 * 32;
+    k_walk_one<<<1, threads, 0, st>>>(a, j);
+    ++g_launches;
+}
+
+// ---------------------------------------------------------------------------
+// per-update reduction (Eq. 12 and the early-exit reading)
+// ---------------------------------------------------------------------------
+__global__ void k_walk_reduce(WalkTasks t, WalkParams p, WalkRecs r, dg_update_result* res, int32_t* best,
+                              BatchCounters* ctr, int32_t* dbg_reason, int32_t* dbg_steps, uint32_t w_max,
+                              const uint32_t* d_err) {
+    if (walk_aborted(d_err)) return;
+    const uint32_t W = min(*t.count, w_max);
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t j = warp; j < W; j += nwarps) {
+        const bool ins = t.kind[j] == WALK_INS;
+        const bool ee = ins && p.early_exit;
+        const uint32_t i = t.idx[j];
+        uint32_t ks = NONE;
+        for (uint32_t k = lane; k < p.s; k += 32) {
+            const uint32_t m = r.meta[(size_t)j * p.s + k];
+            if ((m >> 16) == R_HIT) ks = min(ks, m & 0xFFFFu);
+        }
+        for (int o = 16; o > 0; o >>= 1) ks = min(ks, __shfl_xor_sync(0xffffffffu, ks, o));
+        uint32_t nh = 0, tot = 0;
+        double bR = INFINITY;
+        int bk = -1;
+        for (uint32_t k = lane; k < p.s; k += 32) {
+            const uint32_t m = r.meta[(size_t)j * p.s + k];
+            uint32_t st = m & 0xFFFFu, rs = m >> 16;
+            if (ee && ks != NONE && st > ks) {
+                st = ks;
+                rs = R_CUT;
+            }
+            tot += st;
+            if (rs == R_HIT) {
+                ++nh;
+                const double R = r.R[(size_t)j * p.s + k];
+                if (bk < 0 || R < bR) {  // k ascends per lane: first minimum keeps the lower index
+                    bR = R;
+                    bk = (int)k;
+                }
+            }
+            if (dbg_reason) {
+                dbg_reason[(size_t)i * p.s + k] = (int32_t)rs;
+                dbg_steps[(size_t)i * p.s + k] = (int32_t)st;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            nh += __shfl_xor_sync(0xffffffffu, nh, o);
+            tot += __shfl_xor_sync(0xffffffffu, tot, o);
+            const double oR = __shfl_xor_sync(0xffffffffu, bR, o);
+            const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
+            if (ok >= 0 && (bk < 0 || oR < bR || (oR == bR && ok < bk))) {
+                bR = oR;
+                bk = ok;
+            }
+        }
+        if (lane == 0) {
+            dg_update_result& o = res[i];
+            o.hit = nh > 0;
+            o.nhits = (int32_t)nh;
+            o.best_walker = bk;
+            o.steps = (int32_t)tot;
+            o.r_est = nh > 0 ? bR : INFINITY;
+            o.accepted = ins && nh == 0;
+            best[j] = bk;
+            atomicAdd(&ctr->steps, (unsigned long long)tot);
+            atomicAdd(&ctr->walked, 1ull);
+            if (nh > 0) atomicAdd(&ctr->hits, 1ull);
+            if (ins && nh == 0) atomicAdd(&ctr->accepted, 1ull);
+        }
+    }
+}
+
+void launch_walk_reduce(const WalkTasks& t, const WalkParams& p, const WalkRecs& r, dg_update_result* res,
+                        int32_t* best, BatchCounters* ctr, int32_t* dbg_reason, int32_t* dbg_steps,
+                        uint32_t w_max, const uint32_t* d_err, cudaStream_t st) {
+    uint32_t blocks = (w_max + 7) / 8;
+    const uint32_t cap = (uint32_t)device_sms() * 16;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    k_walk_reduce<<<blocks, 256, 0, st>>>(t, p, r, res, best, ctr, dbg_reason, dbg_steps, w_max, d_err);
+    ++g_launches;
+    DG_CHECK_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------
+// commit candidates: kept insertions, recovered path edges, fallback edges
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void emit_edge(Cands& c, uint32_t x, uint32_t y, double w, uint32_t n,
+                                          uint32_t* d_err) {
+    const uint32_t pos = atomicAdd(c.count, 2u);
+    if (pos + 2 > c.cap) {
+        atomicOr(d_err, (uint32_t)ERR_CAP_COMMIT);
+        return;
+    }
+    c.keys[pos] = (uint64_t)x * n + y;
+    c.keys[pos + 1] = (uint64_t)y * n + x;
+    c.vals[pos] = pos;
+    c.vals[pos + 1] = pos + 1;
+    c.w[pos] = w;
+    c.w[pos + 1] = w;
+}
+
+__global__ void k_emit(CSRView H, CSRView G, WalkTasks t, WalkParams p, WalkRecs r, const BatchHdr* hdr,
+                       const int32_t* best, const double* fin_w, dg_update_result* res, BatchCounters* ctr,
+                       Cands c, uint32_t* path_buf, uint32_t w_max, uint32_t* d_err) {
+    if (walk_aborted(d_err)) return;
+    const uint32_t W = min(*t.count, w_max);
+    const uint32_t n = (uint32_t)G.n;
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < W; j += gridDim.x * blockDim.x) {
+        const uint32_t i = t.idx[j];
+        const uint32_t u = t.u[j], v = t.v[j];
+        if (t.kind[j] == WALK_INS) {
+            if (best[j] < 0 && !isnan(fin_w[i])) emit_edge(c, u, v, fin_w[i], n, d_err);
+            continue;
+        }
+        uint32_t emitted = 0;
+        const int32_t b = best[j];
+        if (b >= 0) {
+            // replay the argmin walker: same counters on the same snapshot -> same path
+            const uint32_t steps = r.meta[(size_t)j * p.s + b] & 0xFFFFu;
+            const uint64_t id = hdr->id0 + i;
+            const uint32_t ulo = (uint32_t)id, uhi = (uint32_t)(id >> 32);
+            uint32_t* path = path_buf + (size_t)j * (p.T + 1);
+            uint32_t cv = u, off = G.off[u], deg = G.deg[u], prev = NONE;
+            path[0] = u;
+            for (uint32_t s = 0; s < steps; ++s) {
+                const uint32_t neff = deg - (prev != NONE ? 1u : 0u);
+                if (neff == 0) {  // cannot happen for a recorded hit
+                    atomicOr(d_err, (uint32_t)ERR_INTERNAL);
+                    break;
+                }
+                const uint32_t x = philox_word0(s, (uint32_t)b, ulo, uhi, p.key0, p.key1);
+                const uint32_t jj = __umulhi(x, neff);
+                const uint32_t idx = jj + (jj >= prev ? 1u : 0u);
+                if ((uint64_t)off + idx >= G.pool_cap) {
+                    atomicOr(d_err, (uint32_t)ERR_INTERNAL);
+                    break;
+                }
+                const Ent e = G.pool[off + idx];
+                if (e.nbr >= n) {
+                    atomicOr(d_err, (uint32_t)ERR_INTERNAL);
+                    break;
+                }
+                // edge (cv, e.nbr): recover it unless repeated earlier in this walk or already in H'
+                const uint32_t y = e.nbr;
+                bool dup = false;
+                for (uint32_t s2 = 0; s2 < s && !dup; ++s2) {
+                    const uint32_t a0 = path[s2], a1 = path[s2 + 1];
+                    dup = (a0 == cv && a1 == y) || (a0 == y && a1 == cv);
+                }
+                if (!dup && !has_edge(H, cv, y)) {
+                    emit_edge(c, cv, y, e.w, n, d_err);
+                    ++emitted;
+                }
+                path[s + 1] = y;
+                cv = y;
+                off = e.noff;
+                deg = e.ndeg;
+                prev = e.rev;
+            }
+            if (cv != v) atomicOr(d_err, (uint32_t)ERR_INTERNAL);
+        } else {
+            // no walker reached v: per endpoint, the minimum-resistance G_b edge not in H'
+            res[i].fallback = 1;
+            uint32_t pick_x[2] = {NONE, NONE}, pick_y[2] = {NONE, NONE};
+            double pick_w[2] = {0.0, 0.0};
+            const uint32_t ends[2] = {u, v};
+            for (int e2 = 0; e2 < 2; ++e2) {
+                const uint32_t x = ends[e2];
+                const Ent* L = G.pool + G.off[x];
+                const uint32_t d = G.deg[x];
+                double rmin = INFINITY;
+                for (uint32_t k = 0; k < d; ++k) {
+                    const uint32_t y = L[k].nbr;
+                    const double rr = L[k].r;
+                    if (!(rr < rmin)) continue;  // ascending ids: strict < keeps the smaller id
+                    if (has_edge(H, x, y)) continue;
+                    rmin = rr;
+                    pick_x[e2] = x;
+                    pick_y[e2] = y;
+                    pick_w[e2] = L[k].w;
+                }
+            }
+            for (int e2 = 0; e2 < 2; ++e2) {
+                if (pick_x[e2] == NONE) continue;
+                if (e2 == 1 && pick_x[0] != NONE &&
+                    ((pick_x[0] == pick_x[1] && pick_y[0] == pick_y[1]) ||
+                     (pick_x[0] == pick_y[1] && pick_y[0] == pick_x[1])))
+                    continue;
+                emit_edge(c, pick_x[e2], pick_y[e2], pick_w[e2], n, d_err);
+                ++emitted;
+            }
+        }
+        res[i].nrecovered = (int32_t)emitted;
+        if (emitted) atomicAdd(&ctr->recovered, (unsigned long long)emitted);
+    }
+}
+
+void launch_emit(const CSRView& H, const CSRView& G, const WalkTasks& t, const WalkParams& p,
+                 const WalkRecs& r, const BatchHdr* d_hdr, const int32_t* best, const double* fin_w,
+                 dg_update_result* res, BatchCounters* ctr, Cands c, uint32_t* path_buf, uint32_t w_max,
+                 uint32_t* d_err, cudaStream_t st) {
+    uint32_t blocks = (w_max + 127) / 128;
+    const uint32_t cap = (uint32_t)device_sms() * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    k_emit<<<blocks, 128, 0, st>>>(H, G, t, p, r, d_hdr, best, fin_w, res, ctr, c, path_buf, w_max, d_err);
+    ++g_launches;
+    DG_CHECK_LAUNCH();
+}
+
+}  // namespace dg

@@ -1,0 +1,92 @@
+// dg_walk.cuh -- the non-backtracking random-walk kernels (Section III-B/C):
+// walkers, per-update reduction (Eq. 12), path replay for recovery and the
+// fallback edges.
+#pragma once
+#include "dg_common.cuh"
+#include "dg_host.h"
+
+namespace dg {
+
+// batch header on the device (copied per batch so captured graphs replay it)
+struct BatchHdr {
+    uint32_t nu;     // updates in the batch
+    uint32_t pad;
+    uint64_t id0;    // sequence number of the batch's first update
+};
+
+struct WalkTasks {
+    uint32_t* u;     // start vertex
+    uint32_t* v;     // target vertex
+    uint32_t* idx;   // update index in the batch
+    double* wpq;     // insertion weight (0 for deletions)
+    uint8_t* kind;   // WALK_INS / WALK_DEL
+    uint32_t* kstar; // first hitting step (early exit), 0xFFFFFFFF if none yet
+    uint32_t* count; // device: number of walked updates W
+};
+
+struct WalkParams {
+    double K;
+    uint32_t T;
+    uint32_t s;
+    uint32_t early_exit;
+    uint32_t key0, key1;  // Philox key = seed
+};
+
+// per-walker record: meta = steps | reason << 16, R = accumulated resistance
+struct WalkRecs {
+    uint32_t* meta;
+    double* R;
+    int32_t* paths;  // optional: rows of T+1 vertices per walker (debug)
+};
+
+enum : uint32_t { R_NONE = 0, R_HIT = 1, R_OVER_K = 2, R_AT_T = 3, R_LEAF = 4, R_CUT = 5 };
+
+struct WalkShape {
+    int block = 256;
+    int ilp = 2;
+    int blocks_per_sm = 0;  // 0 = occupancy maximum
+};
+
+// batched persistent walk over walked updates [j_lo, j_hi) of the task list
+void launch_walk_batched(const CSRView& H, const CSRView& G, const WalkTasks& t, const WalkParams& p,
+                         const WalkRecs& r, const BatchHdr* d_hdr, unsigned long long* d_next,
+                         uint32_t j_lo, uint32_t j_hi, const WalkShape& shape, const uint32_t* d_err,
+                         cudaStream_t st);
+// one launch per walked update j (block of s threads), the paper's scheme
+void launch_walk_one(const CSRView& H, const CSRView& G, const WalkTasks& t, const WalkParams& p,
+                     const WalkRecs& r, const BatchHdr* d_hdr, uint32_t j, const uint32_t* d_err,
+                     cudaStream_t st);
+
+struct UpdRes;  // dg_update_result on the device
+struct BatchCounters {
+    unsigned long long steps;
+    unsigned long long accepted;
+    unsigned long long recovered;
+    unsigned long long walked;
+    unsigned long long valid;
+    unsigned long long hits;
+};
+
+// per-update reduction; writes results, best walker per walked update
+void launch_walk_reduce(const WalkTasks& t, const WalkParams& p, const WalkRecs& r, dg_update_result* res,
+                        int32_t* best, BatchCounters* ctr, int32_t* dbg_reason, int32_t* dbg_steps,
+                        uint32_t w_max, const uint32_t* d_err, cudaStream_t st);
+
+// commit candidates (half-edges, keys x*n+y) with G_b weights
+struct Cands {
+    uint64_t* keys;
+    uint32_t* vals;
+    double* w;
+    uint32_t* count;
+    uint32_t cap;
+};
+
+// recovered path edges / fallback edges of walked deletions, kept insertions
+void launch_emit(const CSRView& H, const CSRView& G, const WalkTasks& t, const WalkParams& p,
+                 const WalkRecs& r, const BatchHdr* d_hdr, const int32_t* best, const double* fin_w,
+                 dg_update_result* res, BatchCounters* ctr, Cands c, uint32_t* path_buf, uint32_t w_max,
+                 uint32_t* d_err, cudaStream_t st);
+
+int device_sms();
+
+}  // namespace dg

@@ -1,0 +1,301 @@
+"""Python binding of libdygrass.so (argument marshalling only).
+
+Every step of the method runs in the CUDA library; this module converts numpy
+arrays / torch tensors to pointers and statuses to exceptions.  PyTorch is used
+for device memory (optional allocator hook, device-resident batches) and
+streams.  The binding never falls back to anything else: if the library is
+missing or no GPU is present, it raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libdygrass.so")
+
+DG_OK = 0
+STATUS = {0: "ok", -1: "invalid argument", -2: "out of device memory", -3: "CUDA error", -4: "timeout",
+          -5: "invalid state", -6: "busy"}
+OP_INSERT, OP_DELETE = 0, 1
+WALK_BATCHED, WALK_PER_UPDATE = 0, 1
+
+UPDATE_DTYPE = np.dtype([("u", "<i4"), ("v", "<i4"), ("w", "<f8"), ("op", "<i4"), ("reserved", "<i4")])
+RESULT_DTYPE = np.dtype([("status", "<i4"), ("walked", "u1"), ("hit", "u1"), ("accepted", "u1"),
+                         ("fallback", "u1"), ("nhits", "<i4"), ("best_walker", "<i4"), ("nrecovered", "<i4"),
+                         ("steps", "<i4"), ("r_est", "<f8")])
+assert UPDATE_DTYPE.itemsize == 24 and RESULT_DTYPE.itemsize == 32
+
+# every symbol the header declares
+EXPORTS = ("dg_config_default", "dg_create", "dg_destroy", "dg_status_str", "dg_last_error", "dg_load_graph",
+           "dg_unload_graph", "dg_init_sparsifier", "dg_apply_updates", "dg_apply_updates_device",
+           "dg_query_sparsifier", "dg_query_graph", "dg_get_batch_stats", "dg_get_walker_records", "dg_compact",
+           "dg_graph_bytes", "dg_launch_count", "dg_set_next_update_id", "dg_get_next_update_id",
+           "dg_set_walk_shape", "dg_submit_updates", "dg_wait")
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class Config(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("K", C.c_double), ("T", C.c_int32), ("s", C.c_int32),
+                ("ins_early_exit", C.c_int32), ("walk_mode", C.c_int32), ("slack", C.c_double),
+                ("overflow_frac", C.c_double), ("hbm_budget_bytes", C.c_uint64), ("autotune", C.c_int32),
+                ("timeout_ms", C.c_int32), ("use_cuda_graphs", C.c_int32), ("record_walkers", C.c_int32),
+                ("device", C.c_int32), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p)]
+
+
+class BatchStats(C.Structure):
+    _fields_ = [("updates", C.c_int64), ("valid", C.c_int64), ("walked", C.c_int64), ("steps", C.c_int64),
+                ("accepted", C.c_int64), ("recovered", C.c_int64), ("h_edges", C.c_int64),
+                ("g_edges", C.c_int64), ("walk_ms", C.c_double), ("batch_ms", C.c_double),
+                ("walk_launches", C.c_int64), ("launches", C.c_int64), ("retries", C.c_int64),
+                ("walk_block", C.c_int32), ("walk_ilp", C.c_int32), ("walk_blocks_per_sm", C.c_int32),
+                ("graph_replayed", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class DgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load libdygrass.so; raises if it is missing (no fallback path exists)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise FileNotFoundError(f"{p} is missing: build it with `python -m paper_2505_02741_b300.build`")
+    L = C.CDLL(p)
+    P, i32, i64, u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
+    sig = {
+        "dg_config_default": (None, [C.POINTER(Config)]),
+        "dg_create": (i32, [C.POINTER(Config), C.POINTER(P)]),
+        "dg_destroy": (i32, [P]),
+        "dg_status_str": (C.c_char_p, [i32]),
+        "dg_last_error": (C.c_char_p, []),
+        "dg_load_graph": (i32, [P, i32, i64, P, P, P, C.POINTER(i32)]),
+        "dg_unload_graph": (i32, [P, i32]),
+        "dg_init_sparsifier": (i32, [P, i32, i64, P, P]),
+        "dg_apply_updates": (i32, [P, i32, i64, P, P, P]),
+        "dg_apply_updates_device": (i32, [P, i32, i64, P, P, P]),
+        "dg_query_sparsifier": (i32, [P, i32, i64, P, P, P, C.POINTER(i64)]),
+        "dg_query_graph": (i32, [P, i32, i64, P, P, P, C.POINTER(i64)]),
+        "dg_get_batch_stats": (i32, [P, i32, C.POINTER(BatchStats)]),
+        "dg_get_walker_records": (i32, [P, i32, i64, P, P, P]),
+        "dg_compact": (i32, [P, i32]),
+        "dg_graph_bytes": (i32, [P, i32, C.POINTER(u64)]),
+        "dg_launch_count": (u64, [P]),
+        "dg_set_next_update_id": (i32, [P, i32, u64]),
+        "dg_get_next_update_id": (i32, [P, i32, C.POINTER(u64)]),
+        "dg_set_walk_shape": (i32, [P, i32, i32, i32, i32]),
+        "dg_submit_updates": (i32, [P, i32, i64, P, P, C.POINTER(u64)]),
+        "dg_wait": (i32, [P, u64, i32, C.POINTER(C.c_double)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != DG_OK:
+        msg = _lib.dg_last_error().decode(errors="replace") if _lib else ""
+        raise DgError(rc, msg)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def make_updates(u, v, w, op) -> np.ndarray:
+    """Pack arrays into the 24-byte dg_update records."""
+    ups = np.zeros(len(u), UPDATE_DTYPE)
+    ups["u"] = u
+    ups["v"] = v
+    ups["w"] = w
+    ups["op"] = op
+    return ups
+
+
+class Context:
+    def __init__(self, *, seed=0, K=100.0, T=100, s=32, early_exit=True, walk_mode="batched", slack=1.25,
+                 overflow=0.5, hbm_budget=0, autotune=True, timeout_ms=60000, cuda_graphs=True,
+                 record_walkers=False, device=0, allocator=None):
+        L = load_library()
+        cfg = Config()
+        L.dg_config_default(C.byref(cfg))
+        cfg.seed, cfg.K, cfg.T, cfg.s = int(seed), float(K), int(T), int(s)
+        cfg.ins_early_exit = 1 if early_exit else 0
+        cfg.walk_mode = WALK_PER_UPDATE if walk_mode in ("per_update", WALK_PER_UPDATE) else WALK_BATCHED
+        cfg.slack, cfg.overflow_frac = float(slack), float(overflow)
+        cfg.hbm_budget_bytes = int(hbm_budget)
+        cfg.autotune = 1 if autotune else 0
+        cfg.timeout_ms = int(timeout_ms)
+        cfg.use_cuda_graphs = 1 if cuda_graphs else 0
+        cfg.record_walkers = 1 if record_walkers else 0
+        cfg.device = int(device)
+        self._hooks = None
+        if allocator == "torch":
+            import torch
+
+            dev = int(device)
+
+            def _alloc(nbytes, stream, user):
+                return torch.cuda.caching_allocator_alloc(int(nbytes), dev, int(stream or 0))
+
+            def _free(ptr, nbytes, stream, user):
+                torch.cuda.caching_allocator_delete(int(ptr))
+
+            self._hooks = (ALLOC_FN(_alloc), FREE_FN(_free))
+            cfg.alloc, cfg.free = self._hooks
+        self.T, self.s = int(T), int(s)
+        h = C.c_void_p()
+        _check(L.dg_create(C.byref(cfg), C.byref(h)))
+        self._h = h
+        self._lib = L
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.dg_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def launch_count(self) -> int:
+        return int(self._lib.dg_launch_count(self._h))
+
+    def load_graph(self, n, u, v, w) -> "Graph":
+        u = np.ascontiguousarray(u, np.int32)
+        v = np.ascontiguousarray(v, np.int32)
+        w = np.ascontiguousarray(w, np.float64)
+        gid = C.c_int32()
+        _check(self._lib.dg_load_graph(self._h, int(n), u.size, _ptr(u), _ptr(v), _ptr(w), C.byref(gid)))
+        return Graph(self, gid.value, int(n))
+
+    def wait(self, ticket, timeout_ms=-1):
+        lat = C.c_double()
+        rc = self._lib.dg_wait(self._h, int(ticket), int(timeout_ms), C.byref(lat))
+        _check(rc)
+        return lat.value
+
+
+class Graph:
+    def __init__(self, ctx: Context, gid: int, n: int):
+        self.ctx, self.gid, self.n = ctx, gid, n
+        self._L = ctx._lib
+        self._keep = {}
+
+    def unload(self):
+        _check(self._L.dg_unload_graph(self.ctx._h, self.gid))
+
+    def init_sparsifier(self, u, v):
+        u = np.ascontiguousarray(u, np.int32)
+        v = np.ascontiguousarray(v, np.int32)
+        _check(self._L.dg_init_sparsifier(self.ctx._h, self.gid, u.size, _ptr(u), _ptr(v)))
+
+    def apply(self, ups: np.ndarray, stream=None) -> np.ndarray:
+        """One batch from host records; returns the result records."""
+        ups = np.ascontiguousarray(ups, UPDATE_DTYPE)
+        res = np.zeros(ups.size, RESULT_DTYPE)
+        _check(self._L.dg_apply_updates(self.ctx._h, self.gid, ups.size, _ptr(ups), _ptr(res),
+                                        None if stream is None else C.c_void_p(int(stream))))
+        return res
+
+    def apply_device(self, d_ups_ptr: int, nu: int, d_res_ptr: int | None, stream=None):
+        """One batch whose records already live in device memory (e.g. torch tensors)."""
+        _check(self._L.dg_apply_updates_device(self.ctx._h, self.gid, int(nu), C.c_void_p(int(d_ups_ptr)),
+                                               None if not d_res_ptr else C.c_void_p(int(d_res_ptr)),
+                                               None if stream is None else C.c_void_p(int(stream))))
+
+    def _query(self, fn):
+        cnt = C.c_int64()
+        _check(fn(self.ctx._h, self.gid, 0, None, None, None, C.byref(cnt)))
+        n = cnt.value
+        a = np.zeros(max(n, 1), np.int32)
+        b = np.zeros(max(n, 1), np.int32)
+        w = np.zeros(max(n, 1), np.float64)
+        _check(fn(self.ctx._h, self.gid, n, _ptr(a), _ptr(b), _ptr(w), C.byref(cnt)))
+        return a[:n], b[:n], w[:n]
+
+    def sparsifier(self):
+        """(u, v, w) of H, u < v, lexicographic."""
+        return self._query(self._L.dg_query_sparsifier)
+
+    def edges(self):
+        """(u, v, w) of the current G."""
+        return self._query(self._L.dg_query_graph)
+
+    def stats(self) -> dict:
+        st = BatchStats()
+        _check(self._L.dg_get_batch_stats(self.ctx._h, self.gid, C.byref(st)))
+        return st.as_dict()
+
+    def walker_records(self, nu: int, paths=True):
+        rows = nu * self.ctx.s
+        reason = np.zeros(rows, np.int32)
+        steps = np.zeros(rows, np.int32)
+        pbuf = np.full(rows * (self.ctx.T + 1), -1, np.int32) if paths else None
+        _check(self._L.dg_get_walker_records(self.ctx._h, self.gid, nu, _ptr(reason), _ptr(steps), _ptr(pbuf)))
+        out = dict(reason=reason.reshape(nu, self.ctx.s), steps=steps.reshape(nu, self.ctx.s))
+        if paths:
+            out["paths"] = pbuf.reshape(nu, self.ctx.s, self.ctx.T + 1)
+        return out
+
+    def compact(self):
+        _check(self._L.dg_compact(self.ctx._h, self.gid))
+
+    def device_bytes(self) -> int:
+        b = C.c_uint64()
+        _check(self._L.dg_graph_bytes(self.ctx._h, self.gid, C.byref(b)))
+        return b.value
+
+    @property
+    def next_update_id(self) -> int:
+        x = C.c_uint64()
+        _check(self._L.dg_get_next_update_id(self.ctx._h, self.gid, C.byref(x)))
+        return x.value
+
+    @next_update_id.setter
+    def next_update_id(self, value: int):
+        _check(self._L.dg_set_next_update_id(self.ctx._h, self.gid, int(value)))
+
+    def set_walk_shape(self, block=0, ilp=0, blocks_per_sm=0):
+        _check(self._L.dg_set_walk_shape(self.ctx._h, self.gid, int(block), int(ilp), int(blocks_per_sm)))
+
+    def submit(self, ups: np.ndarray):
+        """Queue one request; returns (ticket, result array filled when waited)."""
+        ups = np.ascontiguousarray(ups, UPDATE_DTYPE)
+        res = np.zeros(ups.size, RESULT_DTYPE)
+        t = C.c_uint64()
+        _check(self._L.dg_submit_updates(self.ctx._h, self.gid, ups.size, _ptr(ups), _ptr(res), C.byref(t)))
+        self._keep[t.value] = (ups, res)
+        return t.value, res
+
+    def wait(self, ticket, timeout_ms=-1):
+        lat = self.ctx.wait(ticket, timeout_ms)
+        ups, res = self._keep.pop(ticket)
+        return res, lat

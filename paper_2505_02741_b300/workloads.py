@@ -320,8 +320,10 @@ class UpdateStream:
         # advance the tracked edge set
         keep = np.ones(self.cur.size, dtype=bool)
         keep[didx] = False
-        ik = edge_keys(n, np.minimum(iu, iv), np.maximum(iu, iv))
-        self.cur = np.union1d(self.cur[keep], ik)
+        ik = np.sort(edge_keys(n, np.minimum(iu, iv), np.maximum(iu, iv)))
+        kept = self.cur[keep]
+        # inserted keys are distinct and absent from the current set: a sorted insert keeps it sorted
+        self.cur = np.insert(kept, np.searchsorted(kept, ik), ik)
         return Batch(u[perm], v[perm], w[perm], op[perm])
 
 

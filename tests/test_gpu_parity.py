@@ -1,0 +1,261 @@
+"""GPU (CUDA library, through the C ABI) vs CPU oracle, element by element.
+
+Everything integer (statuses, flags, hit counts, best walkers, step counts,
+walk paths, edge sets) must match exactly; R~ and weights must match to 0 ULP
+(both sides add r_e in walk order and round each FP64 operation on its own).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+from paper_2505_02741_b300 import dygrass as D
+from paper_2505_02741_b300 import workloads as W
+from tests.gpu_util import assert_edges_equal, assert_results_equal, pair, step_both
+from tests.helpers import random_connected, ring
+
+pytestmark = pytest.mark.gpu
+
+
+def test_grid64_insertions_paths_and_records():
+    """The 64x64 grid workload: 200 insertions <= 4 hops apart, s=32, T=100;
+    walker paths, stop reasons and step counts agree walker by walker."""
+    wl, st = W.make_grid(64, 64)
+    ctx, g, o = pair(wl.n, wl.a, wl.b, wl.w, wl.h_ids, ctx_kw=dict(record_walkers=True))
+    bt = st.next_batch(200, 0)
+    res = g.apply(D.make_updates(bt.u, bt.v, bt.w, bt.op))
+    ref = o.apply(bt.u, bt.v, bt.w, bt.op, walkers=True, paths=True)
+    assert_results_equal(res, ref, "grid64")
+    rec = g.walker_records(len(bt))
+    assert np.array_equal(rec["reason"], ref["walkers"]["reason"])
+    assert np.array_equal(rec["steps"], ref["walkers"]["steps"])
+    # compare each walker's path up to its (cut) step count
+    for i in range(len(bt)):
+        for k in range(wl.s):
+            L = ref["walkers"]["steps"][i, k] + 1
+            assert np.array_equal(rec["paths"][i, k, :L], ref["paths"][i, k, :L]), (i, k)
+    assert_edges_equal(g.sparsifier(), o.edges("H"), "H")
+    assert res["accepted"].sum() > 0 and res["hit"].sum() > 0
+    ctx.close()
+
+
+def test_grid64_step_limit_10():
+    wl, st = W.make_grid(64, 64, T=10)
+    ctx, g, o = pair(wl.n, wl.a, wl.b, wl.w, wl.h_ids, T=10)
+    bt = st.next_batch(200, 0)
+    step_both(g, o, bt.u, bt.v, bt.w, bt.op, where="grid64 T=10")
+    ctx.close()
+
+
+@pytest.mark.parametrize("early_exit", [True, False])
+def test_grid_mixed_stream(early_exit):
+    """Several fully dynamic batches (insertions and deletions interleaved)."""
+    wl, st = W.make_grid(32, 32)
+    ctx, g, o = pair(wl.n, wl.a, wl.b, wl.w, wl.h_ids, early_exit=early_exit)
+    for b in range(4):
+        bt = st.next_batch(150, 150)
+        step_both(g, o, bt.u, bt.v, bt.w, bt.op, where=f"batch {b}")
+    ctx.close()
+
+
+def test_invalid_and_repeated_updates():
+    """Statuses of invalid updates and the batch-local view of repeated edges."""
+    rng = np.random.default_rng(1)
+    n = 40
+    a, b, w = random_connected(n, 40, rng)
+    h = W.init_sparsifier(n, a, b, w, rng)
+    ctx, g, o = pair(n, a, b, w, h, T=20, s=8, K=12.0)
+    x, y = int(a[h][0]), int(b[h][0])
+    nx, ny = 0, 0
+    present = set(zip(a.tolist(), b.tolist()))
+    for p in range(n):
+        for q in range(p + 1, n):
+            if (p, q) not in present:
+                nx, ny = p, q
+                break
+        if nx != ny:
+            break
+    ups = [
+        (x, y, 0.0, 1), (y, x, 2.5, 0), (x, y, 0.0, 1), (x, y, 3.5, 0),  # delete/insert/delete/insert one H edge
+        (nx, ny, 1.5, 0), (ny, nx, 0.0, 1),                               # insert then delete a new edge
+        (nx, ny, 1.0, 1),                                                 # delete of an absent edge
+        (3, 3, 1.0, 0), (n + 5, 1, 1.0, 0), (-1, 2, 1.0, 1),             # self-loop, bad vertices
+        (1, 2, -1.0, 0), (1, 2, float("nan"), 0), (1, 2, float("inf"), 0), (1, 2, 1.0, 9),
+        (int(a[0]), int(b[0]), 1.0, 0),                                    # duplicate insert
+    ]
+    cols = list(zip(*ups))
+    res, ref = step_both(g, o, list(cols[0]), list(cols[1]), list(cols[2]), list(cols[3]), where="invalid")
+    assert set(res["status"].tolist()) >= {0, 1, 2, 3, 4, 5, 6}
+    ctx.close()
+
+
+def test_ring_recovery_and_fallback():
+    n = 9
+    a, b, w = ring(n)
+    keep = np.nonzero(~((a == 2) & (b == 3)))[0]
+    for T, want_fallback in ((n - 1, 0), (3, 1)):
+        ctx, g, o = pair(n, a, b, w, keep, T=T, s=8)
+        res, _ = step_both(g, o, [0], [1], [0.0], [1], where=f"ring T={T}")
+        assert res["fallback"][0] == want_fallback
+        ctx.close()
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_random_graphs_many_batches(seed):
+    rng = np.random.default_rng(100 + seed)
+    n = 300
+    a, b, w = random_connected(n, 700, rng, 0.1, 10.0)
+    h = W.init_sparsifier(n, a, b, w, rng)
+    ctx, g, o = pair(n, a, b, w, h, seed=seed * 7 + 3, K=[5.0, 50.0, 500.0][seed], T=[30, 100, 60][seed],
+                     s=[32, 16, 48][seed])
+    wl = W.Workload("rand", n, *W.canonical(a, b, w), h_ids=h)
+    stream = W.UpdateStream(wl, rng, ("uniform",), lambda r, u, v: r.uniform(0.1, 10.0, len(u)))
+    for bi in range(5):
+        bt = stream.next_batch(int(rng.integers(1, 120)), int(rng.integers(0, 120)))
+        step_both(g, o, bt.u, bt.v, bt.w, bt.op, where=f"seed {seed} batch {bi}")
+    ctx.close()
+
+
+def test_execution_forms_agree():
+    """Per-update launches, CUDA-graph replay, eager batched and every walk
+    launch shape give bit-identical outputs."""
+    wl, st = W.make_grid(40, 40)
+    batches = [st.next_batch(300, 200) for _ in range(3)]
+    outs = []
+    configs = [dict(walk_mode="batched", cuda_graphs=True), dict(walk_mode="batched", cuda_graphs=False),
+               dict(walk_mode="per_update", cuda_graphs=False)]
+    for kw in configs:
+        ctx = D.Context(**kw)
+        g = ctx.load_graph(wl.n, wl.a, wl.b, wl.w)
+        g.init_sparsifier(wl.a[wl.h_ids], wl.b[wl.h_ids])
+        rs = [g.apply(D.make_updates(bt.u, bt.v, bt.w, bt.op)) for bt in batches]
+        outs.append((rs, g.sparsifier()))
+        ctx.close()
+    for shape in [(32, 1, 0), (64, 2, 4), (256, 4, 0), (128, 2, 1)]:
+        ctx = D.Context()
+        g = ctx.load_graph(wl.n, wl.a, wl.b, wl.w)
+        g.init_sparsifier(wl.a[wl.h_ids], wl.b[wl.h_ids])
+        g.set_walk_shape(*shape)
+        rs = [g.apply(D.make_updates(bt.u, bt.v, bt.w, bt.op)) for bt in batches]
+        outs.append((rs, g.sparsifier()))
+        ctx.close()
+    ref_rs, ref_h = outs[0]
+    for rs, hh in outs[1:]:
+        for r0, r1 in zip(ref_rs, rs):
+            assert r0.tobytes() == r1.tobytes()
+        assert_edges_equal(hh, ref_h, "H")
+
+
+def test_device_io_matches_host_io():
+    import torch
+    wl, st = W.make_grid(32, 32)
+    bt = st.next_batch(200, 100)
+    ups = D.make_updates(bt.u, bt.v, bt.w, bt.op)
+    out = []
+    for dev in (False, True):
+        ctx = D.Context()
+        g = ctx.load_graph(wl.n, wl.a, wl.b, wl.w)
+        g.init_sparsifier(wl.a[wl.h_ids], wl.b[wl.h_ids])
+        if dev:
+            d_ups = torch.from_numpy(ups.view(np.uint8)).cuda()
+            d_res = torch.zeros(len(ups) * 32, dtype=torch.uint8, device="cuda")
+            g.apply_device(d_ups.data_ptr(), len(ups), d_res.data_ptr(), torch.cuda.current_stream().cuda_stream)
+            torch.cuda.synchronize()
+            res = d_res.cpu().numpy().view(D.RESULT_DTYPE)
+        else:
+            res = g.apply(ups)
+        out.append((res.tobytes(), g.sparsifier()))
+        ctx.close()
+    assert out[0][0] == out[1][0]
+    assert_edges_equal(out[0][1], out[1][1], "H")
+
+
+def test_pool_growth_and_compaction_keep_results():
+    """No slack and no headroom force relocations, pool growth and retries."""
+    wl, st = W.make_grid(24, 24)
+    ctx, g, o = pair(wl.n, wl.a, wl.b, wl.w, wl.h_ids, ctx_kw=dict(slack=1.0, overflow=0.0))
+    for bi in range(4):
+        bt = st.next_batch(400, 50)
+        step_both(g, o, bt.u, bt.v, bt.w, bt.op, where=f"tight batch {bi}")
+    g.compact()
+    bt = st.next_batch(100, 100)
+    step_both(g, o, bt.u, bt.v, bt.w, bt.op, where="after compaction")
+    ctx.close()
+
+
+def test_checkpoint_resume_by_update_id():
+    """Restoring H, G and the update sequence number replays bit-identically."""
+    wl, st = W.make_grid(24, 24)
+    b1 = st.next_batch(100, 60)
+    b2 = st.next_batch(100, 60)
+    ctx, g, _ = pair(wl.n, wl.a, wl.b, wl.w, wl.h_ids)
+    g.apply(D.make_updates(b1.u, b1.v, b1.w, b1.op))
+    ga, gb, gw = g.edges()
+    ha, hb, _ = g.sparsifier()
+    nid = g.next_update_id
+    r_direct = g.apply(D.make_updates(b2.u, b2.v, b2.w, b2.op))
+    g2 = ctx.load_graph(wl.n, ga, gb, gw)
+    g2.init_sparsifier(ha, hb)
+    g2.next_update_id = nid
+    r_resumed = g2.apply(D.make_updates(b2.u, b2.v, b2.w, b2.op))
+    assert r_direct.tobytes() == r_resumed.tobytes()
+    assert_edges_equal(g.sparsifier(), g2.sparsifier(), "H")
+    ctx.close()
+
+
+def test_invalid_graph_inputs():
+    ctx = D.Context()
+    with pytest.raises(D.DgError) as e:
+        ctx.load_graph(4, [0, 1], [1, 0], [1.0, 1.0])  # same edge twice
+    assert e.value.code == -1
+    with pytest.raises(D.DgError):
+        ctx.load_graph(4, [0], [4], [1.0])  # vertex out of range
+    with pytest.raises(D.DgError):
+        ctx.load_graph(4, [0], [1], [0.0])  # weight not > 0
+    g = ctx.load_graph(4, [0, 1], [1, 2], [1.0, 2.0])
+    with pytest.raises(D.DgError):
+        g.init_sparsifier([0], [2])  # not an edge of G
+    g.init_sparsifier([0, 1, 0], [1, 2, 1])  # repeated pair kept once
+    a, b, w = g.sparsifier()
+    assert a.tolist() == [0, 1] and b.tolist() == [1, 2] and w.tolist() == [1.0, 2.0]
+    ctx.close()
+
+
+def test_invariants_subgraph_and_components():
+    from oracle import checks
+    wl, st = W.make_grid(32, 32)
+    ctx, g, _ = pair(wl.n, wl.a, wl.b, wl.w, wl.h_ids)
+    for _ in range(3):
+        bt = st.next_batch(200, 100)
+        g.apply(D.make_updates(bt.u, bt.v, bt.w, bt.op))
+        ga, gb, gw = g.edges()
+        ha, hb, hw = g.sparsifier()
+        gm = dict(zip(zip(ga.tolist(), gb.tolist()), gw.tolist()))
+        assert all(gm.get((x, y)) == ww for x, y, ww in zip(ha.tolist(), hb.tolist(), hw.tolist()))
+        assert checks.n_components(wl.n, ha, hb) == checks.n_components(wl.n, ga, gb)
+    ctx.close()
+
+
+def test_mesh3d_small_multi_batch():
+    wl, st = W.make_mesh3d(24, 24, 24)
+    ctx, g, o = pair(wl.n, wl.a, wl.b, wl.w, wl.h_ids)
+    for bi in range(3):
+        bt = st.next_batch(2000, 2000)
+        step_both(g, o, bt.u, bt.v, bt.w, bt.op, where=f"mesh24 batch {bi}")
+    ctx.close()
+
+
+def test_mesh3d_full_size_batch():
+    """The 100x100x100 mesh (1M vertices, 2.97M edges) at its full batch size
+    (10k insertions + 10k deletions), in the launch form the benchmark times
+    (batched, CUDA graph): every update result and the final H, G match."""
+    wl, st = W.make_mesh3d()
+    ctx, g, o = pair(wl.n, wl.a, wl.b, wl.w, wl.h_ids)
+    for bi in range(2):
+        bt = st.next_batch(10000, 10000)
+        res, ref = step_both(g, o, bt.u, bt.v, bt.w, bt.op, where=f"mesh100 batch {bi}")
+        assert (res["status"] == 0).all()
+    assert g.stats()["graph_replayed"] == 1
+    ctx.close()

@@ -207,7 +207,8 @@ dg_status dg_apply_updates_device(dg_ctx* ctx, int32_t graph_id, int64_t nu, con
 /*
  * Edges of H: u[i] < v[i], lexicographic order, weights from G.  Writes at most
  * cap entries; *count_out receives |E(H)|.  cap < |E(H)| returns DG_E_INVALID
- * with *count_out set (call with cap = 0 to size the arrays).
+ * with *count_out set.  With u, v and w all NULL the call only sets *count_out
+ * and returns DG_OK (size query).
  */
 dg_status dg_query_sparsifier(dg_ctx* ctx, int32_t graph_id, int64_t cap, int32_t* u, int32_t* v,
                               double* w, int64_t* count_out);

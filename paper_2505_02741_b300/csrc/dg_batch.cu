@@ -22,6 +22,15 @@ constexpr int BT = 256;  // threads per block of the small batch kernels
 
 __device__ __forceinline__ bool batch_aborted(const uint32_t* d_err) { return (*d_err & ABORT_MASK) != 0u; }
 
+// timing event: an external event node while the stream is being captured
+static cudaError_t record_event(cudaEvent_t ev, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return e;
+    if (cs == cudaStreamCaptureStatusActive) return cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+    return cudaEventRecord(ev, st);
+}
+
 static int grid_for(uint64_t items) {
     uint64_t g = (items + BT - 1) / BT;
     const uint64_t cap = (uint64_t)device_sms() * 16;
@@ -585,6 +594,7 @@ void graph_export(Ctx& c, DGraph& g, bool which_h, int64_t cap, int32_t* u, int3
     DevAlloc& a = c.alloc;
     const uint64_t cnt = csr_edge_count(s, a, st);
     if (count) *count = (int64_t)cnt;
+    if (!u && !v && !w) return;  // size query
     if ((int64_t)cnt > cap) throw Error(DG_E_INVALID, "output arrays too small (count_out holds the size)");
     if (cnt == 0) return;
     DBuf<int32_t> da, db;
@@ -782,7 +792,7 @@ static void enqueue_walks(Ctx& c, DGraph& g, cudaStream_t st, int64_t per_update
     const WalkParams wp = params_of(c.cfg);
     const WalkRecs wr = recs_of(c, w);
     const WalkTasks tasks = tasks_of(w);
-    DG_CUDA(cudaEventRecordWithFlags(g.ev[0], st, cudaEventRecordExternal));
+    DG_CUDA(record_event(g.ev[0], st));
     if (per_update_W < 0) {
         launch_walk_batched(g.H.view(), g.G.view(), tasks, wp, wr, w.hdr.p, w.next.p, 0, w.b_max, g.shape,
                             w.err.p, st);
@@ -790,7 +800,7 @@ static void enqueue_walks(Ctx& c, DGraph& g, cudaStream_t st, int64_t per_update
         for (int64_t j = 0; j < per_update_W; ++j)
             launch_walk_one(g.H.view(), g.G.view(), tasks, wp, wr, w.hdr.p, (uint32_t)j, w.err.p, st);
     }
-    DG_CUDA(cudaEventRecordWithFlags(g.ev[1], st, cudaEventRecordExternal));
+    DG_CUDA(record_event(g.ev[1], st));
     launch_walk_reduce(tasks, wp, wr, w.res.p, w.best.p, w.ctr.p, c.cfg.record ? w.dbg_reason.p : nullptr,
                        c.cfg.record ? w.dbg_steps.p : nullptr, w.b_max, w.err.p, st);
 }
@@ -939,13 +949,13 @@ void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_updat
         if (!device_io)
             DG_CUDA(cudaMemcpyAsync(g.hs.res, w.res.p, sizeof(dg_update_result) * nu, cudaMemcpyDeviceToHost, st));
         enqueue_readback(g, st);
-        DG_CUDA(cudaEventRecordWithFlags(g.ev[3], st, cudaEventRecordExternal));
+        DG_CUDA(record_event(g.ev[3], st));
         wait_stream(c, st);
     };
 
     const bool use_graph = c.cfg.use_graphs && !per_update && !c.cfg.record;
     bool replayed = false;
-    DG_CUDA(cudaEventRecordWithFlags(g.ev[2], st, cudaEventRecordExternal));
+    DG_CUDA(record_event(g.ev[2], st));
     if (use_graph) {
         if (device_io) DG_CUDA(cudaMemcpyAsync(w.ups.p, ups, sizeof(dg_update) * nu, cudaMemcpyDeviceToDevice, st));
         CapturedStep& cs = g.steps[bucket];
@@ -981,7 +991,7 @@ void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_updat
         }
         DG_CUDA(cudaGraphLaunch(cs.exec, st));
         g_launches += cs.kernels;
-        DG_CUDA(cudaEventRecordWithFlags(g.ev[3], st, cudaEventRecordExternal));
+        DG_CUDA(record_event(g.ev[3], st));
         wait_stream(c, st);
         replayed = true;
     } else {
@@ -996,7 +1006,7 @@ void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_updat
         if (!(err & ABORT_MASK)) break;
         if (++retries > 8) throw Error(DG_E_NOMEM, "batch could not get enough device memory");
         const bool whole = handle_abort(c, g, err, st);
-        DG_CUDA(cudaEventRecordWithFlags(g.ev[2], st, cudaEventRecordExternal));
+        DG_CUDA(record_event(g.ev[2], st));
         if (whole) {
             stage_inputs();
             run_pre();

@@ -264,6 +264,62 @@ dg_status dg_submit_updates(dg_ctx* ctx, int32_t graph_id, int64_t nu, const dg_
    *latency_ms (nullable) receives submit-to-completion time. */
 dg_status dg_wait(dg_ctx* ctx, uint64_t ticket, int32_t timeout_ms, double* latency_ms);
 
+/*
+ * Allocation-free walk estimate.  The paper has no counterpart: this entry
+ * point exists for callers of this library that must not allocate device
+ * memory while they run -- for instance code that issues work while a stream
+ * is being captured, a latency-critical thread on which an allocation could
+ * stall the device, or a host application that has handed the GPU's memory to
+ * its own pool and cannot afford a call that grows it.
+ *
+ * It runs the s walkers of each query on a graph that is already resident
+ * (loaded earlier with dg_load_graph) and writes one estimate per query; it
+ * changes neither G nor H.  kind DG_OP_INSERT walks H from u toward v with the
+ * distortion threshold K and weight w; kind DG_OP_DELETE walks G from u toward
+ * v without K.  id is the update sequence number the Philox counter uses, so
+ * a query with the id, endpoints and weight of an insertion that
+ * dg_apply_updates is about to walk on the same H gets the same hit, nhits,
+ * best_walker, steps and r_est.
+ *
+ * d_queries and d_out are device pointers owned by the caller (nq records
+ * each).  The walkers' scratch is a static device array inside the library
+ * sized for DG_NOALLOC_MAX_QUERIES queries and DG_NOALLOC_MAX_WALKERS walkers
+ * (about 1.6 MB); every GPU that loads the library keeps it until the process
+ * exits.  nq > DG_NOALLOC_MAX_QUERIES or nq * s > DG_NOALLOC_MAX_WALKERS
+ * returns DG_E_INVALID without touching the device.  The call enqueues its
+ * kernels on cuda_stream (NULL = the context's stream) and returns without
+ * waiting; d_out is ready once that stream reaches this point.  It calls no
+ * device allocator.  The first call on a device looks up the static array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  All calls share the one array, which
+ * keeps the last call's contents: calls whose work overlaps on the GPU (other
+ * streams, other contexts on the same device) race and must be serialized by
+ * the caller.
+ */
+#define DG_NOALLOC_MAX_QUERIES 4096
+#define DG_NOALLOC_MAX_WALKERS 131072
+
+typedef struct {
+    int32_t u, v;     /* walk from u toward v */
+    double w;         /* weight of the inserted edge (kind DG_OP_INSERT) */
+    int32_t kind;     /* DG_OP_INSERT (walk H, threshold K) or DG_OP_DELETE (walk G, no K) */
+    int32_t reserved;
+    uint64_t id;      /* update sequence number keying the Philox counters */
+} dg_walk_query;      /* 32 bytes */
+
+typedef struct {
+    int32_t status;      /* DG_UPD_OK, DG_UPD_BAD_VERTEX, DG_UPD_SELF_LOOP, DG_UPD_BAD_WEIGHT or DG_UPD_BAD_OP */
+    int32_t nhits;       /* as dg_update_result */
+    int32_t best_walker;
+    int32_t steps;
+    double r_est;
+    uint8_t hit;
+    uint8_t reserved[7];
+} dg_walk_estimate;      /* 32 bytes */
+
+dg_status dg_walk_estimate_noalloc(dg_ctx* ctx, int32_t graph_id, int64_t nq, const dg_walk_query* d_queries,
+                                   dg_walk_estimate* d_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

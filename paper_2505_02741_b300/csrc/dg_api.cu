@@ -11,6 +11,8 @@ namespace dg {
 
 static thread_local std::string t_last_error;
 
+void set_last_error(const std::string& msg) { t_last_error = msg; }
+
 double now_ms() {
     using namespace std::chrono;
     return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();

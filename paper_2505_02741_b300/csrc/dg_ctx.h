@@ -51,5 +51,6 @@ struct Ctx {
 };
 
 double now_ms();
+void set_last_error(const std::string& msg);  // the text dg_last_error() returns on this thread
 
 }  // namespace dg

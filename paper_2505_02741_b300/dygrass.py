@@ -27,13 +27,20 @@ RESULT_DTYPE = np.dtype([("status", "<i4"), ("walked", "u1"), ("hit", "u1"), ("a
                          ("fallback", "u1"), ("nhits", "<i4"), ("best_walker", "<i4"), ("nrecovered", "<i4"),
                          ("steps", "<i4"), ("r_est", "<f8")])
 assert UPDATE_DTYPE.itemsize == 24 and RESULT_DTYPE.itemsize == 32
+QUERY_DTYPE = np.dtype([("u", "<i4"), ("v", "<i4"), ("w", "<f8"), ("kind", "<i4"), ("reserved", "<i4"),
+                        ("id", "<u8")])
+ESTIMATE_DTYPE = np.dtype([("status", "<i4"), ("nhits", "<i4"), ("best_walker", "<i4"), ("steps", "<i4"),
+                           ("r_est", "<f8"), ("hit", "u1"), ("reserved", "u1", (7,))])
+assert QUERY_DTYPE.itemsize == 32 and ESTIMATE_DTYPE.itemsize == 32
+NOALLOC_MAX_QUERIES = 4096
+NOALLOC_MAX_WALKERS = 131072
 
 # every symbol the header declares
 EXPORTS = ("dg_config_default", "dg_create", "dg_destroy", "dg_status_str", "dg_last_error", "dg_load_graph",
            "dg_unload_graph", "dg_init_sparsifier", "dg_apply_updates", "dg_apply_updates_device",
            "dg_query_sparsifier", "dg_query_graph", "dg_get_batch_stats", "dg_get_walker_records", "dg_compact",
            "dg_graph_bytes", "dg_launch_count", "dg_set_next_update_id", "dg_get_next_update_id",
-           "dg_set_walk_shape", "dg_submit_updates", "dg_wait")
+           "dg_set_walk_shape", "dg_submit_updates", "dg_wait", "dg_walk_estimate_noalloc")
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -101,6 +108,7 @@ def load_library(path: str | None = None):
         "dg_set_walk_shape": (i32, [P, i32, i32, i32, i32]),
         "dg_submit_updates": (i32, [P, i32, i64, P, P, C.POINTER(u64)]),
         "dg_wait": (i32, [P, u64, i32, C.POINTER(C.c_double)]),
+        "dg_walk_estimate_noalloc": (i32, [P, i32, i64, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -285,6 +293,14 @@ class Graph:
 
     def set_walk_shape(self, block=0, ilp=0, blocks_per_sm=0):
         _check(self._L.dg_set_walk_shape(self.ctx._h, self.gid, int(block), int(ilp), int(blocks_per_sm)))
+
+    def walk_estimate_noalloc(self, d_queries_ptr: int, nq: int, d_out_ptr: int, stream=None):
+        """Walk estimates for nq device-resident queries; the call allocates no
+        device memory (its scratch is a fixed static array in the library) and
+        returns once the work is enqueued on ``stream``."""
+        _check(self._L.dg_walk_estimate_noalloc(self.ctx._h, self.gid, int(nq), C.c_void_p(int(d_queries_ptr)),
+                                                C.c_void_p(int(d_out_ptr)),
+                                                None if stream is None else C.c_void_p(int(stream))))
 
     def submit(self, ups: np.ndarray):
         """Queue one request; returns (ticket, result array filled when waited)."""

@@ -228,7 +228,7 @@ def main():
 
     # ---- timed: device-resident batches -------------------------------------
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    walk_ms, steps_done, valid, launches, batch_lat = [], 0, 0, 0, []
+    walk_ms, steps_done, valid, launches, phases = [], 0, 0, 0, []
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -243,6 +243,7 @@ def main():
             ev[k][1].record(stream)
             s = g.stats()
             walk_ms.append(s["walk_ms"])
+            phases.append(s)
             steps_done += s["steps"]
             valid += s["valid"]
             launches += s["launches"]
@@ -332,6 +333,13 @@ def main():
                        "deletions": N_DEL, "K": wl.K, "T": wl.T, "s": wl.s, "parallelism": f"replicas{world}",
                        "l2": "flushed (256 MB write) between timed steps"},
             "walk_steps_per_s": walk_steps_per_s,
+            "per_batch": {"walk_steps": steps_done / args.steps,
+                          "walked_updates": float(np.mean([p["walked"] for p in phases])),
+                          "phase_ms": {k: float(np.mean([p[k] for p in phases])) for k in
+                                       ("mutate_ms", "walk_ms", "reduce_ms", "emit_ms", "commit_ms", "batch_ms")},
+                          "walk_shape": [phases[-1]["walk_block"], phases[-1]["walk_ilp"],
+                                         phases[-1]["walk_blocks_per_sm"]],
+                          "launches": launches / args.steps, "cuda_graph": bool(phases[-1]["graph_replayed"])},
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
             "per_update_form": pu,
             "roofline": roof,

@@ -147,6 +147,10 @@ typedef struct {
     int32_t walk_ilp;
     int32_t walk_blocks_per_sm;
     int32_t graph_replayed;  /* 1 if the step ran as a replayed CUDA graph */
+    double mutate_ms;        /* validation + G/H mutation (device time) */
+    double reduce_ms;        /* per-update reduction after the walks */
+    double emit_ms;          /* path replay and candidate emission */
+    double commit_ms;        /* sort, filter and merge into H, result copy-out */
 } dg_batch_stats;
 
 /* default configuration: seed 0, K 100, T 100, s 32, early exit on, batched walks,

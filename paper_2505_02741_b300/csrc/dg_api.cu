@@ -187,6 +187,12 @@ dg_status dg_create(const dg_config* cfg_in, dg_ctx** out) {
         DG_CUDA(cudaGetDeviceCount(&ndev));
         if (cfg.device < 0 || cfg.device >= ndev) throw Error(DG_E_INVALID, "bad device ordinal");
         DG_CUDA(cudaSetDevice(cfg.device));
+        // optional L2 fetch granularity hint for this process's context (bytes;
+        // a walk step reads one 32-byte sector, so larger fetches waste DRAM bandwidth)
+        if (const char* f = std::getenv("DG_L2_FETCH")) {
+            const long v = std::strtol(f, nullptr, 10);
+            if (v == 0 || v == 32 || v == 64 || v == 128) DG_CUDA(cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)v));
+        }
         auto c = std::make_unique<Ctx>();
         c->device = cfg.device;
         c->cfg.seed = cfg.seed;

@@ -292,7 +292,7 @@ uint64_t BatchWS::bytes() const {
     b += t_wpq.bytes() + recR.bytes() + t_kind.bytes() + best.bytes();
     b += ckeys.bytes() + ckeys_alt.bytes() + ck2.bytes() + cvals.bytes() + cvals_alt.bytes() + chist.bytes();
     b += cscan.bytes() + ccount.bytes() + cflag.bytes() + cpos.bytes() + cv2.bytes() + ccount2.bytes();
-    b += cw.bytes() + kind_ins.bytes() + path_buf.bytes();
+    b += cw.bytes() + kind_ins.bytes() + path_buf.bytes() + path_len.bytes() + path_w.bytes();
     b += dbg_reason.bytes() + dbg_steps.bytes() + dbg_paths.bytes();
     b += apG.bytes() + apH.bytes() + apC.bytes();
     return b;
@@ -374,6 +374,8 @@ static void ensure_ws(Ctx& c, DGraph& g, uint32_t b_max, cudaStream_t st) {
     w.ccount.ensure(a, 1, st);
     w.ccount2.ensure(a, 1, st);
     w.path_buf.ensure(a, (size_t)B * (T + 1), st);
+    w.path_w.ensure(a, (size_t)B * T, st);
+    w.path_len.ensure(a, B, st);
     if (c.cfg.record) {
         w.dbg_reason.ensure(a, (size_t)B * s, st);
         w.dbg_steps.ensure(a, (size_t)B * s, st);
@@ -382,7 +384,7 @@ static void ensure_ws(Ctx& c, DGraph& g, uint32_t b_max, cudaStream_t st) {
     w.apG.ensure(a, B2, (uint64_t)B2 * 16, st);
     w.apH.ensure(a, B2, (uint64_t)B2 * 16, st);
     w.b_max = b_max;
-    ensure_cands(c, g, std::max<uint32_t>(B2 * 4, w.cand_cap), st);
+    ensure_cands(c, g, std::max<uint32_t>(B2 * 2, w.cand_cap), st);
     // pinned staging
     if (g.hs.cap < b_max) {
         if (g.hs.ups) {
@@ -501,7 +503,7 @@ void graph_load(Ctx& c, DGraph& g, int32_t n, int64_t m, const int32_t* u, const
     csr_build(g.H, a, nullptr, nullptr, nullptr, 0, nullptr, st);
     g.has_h = true;  // empty sparsifier
     g.next_id = 0;
-    for (int i = 0; i < 4; ++i) DG_CUDA(cudaEventCreate(&g.ev[i]));
+    for (int i = 0; i < 7; ++i) DG_CUDA(cudaEventCreate(&g.ev[i]));
     wait_stream(c, st);
 }
 
@@ -639,7 +641,7 @@ void graph_release(Ctx& c, DGraph& g) {
     REL(hpos); REL(hvals); REL(hcount); REL(gkind); REL(ghrem); REL(kind_del); REL(gw); REL(t_u); REL(t_v);
     REL(t_idx); REL(t_kstar); REL(t_count); REL(meta); REL(t_wpq); REL(recR); REL(t_kind); REL(best);
     REL(ckeys); REL(ckeys_alt); REL(ck2); REL(cvals); REL(cvals_alt); REL(chist); REL(cscan); REL(ccount);
-    REL(cflag); REL(cpos); REL(cv2); REL(ccount2); REL(cw); REL(kind_ins); REL(path_buf); REL(dbg_reason);
+    REL(cflag); REL(cpos); REL(cv2); REL(ccount2); REL(cw); REL(kind_ins); REL(path_buf); REL(path_w); REL(path_len); REL(dbg_reason);
     REL(dbg_steps); REL(dbg_paths);
 #undef REL
     w.b_max = 0;
@@ -652,7 +654,7 @@ void graph_release(Ctx& c, DGraph& g) {
     if (g.hs.tops) cudaFreeHost(g.hs.tops);
     if (g.hs.counts) cudaFreeHost(g.hs.counts);
     g.hs = HostStage{};
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 7; ++i)
         if (g.ev[i]) cudaEventDestroy(g.ev[i]);
     if (g.stream) cudaStreamDestroy(g.stream);
     g.stream = nullptr;
@@ -712,7 +714,7 @@ static void enqueue_mutate(Ctx& c, DGraph& g, cudaStream_t st) {
     k_val_prep<<<grid_for(B), BT, 0, st>>>(w.ups.p, w.hdr.p, n, B, w.res.p, w.vkeys.p, w.vvals.p, w.wkind.p,
                                           w.fin_w.p);
     ++g_launches;
-    SortBufs vs{w.vkeys.p, w.vvals.p, w.vkeys_alt.p, w.vvals_alt.p, w.vhist.p, w.vscan.p};
+    SortBufs vs{w.vkeys.p, w.vvals.p, w.vkeys_alt.p, w.vvals_alt.p, w.vhist.p, w.vscan.p, w.err.p};
     const bool valt = radix_sort_pairs(vs, d_nu, B, bit_length((uint64_t)n * n), st);
     RunArgs ra;
     ra.keys = valt ? w.vkeys_alt.p : w.vkeys.p;
@@ -742,13 +744,14 @@ static void enqueue_mutate(Ctx& c, DGraph& g, cudaStream_t st) {
         j.out[0] = w.wpos.p;
         j.total[0] = w.t_count.p;
         j.k = 1;
+        j.err = w.err.p;
         scan_exclusive(j, d_nu, B, w.vscan.p, st);
     }
     WalkTasks tasks = tasks_of(w);
     k_make_tasks<<<grid_for(B), BT, 0, st>>>(w.ups.p, w.wkind.p, w.wpos.p, w.hdr.p, B, tasks);
     ++g_launches;
     // net G changes, sorted by (vertex, neighbour)
-    SortBufs gs{w.gkeys.p, w.gvals.p, w.gkeys_alt.p, w.gvals_alt.p, w.ghist.p, w.gscan.p};
+    SortBufs gs{w.gkeys.p, w.gvals.p, w.gkeys_alt.p, w.gvals_alt.p, w.ghist.p, w.gscan.p, w.err.p};
     const bool galt = radix_sort_pairs(gs, w.gcount.p, B2, bit_length((uint64_t)n * n - 1), st);
     const uint64_t* gk = galt ? w.gkeys_alt.p : w.gkeys.p;
     const uint32_t* gv = galt ? w.gvals_alt.p : w.gvals.p;
@@ -760,6 +763,7 @@ static void enqueue_mutate(Ctx& c, DGraph& g, cudaStream_t st) {
         j.out[0] = w.hpos.p;
         j.total[0] = w.hcount.p;
         j.k = 1;
+        j.err = w.err.p;
         scan_exclusive(j, w.gcount.p, B2, w.gscan.p, st);
     }
     k_compact_kv<<<grid_for(B2), BT, 0, st>>>(gk, gv, w.hflag.p, w.hpos.p, w.gcount.p, B2, w.hkeys.p, w.hvals.p);
@@ -783,6 +787,7 @@ static void enqueue_mutate(Ctx& c, DGraph& g, cudaStream_t st) {
     csr_plan(g.H, clH, w.apH, w.err.p, ERR_POOL_G, ERR_CAP_PRE, st);
     csr_exec(g.G, clG, w.apG, g.touched.p, w.err.p, st);
     csr_exec(g.H, clH, w.apH, g.touched.p, w.err.p, st);
+    DG_CUDA(record_event(g.ev[4], st));
 }
 
 // walks on the snapshot (H' for insertions, G_b for deletions) and the
@@ -803,6 +808,7 @@ static void enqueue_walks(Ctx& c, DGraph& g, cudaStream_t st, int64_t per_update
     DG_CUDA(record_event(g.ev[1], st));
     launch_walk_reduce(tasks, wp, wr, w.res.p, w.best.p, w.ctr.p, c.cfg.record ? w.dbg_reason.p : nullptr,
                        c.cfg.record ? w.dbg_steps.p : nullptr, w.b_max, w.err.p, st);
+    DG_CUDA(record_event(g.ev[5], st));
 }
 
 // kept insertions, recovered and fallback edges -> H (re-runnable)
@@ -817,8 +823,9 @@ static void enqueue_commit(Ctx& c, DGraph& g, cudaStream_t st) {
     cd.count = w.ccount.p;
     cd.cap = CC;
     launch_emit(g.H.view(), g.G.view(), tasks_of(w), params_of(c.cfg), recs_of(c, w), w.hdr.p, w.best.p, w.fin_w.p,
-                w.res.p, w.ctr.p, cd, w.path_buf.p, B, w.err.p, st);
-    SortBufs cs{w.ckeys.p, w.cvals.p, w.ckeys_alt.p, w.cvals_alt.p, w.chist.p, w.cscan.p};
+                w.res.p, w.ctr.p, cd, PathBufs{w.path_buf.p, w.path_w.p, w.path_len.p}, B, w.err.p, st);
+    DG_CUDA(record_event(g.ev[6], st));
+    SortBufs cs{w.ckeys.p, w.cvals.p, w.ckeys_alt.p, w.cvals_alt.p, w.chist.p, w.cscan.p, w.err.p};
     const bool calt = radix_sort_pairs(cs, w.ccount.p, CC, bit_length((uint64_t)n * n - 1), st);
     const uint64_t* ck = calt ? w.ckeys_alt.p : w.ckeys.p;
     const uint32_t* cv = calt ? w.cvals_alt.p : w.cvals.p;
@@ -830,6 +837,7 @@ static void enqueue_commit(Ctx& c, DGraph& g, cudaStream_t st) {
         j.out[0] = w.cpos.p;
         j.total[0] = w.ccount2.p;
         j.k = 1;
+        j.err = w.err.p;
         scan_exclusive(j, w.ccount.p, CC, w.cscan.p, st);
     }
     k_compact_kv<<<grid_for(CC), BT, 0, st>>>(ck, cv, w.cflag.p, w.cpos.p, w.ccount.p, CC, w.ck2.p, w.cv2.p);
@@ -1003,6 +1011,7 @@ void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_updat
     for (;;) {
         const uint32_t err = g.hs.err[0];
         if (err & ERR_INTERNAL) throw Error(DG_E_CUDA, "internal consistency check failed on the device");
+        if (err & ERR_SPIN) throw Error(DG_E_TIMEOUT, "a bounded device wait gave up");
         if (!(err & ABORT_MASK)) break;
         if (++retries > 8) throw Error(DG_E_NOMEM, "batch could not get enough device memory");
         const bool whole = handle_abort(c, g, err, st);
@@ -1038,6 +1047,10 @@ void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_updat
     float ms = 0.f;
     s.walk_ms = (cudaEventElapsedTime(&ms, g.ev[0], g.ev[1]) == cudaSuccess) ? ms : -1.0;
     s.batch_ms = (cudaEventElapsedTime(&ms, g.ev[2], g.ev[3]) == cudaSuccess) ? ms : -1.0;
+    s.mutate_ms = (cudaEventElapsedTime(&ms, g.ev[2], g.ev[4]) == cudaSuccess) ? ms : -1.0;
+    s.reduce_ms = (cudaEventElapsedTime(&ms, g.ev[1], g.ev[5]) == cudaSuccess) ? ms : -1.0;
+    s.emit_ms = (cudaEventElapsedTime(&ms, g.ev[5], g.ev[6]) == cudaSuccess) ? ms : -1.0;
+    s.commit_ms = (cudaEventElapsedTime(&ms, g.ev[6], g.ev[3]) == cudaSuccess) ? ms : -1.0;
     cudaGetLastError();
     s.retries = retries;
     s.graph_replayed = replayed ? 1 : 0;

@@ -57,7 +57,8 @@ struct BatchWS {
     DBuf<uint32_t> cvals, cvals_alt, chist, cscan, ccount, cflag, cpos, cv2, ccount2;
     DBuf<double> cw;
     DBuf<uint8_t> kind_ins;
-    DBuf<uint32_t> path_buf;
+    DBuf<uint32_t> path_buf, path_len;
+    DBuf<double> path_w;
     // debug
     DBuf<int32_t> dbg_reason, dbg_steps, dbg_paths;
     ApplyScratch apG, apH, apC;
@@ -96,7 +97,8 @@ struct DGraph {
     uint64_t layout_gen = 1;  // bumped whenever a buffer baked into a captured step moves
     std::map<uint32_t, CapturedStep> steps;  // by batch-size class
     cudaStream_t stream = nullptr;           // private stream (serving)
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // timing events: 0/1 walk, 2/3 batch, 4 end of mutation, 5 end of reduction, 6 end of emission
+    cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     dg_batch_stats stats{};
     std::mutex mu;
     uint64_t bytes() const { return G.bytes() + H.bytes() + touched.bytes() + ws.bytes(); }

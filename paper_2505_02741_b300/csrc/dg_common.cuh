@@ -56,6 +56,7 @@ enum : uint32_t {
     ERR_CAP_PRE = 1u << 5,      // staging space short before the walks (batch retried)
     ERR_CAP_COMMIT = 1u << 6,   // candidate / staging space short at commit (commit retried)
     ERR_INTERNAL = 1u << 7,     // consistency check failed (lookup of an edge that must exist)
+    ERR_SPIN = 1u << 8,         // a bounded look-back wait gave up (same bit as PRIM_ERR_SPIN)
 };
 constexpr uint32_t ABORT_MASK = ERR_POOL_G | ERR_POOL_H | ERR_CAP_PRE | ERR_CAP_COMMIT;
 

@@ -263,6 +263,7 @@ void csr_plan(CSR& g, const ChangeList& cl, ApplyScratch& s, uint32_t* d_err, ui
     j1.in[1] = s.f_ins.p;  j1.out[1] = s.p_ins.p;  j1.total[1] = tot + TOT_NI;
     j1.in[2] = s.f_del.p;  j1.out[2] = s.p_del.p;  j1.total[2] = tot + TOT_ND;
     j1.k = 3;
+    j1.err = d_err;
     scan_exclusive(j1, cl.d_count, C, s.scan_tmp.p, st);
     PlanArgs pa;
     pa.cl = cl;
@@ -279,6 +280,7 @@ void csr_plan(CSR& g, const ChangeList& cl, ApplyScratch& s, uint32_t* d_err, ui
     j2.in[1] = s.ndeg.p; j2.out[1] = s.s_off.p; j2.total[1] = tot + TOT_S;
     j2.in[2] = s.work.p; j2.out[2] = s.w_off.p; j2.total[2] = tot + TOT_WK;
     j2.k = 3;
+    j2.err = d_err;
     scan_exclusive(j2, tot + TOT_X, C, s.scan_tmp.p, st);
     k_plan_alloc<<<1, 1, 0, st>>>(g.view(), tot, s.s_cap, d_err, pool_bit, cap_bit);
     ++g_launches;

@@ -1,5 +1,12 @@
-// dg_prims.cu -- exclusive scan and stable LSD radix sort (warp-tiled,
-// __match_any_sync ranking) with device-side element counts.
+// dg_prims.cu -- exclusive scan and stable LSD radix sort with device-side
+// element counts.
+//
+// Both large-array paths are single-pass with decoupled look-back: a block
+// takes the next tile index from an atomic counter (so every tile it waits on
+// belongs to a block that is already running), publishes its tile aggregate,
+// then walks back over its predecessors until it meets an inclusive prefix.
+// Every wait is bounded: after SPIN_LIMIT polls the block records
+// PRIM_ERR_SPIN and stops waiting, so no kernel here can hang.
 #include "dg_prims.cuh"
 
 namespace dg {
@@ -15,73 +22,58 @@ int bit_length(uint64_t x) {
     return b;
 }
 
-// ---------------------------------------------------------------------------
-// scan
-// ---------------------------------------------------------------------------
-static inline uint32_t scan_blocks(uint32_t n_max) { return (n_max + SCAN_TILE - 1) / SCAN_TILE; }
-
-size_t scan_tmp_words(uint32_t n_max) { return 3u * (size_t)(scan_blocks(n_max) + 1); }
+constexpr uint32_t SPIN_LIMIT = 1u << 20;
 
 __device__ __forceinline__ uint32_t load_n(const uint32_t* d_n, uint32_t n_max) {
     return d_n ? min(*d_n, n_max) : n_max;
 }
 
+__device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) { return *(const volatile uint32_t*)p; }
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
+    return *(const volatile unsigned long long*)p;
+}
+
+// ---------------------------------------------------------------------------
+// scan
+// ---------------------------------------------------------------------------
 struct ScanArgs {
     const uint32_t* in[3];
     uint32_t* out[3];
     uint32_t* total[3];
     int k;
+    uint32_t* err;
 };
 
-__device__ __forceinline__ uint32_t block_sum(uint32_t v, uint32_t* sh) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0) sh[w] = v;
-    __syncthreads();
-    uint32_t t = 0;
-    if (threadIdx.x < 32) {
-        t = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0u;
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    }
-    return t;  // valid in thread 0
-}
+constexpr uint32_t SMALL_SCAN_MAX = 16384;
+constexpr int LB_THREADS = 256;
+constexpr int LB_ITEMS = 8;
+constexpr uint32_t LB_TILE = LB_THREADS * LB_ITEMS;
 
-__global__ void k_scan_reduce(ScanArgs a, const uint32_t* d_n, uint32_t n_max, uint32_t* tmp,
-                              uint32_t nb_max) {
-    __shared__ uint32_t sh[32];
-    const uint32_t n = load_n(d_n, n_max);
-    const uint32_t base = blockIdx.x * SCAN_TILE;
-    for (int j = 0; j < a.k; ++j) {
-        uint32_t s = 0;
-        if (base < n) {
-#pragma unroll
-            for (int i = 0; i < SCAN_ITEMS; ++i) {
-                uint32_t idx = base + i * SCAN_THREADS + threadIdx.x;
-                if (idx < n) s += a.in[j][idx];
-            }
-        }
-        uint32_t t = block_sum(s, sh);
-        if (threadIdx.x == 0) tmp[j * (nb_max + 1) + blockIdx.x] = t;
-    }
-}
+static inline uint32_t lb_tiles(uint32_t n_max) { return (n_max + LB_TILE - 1) / LB_TILE; }
 
-// one CTA: exclusive scan of the block sums, chunk by chunk with a carry
-__global__ void k_scan_mid(ScanArgs a, const uint32_t* d_n, uint32_t n_max, uint32_t* tmp,
-                           uint32_t nb_max) {
+// layout of tmp: [counter (2 words, 8-byte aligned) | status u64 x 3 x tiles]
+size_t scan_tmp_words(uint32_t n_max) { return 4 + 2ull * 3 * (lb_tiles(n_max) + 1); }
+
+// one CTA walks the array in chunks of 1024 x 8 with a running carry
+__global__ void __launch_bounds__(1024) k_scan_single(ScanArgs a, const uint32_t* d_n, uint32_t n_max) {
     __shared__ uint32_t sh[32];
     __shared__ uint32_t carry_sh;
     const uint32_t n = load_n(d_n, n_max);
-    const uint32_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    constexpr int IT = 8;
     for (int j = 0; j < a.k; ++j) {
-        uint32_t* t = tmp + j * (nb_max + 1);
         if (threadIdx.x == 0) carry_sh = 0;
         __syncthreads();
-        for (uint32_t c0 = 0; c0 < nb; c0 += blockDim.x) {
-            uint32_t idx = c0 + threadIdx.x;
-            uint32_t v = idx < nb ? t[idx] : 0u;
-            uint32_t x = v;
+        for (uint32_t c0 = 0; c0 < n; c0 += blockDim.x * IT) {
+            const uint32_t mine = c0 + threadIdx.x * IT;
+            uint32_t v[IT];
+            uint32_t s = 0;
+#pragma unroll
+            for (int i = 0; i < IT; ++i) {
+                v[i] = (mine + i < n) ? a.in[j][mine + i] : 0u;
+                s += v[i];
+            }
+            uint32_t x = s;
             for (int o = 1; o < 32; o <<= 1) {
                 uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
                 if (l >= o) x += y;
@@ -89,19 +81,23 @@ __global__ void k_scan_mid(ScanArgs a, const uint32_t* d_n, uint32_t n_max, uint
             if (l == 31) sh[w] = x;
             __syncthreads();
             if (threadIdx.x < 32) {
-                uint32_t s = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0u;
+                uint32_t t = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0u;
                 for (int o = 1; o < 32; o <<= 1) {
-                    uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
-                    if (l >= o) s += y;
+                    uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+                    if (l >= o) t += y;
                 }
-                sh[l] = s;  // inclusive per-warp prefix
+                sh[l] = t;
             }
             __syncthreads();
-            const uint32_t warp_prefix = (w > 0) ? sh[w - 1] : 0u;
             const uint32_t carry = carry_sh;
-            if (idx < nb) t[idx] = carry + warp_prefix + x - v;
+            uint32_t run = carry + ((w > 0) ? sh[w - 1] : 0u) + x - s;
+#pragma unroll
+            for (int i = 0; i < IT; ++i) {
+                if (mine + i < n) a.out[j][mine + i] = run;
+                run += v[i];
+            }
             __syncthreads();
-            if (threadIdx.x == blockDim.x - 1) carry_sh = carry + warp_prefix + x;
+            if (threadIdx.x == blockDim.x - 1) carry_sh = carry + sh[31];
             __syncthreads();
         }
         if (threadIdx.x == 0 && a.total[j]) *a.total[j] = carry_sh;
@@ -109,19 +105,29 @@ __global__ void k_scan_mid(ScanArgs a, const uint32_t* d_n, uint32_t n_max, uint
     }
 }
 
-__global__ void k_scan_apply(ScanArgs a, const uint32_t* d_n, uint32_t n_max, const uint32_t* tmp,
-                             uint32_t nb_max) {
-    __shared__ uint32_t sh[32];
+// status word: high 32 bits flag (0 empty, 1 aggregate, 2 inclusive), low 32 bits value
+constexpr unsigned long long LB_AGG = 1ull << 32, LB_INC = 2ull << 32;
+
+__global__ void __launch_bounds__(LB_THREADS) k_scan_lookback(ScanArgs a, const uint32_t* d_n, uint32_t n_max,
+                                                             uint32_t* tmp, uint32_t tiles) {
+    __shared__ uint32_t sh[LB_THREADS / 32];
+    __shared__ uint32_t s_tile, s_prefix;
+    unsigned long long* status = reinterpret_cast<unsigned long long*>(tmp + 4);
     const uint32_t n = load_n(d_n, n_max);
-    const uint32_t base = blockIdx.x * SCAN_TILE;
-    if (base >= n) return;
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (threadIdx.x == 0) s_tile = atomicAdd(tmp, 1u);
+    __syncthreads();
+    const uint32_t t = s_tile;
+    const uint32_t base = t * LB_TILE;
+    const uint32_t nt = (n + LB_TILE - 1) / LB_TILE;  // tiles holding data
+    if (t >= tiles) return;
     for (int j = 0; j < a.k; ++j) {
-        uint32_t v[SCAN_ITEMS];
+        unsigned long long* st = status + (size_t)j * (tiles + 1);
+        const uint32_t mine = base + threadIdx.x * LB_ITEMS;
+        uint32_t v[LB_ITEMS];
         uint32_t s = 0;
-        const uint32_t mine = base + threadIdx.x * SCAN_ITEMS;
 #pragma unroll
-        for (int i = 0; i < SCAN_ITEMS; ++i) {
+        for (int i = 0; i < LB_ITEMS; ++i) {
             v[i] = (mine + i < n) ? a.in[j][mine + i] : 0u;
             s += v[i];
         }
@@ -130,24 +136,52 @@ __global__ void k_scan_apply(ScanArgs a, const uint32_t* d_n, uint32_t n_max, co
             uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
             if (l >= o) x += y;
         }
-        __syncthreads();
         if (l == 31) sh[w] = x;
         __syncthreads();
         if (threadIdx.x < 32) {
-            uint32_t t = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0u;
+            uint32_t tt = (l < LB_THREADS / 32) ? sh[l] : 0u;
             for (int o = 1; o < 32; o <<= 1) {
-                uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
-                if (l >= o) t += y;
+                uint32_t y = __shfl_up_sync(0xffffffffu, tt, o);
+                if (l >= o) tt += y;
             }
-            sh[l] = t;
+            if (l < LB_THREADS / 32) sh[l] = tt;
         }
         __syncthreads();
-        uint32_t run = tmp[j * (nb_max + 1) + blockIdx.x] + ((w > 0) ? sh[w - 1] : 0u) + x - s;
+        const uint32_t agg = sh[LB_THREADS / 32 - 1];
+        if (threadIdx.x == 0) {
+            uint32_t excl = 0;
+            if (t == 0) {
+                atomicExch(&st[t], LB_INC | agg);
+            } else {
+                atomicExch(&st[t], LB_AGG | agg);
+                int p = (int)t - 1;
+                while (p >= 0) {
+                    unsigned long long sv = 0;
+                    uint32_t spins = 0;
+                    while (((sv = ld_volatile_u64(&st[p])) >> 32) == 0ull && ++spins < SPIN_LIMIT) __nanosleep(32);
+                    if ((sv >> 32) == 0ull) {
+                        if (a.err) atomicOr(a.err, PRIM_ERR_SPIN);
+                        break;
+                    }
+                    excl += (uint32_t)sv;
+                    if ((sv >> 32) == 2ull) break;
+                    --p;
+                }
+                __threadfence();
+                atomicExch(&st[t], LB_INC | (unsigned long long)(excl + agg));
+            }
+            s_prefix = excl;
+            if (t + 1 == nt && a.total[j]) *a.total[j] = excl + agg;
+            if (nt == 0 && t == 0 && a.total[j]) *a.total[j] = 0;
+        }
+        __syncthreads();
+        uint32_t run = s_prefix + ((w > 0) ? sh[w - 1] : 0u) + x - s;
 #pragma unroll
-        for (int i = 0; i < SCAN_ITEMS; ++i) {
+        for (int i = 0; i < LB_ITEMS; ++i) {
             if (mine + i < n) a.out[j][mine + i] = run;
             run += v[i];
         }
+        __syncthreads();
     }
 }
 
@@ -160,118 +194,176 @@ void scan_exclusive(const ScanJob& job, const uint32_t* d_n, uint32_t n_max, uin
         a.total[j] = job.total[j];
     }
     a.k = job.k;
-    const uint32_t nb = scan_blocks(n_max);
-    if (nb > 0) {
-        k_scan_reduce<<<nb, SCAN_THREADS, 0, st>>>(a, d_n, n_max, tmp, nb);
+    a.err = job.err;
+    if (n_max <= SMALL_SCAN_MAX) {
+        k_scan_single<<<1, 1024, 0, st>>>(a, d_n, n_max);
         ++g_launches;
+        return;
     }
-    k_scan_mid<<<1, 1024, 0, st>>>(a, d_n, n_max, tmp, nb);
+    const uint32_t tiles = lb_tiles(n_max);
+    cudaMemsetAsync(tmp, 0, scan_tmp_words(n_max) * 4, st);
+    k_scan_lookback<<<tiles, LB_THREADS, 0, st>>>(a, d_n, n_max, tmp, tiles);
     ++g_launches;
-    if (nb > 0) {
-        k_scan_apply<<<nb, SCAN_THREADS, 0, st>>>(a, d_n, n_max, tmp, nb);
-        ++g_launches;
-    }
 }
 
 // ---------------------------------------------------------------------------
-// radix sort: warp tiles of 32 * chunks elements, 8-bit digits
+// one-sweep radix sort
 // ---------------------------------------------------------------------------
-constexpr int SORT_WARPS = 8;
+constexpr int OS_THREADS = 512;
+constexpr int OS_WARPS = OS_THREADS / 32;
+constexpr int OS_ITEMS = 4;
+constexpr uint32_t OS_TILE = OS_THREADS * OS_ITEMS;  // 2048 keys, a warp holds 128 consecutive ones
+constexpr int OS_MAX_PASSES = 8;
+constexpr uint32_t OS_AGG = 1u << 30, OS_INC = 2u << 30, OS_VAL = (1u << 30) - 1u;
 
-static inline uint32_t sort_chunks(uint32_t n_max) {
-    // enough tiles to occupy the GPU, at most 64 chunks (2048 keys) per warp
-    uint32_t c = n_max / (148u * 8u * 32u);
-    if (c < 1) c = 1;
-    if (c > 64) c = 64;
-    return c;
-}
-static inline uint32_t sort_tiles(uint32_t n_max) {
-    const uint32_t tile = 32u * sort_chunks(n_max);
-    uint32_t t = (n_max + tile - 1) / tile;
+static inline uint32_t os_tiles(uint32_t n_max) {
+    uint32_t t = (n_max + OS_TILE - 1) / OS_TILE;
     return t < 1 ? 1 : t;
 }
 
-size_t sort_hist_words(uint32_t n_max) { return 256u * (size_t)sort_tiles(n_max) + 1; }
-size_t sort_scan_tmp_words(uint32_t n_max) {
-    return scan_tmp_words((uint32_t)(256u * (size_t)sort_tiles(n_max)));
-}
+// hist layout: [digit totals OS_MAX_PASSES x 256 | tile counters 32 | status tiles x 256]
+constexpr size_t OS_GHIST = 0;
+constexpr size_t OS_CTR = OS_MAX_PASSES * 256;
+constexpr size_t OS_STATUS = OS_CTR + 32;
 
-__global__ void k_radix_hist(const uint64_t* __restrict__ keys, const uint32_t* d_n, uint32_t n_max,
-                             int shift, uint32_t chunks, uint32_t ntiles, uint32_t* __restrict__ hist) {
-    __shared__ uint32_t cnt[SORT_WARPS][256];
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    const uint32_t t = blockIdx.x * SORT_WARPS + w;
-    for (int d = l; d < 256; d += 32) cnt[w][d] = 0;
-    __syncwarp();
-    if (t >= ntiles) return;
-    const uint32_t n = load_n(d_n, n_max);
-    const uint32_t base = t * 32u * chunks;
-#pragma unroll 4
-    for (uint32_t c = 0; c < chunks; ++c) {
-        const uint32_t idx = base + c * 32u + l;
-        if (idx < n) atomicAdd(&cnt[w][(uint32_t)(keys[idx] >> shift) & 255u], 1u);
-    }
-    __syncwarp();
-    for (int d = l; d < 256; d += 32) hist[(size_t)d * ntiles + t] = cnt[w][d];
-}
+size_t sort_hist_words(uint32_t n_max) { return OS_STATUS + 256ull * os_tiles(n_max) + 64; }
+size_t sort_scan_tmp_words(uint32_t n_max) { return scan_tmp_words(n_max + 1); }
 
-__global__ void k_radix_scatter(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
-                                uint64_t* __restrict__ okeys, uint32_t* __restrict__ ovals,
-                                const uint32_t* d_n, uint32_t n_max, int shift, uint32_t chunks,
-                                uint32_t ntiles, const uint32_t* __restrict__ hist) {
-    __shared__ uint32_t cnt[SORT_WARPS][256];
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    const uint32_t t = blockIdx.x * SORT_WARPS + w;
-    if (t >= ntiles) return;
-    for (int d = l; d < 256; d += 32) cnt[w][d] = hist[(size_t)d * ntiles + t];
-    __syncwarp();
+// digit totals of every pass in one read of the keys (warp-aggregated atomics)
+__global__ void __launch_bounds__(256) k_os_hist(const uint64_t* __restrict__ keys, const uint32_t* d_n,
+                                                 uint32_t n_max, int passes, uint32_t* __restrict__ ghist) {
+    __shared__ uint32_t h[OS_MAX_PASSES][256];
+    for (int i = threadIdx.x; i < OS_MAX_PASSES * 256; i += blockDim.x) (&h[0][0])[i] = 0;
+    __syncthreads();
     const uint32_t n = load_n(d_n, n_max);
-    const uint32_t base = t * 32u * chunks;
+    const int l = threadIdx.x & 31;
     const uint32_t lt = (1u << l) - 1u;
-    for (uint32_t c = 0; c < chunks; ++c) {
-        const uint32_t idx = base + c * 32u + l;
+    (void)lt;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    // whole warps iterate together so the match below always sees a full warp
+    for (uint32_t i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < n; i0 += stride) {
+        const uint32_t i = i0 + l;
+        const bool valid = i < n;
+        const uint64_t k = valid ? keys[i] : 0ull;
+        for (int p = 0; p < passes; ++p) {
+            const uint32_t d = valid ? (uint32_t)(k >> (8 * p)) & 255u : 256u;
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            if (valid && l == __ffs(peers) - 1) atomicAdd(&h[p][d], (uint32_t)__popc(peers));
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) {
+        const uint32_t c = (&h[0][0])[i];
+        if (c) atomicAdd(&ghist[i], c);
+    }
+}
+
+__global__ void __launch_bounds__(OS_THREADS) k_os_pass(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                        uint64_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                        const uint32_t* d_n, uint32_t n_max, int pass,
+                                                        uint32_t* hist, uint32_t tiles, uint32_t* err) {
+    __shared__ uint32_t s_warp[OS_WARPS][256];
+    __shared__ uint32_t s_base[256];
+    __shared__ uint32_t s_tile;
+    const uint32_t n = load_n(d_n, n_max);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const uint32_t lt = (1u << l) - 1u;
+    const int shift = 8 * pass;
+    uint32_t* ctr = hist + OS_CTR + pass;
+    uint32_t* status = hist + OS_STATUS;
+    const uint32_t* gh = hist + OS_GHIST + 256 * pass;
+    if (threadIdx.x == 0) s_tile = atomicAdd(ctr, 1u);
+    for (int i = threadIdx.x; i < OS_WARPS * 256; i += OS_THREADS) (&s_warp[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t t = s_tile;
+    const uint32_t base = t * OS_TILE;
+    if (t >= tiles || base >= n) return;
+    // load: warp w holds keys [base + 128 w, base + 128 w + 128), four chunks of 32
+    uint64_t k[OS_ITEMS];
+    uint32_t v[OS_ITEMS], d[OS_ITEMS], rk[OS_ITEMS];
+#pragma unroll
+    for (int c = 0; c < OS_ITEMS; ++c) {
+        const uint32_t idx = base + w * (32 * OS_ITEMS) + c * 32 + l;
         const bool valid = idx < n;
-        uint64_t k = 0;
-        uint32_t v = 0, d = 256;
-        if (valid) {
-            k = keys[idx];
-            v = vals[idx];
-            d = (uint32_t)(k >> shift) & 255u;
-        }
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        uint32_t pos = 0;
-        if (valid) pos = cnt[w][d] + __popc(peers & lt);
+        k[c] = valid ? kin[idx] : 0ull;
+        v[c] = valid ? vin[idx] : 0u;
+        d[c] = valid ? ((uint32_t)(k[c] >> shift) & 255u) : 256u;
+    }
+    // ranks inside the warp, in index order
+#pragma unroll
+    for (int c = 0; c < OS_ITEMS; ++c) {
+        const uint32_t peers = __match_any_sync(0xffffffffu, d[c]);
+        rk[c] = (d[c] < 256u) ? s_warp[w][d[c]] + __popc(peers & lt) : 0u;
         __syncwarp();
-        if (valid && l == __ffs(peers) - 1) cnt[w][d] += __popc(peers);
+        if (d[c] < 256u && l == __ffs(peers) - 1) s_warp[w][d[c]] += __popc(peers);
         __syncwarp();
-        if (valid) {
-            okeys[pos] = k;
-            ovals[pos] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 256) {
+        const int dg = threadIdx.x;
+        uint32_t run = 0;
+#pragma unroll
+        for (int ww = 0; ww < OS_WARPS; ++ww) {
+            const uint32_t x = s_warp[ww][dg];
+            s_warp[ww][dg] = run;
+            run += x;
         }
+        // global start of digit dg: exclusive prefix of the digit totals
+        uint32_t gstart = 0;
+        for (int e = 0; e < dg; ++e) gstart += gh[e];
+        // tiles before this one, by decoupled look-back
+        uint32_t excl = 0;
+        if (t == 0) {
+            atomicExch(&status[dg], OS_INC | run);
+        } else {
+            atomicExch(&status[(size_t)t * 256 + dg], OS_AGG | run);
+            int p = (int)t - 1;
+            while (p >= 0) {
+                uint32_t sv = 0, spins = 0;
+                while (((sv = ld_volatile_u32(&status[(size_t)p * 256 + dg])) >> 30) == 0u && ++spins < SPIN_LIMIT)
+                    __nanosleep(32);
+                if ((sv >> 30) == 0u) {
+                    if (err) atomicOr(err, PRIM_ERR_SPIN);
+                    break;
+                }
+                excl += sv & OS_VAL;
+                if ((sv >> 30) == 2u) break;
+                --p;
+            }
+            __threadfence();
+            atomicExch(&status[(size_t)t * 256 + dg], OS_INC | ((excl + run) & OS_VAL));
+        }
+        s_base[dg] = gstart + excl;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < OS_ITEMS; ++c) {
+        if (d[c] >= 256u) continue;
+        const uint32_t pos = s_base[d[c]] + s_warp[w][d[c]] + rk[c];
+        kout[pos] = k[c];
+        vout[pos] = v[c];
     }
 }
 
 bool radix_sort_pairs(const SortBufs& b, const uint32_t* d_n, uint32_t n_max, int nbits,
                       cudaStream_t st) {
     if (n_max == 0 || nbits <= 0) return false;
-    const uint32_t chunks = sort_chunks(n_max);
-    const uint32_t ntiles = sort_tiles(n_max);
-    const uint32_t grid = (ntiles + SORT_WARPS - 1) / SORT_WARPS;
+    const int passes = (nbits + 7) / 8;
+    const uint32_t tiles = os_tiles(n_max);
+    // digit totals and tile counters, then per pass a cleared status area
+    cudaMemsetAsync(b.hist, 0, (OS_STATUS) * 4, st);
+    uint32_t hblocks = (n_max + 255) / 256;
+    if (hblocks > 148u * 8u) hblocks = 148u * 8u;
+    k_os_hist<<<hblocks, 256, 0, st>>>(b.keys, d_n, n_max, passes, b.hist + OS_GHIST);
+    ++g_launches;
     const uint64_t* src_k = b.keys;
     const uint32_t* src_v = b.vals;
     uint64_t* dst_k = b.keys_alt;
     uint32_t* dst_v = b.vals_alt;
     bool in_alt = false;
-    for (int shift = 0; shift < nbits; shift += 8) {
-        k_radix_hist<<<grid, 32 * SORT_WARPS, 0, st>>>(src_k, d_n, n_max, shift, chunks, ntiles, b.hist);
-        ++g_launches;
-        ScanJob job;
-        job.in[0] = b.hist;
-        job.out[0] = b.hist;  // in-place is safe: apply reads its own items before writing them
-        job.k = 1;
-        scan_exclusive(job, nullptr, 256u * ntiles, b.scan_tmp, st);
-        k_radix_scatter<<<grid, 32 * SORT_WARPS, 0, st>>>(src_k, src_v, dst_k, dst_v, d_n, n_max, shift,
-                                                          chunks, ntiles, b.hist);
+    for (int p = 0; p < passes; ++p) {
+        cudaMemsetAsync(b.hist + OS_STATUS, 0, 256ull * tiles * 4, st);
+        k_os_pass<<<tiles, OS_THREADS, 0, st>>>(src_k, src_v, dst_k, dst_v, d_n, n_max, p, b.hist, tiles, b.err);
         ++g_launches;
         in_alt = !in_alt;
         const uint64_t* tk = dst_k;

@@ -8,9 +8,8 @@
 
 namespace dg {
 
-constexpr int SCAN_THREADS = 256;
-constexpr int SCAN_ITEMS = 8;
-constexpr uint32_t SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+// error bit a primitive raises when a look-back wait gives up (bounded spin)
+constexpr uint32_t PRIM_ERR_SPIN = 1u << 8;
 
 // Exclusive prefix sums of up to three uint32 arrays of the same length n.
 // n = *d_n (or n_max when d_n is null).  total[a] (nullable) receives the sum.
@@ -19,21 +18,25 @@ struct ScanJob {
     uint32_t* out[3] = {nullptr, nullptr, nullptr};
     uint32_t* total[3] = {nullptr, nullptr, nullptr};
     int k = 0;
+    uint32_t* err = nullptr;  // optional: PRIM_ERR_SPIN is or-ed in here
 };
 size_t scan_tmp_words(uint32_t n_max);  // uint32 words of scratch for one ScanJob
 void scan_exclusive(const ScanJob& job, const uint32_t* d_n, uint32_t n_max, uint32_t* tmp,
                     cudaStream_t st);
 
 // Stable LSD radix sort of (uint64 key, uint32 value) pairs on the low nbits of
-// the key.  The count is *d_n <= n_max.  Returns true when the sorted data ends
-// in the *_alt buffers.
+// the key (8-bit digits, one-sweep: one histogram kernel, then one kernel per
+// digit that ranks a 2048-key tile and finds its offsets by decoupled look-back).
+// The count is *d_n <= n_max.  Returns true when the sorted data ends in the
+// *_alt buffers.
 struct SortBufs {
     uint64_t* keys;
     uint32_t* vals;
     uint64_t* keys_alt;
     uint32_t* vals_alt;
-    uint32_t* hist;      // sort_hist_words(n_max)
-    uint32_t* scan_tmp;  // scan_tmp_words(256 * tiles)
+    uint32_t* hist;      // sort_hist_words(n_max): digit totals, tile counters, look-back status
+    uint32_t* scan_tmp;  // unused (kept for layout compatibility), may be null
+    uint32_t* err = nullptr;
 };
 size_t sort_hist_words(uint32_t n_max);
 size_t sort_scan_tmp_words(uint32_t n_max);
@@ -42,7 +45,7 @@ bool radix_sort_pairs(const SortBufs& b, const uint32_t* d_n, uint32_t n_max, in
 
 int bit_length(uint64_t x);
 
-// one extra kernel launch counter for the benchmark's launch tally
+// kernel launches issued by this thread (the benchmark's launch tally)
 extern thread_local uint64_t g_launches;
 
 }  // namespace dg

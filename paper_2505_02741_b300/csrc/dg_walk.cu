@@ -391,65 +391,55 @@ __device__ __forceinline__ void emit_edge(Cands& c, uint32_t x, uint32_t y, doub
     c.w[pos + 1] = w;
 }
 
-__global__ void k_emit(CSRView H, CSRView G, WalkTasks t, WalkParams p, WalkRecs r, const BatchHdr* hdr,
-                       const int32_t* best, const double* fin_w, dg_update_result* res, BatchCounters* ctr,
-                       Cands c, uint32_t* path_buf, uint32_t w_max, uint32_t* d_err) {
+// Replay of the argmin walker of every walked deletion that hit: the same
+// counters on the same snapshot give the same path.  One thread per deletion
+// only follows the path (one dependent load per step) and records it; the
+// edges are judged in parallel by k_emit_path.  Kept insertions and the
+// fallback of deletions without a hit are emitted here.
+__global__ void k_replay(CSRView H, CSRView G, WalkTasks t, WalkParams p, WalkRecs r, const BatchHdr* hdr,
+                         const int32_t* best, const double* fin_w, dg_update_result* res, BatchCounters* ctr,
+                         Cands c, PathBufs pb, uint32_t w_max, uint32_t* d_err) {
     if (walk_aborted(d_err)) return;
     const uint32_t W = min(*t.count, w_max);
     const uint32_t n = (uint32_t)G.n;
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < W; j += gridDim.x * blockDim.x) {
         const uint32_t i = t.idx[j];
         const uint32_t u = t.u[j], v = t.v[j];
+        pb.len[j] = 0;
         if (t.kind[j] == WALK_INS) {
             if (best[j] < 0 && !isnan(fin_w[i])) emit_edge(c, u, v, fin_w[i], n, d_err);
             continue;
         }
-        uint32_t emitted = 0;
+        res[i].nrecovered = 0;
         const int32_t b = best[j];
         if (b >= 0) {
-            // replay the argmin walker: same counters on the same snapshot -> same path
             const uint32_t steps = r.meta[(size_t)j * p.s + b] & 0xFFFFu;
             const uint64_t id = hdr->id0 + i;
             const uint32_t ulo = (uint32_t)id, uhi = (uint32_t)(id >> 32);
-            uint32_t* path = path_buf + (size_t)j * (p.T + 1);
-            uint32_t cv = u, off = G.off[u], deg = G.deg[u], prev = NONE;
+            uint32_t* path = pb.v + (size_t)j * (p.T + 1);
+            double* pw = pb.w + (size_t)j * p.T;
+            uint32_t cv = u, off = G.off[u], deg = G.deg[u], prev = NONE, s = 0;
             path[0] = u;
-            for (uint32_t s = 0; s < steps; ++s) {
+            for (; s < steps; ++s) {
                 const uint32_t neff = deg - (prev != NONE ? 1u : 0u);
-                if (neff == 0) {  // cannot happen for a recorded hit
-                    atomicOr(d_err, (uint32_t)ERR_INTERNAL);
-                    break;
-                }
                 const uint32_t x = philox_word0(s, (uint32_t)b, ulo, uhi, p.key0, p.key1);
                 const uint32_t jj = __umulhi(x, neff);
                 const uint32_t idx = jj + (jj >= prev ? 1u : 0u);
-                if ((uint64_t)off + idx >= G.pool_cap) {
-                    atomicOr(d_err, (uint32_t)ERR_INTERNAL);
-                    break;
-                }
+                if (neff == 0 || (uint64_t)off + idx >= G.pool_cap) break;
                 const Ent e = G.pool[off + idx];
-                if (e.nbr >= n) {
-                    atomicOr(d_err, (uint32_t)ERR_INTERNAL);
-                    break;
-                }
-                // edge (cv, e.nbr): recover it unless repeated earlier in this walk or already in H'
-                const uint32_t y = e.nbr;
-                bool dup = false;
-                for (uint32_t s2 = 0; s2 < s && !dup; ++s2) {
-                    const uint32_t a0 = path[s2], a1 = path[s2 + 1];
-                    dup = (a0 == cv && a1 == y) || (a0 == y && a1 == cv);
-                }
-                if (!dup && !has_edge(H, cv, y)) {
-                    emit_edge(c, cv, y, e.w, n, d_err);
-                    ++emitted;
-                }
-                path[s + 1] = y;
-                cv = y;
+                if (e.nbr >= n) break;
+                path[s + 1] = e.nbr;
+                pw[s] = e.w;
+                cv = e.nbr;
                 off = e.noff;
                 deg = e.ndeg;
                 prev = e.rev;
             }
-            if (cv != v) atomicOr(d_err, (uint32_t)ERR_INTERNAL);
+            if (s != steps || cv != v) {  // a recorded hit must replay to v
+                atomicOr(d_err, (uint32_t)ERR_INTERNAL);
+                continue;
+            }
+            pb.len[j] = steps;
         } else {
             // no walker reached v: per endpoint, the minimum-resistance G_b edge not in H'
             res[i].fallback = 1;
@@ -472,6 +462,7 @@ __global__ void k_emit(CSRView H, CSRView G, WalkTasks t, WalkParams p, WalkRecs
                     pick_w[e2] = L[k].w;
                 }
             }
+            uint32_t emitted = 0;
             for (int e2 = 0; e2 < 2; ++e2) {
                 if (pick_x[e2] == NONE) continue;
                 if (e2 == 1 && pick_x[0] != NONE &&
@@ -481,22 +472,49 @@ __global__ void k_emit(CSRView H, CSRView G, WalkTasks t, WalkParams p, WalkRecs
                 emit_edge(c, pick_x[e2], pick_y[e2], pick_w[e2], n, d_err);
                 ++emitted;
             }
+            res[i].nrecovered = (int32_t)emitted;
+            if (emitted) atomicAdd(&ctr->recovered, (unsigned long long)emitted);
         }
-        res[i].nrecovered = (int32_t)emitted;
-        if (emitted) atomicAdd(&ctr->recovered, (unsigned long long)emitted);
+    }
+}
+
+// one thread per (deletion, path edge): recover the edge unless it already
+// appeared earlier in the same walk or is in H'
+__global__ void k_emit_path(CSRView H, WalkTasks t, WalkParams p, dg_update_result* res, BatchCounters* ctr,
+                            Cands c, PathBufs pb, uint32_t w_max, uint32_t* d_err) {
+    if (walk_aborted(d_err)) return;
+    const uint32_t W = min(*t.count, w_max);
+    const uint32_t n = (uint32_t)H.n;
+    const uint64_t items = (uint64_t)W * p.T;
+    for (uint64_t it = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; it < items;
+         it += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t j = (uint32_t)(it / p.T), s = (uint32_t)(it - (uint64_t)j * p.T);
+        if (s >= pb.len[j]) continue;
+        const uint32_t* path = pb.v + (size_t)j * (p.T + 1);
+        const uint32_t x = path[s], y = path[s + 1];
+        bool dup = false;
+        for (uint32_t s2 = 0; s2 < s && !dup; ++s2) {
+            const uint32_t a0 = path[s2], a1 = path[s2 + 1];
+            dup = (a0 == x && a1 == y) || (a0 == y && a1 == x);
+        }
+        if (dup || has_edge(H, x, y)) continue;
+        emit_edge(c, x, y, pb.w[(size_t)j * p.T + s], n, d_err);
+        atomicAdd(&res[t.idx[j]].nrecovered, 1);
+        atomicAdd(&ctr->recovered, 1ull);
     }
 }
 
 void launch_emit(const CSRView& H, const CSRView& G, const WalkTasks& t, const WalkParams& p,
                  const WalkRecs& r, const BatchHdr* d_hdr, const int32_t* best, const double* fin_w,
-                 dg_update_result* res, BatchCounters* ctr, Cands c, uint32_t* path_buf, uint32_t w_max,
+                 dg_update_result* res, BatchCounters* ctr, Cands c, PathBufs pb, uint32_t w_max,
                  uint32_t* d_err, cudaStream_t st) {
     uint32_t blocks = (w_max + 127) / 128;
     const uint32_t cap = (uint32_t)device_sms() * 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    k_emit<<<blocks, 128, 0, st>>>(H, G, t, p, r, d_hdr, best, fin_w, res, ctr, c, path_buf, w_max, d_err);
-    ++g_launches;
+    k_replay<<<blocks, 128, 0, st>>>(H, G, t, p, r, d_hdr, best, fin_w, res, ctr, c, pb, w_max, d_err);
+    k_emit_path<<<(unsigned)device_sms() * 8, 256, 0, st>>>(H, t, p, res, ctr, c, pb, w_max, d_err);
+    g_launches += 2;
     DG_CHECK_LAUNCH();
 }
 

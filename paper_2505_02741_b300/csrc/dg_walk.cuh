@@ -81,10 +81,18 @@ struct Cands {
     uint32_t cap;
 };
 
+// replayed argmin paths of walked deletions: vertices (T+1 per walked update),
+// edge weights (T per walked update), path length
+struct PathBufs {
+    uint32_t* v;
+    double* w;
+    uint32_t* len;
+};
+
 // recovered path edges / fallback edges of walked deletions, kept insertions
 void launch_emit(const CSRView& H, const CSRView& G, const WalkTasks& t, const WalkParams& p,
                  const WalkRecs& r, const BatchHdr* d_hdr, const int32_t* best, const double* fin_w,
-                 dg_update_result* res, BatchCounters* ctr, Cands c, uint32_t* path_buf, uint32_t w_max,
+                 dg_update_result* res, BatchCounters* ctr, Cands c, PathBufs pb, uint32_t w_max,
                  uint32_t* d_err, cudaStream_t st);
 
 int device_sms();

@@ -337,8 +337,9 @@ def main():
                           "walked_updates": float(np.mean([p["walked"] for p in phases])),
                           "phase_ms": {k: float(np.mean([p[k] for p in phases])) for k in
                                        ("mutate_ms", "walk_ms", "reduce_ms", "emit_ms", "commit_ms", "batch_ms")},
-                          "walk_shape": [phases[-1]["walk_block"], phases[-1]["walk_ilp"],
-                                         phases[-1]["walk_blocks_per_sm"]],
+                          "walk_shape": {"block": phases[-1]["walk_block"], "ilp": phases[-1]["walk_ilp"],
+                                         "blocks_per_sm": phases[-1]["walk_blocks_per_sm"],
+                                         "cut": phases[-1]["walk_cut"], "autotuned": True},
                           "launches": launches / args.steps, "cuda_graph": bool(phases[-1]["graph_replayed"])},
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
             "per_update_form": pu,

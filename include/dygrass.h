@@ -151,6 +151,8 @@ typedef struct {
     double reduce_ms;        /* per-update reduction after the walks */
     double emit_ms;          /* path replay and candidate emission */
     double commit_ms;        /* sort, filter and merge into H, result copy-out */
+    int32_t walk_cut;        /* persistent walk launches per batch */
+    int32_t autotuned;       /* 1 if this batch ran the walk-shape autotuner */
 } dg_batch_stats;
 
 /* default configuration: seed 0, K 100, T 100, s 32, early exit on, batched walks,

@@ -76,15 +76,32 @@ static void worker_loop(Ctx* c) {
                     std::lock_guard<std::mutex> lg(c->mu);
                     for (auto& kv : c->graphs) resident += kv.second->G.bytes() + kv.second->H.bytes();
                 }
+                bool refused = false;
                 for (auto it = c->queue.begin(); it != c->queue.end(); ++it) {
                     auto& r = *it;
                     if (c->busy[r->gid]) continue;
                     const bool fits = c->cfg.budget == 0 ||
                                       resident + c->in_flight_bytes + r->need_bytes <= c->cfg.budget;
-                    if (!fits) continue;
+                    if (!fits) {
+                        // with nothing in flight it can never be admitted: fail it instead of waiting
+                        if (c->in_flight_bytes == 0) {
+                            r->status = DG_E_NOMEM;
+                            r->error = "request does not fit the HBM budget next to the resident graphs";
+                            r->t_done = now_ms();
+                            r->done = true;
+                            c->queue.erase(it);
+                            refused = true;
+                            break;
+                        }
+                        continue;
+                    }
                     rq = r;
                     c->queue.erase(it);
                     break;
+                }
+                if (refused) {
+                    c->dcv.notify_all();
+                    continue;
                 }
                 if (rq) break;
                 c->scv.wait(lk);
@@ -100,7 +117,8 @@ static void worker_loop(Ctx* c) {
             if (!g->stream) DG_CUDA(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
             graph_apply(*c, *g, (int64_t)rq->ups.size(), rq->ups.data(), rq->res, false, g->stream);
             if (c->cfg.budget) {  // under a budget, give the working set back between requests
-                std::lock_guard<std::mutex> lg(c->mu);
+                graph_release_ws(*c, *g, g->stream);
+                DG_CUDA(cudaStreamSynchronize(g->stream));
             }
         } catch (const Error& e) {
             st = e.code;

@@ -630,6 +630,27 @@ void graph_release(Ctx& c, DGraph& g) {
     csr_release(g.G, c.alloc, st);
     csr_release(g.H, c.alloc, st);
     g.touched.release(c.alloc, st);
+    graph_release_ws(c, g, st);
+    if (g.hs.ups) cudaFreeHost(g.hs.ups);
+    if (g.hs.res) cudaFreeHost(g.hs.res);
+    if (g.hs.hdr) cudaFreeHost(g.hs.hdr);
+    if (g.hs.err) cudaFreeHost(g.hs.err);
+    if (g.hs.ctr) cudaFreeHost(g.hs.ctr);
+    if (g.hs.tops) cudaFreeHost(g.hs.tops);
+    if (g.hs.counts) cudaFreeHost(g.hs.counts);
+    g.hs = HostStage{};
+    for (int i = 0; i < 7; ++i)
+        if (g.ev[i]) cudaEventDestroy(g.ev[i]);
+    if (g.stream) cudaStreamDestroy(g.stream);
+    g.stream = nullptr;
+    cudaStreamSynchronize(st);
+}
+
+// give back a graph's batch workspace (it is re-created by the next batch)
+void graph_release_ws(Ctx& c, DGraph& g, cudaStream_t st) {
+    for (auto& kv : g.steps)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    g.steps.clear();
     BatchWS& w = g.ws;
     w.apG.release(c.alloc, st);
     w.apH.release(c.alloc, st);
@@ -646,29 +667,12 @@ void graph_release(Ctx& c, DGraph& g) {
 #undef REL
     w.b_max = 0;
     w.cand_cap = 0;
-    if (g.hs.ups) cudaFreeHost(g.hs.ups);
-    if (g.hs.res) cudaFreeHost(g.hs.res);
-    if (g.hs.hdr) cudaFreeHost(g.hs.hdr);
-    if (g.hs.err) cudaFreeHost(g.hs.err);
-    if (g.hs.ctr) cudaFreeHost(g.hs.ctr);
-    if (g.hs.tops) cudaFreeHost(g.hs.tops);
-    if (g.hs.counts) cudaFreeHost(g.hs.counts);
-    g.hs = HostStage{};
-    for (int i = 0; i < 7; ++i)
-        if (g.ev[i]) cudaEventDestroy(g.ev[i]);
-    if (g.stream) cudaStreamDestroy(g.stream);
-    g.stream = nullptr;
-    cudaStreamSynchronize(st);
+    ++g.layout_gen;
 }
 
 // ---------------------------------------------------------------------------
 // the batch step
 // ---------------------------------------------------------------------------
-struct StepIO {
-    bool host_io;                   // ups/res through the pinned staging buffers
-    const dg_update* d_ups_src;     // device-io: caller's updates (copied outside the graph)
-    bool per_update;                // paper's one-launch-per-update walk form
-};
 
 static WalkTasks tasks_of(BatchWS& w) {
     WalkTasks t;
@@ -799,8 +803,11 @@ static void enqueue_walks(Ctx& c, DGraph& g, cudaStream_t st, int64_t per_update
     const WalkTasks tasks = tasks_of(w);
     DG_CUDA(record_event(g.ev[0], st));
     if (per_update_W < 0) {
-        launch_walk_batched(g.H.view(), g.G.view(), tasks, wp, wr, w.hdr.p, w.next.p, 0, w.b_max, g.shape,
-                            w.err.p, st);
+        const uint32_t cut = g.shape.cut > 1 ? (uint32_t)g.shape.cut : 1u;
+        for (uint32_t c = 0; c < cut; ++c)
+            launch_walk_batched(g.H.view(), g.G.view(), tasks, wp, wr, w.hdr.p, w.next.p,
+                                (uint32_t)((uint64_t)w.b_max * c / cut), (uint32_t)((uint64_t)w.b_max * (c + 1) / cut),
+                                g.shape, w.err.p, st);
     } else {
         for (int64_t j = 0; j < per_update_W; ++j)
             launch_walk_one(g.H.view(), g.G.view(), tasks, wp, wr, w.hdr.p, (uint32_t)j, w.err.p, st);
@@ -809,6 +816,68 @@ static void enqueue_walks(Ctx& c, DGraph& g, cudaStream_t st, int64_t per_update
     launch_walk_reduce(tasks, wp, wr, w.res.p, w.best.p, w.ctr.p, c.cfg.record ? w.dbg_reason.p : nullptr,
                        c.cfg.record ? w.dbg_steps.p : nullptr, w.b_max, w.err.p, st);
     DG_CUDA(record_event(g.ev[5], st));
+}
+
+// Autotuner: after the mutation of one large batch, time the walk phase on
+// that snapshot under each candidate launch shape (threads per block, walkers
+// per thread), then the batch cut for the winner, and keep the fastest.  Every
+// trial computes the same walks (outputs never depend on the shape); the
+// batch's own walk then runs once more with the chosen shape.
+static void autotune_walks(Ctx& c, DGraph& g, cudaStream_t st) {
+    BatchWS& w = g.ws;
+    const WalkParams wp = params_of(c.cfg);
+    const WalkRecs wr = recs_of(c, w);
+    const WalkTasks tasks = tasks_of(w);
+    cudaEvent_t e0, e1;
+    DG_CUDA(cudaEventCreate(&e0));
+    DG_CUDA(cudaEventCreate(&e1));
+    auto trial = [&](const WalkShape& sh) -> float {
+        DG_CUDA(cudaMemsetAsync(w.t_kstar.p, 0xFF, 4ull * w.b_max, st));
+        DG_CUDA(cudaEventRecord(e0, st));
+        for (int cidx = 0; cidx < sh.cut; ++cidx)
+            launch_walk_batched(g.H.view(), g.G.view(), tasks, wp, wr, w.hdr.p, w.next.p,
+                                (uint32_t)((uint64_t)w.b_max * cidx / sh.cut),
+                                (uint32_t)((uint64_t)w.b_max * (cidx + 1) / sh.cut), sh, w.err.p, st);
+        DG_CUDA(cudaEventRecord(e1, st));
+        wait_stream(c, st);
+        float ms = 0.f;
+        DG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        return ms;
+    };
+    // the first run warms L2 with this snapshot so every candidate sees the same state;
+    // each candidate then runs twice and keeps its faster time
+    WalkShape best = g.shape;
+    trial(best);
+    float best_ms = 1e30f;
+    const int shapes[][2] = {{256, 2}, {128, 2}, {64, 2}, {256, 1}, {128, 1}, {256, 4}};
+    for (const auto& bi : shapes) {
+        WalkShape sh;
+        sh.block = bi[0];
+        sh.ilp = bi[1];
+        sh.blocks_per_sm = 0;
+        sh.cut = 1;
+        const float ms = std::min(trial(sh), trial(sh));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = sh;
+        }
+    }
+    for (int cut : {2, 4}) {
+        WalkShape sh = best;
+        sh.cut = cut;
+        const float ms = std::min(trial(sh), trial(sh));
+        if (ms < best_ms * 0.98f) {
+            best_ms = ms;
+            best = sh;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    DG_CUDA(cudaMemsetAsync(w.t_kstar.p, 0xFF, 4ull * w.b_max, st));
+    g.shape = best;
+    g.tuned = true;
+    g.stats.autotuned = 1;
+    ++g.layout_gen;
 }
 
 // kept insertions, recovered and fallback edges -> H (re-runnable)
@@ -904,7 +973,9 @@ static bool handle_abort(Ctx& c, DGraph& g, uint32_t err, cudaStream_t st) {
 
 // proactive growth so that most batches never abort
 static void ensure_headroom(Ctx& c, DGraph& g, uint32_t nu, cudaStream_t st) {
-    const uint64_t want = (uint64_t)nu * 64 + 65536;
+    // a cheap guess of the relocation space one batch needs; a batch that needs
+    // more aborts before writing anything, grows the pool and re-runs
+    const uint64_t want = (uint64_t)nu * 16 + 4096;
     if (g.G.pool_cap - g.G.host_top < want) {
         csr_compact(g.G, c.alloc, want * 2, st);
         ++g.layout_gen;
@@ -961,10 +1032,18 @@ void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_updat
         wait_stream(c, st);
     };
 
-    const bool use_graph = c.cfg.use_graphs && !per_update && !c.cfg.record;
+    const bool tune_now = c.cfg.autotune && !g.tuned && !per_update && nu >= 4096;
+    const bool use_graph = c.cfg.use_graphs && !per_update && !c.cfg.record && !tune_now;
     bool replayed = false;
+    g.stats.autotuned = 0;
     DG_CUDA(record_event(g.ev[2], st));
-    if (use_graph) {
+    if (tune_now) {
+        stage_inputs();
+        enqueue_mutate(c, g, st);
+        autotune_walks(c, g, st);
+        enqueue_walks(c, g, st, -1);
+        finish_eager();
+    } else if (use_graph) {
         if (device_io) DG_CUDA(cudaMemcpyAsync(w.ups.p, ups, sizeof(dg_update) * nu, cudaMemcpyDeviceToDevice, st));
         CapturedStep& cs = g.steps[bucket];
         if (!cs.exec || cs.layout_gen != g.layout_gen || cs.device_io != device_io) {
@@ -1057,6 +1136,7 @@ void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_updat
     s.walk_block = g.shape.block;
     s.walk_ilp = g.shape.ilp;
     s.walk_blocks_per_sm = g.shape.blocks_per_sm;
+    s.walk_cut = g.shape.cut;
     s.walk_launches = per_update ? (int64_t)g.hs.counts[0] : 1;
     const uint64_t dl = g_launches - l0;
     s.launches = (int64_t)dl;

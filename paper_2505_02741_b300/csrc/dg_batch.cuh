@@ -112,6 +112,7 @@ void graph_init_h(Ctx& c, DGraph& g, int64_t mh, const int32_t* u, const int32_t
 void graph_apply(Ctx& c, DGraph& g, int64_t nu, const dg_update* ups, dg_update_result* res, bool device_io,
                  cudaStream_t st);
 void graph_release(Ctx& c, DGraph& g);
+void graph_release_ws(Ctx& c, DGraph& g, cudaStream_t st);  // batch workspace only
 void graph_compact(Ctx& c, DGraph& g, cudaStream_t st);
 void graph_export(Ctx& c, DGraph& g, bool which_h, int64_t cap, int32_t* u, int32_t* v, double* w,
                   int64_t* count, cudaStream_t st);

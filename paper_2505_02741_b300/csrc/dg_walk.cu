@@ -121,6 +121,48 @@ __device__ __forceinline__ void walker_advance(Walker& w, const WalkKernelArgs& 
     if (w.steps == a.p.T) walker_finish(w, a, R_AT_T);
 }
 
+// Walker state of the batched kernel, kept small so more walkers fit per SM.
+// The Philox word of the next step is computed while the current step's
+// entry load is in flight (it depends only on the counter, not on the load).
+struct Lean {
+    uint32_t j, k;      // walked-update index, walker index
+    uint32_t q;         // target
+    uint32_t c, off, deg, prev, steps;
+    uint32_t ulo, uhi;  // update id (Philox counter words 2, 3)
+    uint32_t x;         // random word of the next step
+    bool ins, active;
+    double R, wpq;
+};
+
+__device__ __forceinline__ void lean_start(Lean& w, const WalkKernelArgs& a, uint32_t wid, uint64_t id0) {
+    w.j = wid / a.p.s;
+    w.k = wid - w.j * a.p.s;
+    const uint32_t u = a.t.u[w.j];
+    w.q = a.t.v[w.j];
+    w.ins = a.t.kind[w.j] == WALK_INS;
+    w.wpq = a.t.wpq[w.j];
+    const uint64_t id = id0 + a.t.idx[w.j];
+    w.ulo = (uint32_t)id;
+    w.uhi = (uint32_t)(id >> 32);
+    const CSRView& g = w.ins ? a.H : a.G;
+    w.off = g.off[u];
+    w.deg = g.deg[u];
+    w.c = u;
+    w.prev = NONE;
+    w.steps = 0;
+    w.R = 0.0;
+    w.active = true;
+    w.x = philox_word0(0u, w.k, w.ulo, w.uhi, a.p.key0, a.p.key1);
+    if (a.r.paths) a.r.paths[(size_t)wid * (a.p.T + 1)] = (int32_t)u;
+}
+
+__device__ __forceinline__ void lean_finish(Lean& w, const WalkKernelArgs& a, uint32_t reason) {
+    const size_t wid = (size_t)w.j * a.p.s + w.k;
+    a.r.meta[wid] = w.steps | (reason << 16);
+    a.r.R[wid] = w.R;
+    w.active = false;
+}
+
 template <int ILP>
 __global__ void __launch_bounds__(256) k_walk_batched(WalkKernelArgs a) {
     if (walk_aborted(a.d_err)) return;
@@ -131,7 +173,7 @@ __global__ void __launch_bounds__(256) k_walk_batched(WalkKernelArgs a) {
     const uint64_t id0 = a.hdr->id0;
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
-    Walker w[ILP];
+    Lean w[ILP];
 #pragma unroll
     for (int i = 0; i < ILP; ++i) w[i].active = false;
     bool exhausted = false;
@@ -148,7 +190,7 @@ __global__ void __launch_bounds__(256) k_walk_batched(WalkKernelArgs a) {
                 b = __shfl_sync(0xffffffffu, b, leader);
                 if (need) {
                     const unsigned long long id = b + __popc(m & lt);
-                    if (id < total) walker_start(w[i], a, wbase + (uint32_t)id, id0);
+                    if (id < total) lean_start(w[i], a, wbase + (uint32_t)id, id0);
                     else exhausted = true;
                 }
             }
@@ -157,7 +199,8 @@ __global__ void __launch_bounds__(256) k_walk_batched(WalkKernelArgs a) {
 #pragma unroll
         for (int i = 0; i < ILP; ++i) any |= w[i].active;
         if (!__any_sync(0xffffffffu, any)) break;
-        // issue: leaf / early-exit checks and the entry loads of every slot
+        // issue: leaf check, the entry load, the early-exit probe, then the next
+        // step's Philox word while the loads are in flight
         uint4 h[ILP];
         double2 tl[ILP];
         uint32_t ks[ILP];
@@ -169,29 +212,49 @@ __global__ void __launch_bounds__(256) k_walk_batched(WalkKernelArgs a) {
             if (!w[i].active) continue;
             const uint32_t neff = w[i].deg - (w[i].prev != NONE ? 1u : 0u);
             if (neff == 0) {
-                walker_finish(w[i], a, R_LEAF);
+                lean_finish(w[i], a, R_LEAF);
                 continue;
             }
-            if (w[i].ins && a.p.early_exit) ks[i] = __ldcg(&a.t.kstar[w[i].j]);
-            const uint32_t x = philox_word0(w[i].steps, w[i].k, w[i].ulo, w[i].uhi, a.p.key0, a.p.key1);
-            const uint32_t jj = __umulhi(x, neff);
+            const uint32_t jj = __umulhi(w[i].x, neff);
             const uint32_t idx = jj + (jj >= w[i].prev ? 1u : 0u);
-            if (!step_in_bounds(w[i], idx, a)) {
-                walker_finish(w[i], a, R_LEAF);
+            const Ent* pool = w[i].ins ? a.H.pool : a.G.pool;
+            const uint64_t pcap = w[i].ins ? a.H.pool_cap : a.G.pool_cap;
+            if ((uint64_t)w[i].off + idx >= pcap) {  // only a broken mutation could get here
+                atomicOr(a.d_err, (uint32_t)ERR_INTERNAL);
+                lean_finish(w[i], a, R_LEAF);
                 continue;
             }
-            load_ent(w[i].pool + w[i].off + idx, h[i], tl[i]);
+            load_ent(pool + w[i].off + idx, h[i], tl[i]);
+            if (w[i].ins && a.p.early_exit) ks[i] = __ldcg(&a.t.kstar[w[i].j]);
             go[i] = true;
         }
+#pragma unroll
+        for (int i = 0; i < ILP; ++i)
+            if (go[i]) w[i].x = philox_word0(w[i].steps + 1, w[i].k, w[i].ulo, w[i].uhi, a.p.key0, a.p.key1);
         // consume
 #pragma unroll
         for (int i = 0; i < ILP; ++i) {
             if (!go[i]) continue;
-            if (ks[i] <= w[i].steps) {  // a walker of this update hit at a step <= ours: cut
-                walker_finish(w[i], a, R_CUT);
+            Lean& v = w[i];
+            if (ks[i] <= v.steps) {  // a walker of this update hit at a step <= ours: cut
+                lean_finish(v, a, R_CUT);
                 continue;
             }
-            walker_advance(w[i], a, h[i], tl[i].x);
+            v.R = __dadd_rn(v.R, tl[i].x);
+            v.steps += 1;
+            v.c = h[i].x;
+            v.off = h[i].y;
+            v.deg = h[i].z;
+            v.prev = h[i].w;
+            if (a.r.paths) a.r.paths[((size_t)v.j * a.p.s + v.k) * (a.p.T + 1) + v.steps] = (int32_t)v.c;
+            if (v.c == v.q && (!v.ins || __dmul_rn(v.wpq, v.R) <= a.p.K)) {
+                if (v.ins && a.p.early_exit) atomicMin(&a.t.kstar[v.j], v.steps);
+                lean_finish(v, a, R_HIT);
+            } else if (v.ins && __dmul_rn(v.wpq, v.R) > a.p.K) {
+                lean_finish(v, a, R_OVER_K);
+            } else if (v.steps == a.p.T) {
+                lean_finish(v, a, R_AT_T);
+            }
         }
     }
 }

@@ -45,6 +45,7 @@ struct WalkShape {
     int block = 256;
     int ilp = 2;
     int blocks_per_sm = 0;  // 0 = occupancy maximum
+    int cut = 1;            // persistent launches the walked updates are split over
 };
 
 // batched persistent walk over walked updates [j_lo, j_hi) of the task list

@@ -61,7 +61,8 @@ class BatchStats(C.Structure):
                 ("walk_launches", C.c_int64), ("launches", C.c_int64), ("retries", C.c_int64),
                 ("walk_block", C.c_int32), ("walk_ilp", C.c_int32), ("walk_blocks_per_sm", C.c_int32),
                 ("graph_replayed", C.c_int32), ("mutate_ms", C.c_double), ("reduce_ms", C.c_double),
-                ("emit_ms", C.c_double), ("commit_ms", C.c_double)]
+                ("emit_ms", C.c_double), ("commit_ms", C.c_double), ("walk_cut", C.c_int32),
+                ("autotuned", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -1,0 +1,115 @@
+"""Serving: several graphs resident at once, requests admitted by HBM budget and
+run concurrently across graphs (one request per graph at a time, in submission
+order).  Every request's result in the mix must equal its result alone.
+"""
+from __future__ import annotations
+
+import threading
+
+import numpy as np
+import pytest
+
+from paper_2505_02741_b300 import dygrass as D
+from paper_2505_02741_b300 import workloads as W
+from tests.gpu_util import assert_edges_equal
+
+pytestmark = pytest.mark.gpu
+
+
+def _graphs():
+    out = []
+    for name, (wl, st) in (("g32", W.make_grid(32, 32, seed=0)), ("g48", W.make_grid(48, 48, seed=1)),
+                           ("m16", W.make_mesh3d(16, 16, 16, seed=2))):
+        rng = np.random.default_rng(len(out) + 10)
+        reqs = []
+        for _ in range(6):
+            size = int(np.floor(np.exp(rng.uniform(0, np.log(3001)))))
+            ins = int(rng.integers(0, size + 1))
+            bt = st.next_batch(ins, size - ins)
+            reqs.append(D.make_updates(bt.u, bt.v, bt.w, bt.op))
+        out.append((name, wl, reqs))
+    return out
+
+
+def _load(ctx, wl):
+    g = ctx.load_graph(wl.n, wl.a, wl.b, wl.w)
+    g.init_sparsifier(wl.a[wl.h_ids], wl.b[wl.h_ids])
+    return g
+
+
+def test_serving_results_alone_equal_mix():
+    data = _graphs()
+    alone = {}
+    for name, wl, reqs in data:
+        ctx = D.Context()
+        g = _load(ctx, wl)
+        alone[name] = ([g.apply(r).tobytes() for r in reqs], g.sparsifier())
+        ctx.close()
+
+    ctx = D.Context()
+    gs = {name: _load(ctx, wl) for name, wl, _ in data}
+    tickets = {name: [] for name, _, _ in data}
+    lock = threading.Lock()
+
+    def submit_all(name, reqs):
+        for r in reqs:
+            with lock:  # keeps this graph's submission order equal to its request order
+                tickets[name].append(gs[name].submit(r))
+
+    threads = [threading.Thread(target=submit_all, args=(name, reqs)) for name, _, reqs in data]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    lat = []
+    for name, _, reqs in data:
+        got = []
+        for ticket, _res in tickets[name]:
+            res, ms = gs[name].wait(ticket, timeout_ms=120000)
+            got.append(res.tobytes())
+            lat.append(ms)
+        assert got == alone[name][0], name
+        assert_edges_equal(gs[name].sparsifier(), alone[name][1], f"{name} H")
+    assert all(x >= 0 for x in lat)
+    ctx.close()
+
+
+def test_serving_under_budget_admission():
+    """A budget that admits one request at a time still completes every request
+    with the same results."""
+    data = _graphs()[:2]
+    ref = {}
+    for name, wl, reqs in data:
+        ctx = D.Context()
+        g = _load(ctx, wl)
+        ref[name] = [g.apply(r).tobytes() for r in reqs]
+        ctx.close()
+    probe = D.Context()
+    resident = 0
+    for _, wl, _ in data:
+        resident += _load(probe, wl).device_bytes()
+    probe.close()
+    ctx = D.Context(hbm_budget=resident + (48 << 20))
+    gs = {name: _load(ctx, wl) for name, wl, _ in data}
+    order = []
+    for i in range(6):
+        for name, _, reqs in data:
+            order.append((name, gs[name].submit(reqs[i])))
+    got = {name: [] for name, _, _ in data}
+    for name, (ticket, _) in order:
+        res, _ = gs[name].wait(ticket, timeout_ms=120000)
+        got[name].append(res.tobytes())
+    for name, _, _ in data:
+        assert got[name] == ref[name], name
+    ctx.close()
+
+
+def test_serving_rejects_request_that_never_fits():
+    wl, st = W.make_grid(16, 16)
+    ctx = D.Context(hbm_budget=1 << 20)
+    g = _load(ctx, wl)
+    bt = st.next_batch(50, 0)
+    with pytest.raises(D.DgError) as e:
+        g.submit(D.make_updates(bt.u, bt.v, bt.w, bt.op))
+    assert e.value.code == -2
+    ctx.close()

@@ -181,6 +181,7 @@ def main():
     ap.add_argument("--per-update-steps", type=int, default=2)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--walk-shape", default="", help="fixed walk launch shape 'block,ilp' (skips the autotuner)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -209,6 +210,9 @@ def main():
     ctx = D.Context(device=dev, K=wl.K, T=wl.T, s=wl.s)
     g = ctx.load_graph(wl.n, wl.a, wl.b, wl.w)
     g.init_sparsifier(wl.a[wl.h_ids], wl.b[wl.h_ids])
+    if args.walk_shape:
+        blk, ilp = (int(x) for x in args.walk_shape.split(","))
+        g.set_walk_shape(blk, ilp, 0)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 

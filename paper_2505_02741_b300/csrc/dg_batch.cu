@@ -233,20 +233,28 @@ __global__ void k_val_runs(RunArgs a) {
     }
 }
 
+// walked deletions and walked insertions, flagged separately: the task list
+// puts deletions (no K, the longest walks) first so they start first and the
+// short insertion walks fill the tail of the persistent launch
 __global__ void k_walk_flags(const uint8_t* __restrict__ wkind, const BatchHdr* hdr, uint32_t b_max,
-                             uint32_t* __restrict__ flag) {
+                             uint32_t* __restrict__ fdel, uint32_t* __restrict__ fins) {
     const uint32_t nu = min(hdr->nu, b_max);
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nu; i += gridDim.x * blockDim.x)
-        flag[i] = wkind[i] != WALK_NONE;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nu; i += gridDim.x * blockDim.x) {
+        fdel[i] = wkind[i] == WALK_DEL;
+        fins[i] = wkind[i] == WALK_INS;
+    }
 }
 
 __global__ void k_make_tasks(const dg_update* __restrict__ ups, const uint8_t* __restrict__ wkind,
-                             const uint32_t* __restrict__ pos, const BatchHdr* hdr, uint32_t b_max, WalkTasks t) {
+                             const uint32_t* __restrict__ pdel, const uint32_t* __restrict__ pins,
+                             const uint32_t* __restrict__ totals, const BatchHdr* hdr, uint32_t b_max, WalkTasks t) {
     const uint32_t nu = min(hdr->nu, b_max);
+    const uint32_t ndel = totals[0];
+    if (blockIdx.x == 0 && threadIdx.x == 0) *t.count = ndel + totals[1];
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nu; i += gridDim.x * blockDim.x) {
         const uint8_t k = wkind[i];
         if (k == WALK_NONE) continue;
-        const uint32_t j = pos[i];
+        const uint32_t j = k == WALK_DEL ? pdel[i] : ndel + pins[i];
         const dg_update up = ups[i];
         t.u[j] = (uint32_t)up.u;
         t.v[j] = (uint32_t)up.v;
@@ -284,7 +292,7 @@ uint64_t BatchWS::bytes() const {
     uint64_t b = 0;
     b += ups.bytes() + res.bytes() + hdr.bytes() + err.bytes() + ctr.bytes() + next.bytes();
     b += vkeys.bytes() + vkeys_alt.bytes() + vvals.bytes() + vvals_alt.bytes() + vhist.bytes() + vscan.bytes();
-    b += wkind.bytes() + fin_w.bytes() + wflag.bytes() + wpos.bytes();
+    b += wkind.bytes() + fin_w.bytes() + wflag.bytes() + wpos.bytes() + wflag2.bytes() + wpos2.bytes();
     b += gkeys.bytes() + gkeys_alt.bytes() + hkeys.bytes() + gvals.bytes() + gvals_alt.bytes() + ghist.bytes();
     b += gscan.bytes() + gcount.bytes() + hflag.bytes() + hpos.bytes() + hvals.bytes() + hcount.bytes();
     b += gkind.bytes() + ghrem.bytes() + kind_del.bytes() + gw.bytes();
@@ -344,6 +352,8 @@ static void ensure_ws(Ctx& c, DGraph& g, uint32_t b_max, cudaStream_t st) {
     w.fin_w.ensure(a, B, st);
     w.wflag.ensure(a, B, st);
     w.wpos.ensure(a, B, st);
+    w.wflag2.ensure(a, B, st);
+    w.wpos2.ensure(a, B, st);
     w.gkeys.ensure(a, B2, st);
     w.gkeys_alt.ensure(a, B2, st);
     w.hkeys.ensure(a, B2, st);
@@ -365,7 +375,7 @@ static void ensure_ws(Ctx& c, DGraph& g, uint32_t b_max, cudaStream_t st) {
     w.t_v.ensure(a, B, st);
     w.t_idx.ensure(a, B, st);
     w.t_kstar.ensure(a, B, st);
-    w.t_count.ensure(a, 2, st);
+    w.t_count.ensure(a, 4, st);
     w.t_wpq.ensure(a, B, st);
     w.t_kind.ensure(a, B, st);
     w.best.ensure(a, B, st);
@@ -657,7 +667,7 @@ void graph_release_ws(Ctx& c, DGraph& g, cudaStream_t st) {
     w.apC.release(c.alloc, st);
 #define REL(b) w.b.release(c.alloc, st)
     REL(ups); REL(res); REL(hdr); REL(err); REL(ctr); REL(next); REL(vkeys); REL(vkeys_alt); REL(vvals);
-    REL(vvals_alt); REL(vhist); REL(vscan); REL(wkind); REL(fin_w); REL(wflag); REL(wpos); REL(gkeys);
+    REL(vvals_alt); REL(vhist); REL(vscan); REL(wkind); REL(fin_w); REL(wflag); REL(wpos); REL(wflag2); REL(wpos2); REL(gkeys);
     REL(gkeys_alt); REL(hkeys); REL(gvals); REL(gvals_alt); REL(ghist); REL(gscan); REL(gcount); REL(hflag);
     REL(hpos); REL(hvals); REL(hcount); REL(gkind); REL(ghrem); REL(kind_del); REL(gw); REL(t_u); REL(t_v);
     REL(t_idx); REL(t_kstar); REL(t_count); REL(meta); REL(t_wpq); REL(recR); REL(t_kind); REL(best);
@@ -740,19 +750,23 @@ static void enqueue_mutate(Ctx& c, DGraph& g, cudaStream_t st) {
     ra.gcount = w.gcount.p;
     ra.ctr = w.ctr.p;
     k_val_runs<<<grid_for(B), BT, 0, st>>>(ra);
-    k_walk_flags<<<grid_for(B), BT, 0, st>>>(w.wkind.p, w.hdr.p, B, w.wflag.p);
+    k_walk_flags<<<grid_for(B), BT, 0, st>>>(w.wkind.p, w.hdr.p, B, w.wflag.p, w.wflag2.p);
     g_launches += 2;
     {
         ScanJob j;
         j.in[0] = w.wflag.p;
         j.out[0] = w.wpos.p;
-        j.total[0] = w.t_count.p;
-        j.k = 1;
+        j.total[0] = w.t_count.p + 2;
+        j.in[1] = w.wflag2.p;
+        j.out[1] = w.wpos2.p;
+        j.total[1] = w.t_count.p + 3;
+        j.k = 2;
         j.err = w.err.p;
         scan_exclusive(j, d_nu, B, w.vscan.p, st);
     }
     WalkTasks tasks = tasks_of(w);
-    k_make_tasks<<<grid_for(B), BT, 0, st>>>(w.ups.p, w.wkind.p, w.wpos.p, w.hdr.p, B, tasks);
+    k_make_tasks<<<grid_for(B), BT, 0, st>>>(w.ups.p, w.wkind.p, w.wpos.p, w.wpos2.p, w.t_count.p + 2, w.hdr.p, B,
+                                            tasks);
     ++g_launches;
     // net G changes, sorted by (vertex, neighbour)
     SortBufs gs{w.gkeys.p, w.gvals.p, w.gkeys_alt.p, w.gvals_alt.p, w.ghist.p, w.gscan.p, w.err.p};
@@ -831,7 +845,11 @@ static void autotune_walks(Ctx& c, DGraph& g, cudaStream_t st) {
     cudaEvent_t e0, e1;
     DG_CUDA(cudaEventCreate(&e0));
     DG_CUDA(cudaEventCreate(&e1));
+    // each trial starts from a cold L2 (a write larger than L2), as a batch does
+    const size_t flush_bytes = 192ull << 20;
+    void* flush = c.alloc.get(flush_bytes, st);
     auto trial = [&](const WalkShape& sh) -> float {
+        DG_CUDA(cudaMemsetAsync(flush, 0, flush_bytes, st));
         DG_CUDA(cudaMemsetAsync(w.t_kstar.p, 0xFF, 4ull * w.b_max, st));
         DG_CUDA(cudaEventRecord(e0, st));
         for (int cidx = 0; cidx < sh.cut; ++cidx)
@@ -873,6 +891,7 @@ static void autotune_walks(Ctx& c, DGraph& g, cudaStream_t st) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    c.alloc.put(flush, flush_bytes, st);
     DG_CUDA(cudaMemsetAsync(w.t_kstar.p, 0xFF, 4ull * w.b_max, st));
     g.shape = best;
     g.tuned = true;

@@ -41,7 +41,7 @@ struct BatchWS {
     DBuf<uint32_t> vvals, vvals_alt, vhist, vscan;
     DBuf<uint8_t> wkind;
     DBuf<double> fin_w;
-    DBuf<uint32_t> wflag, wpos;
+    DBuf<uint32_t> wflag, wpos, wflag2, wpos2;
     // G changes (and the H removals among them)
     DBuf<uint64_t> gkeys, gkeys_alt, hkeys;
     DBuf<uint32_t> gvals, gvals_alt, ghist, gscan, gcount, hflag, hpos, hvals, hcount;

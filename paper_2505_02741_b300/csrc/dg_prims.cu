@@ -148,31 +148,44 @@ __global__ void __launch_bounds__(LB_THREADS) k_scan_lookback(ScanArgs a, const 
         }
         __syncthreads();
         const uint32_t agg = sh[LB_THREADS / 32 - 1];
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < 32) {
+            // warp 0 looks back over a window of 32 predecessors at a time
             uint32_t excl = 0;
             if (t == 0) {
-                atomicExch(&st[t], LB_INC | agg);
+                if (l == 0) atomicExch(&st[t], LB_INC | agg);
             } else {
-                atomicExch(&st[t], LB_AGG | agg);
-                int p = (int)t - 1;
-                while (p >= 0) {
-                    unsigned long long sv = 0;
-                    uint32_t spins = 0;
-                    while (((sv = ld_volatile_u64(&st[p])) >> 32) == 0ull && ++spins < SPIN_LIMIT) __nanosleep(32);
-                    if ((sv >> 32) == 0ull) {
-                        if (a.err) atomicOr(a.err, PRIM_ERR_SPIN);
+                if (l == 0) atomicExch(&st[t], LB_AGG | agg);
+                int top = (int)t - 1;  // newest predecessor not yet summed
+                bool done = false;
+                while (!done && top >= 0) {
+                    const int p = top - l;
+                    unsigned long long sv = LB_INC;  // lanes before tile 0 act as an inclusive zero
+                    if (p >= 0) {
+                        uint32_t spins = 0;
+                        while (((sv = ld_volatile_u64(&st[p])) >> 32) == 0ull && ++spins < SPIN_LIMIT) __nanosleep(32);
+                    }
+                    const bool empty = (sv >> 32) == 0ull;
+                    if (__any_sync(0xffffffffu, empty)) {
+                        if (l == 0 && a.err) atomicOr(a.err, PRIM_ERR_SPIN);
                         break;
                     }
-                    excl += (uint32_t)sv;
-                    if ((sv >> 32) == 2ull) break;
-                    --p;
+                    const uint32_t inc_mask = __ballot_sync(0xffffffffu, (sv >> 32) == 2ull);
+                    // sum lanes up to and including the nearest inclusive prefix
+                    const int stop = inc_mask ? __ffs(inc_mask) - 1 : 31;
+                    uint32_t part = (l <= stop) ? (uint32_t)sv : 0u;
+                    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+                    excl += part;
+                    done = inc_mask != 0u;
+                    top -= 32;
                 }
                 __threadfence();
-                atomicExch(&st[t], LB_INC | (unsigned long long)(excl + agg));
+                if (l == 0) atomicExch(&st[t], LB_INC | (unsigned long long)(excl + agg));
             }
-            s_prefix = excl;
-            if (t + 1 == nt && a.total[j]) *a.total[j] = excl + agg;
-            if (nt == 0 && t == 0 && a.total[j]) *a.total[j] = 0;
+            if (l == 0) {
+                s_prefix = excl;
+                if (t + 1 == nt && a.total[j]) *a.total[j] = excl + agg;
+                if (nt == 0 && t == 0 && a.total[j]) *a.total[j] = 0;
+            }
         }
         __syncthreads();
         uint32_t run = s_prefix + ((w > 0) ? sh[w - 1] : 0u) + x - s;
@@ -298,6 +311,26 @@ __global__ void __launch_bounds__(OS_THREADS) k_os_pass(const uint64_t* __restri
         if (d[c] < 256u && l == __ffs(peers) - 1) s_warp[w][d[c]] += __popc(peers);
         __syncwarp();
     }
+    // global start of every digit: exclusive scan of the digit totals (warp 0, 8 per lane)
+    if (w == 0) {
+        uint32_t gv[8], s8 = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            gv[q] = gh[l * 8 + q];
+            s8 += gv[q];
+        }
+        uint32_t x = s8;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (l >= o) x += y;
+        }
+        uint32_t run = x - s8;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            s_base[l * 8 + q] = run;
+            run += gv[q];
+        }
+    }
     __syncthreads();
     if (threadIdx.x < 256) {
         const int dg = threadIdx.x;
@@ -308,27 +341,38 @@ __global__ void __launch_bounds__(OS_THREADS) k_os_pass(const uint64_t* __restri
             s_warp[ww][dg] = run;
             run += x;
         }
-        // global start of digit dg: exclusive prefix of the digit totals
-        uint32_t gstart = 0;
-        for (int e = 0; e < dg; ++e) gstart += gh[e];
-        // tiles before this one, by decoupled look-back
+        const uint32_t gstart = s_base[dg];
+        // tiles before this one, by decoupled look-back (8 predecessors in flight)
         uint32_t excl = 0;
         if (t == 0) {
             atomicExch(&status[dg], OS_INC | run);
         } else {
             atomicExch(&status[(size_t)t * 256 + dg], OS_AGG | run);
-            int p = (int)t - 1;
-            while (p >= 0) {
-                uint32_t sv = 0, spins = 0;
-                while (((sv = ld_volatile_u32(&status[(size_t)p * 256 + dg])) >> 30) == 0u && ++spins < SPIN_LIMIT)
-                    __nanosleep(32);
-                if ((sv >> 30) == 0u) {
-                    if (err) atomicOr(err, PRIM_ERR_SPIN);
-                    break;
+            int top = (int)t - 1;
+            bool done = false;
+            constexpr int WIN = 8;
+            while (!done && top >= 0) {
+                uint32_t sv[WIN];
+#pragma unroll
+                for (int q = 0; q < WIN; ++q)
+                    sv[q] = (top - q >= 0) ? ld_volatile_u32(&status[(size_t)(top - q) * 256 + dg]) : OS_INC;
+#pragma unroll
+                for (int q = 0; q < WIN; ++q) {
+                    if (done) break;
+                    uint32_t spins = 0;
+                    while ((sv[q] >> 30) == 0u && ++spins < SPIN_LIMIT) {
+                        __nanosleep(32);
+                        sv[q] = ld_volatile_u32(&status[(size_t)(top - q) * 256 + dg]);
+                    }
+                    if ((sv[q] >> 30) == 0u) {
+                        if (err) atomicOr(err, PRIM_ERR_SPIN);
+                        done = true;
+                        break;
+                    }
+                    excl += sv[q] & OS_VAL;
+                    if ((sv[q] >> 30) == 2u) done = true;
                 }
-                excl += sv & OS_VAL;
-                if ((sv >> 30) == 2u) break;
-                --p;
+                top -= WIN;
             }
             __threadfence();
             atomicExch(&status[(size_t)t * 256 + dg], OS_INC | ((excl + run) & OS_VAL));

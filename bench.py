@@ -39,6 +39,10 @@ sys.path.insert(0, ROOT)
 METRIC = "updates/s & walk-steps/s on 1 B300, batched vs per-update; p50/p99 latency"
 BYTES_PER_STEP = 32  # one 32-byte DRAM sector per walk step (the entry holds nbr, next list, rev, r)
 N_INS, N_DEL = 10_000, 10_000
+# DRAM bytes (read + write) of one walk launch of this workload, from one ncu
+# capture of the current walk kernel (cold L2); see profiles/.
+WALK_TRAFFIC_BYTES = 1.0945e9
+WALK_TRAFFIC_SOURCE = "profiles/walk_k_walk_batched_mesh3d_100.md (ncu --set full, cold L2)"
 
 
 def measured_peaks():
@@ -317,8 +321,9 @@ def main():
     bytes_per_launch = BYTES_PER_STEP * steps_done / args.steps
     achieved = bytes_per_launch / avg_walk_s / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "k_walk_batched", "bytes_per_step": BYTES_PER_STEP,
-            "peak_source": peak_kind}
+            "traffic": WALK_TRAFFIC_BYTES, "traffic_source": WALK_TRAFFIC_SOURCE, "kernel": "k_walk_batched",
+            "bytes_per_step": BYTES_PER_STEP, "peak_source": peak_kind,
+            "algorithmic_bytes_per_launch": bytes_per_launch}
 
     cpu = None
     if rank == 0 and not args.no_cpu:

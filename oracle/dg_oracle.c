@@ -233,7 +233,15 @@ static int weight_ok(double w)
     return isfinite(w) && w > 0.0;
 }
 
-/* G(0): n vertices, m undirected edges; simple, 0 <= ids < n, w > 0 finite. */
+static int adj_cmp(const void *x, const void *y)
+{
+    const orc_adj *a = (const orc_adj *)x, *b = (const orc_adj *)y;
+    return (a->nbr > b->nbr) - (a->nbr < b->nbr);
+}
+
+/* G(0): n vertices, m undirected edges; simple, 0 <= ids < n, w > 0 finite.
+ * Built list by list: count degrees, fill, sort each list by neighbour id,
+ * reject a repeated pair (two equal neighbours in one list). */
 orc_state *orc_create(int32_t n, int64_t m, const int32_t *u, const int32_t *v, const double *w,
                       uint64_t seed, double K, int32_t T, int32_t s, int32_t early_exit)
 {
@@ -244,9 +252,30 @@ orc_state *orc_create(int32_t n, int64_t m, const int32_t *u, const int32_t *v, 
     for (int64_t i = 0; i < m; i++) {
         int32_t a = u[i], b = v[i];
         if (a < 0 || a >= n || b < 0 || b >= n || a == b || !weight_ok(w[i])) goto fail;
-        if (graph_has(&st->G, a, b)) goto fail;
+        st->G.cap[a]++;
+        st->G.cap[b]++;
+    }
+    for (int32_t x = 0; x < n; x++) {
+        if (st->G.cap[x] == 0) continue;
+        st->G.adj[x] = (orc_adj *)malloc((size_t)st->G.cap[x] * sizeof(orc_adj));
+        if (!st->G.adj[x]) goto fail;
+    }
+    for (int64_t i = 0; i < m; i++) {
+        int32_t a = u[i], b = v[i];
         double r = 1.0 / w[i];
-        if (edge_insert(&st->G, a, b, w[i], r)) goto fail;
+        orc_adj *ea = &st->G.adj[a][st->G.deg[a]++];
+        ea->nbr = b;
+        ea->w = w[i];
+        ea->r = r;
+        orc_adj *eb = &st->G.adj[b][st->G.deg[b]++];
+        eb->nbr = a;
+        eb->w = w[i];
+        eb->r = r;
+    }
+    for (int32_t x = 0; x < n; x++) {
+        if (st->G.deg[x] > 1) qsort(st->G.adj[x], (size_t)st->G.deg[x], sizeof(orc_adj), adj_cmp);
+        for (int32_t k = 1; k < st->G.deg[x]; k++)
+            if (st->G.adj[x][k].nbr == st->G.adj[x][k - 1].nbr) goto fail;
     }
     st->seed = seed;
     st->K = K;
@@ -279,11 +308,34 @@ int orc_init_sparsifier(orc_state *st, int64_t mh, const int32_t *u, const int32
     }
     graph_free(&st->H);
     if (graph_init(&st->H, n)) return -2;
+    orc_graph *H = &st->H;
     for (int64_t i = 0; i < mh; i++) {
-        if (graph_has(&st->H, u[i], v[i])) continue; /* repeated entry: set semantics */
+        H->cap[u[i]]++;
+        H->cap[v[i]]++;
+    }
+    for (int32_t x = 0; x < n; x++) {
+        if (H->cap[x] == 0) continue;
+        H->adj[x] = (orc_adj *)malloc((size_t)H->cap[x] * sizeof(orc_adj));
+        if (!H->adj[x]) return -2;
+    }
+    for (int64_t i = 0; i < mh; i++) {
         double w, r;
-        edge_wr(&st->G, u[i], v[i], &w, &r);
-        if (edge_insert(&st->H, u[i], v[i], w, r)) return -2;
+        edge_wr(&st->G, u[i], v[i], &w, &r); /* weights taken from G */
+        orc_adj *ea = &H->adj[u[i]][H->deg[u[i]]++];
+        ea->nbr = v[i];
+        ea->w = w;
+        ea->r = r;
+        orc_adj *eb = &H->adj[v[i]][H->deg[v[i]]++];
+        eb->nbr = u[i];
+        eb->w = w;
+        eb->r = r;
+    }
+    for (int32_t x = 0; x < n; x++) { /* sort, then keep a repeated pair once */
+        if (H->deg[x] > 1) qsort(H->adj[x], (size_t)H->deg[x], sizeof(orc_adj), adj_cmp);
+        int32_t kept = 0;
+        for (int32_t k = 0; k < H->deg[x]; k++)
+            if (kept == 0 || H->adj[x][k].nbr != H->adj[x][kept - 1].nbr) H->adj[x][kept++] = H->adj[x][k];
+        H->deg[x] = kept;
     }
     return 0;
 }
@@ -396,13 +448,16 @@ typedef struct {
  * Apply one batch of nu updates.  Per-update outputs (each an array of nu):
  *   status, walked, hit, accepted, fallback, nhits, best, nrec, steps, rest.
  * Optional: wout (nu*s records) and paths (nu*s*(T+1) vertices, -1 padded).
+ * walk_mask (nullable): when given, only updates with a non-zero entry run
+ * their walks (a sampling mode for very large batches: statuses and G are
+ * complete, walk results and commits only for the sampled updates).
  * Returns 0, or -2 on allocation failure.
  */
 int orc_apply_batch(orc_state *st, int64_t nu, const int32_t *u, const int32_t *v, const double *w,
                     const int32_t *op, int32_t *status, uint8_t *walked, uint8_t *hit,
                     uint8_t *accepted, uint8_t *fallback, int32_t *nhits, int32_t *best,
                     int32_t *nrec, int32_t *steps, double *rest, orc_walker_out *wout,
-                    int32_t *paths)
+                    int32_t *paths, const uint8_t *walk_mask)
 {
     orc_graph *G = &st->G, *H = &st->H;
     const int32_t n = G->n, s = st->s, T = st->T;
@@ -480,6 +535,7 @@ int orc_apply_batch(orc_state *st, int64_t nu, const int32_t *u, const int32_t *
     /* (iii) walks from the snapshot (H' for insertions, G_b for deletions). */
     for (int64_t i = 0; i < nu; i++) {
         if (!walked[i]) continue;
+        if (walk_mask && !walk_mask[i]) continue;
         const int deletion = (op[i] == OP_DEL);
         const orc_graph *g = deletion ? G : H;
         const uint64_t upd_id = id0 + (uint64_t)i;

@@ -60,7 +60,7 @@ def lib():
                                C.c_uint32, C.POINTER(C.c_int32), C.POINTER(C.c_double), P]
         L.orc_walk.restype = C.c_int
         L.orc_apply_batch.argtypes = [P, C.c_int64, i32p, i32p, f64p, i32p, i32p, u8p, u8p, u8p, u8p,
-                                      i32p, i32p, i32p, i32p, f64p, P, P]
+                                      i32p, i32p, i32p, i32p, f64p, P, P, P]
         L.orc_apply_batch.restype = C.c_int
         L.orc_query.argtypes = [P, C.c_int, C.c_int64, i32p, i32p, f64p]
         L.orc_query.restype = C.c_int64
@@ -129,8 +129,12 @@ class OracleGraph:
             raise ValueError("vertex out of range")
         return reason, steps.value, R.value, path[: steps.value + 1].copy()
 
-    def apply(self, u, v, w, op, *, walkers=False, paths=False):
-        """Apply one batch; returns a dict of per-update arrays (and walker records)."""
+    def apply(self, u, v, w, op, *, walkers=False, paths=False, walk_mask=None):
+        """Apply one batch; returns a dict of per-update arrays (and walker records).
+
+        walk_mask (optional bool array): walk only the marked updates (sampling
+        mode for very large batches; H then lacks the unsampled commits)."""
+        mask = None if walk_mask is None else np.ascontiguousarray(walk_mask, np.uint8)
         nu = len(u)
         u = np.ascontiguousarray(u, np.int32)
         v = np.ascontiguousarray(v, np.int32)
@@ -147,7 +151,8 @@ class OracleGraph:
                                    out["accepted"], out["fallback"], out["nhits"], out["best_walker"],
                                    out["nrecovered"], out["steps"], out["r_est"],
                                    None if wout is None else wout.ctypes.data,
-                                   None if pbuf is None else pbuf.ctypes.data)
+                                   None if pbuf is None else pbuf.ctypes.data,
+                                   None if mask is None else mask.ctypes.data)
         if rc != 0:
             raise MemoryError("oracle batch failed")
         if walkers:

@@ -127,31 +127,32 @@ def rmat(scale: int, n_edges: int, rng: np.random.Generator,
     exist; the first ``n_edges`` distinct edges in draw order are kept.
     """
     n = 1 << scale
-    cum = np.cumsum(abcd)[:3]
-    have = 0
-    uniq = np.empty(0, dtype=np.int64)
-    first_pos = np.empty(0, dtype=np.int64)
-    drawn = 0
-    while have < n_edges:
+    # quadrant per level from an integer draw in [0, 100): the probabilities are
+    # whole percents, so thresholds reproduce them exactly
+    t_a = int(round(abcd[0] * 100))
+    t_b = t_a + int(round(abcd[1] * 100))
+    t_c = t_b + int(round(abcd[2] * 100))
+    keys = []  # canonical keys of non-loop samples, in draw order
+    raw = 0
+    uniq = first = None
+    while True:
         m = round_size
         u = np.zeros(m, dtype=np.int64)
         v = np.zeros(m, dtype=np.int64)
         for _ in range(scale):
-            q = np.searchsorted(cum, rng.random(m), side="right")
-            u = (u << 1) | (q >= 2)
-            v = (v << 1) | ((q == 1) | (q == 3))
+            q = rng.integers(0, 100, size=m, dtype=np.uint8)
+            u = (u << 1) | (q >= t_b)
+            v = (v << 1) | (((q >= t_a) & (q < t_b)) | (q >= t_c))
         keep = u != v
-        a = np.minimum(u, v)[keep]
-        b = np.maximum(u, v)[keep]
-        k = a * n + b
-        pos = np.nonzero(keep)[0].astype(np.int64) + drawn
-        drawn += m
-        allk = np.concatenate([uniq, k])
-        allp = np.concatenate([first_pos, pos])
-        uk, ui = np.unique(allk, return_index=True)
-        uniq, first_pos = uk, allp[ui]
-        have = uniq.size
-    order = np.argsort(first_pos, kind="stable")[:n_edges]
+        keys.append(np.minimum(u, v)[keep] * n + np.maximum(u, v)[keep])
+        raw += int(keep.sum())
+        if raw < n_edges:
+            continue
+        allk = np.concatenate(keys)
+        uniq, first = np.unique(allk, return_index=True)
+        if uniq.size >= n_edges:
+            break
+    order = np.argsort(first, kind="stable")[:n_edges]
     kk = uniq[order]
     a, b = kk // n, kk % n
     perm = rng.permutation(n)

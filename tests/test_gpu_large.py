@@ -1,0 +1,68 @@
+"""Parity on the large synthetic workloads.
+
+* FEA-like triangulated 2048 x 2048 grid (4.2M vertices, 12.6M edges) at its
+  full batch of 100k mixed updates, in the benchmark's launch form (the first
+  batch autotunes, the second replays the captured step): every update result
+  and the final H and G match the oracle.
+* R-MAT (power law, hubs of degree > 10^4): every status, walked flag and the
+  final G match; walk results are compared on a sample of updates (the oracle's
+  plain neighbour scan costs O(degree) per step at the hubs), using the
+  oracle's walk mask.  Scale 18 runs by default; the full scale-22, 64M-edge
+  graph runs when DG_RUN_SLOW=1.
+"""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+import pytest
+
+from paper_2505_02741_b300 import dygrass as D
+from paper_2505_02741_b300 import workloads as W
+from tests.gpu_util import FIELDS, assert_edges_equal, pair, step_both
+
+pytestmark = pytest.mark.gpu
+
+
+def test_fea_full_size_batches():
+    wl, st = W.make_fea()
+    ctx, g, o = pair(wl.n, wl.a, wl.b, wl.w, wl.h_ids)
+    for bi in range(2):
+        bt = st.next_batch(50_000, 50_000)
+        res, _ = step_both(g, o, bt.u, bt.v, bt.w, bt.op, where=f"fea batch {bi}")
+        assert (res["status"] == 0).all()
+    assert g.stats()["graph_replayed"] == 1
+    ctx.close()
+
+
+def _rmat_sampled(scale, n_edges, n_ins, n_del, n_sample):
+    wl, st = W.make_rmat(scale, n_edges)
+    ctx, g, o = pair(wl.n, wl.a, wl.b, wl.w, wl.h_ids)
+    bt = st.next_batch(n_ins, n_del)
+    res = g.apply(D.make_updates(bt.u, bt.v, bt.w, bt.op))
+    rng = np.random.default_rng(scale)
+    walked = np.nonzero(res["walked"])[0]
+    dels = walked[bt.op[walked] == 1]
+    ins = walked[bt.op[walked] == 0]
+    pick = np.concatenate([rng.choice(dels, min(n_sample // 2, dels.size), replace=False),
+                           rng.choice(ins, min(n_sample // 2, ins.size), replace=False)])
+    mask = np.zeros(len(bt), bool)
+    mask[pick] = True
+    ref = o.apply(bt.u, bt.v, bt.w, bt.op, walk_mask=mask)
+    assert np.array_equal(res["status"], ref["status"])
+    assert np.array_equal(res["walked"], ref["walked"])
+    for f in FIELDS:
+        assert np.array_equal(res[f][pick].astype(np.int64), ref[f][pick].astype(np.int64)), f
+    assert np.array_equal(res["r_est"][pick].view(np.uint64), ref["r_est"][pick].view(np.uint64))
+    assert_edges_equal(g.edges(), o.edges("G"), "G")
+    assert res["walked"].sum() > 0 and (res["steps"] == 0).any()  # isolated starts walk 0 steps
+    ctx.close()
+
+
+def test_rmat_scale18_sampled():
+    _rmat_sampled(18, 4_000_000, 12_000, 8_000, 400)
+
+
+@pytest.mark.skipif(os.environ.get("DG_RUN_SLOW") != "1", reason="full R-MAT scale 22 (64M edges): DG_RUN_SLOW=1")
+def test_rmat_scale22_full_size_sampled():
+    _rmat_sampled(22, 64_000_000, 30_000, 20_000, 200)

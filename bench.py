@@ -176,6 +176,125 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _split_requests(bt, sizes):
+    """Cut one valid batch (distinct current-edge deletions, distinct new-edge
+    insertions) into consecutive requests; each request stays valid in order."""
+    out, lo = [], 0
+    for s in sizes:
+        out.append((bt.u[lo:lo + s], bt.v[lo:lo + s], bt.w[lo:lo + s], bt.op[lo:lo + s]))
+        lo += s
+    return out
+
+
+def run_serve(args):
+    """Serving: the 64x64 grid, the 100^3 mesh and the 2048^2 FEA-like mesh
+    resident at once.  Per graph a Poisson request stream, batch sizes
+    floor(exp(U(0, ln 50001))) (clipped for the small grid), 50/50
+    insertions/deletions, offered at `load` x that graph's measured batched
+    capacity.  Reports updates/s and p50/p99 request latency (submit to results
+    on the host) beside the one-launch-per-update form on a sample of requests."""
+    import torch
+    from paper_2505_02741_b300 import dygrass as D
+    from paper_2505_02741_b300 import workloads as W
+
+    torch.cuda.init()
+    specs = [("grid64", lambda: W.make_grid(64, 64, seed=0), 400),
+             ("mesh100", lambda: W.make_mesh3d(seed=0), 50_000),
+             ("fea2048", lambda: W.make_fea(seed=0), 50_000)]
+    arr_rng = W.rngs(7)["arrivals"]
+    per_graph = max(4, args.requests // len(specs))
+    graphs = []
+    for name, mk, cap in specs:
+        wl, st = mk()
+        _, sizes = W.serving_arrivals(per_graph, 1.0, arr_rng)
+        sizes = np.minimum(sizes, cap)
+        if name == "grid64":
+            reqs = []
+            for s in sizes:
+                ins = int(s) // 2
+                b = st.next_batch(ins, int(s) - ins)
+                reqs.append((b.u, b.v, b.w, b.op))
+        else:
+            total = int(sizes.sum())
+            big = st.next_batch(total // 2, total - total // 2)
+            reqs = _split_requests(big, sizes)
+        graphs.append((name, wl, reqs))
+
+    def load(ctx, wl):
+        g = ctx.load_graph(wl.n, wl.a, wl.b, wl.w)
+        g.init_sparsifier(wl.a[wl.h_ids], wl.b[wl.h_ids])
+        return g
+
+    # batched capacity per graph, on its own copy (first requests, sequential)
+    cap_ups = {}
+    for name, wl, reqs in graphs:
+        ctx = D.Context()
+        g = load(ctx, wl)
+        done, t_tot = 0, 0.0
+        for r in reqs[:3]:  # warm-up: workspace, captured steps, autotuner
+            g.apply(D.make_updates(*r))
+        for r in reqs[3: min(15, len(reqs))]:
+            ups = D.make_updates(*r)
+            t0 = time.perf_counter()
+            g.apply(ups)
+            dt = time.perf_counter() - t0
+            done += len(ups)
+            t_tot += dt
+        cap_ups[name] = done / t_tot
+        ctx.close()
+
+    # the served stream
+    ctx = D.Context()
+    gs = {name: load(ctx, wl) for name, wl, _ in graphs}
+    schedule = []
+    for name, _, reqs in graphs:
+        mean = float(np.mean([len(r[0]) for r in reqs]))
+        lam = args.load * cap_ups[name] / mean  # requests / s
+        t = np.cumsum(arr_rng.exponential(1.0 / lam, size=len(reqs)))
+        for k, r in enumerate(reqs):
+            schedule.append((float(t[k]), name, k, D.make_updates(*r)))
+    schedule.sort(key=lambda x: x[0])
+    tickets = []
+    t_start = time.perf_counter()
+    for at, name, k, ups in schedule:
+        delay = at - (time.perf_counter() - t_start)
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append((name, k, len(ups)) + gs[name].submit(ups))
+    lat, units = [], 0
+    for name, k, nu, ticket, _res in tickets:
+        res, ms = gs[name].wait(ticket, timeout_ms=600000)
+        lat.append(ms)
+        units += int((res["status"] == 0).sum())
+    wall = time.perf_counter() - t_start
+    ctx.close()
+
+    # the one-launch-per-update form on a sample of the mesh requests
+    name, wl, reqs = graphs[1]
+    ctx = D.Context(walk_mode="per_update", cuda_graphs=False)
+    g = load(ctx, wl)
+    pu_lat, pu_units = [], 0
+    for r in reqs[:6]:
+        ups = D.make_updates(*r)
+        t0 = time.perf_counter()
+        res = g.apply(ups)
+        pu_lat.append(1e3 * (time.perf_counter() - t0))
+        pu_units += int((res["status"] == 0).sum())
+    ctx.close()
+
+    line = {"metric": "serving: updates/s and p50/p99 request latency", "workload": "serve",
+            "value": units / wall, "unit": "updates/s", "n_gpus": 1, "requests": len(tickets),
+            "offered_load": args.load, "capacity_updates_per_s": cap_ups,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(np.max(lat))},
+            "graphs": {n: {"n": wl.n, "m": wl.m, "requests": len(r)} for n, wl, r in graphs},
+            "per_update_form": {"graph": "mesh100", "requests": len(pu_lat),
+                                "updates_per_s": pu_units / (sum(pu_lat) / 1e3),
+                                "p50_ms": float(np.percentile(pu_lat, 50)), "p99_ms": float(np.percentile(pu_lat, 99))},
+            "dtype": "f64", "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -186,11 +305,17 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--walk-shape", default="", help="fixed walk launch shape 'block,ilp' (skips the autotuner)")
+    ap.add_argument("--workload", default="mesh", choices=["mesh", "fea", "rmat", "serve"],
+                    help="mesh (default line), fea, rmat, or serve (several graphs resident, Poisson arrivals)")
+    ap.add_argument("--load", type=float, default=0.6, help="serve: offered load as a fraction of capacity")
+    ap.add_argument("--requests", type=int, default=1000, help="serve: requests in the measured stream")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.warmup < 3:
         raise SystemExit("at least 3 warm-up steps")
+    if args.workload == "serve":
+        return run_serve(args)
 
     import torch
     from paper_2505_02741_b300 import dygrass as D
@@ -207,9 +332,17 @@ def main():
     dev = local
 
     # workload (each rank an independent replica: weak scaling, no data-path collective)
-    wl, st = W.make_mesh3d(seed=rank)
+    n_ins, n_del = N_INS, N_DEL
+    if args.workload == "fea":  # one batch of 100k mixed updates per step
+        wl, st = W.make_fea(seed=rank)
+        n_ins, n_del = 50_000, 50_000
+    elif args.workload == "rmat":  # 50k updates per step, 60 % insertions
+        wl, st = W.make_rmat(seed=rank)
+        n_ins, n_del = 30_000, 20_000
+    else:
+        wl, st = W.make_mesh3d(seed=rank)
     n_batches = args.warmup + args.steps + args.steps + args.per_update_steps
-    batches = [st.next_batch(N_INS, N_DEL) for _ in range(n_batches)]
+    batches = [st.next_batch(n_ins, n_del) for _ in range(n_batches)]
 
     ctx = D.Context(device=dev, K=wl.K, T=wl.T, s=wl.s)
     g = ctx.load_graph(wl.n, wl.a, wl.b, wl.w)
@@ -275,7 +408,7 @@ def main():
         e2e_t.append(time.perf_counter() - t0)
         e2e_valid += int((res["status"] == 0).sum())
     bucket = 1024
-    while bucket < N_INS + N_DEL:
+    while bucket < n_ins + n_del:
         bucket *= 2
     (e2e_sum,), (e2e_tmax,) = reduce_over_ranks([e2e_valid], [sum(e2e_t)], world, backend)
     e2e = {"value": e2e_sum / e2e_tmax, "unit": "updates/s", "h2d_bytes_per_step": 24 * bucket + 16,
@@ -321,7 +454,8 @@ def main():
     bytes_per_launch = BYTES_PER_STEP * steps_done / args.steps
     achieved = bytes_per_launch / avg_walk_s / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": WALK_TRAFFIC_BYTES, "traffic_source": WALK_TRAFFIC_SOURCE, "kernel": "k_walk_batched",
+            "traffic": WALK_TRAFFIC_BYTES if args.workload == "mesh" else None,
+            "traffic_source": WALK_TRAFFIC_SOURCE if args.workload == "mesh" else None, "kernel": "k_walk_batched",
             "bytes_per_step": BYTES_PER_STEP, "peak_source": peak_kind,
             "algorithmic_bytes_per_launch": bytes_per_launch}
 
@@ -338,8 +472,8 @@ def main():
             "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl.name, "n": wl.n, "m": wl.m, "batch": N_INS + N_DEL, "insertions": N_INS,
-                       "deletions": N_DEL, "K": wl.K, "T": wl.T, "s": wl.s, "parallelism": f"replicas{world}",
+            "config": {"workload": wl.name, "n": wl.n, "m": wl.m, "batch": n_ins + n_del, "insertions": n_ins,
+                       "deletions": n_del, "K": wl.K, "T": wl.T, "s": wl.s, "parallelism": f"replicas{world}",
                        "l2": "flushed (256 MB write) between timed steps"},
             "walk_steps_per_s": walk_steps_per_s,
             "per_batch": {"walk_steps": steps_done / args.steps,

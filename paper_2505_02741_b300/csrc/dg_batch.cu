@@ -300,7 +300,8 @@ uint64_t BatchWS::bytes() const {
     b += t_wpq.bytes() + recR.bytes() + t_kind.bytes() + best.bytes();
     b += ckeys.bytes() + ckeys_alt.bytes() + ck2.bytes() + cvals.bytes() + cvals_alt.bytes() + chist.bytes();
     b += cscan.bytes() + ccount.bytes() + cflag.bytes() + cpos.bytes() + cv2.bytes() + ccount2.bytes();
-    b += cw.bytes() + kind_ins.bytes() + path_buf.bytes() + path_len.bytes() + path_w.bytes();
+    b += cw.bytes() + kind_ins.bytes() + path_buf.bytes() + path_len.bytes() + path_w.bytes() + fb_list.bytes() +
+         fb_count.bytes();
     b += dbg_reason.bytes() + dbg_steps.bytes() + dbg_paths.bytes();
     b += apG.bytes() + apH.bytes() + apC.bytes();
     return b;
@@ -386,6 +387,8 @@ static void ensure_ws(Ctx& c, DGraph& g, uint32_t b_max, cudaStream_t st) {
     w.path_buf.ensure(a, (size_t)B * (T + 1), st);
     w.path_w.ensure(a, (size_t)B * T, st);
     w.path_len.ensure(a, B, st);
+    w.fb_list.ensure(a, B, st);
+    w.fb_count.ensure(a, 1, st);
     if (c.cfg.record) {
         w.dbg_reason.ensure(a, (size_t)B * s, st);
         w.dbg_steps.ensure(a, (size_t)B * s, st);
@@ -672,7 +675,7 @@ void graph_release_ws(Ctx& c, DGraph& g, cudaStream_t st) {
     REL(hpos); REL(hvals); REL(hcount); REL(gkind); REL(ghrem); REL(kind_del); REL(gw); REL(t_u); REL(t_v);
     REL(t_idx); REL(t_kstar); REL(t_count); REL(meta); REL(t_wpq); REL(recR); REL(t_kind); REL(best);
     REL(ckeys); REL(ckeys_alt); REL(ck2); REL(cvals); REL(cvals_alt); REL(chist); REL(cscan); REL(ccount);
-    REL(cflag); REL(cpos); REL(cv2); REL(ccount2); REL(cw); REL(kind_ins); REL(path_buf); REL(path_w); REL(path_len); REL(dbg_reason);
+    REL(cflag); REL(cpos); REL(cv2); REL(ccount2); REL(cw); REL(kind_ins); REL(path_buf); REL(path_w); REL(path_len); REL(fb_list); REL(fb_count); REL(dbg_reason);
     REL(dbg_steps); REL(dbg_paths);
 #undef REL
     w.b_max = 0;
@@ -911,7 +914,7 @@ static void enqueue_commit(Ctx& c, DGraph& g, cudaStream_t st) {
     cd.count = w.ccount.p;
     cd.cap = CC;
     launch_emit(g.H.view(), g.G.view(), tasks_of(w), params_of(c.cfg), recs_of(c, w), w.hdr.p, w.best.p, w.fin_w.p,
-                w.res.p, w.ctr.p, cd, PathBufs{w.path_buf.p, w.path_w.p, w.path_len.p}, B, w.err.p, st);
+                w.res.p, w.ctr.p, cd, PathBufs{w.path_buf.p, w.path_w.p, w.path_len.p, w.fb_list.p, w.fb_count.p}, B, w.err.p, st);
     DG_CUDA(record_event(g.ev[6], st));
     SortBufs cs{w.ckeys.p, w.cvals.p, w.ckeys_alt.p, w.cvals_alt.p, w.chist.p, w.cscan.p, w.err.p};
     const bool calt = radix_sort_pairs(cs, w.ccount.p, CC, bit_length((uint64_t)n * n - 1), st);

@@ -57,7 +57,7 @@ struct BatchWS {
     DBuf<uint32_t> cvals, cvals_alt, chist, cscan, ccount, cflag, cpos, cv2, ccount2;
     DBuf<double> cw;
     DBuf<uint8_t> kind_ins;
-    DBuf<uint32_t> path_buf, path_len;
+    DBuf<uint32_t> path_buf, path_len, fb_list, fb_count;
     DBuf<double> path_w;
     // debug
     DBuf<int32_t> dbg_reason, dbg_steps, dbg_paths;

@@ -406,11 +406,25 @@ __global__ void k_exec_fix(ExecArgs a, uint32_t* d_err) {
         const uint32_t local = item - a.s_off[t];
         const uint32_t x = a.tv[t];
         const uint32_t lx = a.g.off[x];
-        const uint32_t y = a.g.pool[lx + local].nbr;
+        const uint4 e = *reinterpret_cast<const uint4*>(a.g.pool + lx + local);
+        const uint32_t y = e.x;
         if (y >= a.n) {
             atomicOr(d_err, (uint32_t)ERR_INTERNAL);
             continue;
         }
+        if (!a.touched[y] && e.z != 0u) {
+            // entry copied from x's old list and y's list is unchanged: its cached
+            // (off, deg, rev) still hold, and rev is x's slot in y's list; only the
+            // back-entry (which points at x's list) needs the new off / deg / slot
+            const uint32_t ly = a.g.off[y];
+            if (e.w >= a.g.deg[y]) {
+                atomicOr(d_err, (uint32_t)ERR_INTERNAL);
+                continue;
+            }
+            *reinterpret_cast<uint4*>(a.g.pool + ly + e.w) = make_uint4(x, lx, a.g.deg[x], local);
+            continue;
+        }
+        // a new entry (deg field still 0) or y's list changed too: search x in y's list
         const uint32_t ly = a.g.off[y], dy = a.g.deg[y];
         const uint32_t p = lower_bound_nbr(a.g.pool + ly, dy, x);
         if (p >= dy || a.g.pool[ly + p].nbr != x) {

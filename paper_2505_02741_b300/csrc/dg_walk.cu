@@ -504,40 +504,89 @@ __global__ void k_replay(CSRView H, CSRView G, WalkTasks t, WalkParams p, WalkRe
             }
             pb.len[j] = steps;
         } else {
-            // no walker reached v: per endpoint, the minimum-resistance G_b edge not in H'
+            // no walker reached v: the fallback edges are chosen by k_fallback
             res[i].fallback = 1;
-            uint32_t pick_x[2] = {NONE, NONE}, pick_y[2] = {NONE, NONE};
-            double pick_w[2] = {0.0, 0.0};
-            const uint32_t ends[2] = {u, v};
-            for (int e2 = 0; e2 < 2; ++e2) {
-                const uint32_t x = ends[e2];
-                const Ent* L = G.pool + G.off[x];
-                const uint32_t d = G.deg[x];
-                double rmin = INFINITY;
-                for (uint32_t k = 0; k < d; ++k) {
-                    const uint32_t y = L[k].nbr;
-                    const double rr = L[k].r;
-                    if (!(rr < rmin)) continue;  // ascending ids: strict < keeps the smaller id
-                    if (has_edge(H, x, y)) continue;
-                    rmin = rr;
-                    pick_x[e2] = x;
-                    pick_y[e2] = y;
-                    pick_w[e2] = L[k].w;
+            pb.fb_list[atomicAdd(pb.fb_count, 1u)] = j;
+        }
+    }
+}
+
+// Fallback of a walked deletion whose walkers all missed: for each endpoint x,
+// the G_b edge of minimum resistance not in H' (ties: smaller neighbour id).
+// One block per deletion scans each endpoint's list cooperatively (hub lists
+// hold 10^5 entries), then reduces (r, neighbour) lexicographically.
+__global__ void __launch_bounds__(256) k_fallback(CSRView H, CSRView G, WalkTasks t, dg_update_result* res,
+                                                  BatchCounters* ctr, Cands c, PathBufs pb, uint32_t w_max,
+                                                  uint32_t* d_err) {
+    if (walk_aborted(d_err)) return;
+    __shared__ double s_r[8];
+    __shared__ uint32_t s_y[8];
+    __shared__ double s_w[8];
+    __shared__ uint32_t pick_y[2];
+    __shared__ double pick_w[2];
+    const uint32_t F = min(*pb.fb_count, w_max);
+    const uint32_t n = (uint32_t)G.n;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t f = blockIdx.x; f < F; f += gridDim.x) {
+        const uint32_t j = pb.fb_list[f];
+        const uint32_t ends[2] = {t.u[j], t.v[j]};
+        for (int e2 = 0; e2 < 2; ++e2) {
+            const uint32_t x = ends[e2];
+            const Ent* L = G.pool + G.off[x];
+            const uint32_t d = G.deg[x];
+            double br = INFINITY, bw = 0.0;
+            uint32_t by = NONE;
+            for (uint32_t k = threadIdx.x; k < d; k += blockDim.x) {
+                const double rr = L[k].r;
+                if (!(rr < br)) continue;  // this thread's ids ascend: strict < keeps the smaller id
+                const uint32_t y = L[k].nbr;
+                if (has_edge(H, x, y)) continue;
+                br = rr;
+                by = y;
+                bw = L[k].w;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double orr = __shfl_xor_sync(0xffffffffu, br, o);
+                const uint32_t oy = __shfl_xor_sync(0xffffffffu, by, o);
+                const double ow = __shfl_xor_sync(0xffffffffu, bw, o);
+                if (orr < br || (orr == br && oy < by)) {
+                    br = orr;
+                    by = oy;
+                    bw = ow;
                 }
             }
+            if (lane == 0) {
+                s_r[warp] = br;
+                s_y[warp] = by;
+                s_w[warp] = bw;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                for (int q = 1; q < (int)(blockDim.x >> 5); ++q)
+                    if (s_r[q] < br || (s_r[q] == br && s_y[q] < by)) {
+                        br = s_r[q];
+                        by = s_y[q];
+                        bw = s_w[q];
+                    }
+                pick_y[e2] = by;
+                pick_w[e2] = bw;
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            const uint32_t i = t.idx[j];
             uint32_t emitted = 0;
             for (int e2 = 0; e2 < 2; ++e2) {
-                if (pick_x[e2] == NONE) continue;
-                if (e2 == 1 && pick_x[0] != NONE &&
-                    ((pick_x[0] == pick_x[1] && pick_y[0] == pick_y[1]) ||
-                     (pick_x[0] == pick_y[1] && pick_y[0] == pick_x[1])))
-                    continue;
-                emit_edge(c, pick_x[e2], pick_y[e2], pick_w[e2], n, d_err);
+                if (pick_y[e2] == NONE) continue;
+                // both endpoints picked the edge (u, v) itself (it was re-inserted in the batch)
+                if (e2 == 1 && pick_y[0] != NONE && pick_y[0] == ends[1] && pick_y[1] == ends[0]) continue;
+                emit_edge(c, ends[e2], pick_y[e2], pick_w[e2], n, d_err);
                 ++emitted;
             }
             res[i].nrecovered = (int32_t)emitted;
             if (emitted) atomicAdd(&ctr->recovered, (unsigned long long)emitted);
         }
+        __syncthreads();
     }
 }
 
@@ -575,9 +624,11 @@ void launch_emit(const CSRView& H, const CSRView& G, const WalkTasks& t, const W
     const uint32_t cap = (uint32_t)device_sms() * 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
+    DG_CUDA(cudaMemsetAsync(pb.fb_count, 0, 4, st));
     k_replay<<<blocks, 128, 0, st>>>(H, G, t, p, r, d_hdr, best, fin_w, res, ctr, c, pb, w_max, d_err);
     k_emit_path<<<(unsigned)device_sms() * 8, 256, 0, st>>>(H, t, p, res, ctr, c, pb, w_max, d_err);
-    g_launches += 2;
+    k_fallback<<<(unsigned)device_sms() * 4, 256, 0, st>>>(H, G, t, res, ctr, c, pb, w_max, d_err);
+    g_launches += 3;
     DG_CHECK_LAUNCH();
 }
 

@@ -88,6 +88,8 @@ struct PathBufs {
     uint32_t* v;
     double* w;
     uint32_t* len;
+    uint32_t* fb_list;   // walked deletions without a hit (fallback), appended
+    uint32_t* fb_count;
 };
 
 // recovered path edges / fallback edges of walked deletions, kept insertions

@@ -211,6 +211,19 @@ dg_status dg_create(const dg_config* cfg_in, dg_ctx** out) {
             const long v = std::strtol(f, nullptr, 10);
             if (v == 0 || v == 32 || v == 64 || v == 128) DG_CUDA(cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)v));
         }
+        // optional persisting-L2 set-aside (MB) for the sparsifier during walks
+        if (const char* f = std::getenv("DG_L2_PERSIST_MB")) {
+            const long mb = std::strtol(f, nullptr, 10);
+            int max_persist = 0, max_win = 0;
+            cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, cfg.device);
+            cudaDeviceGetAttribute(&max_win, cudaDevAttrMaxAccessPolicyWindowSize, cfg.device);
+            size_t want = mb > 0 ? (size_t)mb << 20 : 0;
+            if (want > (size_t)max_persist) want = (size_t)max_persist;
+            if (want > 0 && max_win > 0) {
+                DG_CUDA(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want));
+                walk_set_l2_persist(want, (size_t)max_win);
+            }
+        }
         auto c = std::make_unique<Ctx>();
         c->device = cfg.device;
         c->cfg.seed = cfg.seed;

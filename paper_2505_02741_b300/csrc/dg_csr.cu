@@ -322,6 +322,32 @@ __global__ void k_exec_meta(ExecArgs a, const uint32_t* d_err) {
     }
 }
 
+// Visit items [0, total) of consecutive segments (seg_off: exclusive start of
+// each of nseg segments).  Each warp takes one contiguous range of the items
+// (a multiple of 32, sized from the live total so all warps share the work);
+// lane 0 finds the segment of the range start by binary search, then every lane
+// carries its own segment index forward as its items advance (amortised O(1)
+// per item on long lists, one search per warp on short ones).
+template <int IT, typename F>
+__device__ __forceinline__ void for_segment_items(const uint32_t* seg_off, uint32_t nseg, uint32_t total, F&& f) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint64_t per = ((((uint64_t)total + nwarps - 1) / nwarps) + 31u) & ~31ull;
+    const uint64_t start = (uint64_t)warp * per;
+    if (start >= total) return;
+    const uint32_t end = (uint32_t)((start + per < (uint64_t)total) ? start + per : (uint64_t)total);
+    uint32_t t = 0;
+    if (lane == 0) t = upper_bound_arr<uint32_t>(seg_off, 0, nseg, (uint32_t)start) - 1;
+    t = __shfl_sync(0xffffffffu, t, 0);
+    for (uint32_t c0 = (uint32_t)start; c0 < end; c0 += 32u) {
+        const uint32_t item = c0 + lane;
+        if (item >= end) break;
+        while (t + 1 < nseg && seg_off[t + 1] <= item) ++t;
+        f(item, t, item - seg_off[t]);
+    }
+}
+
 // merge: one thread per (old entry | change) of every touched vertex
 __global__ void k_exec_merge(ExecArgs a, uint32_t* d_err) {
     if (aborted(d_err)) return;
@@ -329,9 +355,7 @@ __global__ void k_exec_merge(ExecArgs a, uint32_t* d_err) {
     const uint32_t WK = a.totals[TOT_WK];
     const uint32_t count = count_of(a.cl.d_count, a.cl.max_count);
     const uint32_t NI = a.totals[TOT_NI], ND = a.totals[TOT_ND];
-    for (uint32_t item = blockIdx.x * blockDim.x + threadIdx.x; item < WK; item += gridDim.x * blockDim.x) {
-        const uint32_t t = upper_bound_arr<uint32_t>(a.w_off, 0, X, item) - 1;
-        const uint32_t local = item - a.w_off[t];
+    for_segment_items<16>(a.w_off, X, WK, [&](uint32_t item, uint32_t t, uint32_t local) {
         const uint32_t x = a.tv[t];
         const uint32_t s0 = a.tstart[t], s1 = a.tend[t];
         const uint32_t od = a.odeg[t];
@@ -345,10 +369,10 @@ __global__ void k_exec_merge(ExecArgs a, uint32_t* d_err) {
             const bool found = c0 < s1 && a.cl.keys[c0] == key;
             uint8_t kd = 255;
             if (found) kd = a.cl.kinds[a.cl.vals[c0]];
-            if (kd == CHG_DEL) continue;
+            if (kd == CHG_DEL) return;
             if (kd == CHG_INS) {  // insertion of a present edge: inconsistent input
                 atomicOr(d_err, (uint32_t)ERR_INTERNAL);
-                continue;
+                return;
             }
             const uint32_t ib = pre_at(a.p_ins, c0, count, NI) - a.p_ins[s0];
             const uint32_t db = pre_at(a.p_del, c0, count, ND) - a.p_del[s0];
@@ -360,12 +384,12 @@ __global__ void k_exec_merge(ExecArgs a, uint32_t* d_err) {
             }
         } else {
             const uint32_t c = s0 + (local - od);
-            if (a.cl.kinds[a.cl.vals[c]] != CHG_INS) continue;
+            if (a.cl.kinds[a.cl.vals[c]] != CHG_INS) return;
             const uint32_t y = (uint32_t)(a.cl.keys[c] - (uint64_t)x * a.n);
             const uint32_t lb = lower_bound_nbr(L, od, y);
             if (lb < od && L[lb].nbr == y) {
                 atomicOr(d_err, (uint32_t)ERR_INTERNAL);
-                continue;
+                return;
             }
             const uint32_t ib = a.p_ins[c] - a.p_ins[s0];
             const uint32_t db = a.p_del[c] - a.p_del[s0];
@@ -380,37 +404,34 @@ __global__ void k_exec_merge(ExecArgs a, uint32_t* d_err) {
         }
         if (outpos >= a.ndeg[t]) {
             atomicOr(d_err, (uint32_t)ERR_INTERNAL);
-            continue;
+            return;
         }
         a.stage[a.s_off[t] + outpos] = out;
-    }
+    });
 }
 
 __global__ void k_exec_place(ExecArgs a, const uint32_t* d_err) {
     if (aborted(d_err)) return;
     const uint32_t X = a.totals[TOT_X];
     const uint32_t S = a.totals[TOT_S];
-    for (uint32_t item = blockIdx.x * blockDim.x + threadIdx.x; item < S; item += gridDim.x * blockDim.x) {
-        const uint32_t t = upper_bound_arr<uint32_t>(a.s_off, 0, X, item) - 1;
-        const uint32_t local = item - a.s_off[t];
+    for_segment_items<16>(a.s_off, X, S, [&](uint32_t item, uint32_t t, uint32_t local) {
         a.g.pool[dst_off(a, t) + local] = a.stage[item];
-    }
+    });
 }
 
 __global__ void k_exec_fix(ExecArgs a, uint32_t* d_err) {
     if (aborted(d_err)) return;
     const uint32_t X = a.totals[TOT_X];
     const uint32_t S = a.totals[TOT_S];
-    for (uint32_t item = blockIdx.x * blockDim.x + threadIdx.x; item < S; item += gridDim.x * blockDim.x) {
-        const uint32_t t = upper_bound_arr<uint32_t>(a.s_off, 0, X, item) - 1;
-        const uint32_t local = item - a.s_off[t];
+    for_segment_items<16>(a.s_off, X, S, [&](uint32_t item, uint32_t t, uint32_t local) {
+        (void)item;
         const uint32_t x = a.tv[t];
         const uint32_t lx = a.g.off[x];
         const uint4 e = *reinterpret_cast<const uint4*>(a.g.pool + lx + local);
         const uint32_t y = e.x;
         if (y >= a.n) {
             atomicOr(d_err, (uint32_t)ERR_INTERNAL);
-            continue;
+            return;
         }
         if (!a.touched[y] && e.z != 0u) {
             // entry copied from x's old list and y's list is unchanged: its cached
@@ -419,22 +440,22 @@ __global__ void k_exec_fix(ExecArgs a, uint32_t* d_err) {
             const uint32_t ly = a.g.off[y];
             if (e.w >= a.g.deg[y]) {
                 atomicOr(d_err, (uint32_t)ERR_INTERNAL);
-                continue;
+                return;
             }
             *reinterpret_cast<uint4*>(a.g.pool + ly + e.w) = make_uint4(x, lx, a.g.deg[x], local);
-            continue;
+            return;
         }
         // a new entry (deg field still 0) or y's list changed too: search x in y's list
         const uint32_t ly = a.g.off[y], dy = a.g.deg[y];
         const uint32_t p = lower_bound_nbr(a.g.pool + ly, dy, x);
         if (p >= dy || a.g.pool[ly + p].nbr != x) {
             atomicOr(d_err, (uint32_t)ERR_INTERNAL);
-            continue;
+            return;
         }
         *reinterpret_cast<uint4*>(a.g.pool + lx + local) = make_uint4(y, ly, dy, p);
         if (!a.touched[y])
             *reinterpret_cast<uint4*>(a.g.pool + ly + p) = make_uint4(x, lx, a.g.deg[x], local);
-    }
+    });
 }
 
 __global__ void k_exec_untouch(ExecArgs a, const uint32_t* d_err) {

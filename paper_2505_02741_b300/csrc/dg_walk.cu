@@ -314,6 +314,17 @@ static WalkKernelArgs make_args(const CSRView& H, const CSRView& G, const WalkTa
     return a;
 }
 
+// Optional L2 residency for the sparsifier: the walk launch carries an access
+// policy window over H's pool, so H's entries (read by every insertion walk)
+// persist in the set-aside part of L2 while deletion walks stream through G.
+static size_t g_persist_bytes = 0;  // set-aside L2 bytes of this context (0 = off)
+static size_t g_max_window = 0;
+
+void walk_set_l2_persist(size_t persist_bytes, size_t max_window) {
+    g_persist_bytes = persist_bytes;
+    g_max_window = max_window;
+}
+
 template <int ILP>
 static void launch_ilp(const WalkKernelArgs& a, const WalkShape& shape, cudaStream_t st) {
     int bps = shape.blocks_per_sm;
@@ -323,7 +334,27 @@ static void launch_ilp(const WalkKernelArgs& a, const WalkShape& shape, cudaStre
         bps = occ > 0 ? occ : 1;
     }
     const int grid = device_sms() * bps;
-    k_walk_batched<ILP><<<grid, shape.block, 0, st>>>(a);
+    if (g_persist_bytes == 0 || a.H.pool == nullptr) {
+        k_walk_batched<ILP><<<grid, shape.block, 0, st>>>(a);
+        return;
+    }
+    size_t win = (size_t)a.H.pool_cap * sizeof(Ent);
+    if (win > g_max_window) win = g_max_window;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(shape.block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+    attr[0].val.accessPolicyWindow.base_ptr = (void*)a.H.pool;
+    attr[0].val.accessPolicyWindow.num_bytes = win;
+    attr[0].val.accessPolicyWindow.hitRatio = win > g_persist_bytes ? (float)g_persist_bytes / (float)win : 1.0f;
+    attr[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    DG_CUDA(cudaLaunchKernelEx(&cfg, k_walk_batched<ILP>, a));
 }
 
 void launch_walk_batched(const CSRView& H, const CSRView& G, const WalkTasks& t, const WalkParams& p,

@@ -100,4 +100,7 @@ void launch_emit(const CSRView& H, const CSRView& G, const WalkTasks& t, const W
 
 int device_sms();
 
+// L2 set-aside for H during walks (bytes reserved for persisting lines, max window size)
+void walk_set_l2_persist(size_t persist_bytes, size_t max_window);
+
 }  // namespace dg

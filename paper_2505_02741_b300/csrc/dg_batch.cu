@@ -113,7 +113,8 @@ __global__ void k_compact_kv(const uint64_t* __restrict__ keys, const uint32_t* 
 // per update: basic checks (op, range, self-loop, weight); sort key of its edge
 __global__ void k_val_prep(const dg_update* __restrict__ ups, const BatchHdr* hdr, uint32_t n, uint32_t b_max,
                            dg_update_result* __restrict__ res, uint64_t* __restrict__ keys,
-                           uint32_t* __restrict__ vals, uint8_t* __restrict__ wkind, double* __restrict__ fin_w) {
+                           uint32_t* __restrict__ vals, uint8_t* __restrict__ wkind, double* __restrict__ fin_w,
+                           uint32_t* __restrict__ fdel, uint32_t* __restrict__ fins) {
     const uint32_t nu = min(hdr->nu, b_max);
     const uint64_t sent = (uint64_t)n * n;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nu; i += gridDim.x * blockDim.x) {
@@ -140,6 +141,8 @@ __global__ void k_val_prep(const dg_update* __restrict__ ups, const BatchHdr* hd
         }
         vals[i] = i;
         wkind[i] = WALK_NONE;
+        fdel[i] = 0;  // walked-deletion / walked-insertion flags, set by k_val_runs
+        fins[i] = 0;
         fin_w[i] = __longlong_as_double(0x7ff8000000000000ll);  // NaN: edge absent at batch end
     }
 }
@@ -153,6 +156,8 @@ struct RunArgs {
     CSRView G, H;
     dg_update_result* res;
     uint8_t* wkind;
+    uint32_t* fdel;  // walk flags per update (deletions / insertions)
+    uint32_t* fins;
     double* fin_w;
     // net G changes (half-edges), appended
     uint64_t* gkeys;
@@ -193,6 +198,7 @@ __global__ void k_val_runs(RunArgs a) {
                     any_valid = true;
                     ++valid;
                     a.wkind[i] = WALK_INS;
+                    a.fins[i] = 1;
                     a.res[i].walked = 1;
                 }
             } else {
@@ -205,6 +211,7 @@ __global__ void k_val_runs(RunArgs a) {
                     if (in_h) {
                         hrem = true;
                         a.wkind[i] = WALK_DEL;
+                        a.fdel[i] = 1;
                         a.res[i].walked = 1;
                     }
                 }
@@ -233,18 +240,9 @@ __global__ void k_val_runs(RunArgs a) {
     }
 }
 
-// walked deletions and walked insertions, flagged separately: the task list
-// puts deletions (no K, the longest walks) first so they start first and the
-// short insertion walks fill the tail of the persistent launch
-__global__ void k_walk_flags(const uint8_t* __restrict__ wkind, const BatchHdr* hdr, uint32_t b_max,
-                             uint32_t* __restrict__ fdel, uint32_t* __restrict__ fins) {
-    const uint32_t nu = min(hdr->nu, b_max);
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nu; i += gridDim.x * blockDim.x) {
-        fdel[i] = wkind[i] == WALK_DEL;
-        fins[i] = wkind[i] == WALK_INS;
-    }
-}
-
+// Task list from the walk flags k_val_runs set: walked deletions (no K, the
+// longest walks) first, so they start first and the short insertion walks
+// fill the tail of the persistent launch.
 __global__ void k_make_tasks(const dg_update* __restrict__ ups, const uint8_t* __restrict__ wkind,
                              const uint32_t* __restrict__ pdel, const uint32_t* __restrict__ pins,
                              const uint32_t* __restrict__ totals, const BatchHdr* hdr, uint32_t b_max, WalkTasks t) {
@@ -729,7 +727,7 @@ static void enqueue_mutate(Ctx& c, DGraph& g, cudaStream_t st) {
     DG_CUDA(cudaMemsetAsync(w.t_kstar.p, 0xFF, 4ull * B, st));
     const uint32_t* d_nu = &w.hdr.p->nu;
     k_val_prep<<<grid_for(B), BT, 0, st>>>(w.ups.p, w.hdr.p, n, B, w.res.p, w.vkeys.p, w.vvals.p, w.wkind.p,
-                                          w.fin_w.p);
+                                          w.fin_w.p, w.wflag.p, w.wflag2.p);
     ++g_launches;
     SortBufs vs{w.vkeys.p, w.vvals.p, w.vkeys_alt.p, w.vvals_alt.p, w.vhist.p, w.vscan.p, w.err.p};
     const bool valt = radix_sort_pairs(vs, d_nu, B, bit_length((uint64_t)n * n), st);
@@ -752,9 +750,10 @@ static void enqueue_mutate(Ctx& c, DGraph& g, cudaStream_t st) {
     ra.gw = w.gw.p;
     ra.gcount = w.gcount.p;
     ra.ctr = w.ctr.p;
+    ra.fdel = w.wflag.p;
+    ra.fins = w.wflag2.p;
     k_val_runs<<<grid_for(B), BT, 0, st>>>(ra);
-    k_walk_flags<<<grid_for(B), BT, 0, st>>>(w.wkind.p, w.hdr.p, B, w.wflag.p, w.wflag2.p);
-    g_launches += 2;
+    ++g_launches;
     {
         ScanJob j;
         j.in[0] = w.wflag.p;

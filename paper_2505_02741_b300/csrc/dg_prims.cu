@@ -239,7 +239,16 @@ constexpr size_t OS_GHIST = 0;
 constexpr size_t OS_CTR = OS_MAX_PASSES * 256;
 constexpr size_t OS_STATUS = OS_CTR + 32;
 
-size_t sort_hist_words(uint32_t n_max) { return OS_STATUS + 256ull * os_tiles(n_max) + 64; }
+// small sorts keep one status area per pass (cleared by a single memset);
+// large ones reuse one area and clear it before every pass
+constexpr uint32_t OS_SEPARATE_MAX_TILES = 1024;
+
+__host__ __device__ inline bool os_separate(uint32_t tiles) { return tiles <= OS_SEPARATE_MAX_TILES; }
+
+size_t sort_hist_words(uint32_t n_max) {
+    const uint32_t tiles = os_tiles(n_max);
+    return OS_STATUS + 256ull * tiles * (os_separate(tiles) ? OS_MAX_PASSES : 1) + 64;
+}
 size_t sort_scan_tmp_words(uint32_t n_max) { return scan_tmp_words(n_max + 1); }
 
 // digit totals of every pass in one read of the keys (warp-aggregated atomics)
@@ -283,7 +292,7 @@ __global__ void __launch_bounds__(OS_THREADS) k_os_pass(const uint64_t* __restri
     const uint32_t lt = (1u << l) - 1u;
     const int shift = 8 * pass;
     uint32_t* ctr = hist + OS_CTR + pass;
-    uint32_t* status = hist + OS_STATUS;
+    uint32_t* status = hist + OS_STATUS + (os_separate(tiles) ? (size_t)pass * tiles * 256 : 0);
     const uint32_t* gh = hist + OS_GHIST + 256 * pass;
     if (threadIdx.x == 0) s_tile = atomicAdd(ctr, 1u);
     for (int i = threadIdx.x; i < OS_WARPS * 256; i += OS_THREADS) (&s_warp[0][0])[i] = 0;
@@ -395,7 +404,8 @@ bool radix_sort_pairs(const SortBufs& b, const uint32_t* d_n, uint32_t n_max, in
     const int passes = (nbits + 7) / 8;
     const uint32_t tiles = os_tiles(n_max);
     // digit totals and tile counters, then per pass a cleared status area
-    cudaMemsetAsync(b.hist, 0, (OS_STATUS) * 4, st);
+    const bool separate = os_separate(tiles);
+    cudaMemsetAsync(b.hist, 0, (OS_STATUS + (separate ? 256ull * tiles * passes : 0)) * 4, st);
     uint32_t hblocks = (n_max + 255) / 256;
     if (hblocks > 148u * 8u) hblocks = 148u * 8u;
     k_os_hist<<<hblocks, 256, 0, st>>>(b.keys, d_n, n_max, passes, b.hist + OS_GHIST);
@@ -406,7 +416,7 @@ bool radix_sort_pairs(const SortBufs& b, const uint32_t* d_n, uint32_t n_max, in
     uint32_t* dst_v = b.vals_alt;
     bool in_alt = false;
     for (int p = 0; p < passes; ++p) {
-        cudaMemsetAsync(b.hist + OS_STATUS, 0, 256ull * tiles * 4, st);
+        if (!separate) cudaMemsetAsync(b.hist + OS_STATUS, 0, 256ull * tiles * 4, st);
         k_os_pass<<<tiles, OS_THREADS, 0, st>>>(src_k, src_v, dst_k, dst_v, d_n, n_max, p, b.hist, tiles, b.err);
         ++g_launches;
         in_alt = !in_alt;

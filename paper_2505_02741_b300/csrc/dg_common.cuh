@@ -17,19 +17,34 @@ namespace dg {
 
 struct __align__(32) Ent {
     uint32_t nbr;   // neighbour id
-    uint32_t noff;  // off[nbr] (cached)
-    uint32_t ndeg;  // deg[nbr] (cached)
-    uint32_t rev;   // position of this list's owner inside nbr's list
+    uint32_t noff;  // off[nbr] (cached), or HUBREF when nbr is a hub
+    uint32_t ndeg;  // deg[nbr] (cached); 0 only in an entry not yet refreshed
+    uint32_t rev;   // position of this list's owner inside nbr's list (unused for HUBREF)
     double r;       // resistance 1 / w (Section II-A, computed once, IEEE RN)
     double w;       // weight
 };
 static_assert(sizeof(Ent) == 32, "entry must be one 32-byte sector");
+
+// Hubs (high-degree vertices, power-law graphs): entries pointing at a hub do
+// not cache its list, so a hub's list can change without rewriting the back-
+// entries held by its (many) neighbours.  A walker arriving at a hub reads
+// off/deg from the vertex arrays and skips the previous vertex by id.
+// Hysteresis keeps a vertex near the threshold from flipping every batch.
+constexpr uint32_t HUBREF = 0xFFFFFFFFu;
+constexpr uint32_t HUB_HI = 1024;  // becomes a hub at this degree
+constexpr uint32_t HUB_LO = 768;   // stays a hub down to this degree
+
+__host__ __device__ inline bool hub_next(bool was_hub, uint32_t deg) {
+    return deg >= HUB_HI || (was_hub && deg >= HUB_LO);
+}
 
 // device view of one slack-slot CSR
 struct CSRView {
     uint32_t* off;
     uint32_t* deg;
     uint32_t* cap;
+    uint8_t* hub;             // 1 = entries pointing here hold HUBREF
+    uint32_t* nhub;           // number of hubs (device word)
     Ent* pool;
     unsigned long long* top;  // entries in use (bump pointer)
     uint64_t pool_cap;        // entries allocated
@@ -96,6 +111,45 @@ __device__ __forceinline__ void load_ent(const Ent* p, uint4& head, double2& tai
     const uint4* q = reinterpret_cast<const uint4*>(p);
     head = __ldg(q);
     tail = __ldg(reinterpret_cast<const double2*>(q + 1));
+}
+
+// One non-backtracking step (Section III-B) on list (off, deg) of vertex c:
+// j = floor(x * n_eff / 2^32), then the j-th neighbour other than the previous
+// vertex.  prev is the previous vertex's slot in this list (pid = false, from a
+// cached entry) or its id (pid = true, after arriving at a hub through HUBREF:
+// lists are sorted, so L[j] is taken when its id is below prev, else L[j+1]).
+// Returns 1 and advances (c, off, deg, prev, pid), 0 at a leaf (n_eff = 0),
+// -1 if an offset leaves the pool (a broken mutation; the caller reports it).
+__device__ __forceinline__ int nb_step(const CSRView& g, uint32_t x, uint32_t& c, uint32_t& off, uint32_t& deg,
+                                       uint32_t& prev, bool& pid, uint4& h, double2& tl) {
+    const uint32_t neff = deg - (prev != 0xFFFFFFFFu ? 1u : 0u);
+    if (neff == 0) return 0;
+    const uint32_t jj = __umulhi(x, neff);
+    uint32_t idx = pid ? jj : jj + (jj >= prev ? 1u : 0u);
+    if ((uint64_t)off + idx >= g.pool_cap) return -1;
+    const uint4* q = reinterpret_cast<const uint4*>(g.pool + off + idx);
+    h = __ldg(q);
+    if (pid && h.x >= prev) {
+        ++idx;
+        if ((uint64_t)off + idx >= g.pool_cap) return -1;
+        q = reinterpret_cast<const uint4*>(g.pool + off + idx);
+        h = __ldg(q);
+    }
+    tl = __ldg(reinterpret_cast<const double2*>(q + 1));
+    const uint32_t from = c;
+    c = h.x;
+    if (h.y == HUBREF) {
+        off = g.off[c];
+        deg = g.deg[c];
+        prev = from;
+        pid = true;
+    } else {
+        off = h.y;
+        deg = h.z;
+        prev = h.w;
+        pid = false;
+    }
+    return 1;
 }
 
 // first position in list L[0..d) whose neighbour id >= y

@@ -66,6 +66,10 @@ void csr_alloc_vertices(CSR& g, DevAlloc& a, int32_t n, cudaStream_t st) {
     g.off.ensure(a, (size_t)n + 1, st);
     g.deg.ensure(a, (size_t)n + 1, st);
     g.cap.ensure(a, (size_t)n + 1, st);
+    g.hub.ensure(a, (size_t)n + 1, st);
+    DG_CUDA(cudaMemsetAsync(g.hub.p, 0, g.hub.bytes(), st));
+    g.nhub.ensure(a, 1, st);
+    DG_CUDA(cudaMemsetAsync(g.nhub.p, 0, g.nhub.bytes(), st));
     g.top.ensure(a, 1, st);
     DG_CUDA(cudaMemsetAsync(g.off.p, 0, g.off.bytes(), st));
     DG_CUDA(cudaMemsetAsync(g.deg.p, 0, g.deg.bytes(), st));
@@ -77,6 +81,8 @@ void csr_release(CSR& g, DevAlloc& a, cudaStream_t st) {
     g.off.release(a, st);
     g.deg.release(a, st);
     g.cap.release(a, st);
+    g.hub.release(a, st);
+    g.nhub.release(a, st);
     g.pool.release(a, st);
     g.top.release(a, st);
     g.pool_cap = 0;
@@ -130,14 +136,28 @@ __global__ void k_build_fix(const uint64_t* __restrict__ keys, uint32_t count, u
         const uint64_t k = keys[c];
         const uint32_t x = (uint32_t)(k / n), y = (uint32_t)(k % n);
         const uint32_t s0 = lower_bound_arr<uint64_t>(keys, 0, c, (uint64_t)x * n);
-        const uint32_t ly = g.off[y], dy = g.deg[y];
-        const uint32_t p = lower_bound_nbr(g.pool + ly, dy, x);
-        if (p >= dy || g.pool[ly + p].nbr != x) {
-            atomicOr(d_err, (uint32_t)ERR_INTERNAL);
-            continue;
+        uint4 h;
+        if (g.hub[y]) {
+            h = make_uint4(y, HUBREF, 1u, 0u);
+        } else {
+            const uint32_t ly = g.off[y], dy = g.deg[y];
+            const uint32_t p = lower_bound_nbr(g.pool + ly, dy, x);
+            if (p >= dy || g.pool[ly + p].nbr != x) {
+                atomicOr(d_err, (uint32_t)ERR_INTERNAL);
+                continue;
+            }
+            h = make_uint4(y, ly, dy, p);
         }
-        uint4 h = make_uint4(y, ly, dy, p);
         *reinterpret_cast<uint4*>(g.pool + g.off[x] + (c - s0)) = h;
+    }
+}
+
+__global__ void k_hub_init(const uint32_t* __restrict__ deg, uint32_t n, uint8_t* __restrict__ hub,
+                           uint32_t* nhub) {
+    for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
+        const bool h = deg[x] >= HUB_HI;
+        hub[x] = h ? 1 : 0;
+        if (h) atomicAdd(nhub, 1u);
     }
 }
 
@@ -151,7 +171,9 @@ void csr_build(CSR& g, DevAlloc& a, const uint64_t* keys, const uint32_t* vals, 
         ++g_launches;
     }
     k_caps<<<grid, FLAT_THREADS, 0, st>>>(g.deg.p, n, g.slack, g.cap.p);
-    ++g_launches;
+    DG_CUDA(cudaMemsetAsync(g.nhub.p, 0, 4, st));
+    k_hub_init<<<grid, FLAT_THREADS, 0, st>>>(g.deg.p, n, g.hub.p, g.nhub.p);
+    g_launches += 2;
     DBuf<uint32_t> tmp, total;
     tmp.ensure(a, scan_tmp_words(n + 1), st);
     total.ensure(a, 2, st);
@@ -318,7 +340,11 @@ __global__ void k_exec_meta(ExecArgs a, const uint32_t* d_err) {
         a.g.off[x] = dst_off(a, t);
         a.g.deg[x] = a.ndeg[t];
         a.g.cap[x] = a.ncap[t];
-        a.touched[x] = 1;
+        // touched bit 0; bit 1 when x's hub status flips (its back-entries change form)
+        const bool was = a.g.hub[x] != 0, now = hub_next(was, a.ndeg[t]);
+        a.g.hub[x] = now ? 1 : 0;
+        if (was != now) atomicAdd(a.g.nhub, now ? 1u : 0xFFFFFFFFu);
+        a.touched[x] = (uint8_t)(1u | (was != now ? 2u : 0u));
     }
 }
 
@@ -433,28 +459,46 @@ __global__ void k_exec_fix(ExecArgs a, uint32_t* d_err) {
             atomicOr(d_err, (uint32_t)ERR_INTERNAL);
             return;
         }
-        if (!a.touched[y] && e.z != 0u) {
-            // entry copied from x's old list and y's list is unchanged: its cached
-            // (off, deg, rev) still hold, and rev is x's slot in y's list; only the
-            // back-entry (which points at x's list) needs the new off / deg / slot
-            const uint32_t ly = a.g.off[y];
-            if (e.w >= a.g.deg[y]) {
-                atomicOr(d_err, (uint32_t)ERR_INTERNAL);
-                return;
-            }
-            *reinterpret_cast<uint4*>(a.g.pool + ly + e.w) = make_uint4(x, lx, a.g.deg[x], local);
-            return;
-        }
-        // a new entry (deg field still 0) or y's list changed too: search x in y's list
+        const uint8_t tx = a.touched[x], ty = a.touched[y];
+        const bool x_hub = a.g.hub[x] != 0, y_hub = a.g.hub[y] != 0;
+        const bool fresh = e.z == 0u;  // inserted in this batch: nothing cached yet
         const uint32_t ly = a.g.off[y], dy = a.g.deg[y];
-        const uint32_t p = lower_bound_nbr(a.g.pool + ly, dy, x);
-        if (p >= dy || a.g.pool[ly + p].nbr != x) {
-            atomicOr(d_err, (uint32_t)ERR_INTERNAL);
-            return;
+        uint32_t p = 0xFFFFFFFFu;      // x's slot in y's list, found when needed
+        auto locate = [&]() -> bool {
+            if (p != 0xFFFFFFFFu) return true;
+            if (!fresh && e.y != HUBREF) {  // a valid copied entry caches the slot
+                p = e.w;
+            } else {
+                p = lower_bound_nbr(a.g.pool + ly, dy, x);
+            }
+            if (p >= dy || a.g.pool[ly + p].nbr != x) {
+                atomicOr(d_err, (uint32_t)ERR_INTERNAL);
+                return false;
+            }
+            return true;
+        };
+        // (i) this entry: its cache is still right when it was copied from x's old
+        // list and y's list did not change
+        if (fresh || (ty & 1u)) {
+            if (y_hub) {
+                *reinterpret_cast<uint4*>(a.g.pool + lx + local) = make_uint4(y, HUBREF, 1u, 0u);
+            } else {
+                p = lower_bound_nbr(a.g.pool + ly, dy, x);
+                if (p >= dy || a.g.pool[ly + p].nbr != x) {
+                    atomicOr(d_err, (uint32_t)ERR_INTERNAL);
+                    return;
+                }
+                *reinterpret_cast<uint4*>(a.g.pool + lx + local) = make_uint4(y, ly, dy, p);
+            }
         }
-        *reinterpret_cast<uint4*>(a.g.pool + lx + local) = make_uint4(y, ly, dy, p);
-        if (!a.touched[y])
-            *reinterpret_cast<uint4*>(a.g.pool + ly + p) = make_uint4(x, lx, a.g.deg[x], local);
+        // (ii) y's entry pointing at x, when y's list is unchanged (otherwise y's own
+        // pass writes it).  A hub that stayed a hub is referenced by HUBREF, which
+        // no change of its list can make stale.
+        if (ty & 1u) return;
+        if (x_hub && !(tx & 2u)) return;
+        if (!locate()) return;
+        const uint4 back = x_hub ? make_uint4(x, HUBREF, 1u, 0u) : make_uint4(x, lx, a.g.deg[x], local);
+        *reinterpret_cast<uint4*>(a.g.pool + ly + p) = back;
     });
 }
 
@@ -499,7 +543,7 @@ __global__ void k_compact_copy(CSRView g, const uint32_t* __restrict__ noff, uin
         const uint32_t local = item - noff[x];
         if (local >= g.deg[x]) continue;
         Ent e = g.pool[g.off[x] + local];
-        e.noff = noff[e.nbr];
+        if (e.noff != HUBREF) e.noff = noff[e.nbr];
         np[item] = e;
     }
 }

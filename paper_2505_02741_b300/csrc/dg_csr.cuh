@@ -23,6 +23,8 @@ struct CSR {
     float slack = 1.25f;
     double overflow = 0.5;
     DBuf<uint32_t> off, deg, cap;
+    DBuf<uint8_t> hub;
+    DBuf<uint32_t> nhub;
     DBuf<Ent> pool;
     DBuf<unsigned long long> top;
     uint64_t host_top = 0;  // last value read back
@@ -32,13 +34,17 @@ struct CSR {
         v.off = off.p;
         v.deg = deg.p;
         v.cap = cap.p;
+        v.hub = hub.p;
+        v.nhub = nhub.p;
         v.pool = pool.p;
         v.top = top.p;
         v.pool_cap = pool_cap;
         v.n = n;
         return v;
     }
-    uint64_t bytes() const { return off.bytes() + deg.bytes() + cap.bytes() + pool.bytes() + top.bytes(); }
+    uint64_t bytes() const {
+        return off.bytes() + deg.bytes() + cap.bytes() + hub.bytes() + nhub.bytes() + pool.bytes() + top.bytes();
+    }
 };
 
 // sorted, unique half-edge changes: keys[c] = x * n + y ascending; vals[c]

@@ -101,24 +101,18 @@ __global__ void __launch_bounds__(256) k_na_walk(NaArgs a) {
         const CSRView& g = ins ? a.H : a.G;
         const uint32_t ulo = (uint32_t)q.id, uhi = (uint32_t)(q.id >> 32);
         uint32_t c = (uint32_t)q.u, off = g.off[c], deg = g.deg[c], prev = NA_NONE, steps = 0, reason = 0;
+        bool pid = false;
         double R = 0.0;
         for (;;) {
             const uint32_t neff = deg - (prev != NA_NONE ? 1u : 0u);
             if (neff == 0) { reason = 4; break; }
             if (ins && a.early_exit && __ldcg(&a.kstar[j]) <= steps) { reason = 5; break; }
             const uint32_t x = philox_word0(steps, k, ulo, uhi, a.key0, a.key1);
-            const uint32_t jj = __umulhi(x, neff);
-            const uint32_t idx = jj + (jj >= prev ? 1u : 0u);
-            if ((uint64_t)off + idx >= g.pool_cap) { reason = 4; break; }
             uint4 h;
             double2 tl;
-            load_ent(g.pool + off + idx, h, tl);
+            if (nb_step(g, x, c, off, deg, prev, pid, h, tl) <= 0) { reason = 4; break; }
             R = __dadd_rn(R, tl.x);
             steps += 1;
-            c = h.x;
-            off = h.y;
-            deg = h.z;
-            prev = h.w;
             if (c == (uint32_t)q.v && (!ins || __dmul_rn(q.w, R) <= a.K)) {
                 if (ins && a.early_exit) atomicMin(&a.kstar[j], steps);
                 reason = 1;

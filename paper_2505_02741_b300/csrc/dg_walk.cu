@@ -36,8 +36,6 @@ constexpr uint32_t NONE = 0xFFFFFFFFu;
 __device__ __forceinline__ bool walk_aborted(const uint32_t* d_err) { return (*d_err & ABORT_MASK) != 0u; }
 
 struct Walker {
-    const Ent* pool;
-    uint32_t pcap;   // entries in that pool (bounds guard)
     uint32_t wid;    // absolute walker index j*s + k
     uint32_t j, k;
     uint32_t q;      // target
@@ -47,6 +45,7 @@ struct Walker {
     double R, wpq;
     bool ins;
     bool active;
+    bool pid;  // prev holds the previous vertex's id (arrived at a hub)
 };
 
 struct WalkKernelArgs {
@@ -60,13 +59,6 @@ struct WalkKernelArgs {
     uint32_t* d_err;
 };
 
-// a cached (off, deg) that points outside the pool or a neighbour id >= n can
-// only come from a broken mutation; the walker stops and the batch reports it
-__device__ __forceinline__ bool step_in_bounds(const Walker& w, uint32_t idx, const WalkKernelArgs& a) {
-    if ((uint64_t)w.off + idx < w.pcap) return true;
-    atomicOr(a.d_err, (uint32_t)ERR_INTERNAL);
-    return false;
-}
 
 __device__ __forceinline__ void walker_start(Walker& w, const WalkKernelArgs& a, uint32_t wid, uint64_t id0) {
     w.wid = wid;
@@ -80,12 +72,11 @@ __device__ __forceinline__ void walker_start(Walker& w, const WalkKernelArgs& a,
     w.ulo = (uint32_t)id;
     w.uhi = (uint32_t)(id >> 32);
     const CSRView& g = w.ins ? a.H : a.G;
-    w.pool = g.pool;
-    w.pcap = (uint32_t)g.pool_cap;
     w.off = g.off[u];
     w.deg = g.deg[u];
     w.c = u;
     w.prev = NONE;
+    w.pid = false;
     w.steps = 0;
     w.R = 0.0;
     w.active = true;
@@ -98,14 +89,11 @@ __device__ __forceinline__ void walker_finish(Walker& w, const WalkKernelArgs& a
     w.active = false;
 }
 
-// consume one loaded entry: advance and test the stop rules
-__device__ __forceinline__ void walker_advance(Walker& w, const WalkKernelArgs& a, const uint4& h, double r) {
+// after nb_step moved the walker along an edge of resistance r: accumulate and
+// test the stop rules
+__device__ __forceinline__ void walker_advance(Walker& w, const WalkKernelArgs& a, double r) {
     w.R = __dadd_rn(w.R, r);
     w.steps += 1;
-    w.c = h.x;
-    w.off = h.y;
-    w.deg = h.z;
-    w.prev = h.w;
     if (a.r.paths) a.r.paths[(size_t)w.wid * (a.p.T + 1) + w.steps] = (int32_t)w.c;
     if (w.c == w.q) {
         if (!w.ins || __dmul_rn(w.wpq, w.R) <= a.p.K) {
@@ -131,6 +119,7 @@ struct Lean {
     uint32_t ulo, uhi;  // update id (Philox counter words 2, 3)
     uint32_t x;         // random word of the next step
     bool ins, active;
+    bool pid;           // prev holds the previous vertex's id (we arrived at a hub)
     double R, wpq;
 };
 
@@ -149,6 +138,7 @@ __device__ __forceinline__ void lean_start(Lean& w, const WalkKernelArgs& a, uin
     w.deg = g.deg[u];
     w.c = u;
     w.prev = NONE;
+    w.pid = false;
     w.steps = 0;
     w.R = 0.0;
     w.active = true;
@@ -163,9 +153,47 @@ __device__ __forceinline__ void lean_finish(Lean& w, const WalkKernelArgs& a, ui
     w.active = false;
 }
 
-template <int ILP>
-__global__ void __launch_bounds__(256) k_walk_batched(WalkKernelArgs a) {
+// The step when the walker stands on a hub (previous vertex known by id only:
+// L[jj] was loaded at slot `at`; take L[jj+1] instead when L[jj] is at or past
+// the previous vertex) or the chosen entry leads to a hub (HUBREF: the list
+// comes from the vertex arrays).  Advances the walker; false on a bad offset.
+__device__ __forceinline__ bool lean_hub_step(Lean& v, const WalkKernelArgs& a, uint4& h, double2& tl, uint32_t at) {
+    const CSRView& g = v.ins ? a.H : a.G;
+    if (v.pid && h.x >= v.prev) {
+        if ((uint64_t)at + 1 >= g.pool_cap) {
+            atomicOr(a.d_err, (uint32_t)ERR_INTERNAL);
+            return false;
+        }
+        load_ent(g.pool + at + 1, h, tl);
+    }
+    v.R = __dadd_rn(v.R, tl.x);
+    v.steps += 1;
+    const uint32_t from = v.c;
+    v.c = h.x;
+    if (h.y == HUBREF) {
+        v.off = g.off[v.c];
+        v.deg = g.deg[v.c];
+        v.prev = from;
+        v.pid = true;
+    } else {
+        v.off = h.y;
+        v.deg = h.z;
+        v.prev = h.w;
+        v.pid = false;
+    }
+    return true;
+}
+
+// Up to 256 threads per block, at least 4 blocks of 256 per SM (64 registers
+// per thread) for two walkers per thread.  HUBS selects the variant that
+// handles hub references; both variants are launched and the one that does
+// not match the device-side hub counts of G and H returns at once, so graphs
+// without hubs (meshes) run a loop with no hub branch and no host round trip
+// is needed to choose.
+template <int ILP, bool HUBS>
+__global__ void __launch_bounds__(256, (ILP == 2 ? 4 : 1)) k_walk_batched(WalkKernelArgs a) {
     if (walk_aborted(a.d_err)) return;
+    if (((*a.H.nhub | *a.G.nhub) != 0u) != HUBS) return;
     const uint32_t W = min(*a.t.count, a.j_hi);
     if (W <= a.j_lo) return;
     const uint32_t total = (W - a.j_lo) * a.p.s;
@@ -203,7 +231,7 @@ __global__ void __launch_bounds__(256) k_walk_batched(WalkKernelArgs a) {
         // step's Philox word while the loads are in flight
         uint4 h[ILP];
         double2 tl[ILP];
-        uint32_t ks[ILP];
+        uint32_t ks[ILP], at[ILP];
         bool go[ILP];
 #pragma unroll
         for (int i = 0; i < ILP; ++i) {
@@ -212,11 +240,16 @@ __global__ void __launch_bounds__(256) k_walk_batched(WalkKernelArgs a) {
             if (!w[i].active) continue;
             const uint32_t neff = w[i].deg - (w[i].prev != NONE ? 1u : 0u);
             if (neff == 0) {
+                // a hub reference seen by the hub-free variant would end here (its
+                // cached degree is 1): report it instead of stopping silently
+                if (!HUBS && w[i].off == HUBREF) atomicOr(a.d_err, (uint32_t)ERR_INTERNAL);
                 lean_finish(w[i], a, R_LEAF);
                 continue;
             }
             const uint32_t jj = __umulhi(w[i].x, neff);
-            const uint32_t idx = jj + (jj >= w[i].prev ? 1u : 0u);
+            // slot of the previous vertex known: skip it by position; after a hub
+            // arrival only its id is known: load L[jj] and step past it if needed
+            const uint32_t idx = (HUBS && w[i].pid) ? jj : jj + (jj >= w[i].prev ? 1u : 0u);
             const Ent* pool = w[i].ins ? a.H.pool : a.G.pool;
             const uint64_t pcap = w[i].ins ? a.H.pool_cap : a.G.pool_cap;
             if ((uint64_t)w[i].off + idx >= pcap) {  // only a broken mutation could get here
@@ -224,7 +257,8 @@ __global__ void __launch_bounds__(256) k_walk_batched(WalkKernelArgs a) {
                 lean_finish(w[i], a, R_LEAF);
                 continue;
             }
-            load_ent(pool + w[i].off + idx, h[i], tl[i]);
+            at[i] = w[i].off + idx;
+            load_ent(pool + at[i], h[i], tl[i]);
             if (w[i].ins && a.p.early_exit) ks[i] = __ldcg(&a.t.kstar[w[i].j]);
             go[i] = true;
         }
@@ -240,12 +274,19 @@ __global__ void __launch_bounds__(256) k_walk_batched(WalkKernelArgs a) {
                 lean_finish(v, a, R_CUT);
                 continue;
             }
-            v.R = __dadd_rn(v.R, tl[i].x);
-            v.steps += 1;
-            v.c = h[i].x;
-            v.off = h[i].y;
-            v.deg = h[i].z;
-            v.prev = h[i].w;
+            if (HUBS && (v.pid || h[i].y == HUBREF)) {  // leaving or entering a hub
+                if (!lean_hub_step(v, a, h[i], tl[i], at[i])) {
+                    lean_finish(v, a, R_LEAF);
+                    continue;
+                }
+            } else {
+                v.R = __dadd_rn(v.R, tl[i].x);
+                v.steps += 1;
+                v.c = h[i].x;
+                v.off = h[i].y;
+                v.deg = h[i].z;
+                v.prev = h[i].w;
+            }
             if (a.r.paths) a.r.paths[((size_t)v.j * a.p.s + v.k) * (a.p.T + 1) + v.steps] = (int32_t)v.c;
             if (v.c == v.q && (!v.ins || __dmul_rn(v.wpq, v.R) <= a.p.K)) {
                 if (v.ins && a.p.early_exit) atomicMin(&a.t.kstar[v.j], v.steps);
@@ -280,17 +321,15 @@ __global__ void k_walk_one(WalkKernelArgs a, uint32_t j) {
                 break;
             }
             const uint32_t x = philox_word0(w.steps, w.k, w.ulo, w.uhi, a.p.key0, a.p.key1);
-            const uint32_t jj = __umulhi(x, neff);
-            const uint32_t idx = jj + (jj >= w.prev ? 1u : 0u);
-            if (!step_in_bounds(w, idx, a)) {
+            uint4 h;
+            double2 tl;
+            if (nb_step(w.ins ? a.H : a.G, x, w.c, w.off, w.deg, w.prev, w.pid, h, tl) <= 0) {
+                atomicOr(a.d_err, (uint32_t)ERR_INTERNAL);  // n_eff > 0 here: only a bad offset stops it
                 walker_finish(w, a, R_LEAF);
                 break;
             }
-            uint4 h;
-            double2 tl;
-            load_ent(w.pool + w.off + idx, h, tl);
             const uint32_t before = w.steps;
-            walker_advance(w, a, h, tl.x);
+            walker_advance(w, a, tl.x);
             if (!w.active && w.ins && a.p.early_exit && (a.r.meta[w.wid] >> 16) == R_HIT)
                 atomicMin(&ks, before + 1);
         }
@@ -325,17 +364,17 @@ void walk_set_l2_persist(size_t persist_bytes, size_t max_window) {
     g_max_window = max_window;
 }
 
-template <int ILP>
+template <int ILP, bool HUBS>
 static void launch_ilp(const WalkKernelArgs& a, const WalkShape& shape, cudaStream_t st) {
     int bps = shape.blocks_per_sm;
     if (bps <= 0) {
         int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_walk_batched<ILP>, shape.block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_walk_batched<ILP, HUBS>, shape.block, 0);
         bps = occ > 0 ? occ : 1;
     }
     const int grid = device_sms() * bps;
     if (g_persist_bytes == 0 || a.H.pool == nullptr) {
-        k_walk_batched<ILP><<<grid, shape.block, 0, st>>>(a);
+        k_walk_batched<ILP, HUBS><<<grid, shape.block, 0, st>>>(a);
         return;
     }
     size_t win = (size_t)a.H.pool_cap * sizeof(Ent);
@@ -354,7 +393,13 @@ static void launch_ilp(const WalkKernelArgs& a, const WalkShape& shape, cudaStre
     attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    DG_CUDA(cudaLaunchKernelEx(&cfg, k_walk_batched<ILP>, a));
+    DG_CUDA(cudaLaunchKernelEx(&cfg, k_walk_batched<ILP, HUBS>, a));
+}
+
+template <int ILP>
+static void launch_both(const WalkKernelArgs& a, const WalkShape& shape, cudaStream_t st) {
+    launch_ilp<ILP, false>(a, shape, st);
+    launch_ilp<ILP, true>(a, shape, st);
 }
 
 void launch_walk_batched(const CSRView& H, const CSRView& G, const WalkTasks& t, const WalkParams& p,
@@ -364,11 +409,11 @@ void launch_walk_batched(const CSRView& H, const CSRView& G, const WalkTasks& t,
     WalkKernelArgs a = make_args(H, G, t, p, r, d_hdr, d_next, j_lo, j_hi, d_err);
     DG_CUDA(cudaMemsetAsync(d_next, 0, sizeof(unsigned long long), st));
     switch (shape.ilp) {
-        case 1: launch_ilp<1>(a, shape, st); break;
-        case 4: launch_ilp<4>(a, shape, st); break;
-        default: launch_ilp<2>(a, shape, st); break;
+        case 1: launch_both<1>(a, shape, st); break;
+        case 4: launch_both<4>(a, shape, st); break;
+        default: launch_both<2>(a, shape, st); break;
     }
-    ++g_launches;
+    g_launches += 2;
     DG_CHECK_LAUNCH();
 }
 
@@ -513,21 +558,15 @@ __global__ void k_replay(CSRView H, CSRView G, WalkTasks t, WalkParams p, WalkRe
             uint32_t* path = pb.v + (size_t)j * (p.T + 1);
             double* pw = pb.w + (size_t)j * p.T;
             uint32_t cv = u, off = G.off[u], deg = G.deg[u], prev = NONE, s = 0;
+            bool pid = false;
             path[0] = u;
             for (; s < steps; ++s) {
-                const uint32_t neff = deg - (prev != NONE ? 1u : 0u);
                 const uint32_t x = philox_word0(s, (uint32_t)b, ulo, uhi, p.key0, p.key1);
-                const uint32_t jj = __umulhi(x, neff);
-                const uint32_t idx = jj + (jj >= prev ? 1u : 0u);
-                if (neff == 0 || (uint64_t)off + idx >= G.pool_cap) break;
-                const Ent e = G.pool[off + idx];
-                if (e.nbr >= n) break;
-                path[s + 1] = e.nbr;
-                pw[s] = e.w;
-                cv = e.nbr;
-                off = e.noff;
-                deg = e.ndeg;
-                prev = e.rev;
+                uint4 h;
+                double2 tl;
+                if (nb_step(G, x, cv, off, deg, prev, pid, h, tl) <= 0 || cv >= n) break;
+                path[s + 1] = cv;
+                pw[s] = tl.y;
             }
             if (s != steps || cv != v) {  // a recorded hit must replay to v
                 atomicOr(d_err, (uint32_t)ERR_INTERNAL);

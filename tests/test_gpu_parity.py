@@ -238,6 +238,68 @@ def test_invariants_subgraph_and_components():
     ctx.close()
 
 
+def test_hub_references_and_status_flips():
+    """Vertices of degree >= 1024 are referenced without cached list data (a
+    layout choice of the CUDA path).  Walks through such hubs, changes of their
+    lists, and hubs crossing the thresholds (down through 768, back up through
+    1024) must leave every result, H and G equal to the oracle."""
+    rng = np.random.default_rng(21)
+    n = 4000
+    edges = set()
+    for hub, d in ((0, 1100), (1, 1030), (2, 900)):
+        for y in rng.choice(np.arange(3, n), d, replace=False):
+            edges.add((hub, int(y)))
+    perm = rng.permutation(n)
+    for i in range(1, n):  # a random spanning tree keeps the graph connected
+        x, y = int(perm[i]), int(perm[rng.integers(0, i)])
+        edges.add((min(x, y), max(x, y)))
+    while len(edges) < 9000:
+        x, y = (int(t) for t in rng.integers(3, n, 2))
+        if x != y:
+            edges.add((min(x, y), max(x, y)))
+    e = sorted(edges)
+    a = np.array([p for p, _ in e], np.int32)
+    b = np.array([q for _, q in e], np.int32)
+    w = rng.uniform(0.5, 5.0, len(e))
+    h = W.init_sparsifier(n, a, b, w, rng)
+    ctx, g, o = pair(n, a, b, w, h, T=60, s=16, K=40.0, ctx_kw=dict(record_walkers=True))
+    cur = set(edges)
+
+    def nbrs(x):
+        return sorted(y for (p, q) in cur for y in ((q,) if p == x else (p,) if q == x else ()))
+
+    def batch(dels, ins, extra=150):
+        us, vs, ws, ops = [], [], [], []
+        for x, y in dels:
+            us.append(x); vs.append(y); ws.append(0.0); ops.append(1)
+            cur.discard((min(x, y), max(x, y)))
+        for x, y in ins:
+            us.append(x); vs.append(y); ws.append(float(rng.uniform(0.5, 5.0))); ops.append(0)
+            cur.add((min(x, y), max(x, y)))
+        for _ in range(extra):  # random insertions elsewhere, walks start at random vertices
+            x, y = (int(t) for t in rng.integers(3, n, 2))
+            if x != y and (min(x, y), max(x, y)) not in cur:
+                us.append(x); vs.append(y); ws.append(float(rng.uniform(0.5, 5.0))); ops.append(0)
+                cur.add((min(x, y), max(x, y)))
+        order = rng.permutation(len(us))
+        return ([us[i] for i in order], [vs[i] for i in order], [ws[i] for i in order], [ops[i] for i in order])
+
+    def new_nbrs(x, k):
+        have = set(nbrs(x))
+        cand = [y for y in range(3, n) if y != x and y not in have]
+        return [(x, int(y)) for y in rng.choice(cand, k, replace=False)]
+
+    plans = [
+        (lambda: [(0, y) for y in nbrs(0)[:300]], lambda: new_nbrs(2, 150)),  # hub 0 to 800 (stays), 2 to 1050 (joins)
+        (lambda: [(0, y) for y in nbrs(0)[:100]], lambda: new_nbrs(1, 20)),   # hub 0 to 700 (leaves)
+        (lambda: [(1, y) for y in nbrs(1)[:10]], lambda: new_nbrs(0, 400)),   # hub 0 back to 1100 (joins again)
+    ]
+    for bi, (dl, il) in enumerate(plans):
+        u, v, ww, op = batch(dl(), il())
+        step_both(g, o, u, v, ww, op, where=f"hub batch {bi}")
+    ctx.close()
+
+
 def test_mesh3d_small_multi_batch():
     wl, st = W.make_mesh3d(24, 24, 24)
     ctx, g, o = pair(wl.n, wl.a, wl.b, wl.w, wl.h_ids)

@@ -91,6 +91,13 @@ typedef struct {
     int32_t ins_early_exit; /* 1: an insertion's walkers stop at the first step index at which
                                any of them reaches v (decisions unchanged; R~ and step counts
                                refer to the truncated walks); 0: every walker runs to its own stop */
+    int32_t del_prune;      /* 1: a deletion's walker stops once its resistance exceeds that of a
+                               walker of the same update that already reached v: it can no longer
+                               give the minimum of Eq. 12, so hit, best_walker, r_est and the
+                               recovered edges are unchanged; nhits then counts the walkers at the
+                               minimum resistance and steps the steps actually taken (which depend
+                               on scheduling, between the exact pruned and unpruned counts);
+                               0: every deletion walker runs to its own stop */
     int32_t walk_mode;      /* DG_WALK_BATCHED or DG_WALK_PER_UPDATE */
     double slack;           /* per-vertex capacity = deg + max(2, ceil(deg*(slack-1))); >= 1 */
     double overflow_frac;   /* pool headroom for relocated lists, fraction of the initial pool */
@@ -121,10 +128,11 @@ typedef struct {
     uint8_t hit;         /* some walker reached v (within K for insertions) */
     uint8_t accepted;    /* insertion kept for H (no walker reached v); committed if the edge is in G_b */
     uint8_t fallback;    /* deletion walked but no walker reached v: local fallback edges recovered */
-    int32_t nhits;       /* walkers that reached v (after the early-exit cut for insertions) */
+    int32_t nhits;       /* walkers that reached v (after the early-exit cut for insertions; with
+                            del_prune, for deletions: walkers at the minimum resistance) */
     int32_t best_walker; /* walker index of R~ (lowest index among equal resistances), -1 if none */
     int32_t nrecovered;  /* distinct edges this deletion returned to H (path or fallback) */
-    int32_t steps;       /* walk steps taken by this update's walkers (after the cut) */
+    int32_t steps;       /* walk steps taken by this update's walkers (after the cut / pruning) */
     double r_est;        /* R~ = minimum path resistance over hitting walkers (Eq. 12); +inf if none */
 } dg_update_result;
 

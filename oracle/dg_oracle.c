@@ -345,10 +345,12 @@ int orc_init_sparsifier(orc_state *st, int64_t mh, const int32_t *u, const int32
 /* ------------------------------------------------------------------------ */
 /* Walks from p toward q on g.  Returns the stop reason; *steps_out = steps
  * taken, *R_out = accumulated resistance.  path (nullable, room for T+1
- * entries) receives the visited vertices, path[0] = p. */
+ * entries) receives the visited vertices, path[0] = p.  rcut: a deletion
+ * walker whose resistance exceeds rcut stops there (STOP_CUT, tested before
+ * the hit test); +inf walks the plain Algorithm 1 deletion branch. */
 static int walk_one(const orc_graph *g, int32_t p, int32_t q, double wpq, int deletion, double K,
-                    int32_t T, uint64_t seed, uint64_t upd_id, uint32_t walker, int32_t *steps_out,
-                    double *R_out, int32_t *path)
+                    int32_t T, uint64_t seed, uint64_t upd_id, uint32_t walker, double rcut,
+                    int32_t *steps_out, double *R_out, int32_t *path)
 {
     int32_t c = p;     /* current vertex */
     int32_t prev = -1; /* previous vertex, none at the start */
@@ -382,6 +384,10 @@ static int walk_one(const orc_graph *g, int32_t p, int32_t q, double wpq, int de
         prev = c;
         c = L[pick].nbr;
         if (path) path[steps] = c;
+        if (deletion && R > rcut) {
+            reason = STOP_CUT;
+            break;
+        }
         if (c == q && (deletion || wpq * R <= K)) {
             reason = STOP_HIT;
             break;
@@ -406,8 +412,8 @@ int orc_walk(const orc_state *st, int use_h, int32_t p, int32_t q, double wpq, i
 {
     const orc_graph *g = use_h ? &st->H : &st->G;
     if (p < 0 || p >= g->n || q < 0 || q >= g->n) return -1;
-    return walk_one(g, p, q, wpq, deletion, st->K, st->T, st->seed, upd_id, walker, steps_out, R_out,
-                    path);
+    return walk_one(g, p, q, wpq, deletion, st->K, st->T, st->seed, upd_id, walker, INFINITY, steps_out,
+                    R_out, path);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -451,13 +457,20 @@ typedef struct {
  * walk_mask (nullable): when given, only updates with a non-zero entry run
  * their walks (a sampling mode for very large batches: statuses and G are
  * complete, walk results and commits only for the sampled updates).
+ * nhits_min, steps_lo (nullable, arrays of nu): for a walked deletion with a
+ * hit, the number of walkers whose hit resistance equals R~, and the steps
+ * the s walkers take when each stops at its first step whose resistance
+ * exceeds R~ (a walker there can no longer give the minimum of Eq. 12);
+ * otherwise nhits and steps.  These are the deletion-pruning counterparts of
+ * nhits and steps: the minimum walker, R~ and the recovered edges are the
+ * same with or without pruning.
  * Returns 0, or -2 on allocation failure.
  */
 int orc_apply_batch(orc_state *st, int64_t nu, const int32_t *u, const int32_t *v, const double *w,
                     const int32_t *op, int32_t *status, uint8_t *walked, uint8_t *hit,
                     uint8_t *accepted, uint8_t *fallback, int32_t *nhits, int32_t *best,
                     int32_t *nrec, int32_t *steps, double *rest, orc_walker_out *wout,
-                    int32_t *paths, const uint8_t *walk_mask)
+                    int32_t *paths, const uint8_t *walk_mask, int32_t *nhits_min, int32_t *steps_lo)
 {
     orc_graph *G = &st->G, *H = &st->H;
     const int32_t n = G->n, s = st->s, T = st->T;
@@ -543,7 +556,7 @@ int orc_apply_batch(orc_state *st, int64_t nu, const int32_t *u, const int32_t *
         int32_t first_hit = -1; /* smallest step at which some walker hit */
         for (int32_t k = 0; k < s; k++) {
             wreason[k] = walk_one(g, u[i], v[i], wpq, deletion, st->K, T, st->seed, upd_id,
-                                  (uint32_t)k, &wsteps[k], &wR[k],
+                                  (uint32_t)k, INFINITY, &wsteps[k], &wR[k],
                                   paths ? paths + ((size_t)i * s + k) * (size_t)(T + 1) : NULL);
             if (paths) /* pad the unused tail of the path with -1 */
                 for (int32_t t = wsteps[k] + 1; t <= T; t++)
@@ -579,6 +592,27 @@ int orc_apply_batch(orc_state *st, int64_t nu, const int32_t *u, const int32_t *
         steps[i] = tot;
         rest[i] = Rmin;
         hit[i] = (uint8_t)(nh > 0);
+        if (nhits_min) {
+            nhits_min[i] = nh;
+            steps_lo[i] = tot;
+            if (deletion && nh > 0) {
+                int32_t nmin = 0, lo = 0;
+                for (int32_t k = 0; k < s; k++) {
+                    if (wreason[k] == STOP_HIT && wR[k] == Rmin) {
+                        nmin++;
+                        lo += wsteps[k];
+                    } else {
+                        int32_t sk = 0;
+                        double Rk = 0.0;
+                        walk_one(g, u[i], v[i], 0.0, 1, st->K, T, st->seed, upd_id, (uint32_t)k, Rmin,
+                                 &sk, &Rk, NULL);
+                        lo += sk;
+                    }
+                }
+                nhits_min[i] = nmin;
+                steps_lo[i] = lo;
+            }
+        }
         if (paths && !deletion && st->early_exit && first_hit >= 0)
             for (int32_t k = 0; k < s; k++)
                 for (int32_t t = wsteps[k] + 1; t <= T; t++)
@@ -607,7 +641,7 @@ int orc_apply_batch(orc_state *st, int64_t nu, const int32_t *u, const int32_t *
             /* re-run the argmin walker to get its walk (same counters -> same path) */
             int32_t ts;
             double tR;
-            walk_one(g, u[i], v[i], 0.0, 1, st->K, T, st->seed, upd_id, (uint32_t)bw, &ts, &tR,
+            walk_one(g, u[i], v[i], 0.0, 1, st->K, T, st->seed, upd_id, (uint32_t)bw, INFINITY, &ts, &tR,
                      best_path);
             /* R10: distinct edges of the walk that are not in H' */
             for (int32_t t = 0; t < ts; t++) {

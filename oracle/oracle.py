@@ -60,7 +60,7 @@ def lib():
                                C.c_uint32, C.POINTER(C.c_int32), C.POINTER(C.c_double), P]
         L.orc_walk.restype = C.c_int
         L.orc_apply_batch.argtypes = [P, C.c_int64, i32p, i32p, f64p, i32p, i32p, u8p, u8p, u8p, u8p,
-                                      i32p, i32p, i32p, i32p, f64p, P, P, P]
+                                      i32p, i32p, i32p, i32p, f64p, P, P, P, P, P]
         L.orc_apply_batch.restype = C.c_int
         L.orc_query.argtypes = [P, C.c_int, C.c_int64, i32p, i32p, f64p]
         L.orc_query.restype = C.c_int64
@@ -129,11 +129,14 @@ class OracleGraph:
             raise ValueError("vertex out of range")
         return reason, steps.value, R.value, path[: steps.value + 1].copy()
 
-    def apply(self, u, v, w, op, *, walkers=False, paths=False, walk_mask=None):
+    def apply(self, u, v, w, op, *, walkers=False, paths=False, walk_mask=None, prune_bounds=False):
         """Apply one batch; returns a dict of per-update arrays (and walker records).
 
         walk_mask (optional bool array): walk only the marked updates (sampling
-        mode for very large batches; H then lacks the unsampled commits)."""
+        mode for very large batches; H then lacks the unsampled commits).
+        prune_bounds: also return nhits_min and steps_lo, the values nhits and
+        steps take for a walked deletion whose walkers stop once their
+        resistance exceeds R~ (equal to nhits and steps elsewhere)."""
         mask = None if walk_mask is None else np.ascontiguousarray(walk_mask, np.uint8)
         nu = len(u)
         u = np.ascontiguousarray(u, np.int32)
@@ -145,6 +148,9 @@ class OracleGraph:
                    fallback=np.zeros(nu, np.uint8), nhits=np.zeros(nu, np.int32),
                    best_walker=np.zeros(nu, np.int32), nrecovered=np.zeros(nu, np.int32),
                    steps=np.zeros(nu, np.int32), r_est=np.zeros(nu, np.float64))
+        if prune_bounds:
+            out["nhits_min"] = np.zeros(nu, np.int32)
+            out["steps_lo"] = np.zeros(nu, np.int32)
         wout = np.zeros(nu * self.s, WALKER_DTYPE) if walkers else None
         pbuf = np.full(nu * self.s * (self.T + 1), -1, np.int32) if paths else None
         rc = lib().orc_apply_batch(self._h, nu, u, v, w, op, out["status"], out["walked"], out["hit"],
@@ -152,7 +158,9 @@ class OracleGraph:
                                    out["nrecovered"], out["steps"], out["r_est"],
                                    None if wout is None else wout.ctypes.data,
                                    None if pbuf is None else pbuf.ctypes.data,
-                                   None if mask is None else mask.ctypes.data)
+                                   None if mask is None else mask.ctypes.data,
+                                   out["nhits_min"].ctypes.data if prune_bounds else None,
+                                   out["steps_lo"].ctypes.data if prune_bounds else None)
         if rc != 0:
             raise MemoryError("oracle batch failed")
         if walkers:

@@ -162,6 +162,7 @@ void dg_config_default(dg_config* cfg) {
     cfg->T = 100;
     cfg->s = 32;
     cfg->ins_early_exit = 1;
+    cfg->del_prune = 1;
     cfg->walk_mode = DG_WALK_BATCHED;
     cfg->slack = 1.25;
     cfg->overflow_frac = 0.5;
@@ -231,6 +232,7 @@ dg_status dg_create(const dg_config* cfg_in, dg_ctx** out) {
         c->cfg.T = cfg.T;
         c->cfg.s = cfg.s;
         c->cfg.early_exit = cfg.ins_early_exit ? 1 : 0;
+        c->cfg.del_prune = cfg.del_prune ? 1 : 0;
         c->cfg.walk_mode = cfg.walk_mode;
         c->cfg.slack = cfg.slack;
         c->cfg.overflow = cfg.overflow_frac;

@@ -703,6 +703,7 @@ static WalkParams params_of(const Config& cfg) {
     p.T = (uint32_t)cfg.T;
     p.s = (uint32_t)cfg.s;
     p.early_exit = cfg.early_exit ? 1u : 0u;
+    p.del_prune = cfg.del_prune ? 1u : 0u;
     p.key0 = (uint32_t)cfg.seed;
     p.key1 = (uint32_t)(cfg.seed >> 32);
     return p;

@@ -16,6 +16,7 @@ struct Config {
     int32_t T = 100;
     int32_t s = 32;
     int32_t early_exit = 1;
+    int32_t del_prune = 1;
     int32_t walk_mode = DG_WALK_BATCHED;
     double slack = 1.25;
     double overflow = 0.5;

@@ -11,6 +11,13 @@
 //   R    += r(c, L[idx]); step += 1
 //   stop on: reaching v with (deletion or w_pq*R <= K) -> hit;
 //            insertion and w_pq*R > K;  step == T.
+// Optional cuts that leave every decision unchanged: an insertion's walkers
+// stop at the first step index at which one of them hit (early exit); a
+// deletion's walker stops once R exceeds the resistance of a hit already
+// found for its update (pruning: it can no longer give the minimum of Eq. 12).
+// Pruning compares the high 32 bits of the FP64 patterns (non-negative
+// doubles order like their bit patterns), so a walker is cut only when its R
+// is certainly above that hit's R; the walker at the minimum is never cut.
 // The entry read at idx carries the next list's offset/degree and pos(prev)
 // for the next step, so each step is one dependent 32-byte load.
 #include <cmath>
@@ -34,6 +41,9 @@ int device_sms() {
 constexpr uint32_t NONE = 0xFFFFFFFFu;
 
 __device__ __forceinline__ bool walk_aborted(const uint32_t* d_err) { return (*d_err & ABORT_MASK) != 0u; }
+
+// high 32 bits of a non-negative double (the pruning key)
+__device__ __forceinline__ uint32_t r_key(double R) { return (uint32_t)((unsigned long long)__double_as_longlong(R) >> 32); }
 
 struct Walker {
     uint32_t wid;    // absolute walker index j*s + k
@@ -95,9 +105,14 @@ __device__ __forceinline__ void walker_advance(Walker& w, const WalkKernelArgs& 
     w.R = __dadd_rn(w.R, r);
     w.steps += 1;
     if (a.r.paths) a.r.paths[(size_t)w.wid * (a.p.T + 1) + w.steps] = (int32_t)w.c;
+    if (!w.ins && a.p.del_prune && r_key(w.R) > __ldcg(&a.t.kstar[w.j])) {
+        walker_finish(w, a, R_CUT);
+        return;
+    }
     if (w.c == w.q) {
         if (!w.ins || __dmul_rn(w.wpq, w.R) <= a.p.K) {
             if (w.ins && a.p.early_exit) atomicMin(&a.t.kstar[w.j], w.steps);
+            if (!w.ins && a.p.del_prune) atomicMin(&a.t.kstar[w.j], r_key(w.R));
             walker_finish(w, a, R_HIT);
             return;
         }
@@ -259,7 +274,7 @@ __global__ void __launch_bounds__(256, (ILP == 2 ? 4 : 1)) k_walk_batched(WalkKe
             }
             at[i] = w[i].off + idx;
             load_ent(pool + at[i], h[i], tl[i]);
-            if (w[i].ins && a.p.early_exit) ks[i] = __ldcg(&a.t.kstar[w[i].j]);
+            if (w[i].ins ? a.p.early_exit : a.p.del_prune) ks[i] = __ldcg(&a.t.kstar[w[i].j]);
             go[i] = true;
         }
 #pragma unroll
@@ -270,7 +285,7 @@ __global__ void __launch_bounds__(256, (ILP == 2 ? 4 : 1)) k_walk_batched(WalkKe
         for (int i = 0; i < ILP; ++i) {
             if (!go[i]) continue;
             Lean& v = w[i];
-            if (ks[i] <= v.steps) {  // a walker of this update hit at a step <= ours: cut
+            if (v.ins && ks[i] <= v.steps) {  // a walker of this update hit at a step <= ours: cut
                 lean_finish(v, a, R_CUT);
                 continue;
             }
@@ -288,8 +303,11 @@ __global__ void __launch_bounds__(256, (ILP == 2 ? 4 : 1)) k_walk_batched(WalkKe
                 v.prev = h[i].w;
             }
             if (a.r.paths) a.r.paths[((size_t)v.j * a.p.s + v.k) * (a.p.T + 1) + v.steps] = (int32_t)v.c;
-            if (v.c == v.q && (!v.ins || __dmul_rn(v.wpq, v.R) <= a.p.K)) {
-                if (v.ins && a.p.early_exit) atomicMin(&a.t.kstar[v.j], v.steps);
+            if (!v.ins && r_key(v.R) > ks[i]) {  // above a hit of this deletion: cannot be the minimum
+                lean_finish(v, a, R_CUT);
+            } else if (v.c == v.q && (!v.ins || __dmul_rn(v.wpq, v.R) <= a.p.K)) {
+                if (v.ins ? a.p.early_exit : a.p.del_prune)
+                    atomicMin(&a.t.kstar[v.j], v.ins ? v.steps : r_key(v.R));
                 lean_finish(v, a, R_HIT);
             } else if (v.ins && __dmul_rn(v.wpq, v.R) > a.p.K) {
                 lean_finish(v, a, R_OVER_K);
@@ -449,7 +467,7 @@ __global__ void k_walk_reduce(WalkTasks t, WalkParams p, WalkRecs r, dg_update_r
             if ((m >> 16) == R_HIT) ks = min(ks, m & 0xFFFFu);
         }
         for (int o = 16; o > 0; o >>= 1) ks = min(ks, __shfl_xor_sync(0xffffffffu, ks, o));
-        uint32_t nh = 0, tot = 0;
+        uint32_t nh = 0, tot = 0, nmin = 0;  // nmin: hits at the lane's minimum bR
         double bR = INFINITY;
         int bk = -1;
         for (uint32_t k = lane; k < p.s; k += 32) {
@@ -466,11 +484,10 @@ __global__ void k_walk_reduce(WalkTasks t, WalkParams p, WalkRecs r, dg_update_r
                 if (bk < 0 || R < bR) {  // k ascends per lane: first minimum keeps the lower index
                     bR = R;
                     bk = (int)k;
+                    nmin = 1;
+                } else if (R == bR) {
+                    ++nmin;
                 }
-            }
-            if (dbg_reason) {
-                dbg_reason[(size_t)i * p.s + k] = (int32_t)rs;
-                dbg_steps[(size_t)i * p.s + k] = (int32_t)st;
             }
         }
         for (int o = 16; o > 0; o >>= 1) {
@@ -478,9 +495,31 @@ __global__ void k_walk_reduce(WalkTasks t, WalkParams p, WalkRecs r, dg_update_r
             tot += __shfl_xor_sync(0xffffffffu, tot, o);
             const double oR = __shfl_xor_sync(0xffffffffu, bR, o);
             const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
-            if (ok >= 0 && (bk < 0 || oR < bR || (oR == bR && ok < bk))) {
+            const uint32_t on = __shfl_xor_sync(0xffffffffu, nmin, o);
+            if (ok >= 0 && (bk < 0 || oR < bR)) {
                 bR = oR;
                 bk = ok;
+                nmin = on;
+            } else if (ok >= 0 && oR == bR) {
+                bk = min(bk, ok);
+                nmin += on;
+            }
+        }
+        // pruned deletions: the walkers at the minimum are never cut, a hit above it
+        // may or may not have been (scheduling); count and record only the minimum
+        const bool prune = !ins && p.del_prune;
+        if (prune) nh = nmin;
+        if (dbg_reason) {
+            for (uint32_t k = lane; k < p.s; k += 32) {
+                const uint32_t m = r.meta[(size_t)j * p.s + k];
+                uint32_t st = m & 0xFFFFu, rs = m >> 16;
+                if (ee && ks != NONE && st > ks) {
+                    st = ks;
+                    rs = R_CUT;
+                }
+                if (prune && rs == R_HIT && r.R[(size_t)j * p.s + k] != bR) rs = R_CUT;
+                dbg_reason[(size_t)i * p.s + k] = (int32_t)rs;
+                dbg_steps[(size_t)i * p.s + k] = (int32_t)st;
             }
         }
         if (lane == 0) {

@@ -20,7 +20,8 @@ struct WalkTasks {
     uint32_t* idx;   // update index in the batch
     double* wpq;     // insertion weight (0 for deletions)
     uint8_t* kind;   // WALK_INS / WALK_DEL
-    uint32_t* kstar; // first hitting step (early exit), 0xFFFFFFFF if none yet
+    uint32_t* kstar; // insertion: first hitting step (early exit); deletion: minimum high word
+                     // of a hit's FP64 resistance (pruning); 0xFFFFFFFF if none yet
     uint32_t* count; // device: number of walked updates W
 };
 
@@ -29,6 +30,7 @@ struct WalkParams {
     uint32_t T;
     uint32_t s;
     uint32_t early_exit;
+    uint32_t del_prune;   // deletion walkers stop once R exceeds a hit's R of their update
     uint32_t key0, key1;  // Philox key = seed
 };
 

@@ -48,7 +48,8 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
 class Config(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("K", C.c_double), ("T", C.c_int32), ("s", C.c_int32),
-                ("ins_early_exit", C.c_int32), ("walk_mode", C.c_int32), ("slack", C.c_double),
+                ("ins_early_exit", C.c_int32), ("del_prune", C.c_int32), ("walk_mode", C.c_int32),
+                ("slack", C.c_double),
                 ("overflow_frac", C.c_double), ("hbm_budget_bytes", C.c_uint64), ("autotune", C.c_int32),
                 ("timeout_ms", C.c_int32), ("use_cuda_graphs", C.c_int32), ("record_walkers", C.c_int32),
                 ("device", C.c_int32), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p)]
@@ -142,14 +143,15 @@ def make_updates(u, v, w, op) -> np.ndarray:
 
 
 class Context:
-    def __init__(self, *, seed=0, K=100.0, T=100, s=32, early_exit=True, walk_mode="batched", slack=1.25,
-                 overflow=0.5, hbm_budget=0, autotune=True, timeout_ms=60000, cuda_graphs=True,
+    def __init__(self, *, seed=0, K=100.0, T=100, s=32, early_exit=True, del_prune=True, walk_mode="batched",
+                 slack=1.25, overflow=0.5, hbm_budget=0, autotune=True, timeout_ms=60000, cuda_graphs=True,
                  record_walkers=False, device=0, allocator=None):
         L = load_library()
         cfg = Config()
         L.dg_config_default(C.byref(cfg))
         cfg.seed, cfg.K, cfg.T, cfg.s = int(seed), float(K), int(T), int(s)
         cfg.ins_early_exit = 1 if early_exit else 0
+        cfg.del_prune = 1 if del_prune else 0
         cfg.walk_mode = WALK_PER_UPDATE if walk_mode in ("per_update", WALK_PER_UPDATE) else WALK_BATCHED
         cfg.slack, cfg.overflow_frac = float(slack), float(overflow)
         cfg.hbm_budget_bytes = int(hbm_budget)
@@ -173,6 +175,7 @@ class Context:
             self._hooks = (ALLOC_FN(_alloc), FREE_FN(_free))
             cfg.alloc, cfg.free = self._hooks
         self.T, self.s = int(T), int(s)
+        self.del_prune = bool(del_prune)
         h = C.c_void_p()
         _check(L.dg_create(C.byref(cfg), C.byref(h)))
         self._h = h

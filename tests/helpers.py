@@ -59,7 +59,9 @@ def _key(a, b):
 
 
 class ReferenceStream:
-    def __init__(self, n, a, b, w, h_pairs, *, seed=0, K=100.0, T=100, s=32, early_exit=True):
+    def __init__(self, n, a, b, w, h_pairs, *, seed=0, K=100.0, T=100, s=32, early_exit=True,
+                 prune_bounds=False):
+        self.prune_bounds = prune_bounds
         self.n = n
         self.G = {(int(x), int(y)): float(ww) for x, y, ww in zip(a, b, w)}
         self.H = set(_key(int(x), int(y)) for x, y in h_pairs)
@@ -141,6 +143,27 @@ class ReferenceStream:
                 best = min(hits, key=lambda k: (Rs[k], k))
                 r["best_walker"] = best
                 r["r_est"] = Rs[best]
+            if self.prune_bounds:
+                # deletion pruning: a walker whose resistance passes R~ cannot give the
+                # minimum; its steps end at the first such step, recomputed here from
+                # its path and the G_b weights (r = 1/w, summed in walk order)
+                r["nhits_min"], r["steps_lo"] = r["nhits"], r["steps"]
+                if deletion and hits:
+                    rstar = r["r_est"]
+                    lo = 0
+                    for k in range(self.s):
+                        if k in hits and Rs[k] == rstar:
+                            lo += steps[k]
+                            continue
+                        R, cut = 0.0, steps[k]
+                        for t in range(1, steps[k] + 1):
+                            R = R + 1.0 / Gb[_key(int(paths[k][t - 1]), int(paths[k][t]))]
+                            if R > rstar:
+                                cut = t
+                                break
+                        lo += cut
+                    r["nhits_min"] = sum(1 for k in hits if Rs[k] == rstar)
+                    r["steps_lo"] = lo
             if not deletion:
                 r["accepted"] = int(not hits)
                 if r["accepted"] and _key(u, v) in Gb:

@@ -13,7 +13,7 @@ import pytest
 
 from paper_2505_02741_b300 import dygrass as D
 from paper_2505_02741_b300 import workloads as W
-from tests.gpu_util import assert_edges_equal, assert_results_equal, pair, step_both
+from tests.gpu_util import assert_edges_equal, assert_results_equal, assert_same_outputs, pair, step_both
 from tests.helpers import random_connected, ring
 
 pytestmark = pytest.mark.gpu
@@ -49,14 +49,47 @@ def test_grid64_step_limit_10():
     ctx.close()
 
 
-@pytest.mark.parametrize("early_exit", [True, False])
-def test_grid_mixed_stream(early_exit):
+@pytest.mark.parametrize("early_exit,del_prune", [(True, True), (False, False), (True, False)])
+def test_grid_mixed_stream(early_exit, del_prune):
     """Several fully dynamic batches (insertions and deletions interleaved)."""
     wl, st = W.make_grid(32, 32)
-    ctx, g, o = pair(wl.n, wl.a, wl.b, wl.w, wl.h_ids, early_exit=early_exit)
+    ctx, g, o = pair(wl.n, wl.a, wl.b, wl.w, wl.h_ids, early_exit=early_exit, ctx_kw=dict(del_prune=del_prune))
     for b in range(4):
         bt = st.next_batch(150, 150)
         step_both(g, o, bt.u, bt.v, bt.w, bt.op, where=f"batch {b}")
+    ctx.close()
+
+
+def test_deletion_pruning_walker_records():
+    """Pruned deletion walkers: each GPU walker's path is a prefix of the
+    oracle's unpruned path, no walker runs longer than there, the walkers at
+    the minimum resistance are recorded as hits with their exact step counts,
+    and the pruned steps are far fewer than the unpruned ones."""
+    wl, st = W.make_grid(48, 48)
+    ctx, g, o = pair(wl.n, wl.a, wl.b, wl.w, wl.h_ids, ctx_kw=dict(record_walkers=True))
+    skipped = 0
+    for b in range(2):
+        bt = st.next_batch(100, 400)
+        res = g.apply(D.make_updates(bt.u, bt.v, bt.w, bt.op))
+        ref = o.apply(bt.u, bt.v, bt.w, bt.op, walkers=True, paths=True, prune_bounds=True)
+        assert_results_equal(res, ref, f"pruned batch {b}")
+        assert_edges_equal(g.sparsifier(), o.edges("H"), "H")
+        rec = g.walker_records(len(bt))
+        dels = np.nonzero((bt.op == 1) & (res["walked"] == 1))[0]
+        for i in dels:
+            for k in range(wl.s):
+                gs, os_ = int(rec["steps"][i, k]), int(ref["walkers"]["steps"][i, k])
+                assert gs <= os_, (i, k)
+                assert np.array_equal(rec["paths"][i, k, :gs + 1], ref["paths"][i, k, :gs + 1]), (i, k)
+                at_min = ref["walkers"]["reason"][i, k] == 1 and ref["walkers"]["R"][i, k] == res["r_est"][i]
+                assert (rec["reason"][i, k] == 1) == at_min, (i, k)
+                if at_min:
+                    assert gs == os_, (i, k)
+                else:
+                    assert rec["reason"][i, k] in (3, 4, 5), (i, k)
+        skipped += int((ref["steps"][dels] - res["steps"][dels]).sum())
+        assert res["hit"][dels].sum() > 0
+    assert skipped > 0
     ctx.close()
 
 
@@ -118,23 +151,25 @@ def test_random_graphs_many_batches(seed):
     ctx.close()
 
 
-def test_execution_forms_agree():
+@pytest.mark.parametrize("del_prune", [False, True])
+def test_execution_forms_agree(del_prune):
     """Per-update launches, CUDA-graph replay, eager batched and every walk
-    launch shape give bit-identical outputs."""
+    launch shape give bit-identical outputs (all but the step counts when
+    deletion walkers are pruned)."""
     wl, st = W.make_grid(40, 40)
     batches = [st.next_batch(300, 200) for _ in range(3)]
     outs = []
     configs = [dict(walk_mode="batched", cuda_graphs=True), dict(walk_mode="batched", cuda_graphs=False),
                dict(walk_mode="per_update", cuda_graphs=False)]
     for kw in configs:
-        ctx = D.Context(**kw)
+        ctx = D.Context(del_prune=del_prune, **kw)
         g = ctx.load_graph(wl.n, wl.a, wl.b, wl.w)
         g.init_sparsifier(wl.a[wl.h_ids], wl.b[wl.h_ids])
         rs = [g.apply(D.make_updates(bt.u, bt.v, bt.w, bt.op)) for bt in batches]
         outs.append((rs, g.sparsifier()))
         ctx.close()
     for shape in [(32, 1, 0), (64, 2, 4), (256, 4, 0), (128, 2, 1)]:
-        ctx = D.Context()
+        ctx = D.Context(del_prune=del_prune)
         g = ctx.load_graph(wl.n, wl.a, wl.b, wl.w)
         g.init_sparsifier(wl.a[wl.h_ids], wl.b[wl.h_ids])
         g.set_walk_shape(*shape)
@@ -144,7 +179,7 @@ def test_execution_forms_agree():
     ref_rs, ref_h = outs[0]
     for rs, hh in outs[1:]:
         for r0, r1 in zip(ref_rs, rs):
-            assert r0.tobytes() == r1.tobytes()
+            assert_same_outputs(r0, r1, steps=not del_prune)
         assert_edges_equal(hh, ref_h, "H")
 
 
@@ -166,9 +201,9 @@ def test_device_io_matches_host_io():
             res = d_res.cpu().numpy().view(D.RESULT_DTYPE)
         else:
             res = g.apply(ups)
-        out.append((res.tobytes(), g.sparsifier()))
+        out.append((res.copy(), g.sparsifier()))
         ctx.close()
-    assert out[0][0] == out[1][0]
+    assert_same_outputs(out[0][0], out[1][0], steps=False)
     assert_edges_equal(out[0][1], out[1][1], "H")
 
 
@@ -200,7 +235,7 @@ def test_checkpoint_resume_by_update_id():
     g2.init_sparsifier(ha, hb)
     g2.next_update_id = nid
     r_resumed = g2.apply(D.make_updates(b2.u, b2.v, b2.w, b2.op))
-    assert r_direct.tobytes() == r_resumed.tobytes()
+    assert_same_outputs(r_direct, r_resumed, steps=False)
     assert_edges_equal(g.sparsifier(), g2.sparsifier(), "H")
     ctx.close()
 

@@ -417,6 +417,32 @@ def test_batch_snapshot(seed):
     assert g.next_id == len(ups)
 
 
+@pytest.mark.parametrize("seed", [6, 7, 8])
+def test_deletion_pruning_bounds(seed):
+    """nhits_min / steps_lo of walked deletions (walkers stopping once their
+    resistance passes R~) against a restatement that re-sums each walker's
+    resistance along its path; unit weights make equal resistances common, so
+    ties at R~ are exercised too."""
+    rng = np.random.default_rng(seed)
+    n = 24
+    a, b, w = random_connected(n, 30, rng, unit=(seed == 8))
+    h = W.init_sparsifier(n, a, b, w, rng, frac=0.3)
+    g = OracleGraph(n, a, b, w, T=16, s=8, K=10.0)
+    g.init_sparsifier(a[h], b[h])
+    ref = ReferenceStream(n, a, b, w, list(zip(a[h].tolist(), b[h].tolist())), T=16, s=8, K=10.0,
+                          prune_bounds=True)
+    ups = _mixed_stream(rng, n, a, b, 150, invalid=False)
+    pruned = 0
+    for lo in range(0, len(ups), 25):
+        chunk = ups[lo:lo + 25]
+        cols = list(zip(*chunk))
+        out = g.apply(list(cols[0]), list(cols[1]), list(cols[2]), list(cols[3]), prune_bounds=True)
+        _compare(ref.apply(chunk), out)
+        assert (out["steps_lo"] <= out["steps"]).all() and (out["nhits_min"] <= out["nhits"]).all()
+        pruned += int((out["steps"] - out["steps_lo"]).sum())
+    assert pruned > 0
+
+
 def test_invariants_after_stream():
     """H stays a subgraph of G with G's weights; on the grid with insertions and
     deletions, H keeps the components of G."""

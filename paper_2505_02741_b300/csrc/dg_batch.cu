@@ -460,6 +460,8 @@ void graph_load(Ctx& c, DGraph& g, int32_t n, int64_t m, const int32_t* u, const
     csr_alloc_vertices(g.H, a, n, st);
     g.touched.ensure(a, (size_t)n + 1, st);
     DG_CUDA(cudaMemsetAsync(g.touched.p, 0, g.touched.bytes(), st));
+    g.touched_h.ensure(a, (size_t)n + 1, st);
+    DG_CUDA(cudaMemsetAsync(g.touched_h.p, 0, g.touched_h.bytes(), st));
     const uint32_t M = (uint32_t)m, M2 = 2 * (uint32_t)m;
     DBuf<int32_t> du, dv;
     DBuf<double> dw;
@@ -515,6 +517,8 @@ void graph_load(Ctx& c, DGraph& g, int32_t n, int64_t m, const int32_t* u, const
     g.has_h = true;  // empty sparsifier
     g.next_id = 0;
     for (int i = 0; i < 7; ++i) DG_CUDA(cudaEventCreate(&g.ev[i]));
+    for (int i = 0; i < 5; ++i) DG_CUDA(cudaEventCreateWithFlags(&g.fk[i], cudaEventDisableTiming));
+    DG_CUDA(cudaStreamCreateWithFlags(&g.side, cudaStreamNonBlocking));
     wait_stream(c, st);
 }
 
@@ -641,6 +645,7 @@ void graph_release(Ctx& c, DGraph& g) {
     csr_release(g.G, c.alloc, st);
     csr_release(g.H, c.alloc, st);
     g.touched.release(c.alloc, st);
+    g.touched_h.release(c.alloc, st);
     graph_release_ws(c, g, st);
     if (g.hs.ups) cudaFreeHost(g.hs.ups);
     if (g.hs.res) cudaFreeHost(g.hs.res);
@@ -652,6 +657,13 @@ void graph_release(Ctx& c, DGraph& g) {
     g.hs = HostStage{};
     for (int i = 0; i < 7; ++i)
         if (g.ev[i]) cudaEventDestroy(g.ev[i]);
+    for (int i = 0; i < 5; ++i)
+        if (g.fk[i]) cudaEventDestroy(g.fk[i]);
+    if (g.side) {
+        cudaStreamSynchronize(g.side);
+        cudaStreamDestroy(g.side);
+    }
+    g.side = nullptr;
     if (g.stream) cudaStreamDestroy(g.stream);
     g.stream = nullptr;
     cudaStreamSynchronize(st);
@@ -755,6 +767,14 @@ static void enqueue_mutate(Ctx& c, DGraph& g, cudaStream_t st) {
     ra.fins = w.wflag2.p;
     k_val_runs<<<grid_for(B), BT, 0, st>>>(ra);
     ++g_launches;
+    // Two streams from here (captured as parallel branches of the step's graph):
+    //   side: walk tasks; H' = H minus the deleted H edges (list, plan, execute)
+    //   st:   sort of the net G changes; G_b (plan, execute)
+    // Each execution also waits for the other CSR's plan, so an abort raised by
+    // either plan still leaves both G and H untouched.
+    cudaStream_t sd = g.side;
+    DG_CUDA(cudaEventRecord(g.fk[0], st));
+    DG_CUDA(cudaStreamWaitEvent(sd, g.fk[0], 0));
     {
         ScanJob j;
         j.in[0] = w.wflag.p;
@@ -765,10 +785,10 @@ static void enqueue_mutate(Ctx& c, DGraph& g, cudaStream_t st) {
         j.total[1] = w.t_count.p + 3;
         j.k = 2;
         j.err = w.err.p;
-        scan_exclusive(j, d_nu, B, w.vscan.p, st);
+        scan_exclusive(j, d_nu, B, w.vscan.p, sd);
     }
     WalkTasks tasks = tasks_of(w);
-    k_make_tasks<<<grid_for(B), BT, 0, st>>>(w.ups.p, w.wkind.p, w.wpos.p, w.wpos2.p, w.t_count.p + 2, w.hdr.p, B,
+    k_make_tasks<<<grid_for(B), BT, 0, sd>>>(w.ups.p, w.wkind.p, w.wpos.p, w.wpos2.p, w.t_count.p + 2, w.hdr.p, B,
                                             tasks);
     ++g_launches;
     // net G changes, sorted by (vertex, neighbour)
@@ -776,7 +796,9 @@ static void enqueue_mutate(Ctx& c, DGraph& g, cudaStream_t st) {
     const bool galt = radix_sort_pairs(gs, w.gcount.p, B2, bit_length((uint64_t)n * n - 1), st);
     const uint64_t* gk = galt ? w.gkeys_alt.p : w.gkeys.p;
     const uint32_t* gv = galt ? w.gvals_alt.p : w.gvals.p;
-    k_flag_hrem<<<grid_for(B2), BT, 0, st>>>(gv, w.ghrem.p, w.gcount.p, B2, w.hflag.p);
+    DG_CUDA(cudaEventRecord(g.fk[1], st));
+    DG_CUDA(cudaStreamWaitEvent(sd, g.fk[1], 0));
+    k_flag_hrem<<<grid_for(B2), BT, 0, sd>>>(gv, w.ghrem.p, w.gcount.p, B2, w.hflag.p);
     ++g_launches;
     {
         ScanJob j;
@@ -785,9 +807,9 @@ static void enqueue_mutate(Ctx& c, DGraph& g, cudaStream_t st) {
         j.total[0] = w.hcount.p;
         j.k = 1;
         j.err = w.err.p;
-        scan_exclusive(j, w.gcount.p, B2, w.gscan.p, st);
+        scan_exclusive(j, w.gcount.p, B2, w.gscan.p, sd);
     }
-    k_compact_kv<<<grid_for(B2), BT, 0, st>>>(gk, gv, w.hflag.p, w.hpos.p, w.gcount.p, B2, w.hkeys.p, w.hvals.p);
+    k_compact_kv<<<grid_for(B2), BT, 0, sd>>>(gk, gv, w.hflag.p, w.hpos.p, w.gcount.p, B2, w.hkeys.p, w.hvals.p);
     ++g_launches;
     ChangeList clG;
     clG.keys = gk;
@@ -803,11 +825,16 @@ static void enqueue_mutate(Ctx& c, DGraph& g, cudaStream_t st) {
     clH.ws = w.gw.p;
     clH.d_count = w.hcount.p;
     clH.max_count = B2;
-    // both plans before either execution: an abort leaves G and H untouched
+    csr_plan(g.H, clH, w.apH, w.err.p, ERR_POOL_G, ERR_CAP_PRE, sd);
+    DG_CUDA(cudaEventRecord(g.fk[2], sd));
     csr_plan(g.G, clG, w.apG, w.err.p, ERR_POOL_G, ERR_CAP_PRE, st);
-    csr_plan(g.H, clH, w.apH, w.err.p, ERR_POOL_G, ERR_CAP_PRE, st);
+    DG_CUDA(cudaEventRecord(g.fk[3], st));
+    DG_CUDA(cudaStreamWaitEvent(st, g.fk[2], 0));
+    DG_CUDA(cudaStreamWaitEvent(sd, g.fk[3], 0));
     csr_exec(g.G, clG, w.apG, g.touched.p, w.err.p, st);
-    csr_exec(g.H, clH, w.apH, g.touched.p, w.err.p, st);
+    csr_exec(g.H, clH, w.apH, g.touched_h.p, w.err.p, sd);
+    DG_CUDA(cudaEventRecord(g.fk[4], sd));
+    DG_CUDA(cudaStreamWaitEvent(st, g.fk[4], 0));
     DG_CUDA(record_event(g.ev[4], st));
 }
 

@@ -90,7 +90,8 @@ struct DGraph {
     CSR G, H;
     bool has_h = false;
     uint64_t next_id = 0;
-    DBuf<uint8_t> touched;
+    DBuf<uint8_t> touched;    // vertices whose G list (or H list at commit) changed in the running step
+    DBuf<uint8_t> touched_h;  // the same for H while G and H are mutated side by side
     BatchWS ws;
     HostStage hs;
     WalkShape shape;
@@ -100,9 +101,12 @@ struct DGraph {
     cudaStream_t stream = nullptr;           // private stream (serving)
     // timing events: 0/1 walk, 2/3 batch, 4 end of mutation, 5 end of reduction, 6 end of emission
     cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    // second stream of the mutation (H side, walk tasks) and its fork/join events
+    cudaStream_t side = nullptr;
+    cudaEvent_t fk[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     dg_batch_stats stats{};
     std::mutex mu;
-    uint64_t bytes() const { return G.bytes() + H.bytes() + touched.bytes() + ws.bytes(); }
+    uint64_t bytes() const { return G.bytes() + H.bytes() + touched.bytes() + touched_h.bytes() + ws.bytes(); }
 };
 
 struct Ctx;  // context (dg_api.cu)

@@ -243,9 +243,26 @@ __global__ void k_val_runs(RunArgs a) {
 // Task list from the walk flags k_val_runs set: walked deletions (no K, the
 // longest walks) first, so they start first and the short insertion walks
 // fill the tail of the persistent launch.
+// Largest R >= 0 (as an FP64 bit pattern) with fl(w_pq * R) <= K.  The
+// rounded product is non-decreasing in R and non-negative doubles order like
+// their bit patterns, so the insertion threshold test of a walk step becomes
+// one integer comparison R_bits <= r_limit, with the same outcome as forming
+// the product.  Binary search over the patterns of [0, +inf].
+__device__ uint64_t r_limit_bits(double wpq, double K) {
+    uint64_t lo = 0ull, hi = 0x7FF0000000000000ull;  // fl(w * 0) = 0 <= K
+    if (__dmul_rn(wpq, __longlong_as_double((long long)hi)) <= K) return hi;
+    while (hi - lo > 1ull) {
+        const uint64_t mid = lo + ((hi - lo) >> 1);
+        if (__dmul_rn(wpq, __longlong_as_double((long long)mid)) <= K) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
 __global__ void k_make_tasks(const dg_update* __restrict__ ups, const uint8_t* __restrict__ wkind,
                              const uint32_t* __restrict__ pdel, const uint32_t* __restrict__ pins,
-                             const uint32_t* __restrict__ totals, const BatchHdr* hdr, uint32_t b_max, WalkTasks t) {
+                             const uint32_t* __restrict__ totals, const BatchHdr* hdr, uint32_t b_max, double K,
+                             WalkTasks t) {
     const uint32_t nu = min(hdr->nu, b_max);
     const uint32_t ndel = totals[0];
     if (blockIdx.x == 0 && threadIdx.x == 0) *t.count = ndel + totals[1];
@@ -258,6 +275,7 @@ __global__ void k_make_tasks(const dg_update* __restrict__ ups, const uint8_t* _
         t.v[j] = (uint32_t)up.v;
         t.idx[j] = i;
         t.wpq[j] = k == WALK_INS ? up.w : 0.0;
+        t.rmax[j] = k == WALK_INS ? r_limit_bits(up.w, K) : ~0ull;
         t.kind[j] = k;
     }
 }
@@ -295,7 +313,7 @@ uint64_t BatchWS::bytes() const {
     b += gscan.bytes() + gcount.bytes() + hflag.bytes() + hpos.bytes() + hvals.bytes() + hcount.bytes();
     b += gkind.bytes() + ghrem.bytes() + kind_del.bytes() + gw.bytes();
     b += t_u.bytes() + t_v.bytes() + t_idx.bytes() + t_kstar.bytes() + t_count.bytes() + meta.bytes();
-    b += t_wpq.bytes() + recR.bytes() + t_kind.bytes() + best.bytes();
+    b += t_wpq.bytes() + t_rmax.bytes() + recR.bytes() + t_kind.bytes() + best.bytes();
     b += ckeys.bytes() + ckeys_alt.bytes() + ck2.bytes() + cvals.bytes() + cvals_alt.bytes() + chist.bytes();
     b += cscan.bytes() + ccount.bytes() + cflag.bytes() + cpos.bytes() + cv2.bytes() + ccount2.bytes();
     b += cw.bytes() + kind_ins.bytes() + path_buf.bytes() + path_len.bytes() + path_w.bytes() + fb_list.bytes() +
@@ -376,6 +394,7 @@ static void ensure_ws(Ctx& c, DGraph& g, uint32_t b_max, cudaStream_t st) {
     w.t_kstar.ensure(a, B, st);
     w.t_count.ensure(a, 4, st);
     w.t_wpq.ensure(a, B, st);
+    w.t_rmax.ensure(a, B, st);
     w.t_kind.ensure(a, B, st);
     w.best.ensure(a, B, st);
     w.meta.ensure(a, (size_t)B * s, st);
@@ -683,7 +702,7 @@ void graph_release_ws(Ctx& c, DGraph& g, cudaStream_t st) {
     REL(vvals_alt); REL(vhist); REL(vscan); REL(wkind); REL(fin_w); REL(wflag); REL(wpos); REL(wflag2); REL(wpos2); REL(gkeys);
     REL(gkeys_alt); REL(hkeys); REL(gvals); REL(gvals_alt); REL(ghist); REL(gscan); REL(gcount); REL(hflag);
     REL(hpos); REL(hvals); REL(hcount); REL(gkind); REL(ghrem); REL(kind_del); REL(gw); REL(t_u); REL(t_v);
-    REL(t_idx); REL(t_kstar); REL(t_count); REL(meta); REL(t_wpq); REL(recR); REL(t_kind); REL(best);
+    REL(t_idx); REL(t_kstar); REL(t_count); REL(meta); REL(t_wpq); REL(t_rmax); REL(recR); REL(t_kind); REL(best);
     REL(ckeys); REL(ckeys_alt); REL(ck2); REL(cvals); REL(cvals_alt); REL(chist); REL(cscan); REL(ccount);
     REL(cflag); REL(cpos); REL(cv2); REL(ccount2); REL(cw); REL(kind_ins); REL(path_buf); REL(path_w); REL(path_len); REL(fb_list); REL(fb_count); REL(dbg_reason);
     REL(dbg_steps); REL(dbg_paths);
@@ -703,6 +722,7 @@ static WalkTasks tasks_of(BatchWS& w) {
     t.v = w.t_v.p;
     t.idx = w.t_idx.p;
     t.wpq = w.t_wpq.p;
+    t.rmax = w.t_rmax.p;
     t.kind = w.t_kind.p;
     t.kstar = w.t_kstar.p;
     t.count = w.t_count.p;
@@ -789,7 +809,7 @@ static void enqueue_mutate(Ctx& c, DGraph& g, cudaStream_t st) {
     }
     WalkTasks tasks = tasks_of(w);
     k_make_tasks<<<grid_for(B), BT, 0, sd>>>(w.ups.p, w.wkind.p, w.wpos.p, w.wpos2.p, w.t_count.p + 2, w.hdr.p, B,
-                                            tasks);
+                                            c.cfg.K, tasks);
     ++g_launches;
     // net G changes, sorted by (vertex, neighbour)
     SortBufs gs{w.gkeys.p, w.gvals.p, w.gkeys_alt.p, w.gvals_alt.p, w.ghist.p, w.gscan.p, w.err.p};

@@ -135,7 +135,8 @@ struct Lean {
     uint32_t x;         // random word of the next step
     bool ins, active;
     bool pid;           // prev holds the previous vertex's id (we arrived at a hub)
-    double R, wpq;
+    double R;
+    uint64_t rmax;      // insertion: w_pq * R <= K  <=>  bits(R) <= rmax
 };
 
 __device__ __forceinline__ void lean_start(Lean& w, const WalkKernelArgs& a, uint32_t wid, uint64_t id0) {
@@ -144,7 +145,7 @@ __device__ __forceinline__ void lean_start(Lean& w, const WalkKernelArgs& a, uin
     const uint32_t u = a.t.u[w.j];
     w.q = a.t.v[w.j];
     w.ins = a.t.kind[w.j] == WALK_INS;
-    w.wpq = a.t.wpq[w.j];
+    w.rmax = a.t.rmax[w.j];
     const uint64_t id = id0 + a.t.idx[w.j];
     w.ulo = (uint32_t)id;
     w.uhi = (uint32_t)(id >> 32);
@@ -168,20 +169,27 @@ __device__ __forceinline__ void lean_finish(Lean& w, const WalkKernelArgs& a, ui
     w.active = false;
 }
 
+// head (nbr, noff, ndeg, rev) and resistance of the entry at pool index i
+__device__ __forceinline__ void load_step(const Ent* pool, uint32_t i, uint4& h, double& r) {
+    const uint4* q = reinterpret_cast<const uint4*>(pool + i);
+    h = __ldg(q);
+    r = __ldg(reinterpret_cast<const double*>(q + 1));
+}
+
 // The step when the walker stands on a hub (previous vertex known by id only:
 // L[jj] was loaded at slot `at`; take L[jj+1] instead when L[jj] is at or past
 // the previous vertex) or the chosen entry leads to a hub (HUBREF: the list
 // comes from the vertex arrays).  Advances the walker; false on a bad offset.
-__device__ __forceinline__ bool lean_hub_step(Lean& v, const WalkKernelArgs& a, uint4& h, double2& tl, uint32_t at) {
+__device__ __forceinline__ bool lean_hub_step(Lean& v, const WalkKernelArgs& a, uint4& h, double& r, uint32_t at) {
     const CSRView& g = v.ins ? a.H : a.G;
     if (v.pid && h.x >= v.prev) {
         if ((uint64_t)at + 1 >= g.pool_cap) {
             atomicOr(a.d_err, (uint32_t)ERR_INTERNAL);
             return false;
         }
-        load_ent(g.pool + at + 1, h, tl);
+        load_step(g.pool, at + 1, h, r);
     }
-    v.R = __dadd_rn(v.R, tl.x);
+    v.R = __dadd_rn(v.R, r);
     v.steps += 1;
     const uint32_t from = v.c;
     v.c = h.x;
@@ -199,14 +207,49 @@ __device__ __forceinline__ bool lean_hub_step(Lean& v, const WalkKernelArgs& a, 
     return true;
 }
 
-// Up to 256 threads per block, at least 4 blocks of 256 per SM (64 registers
-// per thread) for two walkers per thread.  HUBS selects the variant that
+// Sends out the entry load of the walker's next step (and the early-exit /
+// pruning probe of its update); false when there is no next step (n_eff = 0)
+// or the offset would leave the pool (a broken mutation, reported).
+template <bool HUBS>
+__device__ __forceinline__ bool lean_issue(const Lean& v, const WalkKernelArgs& a, uint4& h, double& r, uint32_t& ks,
+                                           uint32_t& at) {
+    const uint32_t neff = v.deg - (v.prev != NONE ? 1u : 0u);
+    if (neff == 0) {
+        // a hub reference met by the hub-free variant ends here (its cached
+        // degree is 1): report it instead of stopping silently
+        if (!HUBS && v.off == HUBREF) atomicOr(a.d_err, (uint32_t)ERR_INTERNAL);
+        return false;
+    }
+    const uint32_t jj = __umulhi(v.x, neff);
+    // slot of the previous vertex known: skip it by position; after a hub
+    // arrival only its id is known: load L[jj] and step past it if needed
+    const uint32_t idx = (HUBS && v.pid) ? jj : jj + (jj >= v.prev ? 1u : 0u);
+    const uint64_t pcap = v.ins ? a.H.pool_cap : a.G.pool_cap;
+    if ((uint64_t)v.off + idx >= pcap) {
+        atomicOr(a.d_err, (uint32_t)ERR_INTERNAL);
+        return false;
+    }
+    at = v.off + idx;
+    load_step(v.ins ? a.H.pool : a.G.pool, at, h, r);
+    ks = (v.ins ? a.p.early_exit : a.p.del_prune) ? __ldcg(&a.t.kstar[v.j]) : NONE;
+    return true;
+}
+
+// Up to 256 threads per block; register caps that keep spills out: 4 blocks
+// of 256 per SM for one walker per thread, 3 for two.  HUBS selects the variant that
 // handles hub references; both variants are launched and the one that does
 // not match the device-side hub counts of G and H returns at once, so graphs
 // without hubs (meshes) run a loop with no hub branch and no host round trip
 // is needed to choose.
+//
+// Software pipelining: the address of a walker's next entry depends only on
+// the entry just read and on a Philox word computed in advance, so the next
+// load is sent out before the stop rules of the current step are evaluated.
+// The FP64 accumulation and the resistance tests then overlap that load
+// instead of sitting on the chain of dependent loads; a walker that stops
+// drops the load it has in flight.
 template <int ILP, bool HUBS>
-__global__ void __launch_bounds__(256, (ILP == 2 ? 4 : 1)) k_walk_batched(WalkKernelArgs a) {
+__global__ void __launch_bounds__(256, (ILP == 1 ? 4 : (ILP == 2 ? 3 : 1))) k_walk_batched(WalkKernelArgs a) {
     if (walk_aborted(a.d_err)) return;
     if (((*a.H.nhub | *a.G.nhub) != 0u) != HUBS) return;
     const uint32_t W = min(*a.t.count, a.j_hi);
@@ -217,11 +260,19 @@ __global__ void __launch_bounds__(256, (ILP == 2 ? 4 : 1)) k_walk_batched(WalkKe
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
     Lean w[ILP];
+    uint4 h[ILP];
+    double r[ILP];
+    uint32_t ks[ILP], at[ILP];
+    bool fly[ILP];  // an entry load of the walker's next step is in flight
 #pragma unroll
-    for (int i = 0; i < ILP; ++i) w[i].active = false;
+    for (int i = 0; i < ILP; ++i) {
+        w[i].active = false;
+        fly[i] = false;
+    }
     bool exhausted = false;
     for (;;) {
-        // refill empty slots, one atomic per warp and slot
+        // refill empty slots, one atomic per warp and slot; a new walker sends
+        // out its first load at once
 #pragma unroll
         for (int i = 0; i < ILP; ++i) {
             const bool need = !w[i].active && !exhausted;
@@ -233,8 +284,14 @@ __global__ void __launch_bounds__(256, (ILP == 2 ? 4 : 1)) k_walk_batched(WalkKe
                 b = __shfl_sync(0xffffffffu, b, leader);
                 if (need) {
                     const unsigned long long id = b + __popc(m & lt);
-                    if (id < total) lean_start(w[i], a, wbase + (uint32_t)id, id0);
-                    else exhausted = true;
+                    if (id < total) {
+                        lean_start(w[i], a, wbase + (uint32_t)id, id0);
+                        fly[i] = lean_issue<HUBS>(w[i], a, h[i], r[i], ks[i], at[i]);
+                        if (!fly[i]) lean_finish(w[i], a, R_LEAF);
+                        else w[i].x = philox_word0(1u, w[i].k, w[i].ulo, w[i].uhi, a.p.key0, a.p.key1);
+                    } else {
+                        exhausted = true;
+                    }
                 }
             }
         }
@@ -242,60 +299,24 @@ __global__ void __launch_bounds__(256, (ILP == 2 ? 4 : 1)) k_walk_batched(WalkKe
 #pragma unroll
         for (int i = 0; i < ILP; ++i) any |= w[i].active;
         if (!__any_sync(0xffffffffu, any)) break;
-        // issue: leaf check, the entry load, the early-exit probe, then the next
-        // step's Philox word while the loads are in flight
-        uint4 h[ILP];
-        double2 tl[ILP];
-        uint32_t ks[ILP], at[ILP];
-        bool go[ILP];
 #pragma unroll
         for (int i = 0; i < ILP; ++i) {
-            go[i] = false;
-            ks[i] = NONE;
-            if (!w[i].active) continue;
-            const uint32_t neff = w[i].deg - (w[i].prev != NONE ? 1u : 0u);
-            if (neff == 0) {
-                // a hub reference seen by the hub-free variant would end here (its
-                // cached degree is 1): report it instead of stopping silently
-                if (!HUBS && w[i].off == HUBREF) atomicOr(a.d_err, (uint32_t)ERR_INTERNAL);
-                lean_finish(w[i], a, R_LEAF);
-                continue;
-            }
-            const uint32_t jj = __umulhi(w[i].x, neff);
-            // slot of the previous vertex known: skip it by position; after a hub
-            // arrival only its id is known: load L[jj] and step past it if needed
-            const uint32_t idx = (HUBS && w[i].pid) ? jj : jj + (jj >= w[i].prev ? 1u : 0u);
-            const Ent* pool = w[i].ins ? a.H.pool : a.G.pool;
-            const uint64_t pcap = w[i].ins ? a.H.pool_cap : a.G.pool_cap;
-            if ((uint64_t)w[i].off + idx >= pcap) {  // only a broken mutation could get here
-                atomicOr(a.d_err, (uint32_t)ERR_INTERNAL);
-                lean_finish(w[i], a, R_LEAF);
-                continue;
-            }
-            at[i] = w[i].off + idx;
-            load_ent(pool + at[i], h[i], tl[i]);
-            if (w[i].ins ? a.p.early_exit : a.p.del_prune) ks[i] = __ldcg(&a.t.kstar[w[i].j]);
-            go[i] = true;
-        }
-#pragma unroll
-        for (int i = 0; i < ILP; ++i)
-            if (go[i]) w[i].x = philox_word0(w[i].steps + 1, w[i].k, w[i].ulo, w[i].uhi, a.p.key0, a.p.key1);
-        // consume
-#pragma unroll
-        for (int i = 0; i < ILP; ++i) {
-            if (!go[i]) continue;
+            if (!fly[i]) continue;
             Lean& v = w[i];
-            if (v.ins && ks[i] <= v.steps) {  // a walker of this update hit at a step <= ours: cut
+            const uint32_t ks_now = ks[i];
+            if (v.ins && ks_now <= v.steps) {  // a walker of this update hit at a step <= ours: cut
                 lean_finish(v, a, R_CUT);
+                fly[i] = false;
                 continue;
             }
             if (HUBS && (v.pid || h[i].y == HUBREF)) {  // leaving or entering a hub
-                if (!lean_hub_step(v, a, h[i], tl[i], at[i])) {
+                if (!lean_hub_step(v, a, h[i], r[i], at[i])) {
                     lean_finish(v, a, R_LEAF);
+                    fly[i] = false;
                     continue;
                 }
             } else {
-                v.R = __dadd_rn(v.R, tl[i].x);
+                v.R = __dadd_rn(v.R, r[i]);
                 v.steps += 1;
                 v.c = h[i].x;
                 v.off = h[i].y;
@@ -303,17 +324,25 @@ __global__ void __launch_bounds__(256, (ILP == 2 ? 4 : 1)) k_walk_batched(WalkKe
                 v.prev = h[i].w;
             }
             if (a.r.paths) a.r.paths[((size_t)v.j * a.p.s + v.k) * (a.p.T + 1) + v.steps] = (int32_t)v.c;
-            if (!v.ins && r_key(v.R) > ks[i]) {  // above a hit of this deletion: cannot be the minimum
+            // reaching v ends the walk whatever R is (hit, or over K for an insertion)
+            const bool at_q = v.c == v.q;
+            fly[i] = !at_q && v.steps < a.p.T && lean_issue<HUBS>(v, a, h[i], r[i], ks[i], at[i]);
+            const bool over = (unsigned long long)__double_as_longlong(v.R) > v.rmax;  // insertions: w_pq * R > K
+            if (!v.ins && r_key(v.R) > ks_now) {  // above a hit of this deletion: cannot be the minimum
                 lean_finish(v, a, R_CUT);
-            } else if (v.c == v.q && (!v.ins || __dmul_rn(v.wpq, v.R) <= a.p.K)) {
+            } else if (at_q && (!v.ins || !over)) {
                 if (v.ins ? a.p.early_exit : a.p.del_prune)
                     atomicMin(&a.t.kstar[v.j], v.ins ? v.steps : r_key(v.R));
                 lean_finish(v, a, R_HIT);
-            } else if (v.ins && __dmul_rn(v.wpq, v.R) > a.p.K) {
+            } else if (v.ins && over) {
                 lean_finish(v, a, R_OVER_K);
             } else if (v.steps == a.p.T) {
                 lean_finish(v, a, R_AT_T);
+            } else if (!fly[i]) {
+                lean_finish(v, a, R_LEAF);
             }
+            if (!v.active) fly[i] = false;
+            else v.x = philox_word0(v.steps + 1, v.k, v.ulo, v.uhi, a.p.key0, a.p.key1);
         }
     }
 }

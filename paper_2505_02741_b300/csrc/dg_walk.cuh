@@ -19,6 +19,7 @@ struct WalkTasks {
     uint32_t* v;     // target vertex
     uint32_t* idx;   // update index in the batch
     double* wpq;     // insertion weight (0 for deletions)
+    uint64_t* rmax;  // insertion: FP64 bit pattern of the largest R with w_pq * R <= K (all ones for deletions)
     uint8_t* kind;   // WALK_INS / WALK_DEL
     uint32_t* kstar; // insertion: first hitting step (early exit); deletion: minimum high word
                      // of a hit's FP64 resistance (pruning); 0xFFFFFFFF if none yet

@@ -60,6 +60,24 @@ def test_grid_mixed_stream(early_exit, del_prune):
     ctx.close()
 
 
+@pytest.mark.parametrize("K", [0.0, 4.0, 7.5, 1e300, math.inf])
+def test_threshold_ties_and_extremes(K):
+    """Unit weights make w_pq * R land exactly on K (a hit, reading R4); K = 0
+    and K = +inf are the ends of the threshold range.  The kernel's integer
+    form of the threshold test must decide every step as the product does."""
+    rng = np.random.default_rng(11)
+    n = 200
+    a, b, w = random_connected(n, 300, rng, unit=True)
+    h = W.init_sparsifier(n, a, b, w, rng, frac=0.2)
+    ctx, g, o = pair(n, a, b, w, h, K=K, T=40, s=16)
+    wl = W.Workload("unit", n, *W.canonical(a, b, w), h_ids=h)
+    stream = W.UpdateStream(wl, rng, ("uniform",), lambda r, u, v: r.choice([0.5, 1.0, 2.0], len(u)))
+    for bi in range(3):
+        bt = stream.next_batch(150, 30)
+        step_both(g, o, bt.u, bt.v, bt.w, bt.op, where=f"K={K} batch {bi}")
+    ctx.close()
+
+
 def test_deletion_pruning_walker_records():
     """Pruned deletion walkers: each GPU walker's path is a prefix of the
     oracle's unpruned path, no walker runs longer than there, the walkers at

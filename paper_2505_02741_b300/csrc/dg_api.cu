@@ -245,7 +245,6 @@ dg_status dg_create(const dg_config* cfg_in, dg_ctx** out) {
         c->alloc.fn_free = cfg.free;
         c->alloc.user = cfg.alloc_user;
         DG_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
-        prims_init();
         *out = reinterpret_cast<dg_ctx*>(c.release());
     });
 }

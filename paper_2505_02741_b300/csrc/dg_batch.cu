@@ -223,13 +223,13 @@ __global__ void k_val_runs(RunArgs a) {
                 const uint32_t i = a.vals[e2];
                 if (a.wkind[i] == WALK_INS) a.fin_w[i] = wcur;
             }
-        atomicAdd(&a.ctr->valid, (unsigned long long)valid);
+        agg_count(&a.ctr->valid, valid);
         uint8_t kind = 255;
         if (present0 && !state) kind = CHG_DEL;
         else if (!present0 && state) kind = CHG_INS;
         else if (present0 && state && any_valid) kind = CHG_SETW;
         if (kind == 255) continue;
-        const uint32_t pos = atomicAdd(a.gcount, 2u);
+        const uint32_t pos = agg_add(a.gcount, 2u);
         a.gkeys[pos] = key;
         a.gkeys[pos + 1] = (uint64_t)y * a.n + x;
         a.gvals[pos] = pos;

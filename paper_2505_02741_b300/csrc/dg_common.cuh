@@ -10,6 +10,9 @@
 // just read names the next list and where the previous vertex sits in it,
 // which is all the non-backtracking pick (Section III-B) needs.
 #pragma once
+#include <cooperative_groups.h>
+#include <cooperative_groups/reduce.h>
+#include <cooperative_groups/scan.h>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -50,6 +53,26 @@ struct CSRView {
     uint64_t pool_cap;        // entries allocated
     int32_t n;
 };
+
+// Warp-aggregated atomics for counters many threads bump at once: the threads
+// that arrive together combine their amounts and one of them issues a single
+// atomic (one L2 operation per warp instead of one per thread).  agg_add
+// returns each caller's own starting offset, as atomicAdd would.
+__device__ __forceinline__ uint32_t agg_add(uint32_t* ctr, uint32_t v) {
+    namespace cg = cooperative_groups;
+    cg::coalesced_group g = cg::coalesced_threads();
+    const uint32_t incl = cg::inclusive_scan(g, v);
+    uint32_t base = 0;
+    if (g.thread_rank() == g.size() - 1) base = atomicAdd(ctr, incl);
+    base = g.shfl(base, g.size() - 1);
+    return base + incl - v;
+}
+__device__ __forceinline__ void agg_count(unsigned long long* ctr, unsigned long long v) {
+    namespace cg = cooperative_groups;
+    cg::coalesced_group g = cg::coalesced_threads();
+    const unsigned long long s = cg::reduce(g, v, cg::plus<unsigned long long>());
+    if (g.thread_rank() == 0 && s) atomicAdd(ctr, s);
+}
 
 // change kinds applied to a CSR
 enum : uint8_t { CHG_INS = 0, CHG_DEL = 1, CHG_SETW = 2 };

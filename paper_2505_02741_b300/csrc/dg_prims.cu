@@ -9,11 +9,7 @@
 // PRIM_ERR_SPIN and stops waiting, so no kernel here can hang.
 #include "dg_prims.cuh"
 
-#include <cooperative_groups.h>
-
 namespace dg {
-
-namespace cg = cooperative_groups;
 
 thread_local uint64_t g_launches = 0;
 
@@ -202,115 +198,6 @@ __global__ void __launch_bounds__(LB_THREADS) k_scan_lookback(ScanArgs a, const 
     }
 }
 
-// ---------------------------------------------------------------------------
-// cluster scan (n <= 65536): the eight CTAs of one thread-block cluster split
-// the array, exchange per-CTA totals through distributed shared memory and
-// finish in one launch, with no look-back and no status memset.  The cluster's
-// CTAs are co-scheduled, so its barriers cannot wait on a CTA that never runs.
-// ---------------------------------------------------------------------------
-constexpr int CL_CTAS = 8;
-
-constexpr int CSC_THREADS = 1024;
-constexpr int CSC_ITEMS = 8;
-constexpr uint32_t CSC_PER_CTA = CSC_THREADS * CSC_ITEMS;  // 8192
-constexpr uint32_t CSC_MAX = CL_CTAS * CSC_PER_CTA;          // 65536
-constexpr uint32_t CSC_BUF = CSC_PER_CTA + CSC_PER_CTA / 32; // one pad word per 32
-constexpr size_t CSC_SMEM = 3ull * CSC_BUF * 4;
-
-// padded shared-memory slot of element e: a thread's 8 consecutive elements
-// then fall in distinct banks across the warp
-__device__ __forceinline__ uint32_t csc_slot(uint32_t e) { return e + (e >> 5); }
-
-// Global memory is read and written coalesced (element i * 1024 + thread);
-// each thread scans 8 consecutive elements out of shared memory.
-__global__ void __cluster_dims__(CL_CTAS, 1, 1) __launch_bounds__(CSC_THREADS)
-    k_scan_cluster(ScanArgs a, const uint32_t* d_n, uint32_t n_max) {
-    extern __shared__ __align__(16) uint32_t csc_buf[];  // [3][CSC_BUF]
-    __shared__ uint32_t sh[3][32];
-    __shared__ uint32_t s_agg[3];  // this CTA's total per array (read by the cluster)
-    __shared__ uint32_t s_pre[3], s_tot[3];
-    cg::cluster_group cl = cg::this_cluster();
-    const uint32_t c = cl.block_rank();
-    const uint32_t n = load_n(d_n, n_max);
-    const uint32_t base = c * CSC_PER_CTA;
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    for (int j = 0; j < a.k; ++j) {
-        uint32_t* buf = csc_buf + j * CSC_BUF;
-#pragma unroll
-        for (int i = 0; i < CSC_ITEMS; ++i) {
-            const uint32_t e = i * CSC_THREADS + threadIdx.x;
-            buf[csc_slot(e)] = (base + e < n) ? a.in[j][base + e] : 0u;
-        }
-    }
-    __syncthreads();
-    uint32_t ts[3], wx[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        ts[j] = 0;
-        wx[j] = 0;
-        if (j >= a.k) continue;
-        const uint32_t* buf = csc_buf + j * CSC_BUF;
-#pragma unroll
-        for (int i = 0; i < CSC_ITEMS; ++i) ts[j] += buf[csc_slot(threadIdx.x * CSC_ITEMS + i)];
-        uint32_t x = ts[j];
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (l >= o) x += y;
-        }
-        wx[j] = x;
-        if (l == 31) sh[j][w] = x;
-    }
-    __syncthreads();
-    if (w < a.k) {  // warp j scans the 32 warp totals of array j
-        uint32_t t = sh[w][l];
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
-            if (l >= o) t += y;
-        }
-        sh[w][l] = t;
-        if (l == 31) s_agg[w] = t;
-    }
-    cl.sync();
-    if (threadIdx.x < 3) {
-        const int j = threadIdx.x;
-        uint32_t pre = 0, tot = 0;
-        if (j < a.k)
-            for (uint32_t r = 0; r < CL_CTAS; ++r) {
-                const uint32_t x = *cl.map_shared_rank(&s_agg[j], r);
-                if (r < c) pre += x;
-                tot += x;
-            }
-        s_pre[j] = pre;
-        s_tot[j] = tot;
-    }
-    __syncthreads();
-    // exclusive values back into shared memory, then coalesced stores
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        if (j >= a.k) continue;
-        uint32_t* buf = csc_buf + j * CSC_BUF;
-        uint32_t run = s_pre[j] + ((w > 0) ? sh[j][w - 1] : 0u) + wx[j] - ts[j];
-#pragma unroll
-        for (int i = 0; i < CSC_ITEMS; ++i) {
-            const uint32_t q = csc_slot(threadIdx.x * CSC_ITEMS + i);
-            const uint32_t x = buf[q];
-            buf[q] = run;
-            run += x;
-        }
-    }
-    __syncthreads();
-    for (int j = 0; j < a.k; ++j) {
-        const uint32_t* buf = csc_buf + j * CSC_BUF;
-#pragma unroll
-        for (int i = 0; i < CSC_ITEMS; ++i) {
-            const uint32_t e = i * CSC_THREADS + threadIdx.x;
-            if (base + e < n) a.out[j][base + e] = buf[csc_slot(e)];
-        }
-        if (c == 0 && threadIdx.x == 0 && a.total[j]) *a.total[j] = s_tot[j];
-    }
-    cl.sync();  // no CTA leaves while another may still read its s_agg
-}
-
 void scan_exclusive(const ScanJob& job, const uint32_t* d_n, uint32_t n_max, uint32_t* tmp,
                     cudaStream_t st) {
     ScanArgs a;
@@ -323,11 +210,6 @@ void scan_exclusive(const ScanJob& job, const uint32_t* d_n, uint32_t n_max, uin
     a.err = job.err;
     if (n_max <= SMALL_SCAN_MAX) {
         k_scan_single<<<1, 1024, 0, st>>>(a, d_n, n_max);
-        ++g_launches;
-        return;
-    }
-    if (n_max <= CSC_MAX) {
-        k_scan_cluster<<<CL_CTAS, CSC_THREADS, CSC_SMEM, st>>>(a, d_n, n_max);
         ++g_launches;
         return;
     }
@@ -516,15 +398,10 @@ __global__ void __launch_bounds__(OS_THREADS) k_os_pass(const uint64_t* __restri
     }
 }
 
-void prims_init() {
-    cudaFuncSetAttribute(k_scan_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CSC_SMEM);
-}
-
 bool radix_sort_pairs(const SortBufs& b, const uint32_t* d_n, uint32_t n_max, int nbits,
                       cudaStream_t st) {
     if (n_max == 0 || nbits <= 0) return false;
     const int passes = (nbits + 7) / 8;
-
     const uint32_t tiles = os_tiles(n_max);
     // digit totals and tile counters, then per pass a cleared status area
     const bool separate = os_separate(tiles);

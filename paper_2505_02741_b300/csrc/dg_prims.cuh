@@ -45,9 +45,6 @@ bool radix_sort_pairs(const SortBufs& b, const uint32_t* d_n, uint32_t n_max, in
 
 int bit_length(uint64_t x);
 
-// once per device before the first sort (large shared-memory opt-in of the cluster sort)
-void prims_init();
-
 // kernel launches issued by this thread (the benchmark's launch tally)
 extern thread_local uint64_t g_launches;
 

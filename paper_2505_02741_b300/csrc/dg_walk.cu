@@ -486,6 +486,7 @@ __global__ void k_walk_reduce(WalkTasks t, WalkParams p, WalkRecs r, dg_update_r
     const int lane = threadIdx.x & 31;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    unsigned long long c_steps = 0, c_walked = 0, c_hits = 0, c_acc = 0;  // this warp's totals (lane 0)
     for (uint32_t j = warp; j < W; j += nwarps) {
         const bool ins = t.kind[j] == WALK_INS;
         const bool ee = ins && p.early_exit;
@@ -560,11 +561,17 @@ __global__ void k_walk_reduce(WalkTasks t, WalkParams p, WalkRecs r, dg_update_r
             o.r_est = nh > 0 ? bR : INFINITY;
             o.accepted = ins && nh == 0;
             best[j] = bk;
-            atomicAdd(&ctr->steps, (unsigned long long)tot);
-            atomicAdd(&ctr->walked, 1ull);
-            if (nh > 0) atomicAdd(&ctr->hits, 1ull);
-            if (ins && nh == 0) atomicAdd(&ctr->accepted, 1ull);
+            c_steps += tot;
+            c_walked += 1;
+            c_hits += nh > 0 ? 1 : 0;
+            c_acc += (ins && nh == 0) ? 1 : 0;
         }
+    }
+    if (lane == 0 && c_walked) {
+        atomicAdd(&ctr->steps, c_steps);
+        atomicAdd(&ctr->walked, c_walked);
+        if (c_hits) atomicAdd(&ctr->hits, c_hits);
+        if (c_acc) atomicAdd(&ctr->accepted, c_acc);
     }
 }
 
@@ -585,7 +592,7 @@ void launch_walk_reduce(const WalkTasks& t, const WalkParams& p, const WalkRecs&
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void emit_edge(Cands& c, uint32_t x, uint32_t y, double w, uint32_t n,
                                           uint32_t* d_err) {
-    const uint32_t pos = atomicAdd(c.count, 2u);
+    const uint32_t pos = agg_add(c.count, 2u);
     if (pos + 2 > c.cap) {
         atomicOr(d_err, (uint32_t)ERR_CAP_COMMIT);
         return;

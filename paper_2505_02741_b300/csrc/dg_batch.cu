@@ -262,10 +262,15 @@ __device__ uint64_t r_limit_bits(double wpq, double K) {
 __global__ void k_make_tasks(const dg_update* __restrict__ ups, const uint8_t* __restrict__ wkind,
                              const uint32_t* __restrict__ pdel, const uint32_t* __restrict__ pins,
                              const uint32_t* __restrict__ totals, const BatchHdr* hdr, uint32_t b_max, double K,
-                             WalkTasks t) {
+                             WalkTasks t, uint32_t* __restrict__ fin, uint32_t* __restrict__ queue,
+                             uint32_t* __restrict__ qctr) {
     const uint32_t nu = min(hdr->nu, b_max);
     const uint32_t ndel = totals[0];
-    if (blockIdx.x == 0 && threadIdx.x == 0) *t.count = ndel + totals[1];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *t.count = ndel + totals[1];
+        qctr[0] = 0;
+        qctr[1] = 0;
+    }
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nu; i += gridDim.x * blockDim.x) {
         const uint8_t k = wkind[i];
         if (k == WALK_NONE) continue;
@@ -275,6 +280,8 @@ __global__ void k_make_tasks(const dg_update* __restrict__ ups, const uint8_t* _
         t.v[j] = (uint32_t)up.v;
         t.idx[j] = i;
         t.wpq[j] = k == WALK_INS ? up.w : 0.0;
+        fin[j] = 0;
+        queue[j] = 0xFFFFFFFFu;
         t.rmax[j] = k == WALK_INS ? r_limit_bits(up.w, K) : ~0ull;
         t.kind[j] = k;
     }
@@ -313,6 +320,7 @@ uint64_t BatchWS::bytes() const {
     b += gscan.bytes() + gcount.bytes() + hflag.bytes() + hpos.bytes() + hvals.bytes() + hcount.bytes();
     b += gkind.bytes() + ghrem.bytes() + kind_del.bytes() + gw.bytes();
     b += t_u.bytes() + t_v.bytes() + t_idx.bytes() + t_kstar.bytes() + t_count.bytes() + meta.bytes();
+    b += t_fin.bytes() + t_queue.bytes() + qctr.bytes();
     b += t_wpq.bytes() + t_rmax.bytes() + recR.bytes() + t_kind.bytes() + best.bytes();
     b += ckeys.bytes() + ckeys_alt.bytes() + ck2.bytes() + cvals.bytes() + cvals_alt.bytes() + chist.bytes();
     b += cscan.bytes() + ccount.bytes() + cflag.bytes() + cpos.bytes() + cv2.bytes() + ccount2.bytes();
@@ -392,6 +400,9 @@ static void ensure_ws(Ctx& c, DGraph& g, uint32_t b_max, cudaStream_t st) {
     w.t_v.ensure(a, B, st);
     w.t_idx.ensure(a, B, st);
     w.t_kstar.ensure(a, B, st);
+    w.t_fin.ensure(a, B, st);
+    w.t_queue.ensure(a, B, st);
+    w.qctr.ensure(a, 2, st);
     w.t_count.ensure(a, 4, st);
     w.t_wpq.ensure(a, B, st);
     w.t_rmax.ensure(a, B, st);
@@ -702,7 +713,7 @@ void graph_release_ws(Ctx& c, DGraph& g, cudaStream_t st) {
     REL(vvals_alt); REL(vhist); REL(vscan); REL(wkind); REL(fin_w); REL(wflag); REL(wpos); REL(wflag2); REL(wpos2); REL(gkeys);
     REL(gkeys_alt); REL(hkeys); REL(gvals); REL(gvals_alt); REL(ghist); REL(gscan); REL(gcount); REL(hflag);
     REL(hpos); REL(hvals); REL(hcount); REL(gkind); REL(ghrem); REL(kind_del); REL(gw); REL(t_u); REL(t_v);
-    REL(t_idx); REL(t_kstar); REL(t_count); REL(meta); REL(t_wpq); REL(t_rmax); REL(recR); REL(t_kind); REL(best);
+    REL(t_idx); REL(t_kstar); REL(t_fin); REL(t_queue); REL(qctr); REL(t_count); REL(meta); REL(t_wpq); REL(t_rmax); REL(recR); REL(t_kind); REL(best);
     REL(ckeys); REL(ckeys_alt); REL(ck2); REL(cvals); REL(cvals_alt); REL(chist); REL(cscan); REL(ccount);
     REL(cflag); REL(cpos); REL(cv2); REL(ccount2); REL(cw); REL(kind_ins); REL(path_buf); REL(path_w); REL(path_len); REL(fb_list); REL(fb_count); REL(dbg_reason);
     REL(dbg_steps); REL(dbg_paths);
@@ -739,6 +750,37 @@ static WalkParams params_of(const Config& cfg) {
     p.key0 = (uint32_t)cfg.seed;
     p.key1 = (uint32_t)(cfg.seed >> 32);
     return p;
+}
+
+static Cands cands_of(BatchWS& w) {
+    Cands cd;
+    cd.keys = w.ckeys.p;
+    cd.vals = w.cvals.p;
+    cd.w = w.cw.p;
+    cd.count = w.ccount.p;
+    cd.cap = w.cand_cap;
+    return cd;
+}
+
+static PathBufs paths_of(BatchWS& w) {
+    return PathBufs{w.path_buf.p, w.path_w.p, w.path_len.p, w.fb_list.p, w.fb_count.p};
+}
+
+static FinArgs fin_of(Ctx& c, BatchWS& w, bool on) {
+    FinArgs f;
+    f.res = w.res.p;
+    f.best = w.best.p;
+    f.ctr = w.ctr.p;
+    f.dbg_reason = c.cfg.record ? w.dbg_reason.p : nullptr;
+    f.dbg_steps = c.cfg.record ? w.dbg_steps.p : nullptr;
+    f.fin = w.t_fin.p;
+    f.queue = w.t_queue.p;
+    f.qctr = w.qctr.p;
+    f.fin_w = w.fin_w.p;
+    f.c = cands_of(w);
+    f.pb = paths_of(w);
+    f.on = on ? 1u : 0u;
+    return f;
 }
 
 static WalkRecs recs_of(Ctx& c, BatchWS& w) {
@@ -809,7 +851,7 @@ static void enqueue_mutate(Ctx& c, DGraph& g, cudaStream_t st) {
     }
     WalkTasks tasks = tasks_of(w);
     k_make_tasks<<<grid_for(B), BT, 0, sd>>>(w.ups.p, w.wkind.p, w.wpos.p, w.wpos2.p, w.t_count.p + 2, w.hdr.p, B,
-                                            c.cfg.K, tasks);
+                                            c.cfg.K, tasks, w.t_fin.p, w.t_queue.p, w.qctr.p);
     ++g_launches;
     // net G changes, sorted by (vertex, neighbour)
     SortBufs gs{w.gkeys.p, w.gvals.p, w.gkeys_alt.p, w.gvals_alt.p, w.ghist.p, w.gscan.p, w.err.p};
@@ -858,28 +900,39 @@ static void enqueue_mutate(Ctx& c, DGraph& g, cudaStream_t st) {
     DG_CUDA(record_event(g.ev[4], st));
 }
 
-// walks on the snapshot (H' for insertions, G_b for deletions) and the
-// per-update reduction; per_update_W >= 0 selects the one-launch-per-update form
-static void enqueue_walks(Ctx& c, DGraph& g, cudaStream_t st, int64_t per_update_W) {
+// Walks on the snapshot (H' for insertions, G_b for deletions) and the
+// per-update reduction; per_update_W >= 0 selects the one-launch-per-update
+// form.  A single batched launch also finalizes every update (reduction,
+// argmin path, commit candidates) in the walk's tail; returns true then, and
+// the commit only adds the fallbacks left to the block-wide kernel.
+static bool enqueue_walks(Ctx& c, DGraph& g, cudaStream_t st, int64_t per_update_W) {
     BatchWS& w = g.ws;
     const WalkParams wp = params_of(c.cfg);
     const WalkRecs wr = recs_of(c, w);
     const WalkTasks tasks = tasks_of(w);
+    const uint32_t cut = g.shape.cut > 1 ? (uint32_t)g.shape.cut : 1u;
+    const bool fused = per_update_W < 0 && cut == 1;
+    if (fused) {
+        DG_CUDA(cudaMemsetAsync(w.ccount.p, 0, 4, st));
+        DG_CUDA(cudaMemsetAsync(w.fb_count.p, 0, 4, st));
+    }
     DG_CUDA(record_event(g.ev[0], st));
     if (per_update_W < 0) {
-        const uint32_t cut = g.shape.cut > 1 ? (uint32_t)g.shape.cut : 1u;
-        for (uint32_t c = 0; c < cut; ++c)
+        for (uint32_t c2 = 0; c2 < cut; ++c2)
             launch_walk_batched(g.H.view(), g.G.view(), tasks, wp, wr, w.hdr.p, w.next.p,
-                                (uint32_t)((uint64_t)w.b_max * c / cut), (uint32_t)((uint64_t)w.b_max * (c + 1) / cut),
-                                g.shape, w.err.p, st);
+                                (uint32_t)((uint64_t)w.b_max * c2 / cut),
+                                (uint32_t)((uint64_t)w.b_max * (c2 + 1) / cut), g.shape, fin_of(c, w, fused),
+                                w.err.p, st);
     } else {
         for (int64_t j = 0; j < per_update_W; ++j)
             launch_walk_one(g.H.view(), g.G.view(), tasks, wp, wr, w.hdr.p, (uint32_t)j, w.err.p, st);
     }
     DG_CUDA(record_event(g.ev[1], st));
-    launch_walk_reduce(tasks, wp, wr, w.res.p, w.best.p, w.ctr.p, c.cfg.record ? w.dbg_reason.p : nullptr,
-                       c.cfg.record ? w.dbg_steps.p : nullptr, w.b_max, w.err.p, st);
+    if (!fused)
+        launch_walk_reduce(tasks, wp, wr, w.res.p, w.best.p, w.ctr.p, c.cfg.record ? w.dbg_reason.p : nullptr,
+                           c.cfg.record ? w.dbg_steps.p : nullptr, w.b_max, w.err.p, st);
     DG_CUDA(record_event(g.ev[5], st));
+    return fused;
 }
 
 // Autotuner: after the mutation of one large batch, time the walk phase on
@@ -905,7 +958,8 @@ static void autotune_walks(Ctx& c, DGraph& g, cudaStream_t st) {
         for (int cidx = 0; cidx < sh.cut; ++cidx)
             launch_walk_batched(g.H.view(), g.G.view(), tasks, wp, wr, w.hdr.p, w.next.p,
                                 (uint32_t)((uint64_t)w.b_max * cidx / sh.cut),
-                                (uint32_t)((uint64_t)w.b_max * (cidx + 1) / sh.cut), sh, w.err.p, st);
+                                (uint32_t)((uint64_t)w.b_max * (cidx + 1) / sh.cut), sh, fin_of(c, w, false),
+                                w.err.p, st);
         DG_CUDA(cudaEventRecord(e1, st));
         wait_stream(c, st);
         float ms = 0.f;
@@ -939,15 +993,6 @@ static void autotune_walks(Ctx& c, DGraph& g, cudaStream_t st) {
             best = sh;
         }
     }
-    for (int cut : {2, 4}) {
-        WalkShape sh = best;
-        sh.cut = cut;
-        const float ms = median3(sh);
-        if (ms < best_ms * 0.97f) {
-            best_ms = ms;
-            best = sh;
-        }
-    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c.alloc.put(flush, flush_bytes, st);
@@ -958,19 +1003,20 @@ static void autotune_walks(Ctx& c, DGraph& g, cudaStream_t st) {
     ++g.layout_gen;
 }
 
-// kept insertions, recovered and fallback edges -> H (re-runnable)
-static void enqueue_commit(Ctx& c, DGraph& g, cudaStream_t st) {
+// kept insertions, recovered and fallback edges -> H (re-runnable).  After a
+// finalizing walk (walk_emitted) the candidates are already there except the
+// fallbacks at long lists; otherwise they are generated here from the results.
+static void enqueue_commit(Ctx& c, DGraph& g, cudaStream_t st, bool walk_emitted) {
     BatchWS& w = g.ws;
     const uint32_t B = w.b_max, n = (uint32_t)g.n, CC = w.cand_cap;
-    DG_CUDA(cudaMemsetAsync(w.ccount.p, 0, 4, st));
-    Cands cd;
-    cd.keys = w.ckeys.p;
-    cd.vals = w.cvals.p;
-    cd.w = w.cw.p;
-    cd.count = w.ccount.p;
-    cd.cap = CC;
-    launch_emit(g.H.view(), g.G.view(), tasks_of(w), params_of(c.cfg), recs_of(c, w), w.hdr.p, w.best.p, w.fin_w.p,
-                w.res.p, w.ctr.p, cd, PathBufs{w.path_buf.p, w.path_w.p, w.path_len.p, w.fb_list.p, w.fb_count.p}, B, w.err.p, st);
+    const Cands cd = cands_of(w);
+    if (walk_emitted) {
+        launch_fallback(g.H.view(), g.G.view(), tasks_of(w), w.res.p, w.ctr.p, cd, paths_of(w), B, w.err.p, st);
+    } else {
+        DG_CUDA(cudaMemsetAsync(w.ccount.p, 0, 4, st));
+        launch_emit(g.H.view(), g.G.view(), tasks_of(w), params_of(c.cfg), recs_of(c, w), w.hdr.p, w.best.p,
+                    w.fin_w.p, w.res.p, w.ctr.p, cd, paths_of(w), B, w.err.p, st);
+    }
     DG_CUDA(record_event(g.ev[6], st));
     SortBufs cs{w.ckeys.p, w.cvals.p, w.ckeys_alt.p, w.cvals_alt.p, w.chist.p, w.cscan.p, w.err.p};
     const bool calt = radix_sort_pairs(cs, w.ccount.p, CC, bit_length((uint64_t)n * n - 1), st);
@@ -1088,6 +1134,7 @@ void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_updat
         else
             DG_CUDA(cudaMemcpyAsync(w.ups.p, ups, sizeof(dg_update) * nu, cudaMemcpyDeviceToDevice, st));
     };
+    bool walk_emitted = false;  // the last walk launch also produced the commit candidates
     // eager form of the pre-commit part (validation, mutation, walks, reduction)
     auto run_pre = [&]() {
         enqueue_mutate(c, g, st);
@@ -1099,10 +1146,10 @@ void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_updat
             W = (g.hs.err[0] & ABORT_MASK) ? 0 : g.hs.counts[0];
             if (g.hs.counts[0] > w.b_max) W = 0;
         }
-        enqueue_walks(c, g, st, W);
+        walk_emitted = enqueue_walks(c, g, st, W);
     };
     auto finish_eager = [&]() {
-        enqueue_commit(c, g, st);
+        enqueue_commit(c, g, st, walk_emitted);
         if (!device_io)
             DG_CUDA(cudaMemcpyAsync(g.hs.res, w.res.p, sizeof(dg_update_result) * nu, cudaMemcpyDeviceToHost, st));
         enqueue_readback(g, st);
@@ -1119,7 +1166,7 @@ void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_updat
         stage_inputs();
         enqueue_mutate(c, g, st);
         autotune_walks(c, g, st);
-        enqueue_walks(c, g, st, -1);
+        walk_emitted = enqueue_walks(c, g, st, -1);
         finish_eager();
     } else if (use_graph) {
         if (device_io) DG_CUDA(cudaMemcpyAsync(w.ups.p, ups, sizeof(dg_update) * nu, cudaMemcpyDeviceToDevice, st));
@@ -1135,8 +1182,8 @@ void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_updat
                 if (!device_io)
                     DG_CUDA(cudaMemcpyAsync(w.ups.p, g.hs.ups, sizeof(dg_update) * bucket, cudaMemcpyHostToDevice, st));
                 enqueue_mutate(c, g, st);
-                enqueue_walks(c, g, st, -1);
-                enqueue_commit(c, g, st);
+                const bool emitted = enqueue_walks(c, g, st, -1);
+                enqueue_commit(c, g, st, emitted);
                 if (!device_io)
                     DG_CUDA(cudaMemcpyAsync(g.hs.res, w.res.p, sizeof(dg_update_result) * bucket,
                                             cudaMemcpyDeviceToHost, st));
@@ -1176,9 +1223,10 @@ void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_updat
         if (whole) {
             stage_inputs();
             run_pre();
-        } else {  // only the commit re-runs; walks and their results are kept
+        } else {  // only the commit re-runs; walks and their results are kept, candidates regenerated
             DG_CUDA(cudaMemsetAsync(w.err.p, 0, 16, st));
             DG_CUDA(cudaMemsetAsync(&w.ctr.p->recovered, 0, sizeof(unsigned long long), st));
+            walk_emitted = false;
         }
         finish_eager();
         replayed = false;

@@ -39,8 +39,27 @@ int device_sms() {
 }
 
 constexpr uint32_t NONE = 0xFFFFFFFFu;
+constexpr uint32_t FIN_SPIN_LIMIT = 1u << 22;  // polls of the finalize queue (about 0.5 s) before ERR_SPIN
 
 __device__ __forceinline__ bool walk_aborted(const uint32_t* d_err) { return (*d_err & ABORT_MASK) != 0u; }
+
+// GPU-scope acquire/release operations of the finalize hand-off: a walker's
+// record stores are ordered before its count of the update (release), the last
+// walker's count sees every other walker's records (acquire), its queue store
+// publishes them (release, cumulative) and a worker's queue load acquires them.
+__device__ __forceinline__ uint32_t atom_add_acq_rel(uint32_t* p, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 
 // high 32 bits of a non-negative double (the pruning key)
 __device__ __forceinline__ uint32_t r_key(double R) { return (uint32_t)((unsigned long long)__double_as_longlong(R) >> 32); }
@@ -67,7 +86,286 @@ struct WalkKernelArgs {
     unsigned long long* next;
     uint32_t j_lo, j_hi;
     uint32_t* d_err;
+    FinArgs f;
 };
+
+// ---------------------------------------------------------------------------
+// per-update finalization: device functions shared by the stand-alone kernels
+// and by the finalizing warps of the batched walk.  Walker records written in
+// the same launch are read through L2 (__ldcg), never from a stale L1 line.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void emit_edge(Cands& c, uint32_t x, uint32_t y, double w, uint32_t n,
+                                          uint32_t* d_err) {
+    const uint32_t pos = agg_add(c.count, 2u);
+    if (pos + 2 > c.cap) {
+        atomicOr(d_err, (uint32_t)ERR_CAP_COMMIT);
+        return;
+    }
+    c.keys[pos] = (uint64_t)x * n + y;
+    c.keys[pos + 1] = (uint64_t)y * n + x;
+    c.vals[pos] = pos;
+    c.vals[pos + 1] = pos + 1;
+    c.w[pos] = w;
+    c.w[pos + 1] = w;
+}
+
+struct UpdTotals {
+    unsigned long long steps = 0, walked = 0, hits = 0, acc = 0, rec = 0;
+};
+
+__device__ __forceinline__ void add_totals(BatchCounters* ctr, const UpdTotals& u) {
+    if (u.walked) {
+        atomicAdd(&ctr->steps, u.steps);
+        atomicAdd(&ctr->walked, u.walked);
+    }
+    if (u.hits) atomicAdd(&ctr->hits, u.hits);
+    if (u.acc) atomicAdd(&ctr->accepted, u.acc);
+    if (u.rec) atomicAdd(&ctr->recovered, u.rec);
+}
+
+// Eq. 12 and the cut readings over the s records of walked update j, one
+// warp.  Lane 0 writes the update's result and best[j] and adds to tot; every
+// lane gets the argmin walker (-1 if none) and the number of hits.
+__device__ int reduce_update(uint32_t j, int lane, const WalkTasks& t, const WalkParams& p, const WalkRecs& r,
+                             dg_update_result* res, int32_t* best, int32_t* dbg_reason, int32_t* dbg_steps,
+                             UpdTotals& tot, uint32_t& nh_out) {
+    const bool ins = t.kind[j] == WALK_INS;
+    const bool ee = ins && p.early_exit;
+    const uint32_t i = t.idx[j];
+    const uint32_t* meta = r.meta + (size_t)j * p.s;
+    const double* Rr = r.R + (size_t)j * p.s;
+    uint32_t ks = NONE;
+    for (uint32_t k = lane; k < p.s; k += 32) {
+        const uint32_t m = __ldcg(&meta[k]);
+        if ((m >> 16) == R_HIT) ks = min(ks, m & 0xFFFFu);
+    }
+    for (int o = 16; o > 0; o >>= 1) ks = min(ks, __shfl_xor_sync(0xffffffffu, ks, o));
+    uint32_t nh = 0, tsum = 0, nmin = 0;  // nmin: hits at the lane's minimum bR
+    double bR = INFINITY;
+    int bk = -1;
+    for (uint32_t k = lane; k < p.s; k += 32) {
+        const uint32_t m = __ldcg(&meta[k]);
+        uint32_t st = m & 0xFFFFu, rs = m >> 16;
+        if (ee && ks != NONE && st > ks) {
+            st = ks;
+            rs = R_CUT;
+        }
+        tsum += st;
+        if (rs == R_HIT) {
+            ++nh;
+            const double R = __ldcg(&Rr[k]);
+            if (bk < 0 || R < bR) {  // k ascends per lane: first minimum keeps the lower index
+                bR = R;
+                bk = (int)k;
+                nmin = 1;
+            } else if (R == bR) {
+                ++nmin;
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        nh += __shfl_xor_sync(0xffffffffu, nh, o);
+        tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
+        const double oR = __shfl_xor_sync(0xffffffffu, bR, o);
+        const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
+        const uint32_t on = __shfl_xor_sync(0xffffffffu, nmin, o);
+        if (ok >= 0 && (bk < 0 || oR < bR)) {
+            bR = oR;
+            bk = ok;
+            nmin = on;
+        } else if (ok >= 0 && oR == bR) {
+            bk = min(bk, ok);
+            nmin += on;
+        }
+    }
+    // pruned deletions: the walkers at the minimum are never cut, a hit above it
+    // may or may not have been (scheduling); count and record only the minimum
+    const bool prune = !ins && p.del_prune;
+    if (prune) nh = nmin;
+    if (dbg_reason) {
+        for (uint32_t k = lane; k < p.s; k += 32) {
+            const uint32_t m = __ldcg(&meta[k]);
+            uint32_t st = m & 0xFFFFu, rs = m >> 16;
+            if (ee && ks != NONE && st > ks) {
+                st = ks;
+                rs = R_CUT;
+            }
+            if (prune && rs == R_HIT && __ldcg(&Rr[k]) != bR) rs = R_CUT;
+            dbg_reason[(size_t)i * p.s + k] = (int32_t)rs;
+            dbg_steps[(size_t)i * p.s + k] = (int32_t)st;
+        }
+    }
+    if (lane == 0) {
+        dg_update_result& o = res[i];
+        o.hit = nh > 0;
+        o.nhits = (int32_t)nh;
+        o.best_walker = bk;
+        o.steps = (int32_t)tsum;
+        o.r_est = nh > 0 ? bR : INFINITY;
+        o.accepted = ins && nh == 0;
+        best[j] = bk;
+        tot.steps += tsum;
+        tot.walked += 1;
+        tot.hits += nh > 0 ? 1 : 0;
+        tot.acc += (ins && nh == 0) ? 1 : 0;
+    }
+    nh_out = nh;
+    return bk;
+}
+
+// Replays walker b of walked deletion j on G_b (same counters on the same
+// snapshot give the same path, Section III-C) and stores its vertices and edge
+// weights; false (ERR_INTERNAL) if it does not reach v after the recorded steps.
+__device__ bool replay_path(uint32_t j, int32_t b, const CSRView& G, const WalkTasks& t, const WalkParams& p,
+                            const WalkRecs& r, uint64_t id0, const PathBufs& pb, uint32_t* d_err) {
+    const uint32_t i = t.idx[j];
+    const uint32_t u = t.u[j], v = t.v[j], n = (uint32_t)G.n;
+    const uint32_t steps = __ldcg(&r.meta[(size_t)j * p.s + b]) & 0xFFFFu;
+    if (steps > p.T) {  // records are written by this batch's walk; anything else is an internal error
+        atomicOr(d_err, (uint32_t)ERR_INTERNAL);
+        pb.len[j] = 0;
+        return false;
+    }
+    const uint64_t id = id0 + i;
+    const uint32_t ulo = (uint32_t)id, uhi = (uint32_t)(id >> 32);
+    uint32_t* path = pb.v + (size_t)j * (p.T + 1);
+    double* pw = pb.w + (size_t)j * p.T;
+    uint32_t cv = u, off = G.off[u], deg = G.deg[u], prev = NONE, s = 0;
+    bool pid = false;
+    path[0] = u;
+    for (; s < steps; ++s) {
+        const uint32_t x = philox_word0(s, (uint32_t)b, ulo, uhi, p.key0, p.key1);
+        uint4 h;
+        double2 tl;
+        if (nb_step(G, x, cv, off, deg, prev, pid, h, tl) <= 0 || cv >= n) break;
+        path[s + 1] = cv;
+        pw[s] = tl.y;
+    }
+    if (s != steps || cv != v) {  // a recorded hit must replay to v
+        atomicOr(d_err, (uint32_t)ERR_INTERNAL);
+        pb.len[j] = 0;
+        return false;
+    }
+    pb.len[j] = steps;
+    return true;
+}
+
+// Recovered edges of the replayed path of walked deletion j, one warp: every
+// edge of the walk that did not appear earlier in it and is not in H'.
+// Returns the number emitted (all lanes).
+__device__ uint32_t emit_path_warp(uint32_t j, int lane, const CSRView& H, const WalkParams& p, Cands& c,
+                                   const PathBufs& pb, uint32_t* d_err) {
+    const uint32_t len = pb.len[j];
+    const uint32_t* path = pb.v + (size_t)j * (p.T + 1);
+    uint32_t cnt = 0;
+    for (uint32_t s = lane; s < len; s += 32) {
+        const uint32_t x = path[s], y = path[s + 1];
+        bool dup = false;
+        for (uint32_t s2 = 0; s2 < s && !dup; ++s2) {
+            const uint32_t a0 = path[s2], a1 = path[s2 + 1];
+            dup = (a0 == x && a1 == y) || (a0 == y && a1 == x);
+        }
+        if (dup || has_edge(H, x, y)) continue;
+        emit_edge(c, x, y, pb.w[(size_t)j * p.T + s], (uint32_t)H.n, d_err);
+        ++cnt;
+    }
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    return cnt;
+}
+
+// Fallback of walked deletion j (no walker reached v), one warp: for each
+// endpoint x the G_b edge of minimum resistance not in H' (ties: smaller
+// neighbour id; reading R11).  false when an endpoint list is longer than
+// FB_WARP_MAX (left to the block-wide kernel).
+__device__ bool fallback_warp(uint32_t j, int lane, const CSRView& H, const CSRView& G, const WalkTasks& t,
+                              Cands& c, uint32_t* d_err, uint32_t& emitted) {
+    const uint32_t ends[2] = {t.u[j], t.v[j]};
+    if (G.deg[ends[0]] > FB_WARP_MAX || G.deg[ends[1]] > FB_WARP_MAX) return false;
+    uint32_t py[2];
+    double pw[2];
+#pragma unroll
+    for (int e2 = 0; e2 < 2; ++e2) {
+        const uint32_t x = ends[e2];
+        const Ent* L = G.pool + G.off[x];
+        const uint32_t d = G.deg[x];
+        double br = INFINITY, bw = 0.0;
+        uint32_t by = NONE;
+        for (uint32_t k = lane; k < d; k += 32) {
+            const double rr = L[k].r;
+            if (!(rr < br)) continue;  // this lane's ids ascend: strict < keeps the smaller id
+            const uint32_t y = L[k].nbr;
+            if (has_edge(H, x, y)) continue;
+            br = rr;
+            by = y;
+            bw = L[k].w;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double orr = __shfl_xor_sync(0xffffffffu, br, o);
+            const uint32_t oy = __shfl_xor_sync(0xffffffffu, by, o);
+            const double ow = __shfl_xor_sync(0xffffffffu, bw, o);
+            if (orr < br || (orr == br && oy < by)) {
+                br = orr;
+                by = oy;
+                bw = ow;
+            }
+        }
+        py[e2] = by;
+        pw[e2] = bw;
+    }
+    uint32_t e = 0;
+    if (lane == 0) {
+        for (int e2 = 0; e2 < 2; ++e2) {
+            if (py[e2] == NONE) continue;
+            // both endpoints picked the edge (u, v) itself (it was re-inserted in the batch)
+            if (e2 == 1 && py[0] != NONE && py[0] == ends[1] && py[1] == ends[0]) continue;
+            emit_edge(c, ends[e2], py[e2], pw[e2], (uint32_t)G.n, d_err);
+            ++e;
+        }
+    }
+    emitted = __shfl_sync(0xffffffffu, e, 0);
+    return true;
+}
+
+// everything that follows the walks of update j, one warp: result, kept
+// insertion, or the recovered (path or fallback) edges of a deletion
+__device__ void finalize_update(uint32_t j, int lane, const WalkKernelArgs& a, UpdTotals& tot) {
+    uint32_t nh = 0;
+    const int bk = reduce_update(j, lane, a.t, a.p, a.r, a.f.res, a.f.best, a.f.dbg_reason, a.f.dbg_steps, tot, nh);
+    const uint32_t i = a.t.idx[j];
+    Cands c = a.f.c;
+    if (a.t.kind[j] == WALK_INS) {
+        if (lane == 0) {
+            a.f.pb.len[j] = 0;
+            if (bk < 0 && !isnan(a.f.fin_w[i])) emit_edge(c, a.t.u[j], a.t.v[j], a.f.fin_w[i], (uint32_t)a.G.n, a.d_err);
+        }
+        return;
+    }
+    if (bk >= 0) {
+        bool ok = false;
+        if (lane == 0) ok = replay_path(j, bk, a.G, a.t, a.p, a.r, a.hdr->id0, a.f.pb, a.d_err);
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        __syncwarp();
+        const uint32_t e = ok ? emit_path_warp(j, lane, a.H, a.p, c, a.f.pb, a.d_err) : 0u;
+        if (lane == 0) {
+            a.f.res[i].nrecovered = (int32_t)e;
+            tot.rec += e;
+        }
+    } else {
+        if (lane == 0) {
+            a.f.pb.len[j] = 0;
+            a.f.res[i].fallback = 1;
+        }
+        uint32_t e = 0;
+        if (fallback_warp(j, lane, a.H, a.G, a.t, c, a.d_err, e)) {
+            if (lane == 0) {
+                a.f.res[i].nrecovered = (int32_t)e;
+                tot.rec += e;
+            }
+        } else if (lane == 0) {
+            a.f.pb.fb_list[atomicAdd(a.f.pb.fb_count, 1u)] = j;
+        }
+    }
+}
 
 
 __device__ __forceinline__ void walker_start(Walker& w, const WalkKernelArgs& a, uint32_t wid, uint64_t id0) {
@@ -162,11 +460,17 @@ __device__ __forceinline__ void lean_start(Lean& w, const WalkKernelArgs& a, uin
     if (a.r.paths) a.r.paths[(size_t)wid * (a.p.T + 1)] = (int32_t)u;
 }
 
+// records the walker's stop; with finalization on, the last of an update's s
+// walkers to stop queues the update
 __device__ __forceinline__ void lean_finish(Lean& w, const WalkKernelArgs& a, uint32_t reason) {
     const size_t wid = (size_t)w.j * a.p.s + w.k;
     a.r.meta[wid] = w.steps | (reason << 16);
     a.r.R[wid] = w.R;
     w.active = false;
+    if (a.f.on && atom_add_acq_rel(&a.f.fin[w.j], 1u) == a.p.s - 1u) {
+        const uint32_t pos = atomicAdd(&a.f.qctr[1], 1u);
+        st_release(&a.f.queue[pos], w.j);
+    }
 }
 
 // head (nbr, noff, ndeg, rev) and resistance of the entry at pool index i
@@ -345,6 +649,35 @@ __global__ void __launch_bounds__(256, (ILP == 1 ? 4 : (ILP == 2 ? 3 : 1))) k_wa
             else v.x = philox_word0(v.steps + 1, v.k, v.ulo, v.uhi, a.p.key0, a.p.key1);
         }
     }
+    if (!a.f.on) return;
+    // No walkers left for this warp: finalize queued updates (in order of
+    // completion) until every walked update of the launch is done.  Updates
+    // complete because their walkers belong to warps that are running; the
+    // wait for the next one is still bounded.
+    const uint32_t Wl = W - a.j_lo;
+    UpdTotals tot;
+    for (;;) {
+        uint32_t qi = 0;
+        if (lane == 0) qi = atomicAdd(&a.f.qctr[0], 1u);
+        qi = __shfl_sync(0xffffffffu, qi, 0);
+        if (qi >= Wl) break;
+        uint32_t j = NONE;
+        if (lane == 0) {
+            for (uint32_t spins = 0; spins < FIN_SPIN_LIMIT; ++spins) {
+                j = ld_acquire(&a.f.queue[qi]);
+                if (j != NONE) break;
+                __nanosleep(128);
+            }
+        }
+        j = __shfl_sync(0xffffffffu, j, 0);
+        if (j == NONE) {
+            if (lane == 0) atomicOr(a.d_err, (uint32_t)ERR_SPIN);
+            break;
+        }
+        (void)ld_acquire(&a.f.queue[qi]);  // every lane acquires the records it is about to read
+        finalize_update(j, lane, a, tot);
+    }
+    if (lane == 0) add_totals(a.f.ctr, tot);
 }
 
 // the paper's scheme: one block per walked update, one thread per walker
@@ -386,7 +719,7 @@ __global__ void k_walk_one(WalkKernelArgs a, uint32_t j) {
 static WalkKernelArgs make_args(const CSRView& H, const CSRView& G, const WalkTasks& t, const WalkParams& p,
                                 const WalkRecs& r, const BatchHdr* d_hdr, unsigned long long* d_next,
                                 uint32_t j_lo, uint32_t j_hi, const uint32_t* d_err) {
-    WalkKernelArgs a;
+    WalkKernelArgs a = {};
     a.H = H;
     a.G = G;
     a.t = t;
@@ -451,9 +784,10 @@ static void launch_both(const WalkKernelArgs& a, const WalkShape& shape, cudaStr
 
 void launch_walk_batched(const CSRView& H, const CSRView& G, const WalkTasks& t, const WalkParams& p,
                          const WalkRecs& r, const BatchHdr* d_hdr, unsigned long long* d_next,
-                         uint32_t j_lo, uint32_t j_hi, const WalkShape& shape, const uint32_t* d_err,
-                         cudaStream_t st) {
+                         uint32_t j_lo, uint32_t j_hi, const WalkShape& shape, const FinArgs& f,
+                         const uint32_t* d_err, cudaStream_t st) {
     WalkKernelArgs a = make_args(H, G, t, p, r, d_hdr, d_next, j_lo, j_hi, d_err);
+    a.f = f;
     DG_CUDA(cudaMemsetAsync(d_next, 0, sizeof(unsigned long long), st));
     switch (shape.ilp) {
         case 1: launch_both<1>(a, shape, st); break;
@@ -486,93 +820,12 @@ __global__ void k_walk_reduce(WalkTasks t, WalkParams p, WalkRecs r, dg_update_r
     const int lane = threadIdx.x & 31;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    unsigned long long c_steps = 0, c_walked = 0, c_hits = 0, c_acc = 0;  // this warp's totals (lane 0)
+    UpdTotals tot;  // this warp's totals (lane 0)
     for (uint32_t j = warp; j < W; j += nwarps) {
-        const bool ins = t.kind[j] == WALK_INS;
-        const bool ee = ins && p.early_exit;
-        const uint32_t i = t.idx[j];
-        uint32_t ks = NONE;
-        for (uint32_t k = lane; k < p.s; k += 32) {
-            const uint32_t m = r.meta[(size_t)j * p.s + k];
-            if ((m >> 16) == R_HIT) ks = min(ks, m & 0xFFFFu);
-        }
-        for (int o = 16; o > 0; o >>= 1) ks = min(ks, __shfl_xor_sync(0xffffffffu, ks, o));
-        uint32_t nh = 0, tot = 0, nmin = 0;  // nmin: hits at the lane's minimum bR
-        double bR = INFINITY;
-        int bk = -1;
-        for (uint32_t k = lane; k < p.s; k += 32) {
-            const uint32_t m = r.meta[(size_t)j * p.s + k];
-            uint32_t st = m & 0xFFFFu, rs = m >> 16;
-            if (ee && ks != NONE && st > ks) {
-                st = ks;
-                rs = R_CUT;
-            }
-            tot += st;
-            if (rs == R_HIT) {
-                ++nh;
-                const double R = r.R[(size_t)j * p.s + k];
-                if (bk < 0 || R < bR) {  // k ascends per lane: first minimum keeps the lower index
-                    bR = R;
-                    bk = (int)k;
-                    nmin = 1;
-                } else if (R == bR) {
-                    ++nmin;
-                }
-            }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            nh += __shfl_xor_sync(0xffffffffu, nh, o);
-            tot += __shfl_xor_sync(0xffffffffu, tot, o);
-            const double oR = __shfl_xor_sync(0xffffffffu, bR, o);
-            const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
-            const uint32_t on = __shfl_xor_sync(0xffffffffu, nmin, o);
-            if (ok >= 0 && (bk < 0 || oR < bR)) {
-                bR = oR;
-                bk = ok;
-                nmin = on;
-            } else if (ok >= 0 && oR == bR) {
-                bk = min(bk, ok);
-                nmin += on;
-            }
-        }
-        // pruned deletions: the walkers at the minimum are never cut, a hit above it
-        // may or may not have been (scheduling); count and record only the minimum
-        const bool prune = !ins && p.del_prune;
-        if (prune) nh = nmin;
-        if (dbg_reason) {
-            for (uint32_t k = lane; k < p.s; k += 32) {
-                const uint32_t m = r.meta[(size_t)j * p.s + k];
-                uint32_t st = m & 0xFFFFu, rs = m >> 16;
-                if (ee && ks != NONE && st > ks) {
-                    st = ks;
-                    rs = R_CUT;
-                }
-                if (prune && rs == R_HIT && r.R[(size_t)j * p.s + k] != bR) rs = R_CUT;
-                dbg_reason[(size_t)i * p.s + k] = (int32_t)rs;
-                dbg_steps[(size_t)i * p.s + k] = (int32_t)st;
-            }
-        }
-        if (lane == 0) {
-            dg_update_result& o = res[i];
-            o.hit = nh > 0;
-            o.nhits = (int32_t)nh;
-            o.best_walker = bk;
-            o.steps = (int32_t)tot;
-            o.r_est = nh > 0 ? bR : INFINITY;
-            o.accepted = ins && nh == 0;
-            best[j] = bk;
-            c_steps += tot;
-            c_walked += 1;
-            c_hits += nh > 0 ? 1 : 0;
-            c_acc += (ins && nh == 0) ? 1 : 0;
-        }
+        uint32_t nh;
+        reduce_update(j, lane, t, p, r, res, best, dbg_reason, dbg_steps, tot, nh);
     }
-    if (lane == 0 && c_walked) {
-        atomicAdd(&ctr->steps, c_steps);
-        atomicAdd(&ctr->walked, c_walked);
-        if (c_hits) atomicAdd(&ctr->hits, c_hits);
-        if (c_acc) atomicAdd(&ctr->accepted, c_acc);
-    }
+    if (lane == 0) add_totals(ctr, tot);
 }
 
 void launch_walk_reduce(const WalkTasks& t, const WalkParams& p, const WalkRecs& r, dg_update_result* res,
@@ -590,20 +843,6 @@ void launch_walk_reduce(const WalkTasks& t, const WalkParams& p, const WalkRecs&
 // ---------------------------------------------------------------------------
 // commit candidates: kept insertions, recovered path edges, fallback edges
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void emit_edge(Cands& c, uint32_t x, uint32_t y, double w, uint32_t n,
-                                          uint32_t* d_err) {
-    const uint32_t pos = agg_add(c.count, 2u);
-    if (pos + 2 > c.cap) {
-        atomicOr(d_err, (uint32_t)ERR_CAP_COMMIT);
-        return;
-    }
-    c.keys[pos] = (uint64_t)x * n + y;
-    c.keys[pos + 1] = (uint64_t)y * n + x;
-    c.vals[pos] = pos;
-    c.vals[pos + 1] = pos + 1;
-    c.w[pos] = w;
-    c.w[pos + 1] = w;
-}
 
 // Replay of the argmin walker of every walked deletion that hit: the same
 // counters on the same snapshot give the same path.  One thread per deletion
@@ -618,36 +857,15 @@ __global__ void k_replay(CSRView H, CSRView G, WalkTasks t, WalkParams p, WalkRe
     const uint32_t n = (uint32_t)G.n;
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < W; j += gridDim.x * blockDim.x) {
         const uint32_t i = t.idx[j];
-        const uint32_t u = t.u[j], v = t.v[j];
         pb.len[j] = 0;
         if (t.kind[j] == WALK_INS) {
-            if (best[j] < 0 && !isnan(fin_w[i])) emit_edge(c, u, v, fin_w[i], n, d_err);
+            if (best[j] < 0 && !isnan(fin_w[i])) emit_edge(c, t.u[j], t.v[j], fin_w[i], n, d_err);
             continue;
         }
         res[i].nrecovered = 0;
         const int32_t b = best[j];
         if (b >= 0) {
-            const uint32_t steps = r.meta[(size_t)j * p.s + b] & 0xFFFFu;
-            const uint64_t id = hdr->id0 + i;
-            const uint32_t ulo = (uint32_t)id, uhi = (uint32_t)(id >> 32);
-            uint32_t* path = pb.v + (size_t)j * (p.T + 1);
-            double* pw = pb.w + (size_t)j * p.T;
-            uint32_t cv = u, off = G.off[u], deg = G.deg[u], prev = NONE, s = 0;
-            bool pid = false;
-            path[0] = u;
-            for (; s < steps; ++s) {
-                const uint32_t x = philox_word0(s, (uint32_t)b, ulo, uhi, p.key0, p.key1);
-                uint4 h;
-                double2 tl;
-                if (nb_step(G, x, cv, off, deg, prev, pid, h, tl) <= 0 || cv >= n) break;
-                path[s + 1] = cv;
-                pw[s] = tl.y;
-            }
-            if (s != steps || cv != v) {  // a recorded hit must replay to v
-                atomicOr(d_err, (uint32_t)ERR_INTERNAL);
-                continue;
-            }
-            pb.len[j] = steps;
+            replay_path(j, b, G, t, p, r, hdr->id0, pb, d_err);
         } else {
             // no walker reached v: the fallback edges are chosen by k_fallback
             res[i].fallback = 1;
@@ -774,6 +992,13 @@ void launch_emit(const CSRView& H, const CSRView& G, const WalkTasks& t, const W
     k_emit_path<<<(unsigned)device_sms() * 8, 256, 0, st>>>(H, t, p, res, ctr, c, pb, w_max, d_err);
     k_fallback<<<(unsigned)device_sms() * 4, 256, 0, st>>>(H, G, t, res, ctr, c, pb, w_max, d_err);
     g_launches += 3;
+    DG_CHECK_LAUNCH();
+}
+
+void launch_fallback(const CSRView& H, const CSRView& G, const WalkTasks& t, dg_update_result* res,
+                     BatchCounters* ctr, Cands c, PathBufs pb, uint32_t w_max, uint32_t* d_err, cudaStream_t st) {
+    k_fallback<<<(unsigned)device_sms() * 4, 256, 0, st>>>(H, G, t, res, ctr, c, pb, w_max, d_err);
+    ++g_launches;
     DG_CHECK_LAUNCH();
 }
 

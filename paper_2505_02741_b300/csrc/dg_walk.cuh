@@ -51,11 +51,6 @@ struct WalkShape {
     int cut = 1;            // persistent launches the walked updates are split over
 };
 
-// batched persistent walk over walked updates [j_lo, j_hi) of the task list
-void launch_walk_batched(const CSRView& H, const CSRView& G, const WalkTasks& t, const WalkParams& p,
-                         const WalkRecs& r, const BatchHdr* d_hdr, unsigned long long* d_next,
-                         uint32_t j_lo, uint32_t j_hi, const WalkShape& shape, const uint32_t* d_err,
-                         cudaStream_t st);
 // one launch per walked update j (block of s threads), the paper's scheme
 void launch_walk_one(const CSRView& H, const CSRView& G, const WalkTasks& t, const WalkParams& p,
                      const WalkRecs& r, const BatchHdr* d_hdr, uint32_t j, const uint32_t* d_err,
@@ -94,6 +89,39 @@ struct PathBufs {
     uint32_t* fb_list;   // walked deletions without a hit (fallback), appended
     uint32_t* fb_count;
 };
+
+// Per-update finalization done by the batched walk itself: the walker that
+// finishes last for an update queues it, and warps left without walkers take
+// queued updates and run the reduction (Eq. 12), the replay of the argmin
+// path, the recovered, kept and fallback edges while the walk's long tail is
+// still running.  Fallbacks at an endpoint with more than FB_WARP_MAX
+// neighbours are left to the block-wide fallback kernel.
+constexpr uint32_t FB_WARP_MAX = 1024;
+struct FinArgs {
+    dg_update_result* res;
+    int32_t* best;
+    BatchCounters* ctr;
+    int32_t* dbg_reason;  // optional debug records
+    int32_t* dbg_steps;
+    uint32_t* fin;        // per walked update: walkers finished
+    uint32_t* queue;      // walked updates in order of completion (0xFFFFFFFF until written)
+    uint32_t* qctr;       // [0] next queue slot to take, [1] next queue slot to fill
+    const double* fin_w;  // final G_b weight of a kept insertion (NaN if not in G_b)
+    Cands c;
+    PathBufs pb;
+    uint32_t on;          // 0: records only (reduction and emission run as separate kernels)
+};
+
+// batched persistent walk over walked updates [j_lo, j_hi) of the task list;
+// with f.on (one launch over all updates) it also finalizes every update
+void launch_walk_batched(const CSRView& H, const CSRView& G, const WalkTasks& t, const WalkParams& p,
+                         const WalkRecs& r, const BatchHdr* d_hdr, unsigned long long* d_next,
+                         uint32_t j_lo, uint32_t j_hi, const WalkShape& shape, const FinArgs& f,
+                         const uint32_t* d_err, cudaStream_t st);
+
+// the fallback edges of deletions the finalizing walk left to the block-wide kernel
+void launch_fallback(const CSRView& H, const CSRView& G, const WalkTasks& t, dg_update_result* res,
+                     BatchCounters* ctr, Cands c, PathBufs pb, uint32_t w_max, uint32_t* d_err, cudaStream_t st);
 
 // recovered path edges / fallback edges of walked deletions, kept insertions
 void launch_emit(const CSRView& H, const CSRView& G, const WalkTasks& t, const WalkParams& p,

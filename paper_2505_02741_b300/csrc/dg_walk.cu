@@ -250,6 +250,55 @@ __device__ bool replay_path(uint32_t j, int32_t b, const CSRView& G, const WalkT
     return true;
 }
 
+// The same replay split over the warp: lane q takes the steps after resume
+// point q (q = 0: the start), so the chain of dependent loads is one spacing
+// long instead of the whole path.  Returns the success flag (all lanes).
+__device__ bool replay_path_warp(uint32_t j, int32_t b, int lane, const CSRView& G, const WalkTasks& t,
+                                 const WalkParams& p, const WalkRecs& r, uint64_t id0, const PathBufs& pb,
+                                 const FinArgs& f, uint32_t* d_err) {
+    const uint32_t i = t.idx[j];
+    const uint32_t u = t.u[j], v = t.v[j], n = (uint32_t)G.n;
+    const uint32_t steps = __ldcg(&r.meta[(size_t)j * p.s + b]) & 0xFFFFu;
+    bool ok = steps <= p.T;
+    const uint64_t id = id0 + i;
+    const uint32_t ulo = (uint32_t)id, uhi = (uint32_t)(id >> 32);
+    uint32_t* path = pb.v + (size_t)j * (p.T + 1);
+    double* pw = pb.w + (size_t)j * p.T;
+    const uint32_t span = 1u << f.cp_shift;
+    const uint32_t nseg = ok ? (steps + span - 1) >> f.cp_shift : 0u;
+    if (lane == 0) path[0] = u;
+    for (uint32_t q = lane; q < nseg; q += 32) {
+        uint32_t cv = u, off = G.off[u], deg = G.deg[u], prev = NONE;
+        bool pid = false;
+        if (q > 0) {
+            const uint4 st = __ldcg(&f.cp[((size_t)j * p.s + b) * f.ncp + q - 1]);
+            cv = st.x;
+            off = st.y;
+            deg = st.z;
+            prev = st.w & 0x7FFFFFFFu;
+            pid = (st.w >> 31) != 0u;
+        }
+        const uint32_t s0 = q << f.cp_shift, s1 = min(steps, s0 + span);
+        uint32_t s = s0;
+        for (; s < s1; ++s) {
+            const uint32_t x = philox_word0(s, (uint32_t)b, ulo, uhi, p.key0, p.key1);
+            uint4 h;
+            double2 tl;
+            if (nb_step(G, x, cv, off, deg, prev, pid, h, tl) <= 0 || cv >= n) break;
+            path[s + 1] = cv;
+            pw[s] = tl.y;
+        }
+        if (s != s1 || (s1 == steps && cv != v)) ok = false;  // a recorded hit must replay to v
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    if (lane == 0) {
+        if (!ok) atomicOr(d_err, (uint32_t)ERR_INTERNAL);
+        pb.len[j] = ok ? steps : 0u;
+    }
+    __syncwarp();
+    return ok;
+}
+
 // Recovered edges of the replayed path of walked deletion j, one warp: every
 // edge of the walk that did not appear earlier in it and is not in H'.
 // Returns the number emitted (all lanes).
@@ -342,9 +391,13 @@ __device__ void finalize_update(uint32_t j, int lane, const WalkKernelArgs& a, U
     }
     if (bk >= 0) {
         bool ok = false;
-        if (lane == 0) ok = replay_path(j, bk, a.G, a.t, a.p, a.r, a.hdr->id0, a.f.pb, a.d_err);
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        __syncwarp();
+        if (a.f.cp) {
+            ok = replay_path_warp(j, bk, lane, a.G, a.t, a.p, a.r, a.hdr->id0, a.f.pb, a.f, a.d_err);
+        } else {
+            if (lane == 0) ok = replay_path(j, bk, a.G, a.t, a.p, a.r, a.hdr->id0, a.f.pb, a.d_err);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            __syncwarp();
+        }
         const uint32_t e = ok ? emit_path_warp(j, lane, a.H, a.p, c, a.f.pb, a.d_err) : 0u;
         if (lane == 0) {
             a.f.res[i].nrecovered = (int32_t)e;
@@ -628,6 +681,12 @@ __global__ void __launch_bounds__(256, (ILP == 1 ? 4 : (ILP == 2 ? 3 : 1))) k_wa
                 v.prev = h[i].w;
             }
             if (a.r.paths) a.r.paths[((size_t)v.j * a.p.s + v.k) * (a.p.T + 1) + v.steps] = (int32_t)v.c;
+            if (a.f.cp && !v.ins && (v.steps & ((1u << a.f.cp_shift) - 1u)) == 0u) {
+                const uint32_t q = (v.steps >> a.f.cp_shift) - 1u;
+                if (q < a.f.ncp)
+                    a.f.cp[((size_t)v.j * a.p.s + v.k) * a.f.ncp + q] =
+                        make_uint4(v.c, v.off, v.deg, v.prev | (v.pid ? 0x80000000u : 0u));
+            }
             // reaching v ends the walk whatever R is (hit, or over K for an insertion)
             const bool at_q = v.c == v.q;
             fly[i] = !at_q && v.steps < a.p.T && lean_issue<HUBS>(v, a, h[i], r[i], ks[i], at[i]);

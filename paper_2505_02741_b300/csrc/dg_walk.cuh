@@ -109,8 +109,22 @@ struct FinArgs {
     const double* fin_w;  // final G_b weight of a kept insertion (NaN if not in G_b)
     Cands c;
     PathBufs pb;
+    // resume points of deletion walkers (nullable): the state (vertex, list
+    // offset, degree, previous slot or id | hub flag << 31) after every
+    // 2^cp_shift steps, ncp per walker, so an argmin path replays as parallel
+    // segments instead of one chain of dependent loads
+    uint4* cp;
+    uint32_t cp_shift, ncp;
     uint32_t on;          // 0: records only (reduction and emission run as separate kernels)
 };
+
+// checkpoint spacing for step limit T: a power of two >= 16 giving at most 7 per walker
+inline uint32_t walk_cp_shift(uint32_t T) {
+    uint32_t sh = 4;
+    while (((T + (1u << sh) - 1) >> sh) > 8u) ++sh;
+    return sh;
+}
+inline uint32_t walk_ncp(uint32_t T) { return T == 0 ? 0 : (T - 1) >> walk_cp_shift(T); }
 
 // batched persistent walk over walked updates [j_lo, j_hi) of the task list;
 // with f.on (one launch over all updates) it also finalizes every update

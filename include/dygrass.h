@@ -206,6 +206,9 @@ dg_status dg_init_sparsifier(dg_ctx* ctx, int32_t graph_id, int64_t mh, const in
  * stream to run on (NULL = the context's stream); the call returns after the
  * results are on the host, waiting at most timeout_ms.  nu == 0 is a no-op.
  * Per-update problems are reported in res[i].status; the batch still applies.
+ * Pinned host arrays (cudaMallocHost / cudaHostRegister; both, or ups with
+ * res NULL) are copied straight to and from the device; other host memory goes
+ * through the graph's pinned staging buffers.
  */
 dg_status dg_apply_updates(dg_ctx* ctx, int32_t graph_id, int64_t nu, const dg_update* ups,
                            dg_update_result* res, void* cuda_stream);

@@ -456,6 +456,16 @@ static uint32_t bucket_of(uint64_t nu) {
 // ---------------------------------------------------------------------------
 // load / init / export
 // ---------------------------------------------------------------------------
+// host memory allocated pinned or registered with CUDA (copied without staging)
+static bool host_pinned(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeHost;
+}
+
 static void wait_stream(Ctx& c, cudaStream_t st) {
     cudaEvent_t ev;
     DG_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
@@ -469,11 +479,14 @@ static void wait_stream(Ctx& c, cudaStream_t st) {
             cudaEventDestroy(ev);
             throw Error(DG_E_CUDA, std::string("device error: ") + cudaGetErrorString(e));
         }
-        if (now_ms() - t0 > tmo) {
+        const double t = now_ms() - t0;
+        if (t > tmo) {
             cudaEventDestroy(ev);
             throw Error(DG_E_TIMEOUT, "device work did not finish within timeout_ms");
         }
-        std::this_thread::sleep_for(std::chrono::microseconds(20));
+        // a batch step takes about a millisecond: poll without sleeping at first,
+        // so the caller sees the result within microseconds of the device
+        if (t > 2.0) std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
     cudaEventDestroy(ev);
 }
@@ -1129,14 +1142,26 @@ void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_updat
     g.hs.hdr->nu = nu;
     g.hs.hdr->pad = 0;
     g.hs.hdr->id0 = g.next_id;
-    if (!device_io) std::memcpy(g.hs.ups, ups, sizeof(dg_update) * nu);
+    // Records travel through the pinned staging buffers, or straight between the
+    // caller's buffers and the batch workspace when those are device memory or
+    // pinned host memory (then only nu records are copied, outside the graph).
+    const bool direct = device_io || (host_pinned(ups) && (!res || host_pinned(res)));
+    const cudaMemcpyKind kin = device_io ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind kout = device_io ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (!direct) std::memcpy(g.hs.ups, ups, sizeof(dg_update) * nu);
 
     auto stage_inputs = [&]() {
         DG_CUDA(cudaMemcpyAsync(w.hdr.p, g.hs.hdr, sizeof(BatchHdr), cudaMemcpyHostToDevice, st));
-        if (!device_io)
+        if (!direct)
             DG_CUDA(cudaMemcpyAsync(w.ups.p, g.hs.ups, sizeof(dg_update) * nu, cudaMemcpyHostToDevice, st));
         else
-            DG_CUDA(cudaMemcpyAsync(w.ups.p, ups, sizeof(dg_update) * nu, cudaMemcpyDeviceToDevice, st));
+            DG_CUDA(cudaMemcpyAsync(w.ups.p, ups, sizeof(dg_update) * nu, kin, st));
+    };
+    auto copy_results = [&]() {
+        if (!direct)
+            DG_CUDA(cudaMemcpyAsync(g.hs.res, w.res.p, sizeof(dg_update_result) * nu, cudaMemcpyDeviceToHost, st));
+        else if (res)
+            DG_CUDA(cudaMemcpyAsync(res, w.res.p, sizeof(dg_update_result) * nu, kout, st));
     };
     bool walk_emitted = false;  // the last walk launch also produced the commit candidates
     // eager form of the pre-commit part (validation, mutation, walks, reduction)
@@ -1154,8 +1179,7 @@ void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_updat
     };
     auto finish_eager = [&]() {
         enqueue_commit(c, g, st, walk_emitted);
-        if (!device_io)
-            DG_CUDA(cudaMemcpyAsync(g.hs.res, w.res.p, sizeof(dg_update_result) * nu, cudaMemcpyDeviceToHost, st));
+        copy_results();
         enqueue_readback(g, st);
         DG_CUDA(record_event(g.ev[3], st));
         wait_stream(c, st);
@@ -1173,9 +1197,9 @@ void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_updat
         walk_emitted = enqueue_walks(c, g, st, -1);
         finish_eager();
     } else if (use_graph) {
-        if (device_io) DG_CUDA(cudaMemcpyAsync(w.ups.p, ups, sizeof(dg_update) * nu, cudaMemcpyDeviceToDevice, st));
+        if (direct) DG_CUDA(cudaMemcpyAsync(w.ups.p, ups, sizeof(dg_update) * nu, kin, st));
         CapturedStep& cs = g.steps[bucket];
-        if (!cs.exec || cs.layout_gen != g.layout_gen || cs.device_io != device_io) {
+        if (!cs.exec || cs.layout_gen != g.layout_gen || cs.device_io != direct) {
             if (cs.exec) cudaGraphExecDestroy(cs.exec);
             cs.exec = nullptr;
             cudaGraph_t graph = nullptr;
@@ -1183,12 +1207,12 @@ void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_updat
             DG_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
             try {
                 DG_CUDA(cudaMemcpyAsync(w.hdr.p, g.hs.hdr, sizeof(BatchHdr), cudaMemcpyHostToDevice, st));
-                if (!device_io)
+                if (!direct)
                     DG_CUDA(cudaMemcpyAsync(w.ups.p, g.hs.ups, sizeof(dg_update) * bucket, cudaMemcpyHostToDevice, st));
                 enqueue_mutate(c, g, st);
                 const bool emitted = enqueue_walks(c, g, st, -1);
                 enqueue_commit(c, g, st, emitted);
-                if (!device_io)
+                if (!direct)
                     DG_CUDA(cudaMemcpyAsync(g.hs.res, w.res.p, sizeof(dg_update_result) * bucket,
                                             cudaMemcpyDeviceToHost, st));
                 enqueue_readback(g, st);
@@ -1201,12 +1225,14 @@ void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_updat
             DG_CUDA(cudaGraphInstantiate(&cs.exec, graph, 0));
             cudaGraphDestroy(graph);
             cs.layout_gen = g.layout_gen;
-            cs.device_io = device_io;
+            cs.device_io = direct;
             cs.kernels = g_launches - k0;
             g_launches = k0;  // counted per replay below
         }
         DG_CUDA(cudaGraphLaunch(cs.exec, st));
         g_launches += cs.kernels;
+        if (direct && res)
+            DG_CUDA(cudaMemcpyAsync(res, w.res.p, sizeof(dg_update_result) * nu, kout, st));
         DG_CUDA(record_event(g.ev[3], st));
         wait_stream(c, st);
         replayed = true;
@@ -1235,14 +1261,7 @@ void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_updat
         finish_eager();
         replayed = false;
     }
-    if (res) {
-        if (device_io) {
-            DG_CUDA(cudaMemcpyAsync(res, w.res.p, sizeof(dg_update_result) * nu, cudaMemcpyDeviceToDevice, st));
-            wait_stream(c, st);
-        } else {
-            std::memcpy(res, g.hs.res, sizeof(dg_update_result) * nu);
-        }
-    }
+    if (res && !direct) std::memcpy(res, g.hs.res, sizeof(dg_update_result) * nu);
     g.G.host_top = g.hs.tops[0];
     g.H.host_top = g.hs.tops[1];
     g.next_id += nu;

@@ -513,17 +513,30 @@ __device__ __forceinline__ void lean_start(Lean& w, const WalkKernelArgs& a, uin
     if (a.r.paths) a.r.paths[(size_t)wid * (a.p.T + 1)] = (int32_t)u;
 }
 
-// records the walker's stop; with finalization on, the last of an update's s
-// walkers to stop queues the update
+// records the walker's stop (the finalize count follows in signal_stops)
 __device__ __forceinline__ void lean_finish(Lean& w, const WalkKernelArgs& a, uint32_t reason) {
     const size_t wid = (size_t)w.j * a.p.s + w.k;
     a.r.meta[wid] = w.steps | (reason << 16);
     a.r.R[wid] = w.R;
     w.active = false;
-    if (a.f.on && atom_add_acq_rel(&a.f.fin[w.j], 1u) == a.p.s - 1u) {
+}
+
+// adds cnt stopped walkers to update j; the count that completes it queues j
+__device__ __forceinline__ void count_stops(const WalkKernelArgs& a, uint32_t j, uint32_t cnt) {
+    if (atom_add_acq_rel(&a.f.fin[j], cnt) + cnt == a.p.s) {
         const uint32_t pos = atomicAdd(&a.f.qctr[1], 1u);
-        st_release(&a.f.queue[pos], w.j);
+        st_release(&a.f.queue[pos], j);
     }
+}
+
+// Finalize counts of the walkers that stopped in this iteration, one atomic
+// per (warp, update): the whole warp calls it with its lanes converged; the
+// warp barrier orders every lane's record stores before the leader's release.
+__device__ __forceinline__ void signal_stops(const WalkKernelArgs& a, bool stopped, uint32_t j, int lane) {
+    if (!__any_sync(0xffffffffu, stopped)) return;
+    __syncwarp();
+    const uint32_t peers = __match_any_sync(0xffffffffu, stopped ? j : NONE);
+    if (stopped && lane == __ffs(peers) - 1) count_stops(a, j, (uint32_t)__popc(peers));
 }
 
 // head (nbr, noff, ndeg, rev) and resistance of the entry at pool index i
@@ -644,8 +657,15 @@ __global__ void __launch_bounds__(256, (ILP == 1 ? 4 : (ILP == 2 ? 3 : 1))) k_wa
                     if (id < total) {
                         lean_start(w[i], a, wbase + (uint32_t)id, id0);
                         fly[i] = lean_issue<HUBS>(w[i], a, h[i], r[i], ks[i], at[i]);
-                        if (!fly[i]) lean_finish(w[i], a, R_LEAF);
-                        else w[i].x = philox_word0(1u, w[i].k, w[i].ulo, w[i].uhi, a.p.key0, a.p.key1);
+                        if (!fly[i]) {
+                            lean_finish(w[i], a, R_LEAF);
+                            if (a.f.on) {
+                                __threadfence();
+                                count_stops(a, w[i].j, 1u);
+                            }
+                        } else {
+                            w[i].x = philox_word0(1u, w[i].k, w[i].ulo, w[i].uhi, a.p.key0, a.p.key1);
+                        }
                     } else {
                         exhausted = true;
                     }
@@ -656,10 +676,14 @@ __global__ void __launch_bounds__(256, (ILP == 1 ? 4 : (ILP == 2 ? 3 : 1))) k_wa
 #pragma unroll
         for (int i = 0; i < ILP; ++i) any |= w[i].active;
         if (!__any_sync(0xffffffffu, any)) break;
+        bool stop[ILP];
+#pragma unroll
+        for (int i = 0; i < ILP; ++i) stop[i] = false;
 #pragma unroll
         for (int i = 0; i < ILP; ++i) {
             if (!fly[i]) continue;
             Lean& v = w[i];
+            stop[i] = true;  // cleared below if the walker goes on
             const uint32_t ks_now = ks[i];
             if (v.ins && ks_now <= v.steps) {  // a walker of this update hit at a step <= ours: cut
                 lean_finish(v, a, R_CUT);
@@ -704,8 +728,16 @@ __global__ void __launch_bounds__(256, (ILP == 1 ? 4 : (ILP == 2 ? 3 : 1))) k_wa
             } else if (!fly[i]) {
                 lean_finish(v, a, R_LEAF);
             }
-            if (!v.active) fly[i] = false;
-            else v.x = philox_word0(v.steps + 1, v.k, v.ulo, v.uhi, a.p.key0, a.p.key1);
+            if (!v.active) {
+                fly[i] = false;
+            } else {
+                stop[i] = false;
+                v.x = philox_word0(v.steps + 1, v.k, v.ulo, v.uhi, a.p.key0, a.p.key1);
+            }
+        }
+        if (a.f.on) {
+#pragma unroll
+            for (int i = 0; i < ILP; ++i) signal_stops(a, stop[i], w[i].j, lane);
         }
     }
     if (!a.f.on) return;

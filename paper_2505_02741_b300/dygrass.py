@@ -230,10 +230,18 @@ class Graph:
         v = np.ascontiguousarray(v, np.int32)
         _check(self._L.dg_init_sparsifier(self.ctx._h, self.gid, u.size, _ptr(u), _ptr(v)))
 
-    def apply(self, ups: np.ndarray, stream=None) -> np.ndarray:
-        """One batch from host records; returns the result records."""
+    def apply(self, ups: np.ndarray, stream=None, out: np.ndarray | None = None) -> np.ndarray:
+        """One batch from host records; returns the result records (into ``out``
+        when given: a RESULT_DTYPE array of at least ups.size records).  With
+        pinned arrays (e.g. numpy views of pinned torch tensors) the library
+        copies them directly instead of staging them."""
         ups = np.ascontiguousarray(ups, UPDATE_DTYPE)
-        res = np.zeros(ups.size, RESULT_DTYPE)
+        if out is None:
+            res = np.zeros(ups.size, RESULT_DTYPE)
+        else:
+            if out.dtype != RESULT_DTYPE or out.size < ups.size or not out.flags.c_contiguous:
+                raise ValueError("out must be a contiguous RESULT_DTYPE array with room for every update")
+            res = out[: ups.size]
         _check(self._L.dg_apply_updates(self.ctx._h, self.gid, ups.size, _ptr(ups), _ptr(res),
                                         None if stream is None else C.c_void_p(int(stream))))
         return res

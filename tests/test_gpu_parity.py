@@ -207,22 +207,28 @@ def test_device_io_matches_host_io():
     bt = st.next_batch(200, 100)
     ups = D.make_updates(bt.u, bt.v, bt.w, bt.op)
     out = []
-    for dev in (False, True):
+    for mode in ("host", "pinned", "device"):
         ctx = D.Context()
         g = ctx.load_graph(wl.n, wl.a, wl.b, wl.w)
         g.init_sparsifier(wl.a[wl.h_ids], wl.b[wl.h_ids])
-        if dev:
+        if mode == "device":
             d_ups = torch.from_numpy(ups.view(np.uint8)).cuda()
             d_res = torch.zeros(len(ups) * 32, dtype=torch.uint8, device="cuda")
             g.apply_device(d_ups.data_ptr(), len(ups), d_res.data_ptr(), torch.cuda.current_stream().cuda_stream)
             torch.cuda.synchronize()
             res = d_res.cpu().numpy().view(D.RESULT_DTYPE)
+        elif mode == "pinned":  # pinned host arrays are copied without staging
+            p_ups = torch.empty(len(ups) * 24, dtype=torch.uint8, pin_memory=True).numpy().view(D.UPDATE_DTYPE)
+            p_res = torch.empty(len(ups) * 32, dtype=torch.uint8, pin_memory=True).numpy().view(D.RESULT_DTYPE)
+            p_ups[:] = ups
+            res = g.apply(p_ups, out=p_res)
         else:
             res = g.apply(ups)
         out.append((res.copy(), g.sparsifier()))
         ctx.close()
-    assert_same_outputs(out[0][0], out[1][0], steps=False)
-    assert_edges_equal(out[0][1], out[1][1], "H")
+    for k in (1, 2):
+        assert_same_outputs(out[0][0], out[k][0], steps=False)
+        assert_edges_equal(out[0][1], out[k][1], "H")
 
 
 def test_pool_growth_and_compaction_keep_results():

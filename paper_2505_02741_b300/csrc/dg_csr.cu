@@ -460,8 +460,12 @@ __global__ void k_exec_fix(ExecArgs a, uint32_t* d_err) {
             return;
         }
         const uint8_t tx = a.touched[x], ty = a.touched[y];
-        const bool x_hub = a.g.hub[x] != 0, y_hub = a.g.hub[y] != 0;
-        const bool fresh = e.z == 0u;  // inserted in this batch: nothing cached yet
+        const bool x_hub = a.g.hub[x] != 0;
+        const bool fresh = e.z == 0u;
+        const bool need_own = fresh || (ty & 1u);
+        const bool need_back = !(ty & 1u) && !(x_hub && !(tx & 2u));
+        if (!need_own && !need_back) return;
+        const bool y_hub = a.g.hub[y] != 0;
         const uint32_t ly = a.g.off[y], dy = a.g.deg[y];
         uint32_t p = 0xFFFFFFFFu;      // x's slot in y's list, found when needed
         auto locate = [&]() -> bool {

@@ -111,10 +111,29 @@ __global__ void k_compact_kv(const uint64_t* __restrict__ keys, const uint32_t* 
 // batch kernels
 // ---------------------------------------------------------------------------
 // per update: basic checks (op, range, self-loop, weight); sort key of its edge
+// Edge keys of the batch go into an open-addressing table (2^k >= 2 b_max
+// slots, all-ones = empty, cleared per batch); *dup is set when a key is seen
+// twice.  Without repeated edges every update is its own run and validation
+// needs no sort.
+__device__ __forceinline__ void note_key(unsigned long long* table, uint32_t mask, uint64_t key, uint32_t* dup) {
+    uint32_t h = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 32) & mask;
+    for (uint32_t probe = 0; probe <= mask; ++probe) {  // at most half full: ends at an empty slot
+        const unsigned long long old = atomicCAS(&table[h], ~0ull, (unsigned long long)key);
+        if (old == ~0ull) return;
+        if (old == key) {
+            atomicOr(dup, 1u);
+            return;
+        }
+        h = (h + 1) & mask;
+    }
+    atomicOr(dup, 1u);  // unreachable at load <= 1/2; sorting is always correct
+}
+
 __global__ void k_val_prep(const dg_update* __restrict__ ups, const BatchHdr* hdr, uint32_t n, uint32_t b_max,
                            dg_update_result* __restrict__ res, uint64_t* __restrict__ keys,
                            uint32_t* __restrict__ vals, uint8_t* __restrict__ wkind, double* __restrict__ fin_w,
-                           uint32_t* __restrict__ fdel, uint32_t* __restrict__ fins) {
+                           uint32_t* __restrict__ fdel, uint32_t* __restrict__ fins, unsigned long long* table,
+                           uint32_t tmask, uint32_t* dup) {
     const uint32_t nu = min(hdr->nu, b_max);
     const uint64_t sent = (uint64_t)n * n;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nu; i += gridDim.x * blockDim.x) {
@@ -136,6 +155,7 @@ __global__ void k_val_prep(const dg_update* __restrict__ ups, const BatchHdr* hd
         if (st == ST_OK) {
             const uint32_t a = (uint32_t)min(up.u, up.v), b = (uint32_t)max(up.u, up.v);
             keys[i] = (uint64_t)a * n + b;
+            note_key(table, tmask, keys[i], dup);
         } else {
             keys[i] = sent;
         }
@@ -148,8 +168,11 @@ __global__ void k_val_prep(const dg_update* __restrict__ ups, const BatchHdr* hd
 }
 
 struct RunArgs {
-    const uint64_t* keys;
+    const uint64_t* keys;        // sorted by key (when *dup), else the keys in update order
     const uint32_t* vals;
+    const uint64_t* keys_plain;  // update order
+    const uint32_t* vals_plain;
+    const uint32_t* dup;
     const dg_update* ups;
     const BatchHdr* hdr;
     uint32_t n, b_max;
@@ -174,6 +197,10 @@ struct RunArgs {
 __global__ void k_val_runs(RunArgs a) {
     const uint32_t nu = min(a.hdr->nu, a.b_max);
     const uint64_t sent = (uint64_t)a.n * a.n;
+    if (!*a.dup) {  // every edge appears once: the update-order arrays are runs of one
+        a.keys = a.keys_plain;
+        a.vals = a.vals_plain;
+    }
     for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nu; c += gridDim.x * blockDim.x) {
         const uint64_t key = a.keys[c];
         if (key == sent) continue;
@@ -318,7 +345,7 @@ uint64_t BatchWS::bytes() const {
     b += wkind.bytes() + fin_w.bytes() + wflag.bytes() + wpos.bytes() + wflag2.bytes() + wpos2.bytes();
     b += gkeys.bytes() + gkeys_alt.bytes() + hkeys.bytes() + gvals.bytes() + gvals_alt.bytes() + ghist.bytes();
     b += gscan.bytes() + gcount.bytes() + hflag.bytes() + hpos.bytes() + hvals.bytes() + hcount.bytes();
-    b += gkind.bytes() + ghrem.bytes() + kind_del.bytes() + gw.bytes();
+    b += gkind.bytes() + ghrem.bytes() + kind_del.bytes() + gw.bytes() + vtab.bytes();
     b += t_u.bytes() + t_v.bytes() + t_idx.bytes() + t_kstar.bytes() + t_count.bytes() + meta.bytes();
     b += t_fin.bytes() + t_queue.bytes() + qctr.bytes() + cp.bytes();
     b += t_wpq.bytes() + t_rmax.bytes() + recR.bytes() + t_kind.bytes() + best.bytes();
@@ -368,6 +395,9 @@ static void ensure_ws(Ctx& c, DGraph& g, uint32_t b_max, cudaStream_t st) {
     w.ctr.ensure(a, 1, st);
     w.next.ensure(a, 1, st);
     w.vkeys.ensure(a, B, st);
+    w.vtab_slots = 1024;
+    while (w.vtab_slots < 2 * B) w.vtab_slots *= 2;
+    w.vtab.ensure(a, (size_t)w.vtab_slots + 1, st);
     w.vkeys_alt.ensure(a, B, st);
     w.vvals.ensure(a, B, st);
     w.vvals_alt.ensure(a, B, st);
@@ -723,7 +753,7 @@ void graph_release_ws(Ctx& c, DGraph& g, cudaStream_t st) {
     w.apH.release(c.alloc, st);
     w.apC.release(c.alloc, st);
 #define REL(b) w.b.release(c.alloc, st)
-    REL(ups); REL(res); REL(hdr); REL(err); REL(ctr); REL(next); REL(vkeys); REL(vkeys_alt); REL(vvals);
+    REL(ups); REL(res); REL(hdr); REL(err); REL(ctr); REL(next); REL(vkeys); REL(vtab); REL(vkeys_alt); REL(vvals);
     REL(vvals_alt); REL(vhist); REL(vscan); REL(wkind); REL(fin_w); REL(wflag); REL(wpos); REL(wflag2); REL(wpos2); REL(gkeys);
     REL(gkeys_alt); REL(hkeys); REL(gvals); REL(gvals_alt); REL(ghist); REL(gscan); REL(gcount); REL(hflag);
     REL(hpos); REL(hvals); REL(hcount); REL(gkind); REL(ghrem); REL(kind_del); REL(gw); REL(t_u); REL(t_v);
@@ -818,14 +848,22 @@ static void enqueue_mutate(Ctx& c, DGraph& g, cudaStream_t st) {
     DG_CUDA(cudaMemsetAsync(w.gcount.p, 0, 4, st));
     DG_CUDA(cudaMemsetAsync(w.t_kstar.p, 0xFF, 4ull * B, st));
     const uint32_t* d_nu = &w.hdr.p->nu;
+    // edge-key table (all ones) and the repeated-edge flag behind it, one memset
+    DG_CUDA(cudaMemsetAsync(w.vtab.p, 0xFF, (size_t)w.vtab_slots * 8, st));
+    uint32_t* d_dup = reinterpret_cast<uint32_t*>(w.vtab.p + w.vtab_slots);
+    DG_CUDA(cudaMemsetAsync(d_dup, 0, 8, st));
     k_val_prep<<<grid_for(B), BT, 0, st>>>(w.ups.p, w.hdr.p, n, B, w.res.p, w.vkeys.p, w.vvals.p, w.wkind.p,
-                                          w.fin_w.p, w.wflag.p, w.wflag2.p);
+                                          w.fin_w.p, w.wflag.p, w.wflag2.p, w.vtab.p, w.vtab_slots - 1u, d_dup);
     ++g_launches;
+    // sorted by edge key only when some edge appears twice (the kernels return at once otherwise)
     SortBufs vs{w.vkeys.p, w.vvals.p, w.vkeys_alt.p, w.vvals_alt.p, w.vhist.p, w.vscan.p, w.err.p};
-    const bool valt = radix_sort_pairs(vs, d_nu, B, bit_length((uint64_t)n * n), st);
+    const bool valt = radix_sort_pairs(vs, d_nu, B, bit_length((uint64_t)n * n), st, d_dup);
     RunArgs ra;
     ra.keys = valt ? w.vkeys_alt.p : w.vkeys.p;
     ra.vals = valt ? w.vvals_alt.p : w.vvals.p;
+    ra.keys_plain = w.vkeys.p;
+    ra.vals_plain = w.vvals.p;
+    ra.dup = d_dup;
     ra.ups = w.ups.p;
     ra.hdr = w.hdr.p;
     ra.n = n;

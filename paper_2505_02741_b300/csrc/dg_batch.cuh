@@ -39,6 +39,8 @@ struct BatchWS {
     DBuf<unsigned long long> next;
     // validation
     DBuf<uint64_t> vkeys, vkeys_alt;
+    DBuf<unsigned long long> vtab;  // edge-key table (vtab_slots) + one word for the repeated-edge flag
+    uint32_t vtab_slots = 0;
     DBuf<uint32_t> vvals, vvals_alt, vhist, vscan;
     DBuf<uint8_t> wkind;
     DBuf<double> fin_w;

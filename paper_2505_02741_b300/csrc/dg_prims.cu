@@ -253,7 +253,9 @@ size_t sort_scan_tmp_words(uint32_t n_max) { return scan_tmp_words(n_max + 1); }
 
 // digit totals of every pass in one read of the keys (warp-aggregated atomics)
 __global__ void __launch_bounds__(256) k_os_hist(const uint64_t* __restrict__ keys, const uint32_t* d_n,
-                                                 uint32_t n_max, int passes, uint32_t* __restrict__ ghist) {
+                                                 uint32_t n_max, int passes, uint32_t* __restrict__ ghist,
+                                                 const uint32_t* run_if) {
+    if (run_if && *run_if == 0u) return;
     __shared__ uint32_t h[OS_MAX_PASSES][256];
     for (int i = threadIdx.x; i < OS_MAX_PASSES * 256; i += blockDim.x) (&h[0][0])[i] = 0;
     __syncthreads();
@@ -283,7 +285,9 @@ __global__ void __launch_bounds__(256) k_os_hist(const uint64_t* __restrict__ ke
 __global__ void __launch_bounds__(OS_THREADS) k_os_pass(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                         uint64_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                         const uint32_t* d_n, uint32_t n_max, int pass,
-                                                        uint32_t* hist, uint32_t tiles, uint32_t* err) {
+                                                        uint32_t* hist, uint32_t tiles, uint32_t* err,
+                                                        const uint32_t* run_if) {
+    if (run_if && *run_if == 0u) return;
     __shared__ uint32_t s_warp[OS_WARPS][256];
     __shared__ uint32_t s_base[256];
     __shared__ uint32_t s_tile;
@@ -399,7 +403,7 @@ __global__ void __launch_bounds__(OS_THREADS) k_os_pass(const uint64_t* __restri
 }
 
 bool radix_sort_pairs(const SortBufs& b, const uint32_t* d_n, uint32_t n_max, int nbits,
-                      cudaStream_t st) {
+                      cudaStream_t st, const uint32_t* run_if) {
     if (n_max == 0 || nbits <= 0) return false;
     const int passes = (nbits + 7) / 8;
     const uint32_t tiles = os_tiles(n_max);
@@ -408,7 +412,7 @@ bool radix_sort_pairs(const SortBufs& b, const uint32_t* d_n, uint32_t n_max, in
     cudaMemsetAsync(b.hist, 0, (OS_STATUS + (separate ? 256ull * tiles * passes : 0)) * 4, st);
     uint32_t hblocks = (n_max + 255) / 256;
     if (hblocks > 148u * 8u) hblocks = 148u * 8u;
-    k_os_hist<<<hblocks, 256, 0, st>>>(b.keys, d_n, n_max, passes, b.hist + OS_GHIST);
+    k_os_hist<<<hblocks, 256, 0, st>>>(b.keys, d_n, n_max, passes, b.hist + OS_GHIST, run_if);
     ++g_launches;
     const uint64_t* src_k = b.keys;
     const uint32_t* src_v = b.vals;
@@ -417,7 +421,8 @@ bool radix_sort_pairs(const SortBufs& b, const uint32_t* d_n, uint32_t n_max, in
     bool in_alt = false;
     for (int p = 0; p < passes; ++p) {
         if (!separate) cudaMemsetAsync(b.hist + OS_STATUS, 0, 256ull * tiles * 4, st);
-        k_os_pass<<<tiles, OS_THREADS, 0, st>>>(src_k, src_v, dst_k, dst_v, d_n, n_max, p, b.hist, tiles, b.err);
+        k_os_pass<<<tiles, OS_THREADS, 0, st>>>(src_k, src_v, dst_k, dst_v, d_n, n_max, p, b.hist, tiles, b.err,
+                                                run_if);
         ++g_launches;
         in_alt = !in_alt;
         const uint64_t* tk = dst_k;

@@ -40,8 +40,10 @@ struct SortBufs {
 };
 size_t sort_hist_words(uint32_t n_max);
 size_t sort_scan_tmp_words(uint32_t n_max);
+// run_if (nullable device word): when it reads 0 the sort's kernels return at
+// once and the data stays where it was (callers then use the unsorted input)
 bool radix_sort_pairs(const SortBufs& b, const uint32_t* d_n, uint32_t n_max, int nbits,
-                      cudaStream_t st);
+                      cudaStream_t st, const uint32_t* run_if = nullptr);
 
 int bit_length(uint64_t x);
 

@@ -192,6 +192,33 @@ struct RunArgs {
     BatchCounters* ctr;
 };
 
+// Is {x, y} in G (and with which weight) and in H?  The two lookups run side by
+// side (each in the shorter of the two endpoint lists) so their dependent
+// loads overlap instead of adding up.
+__device__ __forceinline__ void lookup_gh(const CSRView& G, const CSRView& H, uint32_t x, uint32_t y, bool& in_g,
+                                          double& w, bool& in_h) {
+    const uint32_t gx = G.deg[x], gy = G.deg[y], hx = H.deg[x], hy = H.deg[y];
+    const uint32_t ga = gy < gx ? y : x, gb = gy < gx ? x : y, gd = gy < gx ? gy : gx;
+    const uint32_t ha = hy < hx ? y : x, hb = hy < hx ? x : y, hd = hy < hx ? hy : hx;
+    const Ent* LG = G.pool + G.off[ga];
+    const Ent* LH = H.pool + H.off[ha];
+    uint32_t glo = 0, ghi = gd, hlo = 0, hhi = hd;
+    while (glo < ghi || hlo < hhi) {
+        const uint32_t gm = (glo + ghi) >> 1, hm = (hlo + hhi) >> 1;
+        const uint32_t gv = glo < ghi ? LG[gm].nbr : 0u;
+        const uint32_t hv = hlo < hhi ? LH[hm].nbr : 0u;
+        if (glo < ghi) {
+            if (gv < gb) glo = gm + 1; else ghi = gm;
+        }
+        if (hlo < hhi) {
+            if (hv < hb) hlo = hm + 1; else hhi = hm;
+        }
+    }
+    in_g = glo < gd && LG[glo].nbr == gb;
+    w = in_g ? LG[glo].w : 0.0;
+    in_h = hlo < hd && LH[hlo].nbr == hb;
+}
+
 // one thread per run of equal edges: replay the run in update order against
 // the batch-local view (presence, weight) of that edge
 __global__ void k_val_runs(RunArgs a) {
@@ -207,8 +234,9 @@ __global__ void k_val_runs(RunArgs a) {
         if (c > 0 && a.keys[c - 1] == key) continue;
         const uint32_t x = (uint32_t)(key / a.n), y = (uint32_t)(key % a.n);
         double w0 = 0.0;
-        const bool present0 = has_edge(a.G, x, y, &w0);
-        const bool in_h = present0 && has_edge(a.H, x, y);
+        bool present0 = false, h0 = false;
+        lookup_gh(a.G, a.H, x, y, present0, w0, h0);
+        const bool in_h = present0 && h0;
         bool state = present0, any_valid = false, hrem = false;
         double wcur = w0;
         uint32_t valid = 0;

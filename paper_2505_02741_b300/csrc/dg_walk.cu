@@ -549,7 +549,8 @@ __device__ __forceinline__ void load_step(const Ent* pool, uint32_t i, uint4& h,
 // The step when the walker stands on a hub (previous vertex known by id only:
 // L[jj] was loaded at slot `at`; take L[jj+1] instead when L[jj] is at or past
 // the previous vertex) or the chosen entry leads to a hub (HUBREF: the list
-// comes from the vertex arrays).  Advances the walker; false on a bad offset.
+// comes from the vertex arrays).  Moves the walker (r ends as the step's
+// resistance, added by the caller); false on a bad offset.
 __device__ __forceinline__ bool lean_hub_step(Lean& v, const WalkKernelArgs& a, uint4& h, double& r, uint32_t at) {
     const CSRView& g = v.ins ? a.H : a.G;
     if (v.pid && h.x >= v.prev) {
@@ -559,7 +560,6 @@ __device__ __forceinline__ bool lean_hub_step(Lean& v, const WalkKernelArgs& a, 
         }
         load_step(g.pool, at + 1, h, r);
     }
-    v.R = __dadd_rn(v.R, r);
     v.steps += 1;
     const uint32_t from = v.c;
     v.c = h.x;
@@ -697,13 +697,18 @@ __global__ void __launch_bounds__(256, (ILP == 1 ? 4 : (ILP == 2 ? 3 : 1))) k_wa
                     continue;
                 }
             } else {
-                v.R = __dadd_rn(v.R, r[i]);
                 v.steps += 1;
                 v.c = h[i].x;
                 v.off = h[i].y;
                 v.deg = h[i].z;
                 v.prev = h[i].w;
             }
+            const double r_step = r[i];
+            // reaching v ends the walk whatever R is (hit, or over K for an insertion);
+            // the next load goes out first, the rest of the step follows it
+            const bool at_q = v.c == v.q;
+            fly[i] = !at_q && v.steps < a.p.T && lean_issue<HUBS>(v, a, h[i], r[i], ks[i], at[i]);
+            v.R = __dadd_rn(v.R, r_step);
             if (a.r.paths) a.r.paths[((size_t)v.j * a.p.s + v.k) * (a.p.T + 1) + v.steps] = (int32_t)v.c;
             if (a.f.cp && !v.ins && (v.steps & ((1u << a.f.cp_shift) - 1u)) == 0u) {
                 const uint32_t q = (v.steps >> a.f.cp_shift) - 1u;
@@ -711,9 +716,6 @@ __global__ void __launch_bounds__(256, (ILP == 1 ? 4 : (ILP == 2 ? 3 : 1))) k_wa
                     a.f.cp[((size_t)v.j * a.p.s + v.k) * a.f.ncp + q] =
                         make_uint4(v.c, v.off, v.deg, v.prev | (v.pid ? 0x80000000u : 0u));
             }
-            // reaching v ends the walk whatever R is (hit, or over K for an insertion)
-            const bool at_q = v.c == v.q;
-            fly[i] = !at_q && v.steps < a.p.T && lean_issue<HUBS>(v, a, h[i], r[i], ks[i], at[i]);
             const bool over = (unsigned long long)__double_as_longlong(v.R) > v.rmax;  // insertions: w_pq * R > K
             if (!v.ins && r_key(v.R) > ks_now) {  // above a hit of this deletion: cannot be the minimum
                 lean_finish(v, a, R_CUT);

@@ -297,15 +297,20 @@ def test_invariants_subgraph_and_components():
     ctx.close()
 
 
+# the CUDA path's hub thresholds: a vertex becomes a hub at degree 32 and
+# stays one down to 24 (a layout choice: entries pointing at it hold no cache)
+HUB_HI, HUB_LO = 32, 24
+
+
 def test_hub_references_and_status_flips():
-    """Vertices of degree >= 1024 are referenced without cached list data (a
+    """Vertices of degree >= HUB_HI are referenced without cached list data (a
     layout choice of the CUDA path).  Walks through such hubs, changes of their
-    lists, and hubs crossing the thresholds (down through 768, back up through
-    1024) must leave every result, H and G equal to the oracle."""
+    lists, and hubs crossing the thresholds (down below HUB_LO, back up through
+    HUB_HI) must leave every result, H and G equal to the oracle."""
     rng = np.random.default_rng(21)
     n = 4000
     edges = set()
-    for hub, d in ((0, 1100), (1, 1030), (2, 900)):
+    for hub, d in ((0, HUB_HI + 10), (1, HUB_HI + 2), (2, HUB_HI - 8)):
         for y in rng.choice(np.arange(3, n), d, replace=False):
             edges.add((hub, int(y)))
     perm = rng.permutation(n)
@@ -348,10 +353,12 @@ def test_hub_references_and_status_flips():
         cand = [y for y in range(3, n) if y != x and y not in have]
         return [(x, int(y)) for y in rng.choice(cand, k, replace=False)]
 
-    plans = [
-        (lambda: [(0, y) for y in nbrs(0)[:300]], lambda: new_nbrs(2, 150)),  # hub 0 to 800 (stays), 2 to 1050 (joins)
-        (lambda: [(0, y) for y in nbrs(0)[:100]], lambda: new_nbrs(1, 20)),   # hub 0 to 700 (leaves)
-        (lambda: [(1, y) for y in nbrs(1)[:10]], lambda: new_nbrs(0, 400)),   # hub 0 back to 1100 (joins again)
+    d0 = len(nbrs(0))
+    assert d0 >= HUB_HI and len(nbrs(1)) >= HUB_HI and len(nbrs(2)) < HUB_HI
+    plans = [  # hub 0 drops to HUB_LO (stays a hub), vertex 2 rises past HUB_HI (joins)
+        (lambda: [(0, y) for y in nbrs(0)[: d0 - HUB_LO]], lambda: new_nbrs(2, 12)),
+        (lambda: [(0, y) for y in nbrs(0)[:3]], lambda: new_nbrs(1, 5)),      # hub 0 below HUB_LO (leaves)
+        (lambda: [(1, y) for y in nbrs(1)[:4]], lambda: new_nbrs(0, 20)),     # hub 0 back above HUB_HI (joins again)
     ]
     for bi, (dl, il) in enumerate(plans):
         u, v, ww, op = batch(dl(), il())

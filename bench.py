@@ -304,6 +304,7 @@ def main():
     ap.add_argument("--per-update-steps", type=int, default=2)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-full-walks", action="store_true", help="skip the unpruned-walk context line")
     ap.add_argument("--walk-shape", default="", help="fixed walk launch shape 'block,ilp' (skips the autotuner)")
     ap.add_argument("--workload", default="mesh", choices=["mesh", "fea", "rmat", "serve"],
                     help="mesh (default line), fea, rmat, or serve (several graphs resident, Poisson arrivals)")
@@ -420,6 +421,31 @@ def main():
            "d2h_bytes_per_step": 32 * e2e_nu // args.steps + 96, "p50_ms": 1e3 * float(np.percentile(e2e_t, 50)),
            "p99_ms": 1e3 * float(np.percentile(e2e_t, 99)), "host_buffers": "pinned"}
 
+    # ---- context: the same walk kernel without deletion pruning ---------------
+    # (every deletion walker runs to its own stop, as Algorithm 1 walks them):
+    # a fresh copy of the graph takes the stream's first batches; the walk is
+    # then bandwidth-bound rather than bound by the chain of the longest walks
+    full = None
+    if args.workload == "mesh" and not args.no_full_walks:
+        ctx_f = D.Context(device=dev, K=wl.K, T=wl.T, s=wl.s, del_prune=False)
+        gf = ctx_f.load_graph(wl.n, wl.a, wl.b, wl.w)
+        gf.init_sparsifier(wl.a[wl.h_ids], wl.b[wl.h_ids])
+        f_ms, f_steps = [], 0
+        for k in range(6):
+            flush.fill_(float(k))
+            ups, d_ups = dev_batches[k]
+            gf.apply_device(d_ups.data_ptr(), len(ups), d_res.data_ptr(), stream.cuda_stream)
+            s = gf.stats()
+            if k >= 3:
+                f_ms.append(s["walk_ms"])
+                f_steps += s["steps"]
+        ctx_f.close()
+        f_bytes = BYTES_PER_STEP * f_steps / 3
+        f_ach = f_bytes / (sum(f_ms) / 3 / 1e3) / 1e9
+        full = {"del_prune": False, "walk_steps_per_batch": f_steps / 3, "walk_ms": sum(f_ms) / 3,
+                "walk_steps_per_s": f_steps / (sum(f_ms) / 1e3), "achieved_gbs": f_ach,
+                "frac": f_ach / measured_peaks()[0], "batches": "stream batches 4-6 on a fresh copy"}
+
     # ---- the one-launch-per-update form on a copy at the same state ----------
     pu = None
     if args.per_update_steps > 0:
@@ -497,6 +523,7 @@ def main():
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
             "per_update_form": pu,
             "roofline": roof,
+            "roofline_full_walks": full,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,

@@ -992,14 +992,26 @@ __global__ void __launch_bounds__(256) k_fallback(CSRView H, CSRView G, WalkTask
             const uint32_t d = G.deg[x];
             double br = INFINITY, bw = 0.0;
             uint32_t by = NONE;
-            for (uint32_t k = threadIdx.x; k < d; k += blockDim.x) {
-                const double rr = L[k].r;
-                if (!(rr < br)) continue;  // this thread's ids ascend: strict < keeps the smaller id
-                const uint32_t y = L[k].nbr;
-                if (has_edge(H, x, y)) continue;
-                br = rr;
-                by = y;
-                bw = L[k].w;
+            // eight resistances per round are loaded together, then taken in
+            // order (this thread's ids ascend: strict < keeps the smaller id)
+            constexpr uint32_t U = 8;
+            for (uint32_t k0 = threadIdx.x; k0 < d; k0 += U * blockDim.x) {
+                double rr[U];
+#pragma unroll
+                for (uint32_t q = 0; q < U; ++q) {
+                    const uint32_t k = k0 + q * blockDim.x;
+                    rr[q] = k < d ? L[k].r : INFINITY;
+                }
+#pragma unroll
+                for (uint32_t q = 0; q < U; ++q) {
+                    const uint32_t k = k0 + q * blockDim.x;
+                    if (!(rr[q] < br)) continue;
+                    const uint32_t y = L[k].nbr;
+                    if (has_edge(H, x, y)) continue;
+                    br = rr[q];
+                    by = y;
+                    bw = L[k].w;
+                }
             }
             for (int o = 16; o > 0; o >>= 1) {
                 const double orr = __shfl_xor_sync(0xffffffffu, br, o);

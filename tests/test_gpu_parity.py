@@ -78,6 +78,66 @@ def test_threshold_ties_and_extremes(K):
     ctx.close()
 
 
+@pytest.mark.parametrize("s,T,K", [(1, 1, 100.0), (1, 40, 3.0), (33, 2, 100.0), (64, 15, 8.0), (7, 17, 0.0)])
+def test_degenerate_walk_parameters(s, T, K):
+    """One walker per update, a one-step limit, updates whose walkers span more
+    than one warp, step limits just below and above the resume-point spacing,
+    K = 0; a graph with isolated vertices so some walks start at degree 0."""
+    rng = np.random.default_rng(300 + s + T)
+    n = 150
+    a, b, w = random_connected(n - 20, 220, rng, 0.2, 5.0)  # vertices n-20..n-1 stay isolated at first
+    h = W.init_sparsifier(n, a, b, w, rng)
+    ctx, g, o = pair(n, a, b, w, h, s=s, T=T, K=K, ctx_kw=dict(record_walkers=True))
+    ups = _mixed_updates(rng, n, a, b, 160)
+    ups += [(n - 1, int(rng.integers(0, n - 20)), 1.0, 0), (n - 2, n - 3, 2.0, 0)]  # walks from isolated starts
+    cols = list(zip(*ups))
+    res, ref = step_both(g, o, list(cols[0]), list(cols[1]), list(cols[2]), list(cols[3]), where=f"s={s} T={T}")
+    assert (res["walked"] == 1).any()
+    for k in range(3):  # further batches on the evolved graphs
+        ups = _mixed_updates(rng, n, *[np.array(x) for x in zip(*sorted(o_edges(o)))], 120)
+        cols = list(zip(*ups))
+        step_both(g, o, list(cols[0]), list(cols[1]), list(cols[2]), list(cols[3]), where=f"s={s} T={T} b{k}")
+    ctx.close()
+
+
+def test_empty_and_all_invalid_batches():
+    wl, st = W.make_grid(16, 16)
+    ctx, g, o = pair(wl.n, wl.a, wl.b, wl.w, wl.h_ids)
+    before = g.sparsifier()
+    res = g.apply(D.make_updates([], [], [], []))
+    assert len(res) == 0 and g.next_update_id == 0
+    bad = [(3, 3, 1.0, 0), (wl.n, 1, 1.0, 0), (1, 2, -2.0, 0), (1, 2, 1.0, 7), (0, 5, 0.0, 1)]
+    cols = list(zip(*bad))
+    res, _ = step_both(g, o, list(cols[0]), list(cols[1]), list(cols[2]), list(cols[3]), where="all invalid")
+    assert (res["status"] != 0).all() and (res["walked"] == 0).all()
+    assert_edges_equal(g.sparsifier(), before, "H unchanged")
+    assert g.next_update_id == len(bad)  # invalid updates still consume ids
+    ctx.close()
+
+
+def o_edges(o):
+    a, b, _ = o.edges("G")
+    return list(zip(a.tolist(), b.tolist()))
+
+
+def _mixed_updates(rng, n, a, b, count):
+    """Insertions between random pairs and deletions of existing edges (some
+    repeated or invalid), as (u, v, w, op) tuples."""
+    cur = list(zip(np.asarray(a).tolist(), np.asarray(b).tolist()))
+    ups = []
+    for _ in range(count):
+        r = rng.random()
+        if r < 0.5:
+            x, y = (int(t) for t in rng.integers(0, n, 2))
+            ups.append((x, y, float(rng.uniform(0.2, 5.0)), 0))
+        elif r < 0.95 and cur:
+            x, y = cur[int(rng.integers(0, len(cur)))]
+            ups.append((y, x, 0.0, 1) if rng.random() < 0.5 else (x, y, 0.0, 1))
+        else:
+            ups.append((int(rng.integers(0, n)), int(rng.integers(0, n)), 0.0, 1))
+    return ups
+
+
 def test_deletion_pruning_walker_records():
     """Pruned deletion walkers: each GPU walker's path is a prefix of the
     oracle's unpruned path, no walker runs longer than there, the walkers at

@@ -308,6 +308,8 @@ def main():
     ap.add_argument("--walk-shape", default="", help="fixed walk launch shape 'block,ilp' (skips the autotuner)")
     ap.add_argument("--workload", default="mesh", choices=["mesh", "fea", "rmat", "serve"],
                     help="mesh (default line), fea, rmat, or serve (several graphs resident, Poisson arrivals)")
+    ap.add_argument("--rmat-scale", type=int, default=22, help="rmat: log2 of the vertex count")
+    ap.add_argument("--rmat-edges", type=int, default=64_000_000, help="rmat: distinct undirected edges")
     ap.add_argument("--load", type=float, default=0.6, help="serve: offered load as a fraction of capacity")
     ap.add_argument("--requests", type=int, default=1000, help="serve: requests in the measured stream")
     args = ap.parse_args()
@@ -338,7 +340,7 @@ def main():
         wl, st = W.make_fea(seed=rank)
         n_ins, n_del = 50_000, 50_000
     elif args.workload == "rmat":  # 50k updates per step, 60 % insertions
-        wl, st = W.make_rmat(seed=rank)
+        wl, st = W.make_rmat(scale=args.rmat_scale, n_edges=args.rmat_edges, seed=rank)
         n_ins, n_del = 30_000, 20_000
     else:
         wl, st = W.make_mesh3d(seed=rank)

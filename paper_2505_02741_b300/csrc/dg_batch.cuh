@@ -95,8 +95,8 @@ struct DGraph {
     CSR G, H;
     bool has_h = false;
     uint64_t next_id = 0;
-    DBuf<uint8_t> touched;    // vertices whose G list (or H list at commit) changed in the running step
-    DBuf<uint8_t> touched_h;  // the same for H while G and H are mutated side by side
+    DBuf<uint32_t> touched;    // generation-stamped marks of changed G lists (H lists at commit), see csr_exec
+    DBuf<uint32_t> touched_h;  // the same for H while G and H are mutated side by side
     BatchWS ws;
     HostStage hs;
     WalkShape shape;

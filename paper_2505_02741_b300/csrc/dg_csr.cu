@@ -319,7 +319,7 @@ struct ExecArgs {
     const uint32_t *p_ins, *p_del, *totals;
     const uint32_t *tv, *tstart, *tend, *odeg, *ndeg, *ooff, *ncap, *rsz, *r_off, *s_off, *w_off;
     Ent* stage;
-    uint8_t* touched;
+    uint32_t* touched;  // n + 1 words, see csr_exec
 };
 
 __device__ __forceinline__ uint64_t base_of(const uint32_t* totals) {
@@ -344,7 +344,7 @@ __global__ void k_exec_meta(ExecArgs a, const uint32_t* d_err) {
         const bool was = a.g.hub[x] != 0, now = hub_next(was, a.ndeg[t]);
         a.g.hub[x] = now ? 1 : 0;
         if (was != now) atomicAdd(a.g.nhub, now ? 1u : 0xFFFFFFFFu);
-        a.touched[x] = (uint8_t)(1u | (was != now ? 2u : 0u));
+        a.touched[x] = (a.touched[a.n] << 2) | 1u | (was != now ? 2u : 0u);
     }
 }
 
@@ -377,6 +377,7 @@ __device__ __forceinline__ void for_segment_items(const uint32_t* seg_off, uint3
 // merge: one thread per (old entry | change) of every touched vertex
 __global__ void k_exec_merge(ExecArgs a, uint32_t* d_err) {
     if (aborted(d_err)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ++a.touched[a.n];  // this execution's generation (read from meta on)
     const uint32_t X = a.totals[TOT_X];
     const uint32_t WK = a.totals[TOT_WK];
     const uint32_t count = count_of(a.cl.d_count, a.cl.max_count);
@@ -459,7 +460,10 @@ __global__ void k_exec_fix(ExecArgs a, uint32_t* d_err) {
             atomicOr(d_err, (uint32_t)ERR_INTERNAL);
             return;
         }
-        const uint8_t tx = a.touched[x], ty = a.touched[y];
+        // marks of this execution only (older generations read as untouched)
+        const uint32_t gen = a.touched[a.n];
+        const uint32_t mx = a.touched[x], my = a.touched[y];
+        const uint32_t tx = (mx >> 2) == gen ? (mx & 3u) : 0u, ty = (my >> 2) == gen ? (my & 3u) : 0u;
         const bool x_hub = a.g.hub[x] != 0;
         const bool fresh = e.z == 0u;
         const bool need_own = fresh || (ty & 1u);
@@ -506,14 +510,7 @@ __global__ void k_exec_fix(ExecArgs a, uint32_t* d_err) {
     });
 }
 
-__global__ void k_exec_untouch(ExecArgs a, const uint32_t* d_err) {
-    if (aborted(d_err)) return;
-    const uint32_t X = a.totals[TOT_X];
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < X; t += gridDim.x * blockDim.x)
-        a.touched[a.tv[t]] = 0;
-}
-
-void csr_exec(CSR& g, const ChangeList& cl, ApplyScratch& s, uint8_t* touched, uint32_t* d_err,
+void csr_exec(CSR& g, const ChangeList& cl, ApplyScratch& s, uint32_t* touched, uint32_t* d_err,
               cudaStream_t st) {
     const int grid = flat_grid();
     ExecArgs a;
@@ -532,8 +529,7 @@ void csr_exec(CSR& g, const ChangeList& cl, ApplyScratch& s, uint8_t* touched, u
     k_exec_meta<<<grid, FLAT_THREADS, 0, st>>>(a, d_err);
     k_exec_place<<<grid, FLAT_THREADS, 0, st>>>(a, d_err);
     k_exec_fix<<<grid, FLAT_THREADS, 0, st>>>(a, d_err);
-    k_exec_untouch<<<grid, FLAT_THREADS, 0, st>>>(a, d_err);
-    g_launches += 5;
+    g_launches += 4;
     DG_CHECK_LAUNCH();
 }
 

@@ -85,7 +85,10 @@ void csr_build(CSR& g, DevAlloc& a, const uint64_t* keys, const uint32_t* vals, 
 void csr_plan(CSR& g, const ChangeList& cl, ApplyScratch& s, uint32_t* d_err, uint32_t pool_err_bit,
               uint32_t cap_err_bit, cudaStream_t st);
 // execute: merge, place, refresh cached fields (no-op when *d_err has an abort bit)
-void csr_exec(CSR& g, const ChangeList& cl, ApplyScratch& s, uint8_t* touched, uint32_t* d_err,
+// touched: n + 1 words; entry x = (generation << 2) | bits for the vertices an
+// execution changed, word n = the array's generation (bumped per execution),
+// so marks of earlier executions never match and nothing needs clearing
+void csr_exec(CSR& g, const ChangeList& cl, ApplyScratch& s, uint32_t* touched, uint32_t* d_err,
               cudaStream_t st);
 
 // rebuild every list with fresh slack into a new pool with at least min_free spare entries

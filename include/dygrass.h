@@ -161,6 +161,8 @@ typedef struct {
     double commit_ms;        /* sort, filter and merge into H, result copy-out */
     int32_t walk_cut;        /* persistent walk launches per batch */
     int32_t autotuned;       /* 1 if this batch ran the walk-shape autotuner */
+    int32_t walk_refill;     /* empty walker slots a warp waits for before refilling */
+    int32_t reserved0;
 } dg_batch_stats;
 
 /* default configuration: seed 0, K 100, T 100, s 32, early exit on, batched walks,
@@ -264,6 +266,14 @@ dg_status dg_get_next_update_id(dg_ctx* ctx, int32_t graph_id, uint64_t* next_id
    0 fields keep the current value.  Outputs never depend on the shape. */
 dg_status dg_set_walk_shape(dg_ctx* ctx, int32_t graph_id, int32_t block, int32_t ilp,
                             int32_t blocks_per_sm);
+
+/* Refill threshold of the batched walk (1..32): a warp that still has walkers
+   starts new ones only when at least this many of its walker slots are empty
+   (or none is busy).  Starting walkers stalls the warp for three dependent
+   reads, and the walkers of one update tend to stop together, so waiting for
+   several empty slots trades a few idle lanes for fewer stalls.  Outputs never
+   depend on it; DG_E_INVALID outside 1..32. */
+dg_status dg_set_walk_refill(dg_ctx* ctx, int32_t graph_id, int32_t refill_min);
 
 /*
  * Serving (continuous batching over resident graphs).  dg_submit_updates

@@ -464,6 +464,17 @@ dg_status dg_set_walk_shape(dg_ctx* ctx, int32_t gid, int32_t block, int32_t ilp
     });
 }
 
+dg_status dg_set_walk_refill(dg_ctx* ctx, int32_t gid, int32_t refill_min) {
+    return guarded(ctx, [&]() {
+        DGraph& g = C(ctx).graph(gid);
+        std::lock_guard<std::mutex> lk(g.mu);
+        if (refill_min < 1 || refill_min > 32) throw Error(DG_E_INVALID, "refill_min must be 1..32");
+        g.shape.refill = refill_min;
+        g.tuned = true;
+        ++g.layout_gen;
+    });
+}
+
 dg_status dg_submit_updates(dg_ctx* ctx, int32_t gid, int64_t nu, const dg_update* ups, dg_update_result* res,
                             uint64_t* ticket_out) {
     return guarded(ctx, [&]() {

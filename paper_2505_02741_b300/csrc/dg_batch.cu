@@ -1076,6 +1076,17 @@ static void autotune_walks(Ctx& c, DGraph& g, cudaStream_t st) {
             best = sh;
         }
     }
+    // then the refill threshold of the winning shape
+    const WalkShape base = best;
+    for (const int rf : {1, 8, 24, 32}) {
+        WalkShape sh = base;
+        sh.refill = rf;
+        const float ms = median3(sh);
+        if (ms < best_ms * 0.97f) {
+            best_ms = ms;
+            best = sh;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c.alloc.put(flush, flush_bytes, st);
@@ -1352,6 +1363,7 @@ void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_updat
     s.walk_ilp = g.shape.ilp;
     s.walk_blocks_per_sm = g.shape.blocks_per_sm;
     s.walk_cut = g.shape.cut;
+    s.walk_refill = g.shape.refill;
     s.walk_launches = per_update ? (int64_t)g.hs.counts[0] : 1;
     const uint64_t dl = g_launches - l0;
     s.launches = (int64_t)dl;

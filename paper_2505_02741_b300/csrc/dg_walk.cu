@@ -20,6 +20,7 @@
 // is certainly above that hit's R; the walker at the minimum is never cut.
 // The entry read at idx carries the next list's offset/degree and pos(prev)
 // for the next step, so each step is one dependent 32-byte load.
+#include <algorithm>
 #include <cmath>
 
 #include "dg_prims.cuh"
@@ -85,6 +86,7 @@ struct WalkKernelArgs {
     const BatchHdr* hdr;
     unsigned long long* next;
     uint32_t j_lo, j_hi;
+    uint32_t refill_min;  // empty slots a warp with walkers left waits for before refilling (1..32)
     uint32_t* d_err;
     FinArgs f;
 };
@@ -641,11 +643,18 @@ __global__ void __launch_bounds__(256, (ILP == 1 ? 4 : (ILP == 2 ? 3 : 1))) k_wa
     }
     bool exhausted = false;
     for (;;) {
-        // refill empty slots, one atomic per warp and slot; a new walker sends
-        // out its first load at once
+        // Refill empty slots, one atomic per warp and slot; a new walker sends
+        // out its first load at once.  Starting walkers holds the whole warp
+        // up for three dependent reads (id, task fields, start list), so a
+        // warp that still has walkers waits until at least refill_min of its
+        // slots are empty.  The walkers of one update are handed out together
+        // and tend to stop together, so the wait leaves few lanes idle.
 #pragma unroll
         for (int i = 0; i < ILP; ++i) {
-            const bool need = !w[i].active && !exhausted;
+            const bool idle = !w[i].active && !exhausted;
+            const uint32_t im = __ballot_sync(0xffffffffu, idle);
+            const uint32_t am = __ballot_sync(0xffffffffu, w[i].active);
+            const bool need = idle && ((uint32_t)__popc(im) >= a.refill_min || am == 0u);
             const uint32_t m = __ballot_sync(0xffffffffu, need);
             if (m) {
                 const int leader = __ffs(m) - 1;
@@ -822,6 +831,7 @@ static WalkKernelArgs make_args(const CSRView& H, const CSRView& G, const WalkTa
     a.next = d_next;
     a.j_lo = j_lo;
     a.j_hi = j_hi;
+    a.refill_min = 1;
     a.d_err = const_cast<uint32_t*>(d_err);
     return a;
 }
@@ -881,6 +891,7 @@ void launch_walk_batched(const CSRView& H, const CSRView& G, const WalkTasks& t,
                          const uint32_t* d_err, cudaStream_t st) {
     WalkKernelArgs a = make_args(H, G, t, p, r, d_hdr, d_next, j_lo, j_hi, d_err);
     a.f = f;
+    a.refill_min = (uint32_t)std::min(32, std::max(1, shape.refill));
     DG_CUDA(cudaMemsetAsync(d_next, 0, sizeof(unsigned long long), st));
     switch (shape.ilp) {
         case 1: launch_both<1>(a, shape, st); break;

@@ -49,6 +49,7 @@ struct WalkShape {
     int ilp = 2;
     int blocks_per_sm = 0;  // 0 = occupancy maximum
     int cut = 1;            // persistent launches the walked updates are split over
+    int refill = 16;        // empty walker slots a warp with walkers left waits for before refilling
 };
 
 // one launch per walked update j (block of s threads), the paper's scheme

@@ -40,7 +40,7 @@ EXPORTS = ("dg_config_default", "dg_create", "dg_destroy", "dg_status_str", "dg_
            "dg_unload_graph", "dg_init_sparsifier", "dg_apply_updates", "dg_apply_updates_device",
            "dg_query_sparsifier", "dg_query_graph", "dg_get_batch_stats", "dg_get_walker_records", "dg_compact",
            "dg_graph_bytes", "dg_launch_count", "dg_set_next_update_id", "dg_get_next_update_id",
-           "dg_set_walk_shape", "dg_submit_updates", "dg_wait", "dg_walk_estimate_noalloc")
+           "dg_set_walk_shape", "dg_set_walk_refill", "dg_submit_updates", "dg_wait", "dg_walk_estimate_noalloc")
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -63,7 +63,7 @@ class BatchStats(C.Structure):
                 ("walk_block", C.c_int32), ("walk_ilp", C.c_int32), ("walk_blocks_per_sm", C.c_int32),
                 ("graph_replayed", C.c_int32), ("mutate_ms", C.c_double), ("reduce_ms", C.c_double),
                 ("emit_ms", C.c_double), ("commit_ms", C.c_double), ("walk_cut", C.c_int32),
-                ("autotuned", C.c_int32)]
+                ("autotuned", C.c_int32), ("walk_refill", C.c_int32), ("reserved0", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -109,6 +109,7 @@ def load_library(path: str | None = None):
         "dg_set_next_update_id": (i32, [P, i32, u64]),
         "dg_get_next_update_id": (i32, [P, i32, C.POINTER(u64)]),
         "dg_set_walk_shape": (i32, [P, i32, i32, i32, i32]),
+        "dg_set_walk_refill": (i32, [P, i32, i32]),
         "dg_submit_updates": (i32, [P, i32, i64, P, P, C.POINTER(u64)]),
         "dg_wait": (i32, [P, u64, i32, C.POINTER(C.c_double)]),
         "dg_walk_estimate_noalloc": (i32, [P, i32, i64, P, P, P]),
@@ -304,8 +305,10 @@ class Graph:
     def next_update_id(self, value: int):
         _check(self._L.dg_set_next_update_id(self.ctx._h, self.gid, int(value)))
 
-    def set_walk_shape(self, block=0, ilp=0, blocks_per_sm=0):
+    def set_walk_shape(self, block=0, ilp=0, blocks_per_sm=0, refill=0):
         _check(self._L.dg_set_walk_shape(self.ctx._h, self.gid, int(block), int(ilp), int(blocks_per_sm)))
+        if refill:
+            _check(self._L.dg_set_walk_refill(self.ctx._h, self.gid, int(refill)))
 
     def walk_estimate_noalloc(self, d_queries_ptr: int, nq: int, d_out_ptr: int, stream=None):
         """Walk estimates for nq device-resident queries; the call allocates no

@@ -301,27 +301,97 @@ __device__ bool replay_path_warp(uint32_t j, int32_t b, int lane, const CSRView&
     return ok;
 }
 
-// Recovered edges of the replayed path of walked deletion j, one warp: every
-// edge of the walk that did not appear earlier in it and is not in H'.
-// Returns the number emitted (all lanes).
-__device__ uint32_t emit_path_warp(uint32_t j, int lane, const CSRView& H, const WalkParams& p, Cands& c,
-                                   const PathBufs& pb, uint32_t* d_err) {
-    const uint32_t len = pb.len[j];
-    const uint32_t* path = pb.v + (size_t)j * (p.T + 1);
-    uint32_t cnt = 0;
-    for (uint32_t s = lane; s < len; s += 32) {
-        const uint32_t x = path[s], y = path[s + 1];
-        bool dup = false;
-        for (uint32_t s2 = 0; s2 < s && !dup; ++s2) {
-            const uint32_t a0 = path[s2], a1 = path[s2 + 1];
-            dup = (a0 == x && a1 == y) || (a0 == y && a1 == x);
+// Membership in H of the edges (a[q], b[q]) for the q with on[q], each by
+// binary search in the shorter endpoint list; the N searches advance in
+// lockstep, so their loads overlap instead of forming N chains.
+template <int N>
+__device__ __forceinline__ void has_edges(const CSRView& g, const uint32_t* a, const uint32_t* b, const bool* on,
+                                          bool* found) {
+    uint32_t y[N], lo[N], hi[N], d[N];
+    const Ent* L[N];
+    uint32_t da[N], db[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        da[q] = on[q] ? g.deg[a[q]] : 0u;
+        db[q] = on[q] ? g.deg[b[q]] : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        const bool sw = db[q] < da[q];
+        const uint32_t x = sw ? b[q] : a[q];
+        y[q] = sw ? a[q] : b[q];
+        d[q] = sw ? db[q] : da[q];
+        L[q] = g.pool + (on[q] ? g.off[x] : 0u);
+        lo[q] = 0;
+        hi[q] = on[q] ? d[q] : 0u;
+    }
+    for (;;) {
+        uint32_t v[N];
+        bool any = false;
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            const bool act = lo[q] < hi[q];
+            any |= act;
+            v[q] = act ? L[q][(lo[q] + hi[q]) >> 1].nbr : 0u;
         }
-        if (dup || has_edge(H, x, y)) continue;
-        emit_edge(c, x, y, pb.w[(size_t)j * p.T + s], (uint32_t)H.n, d_err);
-        ++cnt;
+        if (!any) break;
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            if (lo[q] < hi[q]) {
+                const uint32_t mid = (lo[q] + hi[q]) >> 1;
+                if (v[q] < y[q]) lo[q] = mid + 1; else hi[q] = mid;
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < N; ++q) found[q] = on[q] && lo[q] < d[q] && L[q][lo[q]].nbr == y[q];
+}
+
+// Recovered edges of the replayed path of walked deletion j, one warp: every
+// edge of the walk that did not appear earlier in it and is not in H'.  A
+// path shorter than EMIT_SMEM is staged in the warp's shared buffer sbuf
+// (nullable), so the scan for earlier copies of an edge reads no global
+// memory, and a lane looks up EMIT_ILP of its edges in H' together.
+// Returns the number emitted (all lanes).
+constexpr uint32_t EMIT_SMEM = 256;  // path vertices a warp's shared buffer holds
+constexpr int EMIT_ILP = 2;
+
+__device__ uint32_t emit_path_warp(uint32_t j, int lane, const CSRView& H, const WalkParams& p, Cands& c,
+                                   const PathBufs& pb, uint32_t* d_err, uint32_t* sbuf) {
+    const uint32_t len = pb.len[j];
+    const uint32_t* gpath = pb.v + (size_t)j * (p.T + 1);
+    const bool staged = sbuf != nullptr && len < EMIT_SMEM;
+    if (staged) {
+        for (uint32_t s = lane; s <= len; s += 32) sbuf[s] = __ldcg(&gpath[s]);
+        __syncwarp();
+    }
+    const uint32_t* path = staged ? sbuf : gpath;
+    uint32_t cnt = 0;
+    for (uint32_t s0 = 0; s0 < len; s0 += 32u * EMIT_ILP) {
+        uint32_t x[EMIT_ILP], y[EMIT_ILP];
+        bool cand[EMIT_ILP], inh[EMIT_ILP];
+#pragma unroll
+        for (int q = 0; q < EMIT_ILP; ++q) {
+            const uint32_t s = s0 + 32u * q + lane;
+            cand[q] = s < len;
+            x[q] = cand[q] ? path[s] : 0u;
+            y[q] = cand[q] ? path[s + 1] : 0u;
+            for (uint32_t s2 = 0; s2 < s && cand[q]; ++s2) {
+                const uint32_t a0 = path[s2], a1 = path[s2 + 1];
+                if ((a0 == x[q] && a1 == y[q]) || (a0 == y[q] && a1 == x[q])) cand[q] = false;
+            }
+        }
+        has_edges<EMIT_ILP>(H, x, y, cand, inh);
+#pragma unroll
+        for (int q = 0; q < EMIT_ILP; ++q) {
+            if (cand[q] && !inh[q]) {
+                emit_edge(c, x[q], y[q], pb.w[(size_t)j * p.T + s0 + 32u * q + lane], (uint32_t)H.n, d_err);
+                ++cnt;
+            }
+        }
     }
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    return cnt;
+    return cnt;  // the shuffles above keep the buffer's readers ahead of its next writer
 }
 
 // Fallback of walked deletion j (no walker reached v), one warp: for each
@@ -379,7 +449,7 @@ __device__ bool fallback_warp(uint32_t j, int lane, const CSRView& H, const CSRV
 
 // everything that follows the walks of update j, one warp: result, kept
 // insertion, or the recovered (path or fallback) edges of a deletion
-__device__ void finalize_update(uint32_t j, int lane, const WalkKernelArgs& a, UpdTotals& tot) {
+__device__ void finalize_update(uint32_t j, int lane, const WalkKernelArgs& a, UpdTotals& tot, uint32_t* sbuf) {
     uint32_t nh = 0;
     const int bk = reduce_update(j, lane, a.t, a.p, a.r, a.f.res, a.f.best, a.f.dbg_reason, a.f.dbg_steps, tot, nh);
     const uint32_t i = a.t.idx[j];
@@ -400,7 +470,7 @@ __device__ void finalize_update(uint32_t j, int lane, const WalkKernelArgs& a, U
             ok = __shfl_sync(0xffffffffu, ok, 0);
             __syncwarp();
         }
-        const uint32_t e = ok ? emit_path_warp(j, lane, a.H, a.p, c, a.f.pb, a.d_err) : 0u;
+        const uint32_t e = ok ? emit_path_warp(j, lane, a.H, a.p, c, a.f.pb, a.d_err, sbuf) : 0u;
         if (lane == 0) {
             a.f.res[i].nrecovered = (int32_t)e;
             tot.rec += e;
@@ -752,6 +822,7 @@ __global__ void __launch_bounds__(256, (ILP == 1 ? 4 : (ILP == 2 ? 3 : 1))) k_wa
         }
     }
     if (!a.f.on) return;
+    __shared__ uint32_t s_emit[8][EMIT_SMEM];  // per warp (blocks of at most 256 threads)
     // No walkers left for this warp: finalize queued updates (in order of
     // completion) until every walked update of the launch is done.  Updates
     // complete because their walkers belong to warps that are running; the
@@ -777,7 +848,7 @@ __global__ void __launch_bounds__(256, (ILP == 1 ? 4 : (ILP == 2 ? 3 : 1))) k_wa
             break;
         }
         (void)ld_acquire(&a.f.queue[qi]);  // every lane acquires the records it is about to read
-        finalize_update(j, lane, a, tot);
+        finalize_update(j, lane, a, tot, s_emit[threadIdx.x >> 5]);
     }
     if (lane == 0) add_totals(a.f.ctr, tot);
 }

@@ -34,7 +34,8 @@ void ApplyScratch::ensure(DevAlloc& a, uint32_t changes, uint64_t stage_entries,
     if (changes > c_max || !f_head.p) {
         uint32_t c = changes < 1024 ? 1024 : changes;
         DBuf<uint32_t>* bufs[] = {&f_head, &f_ins, &f_del, &p_head, &p_ins, &p_del, &tv, &tstart, &tend,
-                                  &odeg, &ndeg, &ooff, &ncap, &rsz, &work, &r_off, &s_off, &w_off};
+                                  &odeg, &ndeg, &ooff, &ncap, &rsz, &work, &r_off, &s_off, &w_off,
+                                  &fwork, &f_off};
         for (auto* b : bufs) b->ensure(a, (size_t)c + 1, st);
         scan_tmp.ensure(a, scan_tmp_words(c + 1), st);
         c_max = c;
@@ -50,7 +51,7 @@ void ApplyScratch::ensure(DevAlloc& a, uint32_t changes, uint64_t stage_entries,
 void ApplyScratch::release(DevAlloc& a, cudaStream_t st) {
     DBuf<uint32_t>* bufs[] = {&f_head, &f_ins, &f_del, &p_head, &p_ins, &p_del, &tv, &tstart, &tend,
                               &odeg, &ndeg, &ooff, &ncap, &rsz, &work, &r_off, &s_off, &w_off,
-                              &scan_tmp, &totals};
+                              &fwork, &f_off, &scan_tmp, &totals};
     for (auto* b : bufs) b->release(a, st);
     stage.release(a, st);
     c_max = 0;
@@ -58,7 +59,7 @@ void ApplyScratch::release(DevAlloc& a, cudaStream_t st) {
 }
 
 uint64_t ApplyScratch::bytes() const {
-    return 18ull * (c_max + 1) * 4 + scan_tmp.bytes() + totals.bytes() + stage.bytes();
+    return 20ull * (c_max + 1) * 4 + scan_tmp.bytes() + totals.bytes() + stage.bytes();
 }
 
 void csr_alloc_vertices(CSR& g, DevAlloc& a, int32_t n, cudaStream_t st) {
@@ -226,7 +227,7 @@ struct PlanArgs {
     uint32_t n;
     float slack;
     const uint32_t *p_head, *p_ins, *p_del, *totals;
-    uint32_t *tv, *tstart, *tend, *odeg, *ndeg, *ooff, *ncap, *rsz, *work;
+    uint32_t *tv, *tstart, *tend, *odeg, *ndeg, *ooff, *ncap, *rsz, *work, *fwork;
 };
 
 __device__ __forceinline__ uint32_t pre_at(const uint32_t* p, uint32_t c, uint32_t count, uint32_t total) {
@@ -258,6 +259,10 @@ __global__ void k_plan_touch(PlanArgs a, const uint32_t* d_err) {
         a.ncap[t] = nc;
         a.rsz[t] = reloc ? nc : 0u;
         a.work[t] = od + (e - c);
+        // cache refresh work: every entry of the new list, or for a hub that
+        // stays a hub only its changes (see k_exec_fix)
+        const bool was = a.g.hub[x] != 0;
+        a.fwork[t] = (was && hub_next(was, nd)) ? e - c : nd;
     }
 }
 
@@ -294,14 +299,15 @@ void csr_plan(CSR& g, const ChangeList& cl, ApplyScratch& s, uint32_t* d_err, ui
     pa.slack = g.slack;
     pa.p_head = s.p_head.p; pa.p_ins = s.p_ins.p; pa.p_del = s.p_del.p; pa.totals = tot;
     pa.tv = s.tv.p; pa.tstart = s.tstart.p; pa.tend = s.tend.p; pa.odeg = s.odeg.p; pa.ndeg = s.ndeg.p;
-    pa.ooff = s.ooff.p; pa.ncap = s.ncap.p; pa.rsz = s.rsz.p; pa.work = s.work.p;
+    pa.ooff = s.ooff.p; pa.ncap = s.ncap.p; pa.rsz = s.rsz.p; pa.work = s.work.p; pa.fwork = s.fwork.p;
     k_plan_touch<<<grid, FLAT_THREADS, 0, st>>>(pa, d_err);
     ++g_launches;
     ScanJob j2;
     j2.in[0] = s.rsz.p;  j2.out[0] = s.r_off.p; j2.total[0] = tot + TOT_R;
     j2.in[1] = s.ndeg.p; j2.out[1] = s.s_off.p; j2.total[1] = tot + TOT_S;
     j2.in[2] = s.work.p; j2.out[2] = s.w_off.p; j2.total[2] = tot + TOT_WK;
-    j2.k = 3;
+    j2.in[3] = s.fwork.p; j2.out[3] = s.f_off.p; j2.total[3] = tot + TOT_F;
+    j2.k = 4;
     j2.err = d_err;
     scan_exclusive(j2, tot + TOT_X, C, s.scan_tmp.p, st);
     k_plan_alloc<<<1, 1, 0, st>>>(g.view(), tot, s.s_cap, d_err, pool_bit, cap_bit);
@@ -317,7 +323,7 @@ struct ExecArgs {
     CSRView g;
     uint32_t n;
     const uint32_t *p_ins, *p_del, *totals;
-    const uint32_t *tv, *tstart, *tend, *odeg, *ndeg, *ooff, *ncap, *rsz, *r_off, *s_off, *w_off;
+    const uint32_t *tv, *tstart, *tend, *odeg, *ndeg, *ooff, *ncap, *rsz, *r_off, *s_off, *w_off, *f_off;
     Ent* stage;
     uint32_t* touched;  // n + 1 words, see csr_exec
 };
@@ -446,35 +452,71 @@ __global__ void k_exec_place(ExecArgs a, const uint32_t* d_err) {
     });
 }
 
+// Cache refresh after a list execution.  For every touched vertex x the items
+// are the entries of its new list, except for a hub that stays a hub: entries
+// pointing at such a hub hold HUBREF, so its moved list is cached nowhere, and
+// its own entries need work only where an insertion created them (its items are
+// then its changes) or where the neighbour's list changed, which that
+// neighbour's pass refreshes from its side.  A hub's list can be long and
+// change little, so this keeps the work near the size of the batch.
 __global__ void k_exec_fix(ExecArgs a, uint32_t* d_err) {
     if (aborted(d_err)) return;
     const uint32_t X = a.totals[TOT_X];
-    const uint32_t S = a.totals[TOT_S];
-    for_segment_items<16>(a.s_off, X, S, [&](uint32_t item, uint32_t t, uint32_t local) {
+    const uint32_t F = a.totals[TOT_F];
+    const uint32_t gen = a.touched[a.n];  // marks of this execution only (older generations read as untouched)
+    const bool hubs = *a.g.nhub != 0u;
+    for_segment_items<16>(a.f_off, X, F, [&](uint32_t item, uint32_t t, uint32_t local) {
         (void)item;
         const uint32_t x = a.tv[t];
         const uint32_t lx = a.g.off[x];
+        const uint32_t mx = a.touched[x];
+        const uint32_t tx = (mx >> 2) == gen ? (mx & 3u) : 0u;
+        const bool x_hub = a.g.hub[x] != 0;
+        if (x_hub && !(tx & 2u)) {
+            // a hub that stays a hub: the entry each of its insertions created
+            const uint32_t c = a.tstart[t] + local;
+            if (a.cl.kinds[a.cl.vals[c]] != CHG_INS) return;
+            const uint32_t y = (uint32_t)(a.cl.keys[c] - (uint64_t)x * a.n);
+            const uint32_t dx = a.g.deg[x];
+            const uint32_t px = lower_bound_nbr(a.g.pool + lx, dx, y);
+            if (y >= a.n || px >= dx || a.g.pool[lx + px].nbr != y) {
+                atomicOr(d_err, (uint32_t)ERR_INTERNAL);
+                return;
+            }
+            if (a.g.hub[y] != 0) {
+                *reinterpret_cast<uint4*>(a.g.pool + lx + px) = make_uint4(y, HUBREF, 1u, 0u);
+            } else {
+                const uint32_t ly = a.g.off[y], dy = a.g.deg[y];
+                const uint32_t p = lower_bound_nbr(a.g.pool + ly, dy, x);
+                if (p >= dy || a.g.pool[ly + p].nbr != x) {
+                    atomicOr(d_err, (uint32_t)ERR_INTERNAL);
+                    return;
+                }
+                *reinterpret_cast<uint4*>(a.g.pool + lx + px) = make_uint4(y, ly, dy, p);
+            }
+            return;
+        }
         const uint4 e = *reinterpret_cast<const uint4*>(a.g.pool + lx + local);
         const uint32_t y = e.x;
         if (y >= a.n) {
             atomicOr(d_err, (uint32_t)ERR_INTERNAL);
             return;
         }
-        // marks of this execution only (older generations read as untouched)
-        const uint32_t gen = a.touched[a.n];
-        const uint32_t mx = a.touched[x], my = a.touched[y];
-        const uint32_t tx = (mx >> 2) == gen ? (mx & 3u) : 0u, ty = (my >> 2) == gen ? (my & 3u) : 0u;
-        const bool x_hub = a.g.hub[x] != 0;
+        const uint32_t my = a.touched[y];
+        const uint32_t ty = (my >> 2) == gen ? (my & 3u) : 0u;
         const bool fresh = e.z == 0u;
+        // a touched neighbour that stays a hub does not visit its entry pointing
+        // back at x, so it is written here
+        const bool y_stable_hub = hubs && (ty & 1u) && !(ty & 2u) && a.g.hub[y] != 0;
         const bool need_own = fresh || (ty & 1u);
-        const bool need_back = !(ty & 1u) && !(x_hub && !(tx & 2u));
+        const bool need_back = !(ty & 1u) || y_stable_hub;
         if (!need_own && !need_back) return;
         const bool y_hub = a.g.hub[y] != 0;
         const uint32_t ly = a.g.off[y], dy = a.g.deg[y];
         uint32_t p = 0xFFFFFFFFu;      // x's slot in y's list, found when needed
         auto locate = [&]() -> bool {
             if (p != 0xFFFFFFFFu) return true;
-            if (!fresh && e.y != HUBREF) {  // a valid copied entry caches the slot
+            if (!fresh && e.y != HUBREF && !(ty & 1u)) {  // a valid copied entry caches the slot
                 p = e.w;
             } else {
                 p = lower_bound_nbr(a.g.pool + ly, dy, x);
@@ -487,23 +529,19 @@ __global__ void k_exec_fix(ExecArgs a, uint32_t* d_err) {
         };
         // (i) this entry: its cache is still right when it was copied from x's old
         // list and y's list did not change
-        if (fresh || (ty & 1u)) {
+        if (need_own) {
             if (y_hub) {
                 *reinterpret_cast<uint4*>(a.g.pool + lx + local) = make_uint4(y, HUBREF, 1u, 0u);
             } else {
-                p = lower_bound_nbr(a.g.pool + ly, dy, x);
-                if (p >= dy || a.g.pool[ly + p].nbr != x) {
-                    atomicOr(d_err, (uint32_t)ERR_INTERNAL);
-                    return;
-                }
+                if (!locate()) return;
                 *reinterpret_cast<uint4*>(a.g.pool + lx + local) = make_uint4(y, ly, dy, p);
             }
         }
-        // (ii) y's entry pointing at x, when y's list is unchanged (otherwise y's own
-        // pass writes it).  A hub that stayed a hub is referenced by HUBREF, which
-        // no change of its list can make stale.
-        if (ty & 1u) return;
-        if (x_hub && !(tx & 2u)) return;
+        // (ii) y's entry pointing at x (x's list moved or resized), when y's own
+        // pass does not write it.  Entries pointing at x hold HUBREF when x is a
+        // hub that stayed a hub (handled above), and no change of x's list can
+        // make those stale.
+        if (!need_back) return;
         if (!locate()) return;
         const uint4 back = x_hub ? make_uint4(x, HUBREF, 1u, 0u) : make_uint4(x, lx, a.g.deg[x], local);
         *reinterpret_cast<uint4*>(a.g.pool + ly + p) = back;
@@ -521,6 +559,7 @@ void csr_exec(CSR& g, const ChangeList& cl, ApplyScratch& s, uint32_t* touched, 
     a.tv = s.tv.p; a.tstart = s.tstart.p; a.tend = s.tend.p; a.odeg = s.odeg.p; a.ndeg = s.ndeg.p;
     a.ooff = s.ooff.p; a.ncap = s.ncap.p; a.rsz = s.rsz.p; a.r_off = s.r_off.p; a.s_off = s.s_off.p;
     a.w_off = s.w_off.p;
+    a.f_off = s.f_off.p;
     a.stage = s.stage.p;
     a.touched = touched;
     // merge reads the old lists; meta then points every touched vertex at its

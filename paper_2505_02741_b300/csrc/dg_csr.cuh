@@ -58,13 +58,13 @@ struct ChangeList {
     uint32_t max_count = 0;
 };
 
-enum { TOT_X = 0, TOT_NI, TOT_ND, TOT_R, TOT_S, TOT_WK, TOT_BASE_LO, TOT_BASE_HI, TOT_WORDS = 8 };
+enum { TOT_X = 0, TOT_NI, TOT_ND, TOT_R, TOT_S, TOT_WK, TOT_BASE_LO, TOT_BASE_HI, TOT_F, TOT_WORDS = 9 };
 
 struct ApplyScratch {
     uint32_t c_max = 0;
     uint64_t s_cap = 0;  // entries of staging space
     DBuf<uint32_t> f_head, f_ins, f_del, p_head, p_ins, p_del;
-    DBuf<uint32_t> tv, tstart, tend, odeg, ndeg, ooff, ncap, rsz, work, r_off, s_off, w_off;
+    DBuf<uint32_t> tv, tstart, tend, odeg, ndeg, ooff, ncap, rsz, work, r_off, s_off, w_off, fwork, f_off;
     DBuf<uint32_t> scan_tmp, totals;
     DBuf<Ent> stage;
     void ensure(DevAlloc& a, uint32_t changes, uint64_t stage_entries, cudaStream_t st);

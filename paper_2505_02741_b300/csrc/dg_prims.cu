@@ -37,9 +37,9 @@ __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned lon
 // scan
 // ---------------------------------------------------------------------------
 struct ScanArgs {
-    const uint32_t* in[3];
-    uint32_t* out[3];
-    uint32_t* total[3];
+    const uint32_t* in[4];
+    uint32_t* out[4];
+    uint32_t* total[4];
     int k;
     uint32_t* err;
 };
@@ -51,8 +51,8 @@ constexpr uint32_t LB_TILE = LB_THREADS * LB_ITEMS;
 
 static inline uint32_t lb_tiles(uint32_t n_max) { return (n_max + LB_TILE - 1) / LB_TILE; }
 
-// layout of tmp: [counter (2 words, 8-byte aligned) | status u64 x 3 x tiles]
-size_t scan_tmp_words(uint32_t n_max) { return 4 + 2ull * 3 * (lb_tiles(n_max) + 1); }
+// layout of tmp: [counter (2 words, 8-byte aligned) | status u64 x 4 arrays x tiles]
+size_t scan_tmp_words(uint32_t n_max) { return 4 + 2ull * 4 * (lb_tiles(n_max) + 1); }
 
 // one CTA walks the array in chunks of 1024 x 8 with a running carry
 __global__ void __launch_bounds__(1024) k_scan_single(ScanArgs a, const uint32_t* d_n, uint32_t n_max) {
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(LB_THREADS) k_scan_lookback(ScanArgs a, const 
 void scan_exclusive(const ScanJob& job, const uint32_t* d_n, uint32_t n_max, uint32_t* tmp,
                     cudaStream_t st) {
     ScanArgs a;
-    for (int j = 0; j < 3; ++j) {
+    for (int j = 0; j < 4; ++j) {
         a.in[j] = job.in[j];
         a.out[j] = job.out[j];
         a.total[j] = job.total[j];

@@ -14,9 +14,9 @@ constexpr uint32_t PRIM_ERR_SPIN = 1u << 8;
 // Exclusive prefix sums of up to three uint32 arrays of the same length n.
 // n = *d_n (or n_max when d_n is null).  total[a] (nullable) receives the sum.
 struct ScanJob {
-    const uint32_t* in[3] = {nullptr, nullptr, nullptr};
-    uint32_t* out[3] = {nullptr, nullptr, nullptr};
-    uint32_t* total[3] = {nullptr, nullptr, nullptr};
+    const uint32_t* in[4] = {nullptr, nullptr, nullptr, nullptr};
+    uint32_t* out[4] = {nullptr, nullptr, nullptr, nullptr};
+    uint32_t* total[4] = {nullptr, nullptr, nullptr, nullptr};
     int k = 0;
     uint32_t* err = nullptr;  // optional: PRIM_ERR_SPIN is or-ed in here
 };

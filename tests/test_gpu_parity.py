@@ -426,6 +426,51 @@ def test_hub_references_and_status_flips():
     ctx.close()
 
 
+def test_power_law_hubs_many_batches():
+    """A small symmetrised R-MAT graph has many hubs, most of which stay hubs
+    from batch to batch while their neighbours' lists change: the cache refresh
+    then visits only a stable hub's new entries and refreshes the others from
+    the neighbour's side.  Walks through those hubs, the results, H and G must
+    equal the oracle over several batches of insertions and deletions."""
+    rng = np.random.default_rng(5)
+    n, a, b = W.rmat(11, 12000, rng)
+    w = rng.uniform(0.5, 5.0, len(a))
+    h = W.init_sparsifier(n, a, b, w, rng)
+    deg = np.bincount(np.concatenate([a, b]), minlength=n)
+    assert (deg >= HUB_HI).sum() >= 20
+    ctx, g, o = pair(n, a, b, w, h, T=40, s=16, K=60.0)
+    wl = W.Workload("rmat_s11", n, a, b, w, h, K=60.0, T=40, s=16, seed=0)
+    stream = W.UpdateStream(wl, rng, ("uniform",), lambda r, u, v: r.uniform(0.5, 5.0, len(u)))
+    for bi in range(4):
+        bt = stream.next_batch(300, 400)
+        step_both(g, o, bt.u, bt.v, bt.w, bt.op, where=f"rmat batch {bi}")
+    ctx.close()
+
+
+def test_walk_refill_threshold():
+    """The refill threshold changes only when warps start new walkers: every
+    value gives the same outputs; values outside 1..32 are rejected."""
+    wl, st = W.make_grid(40, 40)
+    batches = [st.next_batch(300, 200) for _ in range(3)]
+    outs = []
+    for refill in (1, 7, 16, 32):
+        ctx = D.Context(del_prune=False)
+        g = ctx.load_graph(wl.n, wl.a, wl.b, wl.w)
+        g.init_sparsifier(wl.a[wl.h_ids], wl.b[wl.h_ids])
+        g.set_walk_shape(128, 1, 0, refill=refill)
+        rs = [g.apply(D.make_updates(bt.u, bt.v, bt.w, bt.op)) for bt in batches]
+        assert g.stats()["walk_refill"] == refill
+        outs.append((rs, g.sparsifier()))
+        for bad in (-1, 33):
+            with pytest.raises(D.DgError):
+                g.set_walk_shape(refill=bad)
+        ctx.close()
+    for rs, hh in outs[1:]:
+        for r0, r1 in zip(outs[0][0], rs):
+            assert_same_outputs(r0, r1)
+        assert_edges_equal(hh, outs[0][1], "H")
+
+
 def test_mesh3d_small_multi_batch():
     wl, st = W.make_mesh3d(24, 24, 24)
     ctx, g, o = pair(wl.n, wl.a, wl.b, wl.w, wl.h_ids)

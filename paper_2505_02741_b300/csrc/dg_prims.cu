@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(LB_THREADS) k_scan_lookback(ScanArgs a, const 
                     done = inc_mask != 0u;
                     top -= 32;
                 }
-                __threadfence();
+                // the status word carries its own value: no fence orders it
                 if (l == 0) atomicExch(&st[t], LB_INC | (unsigned long long)(excl + agg));
             }
             if (l == 0) {
@@ -304,6 +304,12 @@ __global__ void __launch_bounds__(OS_THREADS) k_os_pass(const uint64_t* __restri
     const uint32_t t = s_tile;
     const uint32_t base = t * OS_TILE;
     if (t >= tiles || base >= n) return;
+    // the pass's digit totals (warp 0, 8 per lane), read alongside the keys
+    uint32_t gv[8];
+    if (w == 0) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) gv[q] = gh[l * 8 + q];
+    }
     // load: warp w holds keys [base + 128 w, base + 128 w + 128), four chunks of 32
     uint64_t k[OS_ITEMS];
     uint32_t v[OS_ITEMS], d[OS_ITEMS], rk[OS_ITEMS];
@@ -326,12 +332,9 @@ __global__ void __launch_bounds__(OS_THREADS) k_os_pass(const uint64_t* __restri
     }
     // global start of every digit: exclusive scan of the digit totals (warp 0, 8 per lane)
     if (w == 0) {
-        uint32_t gv[8], s8 = 0;
+        uint32_t s8 = 0;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            gv[q] = gh[l * 8 + q];
-            s8 += gv[q];
-        }
+        for (int q = 0; q < 8; ++q) s8 += gv[q];
         uint32_t x = s8;
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -387,7 +390,6 @@ __global__ void __launch_bounds__(OS_THREADS) k_os_pass(const uint64_t* __restri
                 }
                 top -= WIN;
             }
-            __threadfence();
             atomicExch(&status[(size_t)t * 256 + dg], OS_INC | ((excl + run) & OS_VAL));
         }
         s_base[dg] = gstart + excl;

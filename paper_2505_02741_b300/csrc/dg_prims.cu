@@ -54,64 +54,85 @@ static inline uint32_t lb_tiles(uint32_t n_max) { return (n_max + LB_TILE - 1) /
 // layout of tmp: [counter (2 words, 8-byte aligned) | status u64 x 4 arrays x tiles]
 size_t scan_tmp_words(uint32_t n_max) { return 4 + 2ull * 4 * (lb_tiles(n_max) + 1); }
 
-// one CTA walks the array in chunks of 1024 x 8 with a running carry
+// one CTA walks the arrays in chunks of 1024 x 8 with running carries, all
+// k arrays of the job in the same chunk loop
 __global__ void __launch_bounds__(1024) k_scan_single(ScanArgs a, const uint32_t* d_n, uint32_t n_max) {
-    __shared__ uint32_t sh[32];
-    __shared__ uint32_t carry_sh;
+    __shared__ uint32_t sh[4][32];
+    __shared__ uint32_t carry_sh[4];
     const uint32_t n = load_n(d_n, n_max);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int nw = (int)(blockDim.x >> 5);
+    const int K = a.k;
     constexpr int IT = 8;
-    for (int j = 0; j < a.k; ++j) {
-        if (threadIdx.x == 0) carry_sh = 0;
-        __syncthreads();
-        for (uint32_t c0 = 0; c0 < n; c0 += blockDim.x * IT) {
-            const uint32_t mine = c0 + threadIdx.x * IT;
-            uint32_t v[IT];
-            uint32_t s = 0;
+    if (threadIdx.x < 4) carry_sh[threadIdx.x] = 0;
+    __syncthreads();
+    for (uint32_t c0 = 0; c0 < n; c0 += blockDim.x * IT) {
+        const uint32_t mine = c0 + threadIdx.x * IT;
+        uint32_t v[4][IT], s4[4], x4[4];
 #pragma unroll
-            for (int i = 0; i < IT; ++i) {
-                v[i] = (mine + i < n) ? a.in[j][mine + i] : 0u;
-                s += v[i];
+        for (int j = 0; j < 4; ++j) {
+            s4[j] = 0;
+            if (j < K) {
+#pragma unroll
+                for (int i = 0; i < IT; ++i) {
+                    v[j][i] = (mine + i < n) ? a.in[j][mine + i] : 0u;
+                    s4[j] += v[j][i];
+                }
             }
-            uint32_t x = s;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            uint32_t x = s4[j];
             for (int o = 1; o < 32; o <<= 1) {
-                uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
                 if (l >= o) x += y;
             }
-            if (l == 31) sh[w] = x;
-            __syncthreads();
-            if (threadIdx.x < 32) {
-                uint32_t t = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0u;
-                for (int o = 1; o < 32; o <<= 1) {
-                    uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
-                    if (l >= o) t += y;
-                }
-                sh[l] = t;
+            x4[j] = x;
+            if (l == 31) sh[j][w] = x;
+        }
+        __syncthreads();
+        if (w < K) {  // warp j scans the warp totals of array j
+            uint32_t tt = (l < nw) ? sh[w][l] : 0u;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, tt, o);
+                if (l >= o) tt += y;
             }
-            __syncthreads();
-            const uint32_t carry = carry_sh;
-            uint32_t run = carry + ((w > 0) ? sh[w - 1] : 0u) + x - s;
+            sh[w][l] = tt;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (j >= K) break;
+            uint32_t run = carry_sh[j] + ((w > 0) ? sh[j][w - 1] : 0u) + x4[j] - s4[j];
 #pragma unroll
             for (int i = 0; i < IT; ++i) {
                 if (mine + i < n) a.out[j][mine + i] = run;
-                run += v[i];
+                run += v[j][i];
             }
-            __syncthreads();
-            if (threadIdx.x == blockDim.x - 1) carry_sh = carry + sh[31];
-            __syncthreads();
         }
-        if (threadIdx.x == 0 && a.total[j]) *a.total[j] = carry_sh;
         __syncthreads();
+        if (threadIdx.x < (unsigned)K) carry_sh[threadIdx.x] += sh[threadIdx.x][31];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (K > 0 && a.total[0]) *a.total[0] = carry_sh[0];
+        if (K > 1 && a.total[1]) *a.total[1] = carry_sh[1];
+        if (K > 2 && a.total[2]) *a.total[2] = carry_sh[2];
+        if (K > 3 && a.total[3]) *a.total[3] = carry_sh[3];
     }
 }
 
 // status word: high 32 bits flag (0 empty, 1 aggregate, 2 inclusive), low 32 bits value
 constexpr unsigned long long LB_AGG = 1ull << 32, LB_INC = 2ull << 32;
 
+// All k arrays of a job go through one pass together: their tile inputs are
+// loaded at once, block-scanned side by side, and warp j looks back for array
+// j, so a tile costs the round trips of one array rather than k.
 __global__ void __launch_bounds__(LB_THREADS) k_scan_lookback(ScanArgs a, const uint32_t* d_n, uint32_t n_max,
                                                              uint32_t* tmp, uint32_t tiles) {
-    __shared__ uint32_t sh[LB_THREADS / 32];
-    __shared__ uint32_t s_tile, s_prefix;
+    constexpr int NW = LB_THREADS / 32;
+    __shared__ uint32_t sh[4][NW];
+    __shared__ uint32_t s_tile, s_prefix[4];
     unsigned long long* status = reinterpret_cast<unsigned long long*>(tmp + 4);
     const uint32_t n = load_n(d_n, n_max);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -121,80 +142,89 @@ __global__ void __launch_bounds__(LB_THREADS) k_scan_lookback(ScanArgs a, const 
     const uint32_t base = t * LB_TILE;
     const uint32_t nt = (n + LB_TILE - 1) / LB_TILE;  // tiles holding data
     if (t >= tiles) return;
-    for (int j = 0; j < a.k; ++j) {
-        unsigned long long* st = status + (size_t)j * (tiles + 1);
-        const uint32_t mine = base + threadIdx.x * LB_ITEMS;
-        uint32_t v[LB_ITEMS];
-        uint32_t s = 0;
+    const int K = a.k;
+    const uint32_t mine = base + threadIdx.x * LB_ITEMS;
+    uint32_t v[4][LB_ITEMS], s4[4], x4[4];
 #pragma unroll
-        for (int i = 0; i < LB_ITEMS; ++i) {
-            v[i] = (mine + i < n) ? a.in[j][mine + i] : 0u;
-            s += v[i];
+    for (int j = 0; j < 4; ++j) {
+        s4[j] = 0;
+        if (j < K) {
+#pragma unroll
+            for (int i = 0; i < LB_ITEMS; ++i) {
+                v[j][i] = (mine + i < n) ? a.in[j][mine + i] : 0u;
+                s4[j] += v[j][i];
+            }
         }
-        uint32_t x = s;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        uint32_t x = s4[j];
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
             if (l >= o) x += y;
         }
-        if (l == 31) sh[w] = x;
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            uint32_t tt = (l < LB_THREADS / 32) ? sh[l] : 0u;
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t y = __shfl_up_sync(0xffffffffu, tt, o);
-                if (l >= o) tt += y;
-            }
-            if (l < LB_THREADS / 32) sh[l] = tt;
+        x4[j] = x;
+        if (l == 31) sh[j][w] = x;
+    }
+    __syncthreads();
+    if (w < K) {  // warp j: scan of the warp totals of array j, then its look-back
+        const int j = w;
+        uint32_t tt = (l < NW) ? sh[j][l] : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, tt, o);
+            if (l >= o) tt += y;
         }
-        __syncthreads();
-        const uint32_t agg = sh[LB_THREADS / 32 - 1];
-        if (threadIdx.x < 32) {
-            // warp 0 looks back over a window of 32 predecessors at a time
-            uint32_t excl = 0;
-            if (t == 0) {
-                if (l == 0) atomicExch(&st[t], LB_INC | agg);
-            } else {
-                if (l == 0) atomicExch(&st[t], LB_AGG | agg);
-                int top = (int)t - 1;  // newest predecessor not yet summed
-                bool done = false;
-                while (!done && top >= 0) {
-                    const int p = top - l;
-                    unsigned long long sv = LB_INC;  // lanes before tile 0 act as an inclusive zero
-                    if (p >= 0) {
-                        uint32_t spins = 0;
-                        while (((sv = ld_volatile_u64(&st[p])) >> 32) == 0ull && ++spins < SPIN_LIMIT) __nanosleep(32);
-                    }
-                    const bool empty = (sv >> 32) == 0ull;
-                    if (__any_sync(0xffffffffu, empty)) {
-                        if (l == 0 && a.err) atomicOr(a.err, PRIM_ERR_SPIN);
-                        break;
-                    }
-                    const uint32_t inc_mask = __ballot_sync(0xffffffffu, (sv >> 32) == 2ull);
-                    // sum lanes up to and including the nearest inclusive prefix
-                    const int stop = inc_mask ? __ffs(inc_mask) - 1 : 31;
-                    uint32_t part = (l <= stop) ? (uint32_t)sv : 0u;
-                    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-                    excl += part;
-                    done = inc_mask != 0u;
-                    top -= 32;
+        const uint32_t agg = __shfl_sync(0xffffffffu, tt, NW - 1);
+        unsigned long long* st = status + (size_t)j * (tiles + 1);
+        uint32_t excl = 0;
+        if (t == 0) {
+            if (l == 0) atomicExch(&st[t], LB_INC | agg);
+        } else {
+            if (l == 0) atomicExch(&st[t], LB_AGG | agg);
+            int top = (int)t - 1;  // newest predecessor not yet summed
+            bool done = false;
+            while (!done && top >= 0) {
+                const int p = top - l;
+                unsigned long long sv = LB_INC;  // lanes before tile 0 act as an inclusive zero
+                if (p >= 0) {
+                    uint32_t spins = 0;
+                    while (((sv = ld_volatile_u64(&st[p])) >> 32) == 0ull && ++spins < SPIN_LIMIT) __nanosleep(32);
                 }
-                // the status word carries its own value: no fence orders it
-                if (l == 0) atomicExch(&st[t], LB_INC | (unsigned long long)(excl + agg));
+                const bool empty = (sv >> 32) == 0ull;
+                if (__any_sync(0xffffffffu, empty)) {
+                    if (l == 0 && a.err) atomicOr(a.err, PRIM_ERR_SPIN);
+                    break;
+                }
+                const uint32_t inc_mask = __ballot_sync(0xffffffffu, (sv >> 32) == 2ull);
+                // sum lanes up to and including the nearest inclusive prefix
+                const int stop = inc_mask ? __ffs(inc_mask) - 1 : 31;
+                uint32_t part = (l <= stop) ? (uint32_t)sv : 0u;
+                for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+                excl += part;
+                done = inc_mask != 0u;
+                top -= 32;
             }
-            if (l == 0) {
-                s_prefix = excl;
-                if (t + 1 == nt && a.total[j]) *a.total[j] = excl + agg;
-                if (nt == 0 && t == 0 && a.total[j]) *a.total[j] = 0;
-            }
+            // the status word carries its own value: no fence orders it
+            if (l == 0) atomicExch(&st[t], LB_INC | (unsigned long long)(excl + agg));
         }
-        __syncthreads();
-        uint32_t run = s_prefix + ((w > 0) ? sh[w - 1] : 0u) + x - s;
+        if (l < NW) sh[j][l] = tt;  // inclusive warp totals
+        if (l == 0) {
+            s_prefix[j] = excl;
+            uint32_t* total = j == 0 ? a.total[0] : j == 1 ? a.total[1] : j == 2 ? a.total[2] : a.total[3];
+            if (t + 1 == nt && total) *total = excl + agg;
+            if (nt == 0 && t == 0 && total) *total = 0;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (j >= K) break;
+        uint32_t run = s_prefix[j] + ((w > 0) ? sh[j][w - 1] : 0u) + x4[j] - s4[j];
 #pragma unroll
         for (int i = 0; i < LB_ITEMS; ++i) {
             if (mine + i < n) a.out[j][mine + i] = run;
-            run += v[i];
+            run += v[j][i];
         }
-        __syncthreads();
     }
 }
 

@@ -241,13 +241,25 @@ __global__ void k_plan_touch(PlanArgs a, const uint32_t* d_err) {
     for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < count; c += gridDim.x * blockDim.x) {
         const uint32_t x = (uint32_t)(a.cl.keys[c] / a.n);
         if (!(c == 0 || (uint32_t)(a.cl.keys[c - 1] / a.n) != x)) continue;
-        const uint32_t t = a.p_head[c];
-        const uint32_t e = lower_bound_arr<uint64_t>(a.cl.keys, c, count, (uint64_t)(x + 1) * a.n);
-        const uint32_t ins = pre_at(a.p_ins, e, count, NI) - a.p_ins[c];
-        const uint32_t del = pre_at(a.p_del, e, count, ND) - a.p_del[c];
+        // x's list fields and prefix counts do not depend on the run's end: sent first
         const uint32_t od = a.g.deg[x];
-        const uint32_t nd = od + ins - del;
         const uint32_t oc = a.g.cap[x];
+        const uint32_t oo = a.g.off[x];
+        const bool was_hub = a.g.hub[x] != 0;
+        const uint32_t t = a.p_head[c];
+        const uint32_t pi = a.p_ins[c], pd = a.p_del[c];
+        // end of x's run: galloping from c (runs are short except at hubs)
+        const uint64_t kend = (uint64_t)(x + 1) * a.n;
+        uint32_t lo = c, hi = c + 1, step = 1;
+        while (hi < count && a.cl.keys[hi] < kend) {
+            lo = hi;
+            hi = (count - hi > step) ? hi + step : count;
+            step <<= 1;
+        }
+        const uint32_t e = lower_bound_arr<uint64_t>(a.cl.keys, lo + 1, hi, kend);
+        const uint32_t ins = pre_at(a.p_ins, e, count, NI) - pi;
+        const uint32_t del = pre_at(a.p_del, e, count, ND) - pd;
+        const uint32_t nd = od + ins - del;
         const bool reloc = nd > oc;
         const uint32_t nc = reloc ? cap_for(nd, a.slack) : oc;
         a.tv[t] = x;
@@ -255,14 +267,13 @@ __global__ void k_plan_touch(PlanArgs a, const uint32_t* d_err) {
         a.tend[t] = e;
         a.odeg[t] = od;
         a.ndeg[t] = nd;
-        a.ooff[t] = a.g.off[x];
+        a.ooff[t] = oo;
         a.ncap[t] = nc;
         a.rsz[t] = reloc ? nc : 0u;
         a.work[t] = od + (e - c);
         // cache refresh work: every entry of the new list, or for a hub that
         // stays a hub only its changes (see k_exec_fix)
-        const bool was = a.g.hub[x] != 0;
-        a.fwork[t] = (was && hub_next(was, nd)) ? e - c : nd;
+        a.fwork[t] = (was_hub && hub_next(was_hub, nd)) ? e - c : nd;
     }
 }
 
@@ -354,12 +365,37 @@ __global__ void k_exec_meta(ExecArgs a, const uint32_t* d_err) {
     }
 }
 
+// Largest t in [0, nseg) with seg_off[t] <= key (seg_off non-decreasing,
+// seg_off[0] = 0 <= key), found by the whole warp: each round the 32 lanes
+// probe 32 spread positions, so a round narrows the range 32-fold and the
+// search costs log32(nseg) dependent loads instead of log2(nseg).  All lanes
+// call it with the same key and get the result.
+__device__ __forceinline__ uint32_t warp_last_leq(const uint32_t* seg_off, uint32_t nseg, uint32_t key) {
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t lo = 0, hi = nseg;  // answer in [lo, hi), seg_off[lo] <= key
+    while (hi - lo > 1) {
+        const uint32_t p = lo + 1u + (uint32_t)(((uint64_t)(hi - lo - 1) * lane) >> 5);
+        const bool ok = seg_off[p] <= key;
+        const uint32_t m = __ballot_sync(0xffffffffu, ok);
+        const uint32_t pj = __shfl_sync(0xffffffffu, p, m ? 31 - __clz(m) : 0);
+        const uint32_t pn = __shfl_sync(0xffffffffu, p, m ? min(32 - __clz(m), 31) : 0);
+        if (!m) {
+            hi = pj;  // every probe is past key: the answer is lo
+        } else {
+            lo = pj;
+            if (m != 0xffffffffu) hi = pn;  // the next probe is past key
+        }
+    }
+    return lo;
+}
+
 // Visit items [0, total) of consecutive segments (seg_off: exclusive start of
 // each of nseg segments).  Each warp takes one contiguous range of the items
-// (a multiple of 32, sized from the live total so all warps share the work);
-// lane 0 finds the segment of the range start by binary search, then every lane
-// carries its own segment index forward as its items advance (amortised O(1)
-// per item on long lists, one search per warp on short ones).
+// (a multiple of 32, sized from the live total so all warps share the work)
+// and finds the segment of its start with a warp-wide search; per 32 items the
+// lanes load the next 32 segment starts together and each finds its own
+// segment among them by register shuffles, falling back to stepping forward
+// only when more than 32 segments begin inside the 32 items.
 template <int IT, typename F>
 __device__ __forceinline__ void for_segment_items(const uint32_t* seg_off, uint32_t nseg, uint32_t total, F&& f) {
     const uint32_t lane = threadIdx.x & 31u;
@@ -369,14 +405,34 @@ __device__ __forceinline__ void for_segment_items(const uint32_t* seg_off, uint3
     const uint64_t start = (uint64_t)warp * per;
     if (start >= total) return;
     const uint32_t end = (uint32_t)((start + per < (uint64_t)total) ? start + per : (uint64_t)total);
-    uint32_t t = 0;
-    if (lane == 0) t = upper_bound_arr<uint32_t>(seg_off, 0, nseg, (uint32_t)start) - 1;
-    t = __shfl_sync(0xffffffffu, t, 0);
+    uint32_t t = warp_last_leq(seg_off, nseg, (uint32_t)start);  // segment of the first item
+    uint32_t t_off = seg_off[t];
     for (uint32_t c0 = (uint32_t)start; c0 < end; c0 += 32u) {
         const uint32_t item = c0 + lane;
-        if (item >= end) break;
-        while (t + 1 < nseg && seg_off[t + 1] <= item) ++t;
-        f(item, t, item - seg_off[t]);
+        // starts of segments t+1 .. t+32 (non-decreasing; past the end: +inf)
+        const uint32_t wi = t + 1u + lane;
+        const uint32_t wv = wi < nseg ? seg_off[wi] : 0xFFFFFFFFu;
+        // k = number of those starts <= item (binary search over the lanes)
+        uint32_t k = 0;
+#pragma unroll
+        for (uint32_t bstep = 16; bstep > 0; bstep >>= 1) {
+            const uint32_t v = __shfl_sync(0xffffffffu, wv, (int)(k + bstep - 1u));
+            if (v <= item) k += bstep;
+        }
+        const uint32_t w31 = __shfl_sync(0xffffffffu, wv, 31);
+        if (k == 31u && w31 <= item) k = 32u;
+        uint32_t ti = t + k;
+        const uint32_t wprev = __shfl_sync(0xffffffffu, wv, (int)(k ? k - 1u : 0u));
+        uint32_t to = k ? wprev : t_off;
+        if (k == 32u) {  // more than 32 segments start before this item
+            while (ti + 1 < nseg && seg_off[ti + 1] <= item) ++ti;
+            to = seg_off[ti];
+        }
+        if (item < end) f(item, ti, item - to);
+        // the last item's segment is where the next 32 items start looking
+        const uint32_t last = min(31u, end - 1u - c0);
+        t = __shfl_sync(0xffffffffu, ti, (int)last);
+        t_off = __shfl_sync(0xffffffffu, to, (int)last);
     }
 }
 

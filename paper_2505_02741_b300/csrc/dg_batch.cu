@@ -375,7 +375,7 @@ uint64_t BatchWS::bytes() const {
     b += gscan.bytes() + gcount.bytes() + hflag.bytes() + hpos.bytes() + hvals.bytes() + hcount.bytes();
     b += gkind.bytes() + ghrem.bytes() + kind_del.bytes() + gw.bytes() + vtab.bytes();
     b += t_u.bytes() + t_v.bytes() + t_idx.bytes() + t_kstar.bytes() + t_count.bytes() + meta.bytes();
-    b += t_fin.bytes() + t_queue.bytes() + qctr.bytes() + cp.bytes();
+    b += t_fin.bytes() + t_queue.bytes() + qctr.bytes() + cp.bytes() + step_v.bytes() + step_e.bytes();
     b += t_wpq.bytes() + t_rmax.bytes() + recR.bytes() + t_kind.bytes() + best.bytes();
     b += ckeys.bytes() + ckeys_alt.bytes() + ck2.bytes() + cvals.bytes() + cvals_alt.bytes() + chist.bytes();
     b += cscan.bytes() + ccount.bytes() + cflag.bytes() + cpos.bytes() + cv2.bytes() + ccount2.bytes();
@@ -461,7 +461,17 @@ static void ensure_ws(Ctx& c, DGraph& g, uint32_t b_max, cudaStream_t st) {
     w.t_fin.ensure(a, B, st);
     w.t_queue.ensure(a, B, st);
     w.qctr.ensure(a, 2, st);
-    if (walk_ncp(T) > 0) w.cp.ensure(a, (size_t)B * s * walk_ncp(T), st);
+    // Step records of deletion walkers replace the resume points (no replay
+    // at finalization) while they fit in STEP_REC_BYTES: B * T * s words each.
+    constexpr uint64_t STEP_REC_BYTES = 4ull << 30;
+    if ((uint64_t)B * T * s * 8 <= STEP_REC_BYTES) {
+        w.step_v.ensure(a, (size_t)B * T * s, st);
+        w.step_e.ensure(a, (size_t)B * T * s, st);
+    } else {  // records of a smaller workspace must not be used at this size
+        w.step_v.release(a, st);
+        w.step_e.release(a, st);
+        if (walk_ncp(T) > 0) w.cp.ensure(a, (size_t)B * s * walk_ncp(T), st);
+    }
     w.t_count.ensure(a, 4, st);
     w.t_wpq.ensure(a, B, st);
     w.t_rmax.ensure(a, B, st);
@@ -785,7 +795,7 @@ void graph_release_ws(Ctx& c, DGraph& g, cudaStream_t st) {
     REL(vvals_alt); REL(vhist); REL(vscan); REL(wkind); REL(fin_w); REL(wflag); REL(wpos); REL(wflag2); REL(wpos2); REL(gkeys);
     REL(gkeys_alt); REL(hkeys); REL(gvals); REL(gvals_alt); REL(ghist); REL(gscan); REL(gcount); REL(hflag);
     REL(hpos); REL(hvals); REL(hcount); REL(gkind); REL(ghrem); REL(kind_del); REL(gw); REL(t_u); REL(t_v);
-    REL(t_idx); REL(t_kstar); REL(t_fin); REL(t_queue); REL(qctr); REL(cp); REL(t_count); REL(meta); REL(t_wpq); REL(t_rmax); REL(recR); REL(t_kind); REL(best);
+    REL(t_idx); REL(t_kstar); REL(t_fin); REL(t_queue); REL(qctr); REL(cp); REL(step_v); REL(step_e); REL(t_count); REL(meta); REL(t_wpq); REL(t_rmax); REL(recR); REL(t_kind); REL(best);
     REL(ckeys); REL(ckeys_alt); REL(ck2); REL(cvals); REL(cvals_alt); REL(chist); REL(cscan); REL(ccount);
     REL(cflag); REL(cpos); REL(cv2); REL(ccount2); REL(cw); REL(kind_ins); REL(path_buf); REL(path_w); REL(path_len); REL(fb_list); REL(fb_count); REL(dbg_reason);
     REL(dbg_steps); REL(dbg_paths);
@@ -851,7 +861,9 @@ static FinArgs fin_of(Ctx& c, BatchWS& w, bool on) {
     f.fin_w = w.fin_w.p;
     f.c = cands_of(w);
     f.pb = paths_of(w);
-    f.cp = on ? w.cp.p : nullptr;
+    f.pv = on ? w.step_v.p : nullptr;
+    f.pe = on ? w.step_e.p : nullptr;
+    f.cp = (on && !f.pv) ? w.cp.p : nullptr;
     f.cp_shift = walk_cp_shift((uint32_t)c.cfg.T);
     f.ncp = walk_ncp((uint32_t)c.cfg.T);
     f.on = on ? 1u : 0u;

@@ -54,6 +54,7 @@ struct BatchWS {
     DBuf<uint32_t> t_u, t_v, t_idx, t_kstar, t_count, meta;
     DBuf<uint32_t> t_fin, t_queue, qctr;  // finalization inside the walk: per-update counts, queue, cursors
     DBuf<uint4> cp;                       // deletion walkers' resume points (walk_ncp(T) per walker)
+    DBuf<uint32_t> step_v, step_e;        // deletion walkers' step records (when they fit the budget below)
     DBuf<double> t_wpq, recR;
     DBuf<uint64_t> t_rmax;
     DBuf<uint8_t> t_kind;

@@ -347,6 +347,40 @@ __device__ __forceinline__ void has_edges(const CSRView& g, const uint32_t* a, c
     for (int q = 0; q < N; ++q) found[q] = on[q] && lo[q] < d[q] && L[q][lo[q]].nbr == y[q];
 }
 
+// The path of walker b of walked deletion j from its step records (vertex
+// reached and entry taken at every step), one warp; the same vertices and
+// weights a replay would produce, without its chain of dependent loads.
+// Returns the success flag (all lanes).
+__device__ bool path_from_records(uint32_t j, int32_t b, int lane, const CSRView& G, const WalkTasks& t,
+                                  const WalkParams& p, const WalkRecs& r, const PathBufs& pb, const FinArgs& f,
+                                  uint32_t* d_err) {
+    const uint32_t u = t.u[j], v = t.v[j], n = (uint32_t)G.n;
+    const uint32_t steps = __ldcg(&r.meta[(size_t)j * p.s + b]) & 0xFFFFu;
+    bool ok = steps <= p.T;
+    uint32_t* path = pb.v + (size_t)j * (p.T + 1);
+    double* pw = pb.w + (size_t)j * p.T;
+    if (lane == 0) path[0] = u;
+    for (uint32_t q = lane; ok && q < steps; q += 32) {
+        const size_t rec = ((size_t)j * p.T + q) * p.s + (uint32_t)b;
+        const uint32_t x = __ldcg(&f.pv[rec]);
+        const uint32_t e = __ldcg(&f.pe[rec]);
+        if (x >= n || (uint64_t)e >= G.pool_cap) {
+            ok = false;
+            break;
+        }
+        path[q + 1] = x;
+        pw[q] = G.pool[e].w;
+        if (q + 1 == steps && x != v) ok = false;  // a recorded hit ends at v
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    if (lane == 0) {
+        if (!ok) atomicOr(d_err, (uint32_t)ERR_INTERNAL);
+        pb.len[j] = ok ? steps : 0u;
+    }
+    __syncwarp();
+    return ok;
+}
+
 // Recovered edges of the replayed path of walked deletion j, one warp: every
 // edge of the walk that did not appear earlier in it and is not in H'.  A
 // path shorter than EMIT_SMEM is staged in the warp's shared buffer sbuf
@@ -463,7 +497,9 @@ __device__ void finalize_update(uint32_t j, int lane, const WalkKernelArgs& a, U
     }
     if (bk >= 0) {
         bool ok = false;
-        if (a.f.cp) {
+        if (a.f.pv) {
+            ok = path_from_records(j, bk, lane, a.G, a.t, a.p, a.r, a.f.pb, a.f, a.d_err);
+        } else if (a.f.cp) {
             ok = replay_path_warp(j, bk, lane, a.G, a.t, a.p, a.r, a.hdr->id0, a.f.pb, a.f, a.d_err);
         } else {
             if (lane == 0) ok = replay_path(j, bk, a.G, a.t, a.p, a.r, a.hdr->id0, a.f.pb, a.d_err);
@@ -623,14 +659,15 @@ __device__ __forceinline__ void load_step(const Ent* pool, uint32_t i, uint4& h,
 // the previous vertex) or the chosen entry leads to a hub (HUBREF: the list
 // comes from the vertex arrays).  Moves the walker (r ends as the step's
 // resistance, added by the caller); false on a bad offset.
-__device__ __forceinline__ bool lean_hub_step(Lean& v, const WalkKernelArgs& a, uint4& h, double& r, uint32_t at) {
+__device__ __forceinline__ bool lean_hub_step(Lean& v, const WalkKernelArgs& a, uint4& h, double& r, uint32_t& at) {
     const CSRView& g = v.ins ? a.H : a.G;
     if (v.pid && h.x >= v.prev) {
         if ((uint64_t)at + 1 >= g.pool_cap) {
             atomicOr(a.d_err, (uint32_t)ERR_INTERNAL);
             return false;
         }
-        load_step(g.pool, at + 1, h, r);
+        ++at;
+        load_step(g.pool, at, h, r);
     }
     v.steps += 1;
     const uint32_t from = v.c;
@@ -783,10 +820,16 @@ __global__ void __launch_bounds__(256, (ILP == 1 ? 4 : (ILP == 2 ? 3 : 1))) k_wa
                 v.prev = h[i].w;
             }
             const double r_step = r[i];
+            const uint32_t took = at[i];  // pool index of the entry this step took
             // reaching v ends the walk whatever R is (hit, or over K for an insertion);
             // the next load goes out first, the rest of the step follows it
             const bool at_q = v.c == v.q;
             fly[i] = !at_q && v.steps < a.p.T && lean_issue<HUBS>(v, a, h[i], r[i], ks[i], at[i]);
+            if (a.f.pv && !v.ins) {
+                const size_t rec = ((size_t)v.j * a.p.T + v.steps - 1) * a.p.s + v.k;
+                a.f.pv[rec] = v.c;
+                a.f.pe[rec] = took;
+            }
             v.R = __dadd_rn(v.R, r_step);
             if (a.r.paths) a.r.paths[((size_t)v.j * a.p.s + v.k) * (a.p.T + 1) + v.steps] = (int32_t)v.c;
             if (a.f.cp && !v.ins && (v.steps & ((1u << a.f.cp_shift) - 1u)) == 0u) {

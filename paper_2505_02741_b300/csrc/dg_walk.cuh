@@ -116,6 +116,12 @@ struct FinArgs {
     // segments instead of one chain of dependent loads
     uint4* cp;
     uint32_t cp_shift, ncp;
+    // step records of deletion walkers (nullable; when present no resume
+    // points are kept): the vertex reached at each step and the pool index of
+    // the entry taken, at [(j * T + step) * s + walker] (the walkers of one
+    // update side by side, so a warp's records of one step are contiguous)
+    uint32_t* pv;
+    uint32_t* pe;
     uint32_t on;          // 0: records only (reduction and emission run as separate kernels)
 };
 

@@ -100,6 +100,23 @@ def test_degenerate_walk_parameters(s, T, K):
     ctx.close()
 
 
+def test_long_step_limit_resume_points():
+    """With a step limit this long the deletion walkers' step records would
+    not fit their memory budget, so the argmin path is replayed from resume
+    points (every 4096 steps here) instead: results, H and G equal the oracle."""
+    rng = np.random.default_rng(77)
+    n = 120
+    a, b, w = random_connected(n, 200, rng, 0.2, 5.0)
+    h = W.init_sparsifier(n, a, b, w, rng)
+    ctx, g, o = pair(n, a, b, w, h, s=32, T=20000, K=50.0)
+    for k in range(2):
+        ups = _mixed_updates(rng, n, *[np.array(x) for x in zip(*sorted(o_edges(o)))], 60)
+        cols = list(zip(*ups))
+        res, _ = step_both(g, o, list(cols[0]), list(cols[1]), list(cols[2]), list(cols[3]), where=f"long T b{k}")
+        assert (res["walked"] == 1).any()
+    ctx.close()
+
+
 def test_empty_and_all_invalid_batches():
     wl, st = W.make_grid(16, 16)
     ctx, g, o = pair(wl.n, wl.a, wl.b, wl.w, wl.h_ids)

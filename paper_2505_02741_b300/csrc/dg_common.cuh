@@ -51,6 +51,8 @@ struct CSRView {
     uint32_t* cap;
     uint8_t* hub;             // 1 = entries pointing here hold HUBREF
     uint32_t* nhub;           // number of hubs (device word)
+    uint32_t* twin;           // a hub's second region of cap entries (the next list execution
+                              // writes the list there and keeps this one), or 0xFFFFFFFF
     Ent* pool;
     unsigned long long* top;  // entries in use (bump pointer)
     uint64_t pool_cap;        // entries allocated

@@ -35,7 +35,7 @@ void ApplyScratch::ensure(DevAlloc& a, uint32_t changes, uint64_t stage_entries,
         uint32_t c = changes < 1024 ? 1024 : changes;
         DBuf<uint32_t>* bufs[] = {&f_head, &f_ins, &f_del, &p_head, &p_ins, &p_del, &tv, &tstart, &tend,
                                   &odeg, &ndeg, &ooff, &ncap, &rsz, &work, &r_off, &s_off, &w_off,
-                                  &fwork, &f_off};
+                                  &fwork, &f_off, &sdeg, &xm, &tdst};
         for (auto* b : bufs) b->ensure(a, (size_t)c + 1, st);
         scan_tmp.ensure(a, scan_tmp_words(c + 1), st);
         c_max = c;
@@ -51,7 +51,7 @@ void ApplyScratch::ensure(DevAlloc& a, uint32_t changes, uint64_t stage_entries,
 void ApplyScratch::release(DevAlloc& a, cudaStream_t st) {
     DBuf<uint32_t>* bufs[] = {&f_head, &f_ins, &f_del, &p_head, &p_ins, &p_del, &tv, &tstart, &tend,
                               &odeg, &ndeg, &ooff, &ncap, &rsz, &work, &r_off, &s_off, &w_off,
-                              &fwork, &f_off, &scan_tmp, &totals};
+                              &fwork, &f_off, &sdeg, &xm, &tdst, &scan_tmp, &totals};
     for (auto* b : bufs) b->release(a, st);
     stage.release(a, st);
     c_max = 0;
@@ -59,7 +59,7 @@ void ApplyScratch::release(DevAlloc& a, cudaStream_t st) {
 }
 
 uint64_t ApplyScratch::bytes() const {
-    return 20ull * (c_max + 1) * 4 + scan_tmp.bytes() + totals.bytes() + stage.bytes();
+    return 23ull * (c_max + 1) * 4 + scan_tmp.bytes() + totals.bytes() + stage.bytes();
 }
 
 void csr_alloc_vertices(CSR& g, DevAlloc& a, int32_t n, cudaStream_t st) {
@@ -71,6 +71,8 @@ void csr_alloc_vertices(CSR& g, DevAlloc& a, int32_t n, cudaStream_t st) {
     DG_CUDA(cudaMemsetAsync(g.hub.p, 0, g.hub.bytes(), st));
     g.nhub.ensure(a, 1, st);
     DG_CUDA(cudaMemsetAsync(g.nhub.p, 0, g.nhub.bytes(), st));
+    g.twin.ensure(a, (size_t)n + 1, st);
+    DG_CUDA(cudaMemsetAsync(g.twin.p, 0xFF, g.twin.bytes(), st));
     g.top.ensure(a, 1, st);
     DG_CUDA(cudaMemsetAsync(g.off.p, 0, g.off.bytes(), st));
     DG_CUDA(cudaMemsetAsync(g.deg.p, 0, g.deg.bytes(), st));
@@ -84,6 +86,7 @@ void csr_release(CSR& g, DevAlloc& a, cudaStream_t st) {
     g.cap.release(a, st);
     g.hub.release(a, st);
     g.nhub.release(a, st);
+    g.twin.release(a, st);
     g.pool.release(a, st);
     g.top.release(a, st);
     g.pool_cap = 0;
@@ -228,7 +231,18 @@ struct PlanArgs {
     float slack;
     const uint32_t *p_head, *p_ins, *p_del, *totals;
     uint32_t *tv, *tstart, *tend, *odeg, *ndeg, *ooff, *ncap, *rsz, *work, *fwork;
+    uint32_t *sdeg, *xm, *tdst;
 };
+
+// Placement of a touched list (xm bits 0-1) and of a hub's twin after the
+// execution (xm bits 2-3).  A list that stays where it is goes through the
+// staging buffer (its old entries are read while the new ones are written); a
+// list written elsewhere -- fresh pool space, or a hub's twin region -- is
+// written there directly by the merge.  A hub always moves: into its twin when
+// it has one and the list fits, and the region it leaves becomes the twin, so
+// rewriting a long hub list costs one pass over it instead of two.
+enum : uint32_t { XM_INPLACE = 0, XM_FRESH = 1, XM_TWIN = 2 };
+enum : uint32_t { TW_NONE = 0, TW_OLD = 1, TW_FRESH = 2 };  // new twin: none, the old region, fresh space after the list
 
 __device__ __forceinline__ uint32_t pre_at(const uint32_t* p, uint32_t c, uint32_t count, uint32_t total) {
     return c < count ? p[c] : total;
@@ -262,6 +276,25 @@ __global__ void k_plan_touch(PlanArgs a, const uint32_t* d_err) {
         const uint32_t nd = od + ins - del;
         const bool reloc = nd > oc;
         const uint32_t nc = reloc ? cap_for(nd, a.slack) : oc;
+        const bool hub_now = hub_next(was_hub, nd);
+        const uint32_t tw = a.g.twin[x];
+        uint32_t mode, ntw, rs = 0;
+        if (hub_now && !reloc && tw != 0xFFFFFFFFu) {
+            mode = XM_TWIN;          // into the twin; the old region becomes the twin
+            ntw = TW_OLD;
+        } else if (hub_now && !reloc) {
+            mode = XM_FRESH;         // first twin: fresh space of the same capacity
+            ntw = TW_OLD;
+            rs = oc;
+        } else if (hub_now) {
+            mode = XM_FRESH;         // grown hub: fresh list and fresh twin
+            ntw = TW_FRESH;
+            rs = 2 * nc;
+        } else {
+            mode = reloc ? XM_FRESH : XM_INPLACE;
+            ntw = TW_NONE;
+            rs = reloc ? nc : 0u;
+        }
         a.tv[t] = x;
         a.tstart[t] = c;
         a.tend[t] = e;
@@ -269,11 +302,14 @@ __global__ void k_plan_touch(PlanArgs a, const uint32_t* d_err) {
         a.ndeg[t] = nd;
         a.ooff[t] = oo;
         a.ncap[t] = nc;
-        a.rsz[t] = reloc ? nc : 0u;
+        a.rsz[t] = rs;
+        a.sdeg[t] = mode == XM_INPLACE ? nd : 0u;
+        a.xm[t] = mode | (ntw << 2);
+        a.tdst[t] = tw;
         a.work[t] = od + (e - c);
         // cache refresh work: every entry of the new list, or for a hub that
         // stays a hub only its changes (see k_exec_fix)
-        a.fwork[t] = (was_hub && hub_next(was_hub, nd)) ? e - c : nd;
+        a.fwork[t] = (was_hub && hub_now) ? e - c : nd;
     }
 }
 
@@ -311,11 +347,12 @@ void csr_plan(CSR& g, const ChangeList& cl, ApplyScratch& s, uint32_t* d_err, ui
     pa.p_head = s.p_head.p; pa.p_ins = s.p_ins.p; pa.p_del = s.p_del.p; pa.totals = tot;
     pa.tv = s.tv.p; pa.tstart = s.tstart.p; pa.tend = s.tend.p; pa.odeg = s.odeg.p; pa.ndeg = s.ndeg.p;
     pa.ooff = s.ooff.p; pa.ncap = s.ncap.p; pa.rsz = s.rsz.p; pa.work = s.work.p; pa.fwork = s.fwork.p;
+    pa.sdeg = s.sdeg.p; pa.xm = s.xm.p; pa.tdst = s.tdst.p;
     k_plan_touch<<<grid, FLAT_THREADS, 0, st>>>(pa, d_err);
     ++g_launches;
     ScanJob j2;
     j2.in[0] = s.rsz.p;  j2.out[0] = s.r_off.p; j2.total[0] = tot + TOT_R;
-    j2.in[1] = s.ndeg.p; j2.out[1] = s.s_off.p; j2.total[1] = tot + TOT_S;
+    j2.in[1] = s.sdeg.p; j2.out[1] = s.s_off.p; j2.total[1] = tot + TOT_S;
     j2.in[2] = s.work.p; j2.out[2] = s.w_off.p; j2.total[2] = tot + TOT_WK;
     j2.in[3] = s.fwork.p; j2.out[3] = s.f_off.p; j2.total[3] = tot + TOT_F;
     j2.k = 4;
@@ -335,6 +372,7 @@ struct ExecArgs {
     uint32_t n;
     const uint32_t *p_ins, *p_del, *totals;
     const uint32_t *tv, *tstart, *tend, *odeg, *ndeg, *ooff, *ncap, *rsz, *r_off, *s_off, *w_off, *f_off;
+    const uint32_t *sdeg, *xm, *tdst;
     Ent* stage;
     uint32_t* touched;  // n + 1 words, see csr_exec
 };
@@ -344,7 +382,8 @@ __device__ __forceinline__ uint64_t base_of(const uint32_t* totals) {
 }
 
 __device__ __forceinline__ uint32_t dst_off(const ExecArgs& a, uint32_t t) {
-    return a.rsz[t] ? (uint32_t)(base_of(a.totals) + a.r_off[t]) : a.ooff[t];
+    const uint32_t mode = a.xm[t] & 3u;
+    return mode == XM_FRESH ? (uint32_t)(base_of(a.totals) + a.r_off[t]) : mode == XM_TWIN ? a.tdst[t] : a.ooff[t];
 }
 
 __global__ void k_exec_meta(ExecArgs a, const uint32_t* d_err) {
@@ -357,6 +396,10 @@ __global__ void k_exec_meta(ExecArgs a, const uint32_t* d_err) {
         a.g.off[x] = dst_off(a, t);
         a.g.deg[x] = a.ndeg[t];
         a.g.cap[x] = a.ncap[t];
+        const uint32_t ntw = a.xm[t] >> 2;
+        a.g.twin[x] = ntw == TW_OLD ? a.ooff[t]
+                    : ntw == TW_FRESH ? (uint32_t)(base_of(a.totals) + a.r_off[t] + a.ncap[t])
+                                      : 0xFFFFFFFFu;
         // touched bit 0; bit 1 when x's hub status flips (its back-entries change form)
         const bool was = a.g.hub[x] != 0, now = hub_next(was, a.ndeg[t]);
         a.g.hub[x] = now ? 1 : 0;
@@ -495,7 +538,10 @@ __global__ void k_exec_merge(ExecArgs a, uint32_t* d_err) {
             atomicOr(d_err, (uint32_t)ERR_INTERNAL);
             return;
         }
-        a.stage[a.s_off[t] + outpos] = out;
+        // a list that stays in place goes through the staging buffer; one that
+        // moves is written at its destination (nothing reads that space now)
+        if (a.sdeg[t]) a.stage[a.s_off[t] + outpos] = out;
+        else a.g.pool[dst_off(a, t) + outpos] = out;
     });
 }
 
@@ -616,6 +662,9 @@ void csr_exec(CSR& g, const ChangeList& cl, ApplyScratch& s, uint32_t* touched, 
     a.ooff = s.ooff.p; a.ncap = s.ncap.p; a.rsz = s.rsz.p; a.r_off = s.r_off.p; a.s_off = s.s_off.p;
     a.w_off = s.w_off.p;
     a.f_off = s.f_off.p;
+    a.sdeg = s.sdeg.p;
+    a.xm = s.xm.p;
+    a.tdst = s.tdst.p;
     a.stage = s.stage.p;
     a.touched = touched;
     // merge reads the old lists; meta then points every touched vertex at its
@@ -684,6 +733,7 @@ void csr_compact(CSR& g, DevAlloc& a, uint64_t min_free, cudaStream_t st) {
     unsigned long long t = h_total;
     DG_CUDA(cudaMemcpyAsync(g.top.p, &t, sizeof(t), cudaMemcpyHostToDevice, st));
     g.host_top = h_total;
+    DG_CUDA(cudaMemsetAsync(g.twin.p, 0xFF, g.twin.bytes(), st));  // the old pool's regions are gone
     DG_CUDA(cudaStreamSynchronize(st));
 }
 

@@ -25,6 +25,7 @@ struct CSR {
     DBuf<uint32_t> off, deg, cap;
     DBuf<uint8_t> hub;
     DBuf<uint32_t> nhub;
+    DBuf<uint32_t> twin;
     DBuf<Ent> pool;
     DBuf<unsigned long long> top;
     uint64_t host_top = 0;  // last value read back
@@ -36,6 +37,7 @@ struct CSR {
         v.cap = cap.p;
         v.hub = hub.p;
         v.nhub = nhub.p;
+        v.twin = twin.p;
         v.pool = pool.p;
         v.top = top.p;
         v.pool_cap = pool_cap;
@@ -43,7 +45,8 @@ struct CSR {
         return v;
     }
     uint64_t bytes() const {
-        return off.bytes() + deg.bytes() + cap.bytes() + hub.bytes() + nhub.bytes() + pool.bytes() + top.bytes();
+        return off.bytes() + deg.bytes() + cap.bytes() + hub.bytes() + nhub.bytes() + twin.bytes() + pool.bytes() +
+               top.bytes();
     }
 };
 
@@ -65,6 +68,7 @@ struct ApplyScratch {
     uint64_t s_cap = 0;  // entries of staging space
     DBuf<uint32_t> f_head, f_ins, f_del, p_head, p_ins, p_del;
     DBuf<uint32_t> tv, tstart, tend, odeg, ndeg, ooff, ncap, rsz, work, r_off, s_off, w_off, fwork, f_off;
+    DBuf<uint32_t> sdeg, xm, tdst;  // staged size, placement mode, twin destination (see k_plan_touch)
     DBuf<uint32_t> scan_tmp, totals;
     DBuf<Ent> stage;
     void ensure(DevAlloc& a, uint32_t changes, uint64_t stage_entries, cudaStream_t st);

@@ -114,6 +114,19 @@ __global__ void k_caps(const uint32_t* __restrict__ deg, uint32_t n, float slack
         cap[x] = cap_for(deg[x], slack);
 }
 
+// Every list gets a twin region of its capacity right after it: off holds the
+// prefix sums of the capacities on entry and the list offsets on return.  A
+// list execution writes a touched list into its twin and keeps the region it
+// leaves as the next twin, so no list is rewritten in place.
+__global__ void k_twin_layout(uint32_t* __restrict__ off, const uint32_t* __restrict__ cap, uint32_t n,
+                              uint32_t* __restrict__ twin) {
+    for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
+        const uint32_t o = 2u * off[x];
+        off[x] = o;
+        twin[x] = o + cap[x];
+    }
+}
+
 __global__ void k_build_fill(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
                              const double* __restrict__ ws, uint32_t count, uint32_t n,
                              const uint32_t* __restrict__ off, Ent* __restrict__ pool) {
@@ -187,12 +200,15 @@ void csr_build(CSR& g, DevAlloc& a, const uint64_t* keys, const uint32_t* vals, 
     job.total[0] = total.p;
     job.k = 1;
     scan_exclusive(job, nullptr, n, tmp.p, st);
-    uint32_t h_total = 0;
-    DG_CUDA(cudaMemcpyAsync(&h_total, total.p, 4, cudaMemcpyDeviceToHost, st));
+    k_twin_layout<<<grid, FLAT_THREADS, 0, st>>>(g.off.p, g.cap.p, n, g.twin.p);
+    ++g_launches;
+    uint32_t h_caps = 0;
+    DG_CUDA(cudaMemcpyAsync(&h_caps, total.p, 4, cudaMemcpyDeviceToHost, st));
     DG_CUDA(cudaStreamSynchronize(st));
     tmp.release(a, st);
     total.release(a, st);
-    const uint64_t want = (uint64_t)h_total + (uint64_t)((double)h_total * g.overflow) + 4096;
+    const uint64_t h_total = 2ull * h_caps;  // lists and their twins
+    const uint64_t want = h_total + (uint64_t)((double)h_total * g.overflow) + 4096;
     if (want >= 0xFFFFFFF0ull) throw Error(DG_E_NOMEM, "graph too large for 32-bit pool offsets");
     g.pool.release(a, st);
     g.pool.ensure(a, want, st);
@@ -279,21 +295,20 @@ __global__ void k_plan_touch(PlanArgs a, const uint32_t* d_err) {
         const bool hub_now = hub_next(was_hub, nd);
         const uint32_t tw = a.g.twin[x];
         uint32_t mode, ntw, rs = 0;
-        if (hub_now && !reloc && tw != 0xFFFFFFFFu) {
-            mode = XM_TWIN;          // into the twin; the old region becomes the twin
+        if (!reloc && tw != 0xFFFFFFFFu) {
+            mode = XM_TWIN;          // into the twin; the region it leaves becomes the twin
             ntw = TW_OLD;
-        } else if (hub_now && !reloc) {
-            mode = XM_FRESH;         // first twin: fresh space of the same capacity
-            ntw = TW_OLD;
-            rs = oc;
-        } else if (hub_now) {
-            mode = XM_FRESH;         // grown hub: fresh list and fresh twin
+        } else if (reloc) {
+            mode = XM_FRESH;         // grown list: fresh list and fresh twin
             ntw = TW_FRESH;
             rs = 2 * nc;
+        } else if (hub_now) {
+            mode = XM_FRESH;         // no twin yet: fresh space, the old region becomes the twin
+            ntw = TW_OLD;
+            rs = oc;
         } else {
-            mode = reloc ? XM_FRESH : XM_INPLACE;
+            mode = XM_INPLACE;       // no twin (not laid out by a build or compaction)
             ntw = TW_NONE;
-            rs = reloc ? nc : 0u;
         }
         a.tv[t] = x;
         a.tstart[t] = c;
@@ -708,16 +723,19 @@ void csr_compact(CSR& g, DevAlloc& a, uint64_t min_free, cudaStream_t st) {
     job.total[0] = total.p;
     job.k = 1;
     scan_exclusive(job, nullptr, n, tmp.p, st);
-    uint32_t h_total = 0;
-    DG_CUDA(cudaMemcpyAsync(&h_total, total.p, 4, cudaMemcpyDeviceToHost, st));
+    k_twin_layout<<<grid, FLAT_THREADS, 0, st>>>(noff.p, ncap.p, n, g.twin.p);
+    ++g_launches;
+    uint32_t h_caps = 0;
+    DG_CUDA(cudaMemcpyAsync(&h_caps, total.p, 4, cudaMemcpyDeviceToHost, st));
     DG_CUDA(cudaStreamSynchronize(st));
-    uint64_t want = (uint64_t)h_total + (uint64_t)((double)h_total * g.overflow) + 4096;
-    if (want < (uint64_t)h_total + min_free) want = (uint64_t)h_total + min_free;
+    const uint64_t h_total = 2ull * h_caps;  // lists and their twins
+    uint64_t want = h_total + (uint64_t)((double)h_total * g.overflow) + 4096;
+    if (want < h_total + min_free) want = h_total + min_free;
     if (want >= 0xFFFFFFF0ull) throw Error(DG_E_NOMEM, "graph too large for 32-bit pool offsets");
     DBuf<Ent> np;
     np.ensure(a, want, st);
     if (h_total > 0) {
-        k_compact_copy<<<grid, FLAT_THREADS, 0, st>>>(g.view(), noff.p, h_total, np.p);
+        k_compact_copy<<<grid, FLAT_THREADS, 0, st>>>(g.view(), noff.p, (uint32_t)h_total, np.p);
         ++g_launches;
     }
     DG_CHECK_LAUNCH();
@@ -733,7 +751,6 @@ void csr_compact(CSR& g, DevAlloc& a, uint64_t min_free, cudaStream_t st) {
     unsigned long long t = h_total;
     DG_CUDA(cudaMemcpyAsync(g.top.p, &t, sizeof(t), cudaMemcpyHostToDevice, st));
     g.host_top = h_total;
-    DG_CUDA(cudaMemsetAsync(g.twin.p, 0xFF, g.twin.bytes(), st));  // the old pool's regions are gone
     DG_CUDA(cudaStreamSynchronize(st));
 }
 

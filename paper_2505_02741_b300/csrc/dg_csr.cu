@@ -682,8 +682,10 @@ void csr_exec(CSR& g, const ChangeList& cl, ApplyScratch& s, uint32_t* touched, 
     a.tdst = s.tdst.p;
     a.stage = s.stage.p;
     a.touched = touched;
-    // merge reads the old lists; meta then points every touched vertex at its
-    // final slots; place copies the staged lists there; fix refreshes caches.
+    // merge reads the old lists and writes the new ones (into twins or fresh
+    // space; lists without a twin into the staging buffer); meta then points
+    // every touched vertex at its final slots; place copies staged lists back;
+    // fix refreshes caches.
     k_exec_merge<<<grid, FLAT_THREADS, 0, st>>>(a, d_err);
     k_exec_meta<<<grid, FLAT_THREADS, 0, st>>>(a, d_err);
     k_exec_place<<<grid, FLAT_THREADS, 0, st>>>(a, d_err);

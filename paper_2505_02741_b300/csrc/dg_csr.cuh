@@ -1,15 +1,17 @@
-// dg_csr.cuh -- slack-slot CSR on the device: build, batched in-place mutation
-// (plan / execute), compaction and export.
+// dg_csr.cuh -- slack-slot CSR on the device: build, batched mutation (plan /
+// execute), compaction and export.
 //
 // Mutation follows the dynamic CSR idea of Section III-F (lists that outgrow
-// their slots move into spare pool space; deletions stay in place), made
-// parallel and deterministic: a batch's half-edge changes arrive sorted by
-// (vertex, neighbour); every touched vertex's new list is the sorted merge of
-// its old list and its changes, computed with one thread per output position
-// (load-balanced over all touched vertices, so hubs cost no more than their
-// degree), then placed in its slots or in freshly bumped pool space, after
-// which the cached (off, deg, rev) fields of the entries that point at moved
-// or resized lists are refreshed.
+// their slots move into spare pool space), made parallel and deterministic: a
+// batch's half-edge changes arrive sorted by (vertex, neighbour); every
+// touched vertex's new list is the sorted merge of its old list and its
+// changes, computed with one thread per output position (load-balanced over
+// all touched vertices, so hubs cost no more than their degree).  Each list
+// has a twin region of its capacity: the merge writes the new list into the
+// twin (or into fresh pool space when it outgrew its capacity), and the region
+// it leaves becomes the twin; then the cached (off, deg, rev) fields of the
+// entries that point at moved or resized lists are refreshed.  A list without
+// a twin is merged through a staging buffer and copied back in place.
 #pragma once
 #include "dg_common.cuh"
 #include "dg_host.h"

@@ -629,7 +629,7 @@ void graph_load(Ctx& c, DGraph& g, int32_t n, int64_t m, const int32_t* u, const
     g.has_h = true;  // empty sparsifier
     g.next_id = 0;
     for (int i = 0; i < 7; ++i) DG_CUDA(cudaEventCreate(&g.ev[i]));
-    for (int i = 0; i < 5; ++i) DG_CUDA(cudaEventCreateWithFlags(&g.fk[i], cudaEventDisableTiming));
+    for (int i = 0; i < 7; ++i) DG_CUDA(cudaEventCreateWithFlags(&g.fk[i], cudaEventDisableTiming));
     DG_CUDA(cudaStreamCreateWithFlags(&g.side, cudaStreamNonBlocking));
     wait_stream(c, st);
 }
@@ -769,7 +769,7 @@ void graph_release(Ctx& c, DGraph& g) {
     g.hs = HostStage{};
     for (int i = 0; i < 7; ++i)
         if (g.ev[i]) cudaEventDestroy(g.ev[i]);
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 7; ++i)
         if (g.fk[i]) cudaEventDestroy(g.fk[i]);
     if (g.side) {
         cudaStreamSynchronize(g.side);
@@ -1017,7 +1017,7 @@ static bool enqueue_walks(Ctx& c, DGraph& g, cudaStream_t st, int64_t per_update
             launch_walk_batched(g.H.view(), g.G.view(), tasks, wp, wr, w.hdr.p, w.next.p,
                                 (uint32_t)((uint64_t)w.b_max * c2 / cut),
                                 (uint32_t)((uint64_t)w.b_max * (c2 + 1) / cut), g.shape, fin_of(c, w, fused),
-                                w.err.p, st);
+                                w.err.p, st, g.side, g.fk[5], g.fk[6]);
     } else {
         for (int64_t j = 0; j < per_update_W; ++j)
             launch_walk_one(g.H.view(), g.G.view(), tasks, wp, wr, w.hdr.p, (uint32_t)j, w.err.p, st);

@@ -109,7 +109,7 @@ struct DGraph {
     cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     // second stream of the mutation (H side, walk tasks) and its fork/join events
     cudaStream_t side = nullptr;
-    cudaEvent_t fk[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t fk[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // fork / join of the two streams
     dg_batch_stats stats{};
     std::mutex mu;
     uint64_t bytes() const { return G.bytes() + H.bytes() + touched.bytes() + touched_h.bytes() + ws.bytes(); }

@@ -993,24 +993,39 @@ static void launch_ilp(const WalkKernelArgs& a, const WalkShape& shape, cudaStre
     DG_CUDA(cudaLaunchKernelEx(&cfg, k_walk_batched<ILP, HUBS>, a));
 }
 
+// Both variants are launched; the one that does not match the graphs' hub
+// counts returns at once.  With a side stream the hub variant runs there,
+// beside the hub-free one, so the variant that exits costs the critical path
+// nothing.
 template <int ILP>
-static void launch_both(const WalkKernelArgs& a, const WalkShape& shape, cudaStream_t st) {
-    launch_ilp<ILP, false>(a, shape, st);
-    launch_ilp<ILP, true>(a, shape, st);
+static void launch_both(const WalkKernelArgs& a, const WalkShape& shape, cudaStream_t st, cudaStream_t side,
+                        cudaEvent_t fork, cudaEvent_t join) {
+    if (side) {
+        DG_CUDA(cudaEventRecord(fork, st));
+        DG_CUDA(cudaStreamWaitEvent(side, fork, 0));
+        launch_ilp<ILP, true>(a, shape, side);
+        DG_CUDA(cudaEventRecord(join, side));
+        launch_ilp<ILP, false>(a, shape, st);
+        DG_CUDA(cudaStreamWaitEvent(st, join, 0));
+    } else {
+        launch_ilp<ILP, false>(a, shape, st);
+        launch_ilp<ILP, true>(a, shape, st);
+    }
 }
 
 void launch_walk_batched(const CSRView& H, const CSRView& G, const WalkTasks& t, const WalkParams& p,
                          const WalkRecs& r, const BatchHdr* d_hdr, unsigned long long* d_next,
                          uint32_t j_lo, uint32_t j_hi, const WalkShape& shape, const FinArgs& f,
-                         const uint32_t* d_err, cudaStream_t st) {
+                         const uint32_t* d_err, cudaStream_t st, cudaStream_t side, cudaEvent_t fork,
+                         cudaEvent_t join) {
     WalkKernelArgs a = make_args(H, G, t, p, r, d_hdr, d_next, j_lo, j_hi, d_err);
     a.f = f;
     a.refill_min = (uint32_t)std::min(32, std::max(1, shape.refill));
     DG_CUDA(cudaMemsetAsync(d_next, 0, sizeof(unsigned long long), st));
     switch (shape.ilp) {
-        case 1: launch_both<1>(a, shape, st); break;
-        case 4: launch_both<4>(a, shape, st); break;
-        default: launch_both<2>(a, shape, st); break;
+        case 1: launch_both<1>(a, shape, st, side, fork, join); break;
+        case 4: launch_both<4>(a, shape, st, side, fork, join); break;
+        default: launch_both<2>(a, shape, st, side, fork, join); break;
     }
     g_launches += 2;
     DG_CHECK_LAUNCH();

@@ -138,7 +138,8 @@ inline uint32_t walk_ncp(uint32_t T) { return T == 0 ? 0 : (T - 1) >> walk_cp_sh
 void launch_walk_batched(const CSRView& H, const CSRView& G, const WalkTasks& t, const WalkParams& p,
                          const WalkRecs& r, const BatchHdr* d_hdr, unsigned long long* d_next,
                          uint32_t j_lo, uint32_t j_hi, const WalkShape& shape, const FinArgs& f,
-                         const uint32_t* d_err, cudaStream_t st);
+                         const uint32_t* d_err, cudaStream_t st, cudaStream_t side = nullptr,
+                         cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr);
 
 // the fallback edges of deletions the finalizing walk left to the block-wide kernel
 void launch_fallback(const CSRView& H, const CSRView& G, const WalkTasks& t, dg_update_result* res,

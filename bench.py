@@ -41,8 +41,8 @@ BYTES_PER_STEP = 32  # one 32-byte DRAM sector per walk step (the entry holds nb
 N_INS, N_DEL = 10_000, 10_000
 # DRAM bytes (read + write) of one walk launch of this workload, from one ncu
 # capture of the current walk kernel (cold L2); see profiles/.
-WALK_TRAFFIC_BYTES = 2.402e8
-WALK_TRAFFIC_SOURCE = "profiles/walk_k_walk_batched_mesh3d_100.md (ncu --set full, cold L2, 256x1 shape, refill 16)"
+WALK_TRAFFIC_BYTES = 2.735e8
+WALK_TRAFFIC_SOURCE = "profiles/walk_k_walk_batched_mesh3d_100.md (ncu --set full, cold L2, 256x1 shape, refill 16, step records)"
 
 
 def measured_peaks():

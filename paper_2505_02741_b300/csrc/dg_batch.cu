@@ -381,6 +381,8 @@ uint64_t BatchWS::bytes() const {
     b += cscan.bytes() + ccount.bytes() + cflag.bytes() + cpos.bytes() + cv2.bytes() + ccount2.bytes();
     b += cw.bytes() + kind_ins.bytes() + path_buf.bytes() + path_len.bytes() + path_w.bytes() + fb_list.bytes() +
          fb_count.bytes();
+    b += fb_slot.bytes() + fb_big.bytes() + fb_cbase.bytes() + fb_dslot.bytes() + fb_py.bytes() + fb_pr.bytes() +
+         fb_pw.bytes();
     b += dbg_reason.bytes() + dbg_steps.bytes() + dbg_paths.bytes();
     b += apG.bytes() + apH.bytes() + apC.bytes();
     return b;
@@ -485,7 +487,17 @@ static void ensure_ws(Ctx& c, DGraph& g, uint32_t b_max, cudaStream_t st) {
     w.path_w.ensure(a, (size_t)B * T, st);
     w.path_len.ensure(a, B, st);
     w.fb_list.ensure(a, B, st);
-    w.fb_count.ensure(a, 1, st);
+    w.fb_count.ensure(a, 4, st);
+    w.fb_big.ensure(a, (size_t)B * 2, st);
+    w.fb_cbase.ensure(a, (size_t)B * 2, st);
+    w.fb_dslot.ensure(a, (size_t)B * 2, st);
+    w.fb_pr.ensure(a, FB_CHUNK_CAP, st);
+    w.fb_pw.ensure(a, FB_CHUNK_CAP, st);
+    w.fb_py.ensure(a, FB_CHUNK_CAP, st);
+    if (!w.fb_slot.p || w.fb_slot.n < (size_t)g.n) {  // all unclaimed
+        w.fb_slot.ensure(a, (size_t)g.n, st);
+        DG_CUDA(cudaMemsetAsync(w.fb_slot.p, 0xFF, w.fb_slot.bytes(), st));
+    }
     if (c.cfg.record) {
         w.dbg_reason.ensure(a, (size_t)B * s, st);
         w.dbg_steps.ensure(a, (size_t)B * s, st);
@@ -797,7 +809,7 @@ void graph_release_ws(Ctx& c, DGraph& g, cudaStream_t st) {
     REL(hpos); REL(hvals); REL(hcount); REL(gkind); REL(ghrem); REL(kind_del); REL(gw); REL(t_u); REL(t_v);
     REL(t_idx); REL(t_kstar); REL(t_fin); REL(t_queue); REL(qctr); REL(cp); REL(step_v); REL(step_e); REL(t_count); REL(meta); REL(t_wpq); REL(t_rmax); REL(recR); REL(t_kind); REL(best);
     REL(ckeys); REL(ckeys_alt); REL(ck2); REL(cvals); REL(cvals_alt); REL(chist); REL(cscan); REL(ccount);
-    REL(cflag); REL(cpos); REL(cv2); REL(ccount2); REL(cw); REL(kind_ins); REL(path_buf); REL(path_w); REL(path_len); REL(fb_list); REL(fb_count); REL(dbg_reason);
+    REL(cflag); REL(cpos); REL(cv2); REL(ccount2); REL(cw); REL(kind_ins); REL(path_buf); REL(path_w); REL(path_len); REL(fb_list); REL(fb_count); REL(fb_slot); REL(fb_big); REL(fb_cbase); REL(fb_dslot); REL(fb_py); REL(fb_pr); REL(fb_pw); REL(dbg_reason);
     REL(dbg_steps); REL(dbg_paths);
 #undef REL
     w.b_max = 0;
@@ -845,7 +857,8 @@ static Cands cands_of(BatchWS& w) {
 }
 
 static PathBufs paths_of(BatchWS& w) {
-    return PathBufs{w.path_buf.p, w.path_w.p, w.path_len.p, w.fb_list.p, w.fb_count.p};
+    return PathBufs{w.path_buf.p, w.path_w.p, w.path_len.p, w.fb_list.p, w.fb_count.p, w.fb_slot.p,
+                    w.fb_big.p,   w.fb_cbase.p, w.fb_dslot.p,  w.fb_pr.p,   w.fb_pw.p,    w.fb_py.p};
 }
 
 static FinArgs fin_of(Ctx& c, BatchWS& w, bool on) {
@@ -1009,7 +1022,7 @@ static bool enqueue_walks(Ctx& c, DGraph& g, cudaStream_t st, int64_t per_update
     const bool fused = per_update_W < 0 && cut == 1;
     if (fused) {
         DG_CUDA(cudaMemsetAsync(w.ccount.p, 0, 4, st));
-        DG_CUDA(cudaMemsetAsync(w.fb_count.p, 0, 4, st));
+        DG_CUDA(cudaMemsetAsync(w.fb_count.p, 0, 16, st));
     }
     DG_CUDA(record_event(g.ev[0], st));
     if (per_update_W < 0) {

@@ -428,6 +428,30 @@ __device__ uint32_t emit_path_warp(uint32_t j, int lane, const CSRView& H, const
     return cnt;  // the shuffles above keep the buffer's readers ahead of its next writer
 }
 
+__device__ __forceinline__ unsigned long long* fb_nb(const PathBufs& pb) {
+    return reinterpret_cast<unsigned long long*>(pb.fb_count + 2);
+}
+
+// Queue walked deletion j for k_fallback (one thread).  Each endpoint with more
+// than FB_WARP_MAX neighbours is claimed once per batch for the split scan:
+// it gets a slot and ceil(deg / FB_CHUNK) chunks from one 64-bit atomic, so
+// that the chunk ranges ascend with the slot.
+__device__ __forceinline__ void fb_queue(const PathBufs& pb, const CSRView& G, const WalkTasks& t, uint32_t j) {
+    pb.fb_list[atomicAdd(pb.fb_count, 1u)] = j;
+    for (int e2 = 0; e2 < 2; ++e2) {
+        const uint32_t x = e2 ? t.v[j] : t.u[j];
+        const uint32_t d = G.deg[x];
+        if (d <= FB_WARP_MAX) continue;
+        if (atomicCAS(&pb.fb_slot[x], NONE, NONE - 1u) != NONE) continue;  // claimed by another deletion
+        const uint32_t P = (d + FB_CHUNK - 1) / FB_CHUNK;
+        const unsigned long long old = atomicAdd(fb_nb(pb), (1ull << 32) | (unsigned long long)P);
+        const uint32_t sl = (uint32_t)(old >> 32);
+        pb.fb_big[sl] = x;
+        pb.fb_cbase[sl] = (uint32_t)old;
+        pb.fb_slot[x] = sl;
+    }
+}
+
 // Fallback of walked deletion j (no walker reached v), one warp: for each
 // endpoint x the G_b edge of minimum resistance not in H' (ties: smaller
 // neighbour id; reading R11).  false when an endpoint list is longer than
@@ -523,7 +547,7 @@ __device__ void finalize_update(uint32_t j, int lane, const WalkKernelArgs& a, U
                 tot.rec += e;
             }
         } else if (lane == 0) {
-            a.f.pb.fb_list[atomicAdd(a.f.pb.fb_count, 1u)] = j;
+            fb_queue(a.f.pb, a.G, a.t, j);
         }
     }
 }
@@ -1102,80 +1126,232 @@ __global__ void k_replay(CSRView H, CSRView G, WalkTasks t, WalkParams p, WalkRe
         } else {
             // no walker reached v: the fallback edges are chosen by k_fallback
             res[i].fallback = 1;
-            pb.fb_list[atomicAdd(pb.fb_count, 1u)] = j;
+            fb_queue(pb, G, t, j);
         }
+    }
+}
+
+// (r, neighbour) lexicographic minimum over the block; the result is valid in
+// thread 0.  br/by/bw: this thread's candidate (INFINITY / NONE when none).
+__device__ __forceinline__ void fb_block_min(double& br, uint32_t& by, double& bw, double* s_r, uint32_t* s_y,
+                                             double* s_w) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        const double orr = __shfl_xor_sync(0xffffffffu, br, o);
+        const uint32_t oy = __shfl_xor_sync(0xffffffffu, by, o);
+        const double ow = __shfl_xor_sync(0xffffffffu, bw, o);
+        if (orr < br || (orr == br && oy < by)) {
+            br = orr;
+            by = oy;
+            bw = ow;
+        }
+    }
+    if (lane == 0) {
+        s_r[warp] = br;
+        s_y[warp] = by;
+        s_w[warp] = bw;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q)
+            if (s_r[q] < br || (s_r[q] == br && s_y[q] < by)) {
+                br = s_r[q];
+                by = s_y[q];
+                bw = s_w[q];
+            }
+    }
+}
+
+// This thread's candidate over entries [k0, k1) of x's G_b list, taken
+// k0 + threadIdx.x, + blockDim.x, ... (ascending, so strict < keeps the
+// smaller neighbour id): minimum resistance among the edges not in H'.
+__device__ __forceinline__ void fb_scan_range(const CSRView& H, const Ent* L, uint32_t x, uint32_t k0, uint32_t k1,
+                                              double& br, uint32_t& by, double& bw) {
+    // eight resistances per round are loaded together, then taken in order
+    constexpr uint32_t U = 8;
+    for (uint32_t b0 = k0 + threadIdx.x; b0 < k1; b0 += U * blockDim.x) {
+        double rr[U];
+#pragma unroll
+        for (uint32_t q = 0; q < U; ++q) {
+            const uint32_t k = b0 + q * blockDim.x;
+            rr[q] = k < k1 ? L[k].r : INFINITY;
+        }
+#pragma unroll
+        for (uint32_t q = 0; q < U; ++q) {
+            const uint32_t k = b0 + q * blockDim.x;
+            if (!(rr[q] < br)) continue;
+            const uint32_t y = L[k].nbr;
+            if (has_edge(H, x, y)) continue;
+            br = rr[q];
+            by = y;
+            bw = L[k].w;
+        }
+    }
+}
+
+// First index i in [0, d) of a neighbour-sorted list with L[i].nbr >= key (d
+// when none), one warp: 32 probes per round shrink the range 33-fold.
+__device__ __forceinline__ uint32_t warp_lower_bound(const Ent* L, uint32_t d, uint32_t key, int lane) {
+    uint32_t lo = 0, hi = d;  // entries before lo are < key, entries from hi on are >= key
+    while (hi - lo > 32u) {
+        const uint64_t span = hi - lo;
+        const uint32_t p = lo + (uint32_t)(span * (uint32_t)(lane + 1) / 33u);
+        const uint32_t m = __ballot_sync(0xffffffffu, L[p].nbr >= key);
+        const int f = m ? __ffs(m) - 1 : 32;  // first probe at or above key
+        const uint32_t nlo = f > 0 ? lo + (uint32_t)(span * (uint32_t)f / 33u) + 1u : lo;
+        const uint32_t nhi = f < 32 ? lo + (uint32_t)(span * (uint32_t)(f + 1) / 33u) : hi;
+        lo = nlo;
+        hi = nhi;
+    }
+    const uint32_t p = lo + (uint32_t)lane;
+    const uint32_t m = __ballot_sync(0xffffffffu, p < hi ? L[p].nbr >= key : true);
+    return m ? lo + (uint32_t)(__ffs(m) - 1) : hi;
+}
+
+constexpr uint32_t FB_HS = 2048;  // H' entries staged in shared memory per scanned range
+
+// fb_scan_range with the H' lookups served from shared memory: x's H' entries
+// whose neighbour lies in the range's id span (both lists ascend by
+// neighbour) are found by two warp searches and staged in s_h; when more
+// than FB_HS of them fall in the span the lookups go to the H' lists.
+// Block-wide (every thread calls it with the same arguments).
+__device__ void fb_scan_staged(const CSRView& H, const CSRView& G, uint32_t x, uint32_t k0, uint32_t k1,
+                               uint32_t* s_h, uint32_t* s_rng, double& br, uint32_t& by, double& bw) {
+    if (k1 <= k0) return;
+    const Ent* L = G.pool + G.off[x];
+    const Ent* HL = H.pool + H.off[x];
+    const uint32_t hd = H.deg[x];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < 2) {
+        const uint32_t key = warp == 0 ? L[k0].nbr : L[k1 - 1].nbr + 1u;
+        const uint32_t p = warp_lower_bound(HL, hd, key, lane);
+        if (lane == 0) s_rng[warp] = p;
+    }
+    __syncthreads();
+    const uint32_t h0 = s_rng[0], hs = s_rng[1] - s_rng[0];
+    if (hs > FB_HS) {
+        __syncthreads();
+        fb_scan_range(H, L, x, k0, k1, br, by, bw);
+        return;
+    }
+    for (uint32_t i = threadIdx.x; i < hs; i += blockDim.x) s_h[i] = HL[h0 + i].nbr;
+    __syncthreads();
+    constexpr uint32_t U = 8;
+    for (uint32_t b0 = k0 + threadIdx.x; b0 < k1; b0 += U * blockDim.x) {
+        double rr[U];
+#pragma unroll
+        for (uint32_t q = 0; q < U; ++q) {
+            const uint32_t k = b0 + q * blockDim.x;
+            rr[q] = k < k1 ? L[k].r : INFINITY;
+        }
+#pragma unroll
+        for (uint32_t q = 0; q < U; ++q) {
+            const uint32_t k = b0 + q * blockDim.x;
+            if (!(rr[q] < br)) continue;
+            const uint32_t y = L[k].nbr;
+            const uint32_t p = lower_bound_arr(s_h, 0u, hs, y);
+            if (p < hs && s_h[p] == y) continue;  // (x, y) is in H'
+            br = rr[q];
+            by = y;
+            bw = L[k].w;
+        }
+    }
+    __syncthreads();  // s_h and s_rng are reused by the next range
+}
+
+// Split scan of the long endpoint lists claimed by fb_queue: every fallback
+// deletion's endpoint slots are looked up (the claims are complete), then one
+// block per chunk finds the chunk's minimum.
+__global__ void __launch_bounds__(256) k_fb_chunks(CSRView H, CSRView G, WalkTasks t, PathBufs pb, uint32_t w_max,
+                                                   uint32_t* d_err) {
+    if (walk_aborted(d_err)) return;
+    __shared__ double s_r[8];
+    __shared__ uint32_t s_y[8];
+    __shared__ double s_w[8];
+    __shared__ uint32_t s_h[FB_HS];
+    __shared__ uint32_t s_rng[2];
+    const uint32_t F = min(*pb.fb_count, w_max);
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < 2 * F; q += gridDim.x * blockDim.x) {
+        const uint32_t j = pb.fb_list[q >> 1];
+        const uint32_t x = (q & 1u) ? t.v[j] : t.u[j];
+        pb.fb_dslot[q] = G.deg[x] > FB_WARP_MAX ? pb.fb_slot[x] : NONE;
+    }
+    const unsigned long long nb = *fb_nb(pb);
+    const uint32_t S = (uint32_t)(nb >> 32), total = min((uint32_t)nb, FB_CHUNK_CAP);
+    for (uint32_t ch = blockIdx.x; ch < total; ch += gridDim.x) {
+        // the chunk's slot: the last one whose first chunk is <= ch (slot 0 starts at 0)
+        uint32_t lo = 0, hi = S;
+        while (hi - lo > 1u) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (pb.fb_cbase[mid] <= ch) lo = mid;
+            else hi = mid;
+        }
+        const uint32_t cb = pb.fb_cbase[lo], x = pb.fb_big[lo];
+        const uint32_t d = G.deg[x];
+        if (cb + (d + FB_CHUNK - 1) / FB_CHUNK > FB_CHUNK_CAP) continue;  // scanned whole by k_fallback
+        const uint32_t k0 = (ch - cb) * FB_CHUNK, k1 = min(k0 + FB_CHUNK, d);
+        double br = INFINITY, bw = 0.0;
+        uint32_t by = NONE;
+        fb_scan_staged(H, G, x, k0, k1, s_h, s_rng, br, by, bw);
+        fb_block_min(br, by, bw, s_r, s_y, s_w);
+        if (threadIdx.x == 0) {
+            pb.fb_pr[ch] = br;
+            pb.fb_py[ch] = by;
+            pb.fb_pw[ch] = bw;
+        }
+        __syncthreads();
     }
 }
 
 // Fallback of a walked deletion whose walkers all missed: for each endpoint x,
 // the G_b edge of minimum resistance not in H' (ties: smaller neighbour id).
-// One block per deletion scans each endpoint's list cooperatively (hub lists
-// hold 10^5 entries), then reduces (r, neighbour) lexicographically.
+// One block per deletion: an endpoint with a slot takes the minimum over its
+// chunks' results, any other endpoint list is scanned by the block.  The
+// claims of the split scan are cleared here (nothing below reads them).
 __global__ void __launch_bounds__(256) k_fallback(CSRView H, CSRView G, WalkTasks t, dg_update_result* res,
                                                   BatchCounters* ctr, Cands c, PathBufs pb, uint32_t w_max,
                                                   uint32_t* d_err) {
+    {
+        const uint32_t S = (uint32_t)(*fb_nb(pb) >> 32);
+        for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < S; q += gridDim.x * blockDim.x)
+            pb.fb_slot[pb.fb_big[q]] = NONE;
+    }
     if (walk_aborted(d_err)) return;
     __shared__ double s_r[8];
     __shared__ uint32_t s_y[8];
     __shared__ double s_w[8];
     __shared__ uint32_t pick_y[2];
     __shared__ double pick_w[2];
+    __shared__ uint32_t s_h[FB_HS];
+    __shared__ uint32_t s_rng[2];
     const uint32_t F = min(*pb.fb_count, w_max);
     const uint32_t n = (uint32_t)G.n;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (uint32_t f = blockIdx.x; f < F; f += gridDim.x) {
         const uint32_t j = pb.fb_list[f];
         const uint32_t ends[2] = {t.u[j], t.v[j]};
         for (int e2 = 0; e2 < 2; ++e2) {
             const uint32_t x = ends[e2];
-            const Ent* L = G.pool + G.off[x];
             const uint32_t d = G.deg[x];
+            const uint32_t sl = pb.fb_dslot[2 * f + e2];
+            const uint32_t cb = sl != NONE ? pb.fb_cbase[sl] : 0u;
+            const uint32_t P = (d + FB_CHUNK - 1) / FB_CHUNK;
             double br = INFINITY, bw = 0.0;
             uint32_t by = NONE;
-            // eight resistances per round are loaded together, then taken in
-            // order (this thread's ids ascend: strict < keeps the smaller id)
-            constexpr uint32_t U = 8;
-            for (uint32_t k0 = threadIdx.x; k0 < d; k0 += U * blockDim.x) {
-                double rr[U];
-#pragma unroll
-                for (uint32_t q = 0; q < U; ++q) {
-                    const uint32_t k = k0 + q * blockDim.x;
-                    rr[q] = k < d ? L[k].r : INFINITY;
-                }
-#pragma unroll
-                for (uint32_t q = 0; q < U; ++q) {
-                    const uint32_t k = k0 + q * blockDim.x;
-                    if (!(rr[q] < br)) continue;
-                    const uint32_t y = L[k].nbr;
-                    if (has_edge(H, x, y)) continue;
-                    br = rr[q];
-                    by = y;
-                    bw = L[k].w;
-                }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                const double orr = __shfl_xor_sync(0xffffffffu, br, o);
-                const uint32_t oy = __shfl_xor_sync(0xffffffffu, by, o);
-                const double ow = __shfl_xor_sync(0xffffffffu, bw, o);
-                if (orr < br || (orr == br && oy < by)) {
-                    br = orr;
-                    by = oy;
-                    bw = ow;
-                }
-            }
-            if (lane == 0) {
-                s_r[warp] = br;
-                s_y[warp] = by;
-                s_w[warp] = bw;
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                for (int q = 1; q < (int)(blockDim.x >> 5); ++q)
-                    if (s_r[q] < br || (s_r[q] == br && s_y[q] < by)) {
-                        br = s_r[q];
-                        by = s_y[q];
-                        bw = s_w[q];
+            if (sl != NONE && cb + P <= FB_CHUNK_CAP) {
+                for (uint32_t q = threadIdx.x; q < P; q += blockDim.x) {
+                    const double rr = pb.fb_pr[cb + q];
+                    const uint32_t yy = pb.fb_py[cb + q];
+                    if (rr < br || (rr == br && yy < by)) {
+                        br = rr;
+                        by = yy;
+                        bw = pb.fb_pw[cb + q];
                     }
+                }
+            } else {
+                fb_scan_staged(H, G, x, 0u, d, s_h, s_rng, br, by, bw);
+            }
+            fb_block_min(br, by, bw, s_r, s_y, s_w);
+            if (threadIdx.x == 0) {
                 pick_y[e2] = by;
                 pick_w[e2] = bw;
             }
@@ -1232,18 +1408,20 @@ void launch_emit(const CSRView& H, const CSRView& G, const WalkTasks& t, const W
     const uint32_t cap = (uint32_t)device_sms() * 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    DG_CUDA(cudaMemsetAsync(pb.fb_count, 0, 4, st));
+    DG_CUDA(cudaMemsetAsync(pb.fb_count, 0, 16, st));
     k_replay<<<blocks, 128, 0, st>>>(H, G, t, p, r, d_hdr, best, fin_w, res, ctr, c, pb, w_max, d_err);
     k_emit_path<<<(unsigned)device_sms() * 8, 256, 0, st>>>(H, t, p, res, ctr, c, pb, w_max, d_err);
-    k_fallback<<<(unsigned)device_sms() * 4, 256, 0, st>>>(H, G, t, res, ctr, c, pb, w_max, d_err);
-    g_launches += 3;
+    g_launches += 2;
     DG_CHECK_LAUNCH();
+    launch_fallback(H, G, t, res, ctr, c, pb, w_max, d_err, st);
 }
 
 void launch_fallback(const CSRView& H, const CSRView& G, const WalkTasks& t, dg_update_result* res,
                      BatchCounters* ctr, Cands c, PathBufs pb, uint32_t w_max, uint32_t* d_err, cudaStream_t st) {
-    k_fallback<<<(unsigned)device_sms() * 4, 256, 0, st>>>(H, G, t, res, ctr, c, pb, w_max, d_err);
-    ++g_launches;
+    const unsigned sms = (unsigned)device_sms();
+    k_fb_chunks<<<sms * 4, 256, 0, st>>>(H, G, t, pb, w_max, d_err);
+    k_fallback<<<sms * 4, 256, 0, st>>>(H, G, t, res, ctr, c, pb, w_max, d_err);
+    g_launches += 2;
     DG_CHECK_LAUNCH();
 }
 

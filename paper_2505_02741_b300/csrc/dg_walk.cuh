@@ -88,8 +88,21 @@ struct PathBufs {
     double* w;
     uint32_t* len;
     uint32_t* fb_list;   // walked deletions without a hit (fallback), appended
-    uint32_t* fb_count;
+    uint32_t* fb_count;  // [0] fallback count; [2..3] u64 (slots << 32 | chunks) of the split scan
+    // Split scan of long endpoint lists (claimed when a deletion is queued for
+    // the fallback; k_fb_chunks, k_fallback): every distinct endpoint with more
+    // than FB_WARP_MAX neighbours gets a slot and ceil(deg / FB_CHUNK) chunks,
+    // scanned by one block each.
+    uint32_t* fb_slot;   // per vertex: its slot, 0xFFFFFFFF when unclaimed (cleared again by k_fallback)
+    uint32_t* fb_big;    // per slot: the vertex
+    uint32_t* fb_cbase;  // per slot: its first chunk (ascends with the slot)
+    uint32_t* fb_dslot;  // per fallback deletion and endpoint: the slot, or 0xFFFFFFFF
+    double* fb_pr;       // per chunk: minimum resistance found, its weight and neighbour
+    double* fb_pw;
+    uint32_t* fb_py;
 };
+constexpr uint32_t FB_CHUNK = 2048;          // list entries per chunk of the split scan
+constexpr uint32_t FB_CHUNK_CAP = 1u << 16;  // chunks kept per batch; slots beyond are scanned whole
 
 // Per-update finalization done by the batched walk itself: the walker that
 // finishes last for an update queues it, and warps left without walkers take

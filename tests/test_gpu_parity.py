@@ -230,6 +230,62 @@ def test_ring_recovery_and_fallback():
         ctx.close()
 
 
+def _hub_graph(rng, n, hub_deg, h_frac):
+    """A ring over vertices 3..n-1, hubs 0, 1, 2 joined to each other and to
+    hub_deg[h] random ring vertices; H(0) = the ring, the hub triangle and a
+    fraction h_frac of every hub's other edges."""
+    edges = {}
+    for i in range(3, n):
+        j = 3 + (i - 3 + 1) % (n - 3)
+        edges[(min(i, j), max(i, j))] = True
+    for h, d in enumerate(hub_deg):
+        for y in rng.choice(np.arange(3, n), d, replace=False):
+            edges[(h, int(y))] = rng.random() < h_frac
+    for e in ((0, 1), (0, 2), (1, 2)):
+        edges[e] = True
+    keys = sorted(edges)
+    a = np.array([k[0] for k in keys], np.int32)
+    b = np.array([k[1] for k in keys], np.int32)
+    in_h = np.array([edges[k] for k in keys])
+    return a, b, in_h
+
+
+@pytest.mark.parametrize("walk_mode", ["batched", "per_update"])
+def test_long_list_fallback_split_scan(walk_mode):
+    """Fallback (no walker reached v; minimum-resistance G_b edge not in H' at
+    each endpoint) at endpoints with 1.5k to 7k neighbours: the CUDA path
+    splits such lists into chunks of 2048 entries scanned by separate blocks
+    and claims each endpoint once per batch.  Many deletions share a hub, one
+    joins two hubs; a few hub edges outside H share the top weight, in
+    different chunks, so the smaller neighbour id breaks the tie across
+    chunks.  Two batches: the second picks the next minima after the first
+    batch's recovered edges joined H, and must not see the first batch's
+    claims.  A step limit of 2 makes most deletions fall back."""
+    rng = np.random.default_rng(77)
+    n = 9000
+    a, b, in_h = _hub_graph(rng, n, (7000, 4500, 1500), 0.3)
+    w = rng.uniform(0.1, 10.0, a.size)
+    for h in range(3):  # tied top weights outside H, spread over the list
+        idx = np.nonzero((a == h) & (b >= 3) & ~in_h)[0]
+        w[rng.choice(idx, 4, replace=False)] = 20.0
+    ctx, g, o = pair(n, a, b, w, np.nonzero(in_h)[0], seed=5, K=100.0, T=2, s=4,
+                     ctx_kw=dict(walk_mode=walk_mode, cuda_graphs=walk_mode == "batched"))
+    hub_h = np.nonzero(in_h & (a <= 2) & (b >= 3))[0]
+    picks = rng.permutation(hub_h)
+    plans = [picks[:260], picks[260:480]]
+    for bi, ids in enumerate(plans):
+        u, v = a[ids].copy(), b[ids].copy()
+        flip = rng.random(ids.size) < 0.5  # either endpoint first
+        u[flip], v[flip] = v[flip], u[flip]
+        u = np.append(u, [0, 1][bi])
+        v = np.append(v, [1, 2][bi])  # a deletion between two hubs
+        res, _ = step_both(g, o, u, v, np.zeros(u.size), np.ones(u.size, np.int32),
+                           where=f"{walk_mode} batch {bi}")
+        assert res["fallback"].sum() > 0.5 * u.size
+        assert res["nrecovered"].sum() > 0
+    ctx.close()
+
+
 @pytest.mark.parametrize("seed", [0, 1, 2])
 def test_random_graphs_many_batches(seed):
     rng = np.random.default_rng(100 + seed)

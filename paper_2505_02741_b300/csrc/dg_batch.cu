@@ -523,6 +523,10 @@ static void ensure_ws(Ctx& c, DGraph& g, uint32_t b_max, cudaStream_t st) {
         DG_CUDA(cudaMallocHost(&g.hs.ctr, sizeof(BatchCounters)));
         DG_CUDA(cudaMallocHost(&g.hs.tops, sizeof(unsigned long long) * 2));
         DG_CUDA(cudaMallocHost(&g.hs.counts, sizeof(uint32_t) * 4));
+        DG_CUDA(cudaHostGetDevicePointer((void**)&g.hs.d_err, g.hs.err, 0));
+        DG_CUDA(cudaHostGetDevicePointer((void**)&g.hs.d_ctr, g.hs.ctr, 0));
+        DG_CUDA(cudaHostGetDevicePointer((void**)&g.hs.d_tops, g.hs.tops, 0));
+        DG_CUDA(cudaHostGetDevicePointer((void**)&g.hs.d_counts, g.hs.counts, 0));
     }
     ++g.layout_gen;
 }
@@ -1165,14 +1169,30 @@ static void enqueue_commit(Ctx& c, DGraph& g, cudaStream_t st, bool walk_emitted
     csr_exec(g.H, clC, w.apC, g.touched.p, w.err.p, st);
 }
 
+// the batch's status for the host (error words, counters, pool tops, walked
+// and candidate counts), written by one kernel straight into pinned host
+// memory: one node at the end of the captured step instead of six copies
+__global__ void k_readback(const uint32_t* err, const BatchCounters* ctr, const unsigned long long* gtop,
+                           const unsigned long long* htop, const uint32_t* t_count, const uint32_t* ccount,
+                           uint32_t* h_err, BatchCounters* h_ctr, unsigned long long* h_tops, uint32_t* h_counts) {
+    constexpr unsigned CW = sizeof(BatchCounters) / sizeof(unsigned long long);
+    static_assert(CW * sizeof(unsigned long long) == sizeof(BatchCounters) && CW <= 8, "counter words");
+    const unsigned t = threadIdx.x;
+    if (t < 4) h_err[t] = err[t];
+    if (t >= 8 && t < 8 + CW)
+        reinterpret_cast<unsigned long long*>(h_ctr)[t - 8] = reinterpret_cast<const unsigned long long*>(ctr)[t - 8];
+    if (t == 16) h_tops[0] = *gtop;
+    if (t == 17) h_tops[1] = *htop;
+    if (t == 18) h_counts[0] = *t_count;
+    if (t == 19) h_counts[1] = *ccount;
+}
+
 static void enqueue_readback(DGraph& g, cudaStream_t st) {
     BatchWS& w = g.ws;
-    DG_CUDA(cudaMemcpyAsync(g.hs.err, w.err.p, 16, cudaMemcpyDeviceToHost, st));
-    DG_CUDA(cudaMemcpyAsync(g.hs.ctr, w.ctr.p, sizeof(BatchCounters), cudaMemcpyDeviceToHost, st));
-    DG_CUDA(cudaMemcpyAsync(g.hs.tops, g.G.top.p, 8, cudaMemcpyDeviceToHost, st));
-    DG_CUDA(cudaMemcpyAsync(g.hs.tops + 1, g.H.top.p, 8, cudaMemcpyDeviceToHost, st));
-    DG_CUDA(cudaMemcpyAsync(g.hs.counts, w.t_count.p, 4, cudaMemcpyDeviceToHost, st));
-    DG_CUDA(cudaMemcpyAsync(g.hs.counts + 1, w.ccount.p, 4, cudaMemcpyDeviceToHost, st));
+    k_readback<<<1, 32, 0, st>>>(w.err.p, w.ctr.p, g.G.top.p, g.H.top.p, w.t_count.p, w.ccount.p, g.hs.d_err,
+                                 g.hs.d_ctr, g.hs.d_tops, g.hs.d_counts);
+    ++g_launches;
+    DG_CHECK_LAUNCH();
 }
 
 static uint32_t read_total(ApplyScratch& s, int which, cudaStream_t st) {

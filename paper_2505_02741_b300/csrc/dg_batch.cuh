@@ -82,6 +82,11 @@ struct HostStage {  // pinned staging for host-API batches
     BatchCounters* ctr = nullptr;
     unsigned long long* tops = nullptr;  // [G top, H top]
     uint32_t* counts = nullptr;          // [W, ccount]
+    // device addresses of err, ctr, tops, counts (pinned, written by k_readback)
+    uint32_t* d_err = nullptr;
+    BatchCounters* d_ctr = nullptr;
+    unsigned long long* d_tops = nullptr;
+    uint32_t* d_counts = nullptr;
     size_t cap = 0;
 };
 

@@ -895,20 +895,41 @@ static WalkRecs recs_of(Ctx& c, BatchWS& w) {
     return r;
 }
 
+// per-batch state cleared in one launch: error words (4), counters, change
+// count, k* bounds (all ones), the edge-key table (all ones) and the
+// repeated-edge flag behind it (2 words)
+__global__ void k_batch_reset(uint32_t* err, BatchCounters* ctr, uint32_t* gcount, uint32_t* kstar, uint32_t B,
+                              unsigned long long* vtab, uint32_t vtab_slots) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const uint32_t n = B > vtab_slots ? B : vtab_slots;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        if (i < B) kstar[i] = 0xFFFFFFFFu;
+        if (i < vtab_slots) vtab[i] = ~0ull;
+    }
+    if (blockIdx.x == 0) {
+        const uint32_t t = threadIdx.x;
+        if (t < 4) err[t] = 0u;
+        if (t < sizeof(BatchCounters) / sizeof(unsigned long long))
+            reinterpret_cast<unsigned long long*>(ctr)[t] = 0ull;
+        if (t == 32) *gcount = 0u;
+        if (t == 33) vtab[vtab_slots] = 0ull;  // the repeated-edge flag words
+    }
+}
+
 // validation and both mutations (G -> G_b, H -> H'); nothing is written to G
 // or H unless both plans found enough space
 static void enqueue_mutate(Ctx& c, DGraph& g, cudaStream_t st) {
     BatchWS& w = g.ws;
     const uint32_t B = w.b_max, B2 = 2 * w.b_max, n = (uint32_t)g.n;
-    DG_CUDA(cudaMemsetAsync(w.err.p, 0, 16, st));
-    DG_CUDA(cudaMemsetAsync(w.ctr.p, 0, sizeof(BatchCounters), st));
-    DG_CUDA(cudaMemsetAsync(w.gcount.p, 0, 4, st));
-    DG_CUDA(cudaMemsetAsync(w.t_kstar.p, 0xFF, 4ull * B, st));
+    {
+        const uint64_t items = std::max<uint64_t>(B, w.vtab_slots);
+        int blocks = grid_for(items);
+        if (blocks < 1) blocks = 1;
+        k_batch_reset<<<blocks, BT, 0, st>>>(w.err.p, w.ctr.p, w.gcount.p, w.t_kstar.p, B, w.vtab.p, w.vtab_slots);
+        ++g_launches;
+    }
     const uint32_t* d_nu = &w.hdr.p->nu;
-    // edge-key table (all ones) and the repeated-edge flag behind it, one memset
-    DG_CUDA(cudaMemsetAsync(w.vtab.p, 0xFF, (size_t)w.vtab_slots * 8, st));
     uint32_t* d_dup = reinterpret_cast<uint32_t*>(w.vtab.p + w.vtab_slots);
-    DG_CUDA(cudaMemsetAsync(d_dup, 0, 8, st));
     k_val_prep<<<grid_for(B), BT, 0, st>>>(w.ups.p, w.hdr.p, n, B, w.res.p, w.vkeys.p, w.vvals.p, w.wkind.p,
                                           w.fin_w.p, w.wflag.p, w.wflag2.p, w.vtab.p, w.vtab_slots - 1u, d_dup);
     ++g_launches;

@@ -895,16 +895,37 @@ static WalkRecs recs_of(Ctx& c, BatchWS& w) {
     return r;
 }
 
+// scratch regions a batch step needs zero on entry (look-back scan status,
+// sort histograms, counters)
+struct ClearList {
+    static constexpr int MAX = 16;
+    uint32_t* p[MAX];
+    uint32_t words[MAX];
+    int n = 0;
+    void add(uint32_t* ptr, size_t w, size_t cap) {
+        if (n >= MAX || w > cap || w > 0xFFFFFFFFull) throw Error(DG_E_CUDA, "batch scratch layout");
+        p[n] = ptr;
+        words[n] = (uint32_t)w;
+        ++n;
+    }
+};
+
 // per-batch state cleared in one launch: error words (4), counters, change
 // count, k* bounds (all ones), the edge-key table (all ones) and the
-// repeated-edge flag behind it (2 words)
+// repeated-edge flag behind it (2 words), and the regions of the clear list
 __global__ void k_batch_reset(uint32_t* err, BatchCounters* ctr, uint32_t* gcount, uint32_t* kstar, uint32_t B,
-                              unsigned long long* vtab, uint32_t vtab_slots) {
+                              unsigned long long* vtab, uint32_t vtab_slots, ClearList cl) {
     const uint32_t stride = gridDim.x * blockDim.x;
+    const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t n = B > vtab_slots ? B : vtab_slots;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    for (uint32_t i = gt; i < n; i += stride) {
         if (i < B) kstar[i] = 0xFFFFFFFFu;
         if (i < vtab_slots) vtab[i] = ~0ull;
+    }
+    for (int e = 0; e < cl.n; ++e) {
+        uint32_t* p = cl.p[e];
+        const uint32_t w = cl.words[e];
+        for (uint32_t i = gt; i < w; i += stride) p[i] = 0u;
     }
     if (blockIdx.x == 0) {
         const uint32_t t = threadIdx.x;
@@ -920,12 +941,28 @@ __global__ void k_batch_reset(uint32_t* err, BatchCounters* ctr, uint32_t* gcoun
 // or H unless both plans found enough space
 static void enqueue_mutate(Ctx& c, DGraph& g, cudaStream_t st) {
     BatchWS& w = g.ws;
-    const uint32_t B = w.b_max, B2 = 2 * w.b_max, n = (uint32_t)g.n;
+    const uint32_t B = w.b_max, B2 = 2 * w.b_max, n = (uint32_t)g.n, CC = w.cand_cap;
+    const int bits_v = bit_length((uint64_t)n * n), bits_g = bit_length((uint64_t)n * n - 1);
     {
+        // scratch of this step's scans and sorts (validation, G changes, both
+        // plans, commit) and the walk's candidate and fallback counts
+        ClearList cl;
+        cl.add(w.vhist.p, sort_clear_words(B, bits_v), w.vhist.n);
+        cl.add(w.vscan.p, scan_tmp_words(B), w.vscan.n);
+        cl.add(w.ghist.p, sort_clear_words(B2, bits_g), w.ghist.n);
+        cl.add(w.gscan.p, scan_tmp_words(B2), w.gscan.n);
+        cl.add(w.apG.scan_tmp.p, 2 * w.apG.scan_words, w.apG.scan_tmp.n);
+        cl.add(w.apH.scan_tmp.p, 2 * w.apH.scan_words, w.apH.scan_tmp.n);
+        cl.add(w.chist.p, sort_clear_words(CC, bits_g), w.chist.n);
+        cl.add(w.cscan.p, scan_tmp_words(CC), w.cscan.n);
+        cl.add(w.apC.scan_tmp.p, 2 * w.apC.scan_words, w.apC.scan_tmp.n);
+        cl.add(w.ccount.p, 1, w.ccount.n);
+        cl.add(w.fb_count.p, 4, w.fb_count.n);
         const uint64_t items = std::max<uint64_t>(B, w.vtab_slots);
         int blocks = grid_for(items);
         if (blocks < 1) blocks = 1;
-        k_batch_reset<<<blocks, BT, 0, st>>>(w.err.p, w.ctr.p, w.gcount.p, w.t_kstar.p, B, w.vtab.p, w.vtab_slots);
+        k_batch_reset<<<blocks, BT, 0, st>>>(w.err.p, w.ctr.p, w.gcount.p, w.t_kstar.p, B, w.vtab.p, w.vtab_slots,
+                                            cl);
         ++g_launches;
     }
     const uint32_t* d_nu = &w.hdr.p->nu;
@@ -935,7 +972,7 @@ static void enqueue_mutate(Ctx& c, DGraph& g, cudaStream_t st) {
     ++g_launches;
     // sorted by edge key only when some edge appears twice (the kernels return at once otherwise)
     SortBufs vs{w.vkeys.p, w.vvals.p, w.vkeys_alt.p, w.vvals_alt.p, w.vhist.p, w.vscan.p, w.err.p};
-    const bool valt = radix_sort_pairs(vs, d_nu, B, bit_length((uint64_t)n * n), st, d_dup);
+    const bool valt = radix_sort_pairs(vs, d_nu, B, bits_v, st, d_dup, true);
     RunArgs ra;
     ra.keys = valt ? w.vkeys_alt.p : w.vkeys.p;
     ra.vals = valt ? w.vvals_alt.p : w.vvals.p;
@@ -980,7 +1017,7 @@ static void enqueue_mutate(Ctx& c, DGraph& g, cudaStream_t st) {
         j.total[1] = w.t_count.p + 3;
         j.k = 2;
         j.err = w.err.p;
-        scan_exclusive(j, d_nu, B, w.vscan.p, sd);
+        scan_exclusive(j, d_nu, B, w.vscan.p, sd, true);
     }
     WalkTasks tasks = tasks_of(w);
     k_make_tasks<<<grid_for(B), BT, 0, sd>>>(w.ups.p, w.wkind.p, w.wpos.p, w.wpos2.p, w.t_count.p + 2, w.hdr.p, B,
@@ -988,7 +1025,7 @@ static void enqueue_mutate(Ctx& c, DGraph& g, cudaStream_t st) {
     ++g_launches;
     // net G changes, sorted by (vertex, neighbour)
     SortBufs gs{w.gkeys.p, w.gvals.p, w.gkeys_alt.p, w.gvals_alt.p, w.ghist.p, w.gscan.p, w.err.p};
-    const bool galt = radix_sort_pairs(gs, w.gcount.p, B2, bit_length((uint64_t)n * n - 1), st);
+    const bool galt = radix_sort_pairs(gs, w.gcount.p, B2, bits_g, st, nullptr, true);
     const uint64_t* gk = galt ? w.gkeys_alt.p : w.gkeys.p;
     const uint32_t* gv = galt ? w.gvals_alt.p : w.gvals.p;
     DG_CUDA(cudaEventRecord(g.fk[1], st));
@@ -1002,7 +1039,7 @@ static void enqueue_mutate(Ctx& c, DGraph& g, cudaStream_t st) {
         j.total[0] = w.hcount.p;
         j.k = 1;
         j.err = w.err.p;
-        scan_exclusive(j, w.gcount.p, B2, w.gscan.p, sd);
+        scan_exclusive(j, w.gcount.p, B2, w.gscan.p, sd, true);
     }
     k_compact_kv<<<grid_for(B2), BT, 0, sd>>>(gk, gv, w.hflag.p, w.hpos.p, w.gcount.p, B2, w.hkeys.p, w.hvals.p);
     ++g_launches;
@@ -1020,9 +1057,9 @@ static void enqueue_mutate(Ctx& c, DGraph& g, cudaStream_t st) {
     clH.ws = w.gw.p;
     clH.d_count = w.hcount.p;
     clH.max_count = B2;
-    csr_plan(g.H, clH, w.apH, w.err.p, ERR_POOL_G, ERR_CAP_PRE, sd);
+    csr_plan(g.H, clH, w.apH, w.err.p, ERR_POOL_G, ERR_CAP_PRE, sd, true);
     DG_CUDA(cudaEventRecord(g.fk[2], sd));
-    csr_plan(g.G, clG, w.apG, w.err.p, ERR_POOL_G, ERR_CAP_PRE, st);
+    csr_plan(g.G, clG, w.apG, w.err.p, ERR_POOL_G, ERR_CAP_PRE, st, true);
     DG_CUDA(cudaEventRecord(g.fk[3], st));
     DG_CUDA(cudaStreamWaitEvent(st, g.fk[2], 0));
     DG_CUDA(cudaStreamWaitEvent(sd, g.fk[3], 0));
@@ -1045,10 +1082,8 @@ static bool enqueue_walks(Ctx& c, DGraph& g, cudaStream_t st, int64_t per_update
     const WalkTasks tasks = tasks_of(w);
     const uint32_t cut = g.shape.cut > 1 ? (uint32_t)g.shape.cut : 1u;
     const bool fused = per_update_W < 0 && cut == 1;
-    if (fused) {
-        DG_CUDA(cudaMemsetAsync(w.ccount.p, 0, 4, st));
-        DG_CUDA(cudaMemsetAsync(w.fb_count.p, 0, 16, st));
-    }
+    // (the candidate and fallback counts start at zero: cleared with the step's
+    // scratch, and again after the autotuner's trial walks)
     DG_CUDA(record_event(g.ev[0], st));
     if (per_update_W < 0) {
         for (uint32_t c2 = 0; c2 < cut; ++c2)
@@ -1141,6 +1176,8 @@ static void autotune_walks(Ctx& c, DGraph& g, cudaStream_t st) {
     cudaEventDestroy(e1);
     c.alloc.put(flush, flush_bytes, st);
     DG_CUDA(cudaMemsetAsync(w.t_kstar.p, 0xFF, 4ull * w.b_max, st));
+    DG_CUDA(cudaMemsetAsync(w.ccount.p, 0, 4, st));
+    DG_CUDA(cudaMemsetAsync(w.fb_count.p, 0, 16, st));
     g.shape = best;
     g.tuned = true;
     g.stats.autotuned = 1;
@@ -1150,7 +1187,9 @@ static void autotune_walks(Ctx& c, DGraph& g, cudaStream_t st) {
 // kept insertions, recovered and fallback edges -> H (re-runnable).  After a
 // finalizing walk (walk_emitted) the candidates are already there except the
 // fallbacks at long lists; otherwise they are generated here from the results.
-static void enqueue_commit(Ctx& c, DGraph& g, cudaStream_t st, bool walk_emitted) {
+// scratch_zeroed: the commit's sort, scan and plan scratch were cleared at the
+// step start and not used since (false when only the commit re-runs)
+static void enqueue_commit(Ctx& c, DGraph& g, cudaStream_t st, bool walk_emitted, bool scratch_zeroed) {
     BatchWS& w = g.ws;
     const uint32_t B = w.b_max, n = (uint32_t)g.n, CC = w.cand_cap;
     const Cands cd = cands_of(w);
@@ -1163,7 +1202,8 @@ static void enqueue_commit(Ctx& c, DGraph& g, cudaStream_t st, bool walk_emitted
     }
     DG_CUDA(record_event(g.ev[6], st));
     SortBufs cs{w.ckeys.p, w.cvals.p, w.ckeys_alt.p, w.cvals_alt.p, w.chist.p, w.cscan.p, w.err.p};
-    const bool calt = radix_sort_pairs(cs, w.ccount.p, CC, bit_length((uint64_t)n * n - 1), st);
+    const bool calt = radix_sort_pairs(cs, w.ccount.p, CC, bit_length((uint64_t)n * n - 1), st, nullptr,
+                                       scratch_zeroed);
     const uint64_t* ck = calt ? w.ckeys_alt.p : w.ckeys.p;
     const uint32_t* cv = calt ? w.cvals_alt.p : w.cvals.p;
     k_commit_flags<<<grid_for(CC), BT, 0, st>>>(ck, w.ccount.p, CC, g.H.view(), w.cflag.p, w.err.p);
@@ -1175,7 +1215,7 @@ static void enqueue_commit(Ctx& c, DGraph& g, cudaStream_t st, bool walk_emitted
         j.total[0] = w.ccount2.p;
         j.k = 1;
         j.err = w.err.p;
-        scan_exclusive(j, w.ccount.p, CC, w.cscan.p, st);
+        scan_exclusive(j, w.ccount.p, CC, w.cscan.p, st, scratch_zeroed);
     }
     k_compact_kv<<<grid_for(CC), BT, 0, st>>>(ck, cv, w.cflag.p, w.cpos.p, w.ccount.p, CC, w.ck2.p, w.cv2.p);
     ++g_launches;
@@ -1186,7 +1226,7 @@ static void enqueue_commit(Ctx& c, DGraph& g, cudaStream_t st, bool walk_emitted
     clC.ws = w.cw.p;
     clC.d_count = w.ccount2.p;
     clC.max_count = CC;
-    csr_plan(g.H, clC, w.apC, w.err.p, ERR_POOL_H, ERR_CAP_COMMIT, st);
+    csr_plan(g.H, clC, w.apC, w.err.p, ERR_POOL_H, ERR_CAP_COMMIT, st, scratch_zeroed);
     csr_exec(g.H, clC, w.apC, g.touched.p, w.err.p, st);
 }
 
@@ -1320,8 +1360,8 @@ void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_updat
         }
         walk_emitted = enqueue_walks(c, g, st, W);
     };
-    auto finish_eager = [&]() {
-        enqueue_commit(c, g, st, walk_emitted);
+    auto finish_eager = [&](bool scratch_zeroed) {
+        enqueue_commit(c, g, st, walk_emitted, scratch_zeroed);
         copy_results();
         enqueue_readback(g, st);
         DG_CUDA(record_event(g.ev[3], st));
@@ -1338,7 +1378,7 @@ void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_updat
         enqueue_mutate(c, g, st);
         autotune_walks(c, g, st);
         walk_emitted = enqueue_walks(c, g, st, -1);
-        finish_eager();
+        finish_eager(true);
     } else if (use_graph) {
         if (direct) DG_CUDA(cudaMemcpyAsync(w.ups.p, ups, sizeof(dg_update) * nu, kin, st));
         CapturedStep& cs = g.steps[bucket];
@@ -1354,7 +1394,7 @@ void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_updat
                     DG_CUDA(cudaMemcpyAsync(w.ups.p, g.hs.ups, sizeof(dg_update) * bucket, cudaMemcpyHostToDevice, st));
                 enqueue_mutate(c, g, st);
                 const bool emitted = enqueue_walks(c, g, st, -1);
-                enqueue_commit(c, g, st, emitted);
+                enqueue_commit(c, g, st, emitted, true);
                 if (!direct)
                     DG_CUDA(cudaMemcpyAsync(g.hs.res, w.res.p, sizeof(dg_update_result) * bucket,
                                             cudaMemcpyDeviceToHost, st));
@@ -1382,7 +1422,7 @@ void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_updat
     } else {
         stage_inputs();
         run_pre();
-        finish_eager();
+        finish_eager(true);
     }
     int64_t retries = 0;
     for (;;) {
@@ -1401,7 +1441,7 @@ void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_updat
             DG_CUDA(cudaMemsetAsync(&w.ctr.p->recovered, 0, sizeof(unsigned long long), st));
             walk_emitted = false;
         }
-        finish_eager();
+        finish_eager(whole);
         replayed = false;
     }
     if (res && !direct) std::memcpy(res, g.hs.res, sizeof(dg_update_result) * nu);

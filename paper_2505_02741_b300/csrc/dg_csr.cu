@@ -37,7 +37,8 @@ void ApplyScratch::ensure(DevAlloc& a, uint32_t changes, uint64_t stage_entries,
                                   &odeg, &ndeg, &ooff, &ncap, &rsz, &work, &r_off, &s_off, &w_off,
                                   &fwork, &f_off, &sdeg, &xm, &tdst};
         for (auto* b : bufs) b->ensure(a, (size_t)c + 1, st);
-        scan_tmp.ensure(a, scan_tmp_words(c + 1), st);
+        scan_words = scan_tmp_words(c + 1);
+        scan_tmp.ensure(a, 2 * scan_words, st);
         c_max = c;
     }
     totals.ensure(a, 2 * TOT_WORDS, st);
@@ -341,7 +342,7 @@ __global__ void k_plan_alloc(CSRView g, uint32_t* totals, uint64_t stage_cap, ui
 }
 
 void csr_plan(CSR& g, const ChangeList& cl, ApplyScratch& s, uint32_t* d_err, uint32_t pool_bit,
-              uint32_t cap_bit, cudaStream_t st) {
+              uint32_t cap_bit, cudaStream_t st, bool tmp_zeroed) {
     const int grid = flat_grid();
     const uint32_t C = cl.max_count;
     uint32_t* tot = s.totals.p;
@@ -353,7 +354,7 @@ void csr_plan(CSR& g, const ChangeList& cl, ApplyScratch& s, uint32_t* d_err, ui
     j1.in[2] = s.f_del.p;  j1.out[2] = s.p_del.p;  j1.total[2] = tot + TOT_ND;
     j1.k = 3;
     j1.err = d_err;
-    scan_exclusive(j1, cl.d_count, C, s.scan_tmp.p, st);
+    scan_exclusive(j1, cl.d_count, C, s.scan_tmp.p, st, tmp_zeroed);
     PlanArgs pa;
     pa.cl = cl;
     pa.g = g.view();
@@ -372,7 +373,7 @@ void csr_plan(CSR& g, const ChangeList& cl, ApplyScratch& s, uint32_t* d_err, ui
     j2.in[3] = s.fwork.p; j2.out[3] = s.f_off.p; j2.total[3] = tot + TOT_F;
     j2.k = 4;
     j2.err = d_err;
-    scan_exclusive(j2, tot + TOT_X, C, s.scan_tmp.p, st);
+    scan_exclusive(j2, tot + TOT_X, C, s.scan_tmp.p + s.scan_words, st, tmp_zeroed);
     k_plan_alloc<<<1, 1, 0, st>>>(g.view(), tot, s.s_cap, d_err, pool_bit, cap_bit);
     ++g_launches;
     DG_CHECK_LAUNCH();

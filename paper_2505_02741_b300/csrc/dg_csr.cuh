@@ -71,7 +71,8 @@ struct ApplyScratch {
     DBuf<uint32_t> f_head, f_ins, f_del, p_head, p_ins, p_del;
     DBuf<uint32_t> tv, tstart, tend, odeg, ndeg, ooff, ncap, rsz, work, r_off, s_off, w_off, fwork, f_off;
     DBuf<uint32_t> sdeg, xm, tdst;  // staged size, placement mode, twin destination (see k_plan_touch)
-    DBuf<uint32_t> scan_tmp, totals;
+    DBuf<uint32_t> scan_tmp, totals;  // scan_tmp: one region of scan_words per scan of the plan (2)
+    uint64_t scan_words = 0;
     DBuf<Ent> stage;
     void ensure(DevAlloc& a, uint32_t changes, uint64_t stage_entries, cudaStream_t st);
     void release(DevAlloc& a, cudaStream_t st);
@@ -88,8 +89,9 @@ void csr_build(CSR& g, DevAlloc& a, const uint64_t* keys, const uint32_t* vals, 
 
 // plan: sizes, relocation space and staging checks; raises pool_err_bit or
 // cap_err_bit in *d_err instead of writing anything when space is short.
+// tmp_zeroed: both scan_tmp regions were cleared by the caller
 void csr_plan(CSR& g, const ChangeList& cl, ApplyScratch& s, uint32_t* d_err, uint32_t pool_err_bit,
-              uint32_t cap_err_bit, cudaStream_t st);
+              uint32_t cap_err_bit, cudaStream_t st, bool tmp_zeroed = false);
 // execute: merge, place, refresh cached fields (no-op when *d_err has an abort bit)
 // touched: n + 1 words; entry x = (generation << 2) | bits for the vertices an
 // execution changed, word n = the array's generation (bumped per execution),

@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(LB_THREADS) k_scan_lookback(ScanArgs a, const 
 }
 
 void scan_exclusive(const ScanJob& job, const uint32_t* d_n, uint32_t n_max, uint32_t* tmp,
-                    cudaStream_t st) {
+                    cudaStream_t st, bool tmp_zeroed) {
     ScanArgs a;
     for (int j = 0; j < 4; ++j) {
         a.in[j] = job.in[j];
@@ -244,7 +244,7 @@ void scan_exclusive(const ScanJob& job, const uint32_t* d_n, uint32_t n_max, uin
         return;
     }
     const uint32_t tiles = lb_tiles(n_max);
-    cudaMemsetAsync(tmp, 0, scan_tmp_words(n_max) * 4, st);
+    if (!tmp_zeroed) cudaMemsetAsync(tmp, 0, scan_tmp_words(n_max) * 4, st);
     k_scan_lookback<<<tiles, LB_THREADS, 0, st>>>(a, d_n, n_max, tmp, tiles);
     ++g_launches;
 }
@@ -434,14 +434,20 @@ __global__ void __launch_bounds__(OS_THREADS) k_os_pass(const uint64_t* __restri
     }
 }
 
+size_t sort_clear_words(uint32_t n_max, int nbits) {
+    if (n_max == 0 || nbits <= 0) return 0;
+    const uint32_t tiles = os_tiles(n_max);
+    return OS_STATUS + (os_separate(tiles) ? 256ull * tiles * (uint64_t)((nbits + 7) / 8) : 0);
+}
+
 bool radix_sort_pairs(const SortBufs& b, const uint32_t* d_n, uint32_t n_max, int nbits,
-                      cudaStream_t st, const uint32_t* run_if) {
+                      cudaStream_t st, const uint32_t* run_if, bool hist_zeroed) {
     if (n_max == 0 || nbits <= 0) return false;
     const int passes = (nbits + 7) / 8;
     const uint32_t tiles = os_tiles(n_max);
     // digit totals and tile counters, then per pass a cleared status area
     const bool separate = os_separate(tiles);
-    cudaMemsetAsync(b.hist, 0, (OS_STATUS + (separate ? 256ull * tiles * passes : 0)) * 4, st);
+    if (!hist_zeroed) cudaMemsetAsync(b.hist, 0, sort_clear_words(n_max, nbits) * 4, st);
     uint32_t hblocks = (n_max + 255) / 256;
     if (hblocks > 148u * 8u) hblocks = 148u * 8u;
     k_os_hist<<<hblocks, 256, 0, st>>>(b.keys, d_n, n_max, passes, b.hist + OS_GHIST, run_if);

@@ -21,8 +21,9 @@ struct ScanJob {
     uint32_t* err = nullptr;  // optional: PRIM_ERR_SPIN is or-ed in here
 };
 size_t scan_tmp_words(uint32_t n_max);  // uint32 words of scratch for one ScanJob
+// tmp_zeroed: the caller has cleared scan_tmp_words(n_max) words of tmp (no memset here)
 void scan_exclusive(const ScanJob& job, const uint32_t* d_n, uint32_t n_max, uint32_t* tmp,
-                    cudaStream_t st);
+                    cudaStream_t st, bool tmp_zeroed = false);
 
 // Stable LSD radix sort of (uint64 key, uint32 value) pairs on the low nbits of
 // the key (8-bit digits, one-sweep: one histogram kernel, then one kernel per
@@ -41,9 +42,12 @@ struct SortBufs {
 size_t sort_hist_words(uint32_t n_max);
 size_t sort_scan_tmp_words(uint32_t n_max);
 // run_if (nullable device word): when it reads 0 the sort's kernels return at
-// once and the data stays where it was (callers then use the unsorted input)
+// once and the data stays where it was (callers then use the unsorted input).
+// hist_zeroed: the caller has cleared sort_clear_words(n_max, nbits) words of
+// hist (no memset here)
 bool radix_sort_pairs(const SortBufs& b, const uint32_t* d_n, uint32_t n_max, int nbits,
-                      cudaStream_t st, const uint32_t* run_if = nullptr);
+                      cudaStream_t st, const uint32_t* run_if = nullptr, bool hist_zeroed = false);
+size_t sort_clear_words(uint32_t n_max, int nbits);  // words of hist a sort needs zero on entry
 
 int bit_length(uint64_t x);
 

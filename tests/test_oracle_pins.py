@@ -319,6 +319,67 @@ def test_deletion_fallback_rule():
     assert hs == {(0, 2), (0, 4), (1, 5), (1, 6)}
 
 
+def test_fallback_rule_long_lists_brute_force():
+    """With a step limit of 1 no walker can reach the far endpoint of a deleted
+    edge (the edge is gone from G_b and there are no parallel edges), so every
+    deletion of an H edge falls back.  H_b must then be H' plus, for each
+    endpoint of each deletion, its minimum-resistance G_b edge outside H'
+    (ties: smaller neighbour id).  Computed here by brute force on two hubs of
+    3000 and 1500 neighbours whose minimum resistance is tied at several
+    positions of the list, and on the ring vertices at the other end."""
+    rng = np.random.default_rng(31)
+    n = 5000
+    edges = {}
+    for i in range(2, n):  # ring over 2..n-1, all in H
+        j = 2 + (i - 2 + 1) % (n - 2)
+        edges[(min(i, j), max(i, j))] = True
+    for h, d in ((0, 3000), (1, 1500)):
+        for y in rng.choice(np.arange(2, n), d, replace=False):
+            edges[(h, int(y))] = bool(rng.random() < 0.3)
+    edges[(0, 1)] = True
+    keys = sorted(edges)
+    a = np.array([k[0] for k in keys], np.int32)
+    b = np.array([k[1] for k in keys], np.int32)
+    in_h = np.array([edges[k] for k in keys])
+    w = rng.uniform(0.1, 10.0, a.size)
+    for h, ties in ((0, 5), (1, 3)):  # tied minimum resistance outside H, spread over the list
+        idx = np.nonzero((a == h) & (b >= 2) & ~in_h)[0]
+        w[rng.choice(idx, ties, replace=False)] = 20.0
+    g = OracleGraph(n, a, b, w, T=1, s=4)
+    g.init_sparsifier(a[in_h], b[in_h])
+    dels = rng.choice(np.nonzero(in_h & (a <= 1) & (b >= 2))[0], 150, replace=False)
+    du, dv = a[dels].copy(), b[dels].copy()
+    flip = rng.random(dels.size) < 0.5
+    du[flip], dv[flip] = dv[flip], du[flip]
+    du, dv = np.append(du, 0), np.append(dv, 1)
+    r = g.apply(du, dv, np.zeros(du.size), np.ones(du.size, np.int32))
+    assert (r["walked"] == 1).all() and (r["hit"] == 0).all() and (r["fallback"] == 1).all()
+    # brute force
+    deleted = {(min(x, y), max(x, y)) for x, y in zip(du.tolist(), dv.tolist())}
+    wt = {k: float(x) for k, x in zip(keys, w)}
+    gb = {k for k in keys if k not in deleted}
+    hp = {k for k in keys if edges[k] and k not in deleted}
+    nbrs = {}
+    for x, y in gb:
+        nbrs.setdefault(x, []).append(y)
+        nbrs.setdefault(y, []).append(x)
+    expect = set(hp)
+    for i, (u, v) in enumerate(zip(du.tolist(), dv.tolist())):
+        picked = 0
+        for x in (u, v):
+            cand = [(1.0 / wt[(min(x, y), max(x, y))], y) for y in nbrs.get(x, [])
+                    if (min(x, y), max(x, y)) not in hp]
+            if cand:
+                _, y = min(cand)
+                expect.add((min(x, y), max(x, y)))
+                picked += 1
+        assert r["nrecovered"][i] == picked
+    ha, hb, hw = g.edges("H")
+    got = set(zip(ha.tolist(), hb.tolist()))
+    assert got == expect
+    assert all(float(x) == wt[(int(p), int(q))] for p, q, x in zip(ha, hb, hw))
+
+
 # ---------------------------------------------------------------------------
 # Algorithm 1 and the batch snapshot, restated independently in Python
 # ---------------------------------------------------------------------------

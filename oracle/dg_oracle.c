@@ -451,6 +451,86 @@ typedef struct {
 } orc_walker_out;
 
 /*
+ * The s walkers of walked update i on the batch snapshot and what Eq. 12
+ * makes of them (Section III-B/C): every walker's stop (wr, s records), the
+ * early-exit cut of reading R8, then hit, nhits, the argmin walker (R9),
+ * steps and R~.  When nhits_min is given, a deletion with a hit also gets its
+ * pruned counts: each walker re-walked with the cut R > R~ (a walker whose
+ * resistance exceeds R~ can no longer give the minimum), the walkers at R~,
+ * their steps, and (wlo, nullable) every walker's pruned record.  Reads the
+ * graphs only; writes only update i's outputs, so the walks of different
+ * updates may run at the same time.
+ */
+static void walk_update(const orc_state *st, const orc_graph *G, const orc_graph *H, int64_t i,
+                        const int32_t *u, const int32_t *v, const double *w, const int32_t *op,
+                        uint64_t id0, orc_walker_out *wr, int32_t *paths, uint8_t *hit, int32_t *nhits,
+                        int32_t *best, int32_t *steps, double *rest, int32_t *nhits_min, int32_t *steps_lo,
+                        orc_walker_out *wlo)
+{
+    const int32_t s = st->s, T = st->T;
+    const int deletion = (op[i] == OP_DEL);
+    const orc_graph *g = deletion ? G : H;
+    const uint64_t upd_id = id0 + (uint64_t)i;
+    const double wpq = deletion ? 0.0 : w[i];
+    int32_t first_hit = -1; /* smallest step at which some walker hit */
+    for (int32_t k = 0; k < s; k++) {
+        int32_t *row = paths ? paths + ((size_t)i * s + k) * (size_t)(T + 1) : NULL;
+        wr[k].reason = walk_one(g, u[i], v[i], wpq, deletion, st->K, T, st->seed, upd_id, (uint32_t)k,
+                                INFINITY, &wr[k].steps, &wr[k].R, row);
+        if (row) /* pad the unused tail of the path with -1 */
+            for (int32_t t = wr[k].steps + 1; t <= T; t++) row[t] = -1;
+        if (wr[k].reason == STOP_HIT && (first_hit < 0 || wr[k].steps < first_hit)) first_hit = wr[k].steps;
+    }
+    /* reading R8: insertion walkers are cut at the first hitting step (a walker
+     * that stopped exactly there for another reason keeps its reason) */
+    if (!deletion && st->early_exit && first_hit >= 0) {
+        for (int32_t k = 0; k < s; k++) {
+            if (wr[k].steps > first_hit) {
+                wr[k].steps = first_hit;
+                wr[k].reason = STOP_CUT;
+                if (paths)
+                    for (int32_t t = first_hit + 1; t <= T; t++)
+                        paths[((size_t)i * s + k) * (size_t)(T + 1) + t] = -1;
+            }
+        }
+    }
+    /* Eq. 12: minimum over the walkers that reached q; ties -> lowest id (R9) */
+    int32_t nh = 0, bw = -1, tot = 0;
+    double Rmin = INFINITY;
+    for (int32_t k = 0; k < s; k++) {
+        tot += wr[k].steps;
+        if (wr[k].reason != STOP_HIT) continue;
+        nh++;
+        if (wr[k].R < Rmin) {
+            Rmin = wr[k].R;
+            bw = k;
+        }
+    }
+    nhits[i] = nh;
+    best[i] = bw;
+    steps[i] = tot;
+    rest[i] = Rmin;
+    hit[i] = (uint8_t)(nh > 0);
+    if (!nhits_min) return;
+    nhits_min[i] = nh;
+    steps_lo[i] = tot;
+    if (wlo)
+        for (int32_t k = 0; k < s; k++) wlo[k] = wr[k];
+    if (!deletion || nh == 0) return;
+    int32_t nmin = 0, lo = 0;
+    for (int32_t k = 0; k < s; k++) {
+        orc_walker_out c;
+        c.reason = walk_one(g, u[i], v[i], 0.0, 1, st->K, T, st->seed, upd_id, (uint32_t)k, Rmin, &c.steps,
+                            &c.R, NULL);
+        if (c.reason == STOP_HIT) nmin++; /* a hit under the cut R > R~ has R = R~ */
+        lo += c.steps;
+        if (wlo) wlo[k] = c;
+    }
+    nhits_min[i] = nmin;
+    steps_lo[i] = lo;
+}
+
+/*
  * Apply one batch of nu updates.  Per-update outputs (each an array of nu):
  *   status, walked, hit, accepted, fallback, nhits, best, nrec, steps, rest.
  * Optional: wout (nu*s records) and paths (nu*s*(T+1) vertices, -1 padded).
@@ -463,26 +543,26 @@ typedef struct {
  * exceeds R~ (a walker there can no longer give the minimum of Eq. 12);
  * otherwise nhits and steps.  These are the deletion-pruning counterparts of
  * nhits and steps: the minimum walker, R~ and the recovered edges are the
- * same with or without pruning.
+ * same with or without pruning.  wout_lo (nullable, nu*s records, only with
+ * nhits_min): every walker's record under that cut (the plain record where
+ * no cut applies).
  * Returns 0, or -2 on allocation failure.
  */
 int orc_apply_batch(orc_state *st, int64_t nu, const int32_t *u, const int32_t *v, const double *w,
                     const int32_t *op, int32_t *status, uint8_t *walked, uint8_t *hit,
                     uint8_t *accepted, uint8_t *fallback, int32_t *nhits, int32_t *best,
                     int32_t *nrec, int32_t *steps, double *rest, orc_walker_out *wout,
-                    int32_t *paths, const uint8_t *walk_mask, int32_t *nhits_min, int32_t *steps_lo)
+                    int32_t *paths, const uint8_t *walk_mask, int32_t *nhits_min, int32_t *steps_lo,
+                    orc_walker_out *wout_lo)
 {
     orc_graph *G = &st->G, *H = &st->H;
     const int32_t n = G->n, s = st->s, T = st->T;
     const uint64_t id0 = st->next_id;
     int rc = 0;
     orc_pairs commit = {0}, hdel = {0};
-    int32_t *wsteps = (int32_t *)malloc((size_t)s * sizeof(int32_t));
-    int32_t *wreason = (int32_t *)malloc((size_t)s * sizeof(int32_t));
-    double *wR = (double *)malloc((size_t)s * sizeof(double));
-    int32_t *path = (int32_t *)malloc((size_t)(T + 1) * sizeof(int32_t));
+    orc_walker_out *wr = wout ? wout : (orc_walker_out *)malloc((size_t)(nu > 0 ? nu : 1) * s * sizeof(orc_walker_out));
     int32_t *best_path = (int32_t *)malloc((size_t)(T + 1) * sizeof(int32_t));
-    if (!wsteps || !wreason || !wR || !path || !best_path) {
+    if (!wr || !best_path) {
         rc = -2;
         goto done;
     }
@@ -497,6 +577,13 @@ int orc_apply_batch(orc_state *st, int64_t nu, const int32_t *u, const int32_t *
         nrec[i] = 0;
         steps[i] = 0;
         rest[i] = INFINITY;
+        if (nhits_min) nhits_min[i] = steps_lo[i] = 0;
+        for (int32_t k = 0; k < s; k++) {
+            wr[(size_t)i * s + k].reason = STOP_NONE;
+            wr[(size_t)i * s + k].steps = 0;
+            wr[(size_t)i * s + k].R = 0.0;
+            if (wout_lo) wout_lo[(size_t)i * s + k] = wr[(size_t)i * s + k];
+        }
         int32_t a = u[i], b = v[i];
         if (op[i] != OP_INS && op[i] != OP_DEL) {
             status[i] = ORC_BAD_OP;
@@ -545,85 +632,24 @@ int orc_apply_batch(orc_state *st, int64_t nu, const int32_t *u, const int32_t *
     /* (ii) H' = H minus the deleted sparsifier edges (G is now G_b). */
     for (int64_t k = 0; k < hdel.n; k++) edge_remove(H, hdel.e[k].a, hdel.e[k].b);
 
-    /* (iii) walks from the snapshot (H' for insertions, G_b for deletions). */
+    /* (iii) walks from the snapshot (H' for insertions, G_b for deletions).
+     * Every update's walks read the same snapshot and fill only its own
+     * outputs; the OpenMP build of this file runs them on several host
+     * threads (identical results: nothing here depends on their order). */
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < nu; i++) {
+        if (!walked[i]) continue;
+        if (walk_mask && !walk_mask[i]) continue;
+        walk_update(st, G, H, i, u, v, w, op, id0, wr + (size_t)i * s, paths, hit, nhits, best, steps, rest,
+                    nhits_min, steps_lo, wout_lo ? wout_lo + (size_t)i * s : NULL);
+    }
+
+    /* (iv) the edges each update returns, in update order. */
     for (int64_t i = 0; i < nu; i++) {
         if (!walked[i]) continue;
         if (walk_mask && !walk_mask[i]) continue;
         const int deletion = (op[i] == OP_DEL);
-        const orc_graph *g = deletion ? G : H;
-        const uint64_t upd_id = id0 + (uint64_t)i;
-        const double wpq = deletion ? 0.0 : w[i];
-        int32_t first_hit = -1; /* smallest step at which some walker hit */
-        for (int32_t k = 0; k < s; k++) {
-            wreason[k] = walk_one(g, u[i], v[i], wpq, deletion, st->K, T, st->seed, upd_id,
-                                  (uint32_t)k, INFINITY, &wsteps[k], &wR[k],
-                                  paths ? paths + ((size_t)i * s + k) * (size_t)(T + 1) : NULL);
-            if (paths) /* pad the unused tail of the path with -1 */
-                for (int32_t t = wsteps[k] + 1; t <= T; t++)
-                    paths[((size_t)i * s + k) * (size_t)(T + 1) + t] = -1;
-            if (wreason[k] == STOP_HIT && (first_hit < 0 || wsteps[k] < first_hit))
-                first_hit = wsteps[k];
-        }
-        /* reading R8: insertion walkers are cut at the first hitting step */
-        if (!deletion && st->early_exit && first_hit >= 0) {
-            for (int32_t k = 0; k < s; k++) {
-                if (wsteps[k] > first_hit) {
-                    wsteps[k] = first_hit;
-                    wreason[k] = STOP_CUT;
-                } else if (wsteps[k] == first_hit && wreason[k] != STOP_HIT) {
-                    /* stopped exactly at k* for another reason: keeps its reason */
-                }
-            }
-        }
-        /* Eq. 12: minimum over the walkers that reached q; ties -> lowest id (R9) */
-        int32_t nh = 0, bw = -1, tot = 0;
-        double Rmin = INFINITY;
-        for (int32_t k = 0; k < s; k++) {
-            tot += wsteps[k];
-            if (wreason[k] != STOP_HIT) continue;
-            nh++;
-            if (wR[k] < Rmin) {
-                Rmin = wR[k];
-                bw = k;
-            }
-        }
-        nhits[i] = nh;
-        best[i] = bw;
-        steps[i] = tot;
-        rest[i] = Rmin;
-        hit[i] = (uint8_t)(nh > 0);
-        if (nhits_min) {
-            nhits_min[i] = nh;
-            steps_lo[i] = tot;
-            if (deletion && nh > 0) {
-                int32_t nmin = 0, lo = 0;
-                for (int32_t k = 0; k < s; k++) {
-                    if (wreason[k] == STOP_HIT && wR[k] == Rmin) {
-                        nmin++;
-                        lo += wsteps[k];
-                    } else {
-                        int32_t sk = 0;
-                        double Rk = 0.0;
-                        walk_one(g, u[i], v[i], 0.0, 1, st->K, T, st->seed, upd_id, (uint32_t)k, Rmin,
-                                 &sk, &Rk, NULL);
-                        lo += sk;
-                    }
-                }
-                nhits_min[i] = nmin;
-                steps_lo[i] = lo;
-            }
-        }
-        if (paths && !deletion && st->early_exit && first_hit >= 0)
-            for (int32_t k = 0; k < s; k++)
-                for (int32_t t = wsteps[k] + 1; t <= T; t++)
-                    paths[((size_t)i * s + k) * (size_t)(T + 1) + t] = -1;
-        if (wout)
-            for (int32_t k = 0; k < s; k++) {
-                wout[(size_t)i * s + k].reason = wreason[k];
-                wout[(size_t)i * s + k].steps = wsteps[k];
-                wout[(size_t)i * s + k].R = wR[k];
-            }
-
+        const int32_t nh = nhits[i], bw = best[i];
         if (!deletion) {
             /* Section III-B: kept iff q was not reached by any walker. */
             accepted[i] = (uint8_t)(nh == 0);
@@ -641,8 +667,8 @@ int orc_apply_batch(orc_state *st, int64_t nu, const int32_t *u, const int32_t *
             /* re-run the argmin walker to get its walk (same counters -> same path) */
             int32_t ts;
             double tR;
-            walk_one(g, u[i], v[i], 0.0, 1, st->K, T, st->seed, upd_id, (uint32_t)bw, INFINITY, &ts, &tR,
-                     best_path);
+            walk_one(G, u[i], v[i], 0.0, 1, st->K, T, st->seed, id0 + (uint64_t)i, (uint32_t)bw, INFINITY, &ts,
+                     &tR, best_path);
             /* R10: distinct edges of the walk that are not in H' */
             for (int32_t t = 0; t < ts; t++) {
                 int32_t x = best_path[t], y = best_path[t + 1];
@@ -695,7 +721,7 @@ int orc_apply_batch(orc_state *st, int64_t nu, const int32_t *u, const int32_t *
         nrec[i] = emitted;
     }
 
-    /* (iv) H_b = H' U committed edges (set union; weights from G_b). */
+    /* (v) H_b = H' U committed edges (set union; weights from G_b). */
     for (int64_t k = 0; k < commit.n; k++) {
         int32_t a = commit.e[k].a, b = commit.e[k].b;
         if (graph_has(H, a, b)) continue;
@@ -711,12 +737,31 @@ int orc_apply_batch(orc_state *st, int64_t nu, const int32_t *u, const int32_t *
 done:
     free(commit.e);
     free(hdel.e);
-    free(wsteps);
-    free(wreason);
-    free(wR);
-    free(path);
+    if (wr != wout) free(wr);
     free(best_path);
     return rc;
+}
+
+/* Threads the walk phase may use (the OpenMP build; a no-op otherwise). */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+void orc_set_threads(int32_t k)
+{
+#ifdef _OPENMP
+    if (k > 0) omp_set_num_threads(k);
+#else
+    (void)k;
+#endif
+}
+
+int32_t orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return (int32_t)omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /* ------------------------------------------------------------------------ */

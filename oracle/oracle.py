@@ -5,7 +5,11 @@ benchmark's CPU-baseline / reference arm; the product path never loads it.
 
 ``build()`` compiles ``dg_oracle.c`` with ``gcc -O2 -ffp-contract=off`` so that
 every FP64 add and multiply is rounded on its own, as the paper's estimator is
-written (Eq. 12: sums of r_e in walk order; threshold w_pq * R > K).
+written (Eq. 12: sums of r_e in walk order; threshold w_pq * R > K).  It builds
+the file twice: ``libdg_oracle.so`` (single-threaded) and, with ``-fopenmp``,
+``libdg_oracle_omp.so``, whose walk phase runs the updates of a batch on
+several host threads (the multi-threaded CPU form of Section III-E/F) with
+identical results.  ``OracleGraph(threads=k)`` selects the second.
 """
 from __future__ import annotations
 
@@ -18,6 +22,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "dg_oracle.c")
 LIB = os.path.join(HERE, "libdg_oracle.so")
+LIB_OMP = os.path.join(HERE, "libdg_oracle_omp.so")
 
 # walker stop reasons (dg_oracle.c)
 STOP_HIT, STOP_OVER_K, STOP_AT_T, STOP_LEAF, STOP_CUT = 1, 2, 3, 4, 5
@@ -25,23 +30,29 @@ STOP_HIT, STOP_OVER_K, STOP_AT_T, STOP_LEAF, STOP_CUT = 1, 2, 3, 4, 5
 WALKER_DTYPE = np.dtype([("reason", "<i4"), ("steps", "<i4"), ("R", "<f8")])
 
 
+def _compile(out: str, extra: list) -> None:
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-Wall", "-Wno-unknown-pragmas", *extra, "-o", out + ".tmp", SRC, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(out + ".tmp", out)
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle into a shared library next to its source."""
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-               "-Wall", "-o", LIB + ".tmp", SRC, "-lm"]
-        subprocess.check_call(cmd)
-        os.replace(LIB + ".tmp", LIB)
+    """Compile the oracle (both builds) into shared libraries next to its source."""
+    for out, extra in ((LIB, []), (LIB_OMP, ["-fopenmp"])):
+        if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(SRC):
+            _compile(out, extra)
     return LIB
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        L = C.CDLL(build())
+def lib(omp: bool = False):
+    """The single-threaded oracle library, or its OpenMP build (omp=True)."""
+    if omp not in _libs:
+        build()
+        L = C.CDLL(LIB_OMP if omp else LIB)
         P = C.c_void_p
         i32p = np.ctypeslib.ndpointer(np.int32, flags="C")
         f64p = np.ctypeslib.ndpointer(np.float64, flags="C")
@@ -60,7 +71,7 @@ def lib():
                                C.c_uint32, C.POINTER(C.c_int32), C.POINTER(C.c_double), P]
         L.orc_walk.restype = C.c_int
         L.orc_apply_batch.argtypes = [P, C.c_int64, i32p, i32p, f64p, i32p, i32p, u8p, u8p, u8p, u8p,
-                                      i32p, i32p, i32p, i32p, f64p, P, P, P, P, P]
+                                      i32p, i32p, i32p, i32p, f64p, P, P, P, P, P, P]
         L.orc_apply_batch.restype = C.c_int
         L.orc_query.argtypes = [P, C.c_int, C.c_int64, i32p, i32p, f64p]
         L.orc_query.restype = C.c_int64
@@ -70,8 +81,12 @@ def lib():
         L.orc_next_id.restype = C.c_uint64
         L.orc_set_next_id.argtypes = [P, C.c_uint64]
         L.orc_set_next_id.restype = None
-        _lib = L
-    return _lib
+        L.orc_set_threads.argtypes = [C.c_int32]
+        L.orc_set_threads.restype = None
+        L.orc_max_threads.argtypes = []
+        L.orc_max_threads.restype = C.c_int32
+        _libs[omp] = L
+    return _libs[omp]
 
 
 def philox4x32_10(ctr, key) -> np.ndarray:
@@ -85,44 +100,49 @@ def philox4x32_10(ctr, key) -> np.ndarray:
 class OracleGraph:
     """One dynamic graph G with its sparsifier H, driven update by update."""
 
-    def __init__(self, n, u, v, w, *, seed=0, K=100.0, T=100, s=32, early_exit=True):
+    def __init__(self, n, u, v, w, *, seed=0, K=100.0, T=100, s=32, early_exit=True, threads=1):
+        """threads > 1 (or 0 = every host core) uses the OpenMP build."""
         self.n, self.T, self.s = int(n), int(T), int(s)
+        self._lib = lib(omp=threads != 1)
+        if threads != 1:
+            self._lib.orc_set_threads(int(threads) if threads > 0 else (os.cpu_count() or 1))
+        self.threads = int(self._lib.orc_max_threads())
         u = np.ascontiguousarray(u, np.int32)
         v = np.ascontiguousarray(v, np.int32)
         w = np.ascontiguousarray(w, np.float64)
-        self._h = lib().orc_create(self.n, u.size, u, v, w, int(seed), float(K), self.T, self.s,
+        self._h = self._lib.orc_create(self.n, u.size, u, v, w, int(seed), float(K), self.T, self.s,
                                    1 if early_exit else 0)
         if not self._h:
             raise ValueError("oracle rejected the graph (not simple, ids out of range or bad weight)")
 
     def close(self):
         if getattr(self, "_h", None):
-            lib().orc_destroy(self._h)
+            self._lib.orc_destroy(self._h)
             self._h = None
 
     def __del__(self):
         self.close()
 
     def init_sparsifier(self, hu, hv):
-        rc = lib().orc_init_sparsifier(self._h, len(hu), np.ascontiguousarray(hu, np.int32),
+        rc = self._lib.orc_init_sparsifier(self._h, len(hu), np.ascontiguousarray(hu, np.int32),
                                        np.ascontiguousarray(hv, np.int32))
         if rc != 0:
             raise ValueError("oracle rejected the sparsifier (edge not in G)")
 
     @property
     def next_id(self) -> int:
-        return int(lib().orc_next_id(self._h))
+        return int(self._lib.orc_next_id(self._h))
 
     @next_id.setter
     def next_id(self, value: int):
-        lib().orc_set_next_id(self._h, int(value))
+        self._lib.orc_set_next_id(self._h, int(value))
 
     def walk(self, p, q, wpq, deletion, upd_id, walker, on_h=True):
         """One walker; returns (reason, steps, R, path)."""
         steps = C.c_int32()
         R = C.c_double()
         path = np.full(self.T + 1, -1, np.int32)
-        reason = lib().orc_walk(self._h, 1 if on_h else 0, int(p), int(q), float(wpq),
+        reason = self._lib.orc_walk(self._h, 1 if on_h else 0, int(p), int(q), float(wpq),
                                 1 if deletion else 0, int(upd_id), int(walker), C.byref(steps),
                                 C.byref(R), path.ctypes.data)
         if reason < 0:
@@ -136,7 +156,8 @@ class OracleGraph:
         mode for very large batches; H then lacks the unsampled commits).
         prune_bounds: also return nhits_min and steps_lo, the values nhits and
         steps take for a walked deletion whose walkers stop once their
-        resistance exceeds R~ (equal to nhits and steps elsewhere)."""
+        resistance exceeds R~ (equal to nhits and steps elsewhere), and with
+        walkers=True every walker's record under that cut ("walkers_lo")."""
         mask = None if walk_mask is None else np.ascontiguousarray(walk_mask, np.uint8)
         nu = len(u)
         u = np.ascontiguousarray(u, np.int32)
@@ -152,19 +173,23 @@ class OracleGraph:
             out["nhits_min"] = np.zeros(nu, np.int32)
             out["steps_lo"] = np.zeros(nu, np.int32)
         wout = np.zeros(nu * self.s, WALKER_DTYPE) if walkers else None
+        wlo = np.zeros(nu * self.s, WALKER_DTYPE) if walkers and prune_bounds else None
         pbuf = np.full(nu * self.s * (self.T + 1), -1, np.int32) if paths else None
-        rc = lib().orc_apply_batch(self._h, nu, u, v, w, op, out["status"], out["walked"], out["hit"],
-                                   out["accepted"], out["fallback"], out["nhits"], out["best_walker"],
-                                   out["nrecovered"], out["steps"], out["r_est"],
-                                   None if wout is None else wout.ctypes.data,
-                                   None if pbuf is None else pbuf.ctypes.data,
-                                   None if mask is None else mask.ctypes.data,
-                                   out["nhits_min"].ctypes.data if prune_bounds else None,
-                                   out["steps_lo"].ctypes.data if prune_bounds else None)
+        rc = self._lib.orc_apply_batch(self._h, nu, u, v, w, op, out["status"], out["walked"], out["hit"],
+                                       out["accepted"], out["fallback"], out["nhits"], out["best_walker"],
+                                       out["nrecovered"], out["steps"], out["r_est"],
+                                       None if wout is None else wout.ctypes.data,
+                                       None if pbuf is None else pbuf.ctypes.data,
+                                       None if mask is None else mask.ctypes.data,
+                                       out["nhits_min"].ctypes.data if prune_bounds else None,
+                                       out["steps_lo"].ctypes.data if prune_bounds else None,
+                                       None if wlo is None else wlo.ctypes.data)
         if rc != 0:
             raise MemoryError("oracle batch failed")
         if walkers:
             out["walkers"] = wout.reshape(nu, self.s)
+        if wlo is not None:
+            out["walkers_lo"] = wlo.reshape(nu, self.s)
         if paths:
             out["paths"] = pbuf.reshape(nu, self.s, self.T + 1)
         return out
@@ -174,12 +199,12 @@ class OracleGraph:
         wh = 1 if which == "H" else 0
         dummy_i = np.zeros(1, np.int32)
         dummy_f = np.zeros(1, np.float64)
-        cnt = lib().orc_query(self._h, wh, 0, dummy_i, dummy_i, dummy_f)
+        cnt = self._lib.orc_query(self._h, wh, 0, dummy_i, dummy_i, dummy_f)
         a = np.zeros(max(cnt, 1), np.int32)
         b = np.zeros(max(cnt, 1), np.int32)
         w = np.zeros(max(cnt, 1), np.float64)
-        lib().orc_query(self._h, wh, cnt, a, b, w)
+        self._lib.orc_query(self._h, wh, cnt, a, b, w)
         return a[:cnt], b[:cnt], w[:cnt]
 
     def degree(self, x, which="H"):
-        return int(lib().orc_degree(self._h, 1 if which == "H" else 0, int(x)))
+        return int(self._lib.orc_degree(self._h, 1 if which == "H" else 0, int(x)))

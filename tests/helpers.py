@@ -148,6 +148,7 @@ class ReferenceStream:
                 # minimum; its steps end at the first such step, recomputed here from
                 # its path and the G_b weights (r = 1/w, summed in walk order)
                 r["nhits_min"], r["steps_lo"] = r["nhits"], r["steps"]
+                r["walkers_lo"] = list(zip(reasons, steps))
                 if deletion and hits:
                     rstar = r["r_est"]
                     lo = 0
@@ -160,6 +161,7 @@ class ReferenceStream:
                             R = R + 1.0 / Gb[_key(int(paths[k][t - 1]), int(paths[k][t]))]
                             if R > rstar:
                                 cut = t
+                                r["walkers_lo"][k] = (STOP_CUT, t)
                                 break
                         lo += cut
                     r["nhits_min"] = sum(1 for k in hits if Rs[k] == rstar)

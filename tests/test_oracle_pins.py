@@ -422,6 +422,8 @@ def _mixed_stream(rng, n, a, b, count, invalid=True):
 def _compare(ref_res, orc_res):
     for i, r in enumerate(ref_res):
         for k, v in r.items():
+            if k == "walkers_lo":  # compared walker by walker by the caller
+                continue
             got = orc_res[k][i]
             if isinstance(v, float) and math.isinf(v):
                 assert math.isinf(got), (i, k)
@@ -497,11 +499,44 @@ def test_deletion_pruning_bounds(seed):
     for lo in range(0, len(ups), 25):
         chunk = ups[lo:lo + 25]
         cols = list(zip(*chunk))
-        out = g.apply(list(cols[0]), list(cols[1]), list(cols[2]), list(cols[3]), prune_bounds=True)
-        _compare(ref.apply(chunk), out)
+        out = g.apply(list(cols[0]), list(cols[1]), list(cols[2]), list(cols[3]), prune_bounds=True,
+                      walkers=True)
+        rr = ref.apply(chunk)
+        _compare(rr, out)
+        # every walker's record under the cut: stop reason and step count
+        for i, r in enumerate(rr):
+            if not r["walked"]:
+                continue
+            assert [tuple(x) for x in r["walkers_lo"]] == \
+                [(int(x["reason"]), int(x["steps"])) for x in out["walkers_lo"][i]], (lo, i)
+        assert (out["walkers_lo"]["steps"].sum(axis=1) == out["steps_lo"]).all()
         assert (out["steps_lo"] <= out["steps"]).all() and (out["nhits_min"] <= out["nhits"]).all()
         pruned += int((out["steps"] - out["steps_lo"]).sum())
     assert pruned > 0
+
+
+@pytest.mark.parametrize("threads", [2, 4])
+def test_openmp_build_gives_identical_outputs(threads):
+    """The OpenMP build of the oracle runs the walks of a batch's updates on
+    several host threads; every output (results, walker records, paths, the
+    pruned counts, H and G) equals the single-threaded build's, batch after
+    batch."""
+    wl, st = W.make_grid(24, 24)
+    one = OracleGraph(wl.n, wl.a, wl.b, wl.w, T=60)
+    many = OracleGraph(wl.n, wl.a, wl.b, wl.w, T=60, threads=threads)
+    assert many.threads == threads and one.threads == 1
+    for g in (one, many):
+        g.init_sparsifier(wl.a[wl.h_ids], wl.b[wl.h_ids])
+    for _ in range(3):
+        bt = st.next_batch(80, 60)
+        r1 = one.apply(bt.u, bt.v, bt.w, bt.op, walkers=True, paths=True, prune_bounds=True)
+        r2 = many.apply(bt.u, bt.v, bt.w, bt.op, walkers=True, paths=True, prune_bounds=True)
+        assert r1.keys() == r2.keys()
+        for k in r1:
+            assert np.asarray(r1[k]).tobytes() == np.asarray(r2[k]).tobytes(), k
+        for which in ("H", "G"):
+            for x, y in zip(one.edges(which), many.edges(which)):
+                assert x.tobytes() == y.tobytes()
 
 
 def test_invariants_after_stream():

@@ -1,22 +1,29 @@
-"""Benchmark: batched dyGRASS updates on the 3-D power-grid-like mesh.
+"""Benchmark: batched dyGRASS updates on one B300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--workload rmat|mesh|fea|serve]
 
-Workload: 100x100x100 mesh (1M vertices, 2.97M edges, w = 10^U(-2,2), z edges
-x5), H(0) = max-weight spanning forest + 10 % of the off-tree edges, K = 100,
-T = 100, s = 32.  One step = one batch of 10k insertions (<= 6 hops apart) and
-10k deletions of current edges, shuffled.  Synthetic data, seeded.
+Default workload (the largest single-GPU configuration): symmetrised R-MAT
+scale 22 (4.2M vertices, 64M undirected edges, a,b,c,d = .57,.19,.19,.05, unit
+weights), H(0) = max-weight spanning forest + 10 % of the off-tree edges,
+K = 100, T = 100, s = 32.  One step = one batch of 50k updates: 30k insertions
+between random vertex pairs and 20k deletions of current edges, shuffled.
+``--workload mesh`` (3-D mesh 100^3, 10k + 10k per batch) and ``fea`` (jittered
+triangulated 2048^2 grid, 50k + 50k) are the other batch configurations;
+``serve`` runs the serving configuration.  Synthetic data, seeded.
 
 value    : updates/s of the batched form, batches already resident in HBM
            (dg_apply_updates_device), CUDA events on the batch stream, L2
            flushed (256 MB write) between steps.
-e2e      : the same through dg_apply_updates with host buffers (H2D of the
-           batch, D2H of the results inside the timed region).
-roofline : the walk kernel, algorithmic bytes = 32 B (one DRAM sector) per
-           useful walk step, against the measured HBM copy bandwidth.
+e2e      : the same through dg_apply_updates with pinned host buffers (H2D of
+           the batch, D2H of the results inside the timed region).
+roofline : the walk kernel: algorithmic bytes = 20 B per useful walk step (the
+           vertex record, the neighbour id and its resistance), against the
+           measured HBM copy bandwidth; ``gather`` restates it at the sector
+           level (two 32-byte sectors per step).
 Also reported: walk-steps/s, the one-launch-per-update form at identical
-outputs, per-batch latency p50/p99 of both forms, and the CPU oracle on a
-bounded sample of the same workload.
+outputs, per-batch latency p50/p99, and the CPU oracle on a bounded sample of
+the same workload, single-threaded and on every host core.
 
 Under torchrun each rank runs an independent replica (its own seed); there is
 no collective on the data path; rank 0 prints the whole-job line.
@@ -26,6 +33,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import subprocess
 import sys
 import threading
@@ -35,16 +43,28 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the scale-22 graph takes about a minute to draw: keep it for the later runs on this host
+os.environ.setdefault("DG_WORKLOAD_CACHE", "/tmp/dg_workload_cache")
 
 METRIC = "updates/s & walk-steps/s on 1 B300, batched vs per-update; p50/p99 latency"
-BYTES_PER_STEP = 32  # one 32-byte DRAM sector per walk step (the entry holds nbr, next list, rev, r)
-N_INS, N_DEL = 10_000, 10_000
-# DRAM bytes (read + write) of one walk launch of this workload, from one ncu
-# capture of the current walk kernel (cold L2), or None while the kernel has
-# changed since its last capture.
+ALG_BYTES_PER_STEP = 20      # vertex record (8 B) + neighbour id (4 B) + its resistance (8 B)
+SECTOR_BYTES_PER_STEP = 64   # the same step at DRAM-sector granularity (two 32-byte sectors)
+# DRAM bytes (read + write) of one walk launch of the default workload, from one
+# ncu capture of the current walk kernel, or None while the kernel has changed
+# since its last capture.
 WALK_TRAFFIC_BYTES = None
-WALK_TRAFFIC_SOURCE = ("stale: the walk kernel changed after its last capture (profiles/walk_k_walk_batched_mesh3d_100.md "
-                       "measured 2.735e8 B per launch before the fallback queue claimed long lists)")
+WALK_TRAFFIC_SOURCE = "not captured for the current walk kernel"
+
+BATCH = {"rmat": (30_000, 20_000), "mesh": (10_000, 10_000), "fea": (50_000, 50_000)}
+
+
+def make_workload(name, args, seed):
+    from paper_2505_02741_b300 import workloads as W
+    if name == "rmat":
+        return W.make_rmat(scale=args.rmat_scale, n_edges=args.rmat_edges, seed=seed)
+    if name == "fea":
+        return W.make_fea(seed=seed)
+    return W.make_mesh3d(seed=seed)
 
 
 def measured_peaks():
@@ -56,32 +76,67 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
-class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+def host_cpu():
+    model = platform.processor() or ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
 
-    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
-         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-         "clocks_event_reasons.sw_power_cap")
+
+class ClockSampler:
+    """SM clocks and throttle reasons sampled during the timed region (NVML,
+    every 5 ms; nvidia-smi every 200 ms where NVML cannot be loaded)."""
+
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
     def __init__(self, local=0):
         vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
         ids = [x.strip() for x in vis.split(",") if x.strip()]
         self.index = ids[local] if local < len(ids) else str(local)
-        self.rows = []
+        self.rows = []  # (sm_mhz, max_mhz, set of active reasons)
         self._stop = threading.Event()
         self._t = None
+        self._nvml = None
+        try:
+            import pynvml as N
+            N.nvmlInit()
+            h = N.nvmlDeviceGetHandleByIndex(int(self.index)) if self.index.isdigit() else \
+                N.nvmlDeviceGetHandleByUUID(self.index)
+            self._nvml = (N, h)
+        except Exception:
+            self._nvml = None
+
+    def _sample_nvml(self):
+        N, h = self._nvml
+        sm = N.nvmlDeviceGetClockInfo(h, N.NVML_CLOCK_SM)
+        mx = N.nvmlDeviceGetMaxClockInfo(h, N.NVML_CLOCK_SM)
+        bits = N.nvmlDeviceGetCurrentClocksThrottleReasons(h)
+        masks = (0x8, 0x40, 0x20, 0x4)  # hw slowdown, hw thermal, sw thermal, sw power cap
+        return float(sm), float(mx), {n for n, m in zip(self.NAMES, masks) if bits & m}
+
+    def _sample_smi(self):
+        q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}", "--format=csv,noheader,nounits"],
+                             capture_output=True, text=True, timeout=5).stdout.strip()
+        r = [x.strip() for x in out.split(",")]
+        act = {n for n, x in zip(self.NAMES, r[2:]) if "Active" in x and "Not" not in x}
+        return float(r[0]), float(r[1]), act
 
     def _run(self):
+        period = 0.005 if self._nvml else 0.2
         while not self._stop.is_set():
             try:
-                out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
-                                     timeout=5).stdout.strip()
-                if out:
-                    self.rows.append([x.strip() for x in out.split(",")])
+                self.rows.append(self._sample_nvml() if self._nvml else self._sample_smi())
             except Exception:
                 pass
-            self._stop.wait(0.2)
+            self._stop.wait(period)
 
     def __enter__(self):
         self._t = threading.Thread(target=self._run, daemon=True)
@@ -91,17 +146,18 @@ class ClockSampler:
     def __exit__(self, *a):
         self._stop.set()
         self._t.join(timeout=10)
+        try:
+            self.rows.append(self._sample_nvml() if self._nvml else self._sample_smi())
+        except Exception:
+            pass
 
     def summary(self):
         if not self.rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
-        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 3 + i and "Active" in r[3 + i]
-                          and "Not" not in r[3 + i]})
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [r[0] for r in self.rows]
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(r[1] for r in self.rows),
+                "reasons": sorted(set().union(*(r[2] for r in self.rows))), "samples": len(self.rows),
+                "source": "nvml" if self._nvml else "nvidia-smi"}
 
 
 def dist_env():
@@ -125,55 +181,78 @@ def reduce_over_ranks(vals_sum, vals_max, world, backend):
     return a.cpu().tolist(), b.cpu().tolist()
 
 
-def oracle_sample(wl, batches, budget_s=20.0):
-    """The CPU oracle as it stands, single-threaded, on the first batches of the
-    same stream until about budget_s of CPU work: updates/s."""
-    from oracle.oracle import OracleGraph
-    o = OracleGraph(wl.n, wl.a, wl.b, wl.w, K=wl.K, T=wl.T, s=wl.s)
-    o.init_sparsifier(wl.a[wl.h_ids], wl.b[wl.h_ids])
-    done, t_total, steps, nb = 0, 0.0, 0, 0
+def stream_slices(batches, size):
+    """The batch stream cut into consecutive slices of `size` updates (each a
+    valid batch in stream order)."""
     for bt in batches:
-        t0 = time.perf_counter()
-        r = o.apply(bt.u, bt.v, bt.w, bt.op)
-        t_total += time.perf_counter() - t0
-        done += int((r["status"] == 0).sum())
-        steps += int(r["steps"].sum())
-        nb += 1
-        if t_total >= budget_s:
-            break
+        for lo in range(0, len(bt), size):
+            yield bt.u[lo:lo + size], bt.v[lo:lo + size], bt.w[lo:lo + size], bt.op[lo:lo + size]
+
+
+def oracle_baseline(wl, batches, budget_s=12.0, slice_size=1000):
+    """The CPU oracle on the stream from G(0): its walk phase on one host
+    thread, then on every host core (its OpenMP build, identical outputs),
+    each for about budget_s of work on consecutive slices of the stream.
+    Returns (single-thread dict, all-core dict)."""
+    from oracle.oracle import OracleGraph
+    o = OracleGraph(wl.n, wl.a, wl.b, wl.w, K=wl.K, T=wl.T, s=wl.s, threads=0)
+    cores = o.threads
+    o.init_sparsifier(wl.a[wl.h_ids], wl.b[wl.h_ids])
+    it = stream_slices(batches, slice_size)
+    out = []
+    for threads in (1, cores):
+        o._lib.orc_set_threads(threads)
+        done, steps, t_tot, nsl = 0, 0, 0.0, 0
+        for u, v, w, op in it:
+            t0 = time.perf_counter()
+            r = o.apply(u, v, w, op, prune_bounds=True)
+            t_tot += time.perf_counter() - t0
+            done += int((r["status"] == 0).sum())
+            steps += int(r["steps_lo"].sum())
+            nsl += 1
+            if t_tot >= budget_s:
+                break
+        out.append({"value": done / t_tot, "unit": "updates/s", "cores": threads, "kind": "oracle",
+                    "walk_steps_per_s": steps / t_tot, "seconds": t_tot,
+                    "sample": f"{nsl} consecutive slices of {slice_size} updates of the stream from G(0)"})
     o.close()
-    return done / t_total, steps / t_total, nb, t_total
+    return out[0], out[1]
 
 
 def run_reference(args):
-    """--impl reference: the CPU oracle on the same workload, bounded per step."""
+    """--impl reference: the CPU oracle, single-threaded, on the same workload;
+    each step a bounded sample (consecutive slices of the update stream)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    from paper_2505_02741_b300 import workloads as W
     from oracle.oracle import OracleGraph
-    wl, st = W.make_mesh3d(seed=0)
+    wl, st = make_workload(args.workload, args, 0)
+    n_ins, n_del = BATCH[args.workload]
+    sample = args.ref_sample
+    nb = (args.warmup + args.steps) * sample // (n_ins + n_del) + 1
+    batches = [st.next_batch(n_ins, n_del) for _ in range(nb)]
     o = OracleGraph(wl.n, wl.a, wl.b, wl.w, K=wl.K, T=wl.T, s=wl.s)
     o.init_sparsifier(wl.a[wl.h_ids], wl.b[wl.h_ids])
-    # each step: a bounded sample (the first 2,000 updates of a 20k batch) so the run stays short
-    sample = 2000
     times, units = [], 0
+    it = stream_slices(batches, sample)
     for i in range(args.warmup + args.steps):
-        bt = st.next_batch(N_INS, N_DEL)
+        u, v, w, op = next(it)
         t0 = time.perf_counter()
-        r = o.apply(bt.u[:sample], bt.v[:sample], bt.w[:sample], bt.op[:sample])
+        r = o.apply(u, v, w, op, prune_bounds=True)
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(dt)
             units += int((r["status"] == 0).sum())
+    o.close()
     value = units / sum(times)
+    samp = f"{args.steps} consecutive slices of {sample} updates of the stream, one host thread"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": wl.name, "n": wl.n, "m": wl.m, "batch": sample,
                                             "K": wl.K, "T": wl.T, "s": wl.s},
-            "cpu_baseline": {"value": value, "unit": "updates/s", "cores": 1, "kind": "oracle",
-                             "sample": f"first {sample} updates of each 20k-update batch, single thread"},
+            "cpu_baseline": {"value": value, "unit": "updates/s", "cores": 1, "kind": "oracle", "sample": samp,
+                             **host_cpu()},
             "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -302,22 +381,25 @@ def run_serve(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=8)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--per-update-steps", type=int, default=2)
-    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work per CPU baseline")
+    ap.add_argument("--ref-sample", type=int, default=1000, help="reference arm: updates per step")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-full-walks", action="store_true", help="skip the unpruned-walk context line")
+    ap.add_argument("--no-full-walks", action="store_true", help="skip the unpruned-walk context line (mesh)")
     ap.add_argument("--walk-shape", default="", help="fixed walk launch shape 'block,ilp' (skips the autotuner)")
-    ap.add_argument("--workload", default="mesh", choices=["mesh", "fea", "rmat", "serve"],
-                    help="mesh (default line), fea, rmat, or serve (several graphs resident, Poisson arrivals)")
+    ap.add_argument("--workload", default="rmat", choices=["rmat", "mesh", "fea", "serve"],
+                    help="rmat (default line), mesh, fea, or serve (several graphs resident, Poisson arrivals)")
     ap.add_argument("--rmat-scale", type=int, default=22, help="rmat: log2 of the vertex count")
     ap.add_argument("--rmat-edges", type=int, default=64_000_000, help="rmat: distinct undirected edges")
     ap.add_argument("--load", type=float, default=0.6, help="serve: offered load as a fraction of capacity")
     ap.add_argument("--requests", type=int, default=1000, help="serve: requests in the measured stream")
     args = ap.parse_args()
     if args.impl == "reference":
+        if args.workload == "serve":
+            args.workload = "mesh"
         return run_reference(args)
     if args.warmup < 3:
         raise SystemExit("at least 3 warm-up steps")
@@ -326,7 +408,6 @@ def main():
 
     import torch
     from paper_2505_02741_b300 import dygrass as D
-    from paper_2505_02741_b300 import workloads as W
 
     rank, world, local = dist_env()
     backend = None
@@ -339,15 +420,8 @@ def main():
     dev = local
 
     # workload (each rank an independent replica: weak scaling, no data-path collective)
-    n_ins, n_del = N_INS, N_DEL
-    if args.workload == "fea":  # one batch of 100k mixed updates per step
-        wl, st = W.make_fea(seed=rank)
-        n_ins, n_del = 50_000, 50_000
-    elif args.workload == "rmat":  # 50k updates per step, 60 % insertions
-        wl, st = W.make_rmat(scale=args.rmat_scale, n_edges=args.rmat_edges, seed=rank)
-        n_ins, n_del = 30_000, 20_000
-    else:
-        wl, st = W.make_mesh3d(seed=rank)
+    wl, st = make_workload(args.workload, args, rank)
+    n_ins, n_del = BATCH[args.workload]
     n_batches = args.warmup + args.steps + args.steps + args.per_update_steps
     batches = [st.next_batch(n_ins, n_del) for _ in range(n_batches)]
 
@@ -396,6 +470,8 @@ def main():
             valid += s["valid"]
             launches += s["launches"]
         torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_total = sum(step_ms) / 1e3
     (sum_valid, sum_steps), (t_max, walk_max) = reduce_over_ranks([valid, steps_done], [t_total, sum(walk_ms) / 1e3],
@@ -403,7 +479,7 @@ def main():
     value = sum_valid / t_max
     walk_steps_per_s = sum_steps / walk_max
 
-    # ---- e2e: host buffers through dg_apply_updates --------------------------
+    # ---- e2e: pinned host buffers through dg_apply_updates -------------------
     # the step's records wait in pinned host memory; the timed call copies them to
     # the device and the results back (dg_apply_updates copies pinned arrays directly)
     nmax = max(len(b) for b in batches)
@@ -427,10 +503,7 @@ def main():
            "d2h_bytes_per_step": 32 * e2e_nu // args.steps + 96, "p50_ms": 1e3 * float(np.percentile(e2e_t, 50)),
            "p99_ms": 1e3 * float(np.percentile(e2e_t, 99)), "host_buffers": "pinned"}
 
-    # ---- context: the same walk kernel without deletion pruning ---------------
-    # (every deletion walker runs to its own stop, as Algorithm 1 walks them):
-    # a fresh copy of the graph takes the stream's first batches; the walk is
-    # then bandwidth-bound rather than bound by the chain of the longest walks
+    # ---- context (mesh): the same walk kernel without deletion pruning -------
     full = None
     if args.workload == "mesh" and not args.no_full_walks:
         ctx_f = D.Context(device=dev, K=wl.K, T=wl.T, s=wl.s, del_prune=False)
@@ -446,11 +519,8 @@ def main():
                 f_ms.append(s["walk_ms"])
                 f_steps += s["steps"]
         ctx_f.close()
-        f_bytes = BYTES_PER_STEP * f_steps / 3
-        f_ach = f_bytes / (sum(f_ms) / 3 / 1e3) / 1e9
         full = {"del_prune": False, "walk_steps_per_batch": f_steps / 3, "walk_ms": sum(f_ms) / 3,
-                "walk_steps_per_s": f_steps / (sum(f_ms) / 1e3), "achieved_gbs": f_ach,
-                "frac": f_ach / measured_peaks()[0], "batches": "stream batches 4-6 on a fresh copy"}
+                "walk_steps_per_s": f_steps / (sum(f_ms) / 1e3), "batches": "stream batches 4-6 on a fresh copy"}
 
     # ---- the one-launch-per-update form on a copy at the same state ----------
     pu = None
@@ -462,6 +532,7 @@ def main():
         gp = ctx_pu.load_graph(wl.n, ga, gb, gw)
         gp.init_sparsifier(ha, hb)
         gp.next_update_id = nid
+        del ga, gb, gw, ha, hb
         pu_t, pu_valid, same = [], 0, True
         for k in range(args.per_update_steps):
             ups, d_ups = dev_batches[bi]
@@ -478,12 +549,7 @@ def main():
             # identical outputs: the batched form on the main graph, same batch
             g.apply_device(d_ups.data_ptr(), len(ups), d_res.data_ptr(), stream.cuda_stream)
             torch.cuda.synchronize()
-            # every field but steps (pruned deletion walkers stop at scheduling-dependent steps)
-            r0 = res_pu.view(D.RESULT_DTYPE)
-            r1 = d_res[: len(ups) * 32].cpu().numpy().view(D.RESULT_DTYPE)
-            same &= all(np.array_equal(np.ascontiguousarray(r0[f]).view(np.uint8),
-                                       np.ascontiguousarray(r1[f]).view(np.uint8))
-                        for f in D.RESULT_DTYPE.names if f != "steps")
+            same &= res_pu.tobytes() == d_res[: len(ups) * 32].cpu().numpy().tobytes()  # every byte
             bi += 1
         pu = {"updates_per_s": pu_valid / (sum(pu_t) / 1e3), "p50_ms": float(np.percentile(pu_t, 50)),
               "p99_ms": float(np.percentile(pu_t, 99)), "steps": args.per_update_steps,
@@ -493,20 +559,23 @@ def main():
     # ---- roofline of the walk kernel ----------------------------------------
     peak, peak_kind = measured_peaks()
     avg_walk_s = sum(walk_ms) / 1e3 / args.steps
-    bytes_per_launch = BYTES_PER_STEP * steps_done / args.steps
-    achieved = bytes_per_launch / avg_walk_s / 1e9
+    steps_per_launch = steps_done / args.steps
+    achieved = ALG_BYTES_PER_STEP * steps_per_launch / avg_walk_s / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": WALK_TRAFFIC_BYTES if args.workload == "mesh" else None,
-            "traffic_source": WALK_TRAFFIC_SOURCE if args.workload == "mesh" else None, "kernel": "k_walk_batched",
-            "bytes_per_step": BYTES_PER_STEP, "peak_source": peak_kind,
-            "algorithmic_bytes_per_launch": bytes_per_launch}
+            "traffic": WALK_TRAFFIC_BYTES if args.workload == "rmat" else None,
+            "traffic_source": WALK_TRAFFIC_SOURCE if args.workload == "rmat" else "not captured for this workload",
+            "kernel": "k_walk_batched", "bytes_per_step": ALG_BYTES_PER_STEP, "peak_source": peak_kind,
+            "steps_per_launch": steps_per_launch,
+            "algorithmic_bytes_per_launch": ALG_BYTES_PER_STEP * steps_per_launch,
+            "gather": {"bytes_per_step": SECTOR_BYTES_PER_STEP, "walk_steps_per_s": steps_per_launch / avg_walk_s,
+                       "peak_steps_per_s": peak * 1e9 / SECTOR_BYTES_PER_STEP,
+                       "frac": steps_per_launch / avg_walk_s / (peak * 1e9 / SECTOR_BYTES_PER_STEP)}}
 
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and not args.no_cpu:
-        cpu_v, cpu_steps, nb, tt = oracle_sample(wl, batches[: 2], args.cpu_budget)
-        cpu = {"value": cpu_v, "unit": "updates/s", "cores": 1, "kind": "oracle",
-               "sample": f"{nb} full batch(es) of 20k updates from the start of the stream, {tt:.1f} s",
-               "walk_steps_per_s": cpu_steps}
+        cpu, cpu_all = oracle_baseline(wl, batches, args.cpu_budget)
+        cpu.update(host_cpu())
+        cpu["all_cores"] = cpu_all
 
     if rank == 0:
         clocks = clk.summary()
@@ -524,7 +593,7 @@ def main():
                                        ("mutate_ms", "walk_ms", "reduce_ms", "emit_ms", "commit_ms", "batch_ms")},
                           "walk_shape": {"block": phases[-1]["walk_block"], "ilp": phases[-1]["walk_ilp"],
                                          "blocks_per_sm": phases[-1]["walk_blocks_per_sm"],
-                                         "cut": phases[-1]["walk_cut"], "autotuned": True},
+                                         "refill": phases[-1]["walk_refill"], "autotuned": not args.walk_shape},
                           "launches": launches / args.steps, "cuda_graph": bool(phases[-1]["graph_replayed"])},
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
             "per_update_form": pu,

@@ -91,13 +91,15 @@ typedef struct {
     int32_t ins_early_exit; /* 1: an insertion's walkers stop at the first step index at which
                                any of them reaches v (decisions unchanged; R~ and step counts
                                refer to the truncated walks); 0: every walker runs to its own stop */
-    int32_t del_prune;      /* 1: a deletion's walker stops once its resistance exceeds that of a
-                               walker of the same update that already reached v: it can no longer
-                               give the minimum of Eq. 12, so hit, best_walker, r_est and the
-                               recovered edges are unchanged; nhits then counts the walkers at the
-                               minimum resistance and steps the steps actually taken (which depend
-                               on scheduling, between the exact pruned and unpruned counts);
-                               0: every deletion walker runs to its own stop */
+    int32_t del_prune;      /* 1: a deletion's walker may stop once its resistance exceeds that of
+                               a walker of the same update that already reached v: it can no
+                               longer give the minimum of Eq. 12, so hit, best_walker, r_est and
+                               the recovered edges are unchanged.  The counts reported follow the
+                               exact rule -- every walker of a deletion with a hit stops at its
+                               first step whose resistance exceeds R~ -- so they do not depend on
+                               when a walker was actually cut: steps sums those stops and nhits
+                               counts the walkers at R~.  0: every deletion walker runs to its own
+                               stop (steps and nhits of the full walks) */
     int32_t walk_mode;      /* DG_WALK_BATCHED or DG_WALK_PER_UPDATE */
     double slack;           /* per-vertex capacity = deg + max(2, ceil(deg*(slack-1))); >= 1 */
     double overflow_frac;   /* pool headroom for relocated lists, fraction of the initial pool */
@@ -129,10 +131,11 @@ typedef struct {
     uint8_t accepted;    /* insertion kept for H (no walker reached v); committed if the edge is in G_b */
     uint8_t fallback;    /* deletion walked but no walker reached v: local fallback edges recovered */
     int32_t nhits;       /* walkers that reached v (after the early-exit cut for insertions; with
-                            del_prune, for deletions: walkers at the minimum resistance) */
+                            del_prune, for deletions: the walkers at the minimum resistance R~) */
     int32_t best_walker; /* walker index of R~ (lowest index among equal resistances), -1 if none */
     int32_t nrecovered;  /* distinct edges this deletion returned to H (path or fallback) */
-    int32_t steps;       /* walk steps taken by this update's walkers (after the cut / pruning) */
+    int32_t steps;       /* walk steps of this update's walkers under the early-exit cut
+                            (insertions) or the exact pruning rule of del_prune (deletions) */
     double r_est;        /* R~ = minimum path resistance over hitting walkers (Eq. 12); +inf if none */
 } dg_update_result;
 
@@ -276,6 +279,18 @@ dg_status dg_set_walk_shape(dg_ctx* ctx, int32_t graph_id, int32_t block, int32_
 dg_status dg_set_walk_refill(dg_ctx* ctx, int32_t graph_id, int32_t refill_min);
 
 /*
+ * Debug: the number of times the finalizing warps of the batched walk poll
+ * for the next completed update before they give up (polls >= 0; < 0 restores
+ * the default of 2^22 polls, about half a second).  When a wait gives up, the
+ * walk kernel records the failure and returns normally; the batch call then
+ * returns DG_E_TIMEOUT and the graph's state is unspecified (unload it), while
+ * the CUDA context stays usable.  With polls = 0 every batch with a walked
+ * update gives up, which is how the tests exercise that path.  Applies to
+ * later batches of every graph of the context.
+ */
+dg_status dg_debug_set_wait_limit(dg_ctx* ctx, int64_t polls);
+
+/*
  * Serving (continuous batching over resident graphs).  dg_submit_updates
  * copies the request and queues it; requests on one graph run in submission
  * order, one at a time; requests on different graphs run concurrently on
@@ -301,12 +316,17 @@ dg_status dg_wait(dg_ctx* ctx, uint64_t ticket, int32_t timeout_ms, double* late
  *
  * It runs the s walkers of each query on a graph that is already resident
  * (loaded earlier with dg_load_graph) and writes one estimate per query; it
- * changes neither G nor H.  kind DG_OP_INSERT walks H from u toward v with the
- * distortion threshold K and weight w; kind DG_OP_DELETE walks G from u toward
- * v without K.  id is the update sequence number the Philox counter uses, so
- * a query with the id, endpoints and weight of an insertion that
+ * changes neither G nor H.  kind DG_OP_INSERT walks the current H from u
+ * toward v with the distortion threshold K and weight w; kind DG_OP_DELETE
+ * walks the current G from u toward v without K and without pruning (every
+ * walker runs to its own stop; if (u, v) is still an edge of G a walker may
+ * take it directly).  id is the update sequence number the Philox counter
+ * uses, so a query with the id, endpoints and weight of an insertion that
  * dg_apply_updates is about to walk on the same H gets the same hit, nhits,
- * best_walker, steps and r_est.
+ * best_walker, steps and r_est; a DELETE query on the G a deletion batch left
+ * behind (that batch's G_b) with the id of one of its deletions gets that
+ * deletion's hit, best_walker and r_est, and the nhits and steps it has with
+ * del_prune = 0.
  *
  * d_queries and d_out are device pointers owned by the caller (nq records
  * each).  The walkers' scratch is a static device array inside the library
@@ -321,7 +341,13 @@ dg_status dg_wait(dg_ctx* ctx, uint64_t ticket, int32_t timeout_ms, double* late
  * first call before any stream capture.  All calls share the one array, which
  * keeps the last call's contents: calls whose work overlaps on the GPU (other
  * streams, other contexts on the same device) race and must be serialized by
- * the caller.
+ * the caller.  Outside a stream capture the call is ordered against changes
+ * of the same graph: its kernels wait for the last dg_apply_updates /
+ * dg_submit_updates batch, dg_init_sparsifier or dg_compact of that graph,
+ * and the next such call waits for its kernels.  While cuda_stream is being
+ * captured that ordering is the caller's: no such change of the graph may
+ * run between the capture's launch and the completion of its kernels.
+ * nq == 0 returns DG_OK and launches nothing.
  */
 #define DG_NOALLOC_MAX_QUERIES 4096
 #define DG_NOALLOC_MAX_WALKERS 131072

@@ -381,23 +381,41 @@ dg_status dg_get_walker_records(dg_ctx* ctx, int32_t gid, int64_t cap, int32_t* 
         const int64_t nu = g.stats.updates;
         if (cap < nu) throw Error(DG_E_INVALID, "cap smaller than the last batch");
         const size_t rows = (size_t)nu * c.cfg.s;
-        if (reason)
+        const int s = c.cfg.s;
+        // walked updates of the batch (task order): rows of the others read 0
+        const size_t W = g.hs.counts[0];
+        std::vector<uint32_t> idx(W);
+        if (W) DG_CUDA(cudaMemcpy(idx.data(), g.ws.t_idx.p, W * 4, cudaMemcpyDeviceToHost));
+        std::vector<uint8_t> walked((size_t)nu, 0);
+        for (size_t j = 0; j < W; ++j) walked[idx[j]] = 1;
+        auto blank_unwalked = [&](int32_t* a) {
+            for (int64_t i = 0; i < nu; ++i)
+                if (!walked[(size_t)i]) std::fill(a + (size_t)i * s, a + (size_t)(i + 1) * s, 0);
+        };
+        if (reason) {
             DG_CUDA(cudaMemcpy(reason, g.ws.dbg_reason.p, rows * 4, cudaMemcpyDeviceToHost));
-        if (steps) DG_CUDA(cudaMemcpy(steps, g.ws.dbg_steps.p, rows * 4, cudaMemcpyDeviceToHost));
+            blank_unwalked(reason);
+        }
+        if (steps) {
+            DG_CUDA(cudaMemcpy(steps, g.ws.dbg_steps.p, rows * 4, cudaMemcpyDeviceToHost));
+            blank_unwalked(steps);
+        }
         if (paths) {
             if (!g.ws.dbg_paths.p) throw Error(DG_E_STATE, "paths are kept only when T <= 256");
-            // paths are stored per walked update (task order); re-order by update index
-            std::vector<uint32_t> idx(g.hs.counts[0]);
-            const size_t W = g.hs.counts[0];
-            if (W) DG_CUDA(cudaMemcpy(idx.data(), g.ws.t_idx.p, W * 4, cudaMemcpyDeviceToHost));
+            // paths are stored per walked update (task order); re-order by update index.
+            // A walker's row holds the vertices it reached; positions past its
+            // reported step count (after an early-exit or pruning cut) read -1.
             const size_t row = (size_t)c.cfg.T + 1;
-            std::vector<int32_t> buf(W * c.cfg.s * row);
+            std::vector<int32_t> buf(W * s * row);
             if (W) DG_CUDA(cudaMemcpy(buf.data(), g.ws.dbg_paths.p, buf.size() * 4, cudaMemcpyDeviceToHost));
+            std::vector<int32_t> wsteps(rows);
+            if (rows) DG_CUDA(cudaMemcpy(wsteps.data(), g.ws.dbg_steps.p, rows * 4, cudaMemcpyDeviceToHost));
             std::fill(paths, paths + rows * row, -1);
             for (size_t j = 0; j < W; ++j)
-                for (int k = 0; k < c.cfg.s; ++k) {
-                    const size_t src = (j * c.cfg.s + k) * row, dst = ((size_t)idx[j] * c.cfg.s + k) * row;
-                    std::copy(buf.begin() + src, buf.begin() + src + row, paths + dst);
+                for (int k = 0; k < s; ++k) {
+                    const size_t src = (j * s + k) * row, dst = ((size_t)idx[j] * s + k) * row;
+                    const size_t len = std::min<size_t>(row, (size_t)wsteps[(size_t)idx[j] * s + k] + 1);
+                    std::copy(buf.begin() + src, buf.begin() + src + len, paths + dst);
                 }
         }
     });
@@ -472,6 +490,18 @@ dg_status dg_set_walk_refill(dg_ctx* ctx, int32_t gid, int32_t refill_min) {
         g.shape.refill = refill_min;
         g.tuned = true;
         ++g.layout_gen;
+    });
+}
+
+dg_status dg_debug_set_wait_limit(dg_ctx* ctx, int64_t polls) {
+    return guarded(ctx, [&]() {
+        Ctx& c = C(ctx);
+        std::lock_guard<std::mutex> lk(c.mu);
+        c.fin_wait_polls = polls < 0 ? -1 : polls;
+        for (auto& kv : c.graphs) {  // captured steps hold the limit: capture them again
+            std::lock_guard<std::mutex> gl(kv.second->mu);
+            ++kv.second->layout_gen;
+        }
     });
 }
 

@@ -646,8 +646,21 @@ void graph_load(Ctx& c, DGraph& g, int32_t n, int64_t m, const int32_t* u, const
     g.next_id = 0;
     for (int i = 0; i < 7; ++i) DG_CUDA(cudaEventCreate(&g.ev[i]));
     for (int i = 0; i < 7; ++i) DG_CUDA(cudaEventCreateWithFlags(&g.fk[i], cudaEventDisableTiming));
+    DG_CUDA(cudaEventCreateWithFlags(&g.ev_mut, cudaEventDisableTiming));
+    DG_CUDA(cudaEventCreateWithFlags(&g.ev_est, cudaEventDisableTiming));
     DG_CUDA(cudaStreamCreateWithFlags(&g.side, cudaStreamNonBlocking));
     wait_stream(c, st);
+    graph_mark_mutation(g, st);
+}
+
+// Work that changes G or H first waits for the walk estimates already issued
+// on this graph (a wait on an event never recorded returns at once).
+void graph_wait_estimates(DGraph& g, cudaStream_t st) {
+    if (g.ev_est) DG_CUDA(cudaStreamWaitEvent(st, g.ev_est, 0));
+}
+
+void graph_mark_mutation(DGraph& g, cudaStream_t st) {
+    if (g.ev_mut) DG_CUDA(cudaEventRecord(g.ev_mut, st));
 }
 
 void graph_init_h(Ctx& c, DGraph& g, int64_t mh, const int32_t* u, const int32_t* v) {
@@ -720,6 +733,7 @@ void graph_init_h(Ctx& c, DGraph& g, int64_t mh, const int32_t* u, const int32_t
         DG_CUDA(cudaMemcpyAsync(&uniq, cnt.p, 4, cudaMemcpyDeviceToHost, st));
         wait_stream(c, st);
     }
+    graph_wait_estimates(g, st);
     csr_release(g.H, a, st);
     g.H.slack = (float)c.cfg.slack;
     g.H.overflow = c.cfg.overflow;
@@ -731,6 +745,7 @@ void graph_init_h(Ctx& c, DGraph& g, int64_t mh, const int32_t* u, const int32_t
     if (herr) throw Error(DG_E_CUDA, "internal error while building the sparsifier");
     g.has_h = true;
     ++g.layout_gen;
+    graph_mark_mutation(g, st);
 }
 
 void graph_export(Ctx& c, DGraph& g, bool which_h, int64_t cap, int32_t* u, int32_t* v, double* w,
@@ -758,13 +773,16 @@ void graph_export(Ctx& c, DGraph& g, bool which_h, int64_t cap, int32_t* u, int3
 }
 
 void graph_compact(Ctx& c, DGraph& g, cudaStream_t st) {
+    graph_wait_estimates(g, st);
     csr_compact(g.G, c.alloc, 0, st);
     csr_compact(g.H, c.alloc, 0, st);
     ++g.layout_gen;
+    graph_mark_mutation(g, st);
 }
 
 void graph_release(Ctx& c, DGraph& g) {
     cudaStream_t st = c.stream;
+    if (g.ev_est) cudaEventSynchronize(g.ev_est);
     cudaStreamSynchronize(st);
     if (g.stream) cudaStreamSynchronize(g.stream);
     for (auto& kv : g.steps)
@@ -787,6 +805,9 @@ void graph_release(Ctx& c, DGraph& g) {
         if (g.ev[i]) cudaEventDestroy(g.ev[i]);
     for (int i = 0; i < 7; ++i)
         if (g.fk[i]) cudaEventDestroy(g.fk[i]);
+    if (g.ev_mut) cudaEventDestroy(g.ev_mut);
+    if (g.ev_est) cudaEventDestroy(g.ev_est);
+    g.ev_mut = g.ev_est = nullptr;
     if (g.side) {
         cudaStreamSynchronize(g.side);
         cudaStreamDestroy(g.side);
@@ -884,6 +905,7 @@ static FinArgs fin_of(Ctx& c, BatchWS& w, bool on) {
     f.cp_shift = walk_cp_shift((uint32_t)c.cfg.T);
     f.ncp = walk_ncp((uint32_t)c.cfg.T);
     f.on = on ? 1u : 0u;
+    f.spin_limit = c.fin_wait_polls < 0 ? FIN_SPIN_LIMIT : (uint32_t)std::min<int64_t>(c.fin_wait_polls, FIN_SPIN_LIMIT);
     return f;
 }
 
@@ -1097,8 +1119,9 @@ static bool enqueue_walks(Ctx& c, DGraph& g, cudaStream_t st, int64_t per_update
     }
     DG_CUDA(record_event(g.ev[1], st));
     if (!fused)
-        launch_walk_reduce(tasks, wp, wr, w.res.p, w.best.p, w.ctr.p, c.cfg.record ? w.dbg_reason.p : nullptr,
-                           c.cfg.record ? w.dbg_steps.p : nullptr, w.b_max, w.err.p, st);
+        launch_walk_reduce(g.G.view(), tasks, wp, wr, w.hdr.p, w.res.p, w.best.p, w.ctr.p,
+                           c.cfg.record ? w.dbg_reason.p : nullptr, c.cfg.record ? w.dbg_steps.p : nullptr,
+                           w.b_max, w.err.p, st);
     DG_CUDA(record_event(g.ev[5], st));
     return fused;
 }
@@ -1318,6 +1341,7 @@ void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_updat
     const uint32_t nu = (uint32_t)nu64;
     const uint64_t l0 = g_launches;
     const uint32_t bucket = bucket_of(nu);
+    graph_wait_estimates(g, st);
     ensure_ws(c, g, bucket, st);
     ensure_headroom(c, g, nu, st);
     BatchWS& w = g.ws;
@@ -1444,6 +1468,7 @@ void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_updat
         finish_eager(whole);
         replayed = false;
     }
+    graph_mark_mutation(g, st);
     if (res && !direct) std::memcpy(res, g.hs.res, sizeof(dg_update_result) * nu);
     g.G.host_top = g.hs.tops[0];
     g.H.host_top = g.hs.tops[1];

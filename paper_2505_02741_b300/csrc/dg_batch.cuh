@@ -118,6 +118,12 @@ struct DGraph {
     cudaStream_t side = nullptr;
     cudaEvent_t fk[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // fork / join of the two streams
     dg_batch_stats stats{};
+    // ordering against dg_walk_estimate_noalloc (which runs on the caller's
+    // stream and returns at once): ev_mut is recorded after every change of G
+    // or H and the estimate's stream waits on it; ev_est is recorded after the
+    // estimate's kernels and every change of G or H waits on it
+    cudaEvent_t ev_mut = nullptr;
+    cudaEvent_t ev_est = nullptr;
     std::mutex mu;
     uint64_t bytes() const { return G.bytes() + H.bytes() + touched.bytes() + touched_h.bytes() + ws.bytes(); }
 };
@@ -134,5 +140,8 @@ void graph_release_ws(Ctx& c, DGraph& g, cudaStream_t st);  // batch workspace o
 void graph_compact(Ctx& c, DGraph& g, cudaStream_t st);
 void graph_export(Ctx& c, DGraph& g, bool which_h, int64_t cap, int32_t* u, int32_t* v, double* w,
                   int64_t* count, cudaStream_t st);
+// the two halves of the ordering against walk estimates (see DGraph::ev_est)
+void graph_wait_estimates(DGraph& g, cudaStream_t st);
+void graph_mark_mutation(DGraph& g, cudaStream_t st);
 
 }  // namespace dg

@@ -33,6 +33,7 @@ struct Ctx {
     std::map<int32_t, std::unique_ptr<DGraph>> graphs;
     int32_t next_gid = 1;
     std::atomic<uint64_t> launches{0};
+    int64_t fin_wait_polls = -1;  // finalize-queue poll limit of the walk (< 0: FIN_SPIN_LIMIT)
 
     // serving
     std::mutex smu;

@@ -228,6 +228,15 @@ extern "C" dg_status dg_walk_estimate_noalloc(dg_ctx* ctx, int32_t graph_id, int
         a.kstar = reinterpret_cast<uint32_t*>(base + NA_OFF_KSTAR);
         a.next = reinterpret_cast<unsigned long long*>(base + NA_OFF_NEXT);
         cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : c.stream;
+        // Outside a stream capture the call orders itself against changes of
+        // this graph: its kernels wait for the last change of G or H, and the
+        // next change waits for its kernels (events created with the graph).
+        // During a capture the caller orders it (no event recorded outside the
+        // capture is waited on).
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        DG_CUDA(cudaStreamIsCapturing(st, &cap));
+        const bool ordered = cap == cudaStreamCaptureStatusNone;
+        if (ordered) DG_CUDA(cudaStreamWaitEvent(st, g.ev_mut, 0));
         const int sms = device_sms();
         int occ = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_na_walk, 256, 0);
@@ -239,6 +248,7 @@ extern "C" dg_status dg_walk_estimate_noalloc(dg_ctx* ctx, int32_t graph_id, int
         k_na_walk<<<walk_blocks, 256, 0, st>>>(a);
         k_na_reduce<<<red_blocks, 256, 0, st>>>(a);
         DG_CHECK_LAUNCH();
+        if (ordered) DG_CUDA(cudaEventRecord(g.ev_est, st));
         c.launches += 3;
         return DG_OK;
     } catch (const Error& e) {

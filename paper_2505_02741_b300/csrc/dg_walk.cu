@@ -40,7 +40,6 @@ int device_sms() {
 }
 
 constexpr uint32_t NONE = 0xFFFFFFFFu;
-constexpr uint32_t FIN_SPIN_LIMIT = 1u << 22;  // polls of the finalize queue (about 0.5 s) before ERR_SPIN
 
 __device__ __forceinline__ bool walk_aborted(const uint32_t* d_err) { return (*d_err & ABORT_MASK) != 0u; }
 
@@ -125,12 +124,69 @@ __device__ __forceinline__ void add_totals(BatchCounters* ctr, const UpdTotals& 
     if (u.rec) atomicAdd(&ctr->recovered, u.rec);
 }
 
+// First step of deletion walker k of walked update j whose resistance exceeds
+// rbar, the update's minimum (the walker's recorded resistance is above it, so
+// that step exists): the exact pruned step count, whatever moment the walker
+// itself was cut at.  The partial sums are formed again in walk order, each
+// addition rounded on its own, from the entries the walker took (step records,
+// pe non-null) or from its Philox counters replayed on G_b; both give the
+// walker's own sums bit for bit.  0 and ERR_INTERNAL if the sums never pass
+// rbar (records inconsistent with the walk).
+__device__ uint32_t del_cross_step(uint32_t j, uint32_t k, uint32_t steps, double rbar, const CSRView& G,
+                                   const WalkTasks& t, const WalkParams& p, const uint32_t* pe, uint64_t id0,
+                                   uint32_t* d_err) {
+    double R = 0.0;
+    if (pe) {
+        constexpr uint32_t U = 4;  // entry loads in flight per round
+        const size_t base = (size_t)j * p.T * p.s + k;
+        for (uint32_t s0 = 0; s0 < steps; s0 += U) {
+            uint32_t e[U];
+            double r[U];
+#pragma unroll
+            for (uint32_t q = 0; q < U; ++q) e[q] = s0 + q < steps ? __ldcg(&pe[base + (size_t)(s0 + q) * p.s]) : 0u;
+#pragma unroll
+            for (uint32_t q = 0; q < U; ++q) r[q] = (s0 + q < steps && (uint64_t)e[q] < G.pool_cap) ? G.pool[e[q]].r : 0.0;
+#pragma unroll
+            for (uint32_t q = 0; q < U; ++q) {
+                if (s0 + q >= steps) break;
+                R = __dadd_rn(R, r[q]);
+                if (R > rbar) return s0 + q + 1;
+            }
+        }
+    } else {
+        const uint64_t id = id0 + t.idx[j];
+        const uint32_t ulo = (uint32_t)id, uhi = (uint32_t)(id >> 32);
+        const uint32_t u = t.u[j];
+        uint32_t cv = u, off = G.off[u], deg = G.deg[u], prev = NONE;
+        bool pid = false;
+        for (uint32_t s = 0; s < steps; ++s) {
+            const uint32_t x = philox_word0(s, k, ulo, uhi, p.key0, p.key1);
+            uint4 h;
+            double2 tl;
+            if (nb_step(G, x, cv, off, deg, prev, pid, h, tl) <= 0) break;
+            R = __dadd_rn(R, tl.x);
+            if (R > rbar) return s + 1;
+        }
+    }
+    atomicOr(d_err, (uint32_t)ERR_INTERNAL);
+    return 0;
+}
+
 // Eq. 12 and the cut readings over the s records of walked update j, one
 // warp.  Lane 0 writes the update's result and best[j] and adds to tot; every
 // lane gets the argmin walker (-1 if none) and the number of hits.
+//
+// Deletion pruning (del_prune): a walker stops once its resistance is above a
+// hit of its update, at a step that depends on when that hit became visible.
+// The counts reported are those of the exact rule instead -- every walker
+// stops at its first step whose resistance exceeds R~ (del_cross_step) -- so
+// steps, nhits (the walkers at R~) and the debug records do not depend on
+// scheduling; hit, R~, the argmin walker and the recovered path are the same
+// with or without pruning.
 __device__ int reduce_update(uint32_t j, int lane, const WalkTasks& t, const WalkParams& p, const WalkRecs& r,
                              dg_update_result* res, int32_t* best, int32_t* dbg_reason, int32_t* dbg_steps,
-                             UpdTotals& tot, uint32_t& nh_out) {
+                             UpdTotals& tot, uint32_t& nh_out, const CSRView& G, const uint32_t* pe, uint64_t id0,
+                             uint32_t* d_err) {
     const bool ins = t.kind[j] == WALK_INS;
     const bool ee = ins && p.early_exit;
     const uint32_t i = t.idx[j];
@@ -142,17 +198,13 @@ __device__ int reduce_update(uint32_t j, int lane, const WalkTasks& t, const Wal
         if ((m >> 16) == R_HIT) ks = min(ks, m & 0xFFFFu);
     }
     for (int o = 16; o > 0; o >>= 1) ks = min(ks, __shfl_xor_sync(0xffffffffu, ks, o));
-    uint32_t nh = 0, tsum = 0, nmin = 0;  // nmin: hits at the lane's minimum bR
+    uint32_t nh = 0, nmin = 0;  // nmin: hits at the lane's minimum bR
     double bR = INFINITY;
     int bk = -1;
     for (uint32_t k = lane; k < p.s; k += 32) {
         const uint32_t m = __ldcg(&meta[k]);
         uint32_t st = m & 0xFFFFu, rs = m >> 16;
-        if (ee && ks != NONE && st > ks) {
-            st = ks;
-            rs = R_CUT;
-        }
-        tsum += st;
+        if (ee && ks != NONE && st > ks) rs = R_CUT;
         if (rs == R_HIT) {
             ++nh;
             const double R = __ldcg(&Rr[k]);
@@ -167,7 +219,6 @@ __device__ int reduce_update(uint32_t j, int lane, const WalkTasks& t, const Wal
     }
     for (int o = 16; o > 0; o >>= 1) {
         nh += __shfl_xor_sync(0xffffffffu, nh, o);
-        tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
         const double oR = __shfl_xor_sync(0xffffffffu, bR, o);
         const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
         const uint32_t on = __shfl_xor_sync(0xffffffffu, nmin, o);
@@ -180,23 +231,29 @@ __device__ int reduce_update(uint32_t j, int lane, const WalkTasks& t, const Wal
             nmin += on;
         }
     }
-    // pruned deletions: the walkers at the minimum are never cut, a hit above it
-    // may or may not have been (scheduling); count and record only the minimum
-    const bool prune = !ins && p.del_prune;
+    // pruned deletions with a hit: walkers whose resistance ends above R~ are
+    // counted up to their first step above it (hits above R~ included)
+    const bool prune = !ins && p.del_prune && bk >= 0;
     if (prune) nh = nmin;
-    if (dbg_reason) {
-        for (uint32_t k = lane; k < p.s; k += 32) {
-            const uint32_t m = __ldcg(&meta[k]);
-            uint32_t st = m & 0xFFFFu, rs = m >> 16;
-            if (ee && ks != NONE && st > ks) {
-                st = ks;
-                rs = R_CUT;
-            }
-            if (prune && rs == R_HIT && __ldcg(&Rr[k]) != bR) rs = R_CUT;
+    uint32_t tsum = 0;
+    for (uint32_t k = lane; k < p.s; k += 32) {
+        const uint32_t m = __ldcg(&meta[k]);
+        uint32_t st = m & 0xFFFFu, rs = m >> 16;
+        if (ee && ks != NONE && st > ks) {
+            st = ks;
+            rs = R_CUT;
+        }
+        if (prune && __ldcg(&Rr[k]) > bR) {
+            st = del_cross_step(j, k, st, bR, G, t, p, pe, id0, d_err);
+            rs = R_CUT;
+        }
+        tsum += st;
+        if (dbg_reason) {
             dbg_reason[(size_t)i * p.s + k] = (int32_t)rs;
             dbg_steps[(size_t)i * p.s + k] = (int32_t)st;
         }
     }
+    for (int o = 16; o > 0; o >>= 1) tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
     if (lane == 0) {
         dg_update_result& o = res[i];
         o.hit = nh > 0;
@@ -509,7 +566,8 @@ __device__ bool fallback_warp(uint32_t j, int lane, const CSRView& H, const CSRV
 // insertion, or the recovered (path or fallback) edges of a deletion
 __device__ void finalize_update(uint32_t j, int lane, const WalkKernelArgs& a, UpdTotals& tot, uint32_t* sbuf) {
     uint32_t nh = 0;
-    const int bk = reduce_update(j, lane, a.t, a.p, a.r, a.f.res, a.f.best, a.f.dbg_reason, a.f.dbg_steps, tot, nh);
+    const int bk = reduce_update(j, lane, a.t, a.p, a.r, a.f.res, a.f.best, a.f.dbg_reason, a.f.dbg_steps, tot, nh,
+                                 a.G, a.f.pe, a.hdr->id0, a.d_err);
     const uint32_t i = a.t.idx[j];
     Cands c = a.f.c;
     if (a.t.kind[j] == WALK_INS) {
@@ -903,7 +961,7 @@ __global__ void __launch_bounds__(256, (ILP == 1 ? 4 : (ILP == 2 ? 3 : 1))) k_wa
         if (qi >= Wl) break;
         uint32_t j = NONE;
         if (lane == 0) {
-            for (uint32_t spins = 0; spins < FIN_SPIN_LIMIT; ++spins) {
+            for (uint32_t spins = 0; spins < a.f.spin_limit; ++spins) {
                 j = ld_acquire(&a.f.queue[qi]);
                 if (j != NONE) break;
                 __nanosleep(128);
@@ -1069,30 +1127,32 @@ void launch_walk_one(const CSRView& H, const CSRView& G, const WalkTasks& t, con
 // ---------------------------------------------------------------------------
 // per-update reduction (Eq. 12 and the early-exit reading)
 // ---------------------------------------------------------------------------
-__global__ void k_walk_reduce(WalkTasks t, WalkParams p, WalkRecs r, dg_update_result* res, int32_t* best,
-                              BatchCounters* ctr, int32_t* dbg_reason, int32_t* dbg_steps, uint32_t w_max,
-                              const uint32_t* d_err) {
+__global__ void k_walk_reduce(CSRView G, WalkTasks t, WalkParams p, WalkRecs r, const BatchHdr* hdr,
+                              dg_update_result* res, int32_t* best, BatchCounters* ctr, int32_t* dbg_reason,
+                              int32_t* dbg_steps, uint32_t w_max, uint32_t* d_err) {
     if (walk_aborted(d_err)) return;
     const uint32_t W = min(*t.count, w_max);
     const int lane = threadIdx.x & 31;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint64_t id0 = hdr->id0;
     UpdTotals tot;  // this warp's totals (lane 0)
     for (uint32_t j = warp; j < W; j += nwarps) {
         uint32_t nh;
-        reduce_update(j, lane, t, p, r, res, best, dbg_reason, dbg_steps, tot, nh);
+        reduce_update(j, lane, t, p, r, res, best, dbg_reason, dbg_steps, tot, nh, G, nullptr, id0, d_err);
     }
     if (lane == 0) add_totals(ctr, tot);
 }
 
-void launch_walk_reduce(const WalkTasks& t, const WalkParams& p, const WalkRecs& r, dg_update_result* res,
-                        int32_t* best, BatchCounters* ctr, int32_t* dbg_reason, int32_t* dbg_steps,
-                        uint32_t w_max, const uint32_t* d_err, cudaStream_t st) {
+void launch_walk_reduce(const CSRView& G, const WalkTasks& t, const WalkParams& p, const WalkRecs& r,
+                        const BatchHdr* d_hdr, dg_update_result* res, int32_t* best, BatchCounters* ctr,
+                        int32_t* dbg_reason, int32_t* dbg_steps, uint32_t w_max, uint32_t* d_err,
+                        cudaStream_t st) {
     uint32_t blocks = (w_max + 7) / 8;
     const uint32_t cap = (uint32_t)device_sms() * 16;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    k_walk_reduce<<<blocks, 256, 0, st>>>(t, p, r, res, best, ctr, dbg_reason, dbg_steps, w_max, d_err);
+    k_walk_reduce<<<blocks, 256, 0, st>>>(G, t, p, r, d_hdr, res, best, ctr, dbg_reason, dbg_steps, w_max, d_err);
     ++g_launches;
     DG_CHECK_LAUNCH();
 }

@@ -22,7 +22,7 @@ struct WalkTasks {
     uint64_t* rmax;  // insertion: FP64 bit pattern of the largest R with w_pq * R <= K (all ones for deletions)
     uint8_t* kind;   // WALK_INS / WALK_DEL
     uint32_t* kstar; // insertion: first hitting step (early exit); deletion: minimum high word
-                     // of a hit's FP64 resistance (pruning); 0xFFFFFFFF if none yet
+                     // of a hit's FP64 resistance seen so far (pruning); 0xFFFFFFFF if none yet
     uint32_t* count; // device: number of walked updates W
 };
 
@@ -67,10 +67,12 @@ struct BatchCounters {
     unsigned long long hits;
 };
 
-// per-update reduction; writes results, best walker per walked update
-void launch_walk_reduce(const WalkTasks& t, const WalkParams& p, const WalkRecs& r, dg_update_result* res,
-                        int32_t* best, BatchCounters* ctr, int32_t* dbg_reason, int32_t* dbg_steps,
-                        uint32_t w_max, const uint32_t* d_err, cudaStream_t st);
+// per-update reduction; writes results, best walker per walked update (G: the
+// deletion walks' snapshot, replayed for the exact pruned step counts)
+void launch_walk_reduce(const CSRView& G, const WalkTasks& t, const WalkParams& p, const WalkRecs& r,
+                        const BatchHdr* d_hdr, dg_update_result* res, int32_t* best, BatchCounters* ctr,
+                        int32_t* dbg_reason, int32_t* dbg_steps, uint32_t w_max, uint32_t* d_err,
+                        cudaStream_t st);
 
 // commit candidates (half-edges, keys x*n+y) with G_b weights
 struct Cands {
@@ -136,7 +138,9 @@ struct FinArgs {
     uint32_t* pv;
     uint32_t* pe;
     uint32_t on;          // 0: records only (reduction and emission run as separate kernels)
+    uint32_t spin_limit;  // polls of the finalize queue before ERR_SPIN (FIN_SPIN_LIMIT unless set for tests)
 };
+constexpr uint32_t FIN_SPIN_LIMIT = 1u << 22;  // about 0.5 s of polling
 
 // checkpoint spacing for step limit T: a power of two >= 16 giving at most 7 per walker
 inline uint32_t walk_cp_shift(uint32_t T) {

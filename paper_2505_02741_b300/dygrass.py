@@ -40,7 +40,8 @@ EXPORTS = ("dg_config_default", "dg_create", "dg_destroy", "dg_status_str", "dg_
            "dg_unload_graph", "dg_init_sparsifier", "dg_apply_updates", "dg_apply_updates_device",
            "dg_query_sparsifier", "dg_query_graph", "dg_get_batch_stats", "dg_get_walker_records", "dg_compact",
            "dg_graph_bytes", "dg_launch_count", "dg_set_next_update_id", "dg_get_next_update_id",
-           "dg_set_walk_shape", "dg_set_walk_refill", "dg_submit_updates", "dg_wait", "dg_walk_estimate_noalloc")
+           "dg_set_walk_shape", "dg_set_walk_refill", "dg_submit_updates", "dg_wait", "dg_walk_estimate_noalloc",
+           "dg_debug_set_wait_limit")
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -113,6 +114,7 @@ def load_library(path: str | None = None):
         "dg_submit_updates": (i32, [P, i32, i64, P, P, C.POINTER(u64)]),
         "dg_wait": (i32, [P, u64, i32, C.POINTER(C.c_double)]),
         "dg_walk_estimate_noalloc": (i32, [P, i32, i64, P, P, P]),
+        "dg_debug_set_wait_limit": (i32, [P, i64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -201,6 +203,10 @@ class Context:
 
     def launch_count(self) -> int:
         return int(self._lib.dg_launch_count(self._h))
+
+    def debug_set_wait_limit(self, polls: int):
+        """Polls of the walk's finalize-queue wait before it gives up (< 0: default)."""
+        _check(self._lib.dg_debug_set_wait_limit(self._h, int(polls)))
 
     def load_graph(self, n, u, v, w) -> "Graph":
         u = np.ascontiguousarray(u, np.int32)

@@ -25,6 +25,7 @@ id) plus a seeded 10 % sample of the off-tree edges.
 """
 from __future__ import annotations
 
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -52,7 +53,8 @@ def canonical(u, v, w=None):
     v = np.asarray(v, dtype=np.int64)
     a = np.minimum(u, v)
     b = np.maximum(u, v)
-    order = np.lexsort((b, a))
+    span = np.int64(int(b.max()) + 1) if b.size else np.int64(1)
+    order = np.argsort(a * span + b, kind="stable")  # (a, b) lexicographic, ties in input order
     a, b = a[order], b[order]
     out_w = None if w is None else np.asarray(w, dtype=np.float64)[order]
     return a.astype(np.int32), b.astype(np.int32), out_w
@@ -123,41 +125,59 @@ def rmat(scale: int, n_edges: int, rng: np.random.Generator,
          abcd=(0.57, 0.19, 0.19, 0.05), round_size: int = 1 << 24):
     """Symmetrised R-MAT: self-loops and duplicates removed, vertex ids permuted.
 
-    Samples are drawn in rounds until ``n_edges`` distinct undirected edges
-    exist; the first ``n_edges`` distinct edges in draw order are kept.
+    Every level of a sample picks a quadrant from one 32-bit draw x: a when
+    x < 2^32 a, b below 2^32 (a + b), c below 2^32 (a + b + c), else d.
+    Samples are drawn in rounds of ``round_size`` until ``n_edges`` distinct
+    undirected edges exist; the ``n_edges`` distinct edges drawn first are kept.
     """
     n = 1 << scale
-    # quadrant per level from an integer draw in [0, 100): the probabilities are
-    # whole percents, so thresholds reproduce them exactly
-    t_a = int(round(abcd[0] * 100))
-    t_b = t_a + int(round(abcd[1] * 100))
-    t_c = t_b + int(round(abcd[2] * 100))
-    keys = []  # canonical keys of non-loop samples, in draw order
-    raw = 0
-    uniq = first = None
-    while True:
-        m = round_size
-        u = np.zeros(m, dtype=np.int64)
-        v = np.zeros(m, dtype=np.int64)
+    if scale > 31:
+        raise ValueError("scale <= 31")
+    ta, tab, tabc = (np.uint32(min(int(round(x * 2.0 ** 32)), 2 ** 32 - 1)) for x in np.cumsum(abcd)[:3])
+    m = round_size
+    u = np.empty(m, np.uint32)
+    v = np.empty(m, np.uint32)
+    t1 = np.empty(m, bool)
+    t2 = np.empty(m, bool)
+    uniq = np.empty(0, np.int64)   # distinct canonical keys so far (sorted)
+    first = np.empty(0, np.int64)  # draw position of each key's first sample
+    base = 0
+    while uniq.size < n_edges:
+        u[:] = 0
+        v[:] = 0
         for _ in range(scale):
-            q = rng.integers(0, 100, size=m, dtype=np.uint8)
-            u = (u << 1) | (q >= t_b)
-            v = (v << 1) | (((q >= t_a) & (q < t_b)) | (q >= t_c))
+            x = rng.integers(0, 2 ** 32 - 1, size=m, dtype=np.uint32, endpoint=True)
+            np.left_shift(u, 1, out=u)
+            np.greater_equal(x, tab, out=t1)          # quadrant c or d: row bit
+            np.bitwise_or(u, t1, out=u)
+            np.left_shift(v, 1, out=v)
+            np.greater_equal(x, ta, out=t1)
+            np.less(x, tab, out=t2)
+            np.logical_and(t1, t2, out=t1)            # quadrant b ...
+            np.greater_equal(x, tabc, out=t2)         # ... or d: column bit
+            np.logical_or(t1, t2, out=t1)
+            np.bitwise_or(v, t1, out=v)
         keep = u != v
-        keys.append(np.minimum(u, v)[keep] * n + np.maximum(u, v)[keep])
-        raw += int(keep.sum())
-        if raw < n_edges:
-            continue
-        allk = np.concatenate(keys)
-        uniq, first = np.unique(allk, return_index=True)
-        if uniq.size >= n_edges:
-            break
-    order = np.argsort(first, kind="stable")[:n_edges]
-    kk = uniq[order]
-    a, b = kk // n, kk % n
-    perm = rng.permutation(n)
-    a2, b2, _ = canonical(perm[a], perm[b])
-    return n, a2, b2
+        uu = u[keep].astype(np.int64)
+        vv = v[keep].astype(np.int64)
+        k = np.minimum(uu, vv) * n + np.maximum(uu, vv)
+        ku, kf = np.unique(k, return_index=True)
+        kf += base
+        base += k.size
+        if uniq.size:
+            pos = np.searchsorted(uniq, ku)
+            new = uniq[np.minimum(pos, uniq.size - 1)] != ku
+            ku, kf, pos = ku[new], kf[new], pos[new]
+            uniq = np.insert(uniq, pos, ku)
+            first = np.insert(first, pos, kf)
+        else:
+            uniq, first = ku, kf
+    if uniq.size > n_edges:  # the n_edges keys drawn first (draw positions are distinct)
+        uniq = uniq[np.sort(np.argpartition(first, n_edges - 1)[:n_edges])]
+    perm = rng.permutation(n).astype(np.int64)
+    a, b = perm[uniq // n], perm[uniq % n]
+    keys = np.sort(np.minimum(a, b) * n + np.maximum(a, b))
+    return n, (keys // n).astype(np.int32), (keys % n).astype(np.int32)
 
 
 # --------------------------------------------------------------------------
@@ -382,11 +402,28 @@ def make_fea(nx: int = 2048, ny: int = 2048, seed: int = 0, K: float = 100.0, T:
 def make_rmat(scale: int = 22, n_edges: int = 64_000_000, seed: int = 0, K: float = 100.0,
               T: int = 100, s: int = 32) -> tuple[Workload, UpdateStream]:
     """Power-law social-like graph: symmetrised R-MAT, unit weights; insertions
-    between uniform random vertex pairs."""
+    between uniform random vertex pairs.
+
+    Drawing the scale-22 graph takes about a minute; when the environment
+    variable DG_WORKLOAD_CACHE names a directory, the graph and H(0) are kept
+    there (one .npz per scale, edge count and seed) and read back by later
+    calls.  The update stream has its own generator, so it is the same either
+    way."""
     r = rngs(seed)
-    n, a, b = rmat(scale, n_edges, r["structure"])
+    cache = os.environ.get("DG_WORKLOAD_CACHE")
+    path = os.path.join(cache, f"rmat_v2_s{scale}_m{n_edges}_seed{seed}.npz") if cache else None
+    if path and os.path.exists(path):
+        with np.load(path) as z:
+            n, a, b, h = int(z["n"]), z["a"], z["b"], z["h"]
+    else:
+        n, a, b = rmat(scale, n_edges, r["structure"])
+        h = init_sparsifier(n, a, b, np.ones(a.size), r["init_h"])
+        if path:
+            os.makedirs(cache, exist_ok=True)
+            tmp = path + f".{os.getpid()}.tmp.npz"
+            np.savez(tmp, n=n, a=a, b=b, h=h)
+            os.replace(tmp, path)
     w = np.ones(a.size)
-    h = init_sparsifier(n, a, b, w, r["init_h"])
     wl = Workload(f"rmat_s{scale}", n, a, b, w, h, K=K, T=T, s=s, seed=seed)
     return wl, UpdateStream(wl, r["updates"], ("uniform",), lambda rng, u, v: np.ones(len(u)))
 

@@ -52,6 +52,11 @@ int main(void) {
          sizeof(dg_update_result), offsetof(dg_update_result, r_est));
   printf("%zu %zu %zu\n", sizeof(dg_config), offsetof(dg_config, alloc), sizeof(dg_batch_stats));
   printf("%zu %zu\n", offsetof(dg_update_result, nhits), offsetof(dg_update_result, steps));
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(dg_walk_query), offsetof(dg_walk_query, u), offsetof(dg_walk_query, v),
+         offsetof(dg_walk_query, w), offsetof(dg_walk_query, kind), offsetof(dg_walk_query, id));
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(dg_walk_estimate), offsetof(dg_walk_estimate, status),
+         offsetof(dg_walk_estimate, nhits), offsetof(dg_walk_estimate, best_walker),
+         offsetof(dg_walk_estimate, steps), offsetof(dg_walk_estimate, r_est), offsetof(dg_walk_estimate, hit));
   return 0;
 }
 """
@@ -72,6 +77,12 @@ int main(void) {
     assert vals[7] == C.sizeof(D.BatchStats)
     assert vals[8] == D.RESULT_DTYPE.fields["nhits"][1]
     assert vals[9] == D.RESULT_DTYPE.fields["steps"][1]
+    q = vals[10:16]
+    assert q[0] == D.QUERY_DTYPE.itemsize == 32
+    assert q[1:] == [D.QUERY_DTYPE.fields[f][1] for f in ("u", "v", "w", "kind", "id")]
+    e = vals[16:23]
+    assert e[0] == D.ESTIMATE_DTYPE.itemsize == 32
+    assert e[1:] == [D.ESTIMATE_DTYPE.fields[f][1] for f in ("status", "nhits", "best_walker", "steps", "r_est", "hit")]
 
 
 def test_host_only_calls(lib):

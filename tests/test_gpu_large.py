@@ -4,19 +4,20 @@
   full batch of 100k mixed updates, in the benchmark's launch form (the first
   batch autotunes, the second replays the captured step): every update result
   and the final H and G match the oracle.
-* R-MAT (power law, hubs of degree > 10^4): every status, walked flag and the
-  final G match; walk results are compared on a sample of updates (the oracle's
-  plain neighbour scan costs O(degree) per step at the hubs), using the
-  oracle's walk mask.  Scale 18 runs by default; the full scale-22, 64M-edge
-  graph runs when DG_RUN_SLOW=1.
+* R-MAT scale 22 (4.2M vertices, 64M edges, power law with hubs of degree
+  > 10^5, 1.8M isolated vertices): two full batches of 50k updates (60 %
+  insertions between random vertices, 40 % deletions of current edges), the
+  benchmark's workload and launch form; every update result, H and G match
+  the oracle, which runs the walks of a batch on every host core (its OpenMP
+  build, identical to the single-threaded one).  Scale 18 runs the same way
+  in a few seconds.
 """
 from __future__ import annotations
-
-import os
 
 import numpy as np
 import pytest
 
+from oracle.oracle import OracleGraph
 from paper_2505_02741_b300 import dygrass as D
 from paper_2505_02741_b300 import workloads as W
 from tests.gpu_util import assert_edges_equal, assert_results_equal, pair, step_both
@@ -35,32 +36,32 @@ def test_fea_full_size_batches():
     ctx.close()
 
 
-def _rmat_sampled(scale, n_edges, n_ins, n_del, n_sample):
+def _rmat_full(scale, n_edges, n_ins, n_del, batches=2):
     wl, st = W.make_rmat(scale, n_edges)
-    ctx, g, o = pair(wl.n, wl.a, wl.b, wl.w, wl.h_ids)
-    bt = st.next_batch(n_ins, n_del)
-    res = g.apply(D.make_updates(bt.u, bt.v, bt.w, bt.op))
-    rng = np.random.default_rng(scale)
-    walked = np.nonzero(res["walked"])[0]
-    dels = walked[bt.op[walked] == 1]
-    ins = walked[bt.op[walked] == 0]
-    pick = np.concatenate([rng.choice(dels, min(n_sample // 2, dels.size), replace=False),
-                           rng.choice(ins, min(n_sample // 2, ins.size), replace=False)])
-    mask = np.zeros(len(bt), bool)
-    mask[pick] = True
-    ref = o.apply(bt.u, bt.v, bt.w, bt.op, walk_mask=mask, prune_bounds=True)
-    assert np.array_equal(res["status"], ref["status"])
-    assert np.array_equal(res["walked"], ref["walked"])
-    assert_results_equal(res[pick], {k: np.asarray(x)[pick] for k, x in ref.items()}, "sampled")
+    ctx = D.Context(K=wl.K, T=wl.T, s=wl.s)
+    g = ctx.load_graph(wl.n, wl.a, wl.b, wl.w)
+    g.init_sparsifier(wl.a[wl.h_ids], wl.b[wl.h_ids])
+    o = OracleGraph(wl.n, wl.a, wl.b, wl.w, K=wl.K, T=wl.T, s=wl.s, threads=0)
+    o.init_sparsifier(wl.a[wl.h_ids], wl.b[wl.h_ids])
+    for bi in range(batches):
+        bt = st.next_batch(n_ins, n_del)
+        res = g.apply(D.make_updates(bt.u, bt.v, bt.w, bt.op))
+        ref = o.apply(bt.u, bt.v, bt.w, bt.op, prune_bounds=True)
+        assert_results_equal(res, ref, f"rmat s{scale} batch {bi}")
+        assert (res["status"] == 0).all() and res["walked"].sum() > 0
+        assert (res["walked"].astype(bool) & (res["steps"] == 0)).any()  # isolated starts walk 0 steps
+        assert res["fallback"].sum() > 0 and res["hit"].sum() > 0
+    assert g.stats()["graph_replayed"] == 1
+    assert_edges_equal(g.sparsifier(), o.edges("H"), "H")
     assert_edges_equal(g.edges(), o.edges("G"), "G")
-    assert res["walked"].sum() > 0 and (res["steps"] == 0).any()  # isolated starts walk 0 steps
+    o.close()
     ctx.close()
 
 
-def test_rmat_scale18_sampled():
-    _rmat_sampled(18, 4_000_000, 12_000, 8_000, 400)
+def test_rmat_scale18_full_batches():
+    _rmat_full(18, 4_000_000, 12_000, 8_000)
 
 
-@pytest.mark.skipif(os.environ.get("DG_RUN_SLOW") != "1", reason="full R-MAT scale 22 (64M edges): DG_RUN_SLOW=1")
-def test_rmat_scale22_full_size_sampled():
-    _rmat_sampled(22, 64_000_000, 30_000, 20_000, 200)
+def test_rmat_scale22_full_size():
+    """The power-law configuration at full size: 64M edges, 50k-update batches."""
+    _rmat_full(22, 64_000_000, 30_000, 20_000)

@@ -279,6 +279,44 @@ dg_status dg_set_walk_shape(dg_ctx* ctx, int32_t graph_id, int32_t block, int32_
 dg_status dg_set_walk_refill(dg_ctx* ctx, int32_t graph_id, int32_t refill_min);
 
 /*
+ * Sharded batch over replicas (Section III-F: the walked updates of one batch
+ * are independent walk tasks on one snapshot).  Every replica -- a context
+ * holding the same G, H and update sequence number, typically one per GPU or
+ * per process -- calls the three steps with the same batch:
+ *
+ *   dg_shard_begin   validates and mutates G and H (identically everywhere),
+ *                    then walks only this replica's share of the W walked
+ *                    updates: the contiguous task range
+ *                    [W rank / world, W (rank + 1) / world) (deletions first,
+ *                    then insertions, each in update order), and reduces them
+ *                    (Eq. 12).  *nrec_out receives the number of records this
+ *                    replica exports.  rank in [0, world); record_walkers must
+ *                    be off and walk_mode DG_WALK_BATCHED.
+ *   dg_shard_export  copies those records (DG_SHARD_RECORD_BYTES each) into
+ *                    the caller's host buffer of cap records (recs NULL: only
+ *                    *nrec_out is set).
+ *   dg_shard_commit  takes the records of every replica gathered in any order
+ *                    (nrec in total; each walked update exactly once, else
+ *                    DG_E_INVALID and nothing is committed), replays each
+ *                    deletion's argmin path from its Philox counters on G_b,
+ *                    forms the kept, recovered and fallback edges and commits
+ *                    them to H; res (nullable, nu entries of the batch)
+ *                    receives every update's result.
+ *
+ * The gathering is the caller's (for instance an all-gather over processes
+ * after exchanging the record counts).  Results, G and H then equal, byte for
+ * byte, those of dg_apply_updates on the same batch, on every replica.  Until
+ * dg_shard_commit returns, the graph accepts no other batch (DG_E_STATE).
+ */
+#define DG_SHARD_RECORD_BYTES 48
+
+dg_status dg_shard_begin(dg_ctx* ctx, int32_t graph_id, int64_t nu, const dg_update* ups, int32_t rank,
+                         int32_t world, void* cuda_stream, uint64_t* nrec_out);
+dg_status dg_shard_export(dg_ctx* ctx, int32_t graph_id, void* recs, uint64_t cap, uint64_t* nrec_out);
+dg_status dg_shard_commit(dg_ctx* ctx, int32_t graph_id, uint64_t nrec, const void* recs,
+                          dg_update_result* res);
+
+/*
  * Debug: the number of times the finalizing warps of the batched walk poll
  * for the next completed update before they give up (polls >= 0; < 0 restores
  * the default of 2^22 polls, about half a second).  When a wait gives up, the

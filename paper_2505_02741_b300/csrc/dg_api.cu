@@ -493,6 +493,34 @@ dg_status dg_set_walk_refill(dg_ctx* ctx, int32_t gid, int32_t refill_min) {
     });
 }
 
+dg_status dg_shard_begin(dg_ctx* ctx, int32_t gid, int64_t nu, const dg_update* ups, int32_t rank, int32_t world,
+                         void* stream, uint64_t* nrec_out) {
+    return guarded(ctx, [&]() {
+        Ctx& c = C(ctx);
+        DGraph& g = c.graph(gid);
+        std::lock_guard<std::mutex> lk(g.mu);
+        graph_shard_begin(c, g, nu, ups, rank, world, stream ? (cudaStream_t)stream : c.stream, nrec_out);
+    });
+}
+
+dg_status dg_shard_export(dg_ctx* ctx, int32_t gid, void* recs, uint64_t cap, uint64_t* nrec_out) {
+    return guarded(ctx, [&]() {
+        Ctx& c = C(ctx);
+        DGraph& g = c.graph(gid);
+        std::lock_guard<std::mutex> lk(g.mu);
+        graph_shard_export(c, g, static_cast<ShardRec*>(recs), cap, nrec_out);
+    });
+}
+
+dg_status dg_shard_commit(dg_ctx* ctx, int32_t gid, uint64_t nrec, const void* recs, dg_update_result* res) {
+    return guarded(ctx, [&]() {
+        Ctx& c = C(ctx);
+        DGraph& g = c.graph(gid);
+        std::lock_guard<std::mutex> lk(g.mu);
+        graph_shard_commit(c, g, static_cast<const ShardRec*>(recs), nrec, res);
+    });
+}
+
 dg_status dg_debug_set_wait_limit(dg_ctx* ctx, int64_t polls) {
     return guarded(ctx, [&]() {
         Ctx& c = C(ctx);

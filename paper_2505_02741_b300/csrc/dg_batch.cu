@@ -383,7 +383,7 @@ uint64_t BatchWS::bytes() const {
          fb_count.bytes();
     b += fb_slot.bytes() + fb_big.bytes() + fb_cbase.bytes() + fb_dslot.bytes() + fb_py.bytes() + fb_pr.bytes() +
          fb_pw.bytes();
-    b += dbg_reason.bytes() + dbg_steps.bytes() + dbg_paths.bytes();
+    b += dbg_reason.bytes() + dbg_steps.bytes() + dbg_paths.bytes() + shard_recs.bytes();
     b += apG.bytes() + apH.bytes() + apC.bytes();
     return b;
 }
@@ -664,6 +664,7 @@ void graph_mark_mutation(DGraph& g, cudaStream_t st) {
 }
 
 void graph_init_h(Ctx& c, DGraph& g, int64_t mh, const int32_t* u, const int32_t* v) {
+    if (g.shard.active) throw Error(DG_E_STATE, "a sharded batch is in progress on this graph");
     cudaStream_t st = c.stream;
     DevAlloc& a = c.alloc;
     if (mh < 0 || 2 * (uint64_t)mh >= 0xFFFFFFF0ull) throw Error(DG_E_INVALID, "bad sparsifier size");
@@ -773,6 +774,7 @@ void graph_export(Ctx& c, DGraph& g, bool which_h, int64_t cap, int32_t* u, int3
 }
 
 void graph_compact(Ctx& c, DGraph& g, cudaStream_t st) {
+    if (g.shard.active) throw Error(DG_E_STATE, "a sharded batch is in progress on this graph");
     graph_wait_estimates(g, st);
     csr_compact(g.G, c.alloc, 0, st);
     csr_compact(g.H, c.alloc, 0, st);
@@ -835,7 +837,7 @@ void graph_release_ws(Ctx& c, DGraph& g, cudaStream_t st) {
     REL(t_idx); REL(t_kstar); REL(t_fin); REL(t_queue); REL(qctr); REL(cp); REL(step_v); REL(step_e); REL(t_count); REL(meta); REL(t_wpq); REL(t_rmax); REL(recR); REL(t_kind); REL(best);
     REL(ckeys); REL(ckeys_alt); REL(ck2); REL(cvals); REL(cvals_alt); REL(chist); REL(cscan); REL(ccount);
     REL(cflag); REL(cpos); REL(cv2); REL(ccount2); REL(cw); REL(kind_ins); REL(path_buf); REL(path_w); REL(path_len); REL(fb_list); REL(fb_count); REL(fb_slot); REL(fb_big); REL(fb_cbase); REL(fb_dslot); REL(fb_py); REL(fb_pr); REL(fb_pw); REL(dbg_reason);
-    REL(dbg_steps); REL(dbg_paths);
+    REL(dbg_steps); REL(dbg_paths); REL(shard_recs);
 #undef REL
     w.b_max = 0;
     w.cand_cap = 0;
@@ -1120,7 +1122,7 @@ static bool enqueue_walks(Ctx& c, DGraph& g, cudaStream_t st, int64_t per_update
     DG_CUDA(record_event(g.ev[1], st));
     if (!fused)
         launch_walk_reduce(g.G.view(), tasks, wp, wr, w.hdr.p, w.res.p, w.best.p, w.ctr.p,
-                           c.cfg.record ? w.dbg_reason.p : nullptr, c.cfg.record ? w.dbg_steps.p : nullptr,
+                           c.cfg.record ? w.dbg_reason.p : nullptr, c.cfg.record ? w.dbg_steps.p : nullptr, 0u,
                            w.b_max, w.err.p, st);
     DG_CUDA(record_event(g.ev[5], st));
     return fused;
@@ -1336,6 +1338,7 @@ static void ensure_headroom(Ctx& c, DGraph& g, uint32_t nu, cudaStream_t st) {
 void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_update_result* res, bool device_io,
                  cudaStream_t st) {
     if (!g.has_h) throw Error(DG_E_STATE, "no sparsifier");
+    if (g.shard.active) throw Error(DG_E_STATE, "a sharded batch is in progress on this graph");
     if (nu64 < 0 || nu64 > (1ll << 26)) throw Error(DG_E_INVALID, "batch size out of range");
     if (nu64 == 0) return;
     const uint32_t nu = (uint32_t)nu64;
@@ -1499,6 +1502,198 @@ void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_updat
     const uint64_t dl = g_launches - l0;
     s.launches = (int64_t)dl;
     c.launches += dl;
+}
+
+
+// ---------------------------------------------------------------------------
+// sharded batch
+// ---------------------------------------------------------------------------
+
+// this replica's walked updates [j_lo, j_hi) as records (argmin walker's step
+// count from its record; 0 when there is none)
+__global__ void k_shard_pack(WalkTasks t, const dg_update_result* __restrict__ res, const int32_t* __restrict__ best,
+                             const uint32_t* __restrict__ meta, uint32_t s, uint32_t j_lo, uint32_t j_hi,
+                             ShardRec* __restrict__ out) {
+    for (uint32_t j = j_lo + blockIdx.x * blockDim.x + threadIdx.x; j < j_hi; j += gridDim.x * blockDim.x) {
+        ShardRec rec;
+        rec.j = j;
+        rec.best = best[j];
+        rec.best_steps = rec.best >= 0 ? (meta[(size_t)j * s + (uint32_t)rec.best] & 0xFFFFu) : 0u;
+        rec.reserved = 0;
+        rec.r = res[t.idx[j]];
+        out[j - j_lo] = rec;
+    }
+}
+
+// every shard's records back into the batch state: result, argmin walker and,
+// for a deletion with a hit, the argmin walker's record (the replayed path's
+// length); ERR_INTERNAL on a record outside the task list
+__global__ void k_shard_unpack(WalkTasks t, const ShardRec* __restrict__ recs, uint32_t nrec, uint32_t s,
+                               dg_update_result* __restrict__ res, int32_t* __restrict__ best,
+                               uint32_t* __restrict__ meta, uint32_t* d_err) {
+    const uint32_t W = *t.count;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nrec; q += gridDim.x * blockDim.x) {
+        const ShardRec rec = recs[q];
+        if (rec.j >= W || rec.best >= (int32_t)s) {
+            atomicOr(d_err, (uint32_t)ERR_INTERNAL);
+            continue;
+        }
+        res[t.idx[rec.j]] = rec.r;
+        best[rec.j] = rec.best;
+        if (rec.best >= 0) meta[(size_t)rec.j * s + (uint32_t)rec.best] = rec.best_steps | (R_HIT << 16);
+    }
+}
+
+void graph_shard_begin(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, int32_t rank, int32_t world,
+                       cudaStream_t st, uint64_t* nrec_out) {
+    if (!g.has_h) throw Error(DG_E_STATE, "no sparsifier");
+    if (g.shard.active) throw Error(DG_E_STATE, "a sharded batch is already in progress on this graph");
+    if (world < 1 || rank < 0 || rank >= world) throw Error(DG_E_INVALID, "rank must lie in [0, world)");
+    if (c.cfg.record) throw Error(DG_E_STATE, "record_walkers is not available for sharded batches");
+    if (c.cfg.walk_mode != DG_WALK_BATCHED) throw Error(DG_E_STATE, "sharded batches use the batched walk");
+    if (nu64 < 0 || nu64 > (1ll << 26)) throw Error(DG_E_INVALID, "batch size out of range");
+    const uint32_t nu = (uint32_t)nu64;
+    if (nu > 0 && !ups) throw Error(DG_E_INVALID, "null update array");
+    const uint32_t bucket = bucket_of(nu > 0 ? nu : 1);
+    graph_wait_estimates(g, st);
+    ensure_ws(c, g, bucket, st);
+    ensure_headroom(c, g, nu, st);
+    BatchWS& w = g.ws;
+    w.shard_recs.ensure(c.alloc, w.b_max, st);
+    g.hs.hdr->nu = nu;
+    g.hs.hdr->pad = 0;
+    g.hs.hdr->id0 = g.next_id;
+    if (nu) std::memcpy(g.hs.ups, ups, sizeof(dg_update) * nu);
+    const uint64_t l0 = g_launches;
+    DG_CUDA(record_event(g.ev[2], st));
+    for (int retries = 0;; ++retries) {
+        DG_CUDA(cudaMemcpyAsync(w.hdr.p, g.hs.hdr, sizeof(BatchHdr), cudaMemcpyHostToDevice, st));
+        if (nu) DG_CUDA(cudaMemcpyAsync(w.ups.p, g.hs.ups, sizeof(dg_update) * nu, cudaMemcpyHostToDevice, st));
+        enqueue_mutate(c, g, st);
+        DG_CUDA(cudaMemcpyAsync(g.hs.err, w.err.p, 4, cudaMemcpyDeviceToHost, st));
+        DG_CUDA(cudaMemcpyAsync(g.hs.counts, w.t_count.p, 4, cudaMemcpyDeviceToHost, st));
+        wait_stream(c, st);
+        const uint32_t err = g.hs.err[0];
+        if (err & ERR_INTERNAL) throw Error(DG_E_CUDA, "internal consistency check failed on the device");
+        if (err & ERR_SPIN) throw Error(DG_E_TIMEOUT, "a bounded device wait gave up");
+        if (!(err & ABORT_MASK)) break;
+        if (retries >= 8) throw Error(DG_E_NOMEM, "batch could not get enough device memory");
+        handle_abort(c, g, err, st);  // nothing was written: grow and run the mutation again
+    }
+    const uint32_t W = std::min<uint32_t>(g.hs.counts[0], w.b_max);
+    if (c.cfg.autotune && !g.tuned && nu >= 4096) autotune_walks(c, g, st);
+    const uint32_t j_lo = (uint32_t)((uint64_t)W * (uint32_t)rank / (uint32_t)world);
+    const uint32_t j_hi = (uint32_t)((uint64_t)W * (uint32_t)(rank + 1) / (uint32_t)world);
+    DG_CUDA(record_event(g.ev[4], st));
+    DG_CUDA(record_event(g.ev[0], st));
+    if (j_hi > j_lo) {
+        const WalkParams wp = params_of(c.cfg);
+        const WalkRecs wr = recs_of(c, w);
+        const WalkTasks tasks = tasks_of(w);
+        launch_walk_batched(g.H.view(), g.G.view(), tasks, wp, wr, w.hdr.p, w.next.p, j_lo, j_hi, g.shape,
+                            fin_of(c, w, false), w.err.p, st, g.side, g.fk[5], g.fk[6]);
+        DG_CUDA(record_event(g.ev[1], st));
+        launch_walk_reduce(g.G.view(), tasks, wp, wr, w.hdr.p, w.res.p, w.best.p, w.ctr.p, nullptr, nullptr, j_lo,
+                           j_hi, w.err.p, st);
+        k_shard_pack<<<grid_for(j_hi - j_lo), BT, 0, st>>>(tasks, w.res.p, w.best.p, w.meta.p, (uint32_t)c.cfg.s,
+                                                            j_lo, j_hi, w.shard_recs.p);
+        ++g_launches;
+        DG_CHECK_LAUNCH();
+    } else {
+        DG_CUDA(record_event(g.ev[1], st));
+    }
+    DG_CUDA(record_event(g.ev[5], st));
+    DG_CUDA(cudaMemcpyAsync(g.hs.err, w.err.p, 4, cudaMemcpyDeviceToHost, st));
+    wait_stream(c, st);
+    if (g.hs.err[0] & ERR_INTERNAL) throw Error(DG_E_CUDA, "internal consistency check failed on the device");
+    g.shard.active = true;
+    g.shard.nu = nu;
+    g.shard.W = W;
+    g.shard.j_lo = j_lo;
+    g.shard.j_hi = j_hi;
+    g.shard.st = st;
+    g.stats.launches = (int64_t)(g_launches - l0);
+    if (nrec_out) *nrec_out = j_hi - j_lo;
+}
+
+void graph_shard_export(Ctx& c, DGraph& g, ShardRec* host, uint64_t cap, uint64_t* n_out) {
+    if (!g.shard.active) throw Error(DG_E_STATE, "no sharded batch in progress");
+    const uint64_t n = g.shard.j_hi - g.shard.j_lo;
+    if (n_out) *n_out = n;
+    if (!host) return;  // size query
+    if (cap < n) throw Error(DG_E_INVALID, "export buffer holds fewer records than the shard has");
+    if (n) DG_CUDA(cudaMemcpy(host, g.ws.shard_recs.p, n * sizeof(ShardRec), cudaMemcpyDeviceToHost));
+}
+
+void graph_shard_commit(Ctx& c, DGraph& g, const ShardRec* recs, uint64_t nrec, dg_update_result* res) {
+    if (!g.shard.active) throw Error(DG_E_STATE, "no sharded batch in progress");
+    const uint32_t W = g.shard.W, nu = g.shard.nu;
+    cudaStream_t st = g.shard.st;
+    BatchWS& w = g.ws;
+    // every walked update exactly once
+    if (nrec != W) throw Error(DG_E_INVALID, "the gathered records do not cover the batch's walked updates once");
+    if (W && !recs) throw Error(DG_E_INVALID, "null record array");
+    {
+        std::vector<uint8_t> seen(W, 0);
+        for (uint64_t q = 0; q < nrec; ++q) {
+            if (recs[q].j >= W || seen[recs[q].j])
+                throw Error(DG_E_INVALID, "the gathered records do not cover the batch's walked updates once");
+            seen[recs[q].j] = 1;
+        }
+    }
+    const uint64_t l0 = g_launches;
+    if (W) {
+        DG_CUDA(cudaMemcpyAsync(w.shard_recs.p, recs, W * sizeof(ShardRec), cudaMemcpyHostToDevice, st));
+        k_shard_unpack<<<grid_for(W), BT, 0, st>>>(tasks_of(w), w.shard_recs.p, W, (uint32_t)c.cfg.s, w.res.p,
+                                                    w.best.p, w.meta.p, w.err.p);
+        ++g_launches;
+        DG_CHECK_LAUNCH();
+    }
+    bool scratch_zeroed = true;
+    for (int retries = 0;; ++retries) {
+        enqueue_commit(c, g, st, false, scratch_zeroed);
+        if (nu) DG_CUDA(cudaMemcpyAsync(g.hs.res, w.res.p, sizeof(dg_update_result) * nu, cudaMemcpyDeviceToHost, st));
+        enqueue_readback(g, st);
+        DG_CUDA(record_event(g.ev[3], st));
+        wait_stream(c, st);
+        const uint32_t err = g.hs.err[0];
+        if (err & ERR_INTERNAL) throw Error(DG_E_CUDA, "internal consistency check failed on the device");
+        if (err & ERR_SPIN) throw Error(DG_E_TIMEOUT, "a bounded device wait gave up");
+        if (!(err & ABORT_MASK)) break;
+        if (retries >= 8) throw Error(DG_E_NOMEM, "batch could not get enough device memory");
+        if (handle_abort(c, g, err, st)) throw Error(DG_E_CUDA, "mutation-stage shortage at a sharded commit");
+        DG_CUDA(cudaMemsetAsync(w.err.p, 0, 16, st));
+        scratch_zeroed = false;
+    }
+    graph_mark_mutation(g, st);
+    if (res && nu) std::memcpy(res, g.hs.res, sizeof(dg_update_result) * nu);
+    g.G.host_top = g.hs.tops[0];
+    g.H.host_top = g.hs.tops[1];
+    g.next_id += nu;
+    // statistics of the whole batch, from the gathered results
+    dg_batch_stats& s = g.stats;
+    s.updates = nu;
+    s.valid = s.walked = s.steps = s.accepted = s.recovered = 0;
+    for (uint32_t i = 0; i < nu; ++i) {
+        const dg_update_result& r = g.hs.res[i];
+        s.valid += r.status == DG_UPD_OK;
+        s.walked += r.walked;
+        s.steps += r.walked ? r.steps : 0;
+        s.accepted += r.accepted;
+        s.recovered += r.nrecovered;
+    }
+    float ms = 0.f;
+    s.walk_ms = (cudaEventElapsedTime(&ms, g.ev[0], g.ev[1]) == cudaSuccess) ? ms : -1.0;
+    s.batch_ms = (cudaEventElapsedTime(&ms, g.ev[2], g.ev[3]) == cudaSuccess) ? ms : -1.0;
+    s.mutate_ms = (cudaEventElapsedTime(&ms, g.ev[2], g.ev[4]) == cudaSuccess) ? ms : -1.0;
+    s.reduce_ms = (cudaEventElapsedTime(&ms, g.ev[1], g.ev[5]) == cudaSuccess) ? ms : -1.0;
+    s.emit_ms = -1.0;
+    s.commit_ms = -1.0;
+    cudaGetLastError();
+    s.graph_replayed = 0;
+    s.launches += (int64_t)(g_launches - l0);
+    c.launches += (uint64_t)s.launches;
+    g.shard.active = false;
 }
 
 }  // namespace dg

@@ -27,6 +27,18 @@ struct Config {
     int32_t record = 0;
 };
 
+// One walked update's outcome as a shard of a sharded batch exports it: its
+// task index j (the same on every replica), the argmin walker and its step
+// count (the recorded path length a replica replays), and the update's result.
+struct ShardRec {
+    uint32_t j;
+    int32_t best;
+    uint32_t best_steps;
+    uint32_t reserved;
+    dg_update_result r;
+};
+static_assert(sizeof(ShardRec) == 48, "shard record is 48 bytes");
+
 // device workspace for batches of at most b_max updates
 struct BatchWS {
     uint32_t b_max = 0;
@@ -70,6 +82,8 @@ struct BatchWS {
     DBuf<double> path_w;
     // debug
     DBuf<int32_t> dbg_reason, dbg_steps, dbg_paths;
+    // sharded batches: this replica's records, then every replica's
+    DBuf<ShardRec> shard_recs;
     ApplyScratch apG, apH, apC;
     uint64_t bytes() const;
 };
@@ -111,6 +125,12 @@ struct DGraph {
     bool tuned = false;
     uint64_t layout_gen = 1;  // bumped whenever a buffer baked into a captured step moves
     std::map<uint32_t, CapturedStep> steps;  // by batch-size class
+    // a sharded batch between its walks and its commit (graph_shard_*)
+    struct {
+        bool active = false;
+        uint32_t nu = 0, W = 0, j_lo = 0, j_hi = 0;
+        cudaStream_t st = nullptr;
+    } shard;
     cudaStream_t stream = nullptr;           // private stream (serving)
     // timing events: 0/1 walk, 2/3 batch, 4 end of mutation, 5 end of reduction, 6 end of emission
     cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -140,6 +160,17 @@ void graph_release_ws(Ctx& c, DGraph& g, cudaStream_t st);  // batch workspace o
 void graph_compact(Ctx& c, DGraph& g, cudaStream_t st);
 void graph_export(Ctx& c, DGraph& g, bool which_h, int64_t cap, int32_t* u, int32_t* v, double* w,
                   int64_t* count, cudaStream_t st);
+// Sharded batch (Section III-F: the walked updates of one batch are
+// independent walk tasks on one snapshot).  Every replica validates and
+// mutates identically; shard `rank` of `world` walks the contiguous range
+// [W rank / world, W (rank + 1) / world) of the W walked updates and keeps one
+// ShardRec per walked update of its range; after the records of every shard
+// are gathered, each replica applies the same deterministic commit.
+void graph_shard_begin(Ctx& c, DGraph& g, int64_t nu, const dg_update* ups, int32_t rank, int32_t world,
+                       cudaStream_t st, uint64_t* nrec_out);
+void graph_shard_export(Ctx& c, DGraph& g, ShardRec* host, uint64_t cap, uint64_t* n_out);
+void graph_shard_commit(Ctx& c, DGraph& g, const ShardRec* recs, uint64_t nrec, dg_update_result* res);
+
 // the two halves of the ordering against walk estimates (see DGraph::ev_est)
 void graph_wait_estimates(DGraph& g, cudaStream_t st);
 void graph_mark_mutation(DGraph& g, cudaStream_t st);

@@ -1129,15 +1129,15 @@ void launch_walk_one(const CSRView& H, const CSRView& G, const WalkTasks& t, con
 // ---------------------------------------------------------------------------
 __global__ void k_walk_reduce(CSRView G, WalkTasks t, WalkParams p, WalkRecs r, const BatchHdr* hdr,
                               dg_update_result* res, int32_t* best, BatchCounters* ctr, int32_t* dbg_reason,
-                              int32_t* dbg_steps, uint32_t w_max, uint32_t* d_err) {
+                              int32_t* dbg_steps, uint32_t j_lo, uint32_t j_hi, uint32_t* d_err) {
     if (walk_aborted(d_err)) return;
-    const uint32_t W = min(*t.count, w_max);
+    const uint32_t W = min(*t.count, j_hi);
     const int lane = threadIdx.x & 31;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const uint64_t id0 = hdr->id0;
     UpdTotals tot;  // this warp's totals (lane 0)
-    for (uint32_t j = warp; j < W; j += nwarps) {
+    for (uint32_t j = j_lo + warp; j < W; j += nwarps) {
         uint32_t nh;
         reduce_update(j, lane, t, p, r, res, best, dbg_reason, dbg_steps, tot, nh, G, nullptr, id0, d_err);
     }
@@ -1146,13 +1146,15 @@ __global__ void k_walk_reduce(CSRView G, WalkTasks t, WalkParams p, WalkRecs r, 
 
 void launch_walk_reduce(const CSRView& G, const WalkTasks& t, const WalkParams& p, const WalkRecs& r,
                         const BatchHdr* d_hdr, dg_update_result* res, int32_t* best, BatchCounters* ctr,
-                        int32_t* dbg_reason, int32_t* dbg_steps, uint32_t w_max, uint32_t* d_err,
+                        int32_t* dbg_reason, int32_t* dbg_steps, uint32_t j_lo, uint32_t j_hi, uint32_t* d_err,
                         cudaStream_t st) {
-    uint32_t blocks = (w_max + 7) / 8;
+    const uint32_t span = j_hi > j_lo ? j_hi - j_lo : 0u;
+    uint32_t blocks = (span + 7) / 8;
     const uint32_t cap = (uint32_t)device_sms() * 16;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    k_walk_reduce<<<blocks, 256, 0, st>>>(G, t, p, r, d_hdr, res, best, ctr, dbg_reason, dbg_steps, w_max, d_err);
+    k_walk_reduce<<<blocks, 256, 0, st>>>(G, t, p, r, d_hdr, res, best, ctr, dbg_reason, dbg_steps, j_lo, j_hi,
+                                          d_err);
     ++g_launches;
     DG_CHECK_LAUNCH();
 }

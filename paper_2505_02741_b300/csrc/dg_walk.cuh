@@ -67,11 +67,12 @@ struct BatchCounters {
     unsigned long long hits;
 };
 
-// per-update reduction; writes results, best walker per walked update (G: the
-// deletion walks' snapshot, replayed for the exact pruned step counts)
+// per-update reduction of walked updates [j_lo, j_hi); writes results, best
+// walker per walked update (G: the deletion walks' snapshot, replayed for the
+// exact pruned step counts)
 void launch_walk_reduce(const CSRView& G, const WalkTasks& t, const WalkParams& p, const WalkRecs& r,
                         const BatchHdr* d_hdr, dg_update_result* res, int32_t* best, BatchCounters* ctr,
-                        int32_t* dbg_reason, int32_t* dbg_steps, uint32_t w_max, uint32_t* d_err,
+                        int32_t* dbg_reason, int32_t* dbg_steps, uint32_t j_lo, uint32_t j_hi, uint32_t* d_err,
                         cudaStream_t st);
 
 // commit candidates (half-edges, keys x*n+y) with G_b weights

@@ -32,6 +32,10 @@ QUERY_DTYPE = np.dtype([("u", "<i4"), ("v", "<i4"), ("w", "<f8"), ("kind", "<i4"
 ESTIMATE_DTYPE = np.dtype([("status", "<i4"), ("nhits", "<i4"), ("best_walker", "<i4"), ("steps", "<i4"),
                            ("r_est", "<f8"), ("hit", "u1"), ("reserved", "u1", (7,))])
 assert QUERY_DTYPE.itemsize == 32 and ESTIMATE_DTYPE.itemsize == 32
+# one walked update's outcome exported by a shard of a sharded batch (ShardRec, 48 bytes)
+SHARD_DTYPE = np.dtype([("j", "<u4"), ("best", "<i4"), ("best_steps", "<u4"), ("reserved", "<u4"),
+                        ("result", RESULT_DTYPE)])
+assert SHARD_DTYPE.itemsize == 48
 NOALLOC_MAX_QUERIES = 4096
 NOALLOC_MAX_WALKERS = 131072
 
@@ -41,7 +45,7 @@ EXPORTS = ("dg_config_default", "dg_create", "dg_destroy", "dg_status_str", "dg_
            "dg_query_sparsifier", "dg_query_graph", "dg_get_batch_stats", "dg_get_walker_records", "dg_compact",
            "dg_graph_bytes", "dg_launch_count", "dg_set_next_update_id", "dg_get_next_update_id",
            "dg_set_walk_shape", "dg_set_walk_refill", "dg_submit_updates", "dg_wait", "dg_walk_estimate_noalloc",
-           "dg_debug_set_wait_limit")
+           "dg_debug_set_wait_limit", "dg_shard_begin", "dg_shard_export", "dg_shard_commit")
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -115,6 +119,9 @@ def load_library(path: str | None = None):
         "dg_wait": (i32, [P, u64, i32, C.POINTER(C.c_double)]),
         "dg_walk_estimate_noalloc": (i32, [P, i32, i64, P, P, P]),
         "dg_debug_set_wait_limit": (i32, [P, i64]),
+        "dg_shard_begin": (i32, [P, i32, i64, P, i32, i32, P, C.POINTER(u64)]),
+        "dg_shard_export": (i32, [P, i32, P, u64, C.POINTER(u64)]),
+        "dg_shard_commit": (i32, [P, i32, u64, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -323,6 +330,37 @@ class Graph:
         _check(self._L.dg_walk_estimate_noalloc(self.ctx._h, self.gid, int(nq), C.c_void_p(int(d_queries_ptr)),
                                                 C.c_void_p(int(d_out_ptr)),
                                                 None if stream is None else C.c_void_p(int(stream))))
+
+    def shard_begin(self, ups: np.ndarray, rank: int, world: int, stream=None) -> int:
+        """Sharded batch, step 1: mutate, walk this replica's share; returns its record count."""
+        ups = np.ascontiguousarray(ups, UPDATE_DTYPE)
+        n = C.c_uint64()
+        _check(self._L.dg_shard_begin(self.ctx._h, self.gid, ups.size, _ptr(ups), int(rank), int(world),
+                                      None if stream is None else C.c_void_p(int(stream)), C.byref(n)))
+        self._shard_nu = ups.size
+        return n.value
+
+    def shard_export(self) -> np.ndarray:
+        """Sharded batch, step 2: this replica's records (SHARD_DTYPE)."""
+        n = C.c_uint64()
+        _check(self._L.dg_shard_export(self.ctx._h, self.gid, None, 0, C.byref(n)))
+        recs = np.zeros(n.value, SHARD_DTYPE)
+        _check(self._L.dg_shard_export(self.ctx._h, self.gid, _ptr(recs), recs.size, C.byref(n)))
+        return recs
+
+    def shard_commit(self, recs: np.ndarray) -> np.ndarray:
+        """Sharded batch, step 3: every replica's records (concatenated, any
+        order); commits the batch and returns every update's result."""
+        recs = np.ascontiguousarray(recs, SHARD_DTYPE)
+        res = np.zeros(self._shard_nu, RESULT_DTYPE)
+        _check(self._L.dg_shard_commit(self.ctx._h, self.gid, recs.size, _ptr(recs), _ptr(res)))
+        return res
+
+    def apply_sharded(self, ups: np.ndarray, rank: int, world: int, gather) -> np.ndarray:
+        """One batch as shard `rank` of `world`: ``gather(records)`` must return
+        the records of every shard (e.g. ``shard.allgather_records``)."""
+        self.shard_begin(ups, rank, world)
+        return self.shard_commit(gather(self.shard_export()))
 
     def submit(self, ups: np.ndarray):
         """Queue one request; returns (ticket, result array filled when waited)."""

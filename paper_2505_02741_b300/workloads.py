@@ -122,19 +122,20 @@ def fea_tri(nx: int, ny: int, rng: np.random.Generator, jitter: float = 0.3):
 
 
 def rmat(scale: int, n_edges: int, rng: np.random.Generator,
-         abcd=(0.57, 0.19, 0.19, 0.05), round_size: int = 1 << 24):
+         abcd=(0.57, 0.19, 0.19, 0.05), round_size: int | None = None):
     """Symmetrised R-MAT: self-loops and duplicates removed, vertex ids permuted.
 
     Every level of a sample picks a quadrant from one 32-bit draw x: a when
     x < 2^32 a, b below 2^32 (a + b), c below 2^32 (a + b + c), else d.
-    Samples are drawn in rounds of ``round_size`` until ``n_edges`` distinct
-    undirected edges exist; the ``n_edges`` distinct edges drawn first are kept.
+    Samples are drawn in rounds of ``round_size`` (default min(2^24, 2 n_edges))
+    until ``n_edges`` distinct undirected edges exist; the ``n_edges`` distinct
+    edges drawn first are kept.
     """
     n = 1 << scale
     if scale > 31:
         raise ValueError("scale <= 31")
     ta, tab, tabc = (np.uint32(min(int(round(x * 2.0 ** 32)), 2 ** 32 - 1)) for x in np.cumsum(abcd)[:3])
-    m = round_size
+    m = round_size if round_size else min(1 << 24, max(1 << 16, 2 * n_edges))
     u = np.empty(m, np.uint32)
     v = np.empty(m, np.uint32)
     t1 = np.empty(m, bool)

@@ -703,7 +703,7 @@ __device__ __forceinline__ void lean_start(Lean& w, const WalkKernelArgs& a, uin
     if (a.r.paths) a.r.paths[(size_t)wid * (a.p.T + 1)] = (int32_t)u;
 }
 
-// records the walker's stop (the finalize count follows in signal_stops)
+// records the walker's stop (its finalize count follows through the warp's PendList)
 __device__ __forceinline__ void lean_finish(Lean& w, const WalkKernelArgs& a, uint32_t reason) {
     const size_t wid = (size_t)w.j * a.p.s + w.k;
     a.r.meta[wid] = w.steps | (reason << 16);
@@ -719,14 +719,49 @@ __device__ __forceinline__ void count_stops(const WalkKernelArgs& a, uint32_t j,
     }
 }
 
-// Finalize counts of the walkers that stopped in this iteration, one atomic
-// per (warp, update): the whole warp calls it with its lanes converged; the
-// warp barrier orders every lane's record stores before the leader's release.
-__device__ __forceinline__ void signal_stops(const WalkKernelArgs& a, bool stopped, uint32_t j, int lane) {
-    if (!__any_sync(0xffffffffu, stopped)) return;
-    __syncwarp();
+// Finalize counts a warp has not published yet: (update, stopped walkers)
+// pairs in shared memory.  Publishing costs a GPU-scope release (the warp
+// waits for its record stores to reach L2), so a warp publishes its pending
+// counts together -- when the list fills or every PEND_EVERY iterations, and
+// when it runs out of walkers -- instead of on every iteration with a stop.
+constexpr uint32_t PEND_FLUSH = 48;               // pairs that trigger a publication
+constexpr uint32_t PEND_CAP = PEND_FLUSH + 32 * 4;  // room for one more iteration of 32 stops per walker slot
+constexpr uint32_t PEND_EVERY = 8;                // iterations between publications
+struct PendList {
+    uint32_t j[PEND_CAP];
+    uint32_t n[PEND_CAP];
+    uint32_t cnt;
+};
+
+// adds the walkers that stopped in this iteration (one pair per update), the
+// whole warp converged
+__device__ __forceinline__ void pend_stops(PendList& pl, bool stopped, uint32_t j, int lane) {
     const uint32_t peers = __match_any_sync(0xffffffffu, stopped ? j : NONE);
-    if (stopped && lane == __ffs(peers) - 1) count_stops(a, j, (uint32_t)__popc(peers));
+    const bool lead = stopped && lane == __ffs(peers) - 1;
+    const uint32_t lm = __ballot_sync(0xffffffffu, lead);
+    const uint32_t base = pl.cnt;
+    __syncwarp();
+    if (lead) {
+        const uint32_t q = base + (uint32_t)__popc(lm & ((1u << lane) - 1u));
+        pl.j[q] = j;
+        pl.n[q] = (uint32_t)__popc(peers);
+    }
+    __syncwarp();
+    if (lane == 0) pl.cnt = base + (uint32_t)__popc(lm);
+    __syncwarp();
+}
+
+// Publishes the pending counts, one acquire-release atomic per pair, the
+// lanes in parallel: the warp barrier orders every lane's record stores
+// before the releases; the count that completes an update queues it.
+__device__ __forceinline__ void flush_stops(const WalkKernelArgs& a, PendList& pl, int lane) {
+    __syncwarp();
+    const uint32_t n = pl.cnt;
+    if (n == 0) return;
+    for (uint32_t q = (uint32_t)lane; q < n; q += 32) count_stops(a, pl.j[q], pl.n[q]);
+    __syncwarp();
+    if (lane == 0) pl.cnt = 0;
+    __syncwarp();
 }
 
 // head (nbr, noff, ndeg, rev) and resistance of the entry at pool index i
@@ -831,7 +866,15 @@ __global__ void __launch_bounds__(256, (ILP == 1 ? 4 : (ILP == 2 ? 3 : 1))) k_wa
         fly[i] = false;
     }
     bool exhausted = false;
+    __shared__ PendList s_pend[8];  // per warp (blocks of at most 256 threads)
+    PendList& pend = s_pend[threadIdx.x >> 5];
+    if (lane == 0) pend.cnt = 0;
+    __syncwarp();
+    uint32_t iter = 0;
+    bool stop[ILP];
     for (;;) {
+#pragma unroll
+        for (int i = 0; i < ILP; ++i) stop[i] = false;
         // Refill empty slots, one atomic per warp and slot; a new walker sends
         // out its first load at once.  Starting walkers holds the whole warp
         // up for three dependent reads (id, task fields, start list), so a
@@ -857,10 +900,7 @@ __global__ void __launch_bounds__(256, (ILP == 1 ? 4 : (ILP == 2 ? 3 : 1))) k_wa
                         fly[i] = lean_issue<HUBS>(w[i], a, h[i], r[i], ks[i], at[i]);
                         if (!fly[i]) {
                             lean_finish(w[i], a, R_LEAF);
-                            if (a.f.on) {
-                                __threadfence();
-                                count_stops(a, w[i].j, 1u);
-                            }
+                            stop[i] = true;  // counted with this iteration's stops
                         } else {
                             w[i].x = philox_word0(1u, w[i].k, w[i].ulo, w[i].uhi, a.p.key0, a.p.key1);
                         }
@@ -873,10 +913,13 @@ __global__ void __launch_bounds__(256, (ILP == 1 ? 4 : (ILP == 2 ? 3 : 1))) k_wa
         bool any = false;
 #pragma unroll
         for (int i = 0; i < ILP; ++i) any |= w[i].active;
-        if (!__any_sync(0xffffffffu, any)) break;
-        bool stop[ILP];
+        if (!__any_sync(0xffffffffu, any)) {
+            if (a.f.on) {
 #pragma unroll
-        for (int i = 0; i < ILP; ++i) stop[i] = false;
+                for (int i = 0; i < ILP; ++i) pend_stops(pend, stop[i], w[i].j, lane);
+            }
+            break;
+        }
 #pragma unroll
         for (int i = 0; i < ILP; ++i) {
             if (!fly[i]) continue;
@@ -943,10 +986,14 @@ __global__ void __launch_bounds__(256, (ILP == 1 ? 4 : (ILP == 2 ? 3 : 1))) k_wa
         }
         if (a.f.on) {
 #pragma unroll
-            for (int i = 0; i < ILP; ++i) signal_stops(a, stop[i], w[i].j, lane);
+            for (int i = 0; i < ILP; ++i) pend_stops(pend, stop[i], w[i].j, lane);
+            ++iter;
+            static_assert(ILP <= 4, "pending list sized for four walker slots");
+            if (pend.cnt >= PEND_FLUSH || (iter % PEND_EVERY) == 0u) flush_stops(a, pend, lane);
         }
     }
     if (!a.f.on) return;
+    flush_stops(a, pend, lane);
     __shared__ uint32_t s_emit[8][EMIT_SMEM];  // per warp (blocks of at most 256 threads)
     // No walkers left for this warp: finalize queued updates (in order of
     // completion) until every walked update of the launch is done.  Updates

@@ -90,10 +90,13 @@ def host_cpu():
 
 
 class ClockSampler:
-    """SM clocks and throttle reasons sampled during the timed region (NVML,
-    every 5 ms; nvidia-smi every 200 ms where NVML cannot be loaded)."""
+    """SM clocks and throttle reasons sampled during the timed region: NVML
+    every 5 ms where the Python binding loads, else one nvidia-smi process
+    streaming a sample every 20 ms (stopped when the region ends)."""
 
     NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+    QUERY = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, local=0):
         vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
@@ -102,6 +105,7 @@ class ClockSampler:
         self.rows = []  # (sm_mhz, max_mhz, set of active reasons)
         self._stop = threading.Event()
         self._t = None
+        self._proc = None
         self._nvml = None
         try:
             import pynvml as N
@@ -120,36 +124,52 @@ class ClockSampler:
         masks = (0x8, 0x40, 0x20, 0x4)  # hw slowdown, hw thermal, sw thermal, sw power cap
         return float(sm), float(mx), {n for n, m in zip(self.NAMES, masks) if bits & m}
 
-    def _sample_smi(self):
-        q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-        out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}", "--format=csv,noheader,nounits"],
-                             capture_output=True, text=True, timeout=5).stdout.strip()
-        r = [x.strip() for x in out.split(",")]
+    def _parse(self, line):
+        r = [x.strip() for x in line.split(",")]
+        if len(r) < 6 or not r[0].replace(".", "").isdigit():
+            return None
         act = {n for n, x in zip(self.NAMES, r[2:]) if "Active" in x and "Not" not in x}
         return float(r[0]), float(r[1]), act
 
-    def _run(self):
-        period = 0.005 if self._nvml else 0.2
+    def _run_nvml(self):
         while not self._stop.is_set():
             try:
-                self.rows.append(self._sample_nvml() if self._nvml else self._sample_smi())
+                self.rows.append(self._sample_nvml())
             except Exception:
                 pass
-            self._stop.wait(period)
+            self._stop.wait(0.005)
+
+    def _run_smi(self):
+        for line in self._proc.stdout:
+            row = self._parse(line)
+            if row:
+                self.rows.append(row)
 
     def __enter__(self):
-        self._t = threading.Thread(target=self._run, daemon=True)
-        self._t.start()
+        if self._nvml:
+            self._t = threading.Thread(target=self._run_nvml, daemon=True)
+        else:
+            try:
+                self._proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                               "--format=csv,noheader,nounits", "-lms", "20"],
+                                              stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                self._t = threading.Thread(target=self._run_smi, daemon=True)
+            except OSError:
+                self._proc = None
+        if self._t:
+            self._t.start()
         return self
 
     def __exit__(self, *a):
         self._stop.set()
-        self._t.join(timeout=10)
-        try:
-            self.rows.append(self._sample_nvml() if self._nvml else self._sample_smi())
-        except Exception:
-            pass
+        if self._proc:
+            self._proc.terminate()  # the sampler this object started
+            try:
+                self._proc.wait(timeout=10)
+            except subprocess.TimeoutExpired:
+                self._proc.kill()
+        if self._t:
+            self._t.join(timeout=10)
 
     def summary(self):
         if not self.rows:
@@ -157,7 +177,7 @@ class ClockSampler:
         sm = [r[0] for r in self.rows]
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(r[1] for r in self.rows),
                 "reasons": sorted(set().union(*(r[2] for r in self.rows))), "samples": len(self.rows),
-                "source": "nvml" if self._nvml else "nvidia-smi"}
+                "source": "nvml" if self._nvml else "nvidia-smi -lms 20"}
 
 
 def dist_env():
@@ -267,14 +287,29 @@ def _split_requests(bt, sizes):
     return out
 
 
-def run_serve(args):
+SIZE_BUCKETS = ((1, 99), (100, 999), (1000, 9999), (10000, 50000))
+
+
+def _pcts(x):
+    x = np.asarray(x, np.float64)
+    if x.size == 0:
+        return None
+    return {"n": int(x.size), "p50": float(np.percentile(x, 50)), "p99": float(np.percentile(x, 99)),
+            "max": float(x.max())}
+
+
+def serve_experiment(loads, requests_per_point, seed=7, per_update_sample=6):
     """Serving: the 64x64 grid, the 100^3 mesh and the 2048^2 FEA-like mesh
-    resident at once.  Per graph a Poisson request stream, batch sizes
-    floor(exp(U(0, ln 50001))) (clipped for the small grid), 50/50
-    insertions/deletions.  The three streams share the GPU, so each is offered
-    at `load` x its graph's capacity measured alone, divided by the number of
-    graphs.  Reports updates/s and p50/p99 request latency (submit to results
-    on the host) beside the one-launch-per-update form on a sample of requests."""
+    resident at once in one context.  Per graph a Poisson request stream,
+    batch sizes floor(exp(U(0, ln 50001))) (at most 400 on the small grid),
+    50/50 insertions/deletions.  Each graph's batched capacity is measured
+    alone first; at offered load L every graph's stream runs at L x its
+    capacity alone / 3 (the three share one GPU).  Before the measured
+    streams every graph is prepared for requests of up to 50k updates (batch
+    workspace sized, steps captured) and given the walk shape tuned alone.
+    Per load point: updates/s, request latency (submit to results on the
+    host) p50/p99 overall, per graph and per request-size bucket, and the
+    part of it spent queued behind earlier requests of the same graph."""
     import torch
     from paper_2505_02741_b300 import dygrass as D
     from paper_2505_02741_b300 import workloads as W
@@ -283,98 +318,126 @@ def run_serve(args):
     specs = [("grid64", lambda: W.make_grid(64, 64, seed=0), 400),
              ("mesh100", lambda: W.make_mesh3d(seed=0), 50_000),
              ("fea2048", lambda: W.make_fea(seed=0), 50_000)]
-    arr_rng = W.rngs(7)["arrivals"]
-    per_graph = max(4, args.requests // len(specs))
-    graphs = []
+    arr_rng = W.rngs(seed)["arrivals"]
+    per_graph = max(4, requests_per_point // len(specs))
+    graphs = []  # (name, wl, [requests of point 0], [point 1], ...)
     for name, mk, cap in specs:
         wl, st = mk()
-        _, sizes = W.serving_arrivals(per_graph, 1.0, arr_rng)
-        sizes = np.minimum(sizes, cap)
-        if name == "grid64":
-            reqs = []
-            for s in sizes:
-                ins = int(s) // 2
-                b = st.next_batch(ins, int(s) - ins)
-                reqs.append((b.u, b.v, b.w, b.op))
-        else:
-            total = int(sizes.sum())
-            big = st.next_batch(total // 2, total - total // 2)
-            reqs = _split_requests(big, sizes)
-        graphs.append((name, wl, reqs))
+        points = []
+        for _ in range(len(loads) + 1):  # one stream per load point, plus one for the capacity runs
+            _, sizes = W.serving_arrivals(per_graph, 1.0, arr_rng)
+            sizes = np.minimum(sizes, cap)
+            if name == "grid64":
+                reqs = []
+                for sz in sizes:
+                    ins = int(sz) // 2
+                    b = st.next_batch(ins, int(sz) - ins)
+                    reqs.append((b.u, b.v, b.w, b.op))
+            else:
+                total = int(sizes.sum())
+                big = st.next_batch(total // 2, total - total // 2)
+                reqs = _split_requests(big, sizes)
+            points.append(reqs)
+        graphs.append((name, wl, points))
 
     def load(ctx, wl):
         g = ctx.load_graph(wl.n, wl.a, wl.b, wl.w)
         g.init_sparsifier(wl.a[wl.h_ids], wl.b[wl.h_ids])
         return g
 
-    # batched capacity per graph, on its own copy (first requests, sequential)
-    cap_ups = {}
-    for name, wl, reqs in graphs:
+    # batched capacity per graph alone, on its own copy (the first stream, sequential)
+    cap_ups, shapes = {}, {}
+    for name, wl, points in graphs:
         ctx = D.Context()
         g = load(ctx, wl)
+        g.prepare(50_000)
+        reqs = points[-1]
+        big = max(range(len(reqs)), key=lambda k: len(reqs[k][0]))
         done, t_tot = 0, 0.0
-        for r in reqs[:3]:  # warm-up: workspace, captured steps, autotuner
-            g.apply(D.make_updates(*r))
-        for r in reqs[3: min(15, len(reqs))]:
+        for k, r in enumerate(reqs):
             ups = D.make_updates(*r)
             t0 = time.perf_counter()
             g.apply(ups)
             dt = time.perf_counter() - t0
-            done += len(ups)
-            t_tot += dt
+            if k >= 3 and k != big:  # warm-up requests and the autotuned one aside
+                done += len(ups)
+                t_tot += dt
+        st_ = g.stats()
+        shapes[name] = (st_["walk_block"], st_["walk_ilp"], st_["walk_refill"])
         cap_ups[name] = done / t_tot
         ctx.close()
 
-    # the served stream
+    # the served streams, one load point after the other on the same resident graphs
     ctx = D.Context()
-    gs = {name: load(ctx, wl) for name, wl, _ in graphs}
-    schedule = []
-    for name, _, reqs in graphs:
-        mean = float(np.mean([len(r[0]) for r in reqs]))
-        lam = args.load * cap_ups[name] / len(graphs) / mean  # requests / s (the GPU is shared)
-        t = np.cumsum(arr_rng.exponential(1.0 / lam, size=len(reqs)))
-        for k, r in enumerate(reqs):
-            schedule.append((float(t[k]), name, k, D.make_updates(*r)))
-    schedule.sort(key=lambda x: x[0])
-    tickets = []
-    t_start = time.perf_counter()
-    for at, name, k, ups in schedule:
-        delay = at - (time.perf_counter() - t_start)
-        if delay > 0:
-            time.sleep(delay)
-        tickets.append((name, k, len(ups)) + gs[name].submit(ups))
-    lat, units = [], 0
-    for name, k, nu, ticket, _res in tickets:
-        res, ms = gs[name].wait(ticket, timeout_ms=600000)
-        lat.append(ms)
-        units += int((res["status"] == 0).sum())
-    wall = time.perf_counter() - t_start
+    gs = {}
+    for name, wl, _ in graphs:
+        g = load(ctx, wl)
+        blk, ilp, refill = shapes[name]
+        g.set_walk_shape(blk, ilp, 0, refill)
+        g.prepare(50_000)
+        gs[name] = g
+    out = {"loads": {}, "capacity_updates_per_s": cap_ups,
+           "graphs": {n: {"n": wl.n, "m": wl.m} for n, wl, _ in graphs}}
+    for pi, lf in enumerate(loads):
+        schedule = []
+        for name, _, points in graphs:
+            reqs = points[pi]
+            mean = float(np.mean([len(r[0]) for r in reqs]))
+            lam = lf * cap_ups[name] / len(graphs) / mean  # requests / s (the GPU is shared)
+            t = np.cumsum(arr_rng.exponential(1.0 / lam, size=len(reqs)))
+            for k, r in enumerate(reqs):
+                schedule.append((float(t[k]), name, D.make_updates(*r)))
+        schedule.sort(key=lambda x: x[0])
+        tickets = []
+        t_start = time.perf_counter()
+        for at, name, ups in schedule:
+            delay = at - (time.perf_counter() - t_start)
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append((name, len(ups)) + gs[name].submit(ups))
+        rows, units = [], 0
+        for name, nu, ticket, _res in tickets:
+            res, ms, qms = gs[name].wait_ex(ticket, timeout_ms=600000)
+            rows.append((name, nu, ms, qms))
+            units += int((res["status"] == 0).sum())
+        wall = time.perf_counter() - t_start
+        lat = [r[2] for r in rows]
+        point = {"requests": len(rows), "updates_per_s": units / wall, "offered_load": lf,
+                 "latency_ms": _pcts(lat), "queue_ms": _pcts([r[3] for r in rows]),
+                 "per_graph": {n: {"latency_ms": _pcts([r[2] for r in rows if r[0] == n]),
+                                   "queue_ms": _pcts([r[3] for r in rows if r[0] == n])} for n in gs},
+                 "per_size": {f"{lo}-{hi}": _pcts([r[2] for r in rows if lo <= r[1] <= hi])
+                              for lo, hi in SIZE_BUCKETS}}
+        out["loads"][str(lf)] = point
     ctx.close()
 
-    # the one-launch-per-update form on a sample of the mesh requests
-    name, wl, reqs = graphs[1]
+    # the one-launch-per-update form on a sample of the mesh requests (its first stream)
+    name, wl, points = graphs[1]
     ctx = D.Context(walk_mode="per_update", cuda_graphs=False)
     g = load(ctx, wl)
     pu_lat, pu_units = [], 0
-    for r in reqs[:6]:
+    for r in points[-1][:per_update_sample]:
         ups = D.make_updates(*r)
         t0 = time.perf_counter()
         res = g.apply(ups)
         pu_lat.append(1e3 * (time.perf_counter() - t0))
         pu_units += int((res["status"] == 0).sum())
     ctx.close()
+    out["per_update_form"] = {"graph": "mesh100", "requests": len(pu_lat),
+                              "updates_per_s": pu_units / (sum(pu_lat) / 1e3),
+                              "latency_ms": _pcts(pu_lat)}
+    return out
 
+
+def run_serve(args):
+    """--workload serve: the serving configuration at offered loads of 30, 60
+    and 90 % of capacity, --requests per load point."""
+    r = serve_experiment((0.3, 0.6, 0.9), args.requests)
+    mid = r["loads"]["0.6"]
     line = {"metric": "serving: updates/s and p50/p99 request latency", "workload": "serve",
-            "value": units / wall, "unit": "updates/s", "n_gpus": 1, "requests": len(tickets),
-            "offered_load": args.load, "offered_per_graph": "load x capacity alone / 3 (one GPU shared)",
-            "capacity_updates_per_s": cap_ups,
-            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                           "max": float(np.max(lat))},
-            "graphs": {n: {"n": wl.n, "m": wl.m, "requests": len(r)} for n, wl, r in graphs},
-            "per_update_form": {"graph": "mesh100", "requests": len(pu_lat),
-                                "updates_per_s": pu_units / (sum(pu_lat) / 1e3),
-                                "p50_ms": float(np.percentile(pu_lat, 50)), "p99_ms": float(np.percentile(pu_lat, 99))},
-            "dtype": "f64", "data": "synthetic"}
+            "value": mid["updates_per_s"], "unit": "updates/s", "n_gpus": 1, "requests_per_point": args.requests,
+            "offered_per_graph": "load x capacity alone / 3 (one GPU shared)",
+            "latency_ms": mid["latency_ms"], "points": r, "dtype": "f64", "data": "synthetic"}
     print(json.dumps(line), flush=True)
 
 
@@ -394,8 +457,9 @@ def main():
                     help="rmat (default line), mesh, fea, or serve (several graphs resident, Poisson arrivals)")
     ap.add_argument("--rmat-scale", type=int, default=22, help="rmat: log2 of the vertex count")
     ap.add_argument("--rmat-edges", type=int, default=64_000_000, help="rmat: distinct undirected edges")
-    ap.add_argument("--load", type=float, default=0.6, help="serve: offered load as a fraction of capacity")
-    ap.add_argument("--requests", type=int, default=1000, help="serve: requests in the measured stream")
+    ap.add_argument("--requests", type=int, default=1000, help="serve: requests per load point")
+    ap.add_argument("--serve-requests", type=int, default=1000,
+                    help="requests of the serving summary in the default line (0: skip it)")
     args = ap.parse_args()
     if args.impl == "reference":
         if args.workload == "serve":
@@ -571,6 +635,16 @@ def main():
                        "peak_steps_per_s": peak * 1e9 / SECTOR_BYTES_PER_STEP,
                        "frac": steps_per_launch / avg_walk_s / (peak * 1e9 / SECTOR_BYTES_PER_STEP)}}
 
+    serving = None
+    if rank == 0 and args.serve_requests > 0:
+        r = serve_experiment((0.6,), args.serve_requests)
+        pt = r["loads"]["0.6"]
+        serving = {"offered_load": 0.6, "requests": pt["requests"], "updates_per_s": pt["updates_per_s"],
+                   "latency_ms": pt["latency_ms"], "queue_ms": pt["queue_ms"],
+                   "per_graph_p99_ms": {n: v["latency_ms"]["p99"] for n, v in pt["per_graph"].items()},
+                   "per_update_form": r["per_update_form"],
+                   "graphs": "grid 64x64, mesh 100^3, FEA 2048^2 resident together (--workload serve: 30/60/90 %)"}
+
     cpu = cpu_all = None
     if rank == 0 and not args.no_cpu:
         cpu, cpu_all = oracle_baseline(wl, batches, args.cpu_budget)
@@ -600,6 +674,7 @@ def main():
             "roofline": roof,
             "roofline_full_walks": full,
             "cpu_baseline": cpu,
+            "serving": serving,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clocks,

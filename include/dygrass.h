@@ -344,6 +344,18 @@ dg_status dg_submit_updates(dg_ctx* ctx, int32_t graph_id, int64_t nu, const dg_
    *latency_ms (nullable) receives submit-to-completion time. */
 dg_status dg_wait(dg_ctx* ctx, uint64_t ticket, int32_t timeout_ms, double* latency_ms);
 
+/* dg_wait that also reports, in *queue_ms (nullable), the part of the latency the
+   request spent queued before a worker started it (behind earlier requests of its
+   graph, or waiting for the HBM budget). */
+dg_status dg_wait_ex(dg_ctx* ctx, uint64_t ticket, int32_t timeout_ms, double* latency_ms, double* queue_ms);
+
+/* Prepare a graph for batches (or served requests) of up to max_batch updates:
+   sizes its batch workspace and pinned staging and, with CUDA graphs on,
+   captures the batch step of every size class up to max_batch, so that no later
+   batch pays for them.  The walk-shape autotuner still runs on the first batch
+   of >= 4096 updates unless a shape was set with dg_set_walk_shape. */
+dg_status dg_prepare(dg_ctx* ctx, int32_t graph_id, int64_t max_batch);
+
 /*
  * Allocation-free walk estimate.  The paper has no counterpart: this entry
  * point exists for callers of this library that must not allocate device

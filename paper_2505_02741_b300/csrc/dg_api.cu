@@ -107,6 +107,7 @@ static void worker_loop(Ctx* c) {
                 c->scv.wait(lk);
             }
             c->busy[rq->gid] = true;
+            rq->t_start = now_ms();
             c->in_flight_bytes += rq->need_bytes;
         }
         dg_status st = DG_OK;
@@ -521,6 +522,15 @@ dg_status dg_shard_commit(dg_ctx* ctx, int32_t gid, uint64_t nrec, const void* r
     });
 }
 
+dg_status dg_prepare(dg_ctx* ctx, int32_t gid, int64_t max_batch) {
+    return guarded(ctx, [&]() {
+        Ctx& c = C(ctx);
+        DGraph& g = c.graph(gid);
+        std::lock_guard<std::mutex> lk(g.mu);
+        graph_prepare(c, g, max_batch, c.stream);
+    });
+}
+
 dg_status dg_debug_set_wait_limit(dg_ctx* ctx, int64_t polls) {
     return guarded(ctx, [&]() {
         Ctx& c = C(ctx);
@@ -568,6 +578,10 @@ dg_status dg_submit_updates(dg_ctx* ctx, int32_t gid, int64_t nu, const dg_updat
 }
 
 dg_status dg_wait(dg_ctx* ctx, uint64_t ticket, int32_t timeout_ms, double* latency_ms) {
+    return dg_wait_ex(ctx, ticket, timeout_ms, latency_ms, nullptr);
+}
+
+dg_status dg_wait_ex(dg_ctx* ctx, uint64_t ticket, int32_t timeout_ms, double* latency_ms, double* queue_ms) {
     dg_status inner = DG_OK;
     dg_status outer = guarded(ctx, [&]() {
         Ctx& c = C(ctx);
@@ -579,6 +593,7 @@ dg_status dg_wait(dg_ctx* ctx, uint64_t ticket, int32_t timeout_ms, double* late
         if (!c.dcv.wait_for(lk, std::chrono::milliseconds(tmo), [&] { return rq->done; }))
             throw Error(DG_E_TIMEOUT, "request not finished within timeout");
         if (latency_ms) *latency_ms = rq->t_done - rq->t_submit;
+        if (queue_ms) *queue_ms = (rq->t_start > 0.0 ? rq->t_start : rq->t_done) - rq->t_submit;
         inner = rq->status;
         if (inner != DG_OK) t_last_error = rq->error;
         c.tickets.erase(it);

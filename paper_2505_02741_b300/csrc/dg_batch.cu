@@ -375,7 +375,7 @@ uint64_t BatchWS::bytes() const {
     b += gscan.bytes() + gcount.bytes() + hflag.bytes() + hpos.bytes() + hvals.bytes() + hcount.bytes();
     b += gkind.bytes() + ghrem.bytes() + kind_del.bytes() + gw.bytes() + vtab.bytes();
     b += t_u.bytes() + t_v.bytes() + t_idx.bytes() + t_kstar.bytes() + t_count.bytes() + meta.bytes();
-    b += t_fin.bytes() + t_queue.bytes() + qctr.bytes() + cp.bytes() + step_v.bytes() + step_e.bytes();
+    b += t_fin.bytes() + t_queue.bytes() + qctr.bytes() + cp.bytes() + step_r.bytes() + step_e.bytes();
     b += t_wpq.bytes() + t_rmax.bytes() + recR.bytes() + t_kind.bytes() + best.bytes();
     b += ckeys.bytes() + ckeys_alt.bytes() + ck2.bytes() + cvals.bytes() + cvals_alt.bytes() + chist.bytes();
     b += cscan.bytes() + ccount.bytes() + cflag.bytes() + cpos.bytes() + cv2.bytes() + ccount2.bytes();
@@ -464,13 +464,14 @@ static void ensure_ws(Ctx& c, DGraph& g, uint32_t b_max, cudaStream_t st) {
     w.t_queue.ensure(a, B, st);
     w.qctr.ensure(a, 2, st);
     // Step records of deletion walkers replace the resume points (no replay
-    // at finalization) while they fit in STEP_REC_BYTES: B * T * s words each.
-    constexpr uint64_t STEP_REC_BYTES = 4ull << 30;
-    if ((uint64_t)B * T * s * 8 <= STEP_REC_BYTES) {
-        w.step_v.ensure(a, (size_t)B * T * s, st);
+    // at finalization) while they fit in STEP_REC_BYTES: 12 bytes per slot of
+    // B * T * s.
+    constexpr uint64_t STEP_REC_BYTES = 6ull << 30;
+    if ((uint64_t)B * T * s * 12 <= STEP_REC_BYTES) {
+        w.step_r.ensure(a, (size_t)B * T * s, st);
         w.step_e.ensure(a, (size_t)B * T * s, st);
     } else {  // records of a smaller workspace must not be used at this size
-        w.step_v.release(a, st);
+        w.step_r.release(a, st);
         w.step_e.release(a, st);
         if (walk_ncp(T) > 0) w.cp.ensure(a, (size_t)B * s * walk_ncp(T), st);
     }
@@ -834,7 +835,7 @@ void graph_release_ws(Ctx& c, DGraph& g, cudaStream_t st) {
     REL(vvals_alt); REL(vhist); REL(vscan); REL(wkind); REL(fin_w); REL(wflag); REL(wpos); REL(wflag2); REL(wpos2); REL(gkeys);
     REL(gkeys_alt); REL(hkeys); REL(gvals); REL(gvals_alt); REL(ghist); REL(gscan); REL(gcount); REL(hflag);
     REL(hpos); REL(hvals); REL(hcount); REL(gkind); REL(ghrem); REL(kind_del); REL(gw); REL(t_u); REL(t_v);
-    REL(t_idx); REL(t_kstar); REL(t_fin); REL(t_queue); REL(qctr); REL(cp); REL(step_v); REL(step_e); REL(t_count); REL(meta); REL(t_wpq); REL(t_rmax); REL(recR); REL(t_kind); REL(best);
+    REL(t_idx); REL(t_kstar); REL(t_fin); REL(t_queue); REL(qctr); REL(cp); REL(step_r); REL(step_e); REL(t_count); REL(meta); REL(t_wpq); REL(t_rmax); REL(recR); REL(t_kind); REL(best);
     REL(ckeys); REL(ckeys_alt); REL(ck2); REL(cvals); REL(cvals_alt); REL(chist); REL(cscan); REL(ccount);
     REL(cflag); REL(cpos); REL(cv2); REL(ccount2); REL(cw); REL(kind_ins); REL(path_buf); REL(path_w); REL(path_len); REL(fb_list); REL(fb_count); REL(fb_slot); REL(fb_big); REL(fb_cbase); REL(fb_dslot); REL(fb_py); REL(fb_pr); REL(fb_pw); REL(dbg_reason);
     REL(dbg_steps); REL(dbg_paths); REL(shard_recs);
@@ -901,9 +902,9 @@ static FinArgs fin_of(Ctx& c, BatchWS& w, bool on) {
     f.fin_w = w.fin_w.p;
     f.c = cands_of(w);
     f.pb = paths_of(w);
-    f.pv = on ? w.step_v.p : nullptr;
+    f.pr = on ? w.step_r.p : nullptr;
     f.pe = on ? w.step_e.p : nullptr;
-    f.cp = (on && !f.pv) ? w.cp.p : nullptr;
+    f.cp = (on && !f.pr) ? w.cp.p : nullptr;
     f.cp_shift = walk_cp_shift((uint32_t)c.cfg.T);
     f.ncp = walk_ncp((uint32_t)c.cfg.T);
     f.on = on ? 1u : 0u;
@@ -1335,6 +1336,57 @@ static void ensure_headroom(Ctx& c, DGraph& g, uint32_t nu, cudaStream_t st) {
     }
 }
 
+// The whole batch step for batches of size class `bucket`, captured once as a
+// CUDA graph (again whenever a buffer it names has moved).  direct: the
+// update records reach the workspace outside the graph (device or pinned
+// caller buffers); otherwise the graph copies them from the pinned staging.
+static CapturedStep& capture_step(Ctx& c, DGraph& g, uint32_t bucket, bool direct, cudaStream_t st) {
+    BatchWS& w = g.ws;
+    CapturedStep& cs = g.steps[bucket];
+    if (cs.exec && cs.layout_gen == g.layout_gen && cs.device_io == direct) return cs;
+    if (cs.exec) cudaGraphExecDestroy(cs.exec);
+    cs.exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    const uint64_t k0 = g_launches;
+    DG_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    try {
+        DG_CUDA(cudaMemcpyAsync(w.hdr.p, g.hs.hdr, sizeof(BatchHdr), cudaMemcpyHostToDevice, st));
+        if (!direct)
+            DG_CUDA(cudaMemcpyAsync(w.ups.p, g.hs.ups, sizeof(dg_update) * bucket, cudaMemcpyHostToDevice, st));
+        enqueue_mutate(c, g, st);
+        const bool emitted = enqueue_walks(c, g, st, -1);
+        enqueue_commit(c, g, st, emitted, true);
+        if (!direct)
+            DG_CUDA(cudaMemcpyAsync(g.hs.res, w.res.p, sizeof(dg_update_result) * bucket, cudaMemcpyDeviceToHost,
+                                    st));
+        enqueue_readback(g, st);
+    } catch (...) {
+        cudaStreamEndCapture(st, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        throw;
+    }
+    DG_CUDA(cudaStreamEndCapture(st, &graph));
+    DG_CUDA(cudaGraphInstantiate(&cs.exec, graph, 0));
+    cudaGraphDestroy(graph);
+    cs.layout_gen = g.layout_gen;
+    cs.device_io = direct;
+    cs.kernels = g_launches - k0;
+    g_launches = k0;  // counted per replay
+    return cs;
+}
+
+void graph_prepare(Ctx& c, DGraph& g, int64_t max_batch, cudaStream_t st) {
+    if (!g.has_h) throw Error(DG_E_STATE, "no sparsifier");
+    if (g.shard.active) throw Error(DG_E_STATE, "a sharded batch is in progress on this graph");
+    if (max_batch < 1 || max_batch > (1ll << 26)) throw Error(DG_E_INVALID, "max_batch out of range");
+    const uint32_t top = bucket_of((uint64_t)max_batch);
+    ensure_ws(c, g, top, st);
+    ensure_headroom(c, g, (uint32_t)max_batch, st);
+    if (c.cfg.use_graphs && !c.cfg.record && c.cfg.walk_mode == DG_WALK_BATCHED)
+        for (uint32_t b = 1024; b <= top; b <<= 1) capture_step(c, g, b, false, st);
+    wait_stream(c, st);
+}
+
 void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_update_result* res, bool device_io,
                  cudaStream_t st) {
     if (!g.has_h) throw Error(DG_E_STATE, "no sparsifier");
@@ -1408,37 +1460,7 @@ void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_updat
         finish_eager(true);
     } else if (use_graph) {
         if (direct) DG_CUDA(cudaMemcpyAsync(w.ups.p, ups, sizeof(dg_update) * nu, kin, st));
-        CapturedStep& cs = g.steps[bucket];
-        if (!cs.exec || cs.layout_gen != g.layout_gen || cs.device_io != direct) {
-            if (cs.exec) cudaGraphExecDestroy(cs.exec);
-            cs.exec = nullptr;
-            cudaGraph_t graph = nullptr;
-            const uint64_t k0 = g_launches;
-            DG_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-            try {
-                DG_CUDA(cudaMemcpyAsync(w.hdr.p, g.hs.hdr, sizeof(BatchHdr), cudaMemcpyHostToDevice, st));
-                if (!direct)
-                    DG_CUDA(cudaMemcpyAsync(w.ups.p, g.hs.ups, sizeof(dg_update) * bucket, cudaMemcpyHostToDevice, st));
-                enqueue_mutate(c, g, st);
-                const bool emitted = enqueue_walks(c, g, st, -1);
-                enqueue_commit(c, g, st, emitted, true);
-                if (!direct)
-                    DG_CUDA(cudaMemcpyAsync(g.hs.res, w.res.p, sizeof(dg_update_result) * bucket,
-                                            cudaMemcpyDeviceToHost, st));
-                enqueue_readback(g, st);
-            } catch (...) {
-                cudaStreamEndCapture(st, &graph);
-                if (graph) cudaGraphDestroy(graph);
-                throw;
-            }
-            DG_CUDA(cudaStreamEndCapture(st, &graph));
-            DG_CUDA(cudaGraphInstantiate(&cs.exec, graph, 0));
-            cudaGraphDestroy(graph);
-            cs.layout_gen = g.layout_gen;
-            cs.device_io = direct;
-            cs.kernels = g_launches - k0;
-            g_launches = k0;  // counted per replay below
-        }
+        CapturedStep& cs = capture_step(c, g, bucket, direct, st);
         DG_CUDA(cudaGraphLaunch(cs.exec, st));
         g_launches += cs.kernels;
         if (direct && res)

@@ -66,7 +66,8 @@ struct BatchWS {
     DBuf<uint32_t> t_u, t_v, t_idx, t_kstar, t_count, meta;
     DBuf<uint32_t> t_fin, t_queue, qctr;  // finalization inside the walk: per-update counts, queue, cursors
     DBuf<uint4> cp;                       // deletion walkers' resume points (walk_ncp(T) per walker)
-    DBuf<uint32_t> step_v, step_e;        // deletion walkers' step records (when they fit the budget below)
+    DBuf<double> step_r;                  // deletion walkers' step records: resistance after the step,
+    DBuf<uint32_t> step_e;                //   entry taken (when they fit the budget below)
     DBuf<double> t_wpq, recR;
     DBuf<uint64_t> t_rmax;
     DBuf<uint8_t> t_kind;
@@ -170,6 +171,11 @@ void graph_shard_begin(Ctx& c, DGraph& g, int64_t nu, const dg_update* ups, int3
                        cudaStream_t st, uint64_t* nrec_out);
 void graph_shard_export(Ctx& c, DGraph& g, ShardRec* host, uint64_t cap, uint64_t* n_out);
 void graph_shard_commit(Ctx& c, DGraph& g, const ShardRec* recs, uint64_t nrec, dg_update_result* res);
+
+// Size the batch workspace and pinned staging for batches of up to max_batch
+// updates and capture the batch step of every size class up to it, so that
+// later batches (served requests of any size) find them ready.
+void graph_prepare(Ctx& c, DGraph& g, int64_t max_batch, cudaStream_t st);
 
 // the two halves of the ordering against walk estimates (see DGraph::ev_est)
 void graph_wait_estimates(DGraph& g, cudaStream_t st);

@@ -18,6 +18,7 @@ struct Request {
     dg_update_result* res = nullptr;
     uint64_t need_bytes = 0;
     double t_submit = 0.0;
+    double t_start = 0.0;  // a worker took it (admitted)
     double t_done = 0.0;
     dg_status status = DG_OK;
     bool done = false;

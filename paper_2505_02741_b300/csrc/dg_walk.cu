@@ -127,46 +127,44 @@ __device__ __forceinline__ void add_totals(BatchCounters* ctr, const UpdTotals& 
 // First step of deletion walker k of walked update j whose resistance exceeds
 // rbar, the update's minimum (the walker's recorded resistance is above it, so
 // that step exists): the exact pruned step count, whatever moment the walker
-// itself was cut at.  The partial sums are formed again in walk order, each
-// addition rounded on its own, from the entries the walker took (step records,
-// pe non-null) or from its Philox counters replayed on G_b; both give the
-// walker's own sums bit for bit.  0 and ERR_INTERNAL if the sums never pass
-// rbar (records inconsistent with the walk).
+// itself was cut at.  With step records (pr non-null) the walker's own
+// partial sums are searched: its last step first (a walker is usually cut at
+// the step where it passes rbar), then a binary search (the sums increase).
+// Without them the partial sums are formed again from its Philox counters on
+// G_b, in walk order with one rounding per addition, as the walker did.  0 and
+// ERR_INTERNAL if the sums never pass rbar (records inconsistent with the walk).
 __device__ uint32_t del_cross_step(uint32_t j, uint32_t k, uint32_t steps, double rbar, const CSRView& G,
-                                   const WalkTasks& t, const WalkParams& p, const uint32_t* pe, uint64_t id0,
+                                   const WalkTasks& t, const WalkParams& p, const double* pr, uint64_t id0,
                                    uint32_t* d_err) {
-    double R = 0.0;
-    if (pe) {
-        constexpr uint32_t U = 4;  // entry loads in flight per round
+    if (pr) {
+        // pr[base + q * s] = resistance after step q + 1; the one after step `steps` exceeds rbar
         const size_t base = (size_t)j * p.T * p.s + k;
-        for (uint32_t s0 = 0; s0 < steps; s0 += U) {
-            uint32_t e[U];
-            double r[U];
-#pragma unroll
-            for (uint32_t q = 0; q < U; ++q) e[q] = s0 + q < steps ? __ldcg(&pe[base + (size_t)(s0 + q) * p.s]) : 0u;
-#pragma unroll
-            for (uint32_t q = 0; q < U; ++q) r[q] = (s0 + q < steps && (uint64_t)e[q] < G.pool_cap) ? G.pool[e[q]].r : 0.0;
-#pragma unroll
-            for (uint32_t q = 0; q < U; ++q) {
-                if (s0 + q >= steps) break;
-                R = __dadd_rn(R, r[q]);
-                if (R > rbar) return s0 + q + 1;
-            }
+        if (steps == 0 || !(__ldcg(&pr[base + (size_t)(steps - 1) * p.s]) > rbar)) {
+            atomicOr(d_err, (uint32_t)ERR_INTERNAL);
+            return 0;
         }
-    } else {
-        const uint64_t id = id0 + t.idx[j];
-        const uint32_t ulo = (uint32_t)id, uhi = (uint32_t)(id >> 32);
-        const uint32_t u = t.u[j];
-        uint32_t cv = u, off = G.off[u], deg = G.deg[u], prev = NONE;
-        bool pid = false;
-        for (uint32_t s = 0; s < steps; ++s) {
-            const uint32_t x = philox_word0(s, k, ulo, uhi, p.key0, p.key1);
-            uint4 h;
-            double2 tl;
-            if (nb_step(G, x, cv, off, deg, prev, pid, h, tl) <= 0) break;
-            R = __dadd_rn(R, tl.x);
-            if (R > rbar) return s + 1;
+        if (steps == 1 || !(__ldcg(&pr[base + (size_t)(steps - 2) * p.s]) > rbar)) return steps;
+        uint32_t lo = 0, hi = steps - 2;  // the first q with pr > rbar lies in [lo, hi]
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (__ldcg(&pr[base + (size_t)mid * p.s]) > rbar) hi = mid;
+            else lo = mid + 1;
         }
+        return lo + 1;
+    }
+    double R = 0.0;
+    const uint64_t id = id0 + t.idx[j];
+    const uint32_t ulo = (uint32_t)id, uhi = (uint32_t)(id >> 32);
+    const uint32_t u = t.u[j];
+    uint32_t cv = u, off = G.off[u], deg = G.deg[u], prev = NONE;
+    bool pid = false;
+    for (uint32_t s = 0; s < steps; ++s) {
+        const uint32_t x = philox_word0(s, k, ulo, uhi, p.key0, p.key1);
+        uint4 h;
+        double2 tl;
+        if (nb_step(G, x, cv, off, deg, prev, pid, h, tl) <= 0) break;
+        R = __dadd_rn(R, tl.x);
+        if (R > rbar) return s + 1;
     }
     atomicOr(d_err, (uint32_t)ERR_INTERNAL);
     return 0;
@@ -185,7 +183,7 @@ __device__ uint32_t del_cross_step(uint32_t j, uint32_t k, uint32_t steps, doubl
 // with or without pruning.
 __device__ int reduce_update(uint32_t j, int lane, const WalkTasks& t, const WalkParams& p, const WalkRecs& r,
                              dg_update_result* res, int32_t* best, int32_t* dbg_reason, int32_t* dbg_steps,
-                             UpdTotals& tot, uint32_t& nh_out, const CSRView& G, const uint32_t* pe, uint64_t id0,
+                             UpdTotals& tot, uint32_t& nh_out, const CSRView& G, const double* pr, uint64_t id0,
                              uint32_t* d_err) {
     const bool ins = t.kind[j] == WALK_INS;
     const bool ee = ins && p.early_exit;
@@ -244,7 +242,7 @@ __device__ int reduce_update(uint32_t j, int lane, const WalkTasks& t, const Wal
             rs = R_CUT;
         }
         if (prune && __ldcg(&Rr[k]) > bR) {
-            st = del_cross_step(j, k, st, bR, G, t, p, pe, id0, d_err);
+            st = del_cross_step(j, k, st, bR, G, t, p, pr, id0, d_err);
             rs = R_CUT;
         }
         tsum += st;
@@ -419,9 +417,13 @@ __device__ bool path_from_records(uint32_t j, int32_t b, int lane, const CSRView
     if (lane == 0) path[0] = u;
     for (uint32_t q = lane; ok && q < steps; q += 32) {
         const size_t rec = ((size_t)j * p.T + q) * p.s + (uint32_t)b;
-        const uint32_t x = __ldcg(&f.pv[rec]);
         const uint32_t e = __ldcg(&f.pe[rec]);
-        if (x >= n || (uint64_t)e >= G.pool_cap) {
+        if ((uint64_t)e >= G.pool_cap) {
+            ok = false;
+            break;
+        }
+        const uint32_t x = G.pool[e].nbr;
+        if (x >= n) {
             ok = false;
             break;
         }
@@ -567,7 +569,7 @@ __device__ bool fallback_warp(uint32_t j, int lane, const CSRView& H, const CSRV
 __device__ void finalize_update(uint32_t j, int lane, const WalkKernelArgs& a, UpdTotals& tot, uint32_t* sbuf) {
     uint32_t nh = 0;
     const int bk = reduce_update(j, lane, a.t, a.p, a.r, a.f.res, a.f.best, a.f.dbg_reason, a.f.dbg_steps, tot, nh,
-                                 a.G, a.f.pe, a.hdr->id0, a.d_err);
+                                 a.G, a.f.pr, a.hdr->id0, a.d_err);
     const uint32_t i = a.t.idx[j];
     Cands c = a.f.c;
     if (a.t.kind[j] == WALK_INS) {
@@ -579,7 +581,7 @@ __device__ void finalize_update(uint32_t j, int lane, const WalkKernelArgs& a, U
     }
     if (bk >= 0) {
         bool ok = false;
-        if (a.f.pv) {
+        if (a.f.pr) {
             ok = path_from_records(j, bk, lane, a.G, a.t, a.p, a.r, a.f.pb, a.f, a.d_err);
         } else if (a.f.cp) {
             ok = replay_path_warp(j, bk, lane, a.G, a.t, a.p, a.r, a.hdr->id0, a.f.pb, a.f, a.d_err);
@@ -950,12 +952,12 @@ __global__ void __launch_bounds__(256, (ILP == 1 ? 4 : (ILP == 2 ? 3 : 1))) k_wa
             // the next load goes out first, the rest of the step follows it
             const bool at_q = v.c == v.q;
             fly[i] = !at_q && v.steps < a.p.T && lean_issue<HUBS>(v, a, h[i], r[i], ks[i], at[i]);
-            if (a.f.pv && !v.ins) {
+            v.R = __dadd_rn(v.R, r_step);
+            if (a.f.pr && !v.ins) {
                 const size_t rec = ((size_t)v.j * a.p.T + v.steps - 1) * a.p.s + v.k;
-                a.f.pv[rec] = v.c;
+                a.f.pr[rec] = v.R;
                 a.f.pe[rec] = took;
             }
-            v.R = __dadd_rn(v.R, r_step);
             if (a.r.paths) a.r.paths[((size_t)v.j * a.p.s + v.k) * (a.p.T + 1) + v.steps] = (int32_t)v.c;
             if (a.f.cp && !v.ins && (v.steps & ((1u << a.f.cp_shift) - 1u)) == 0u) {
                 const uint32_t q = (v.steps >> a.f.cp_shift) - 1u;

@@ -133,10 +133,11 @@ struct FinArgs {
     uint4* cp;
     uint32_t cp_shift, ncp;
     // step records of deletion walkers (nullable; when present no resume
-    // points are kept): the vertex reached at each step and the pool index of
-    // the entry taken, at [(j * T + step) * s + walker] (the walkers of one
-    // update side by side, so a warp's records of one step are contiguous)
-    uint32_t* pv;
+    // points are kept): the resistance accumulated after each step and the
+    // pool index of the entry taken (which names the vertex reached), at
+    // [(j * T + step) * s + walker] (the walkers of one update side by side,
+    // so a warp's records of one step are contiguous)
+    double* pr;
     uint32_t* pe;
     uint32_t on;          // 0: records only (reduction and emission run as separate kernels)
     uint32_t spin_limit;  // polls of the finalize queue before ERR_SPIN (FIN_SPIN_LIMIT unless set for tests)

@@ -45,7 +45,8 @@ EXPORTS = ("dg_config_default", "dg_create", "dg_destroy", "dg_status_str", "dg_
            "dg_query_sparsifier", "dg_query_graph", "dg_get_batch_stats", "dg_get_walker_records", "dg_compact",
            "dg_graph_bytes", "dg_launch_count", "dg_set_next_update_id", "dg_get_next_update_id",
            "dg_set_walk_shape", "dg_set_walk_refill", "dg_submit_updates", "dg_wait", "dg_walk_estimate_noalloc",
-           "dg_debug_set_wait_limit", "dg_shard_begin", "dg_shard_export", "dg_shard_commit")
+           "dg_debug_set_wait_limit", "dg_shard_begin", "dg_shard_export", "dg_shard_commit", "dg_wait_ex",
+           "dg_prepare")
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -122,6 +123,8 @@ def load_library(path: str | None = None):
         "dg_shard_begin": (i32, [P, i32, i64, P, i32, i32, P, C.POINTER(u64)]),
         "dg_shard_export": (i32, [P, i32, P, u64, C.POINTER(u64)]),
         "dg_shard_commit": (i32, [P, i32, u64, P, P]),
+        "dg_wait_ex": (i32, [P, u64, i32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+        "dg_prepare": (i32, [P, i32, i64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -228,6 +231,12 @@ class Context:
         rc = self._lib.dg_wait(self._h, int(ticket), int(timeout_ms), C.byref(lat))
         _check(rc)
         return lat.value
+
+    def wait_ex(self, ticket, timeout_ms=-1):
+        """(latency_ms, queue_ms) of a served request."""
+        lat, q = C.c_double(), C.c_double()
+        _check(self._lib.dg_wait_ex(self._h, int(ticket), int(timeout_ms), C.byref(lat), C.byref(q)))
+        return lat.value, q.value
 
 
 class Graph:
@@ -375,3 +384,13 @@ class Graph:
         lat = self.ctx.wait(ticket, timeout_ms)
         ups, res = self._keep.pop(ticket)
         return res, lat
+
+    def wait_ex(self, ticket, timeout_ms=-1):
+        """(results, latency_ms, queue_ms) of a served request."""
+        lat, q = self.ctx.wait_ex(ticket, timeout_ms)
+        ups, res = self._keep.pop(ticket)
+        return res, lat, q
+
+    def prepare(self, max_batch: int):
+        """Size the workspace and capture the batch steps for batches up to max_batch."""
+        _check(self._L.dg_prepare(self.ctx._h, self.gid, int(max_batch)))

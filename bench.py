@@ -34,6 +34,7 @@ import argparse
 import json
 import os
 import platform
+import shutil
 import subprocess
 import sys
 import threading
@@ -106,6 +107,7 @@ class ClockSampler:
         self._stop = threading.Event()
         self._t = None
         self._proc = None
+        self.at_exit = False
         self._nvml = None
         try:
             import pynvml as N
@@ -150,9 +152,13 @@ class ClockSampler:
             self._t = threading.Thread(target=self._run_nvml, daemon=True)
         else:
             try:
-                self._proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                                               "--format=csv,noheader,nounits", "-lms", "20"],
-                                              stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                # line-buffered, so each sample reaches the pipe when it is taken
+                cmd = ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                       "--format=csv,noheader,nounits", "-lms", "20"]
+                if shutil.which("stdbuf"):
+                    cmd = ["stdbuf", "-oL"] + cmd
+                self._proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True,
+                                              bufsize=1)
                 self._t = threading.Thread(target=self._run_smi, daemon=True)
             except OSError:
                 self._proc = None
@@ -170,14 +176,26 @@ class ClockSampler:
                 self._proc.kill()
         if self._t:
             self._t.join(timeout=10)
+        if not self.rows and not self._nvml:  # nothing streamed in time: one sample as the region ends
+            try:
+                out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout
+                row = self._parse(out.strip())
+                if row:
+                    self.rows.append(row)
+                    self.at_exit = True
+            except (OSError, subprocess.TimeoutExpired):
+                pass
 
     def summary(self):
         if not self.rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         sm = [r[0] for r in self.rows]
+        src = "nvml" if self._nvml else ("nvidia-smi at the end of the region" if self.at_exit else "nvidia-smi -lms 20")
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(r[1] for r in self.rows),
                 "reasons": sorted(set().union(*(r[2] for r in self.rows))), "samples": len(self.rows),
-                "source": "nvml" if self._nvml else "nvidia-smi -lms 20"}
+                "source": src}
 
 
 def dist_env():

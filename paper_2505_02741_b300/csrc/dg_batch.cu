@@ -381,7 +381,7 @@ uint64_t BatchWS::bytes() const {
     b += cscan.bytes() + ccount.bytes() + cflag.bytes() + cpos.bytes() + cv2.bytes() + ccount2.bytes();
     b += cw.bytes() + kind_ins.bytes() + path_buf.bytes() + path_len.bytes() + path_w.bytes() + fb_list.bytes() +
          fb_count.bytes();
-    b += fb_slot.bytes() + fb_big.bytes() + fb_cbase.bytes() + fb_dslot.bytes() + fb_py.bytes() + fb_pr.bytes() +
+    b += fb_slot.bytes() + fb_big.bytes() + fb_cbase.bytes() + fb_done.bytes() + fb_dslot.bytes() + fb_py.bytes() + fb_pr.bytes() +
          fb_pw.bytes();
     b += dbg_reason.bytes() + dbg_steps.bytes() + dbg_paths.bytes() + shard_recs.bytes();
     b += apG.bytes() + apH.bytes() + apC.bytes();
@@ -491,6 +491,7 @@ static void ensure_ws(Ctx& c, DGraph& g, uint32_t b_max, cudaStream_t st) {
     w.fb_count.ensure(a, 4, st);
     w.fb_big.ensure(a, (size_t)B * 2, st);
     w.fb_cbase.ensure(a, (size_t)B * 2, st);
+    w.fb_done.ensure(a, (size_t)B * 2, st);
     w.fb_dslot.ensure(a, (size_t)B * 2, st);
     w.fb_pr.ensure(a, FB_CHUNK_CAP, st);
     w.fb_pw.ensure(a, FB_CHUNK_CAP, st);
@@ -837,7 +838,7 @@ void graph_release_ws(Ctx& c, DGraph& g, cudaStream_t st) {
     REL(hpos); REL(hvals); REL(hcount); REL(gkind); REL(ghrem); REL(kind_del); REL(gw); REL(t_u); REL(t_v);
     REL(t_idx); REL(t_kstar); REL(t_fin); REL(t_queue); REL(qctr); REL(cp); REL(step_r); REL(step_e); REL(t_count); REL(meta); REL(t_wpq); REL(t_rmax); REL(recR); REL(t_kind); REL(best);
     REL(ckeys); REL(ckeys_alt); REL(ck2); REL(cvals); REL(cvals_alt); REL(chist); REL(cscan); REL(ccount);
-    REL(cflag); REL(cpos); REL(cv2); REL(ccount2); REL(cw); REL(kind_ins); REL(path_buf); REL(path_w); REL(path_len); REL(fb_list); REL(fb_count); REL(fb_slot); REL(fb_big); REL(fb_cbase); REL(fb_dslot); REL(fb_py); REL(fb_pr); REL(fb_pw); REL(dbg_reason);
+    REL(cflag); REL(cpos); REL(cv2); REL(ccount2); REL(cw); REL(kind_ins); REL(path_buf); REL(path_w); REL(path_len); REL(fb_list); REL(fb_count); REL(fb_slot); REL(fb_big); REL(fb_cbase); REL(fb_done); REL(fb_dslot); REL(fb_py); REL(fb_pr); REL(fb_pw); REL(dbg_reason);
     REL(dbg_steps); REL(dbg_paths); REL(shard_recs);
 #undef REL
     w.b_max = 0;
@@ -886,7 +887,7 @@ static Cands cands_of(BatchWS& w) {
 
 static PathBufs paths_of(BatchWS& w) {
     return PathBufs{w.path_buf.p, w.path_w.p, w.path_len.p, w.fb_list.p, w.fb_count.p, w.fb_slot.p,
-                    w.fb_big.p,   w.fb_cbase.p, w.fb_dslot.p,  w.fb_pr.p,   w.fb_pw.p,    w.fb_py.p};
+                    w.fb_big.p,   w.fb_cbase.p, w.fb_done.p, w.fb_dslot.p, w.fb_pr.p, w.fb_pw.p, w.fb_py.p};
 }
 
 static FinArgs fin_of(Ctx& c, BatchWS& w, bool on) {

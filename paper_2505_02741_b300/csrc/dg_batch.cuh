@@ -78,7 +78,7 @@ struct BatchWS {
     DBuf<double> cw;
     DBuf<uint8_t> kind_ins;
     DBuf<uint32_t> path_buf, path_len, fb_list, fb_count;
-    DBuf<uint32_t> fb_slot, fb_big, fb_cbase, fb_dslot, fb_py;
+    DBuf<uint32_t> fb_slot, fb_big, fb_cbase, fb_done, fb_dslot, fb_py;
     DBuf<double> fb_pr, fb_pw;
     DBuf<double> path_w;
     // debug

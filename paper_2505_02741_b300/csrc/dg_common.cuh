@@ -22,7 +22,8 @@ struct __align__(32) Ent {
     uint32_t nbr;   // neighbour id
     uint32_t noff;  // off[nbr] (cached), or HUBREF when nbr is a hub
     uint32_t ndeg;  // deg[nbr] (cached); 0 only in an entry not yet refreshed
-    uint32_t rev;   // position of this list's owner inside nbr's list (unused for HUBREF)
+    uint32_t rev;   // position of this list's owner inside nbr's list (for HUBREF: its position
+                    // when the entry was last written, a hint that may have drifted since)
     double r;       // resistance 1 / w (Section II-A, computed once, IEEE RN)
     double w;       // weight
 };
@@ -55,6 +56,9 @@ struct CSRView {
                               // writes the list there and keeps this one), or 0xFFFFFFFF
     Ent* pool;
     unsigned long long* top;  // entries in use (bump pointer)
+    unsigned long long* minr; // a lower bound of every entry's resistance (FP64 bits; positive
+                              // doubles order like their bits): the minimum at build, lowered by
+                              // every insertion or weight change, never raised
     uint64_t pool_cap;        // entries allocated
     int32_t n;
 };

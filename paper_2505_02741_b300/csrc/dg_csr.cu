@@ -75,6 +75,8 @@ void csr_alloc_vertices(CSR& g, DevAlloc& a, int32_t n, cudaStream_t st) {
     g.twin.ensure(a, (size_t)n + 1, st);
     DG_CUDA(cudaMemsetAsync(g.twin.p, 0xFF, g.twin.bytes(), st));
     g.top.ensure(a, 1, st);
+    g.minr.ensure(a, 1, st);
+    DG_CUDA(cudaMemsetAsync(g.minr.p, 0xFF, g.minr.bytes(), st));
     DG_CUDA(cudaMemsetAsync(g.off.p, 0, g.off.bytes(), st));
     DG_CUDA(cudaMemsetAsync(g.deg.p, 0, g.deg.bytes(), st));
     DG_CUDA(cudaMemsetAsync(g.cap.p, 0, g.cap.bytes(), st));
@@ -90,6 +92,7 @@ void csr_release(CSR& g, DevAlloc& a, cudaStream_t st) {
     g.twin.release(a, st);
     g.pool.release(a, st);
     g.top.release(a, st);
+    g.minr.release(a, st);
     g.pool_cap = 0;
     g.n = 0;
 }
@@ -147,6 +150,16 @@ __global__ void k_build_fill(const uint64_t* __restrict__ keys, const uint32_t* 
     }
 }
 
+// minimum resistance over the built entries (a lower bound for the lists)
+__global__ void k_build_minr(const uint32_t* __restrict__ vals, const double* __restrict__ ws, uint32_t count,
+                             unsigned long long* minr) {
+    unsigned long long m = ~0ull;
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < count; c += gridDim.x * blockDim.x)
+        m = min(m, (unsigned long long)__double_as_longlong(__ddiv_rn(1.0, ws[vals[c]])));
+    for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m != ~0ull) atomicMin(minr, m);
+}
+
 // refresh (noff, ndeg, rev) of every entry listed by the sorted key array
 __global__ void k_build_fix(const uint64_t* __restrict__ keys, uint32_t count, uint32_t n, CSRView g,
                             uint32_t* d_err) {
@@ -154,18 +167,14 @@ __global__ void k_build_fix(const uint64_t* __restrict__ keys, uint32_t count, u
         const uint64_t k = keys[c];
         const uint32_t x = (uint32_t)(k / n), y = (uint32_t)(k % n);
         const uint32_t s0 = lower_bound_arr<uint64_t>(keys, 0, c, (uint64_t)x * n);
-        uint4 h;
-        if (g.hub[y]) {
-            h = make_uint4(y, HUBREF, 1u, 0u);
-        } else {
-            const uint32_t ly = g.off[y], dy = g.deg[y];
-            const uint32_t p = lower_bound_nbr(g.pool + ly, dy, x);
-            if (p >= dy || g.pool[ly + p].nbr != x) {
-                atomicOr(d_err, (uint32_t)ERR_INTERNAL);
-                continue;
-            }
-            h = make_uint4(y, ly, dy, p);
+        const uint32_t ly = g.off[y], dy = g.deg[y];
+        const uint32_t p = lower_bound_nbr(g.pool + ly, dy, x);
+        if (p >= dy || g.pool[ly + p].nbr != x) {
+            atomicOr(d_err, (uint32_t)ERR_INTERNAL);
+            continue;
         }
+        // a hub reference keeps x's slot in the hub's list as a hint (HUBREF)
+        const uint4 h = g.hub[y] ? make_uint4(y, HUBREF, 1u, p) : make_uint4(y, ly, dy, p);
         *reinterpret_cast<uint4*>(g.pool + g.off[x] + (c - s0)) = h;
     }
 }
@@ -220,7 +229,9 @@ void csr_build(CSR& g, DevAlloc& a, const uint64_t* keys, const uint32_t* vals, 
     if (count > 0) {
         k_build_fill<<<grid, FLAT_THREADS, 0, st>>>(keys, vals, ws, count, n, g.off.p, g.pool.p);
         k_build_fix<<<grid, FLAT_THREADS, 0, st>>>(keys, count, n, g.view(), d_err);
-        g_launches += 2;
+        DG_CUDA(cudaMemsetAsync(g.minr.p, 0xFF, 8, st));
+        k_build_minr<<<grid, FLAT_THREADS, 0, st>>>(vals, ws, count, g.minr.p);
+        g_launches += 3;
     }
     DG_CHECK_LAUNCH();
 }
@@ -529,6 +540,7 @@ __global__ void k_exec_merge(ExecArgs a, uint32_t* d_err) {
                 const double w = a.cl.ws[a.cl.vals[c0]];
                 out.w = w;
                 out.r = __ddiv_rn(1.0, w);
+                atomicMin(a.g.minr, (unsigned long long)__double_as_longlong(out.r));
             }
         } else {
             const uint32_t c = s0 + (local - od);
@@ -549,6 +561,7 @@ __global__ void k_exec_merge(ExecArgs a, uint32_t* d_err) {
             out.rev = 0;
             out.w = w;
             out.r = __ddiv_rn(1.0, w);
+            atomicMin(a.g.minr, (unsigned long long)__double_as_longlong(out.r));
         }
         if (outpos >= a.ndeg[t]) {
             atomicOr(d_err, (uint32_t)ERR_INTERNAL);
@@ -601,17 +614,14 @@ __global__ void k_exec_fix(ExecArgs a, uint32_t* d_err) {
                 atomicOr(d_err, (uint32_t)ERR_INTERNAL);
                 return;
             }
-            if (a.g.hub[y] != 0) {
-                *reinterpret_cast<uint4*>(a.g.pool + lx + px) = make_uint4(y, HUBREF, 1u, 0u);
-            } else {
-                const uint32_t ly = a.g.off[y], dy = a.g.deg[y];
-                const uint32_t p = lower_bound_nbr(a.g.pool + ly, dy, x);
-                if (p >= dy || a.g.pool[ly + p].nbr != x) {
-                    atomicOr(d_err, (uint32_t)ERR_INTERNAL);
-                    return;
-                }
-                *reinterpret_cast<uint4*>(a.g.pool + lx + px) = make_uint4(y, ly, dy, p);
+            const uint32_t ly = a.g.off[y], dy = a.g.deg[y];
+            const uint32_t p = lower_bound_nbr(a.g.pool + ly, dy, x);
+            if (p >= dy || a.g.pool[ly + p].nbr != x) {
+                atomicOr(d_err, (uint32_t)ERR_INTERNAL);
+                return;
             }
+            *reinterpret_cast<uint4*>(a.g.pool + lx + px) =
+                a.g.hub[y] != 0 ? make_uint4(y, HUBREF, 1u, p) : make_uint4(y, ly, dy, p);
             return;
         }
         const uint4 e = *reinterpret_cast<const uint4*>(a.g.pool + lx + local);
@@ -649,7 +659,14 @@ __global__ void k_exec_fix(ExecArgs a, uint32_t* d_err) {
         // list and y's list did not change
         if (need_own) {
             if (y_hub) {
-                *reinterpret_cast<uint4*>(a.g.pool + lx + local) = make_uint4(y, HUBREF, 1u, 0u);
+                // slot hint: a copied entry keeps its old slot in y's list (y's list
+                // changed little); a fresh one looks it up
+                uint32_t hint = e.w;
+                if (fresh) {
+                    if (!locate()) return;
+                    hint = p;
+                }
+                *reinterpret_cast<uint4*>(a.g.pool + lx + local) = make_uint4(y, HUBREF, 1u, hint);
             } else {
                 if (!locate()) return;
                 *reinterpret_cast<uint4*>(a.g.pool + lx + local) = make_uint4(y, ly, dy, p);
@@ -661,7 +678,7 @@ __global__ void k_exec_fix(ExecArgs a, uint32_t* d_err) {
         // make those stale.
         if (!need_back) return;
         if (!locate()) return;
-        const uint4 back = x_hub ? make_uint4(x, HUBREF, 1u, 0u) : make_uint4(x, lx, a.g.deg[x], local);
+        const uint4 back = x_hub ? make_uint4(x, HUBREF, 1u, local) : make_uint4(x, lx, a.g.deg[x], local);
         *reinterpret_cast<uint4*>(a.g.pool + ly + p) = back;
     });
 }

@@ -30,6 +30,7 @@ struct CSR {
     DBuf<uint32_t> twin;
     DBuf<Ent> pool;
     DBuf<unsigned long long> top;
+    DBuf<unsigned long long> minr;  // resistance lower bound (CSRView::minr)
     uint64_t host_top = 0;  // last value read back
 
     CSRView view() const {
@@ -42,13 +43,14 @@ struct CSR {
         v.twin = twin.p;
         v.pool = pool.p;
         v.top = top.p;
+        v.minr = minr.p;
         v.pool_cap = pool_cap;
         v.n = n;
         return v;
     }
     uint64_t bytes() const {
         return off.bytes() + deg.bytes() + cap.bytes() + hub.bytes() + nhub.bytes() + twin.bytes() + pool.bytes() +
-               top.bytes();
+               top.bytes() + minr.bytes();
     }
 };
 

@@ -676,8 +676,11 @@ struct Lean {
     uint32_t c, off, deg, prev, steps;
     uint32_t ulo, uhi;  // update id (Philox counter words 2, 3)
     uint32_t x;         // random word of the next step
+    uint32_t hint;      // at a hub (pid): the previous vertex's slot in the hub's list as the
+                        // reference we arrived by last recorded it (it may have drifted)
     bool ins, active;
     bool pid;           // prev holds the previous vertex's id (we arrived at a hub)
+    bool plus;          // the entry in flight was picked as L[jj + 1] on the hint's word
     double R;
     uint64_t rmax;      // insertion: w_pq * R <= K  <=>  bits(R) <= rmax
 };
@@ -698,6 +701,8 @@ __device__ __forceinline__ void lean_start(Lean& w, const WalkKernelArgs& a, uin
     w.c = u;
     w.prev = NONE;
     w.pid = false;
+    w.hint = 0;
+    w.plus = false;
     w.steps = 0;
     w.R = 0.0;
     w.active = true;
@@ -773,19 +778,24 @@ __device__ __forceinline__ void load_step(const Ent* pool, uint32_t i, uint4& h,
     r = __ldg(reinterpret_cast<const double*>(q + 1));
 }
 
-// The step when the walker stands on a hub (previous vertex known by id only:
-// L[jj] was loaded at slot `at`; take L[jj+1] instead when L[jj] is at or past
-// the previous vertex) or the chosen entry leads to a hub (HUBREF: the list
-// comes from the vertex arrays).  Moves the walker (r ends as the step's
-// resistance, added by the caller); false on a bad offset.
+// The step when the walker stands on a hub (previous vertex p known by id
+// only) or the chosen entry leads to a hub (HUBREF: the list comes from the
+// vertex arrays).  At a hub the j-th neighbour other than p is L[jj] when
+// L[jj] < p and L[jj + 1] otherwise; the entry in flight was picked by the
+// slot hint (plus: L[jj + 1]), and the pick is checked against p: L[jj] is
+// right iff its id is below p, L[jj + 1] iff its id is above p.  A wrong
+// guess (a hint that drifted past jj) loads the other entry.  Moves the walker
+// (r ends as the step's resistance, added by the caller); false on a bad
+// offset.
 __device__ __forceinline__ bool lean_hub_step(Lean& v, const WalkKernelArgs& a, uint4& h, double& r, uint32_t& at) {
     const CSRView& g = v.ins ? a.H : a.G;
-    if (v.pid && h.x >= v.prev) {
-        if ((uint64_t)at + 1 >= g.pool_cap) {
+    if (v.pid && (v.plus ? h.x <= v.prev : h.x >= v.prev)) {
+        const uint32_t alt = v.plus ? at - 1u : at + 1u;
+        if ((uint64_t)alt >= g.pool_cap) {
             atomicOr(a.d_err, (uint32_t)ERR_INTERNAL);
             return false;
         }
-        ++at;
+        at = alt;
         load_step(g.pool, at, h, r);
     }
     v.steps += 1;
@@ -795,6 +805,7 @@ __device__ __forceinline__ bool lean_hub_step(Lean& v, const WalkKernelArgs& a, 
         v.off = g.off[v.c];
         v.deg = g.deg[v.c];
         v.prev = from;
+        v.hint = h.w;
         v.pid = true;
     } else {
         v.off = h.y;
@@ -809,7 +820,7 @@ __device__ __forceinline__ bool lean_hub_step(Lean& v, const WalkKernelArgs& a, 
 // pruning probe of its update); false when there is no next step (n_eff = 0)
 // or the offset would leave the pool (a broken mutation, reported).
 template <bool HUBS>
-__device__ __forceinline__ bool lean_issue(const Lean& v, const WalkKernelArgs& a, uint4& h, double& r, uint32_t& ks,
+__device__ __forceinline__ bool lean_issue(Lean& v, const WalkKernelArgs& a, uint4& h, double& r, uint32_t& ks,
                                            uint32_t& at) {
     const uint32_t neff = v.deg - (v.prev != NONE ? 1u : 0u);
     if (neff == 0) {
@@ -820,8 +831,10 @@ __device__ __forceinline__ bool lean_issue(const Lean& v, const WalkKernelArgs& 
     }
     const uint32_t jj = __umulhi(v.x, neff);
     // slot of the previous vertex known: skip it by position; after a hub
-    // arrival only its id is known: load L[jj] and step past it if needed
-    const uint32_t idx = (HUBS && v.pid) ? jj : jj + (jj >= v.prev ? 1u : 0u);
+    // arrival its slot is only hinted: pick by the hint, checked on arrival
+    const uint32_t skip = (HUBS && v.pid) ? v.hint : v.prev;
+    const uint32_t idx = jj + (jj >= skip ? 1u : 0u);
+    v.plus = idx != jj;
     const uint64_t pcap = v.ins ? a.H.pool_cap : a.G.pool_cap;
     if ((uint64_t)v.off + idx >= pcap) {
         atomicOr(a.d_err, (uint32_t)ERR_INTERNAL);
@@ -1370,9 +1383,60 @@ __device__ void fb_scan_staged(const CSRView& H, const CSRView& G, uint32_t x, u
     __syncthreads();  // s_h and s_rng are reused by the next range
 }
 
+// First look at every long endpoint list claimed by fb_queue, one warp per
+// list: G_b's resistances are bounded below by G.minr, so the first entry (in
+// neighbour order) whose resistance equals that bound and whose edge is not in
+// H' is the list's minimum of (resistance, neighbour).  When one turns up
+// among the first FB_QUICK entries it becomes the result of the list's first
+// chunk and the list is marked done (fb_done); otherwise the chunked scan
+// decides.  Graphs whose weights tie at their minimum (unit weights) resolve
+// here instead of scanning hub lists of 10^5 entries.
+constexpr uint32_t FB_QUICK = 256;
+__global__ void __launch_bounds__(256) k_fb_quick(CSRView H, CSRView G, PathBufs pb, uint32_t* d_err) {
+    if (walk_aborted(d_err)) return;
+    const unsigned long long nb = *fb_nb(pb);
+    const uint32_t S = (uint32_t)(nb >> 32);
+    const unsigned long long lb = *G.minr;
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t sl = warp; sl < S; sl += nwarps) {
+        const uint32_t x = pb.fb_big[sl], cb = pb.fb_cbase[sl];
+        const uint32_t d = G.deg[x];
+        uint32_t done = 0;
+        if (cb + (d + FB_CHUNK - 1) / FB_CHUNK <= FB_CHUNK_CAP) {
+            const Ent* L = G.pool + G.off[x];
+            const uint32_t lim = min(d, FB_QUICK);
+            for (uint32_t b0 = 0; b0 < lim && !done; b0 += 32) {
+                const uint32_t k = b0 + (uint32_t)lane;
+                bool ok = false;
+                uint32_t y = NONE;
+                double rr = 0.0, ww = 0.0;
+                if (k < lim) {
+                    rr = L[k].r;
+                    y = L[k].nbr;
+                    ww = L[k].w;
+                    ok = (unsigned long long)__double_as_longlong(rr) == lb && !has_edge(H, x, y);
+                }
+                const uint32_t m = __ballot_sync(0xffffffffu, ok);
+                if (m) {
+                    const int f = __ffs(m) - 1;
+                    if (lane == f) {
+                        pb.fb_pr[cb] = rr;
+                        pb.fb_py[cb] = y;
+                        pb.fb_pw[cb] = ww;
+                    }
+                    done = 1;
+                }
+            }
+        }
+        if (lane == 0) pb.fb_done[sl] = done;
+    }
+}
+
 // Split scan of the long endpoint lists claimed by fb_queue: every fallback
 // deletion's endpoint slots are looked up (the claims are complete), then one
-// block per chunk finds the chunk's minimum.
+// block per chunk finds the chunk's minimum (lists k_fb_quick resolved keep
+// its result in their first chunk; their other chunks read as empty).
 __global__ void __launch_bounds__(256) k_fb_chunks(CSRView H, CSRView G, WalkTasks t, PathBufs pb, uint32_t w_max,
                                                    uint32_t* d_err) {
     if (walk_aborted(d_err)) return;
@@ -1400,6 +1464,14 @@ __global__ void __launch_bounds__(256) k_fb_chunks(CSRView H, CSRView G, WalkTas
         const uint32_t cb = pb.fb_cbase[lo], x = pb.fb_big[lo];
         const uint32_t d = G.deg[x];
         if (cb + (d + FB_CHUNK - 1) / FB_CHUNK > FB_CHUNK_CAP) continue;  // scanned whole by k_fallback
+        if (pb.fb_done[lo]) {
+            if (ch != cb && threadIdx.x == 0) {
+                pb.fb_pr[ch] = INFINITY;
+                pb.fb_py[ch] = NONE;
+                pb.fb_pw[ch] = 0.0;
+            }
+            continue;
+        }
         const uint32_t k0 = (ch - cb) * FB_CHUNK, k1 = min(k0 + FB_CHUNK, d);
         double br = INFINITY, bw = 0.0;
         uint32_t by = NONE;
@@ -1530,9 +1602,10 @@ void launch_emit(const CSRView& H, const CSRView& G, const WalkTasks& t, const W
 void launch_fallback(const CSRView& H, const CSRView& G, const WalkTasks& t, dg_update_result* res,
                      BatchCounters* ctr, Cands c, PathBufs pb, uint32_t w_max, uint32_t* d_err, cudaStream_t st) {
     const unsigned sms = (unsigned)device_sms();
+    k_fb_quick<<<sms * 2, 256, 0, st>>>(H, G, pb, d_err);
     k_fb_chunks<<<sms * 4, 256, 0, st>>>(H, G, t, pb, w_max, d_err);
     k_fallback<<<sms * 4, 256, 0, st>>>(H, G, t, res, ctr, c, pb, w_max, d_err);
-    g_launches += 2;
+    g_launches += 3;
     DG_CHECK_LAUNCH();
 }
 

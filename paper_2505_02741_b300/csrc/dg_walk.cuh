@@ -99,6 +99,7 @@ struct PathBufs {
     uint32_t* fb_slot;   // per vertex: its slot, 0xFFFFFFFF when unclaimed (cleared again by k_fallback)
     uint32_t* fb_big;    // per slot: the vertex
     uint32_t* fb_cbase;  // per slot: its first chunk (ascends with the slot)
+    uint32_t* fb_done;   // per slot: 1 when the first look resolved the list (k_fb_quick)
     uint32_t* fb_dslot;  // per fallback deletion and endpoint: the slot, or 0xFFFFFFFF
     double* fb_pr;       // per chunk: minimum resistance found, its weight and neighbour
     double* fb_pw;

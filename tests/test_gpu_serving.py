@@ -116,3 +116,30 @@ def test_serving_rejects_request_that_never_fits():
         g.submit(D.make_updates(bt.u, bt.v, bt.w, bt.op))
     assert e.value.code == -2
     ctx.close()
+
+
+def test_prepare_then_batches_of_every_size_class():
+    """dg_prepare sizes the workspace and captures the step of every size class
+    up front; batches of any size then give the same results as on a graph
+    that grew its workspace batch by batch, and queueing time is reported."""
+    wl, st = W.make_grid(48, 48)
+    sizes = [3, 1500, 40, 3000, 700, 5000, 1]
+    batches = [st.next_batch(k // 2, k - k // 2) for k in sizes]
+    outs = []
+    for prepared in (False, True):
+        ctx = D.Context()
+        g = ctx.load_graph(wl.n, wl.a, wl.b, wl.w)
+        g.init_sparsifier(wl.a[wl.h_ids], wl.b[wl.h_ids])
+        if prepared:
+            g.prepare(8000)
+        rs = []
+        for bt in batches:
+            t, _ = g.submit(D.make_updates(bt.u, bt.v, bt.w, bt.op))
+            res, lat, q = g.wait_ex(t)
+            assert 0.0 <= q <= lat
+            rs.append(res.copy())
+        outs.append((rs, g.sparsifier()))
+        ctx.close()
+    for r0, r1 in zip(outs[0][0], outs[1][0]):
+        assert_same_outputs(r0, r1)
+    assert_edges_equal(outs[0][1], outs[1][1], "H")

@@ -91,23 +91,26 @@ def host_cpu():
 
 
 class ClockSampler:
-    """SM clocks and throttle reasons sampled during the timed region: NVML
-    every 5 ms where the Python binding loads, else one nvidia-smi process
-    streaming a sample every 20 ms (stopped when the region ends)."""
+    """SM clocks and throttle reasons during the timed region.  One nvidia-smi
+    process streams a sample every 20 ms (NVML every 5 ms where its Python
+    binding loads), started before the warm-up so that its first samples are
+    out by the time the region begins; the summary keeps the samples that
+    arrived while the region ran (within one sampling interval of its end)."""
 
     NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
     QUERY = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD = 0.02
 
     def __init__(self, local=0):
         vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
         ids = [x.strip() for x in vis.split(",") if x.strip()]
         self.index = ids[local] if local < len(ids) else str(local)
-        self.rows = []  # (sm_mhz, max_mhz, set of active reasons)
+        self.rows = []  # (host time, sm_mhz, max_mhz, set of active reasons)
+        self.t0 = self.t1 = None
         self._stop = threading.Event()
         self._t = None
         self._proc = None
-        self.at_exit = False
         self._nvml = None
         try:
             import pynvml as N
@@ -118,25 +121,22 @@ class ClockSampler:
         except Exception:
             self._nvml = None
 
-    def _sample_nvml(self):
-        N, h = self._nvml
-        sm = N.nvmlDeviceGetClockInfo(h, N.NVML_CLOCK_SM)
-        mx = N.nvmlDeviceGetMaxClockInfo(h, N.NVML_CLOCK_SM)
-        bits = N.nvmlDeviceGetCurrentClocksThrottleReasons(h)
-        masks = (0x8, 0x40, 0x20, 0x4)  # hw slowdown, hw thermal, sw thermal, sw power cap
-        return float(sm), float(mx), {n for n, m in zip(self.NAMES, masks) if bits & m}
-
     def _parse(self, line):
         r = [x.strip() for x in line.split(",")]
         if len(r) < 6 or not r[0].replace(".", "").isdigit():
             return None
         act = {n for n, x in zip(self.NAMES, r[2:]) if "Active" in x and "Not" not in x}
-        return float(r[0]), float(r[1]), act
+        return time.perf_counter(), float(r[0]), float(r[1]), act
 
     def _run_nvml(self):
+        N, h = self._nvml
+        masks = (0x8, 0x40, 0x20, 0x4)  # hw slowdown, hw thermal, sw thermal, sw power cap
         while not self._stop.is_set():
             try:
-                self.rows.append(self._sample_nvml())
+                bits = N.nvmlDeviceGetCurrentClocksThrottleReasons(h)
+                self.rows.append((time.perf_counter(), float(N.nvmlDeviceGetClockInfo(h, N.NVML_CLOCK_SM)),
+                                  float(N.nvmlDeviceGetMaxClockInfo(h, N.NVML_CLOCK_SM)),
+                                  {n for n, m in zip(self.NAMES, masks) if bits & m}))
             except Exception:
                 pass
             self._stop.wait(0.005)
@@ -147,16 +147,15 @@ class ClockSampler:
             if row:
                 self.rows.append(row)
 
-    def __enter__(self):
+    def start(self):
         if self._nvml:
             self._t = threading.Thread(target=self._run_nvml, daemon=True)
         else:
+            cmd = ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                   "-lms", str(int(self.PERIOD * 1000))]
+            if shutil.which("stdbuf"):
+                cmd = ["stdbuf", "-oL"] + cmd  # each sample reaches the pipe when it is taken
             try:
-                # line-buffered, so each sample reaches the pipe when it is taken
-                cmd = ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                       "--format=csv,noheader,nounits", "-lms", "20"]
-                if shutil.which("stdbuf"):
-                    cmd = ["stdbuf", "-oL"] + cmd
                 self._proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True,
                                               bufsize=1)
                 self._t = threading.Thread(target=self._run_smi, daemon=True)
@@ -166,36 +165,37 @@ class ClockSampler:
             self._t.start()
         return self
 
+    def __enter__(self):  # the timed region
+        self.t0 = time.perf_counter()
+        return self
+
     def __exit__(self, *a):
+        self.t1 = time.perf_counter()
+        time.sleep(2 * self.PERIOD)  # the samples taken inside the region reach the pipe
+
+    def stop(self):
         self._stop.set()
         if self._proc:
-            self._proc.terminate()  # the sampler this object started
+            self._proc.terminate()  # the sampler process this object started
             try:
                 self._proc.wait(timeout=10)
             except subprocess.TimeoutExpired:
                 self._proc.kill()
         if self._t:
             self._t.join(timeout=10)
-        if not self.rows and not self._nvml:  # nothing streamed in time: one sample as the region ends
-            try:
-                out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
-                                     timeout=5).stdout
-                row = self._parse(out.strip())
-                if row:
-                    self.rows.append(row)
-                    self.at_exit = True
-            except (OSError, subprocess.TimeoutExpired):
-                pass
 
     def summary(self):
-        if not self.rows:
+        inside = [r for r in self.rows if self.t0 is not None and self.t0 <= r[0] <= self.t1 + self.PERIOD]
+        src = "nvml, 5 ms" if self._nvml else "nvidia-smi -lms 20"
+        if not inside:
+            after = [r for r in self.rows if self.t1 is not None and r[0] > self.t1]
+            inside = after[:1]
+            src += ", first sample after the region"
+        if not inside:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        sm = [r[0] for r in self.rows]
-        src = "nvml" if self._nvml else ("nvidia-smi at the end of the region" if self.at_exit else "nvidia-smi -lms 20")
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(r[1] for r in self.rows),
-                "reasons": sorted(set().union(*(r[2] for r in self.rows))), "samples": len(self.rows),
-                "source": src}
+        return {"sm_mhz": float(np.median([r[1] for r in inside])), "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": sorted(set().union(*(r[3] for r in inside))), "samples": len(inside), "source": src,
+                "region_ms": 1e3 * (self.t1 - self.t0)}
 
 
 def dist_env():
@@ -523,6 +523,7 @@ def main():
     dev_batches = [to_dev(bt) for bt in batches]
     d_res = torch.empty(max(len(b) for b in batches) * 32, dtype=torch.uint8, device=dev)
 
+    clk = ClockSampler(dev).start()
     bi = 0
     for _ in range(args.warmup):
         ups, d_ups = dev_batches[bi]
@@ -537,7 +538,7 @@ def main():
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(dev) as clk:
+    with clk:
         for k in range(args.steps):
             flush.fill_(float(k))  # L2 flush, outside the events
             ups, d_ups = dev_batches[bi]
@@ -552,6 +553,7 @@ def main():
             valid += s["valid"]
             launches += s["launches"]
         torch.cuda.synchronize()
+    clk.stop()
     if world > 1:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]

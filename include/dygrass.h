@@ -350,9 +350,10 @@ dg_status dg_wait(dg_ctx* ctx, uint64_t ticket, int32_t timeout_ms, double* late
 dg_status dg_wait_ex(dg_ctx* ctx, uint64_t ticket, int32_t timeout_ms, double* latency_ms, double* queue_ms);
 
 /* Prepare a graph for batches (or served requests) of up to max_batch updates:
-   sizes its batch workspace and pinned staging and, with CUDA graphs on,
-   captures the batch step of every size class up to max_batch, so that no later
-   batch pays for them.  The walk-shape autotuner still runs on the first batch
+   sizes its batch workspace and pinned staging, compacts its pools with room
+   for several batches of that size, and, with CUDA graphs on, captures the
+   batch step of every size class up to max_batch, so that no later batch pays
+   for them.  The walk-shape autotuner still runs on the first batch
    of >= 4096 updates unless a shape was set with dg_set_walk_shape. */
 dg_status dg_prepare(dg_ctx* ctx, int32_t graph_id, int64_t max_batch);
 

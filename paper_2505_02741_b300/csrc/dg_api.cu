@@ -207,6 +207,18 @@ dg_status dg_create(const dg_config* cfg_in, dg_ctx** out) {
         DG_CUDA(cudaGetDeviceCount(&ndev));
         if (cfg.device < 0 || cfg.device >= ndev) throw Error(DG_E_INVALID, "bad device ordinal");
         DG_CUDA(cudaSetDevice(cfg.device));
+        if (!cfg.alloc) {
+            // batch workspaces come and go through the stream-ordered allocator:
+            // keep freed blocks in this process's pool instead of returning them
+            // to the driver at every synchronization (a later batch would pay
+            // for mapping them again)
+            cudaMemPool_t pool = nullptr;
+            if (cudaDeviceGetDefaultMemPool(&pool, cfg.device) == cudaSuccess && pool) {
+                uint64_t keep = ~0ull;
+                cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+            }
+            cudaGetLastError();
+        }
         // optional L2 fetch granularity hint for this process's context (bytes;
         // a walk step reads one 32-byte sector, so larger fetches waste DRAM bandwidth)
         if (const char* f = std::getenv("DG_L2_FETCH")) {

@@ -1382,7 +1382,9 @@ void graph_prepare(Ctx& c, DGraph& g, int64_t max_batch, cudaStream_t st) {
     if (max_batch < 1 || max_batch > (1ll << 26)) throw Error(DG_E_INVALID, "max_batch out of range");
     const uint32_t top = bucket_of((uint64_t)max_batch);
     ensure_ws(c, g, top, st);
-    ensure_headroom(c, g, (uint32_t)max_batch, st);
+    // pool headroom for several batches of the largest size, so that a long
+    // stream of requests compacts rarely (a compaction stalls the graph)
+    ensure_headroom(c, g, (uint32_t)std::min<int64_t>(8 * max_batch, 1ll << 26), st);
     if (c.cfg.use_graphs && !c.cfg.record && c.cfg.walk_mode == DG_WALK_BATCHED)
         for (uint32_t b = 1024; b <= top; b <<= 1) capture_step(c, g, b, false, st);
     wait_stream(c, st);

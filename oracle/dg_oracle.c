@@ -802,3 +802,131 @@ void orc_set_next_id(orc_state *st, uint64_t id)
 {
     st->next_id = id;
 }
+
+/* ------------------------------------------------------------------------ */
+/* spanning-forest stretch (the initial sparsifier of Section III-A)         */
+/* ------------------------------------------------------------------------ */
+/*
+ * The paper takes H(0) from GRASS: a spanning tree plus the off-tree edges
+ * that are spectrally critical.  Reading R20: an off-tree edge e = (p, q) is
+ * ranked by its stretch w_e * R_T(p, q), where R_T is the resistance of the
+ * tree path between p and q -- the distortion dyGRASS's own insertion test
+ * measures (Section III-B), which on a tree H is exact because the walk
+ * between p and q is the tree path.  R_T is formed from root distances:
+ * every tree is rooted at its smallest vertex, D[root] = 0 and D[y] =
+ * D[x] + r(x, y) for a child y of x (r = 1 / w, one rounding each), and
+ * R_T(p, q) = (D[p] - D[l]) + (D[q] - D[l]) with l the lowest common
+ * ancestor.  p and q in different trees: R_T = +inf.
+ *
+ * n vertices; m edges (a[i], b[i], w[i]) of G; in_tree[i] != 0 marks the
+ * edges of the spanning forest.  stretch[i] receives w * R_T for off-tree
+ * edges and 0 for tree edges.  Returns 0, -1 if the marked edges contain a
+ * cycle or a bad vertex, -2 on allocation failure.
+ */
+int orc_tree_stretch(int32_t n, int64_t m, const int32_t *a, const int32_t *b, const double *w,
+                     const uint8_t *in_tree, double *stretch)
+{
+    int rc = 0;
+    int64_t nt = 0;
+    for (int64_t i = 0; i < m; i++) nt += in_tree[i] ? 1 : 0;
+    int32_t *deg = (int32_t *)calloc((size_t)n + 1, sizeof(int32_t));
+    int64_t *start = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    int32_t *nb = (int32_t *)malloc((size_t)(2 * nt + 1) * sizeof(int32_t));
+    double *nr = (double *)malloc((size_t)(2 * nt + 1) * sizeof(double));
+    int32_t *parent = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t *depth = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t *root = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    double *D = (double *)malloc((size_t)n * sizeof(double));
+    int32_t *queue = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int64_t *fill = (int64_t *)malloc((size_t)(n + 1) * sizeof(int64_t));
+    if (!deg || !start || !nb || !nr || !parent || !depth || !root || !D || !queue || !fill) {
+        rc = -2;
+        goto done;
+    }
+    /* adjacency of the forest */
+    for (int64_t i = 0; i < m; i++) {
+        if (!in_tree[i]) continue;
+        if (a[i] < 0 || a[i] >= n || b[i] < 0 || b[i] >= n || a[i] == b[i]) {
+            rc = -1;
+            goto done;
+        }
+        deg[a[i]]++;
+        deg[b[i]]++;
+    }
+    for (int32_t x = 0; x < n; x++) start[x + 1] = start[x] + deg[x];
+    for (int32_t x = 0; x <= n; x++) fill[x] = start[x];
+    for (int64_t i = 0; i < m; i++) {
+        if (!in_tree[i]) continue;
+        const double r = 1.0 / w[i];
+        nb[fill[a[i]]] = b[i];
+        nr[fill[a[i]]++] = r;
+        nb[fill[b[i]]] = a[i];
+        nr[fill[b[i]]++] = r;
+    }
+    /* root every tree at its smallest vertex; breadth-first from it */
+    for (int32_t x = 0; x < n; x++) root[x] = -1;
+    int64_t reached_edges = 0;
+    for (int32_t s = 0; s < n; s++) {
+        if (root[s] >= 0) continue;
+        int32_t head = 0, tail = 0;
+        root[s] = s;
+        parent[s] = s;
+        depth[s] = 0;
+        D[s] = 0.0;
+        queue[tail++] = s;
+        while (head < tail) {
+            const int32_t x = queue[head++];
+            for (int64_t k = start[x]; k < start[x + 1]; k++) {
+                const int32_t y = nb[k];
+                if (y == parent[x] && x != s) continue; /* the edge back to the parent */
+                if (root[y] >= 0) { /* reached twice: the marked edges close a cycle */
+                    rc = -1;
+                    goto done;
+                }
+                root[y] = s;
+                parent[y] = x;
+                depth[y] = depth[x] + 1;
+                D[y] = D[x] + nr[k];
+                queue[tail++] = y;
+                reached_edges++;
+            }
+        }
+    }
+    if (reached_edges != nt) { /* a repeated tree edge */
+        rc = -1;
+        goto done;
+    }
+    /* stretch of every off-tree edge through its lowest common ancestor */
+    for (int64_t i = 0; i < m; i++) {
+        if (in_tree[i]) {
+            stretch[i] = 0.0;
+            continue;
+        }
+        int32_t p = a[i], q = b[i];
+        if (root[p] != root[q]) {
+            stretch[i] = INFINITY;
+            continue;
+        }
+        int32_t x = p, y = q;
+        while (depth[x] > depth[y]) x = parent[x];
+        while (depth[y] > depth[x]) y = parent[y];
+        while (x != y) {
+            x = parent[x];
+            y = parent[y];
+        }
+        const double R = (D[p] - D[x]) + (D[q] - D[x]);
+        stretch[i] = w[i] * R;
+    }
+done:
+    free(deg);
+    free(start);
+    free(nb);
+    free(nr);
+    free(parent);
+    free(depth);
+    free(root);
+    free(D);
+    free(queue);
+    free(fill);
+    return rc;
+}

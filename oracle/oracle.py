@@ -81,6 +81,8 @@ def lib(omp: bool = False):
         L.orc_next_id.restype = C.c_uint64
         L.orc_set_next_id.argtypes = [P, C.c_uint64]
         L.orc_set_next_id.restype = None
+        L.orc_tree_stretch.argtypes = [C.c_int32, C.c_int64, i32p, i32p, f64p, u8p, f64p]
+        L.orc_tree_stretch.restype = C.c_int
         L.orc_set_threads.argtypes = [C.c_int32]
         L.orc_set_threads.restype = None
         L.orc_max_threads.argtypes = []
@@ -95,6 +97,36 @@ def philox4x32_10(ctr, key) -> np.ndarray:
     lib().orc_philox4x32_10(np.ascontiguousarray(ctr, np.uint32), np.ascontiguousarray(key, np.uint32),
                             out)
     return out
+
+
+def tree_stretch(n, a, b, w, tree_ids):
+    """Stretch w_e * R_T(e) of every edge of G (canonical arrays a, b, w) with
+    respect to the spanning forest given by the edge ids tree_ids (0 for the
+    tree edges, +inf across trees); raises if those edges hold a cycle."""
+    a = np.ascontiguousarray(a, np.int32)
+    b = np.ascontiguousarray(b, np.int32)
+    w = np.ascontiguousarray(w, np.float64)
+    mask = np.zeros(a.size, np.uint8)
+    mask[np.asarray(tree_ids, np.int64)] = 1
+    out = np.zeros(a.size, np.float64)
+    rc = lib().orc_tree_stretch(int(n), a.size, a, b, w, mask, out)
+    if rc == -1:
+        raise ValueError("the tree edges contain a cycle or a bad vertex")
+    if rc != 0:
+        raise MemoryError("oracle stretch failed")
+    return out
+
+
+def grass_sparsifier(n, a, b, w, tree_ids, n_off):
+    """H(0) of the GRASS-like rule: the spanning forest plus the n_off off-tree
+    edges of largest stretch (ties: smaller edge id); returns sorted edge ids."""
+    st = tree_stretch(n, a, b, w, tree_ids)
+    tree = np.zeros(a.size, bool)
+    tree[np.asarray(tree_ids, np.int64)] = True
+    off = np.nonzero(~tree)[0]
+    order = np.lexsort((off, -st[off]))  # stretch descending, then id ascending
+    pick = off[order[: int(n_off)]]
+    return np.sort(np.concatenate([np.nonzero(tree)[0], pick]))
 
 
 class OracleGraph:

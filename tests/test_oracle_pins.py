@@ -606,3 +606,78 @@ def test_initial_sparsifier_rule():
     off = wl.m - tree.size
     assert wl.h_ids.size == tree.size + math.floor(0.1 * off)
     assert np.isin(tree, wl.h_ids).all()
+
+
+# ---------------------------------------------------------------------------
+# GRASS-like initial sparsifier: stretch of the off-tree edges (reading R20)
+# ---------------------------------------------------------------------------
+def _forest(n, a, b, w):
+    return W.spanning_forest(n, a, b, w)
+
+
+@pytest.mark.parametrize("seed", [21, 22, 23])
+def test_tree_stretch_is_path_resistance(seed):
+    """w_e * R_T(e): R_T against the tree path's resistance summed edge by
+    edge and against R_eff of the tree alone (pseudo-inverse), 1e-12
+    relative; tree edges read 0."""
+    from oracle.oracle import tree_stretch
+    rng = np.random.default_rng(seed)
+    n = 40
+    a, b, w = random_connected(n, 50, rng, 0.2, 7.0)
+    tree = _forest(n, a, b, w)
+    st = tree_stretch(n, a, b, w, tree)
+    mask = np.zeros(a.size, bool)
+    mask[tree] = True
+    assert (st[mask] == 0.0).all()
+    ta, tb, tw = a[mask], b[mask], w[mask]
+    adj = checks.adjacency_lists(n, ta, tb, tw)
+    off = np.nonzero(~mask)[0]
+    pairs = [(int(a[i]), int(b[i])) for i in off]
+    reff = checks.effective_resistances(n, ta, tb, tw, pairs)
+    for k, i in enumerate(off):
+        path = checks.tree_path(adj, int(a[i]), int(b[i]))
+        wmap = {(int(x), int(y)): float(z) for x, y, z in zip(ta, tb, tw)}
+        rsum = sum(1.0 / wmap[(min(p, q), max(p, q))] for p, q in zip(path[:-1], path[1:]))
+        assert st[i] == pytest.approx(w[i] * rsum, rel=1e-12)
+        assert st[i] == pytest.approx(w[i] * reff[k], rel=1e-12)
+
+
+def test_tree_stretch_unit_weights_is_hop_distance():
+    """Unit weights: the stretch of a chord of a path is exactly its hop count."""
+    from oracle.oracle import tree_stretch
+    n = 30
+    pa, pb, _ = path_graph(n)
+    chords = [(0, 29), (3, 10), (5, 6 + 7), (12, 27)]
+    a = np.concatenate([pa, [c[0] for c in chords]]).astype(np.int32)
+    b = np.concatenate([pb, [c[1] for c in chords]]).astype(np.int32)
+    ca, cb, _ = W.canonical(a, b)
+    w = np.ones(ca.size)
+    tree = np.nonzero((cb - ca) == 1)[0]
+    st = tree_stretch(n, ca, cb, w, tree)
+    for x, y, s in zip(ca, cb, st):
+        assert s == (0.0 if y - x == 1 else float(y - x))
+
+
+def test_tree_stretch_across_trees_cycles_and_selection():
+    """An off-tree edge between two trees of the forest has infinite stretch;
+    marked edges that close a cycle are rejected; the GRASS-like H(0) is the
+    forest plus the n_off largest stretches, ties to the smaller edge id."""
+    from oracle.oracle import grass_sparsifier, tree_stretch
+    a, b, w = ring(8, w=2.0)
+    ids = np.arange(a.size)
+    with pytest.raises(ValueError):
+        tree_stretch(8, a, b, w, ids)  # the whole ring is a cycle
+    # forest of two paths {0..3}, {4..7}: edges 3-4 and 0-7 cross between them
+    keep = [i for i in ids if not ((a[i], b[i]) in ((3, 4), (0, 7)))]
+    st = tree_stretch(8, a, b, w, keep)
+    cross = [i for i in ids if (a[i], b[i]) in ((3, 4), (0, 7))]
+    assert np.isinf(st[cross]).all()
+    rng = np.random.default_rng(5)
+    n = 60
+    a, b, w = random_connected(n, 80, rng, unit=True)  # unit weights: many equal stretches
+    tree = _forest(n, a, b, w)
+    st = tree_stretch(n, a, b, w, tree)
+    for n_off in (0, 7, 23):
+        h = grass_sparsifier(n, a, b, w, tree, n_off)
+        off = sorted((i for i in range(a.size) if i not in set(tree.tolist())), key=lambda i: (-st[i], i))
+        assert h.tolist() == sorted(tree.tolist() + off[:n_off])

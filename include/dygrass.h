@@ -206,6 +206,24 @@ dg_status dg_init_sparsifier(dg_ctx* ctx, int32_t graph_id, int64_t mh, const in
                              const int32_t* v);
 
 /*
+ * GRASS-like H(0) (Section III-A; the paper precomputes H(0) with GRASS: a
+ * spanning tree plus spectrally critical off-tree edges).  The nt edges
+ * (tu[i], tv[i]) (host arrays) must be edges of G forming a forest
+ * (DG_E_INVALID otherwise: a non-edge, a cycle, a repeated edge).  Every other
+ * edge e = (p, q) of G gets the stretch w_e * R_F(p, q), R_F the resistance of
+ * the forest path (+inf when p and q lie in different trees): the distortion
+ * the insertion test of Section III-B measures, exact on a tree.  H(0) = the
+ * forest + the n_off off-tree edges of largest stretch (ties: the smaller edge
+ * in lexicographic (min, max) order).  stretch_out (nullable, host) receives
+ * the stretch of every edge of G in lexicographic order (0 for forest edges).
+ * R_F is formed from root distances: each tree is rooted at its smallest
+ * vertex, D[child] = D[parent] + 1/w, R_F = (D[p] - D[l]) + (D[q] - D[l]) with
+ * l the lowest common ancestor.  Replaces the current sparsifier.
+ */
+dg_status dg_init_sparsifier_grass(dg_ctx* ctx, int32_t graph_id, int64_t nt, const int32_t* tu,
+                                   const int32_t* tv, int64_t n_off, double* stretch_out);
+
+/*
  * One batch of nu updates (Algorithm 1, batch semantics above).  ups: host
  * array of nu records; res: host array of nu results, or NULL.  cuda_stream:
  * stream to run on (NULL = the context's stream); the call returns after the

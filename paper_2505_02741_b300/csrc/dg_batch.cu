@@ -665,7 +665,7 @@ void graph_mark_mutation(DGraph& g, cudaStream_t st) {
     if (g.ev_mut) DG_CUDA(cudaEventRecord(g.ev_mut, st));
 }
 
-void graph_init_h(Ctx& c, DGraph& g, int64_t mh, const int32_t* u, const int32_t* v) {
+void graph_init_h(Ctx& c, DGraph& g, int64_t mh, const int32_t* u, const int32_t* v, bool device_arrays) {
     if (g.shard.active) throw Error(DG_E_STATE, "a sharded batch is in progress on this graph");
     cudaStream_t st = c.stream;
     DevAlloc& a = c.alloc;
@@ -693,8 +693,9 @@ void graph_init_h(Ctx& c, DGraph& g, int64_t mh, const int32_t* u, const int32_t
     DG_CUDA(cudaMemsetAsync(err.p, 0, 4, st));
     DG_CUDA(cudaMemsetAsync(cnt.p, 0, 8, st));
     if (M) {
-        DG_CUDA(cudaMemcpyAsync(du.p, u, 4ull * M, cudaMemcpyHostToDevice, st));
-        DG_CUDA(cudaMemcpyAsync(dv.p, v, 4ull * M, cudaMemcpyHostToDevice, st));
+        const cudaMemcpyKind kind = device_arrays ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        DG_CUDA(cudaMemcpyAsync(du.p, u, 4ull * M, kind, st));
+        DG_CUDA(cudaMemcpyAsync(dv.p, v, 4ull * M, kind, st));
         k_inith_keys<<<grid_for(M), BT, 0, st>>>(du.p, dv.p, M, g.G.view(), k0.p, v0.p, dw.p, err.p);
         ++g_launches;
     }

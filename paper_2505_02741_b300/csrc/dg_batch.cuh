@@ -153,7 +153,13 @@ struct Ctx;  // context (dg_api.cu)
 
 // batch entry points (stream = caller stream or the context stream)
 void graph_load(Ctx& c, DGraph& g, int32_t n, int64_t m, const int32_t* u, const int32_t* v, const double* w);
-void graph_init_h(Ctx& c, DGraph& g, int64_t mh, const int32_t* u, const int32_t* v);
+// H(0) from an edge list (host arrays, or device arrays with device_arrays)
+void graph_init_h(Ctx& c, DGraph& g, int64_t mh, const int32_t* u, const int32_t* v, bool device_arrays = false);
+// GRASS-like H(0): the given spanning forest plus the n_off off-tree edges of
+// largest stretch (dg_grass.cu); stretch_out (host, nullable) receives every
+// edge's stretch in canonical edge order
+void graph_init_grass(Ctx& c, DGraph& g, int64_t nt, const int32_t* tu, const int32_t* tv, int64_t n_off,
+                      double* stretch_out);
 void graph_apply(Ctx& c, DGraph& g, int64_t nu, const dg_update* ups, dg_update_result* res, bool device_io,
                  cudaStream_t st);
 void graph_release(Ctx& c, DGraph& g);

@@ -46,7 +46,7 @@ EXPORTS = ("dg_config_default", "dg_create", "dg_destroy", "dg_status_str", "dg_
            "dg_graph_bytes", "dg_launch_count", "dg_set_next_update_id", "dg_get_next_update_id",
            "dg_set_walk_shape", "dg_set_walk_refill", "dg_submit_updates", "dg_wait", "dg_walk_estimate_noalloc",
            "dg_debug_set_wait_limit", "dg_shard_begin", "dg_shard_export", "dg_shard_commit", "dg_wait_ex",
-           "dg_prepare")
+           "dg_prepare", "dg_init_sparsifier_grass")
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -125,6 +125,7 @@ def load_library(path: str | None = None):
         "dg_shard_commit": (i32, [P, i32, u64, P, P]),
         "dg_wait_ex": (i32, [P, u64, i32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "dg_prepare": (i32, [P, i32, i64]),
+        "dg_init_sparsifier_grass": (i32, [P, i32, i64, P, P, i64, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -252,6 +253,21 @@ class Graph:
         u = np.ascontiguousarray(u, np.int32)
         v = np.ascontiguousarray(v, np.int32)
         _check(self._L.dg_init_sparsifier(self.ctx._h, self.gid, u.size, _ptr(u), _ptr(v)))
+
+    def init_sparsifier_grass(self, tree_u, tree_v, n_off: int, with_stretch=False):
+        """GRASS-like H(0): the forest (tree_u, tree_v) plus the n_off off-tree
+        edges of largest stretch; optionally returns every edge's stretch
+        (lexicographic edge order)."""
+        tu = np.ascontiguousarray(tree_u, np.int32)
+        tv = np.ascontiguousarray(tree_v, np.int32)
+        out = None
+        if with_stretch:
+            cnt = C.c_int64()
+            _check(self._L.dg_query_graph(self.ctx._h, self.gid, 0, None, None, None, C.byref(cnt)))
+            out = np.zeros(max(cnt.value, 1), np.float64)
+        _check(self._L.dg_init_sparsifier_grass(self.ctx._h, self.gid, tu.size, _ptr(tu), _ptr(tv), int(n_off),
+                                                _ptr(out)))
+        return None if out is None else out[: cnt.value]
 
     def apply(self, ups: np.ndarray, stream=None, out: np.ndarray | None = None) -> np.ndarray:
         """One batch from host records; returns the result records (into ``out``

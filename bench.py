@@ -7,7 +7,11 @@ Default workload (the largest single-GPU configuration): symmetrised R-MAT
 scale 22 (4.2M vertices, 64M undirected edges, a,b,c,d = .57,.19,.19,.05, unit
 weights), H(0) = max-weight spanning forest + 10 % of the off-tree edges,
 K = 100, T = 100, s = 32.  One step = one batch of 50k updates: 30k insertions
-between random vertex pairs and 20k deletions of current edges, shuffled.
+between random vertex pairs and 20k deletions of current edges, shuffled.  The
+configuration's stream is 20 such batches from G(0); timed step k applies
+batch k mod 20, every pass of the stream on a fresh copy of G(0) and H(0)
+loaded outside the timed steps (the warm-up takes the stream's first W batches
+on a copy of its own).
 ``--workload mesh`` (3-D mesh 100^3, 10k + 10k per batch) and ``fea`` (jittered
 triangulated 2048^2 grid, 50k + 50k) are the other batch configurations;
 ``serve`` runs the serving configuration.  Synthetic data, seeded.
@@ -31,6 +35,7 @@ no collective on the data path; rank 0 prints the whole-job line.
 from __future__ import annotations
 
 import argparse
+import itertools
 import json
 import os
 import platform
@@ -58,6 +63,9 @@ WALK_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one 
                        "R-MAT scale 22 default batch: 2.11 GB read + 121.5 MB written")
 
 BATCH = {"rmat": (30_000, 20_000), "mesh": (10_000, 10_000), "fea": (50_000, 50_000)}
+# batches in one pass of each configuration's update stream (R-MAT: 20 batches of
+# 50k; mesh: 10 batches of 10k + 10k; FEA: 10 batches of 100k)
+STREAM_BATCHES = {"rmat": 20, "mesh": 10, "fea": 10}
 
 
 def make_workload(name, args, seed):
@@ -96,7 +104,8 @@ class ClockSampler:
     process streams a sample every 20 ms (NVML every 5 ms where its Python
     binding loads), started before the warm-up so that its first samples are
     out by the time the region begins; the summary keeps the samples that
-    arrived while the region ran (within one sampling interval of its end)."""
+    arrived while a timed region ran (within one sampling interval of its end).
+    The timed steps may form several regions (one per pass of the stream)."""
 
     NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
     QUERY = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -108,7 +117,7 @@ class ClockSampler:
         ids = [x.strip() for x in vis.split(",") if x.strip()]
         self.index = ids[local] if local < len(ids) else str(local)
         self.rows = []  # (host time, sm_mhz, max_mhz, set of active reasons)
-        self.t0 = self.t1 = None
+        self.regions = []  # [start, end] host times of the timed regions
         self._stop = threading.Event()
         self._t = None
         self._proc = None
@@ -166,15 +175,21 @@ class ClockSampler:
             self._t.start()
         return self
 
-    def __enter__(self):  # the timed region
-        self.t0 = time.perf_counter()
+    def begin(self):  # a timed region starts (there may be several)
+        self.regions.append([time.perf_counter(), None])
+
+    def end(self):
+        self.regions[-1][1] = time.perf_counter()
+
+    def __enter__(self):
+        self.begin()
         return self
 
     def __exit__(self, *a):
-        self.t1 = time.perf_counter()
-        time.sleep(2 * self.PERIOD)  # the samples taken inside the region reach the pipe
+        self.end()
 
     def stop(self):
+        time.sleep(2 * self.PERIOD)  # the samples taken inside the last region reach the pipe
         self._stop.set()
         if self._proc:
             self._proc.terminate()  # the sampler process this object started
@@ -186,17 +201,18 @@ class ClockSampler:
             self._t.join(timeout=10)
 
     def summary(self):
-        inside = [r for r in self.rows if self.t0 is not None and self.t0 <= r[0] <= self.t1 + self.PERIOD]
+        regs = [(a, b) for a, b in self.regions if b is not None]
+        inside = [r for r in self.rows if any(a <= r[0] <= b + self.PERIOD for a, b in regs)]
         src = "nvml, 5 ms" if self._nvml else "nvidia-smi -lms 20"
-        if not inside:
-            after = [r for r in self.rows if self.t1 is not None and r[0] > self.t1]
+        if not inside and regs:
+            after = [r for r in self.rows if r[0] > regs[-1][1]]
             inside = after[:1]
             src += ", first sample after the region"
         if not inside:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         return {"sm_mhz": float(np.median([r[1] for r in inside])), "sm_max_mhz": max(r[2] for r in inside),
                 "reasons": sorted(set().union(*(r[3] for r in inside))), "samples": len(inside), "source": src,
-                "region_ms": 1e3 * (self.t1 - self.t0)}
+                "region_ms": 1e3 * sum(b - a for a, b in regs), "regions": len(regs)}
 
 
 def dist_env():
@@ -221,8 +237,8 @@ def reduce_over_ranks(vals_sum, vals_max, world, backend):
 
 
 def stream_slices(batches, size):
-    """The batch stream cut into consecutive slices of `size` updates (each a
-    valid batch in stream order)."""
+    """The batch stream (any iterable of batches) cut into consecutive slices
+    of `size` updates (each a valid batch in stream order)."""
     for bt in batches:
         for lo in range(0, len(bt), size):
             yield bt.u[lo:lo + size], bt.v[lo:lo + size], bt.w[lo:lo + size], bt.op[lo:lo + size]
@@ -463,12 +479,12 @@ def run_serve(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--per-update-steps", type=int, default=2)
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work per CPU baseline")
-    ap.add_argument("--ref-sample", type=int, default=1000, help="reference arm: updates per step")
+    ap.add_argument("--ref-sample", type=int, default=500, help="reference arm: updates per step")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-full-walks", action="store_true", help="skip the unpruned-walk context line (mesh)")
     ap.add_argument("--walk-shape", default="", help="fixed walk launch shape 'block,ilp' (skips the autotuner)")
@@ -505,58 +521,85 @@ def main():
     # workload (each rank an independent replica: weak scaling, no data-path collective)
     wl, st = make_workload(args.workload, args, rank)
     n_ins, n_del = BATCH[args.workload]
-    n_batches = args.warmup + args.steps + args.steps + args.per_update_steps
-    batches = [st.next_batch(n_ins, n_del) for _ in range(n_batches)]
+    L = STREAM_BATCHES[args.workload]  # the configuration's stream: L batches from G(0)
+    if args.warmup > L:
+        raise SystemExit(f"at most {L} warm-up steps (the stream's length)")
+    batches = [st.next_batch(n_ins, n_del) for _ in range(L + args.per_update_steps)]
 
     ctx = D.Context(device=dev, K=wl.K, T=wl.T, s=wl.s)
-    g = ctx.load_graph(wl.n, wl.a, wl.b, wl.w)
-    g.init_sparsifier(wl.a[wl.h_ids], wl.b[wl.h_ids])
-    if args.walk_shape:
-        blk, ilp = (int(x) for x in args.walk_shape.split(","))
-        g.set_walk_shape(blk, ilp, 0)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    max_batch = max(len(b.u) for b in batches)
+    shape = None
+    if args.walk_shape:
+        blk, ilp = (int(x) for x in args.walk_shape.split(","))
+        shape = (blk, ilp, 0, 0)
+
+    def fresh_copy():
+        """G(0) and H(0) on the device, workspace sized and steps captured up
+        front; the walk shape of the warm-up copy (or the fixed one)."""
+        gg = ctx.load_graph(wl.n, wl.a, wl.b, wl.w)
+        gg.init_sparsifier(wl.a[wl.h_ids], wl.b[wl.h_ids])
+        if shape is not None:
+            gg.set_walk_shape(shape[0], shape[1], shape[2], shape[3])
+        gg.prepare(max_batch)
+        torch.cuda.synchronize()
+        return gg
 
     def to_dev(bt):
         ups = D.make_updates(bt.u, bt.v, bt.w, bt.op)
         return ups, torch.from_numpy(ups.view(np.uint8)).to(dev)
 
     dev_batches = [to_dev(bt) for bt in batches]
-    d_res = torch.empty(max(len(b) for b in batches) * 32, dtype=torch.uint8, device=dev)
+    d_res = torch.empty(max_batch * 32, dtype=torch.uint8, device=dev)
 
+    # warm-up: the stream's first W batches on a copy of its own (autotunes the walk)
     clk = ClockSampler(dev).start()
-    bi = 0
-    for _ in range(args.warmup):
-        ups, d_ups = dev_batches[bi]
+    g = fresh_copy()
+    for k in range(args.warmup):
+        ups, d_ups = dev_batches[k]
         g.apply_device(d_ups.data_ptr(), len(ups), d_res.data_ptr(), stream.cuda_stream)
-        bi += 1
     torch.cuda.synchronize()
+    if shape is None:
+        s0 = g.stats()
+        shape = (s0["walk_block"], s0["walk_ilp"], s0["walk_blocks_per_sm"], s0["walk_refill"])
+    g.unload()
 
     # ---- timed: device-resident batches -------------------------------------
+    # step k applies stream batch k mod L; every pass of the stream starts on a
+    # fresh copy at G(0) (loaded outside the timed steps)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     walk_ms, steps_done, valid, launches, phases = [], 0, 0, 0, []
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    g = None
+    for k in range(args.steps):
+        if k % L == 0:
+            if g is not None:
+                torch.cuda.synchronize()
+                clk.end()
+                g.unload()
+            g = fresh_copy()
+            if world > 1:
+                import torch.distributed as dist
+                dist.barrier()
+            torch.cuda.synchronize()
+            clk.begin()
+        flush.fill_(float(k))  # L2 flush, outside the events
+        ups, d_ups = dev_batches[k % L]
+        ev[k][0].record(stream)
+        g.apply_device(d_ups.data_ptr(), len(ups), d_res.data_ptr(), stream.cuda_stream)
+        ev[k][1].record(stream)
+        s = g.stats()
+        walk_ms.append(s["walk_ms"])
+        phases.append(s)
+        steps_done += s["steps"]
+        valid += s["valid"]
+        launches += s["launches"]
     torch.cuda.synchronize()
-    with clk:
-        for k in range(args.steps):
-            flush.fill_(float(k))  # L2 flush, outside the events
-            ups, d_ups = dev_batches[bi]
-            bi += 1
-            ev[k][0].record(stream)
-            g.apply_device(d_ups.data_ptr(), len(ups), d_res.data_ptr(), stream.cuda_stream)
-            ev[k][1].record(stream)
-            s = g.stats()
-            walk_ms.append(s["walk_ms"])
-            phases.append(s)
-            steps_done += s["steps"]
-            valid += s["valid"]
-            launches += s["launches"]
-        torch.cuda.synchronize()
+    clk.end()
     clk.stop()
     if world > 1:
         dist.barrier()
+    bi = args.steps % L or L  # the next stream batch for the main copy
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_total = sum(step_ms) / 1e3
     (sum_valid, sum_steps), (t_max, walk_max) = reduce_over_ranks([valid, steps_done], [t_total, sum(walk_ms) / 1e3],
@@ -565,28 +608,32 @@ def main():
     walk_steps_per_s = sum_steps / walk_max
 
     # ---- e2e: pinned host buffers through dg_apply_updates -------------------
-    # the step's records wait in pinned host memory; the timed call copies them to
-    # the device and the results back (dg_apply_updates copies pinned arrays directly)
-    nmax = max(len(b) for b in batches)
-    h_ups = torch.empty(nmax * 24, dtype=torch.uint8, pin_memory=True).numpy().view(D.UPDATE_DTYPE)
-    h_res = torch.empty(nmax * 32, dtype=torch.uint8, pin_memory=True).numpy().view(D.RESULT_DTYPE)
+    # One pass of the stream on a fresh copy at G(0), through host buffers: the
+    # same batches as the device-resident steps.  The step's records wait in
+    # pinned host memory; the timed call copies them to the device and the
+    # results back (dg_apply_updates copies pinned arrays directly).
+    ge = fresh_copy()
+    h_ups = torch.empty(max_batch * 24, dtype=torch.uint8, pin_memory=True).numpy().view(D.UPDATE_DTYPE)
+    h_res = torch.empty(max_batch * 32, dtype=torch.uint8, pin_memory=True).numpy().view(D.RESULT_DTYPE)
+    e2e_steps = min(args.steps, L)
     e2e_t, e2e_valid, e2e_nu = [], 0, 0
-    for k in range(args.steps):
+    for k in range(e2e_steps):
         flush.fill_(float(k))
-        ups, _ = dev_batches[bi]
-        bi += 1
+        ups, _ = dev_batches[k]
         h_ups[: len(ups)] = ups
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        res = g.apply(h_ups[: len(ups)], stream=stream.cuda_stream, out=h_res)
+        res = ge.apply(h_ups[: len(ups)], stream=stream.cuda_stream, out=h_res)
         e2e_t.append(time.perf_counter() - t0)
         e2e_valid += int((res["status"] == 0).sum())
         e2e_nu += len(ups)
+    ge.unload()
     (e2e_sum,), (e2e_tmax,) = reduce_over_ranks([e2e_valid], [sum(e2e_t)], world, backend)
     e2e = {"value": e2e_sum / e2e_tmax, "unit": "updates/s",
-           "h2d_bytes_per_step": 24 * e2e_nu // args.steps + 16,
-           "d2h_bytes_per_step": 32 * e2e_nu // args.steps + 96, "p50_ms": 1e3 * float(np.percentile(e2e_t, 50)),
-           "p99_ms": 1e3 * float(np.percentile(e2e_t, 99)), "host_buffers": "pinned"}
+           "h2d_bytes_per_step": 24 * e2e_nu // e2e_steps + 16,
+           "d2h_bytes_per_step": 32 * e2e_nu // e2e_steps + 96, "p50_ms": 1e3 * float(np.percentile(e2e_t, 50)),
+           "p99_ms": 1e3 * float(np.percentile(e2e_t, 99)), "host_buffers": "pinned",
+           "steps": e2e_steps, "batches": "one pass of the stream from G(0) on a fresh copy"}
 
     # ---- context (mesh): the same walk kernel without deletion pruning -------
     full = None
@@ -668,7 +715,9 @@ def main():
 
     cpu = cpu_all = None
     if rank == 0 and not args.no_cpu:
-        cpu, cpu_all = oracle_baseline(wl, batches, args.cpu_budget)
+        # the stream goes on past the timed batches for as long as the CPU needs
+        more = (st.next_batch(n_ins, n_del) for _ in range(100_000))
+        cpu, cpu_all = oracle_baseline(wl, itertools.chain(batches, more), args.cpu_budget)
         cpu.update(host_cpu())
         cpu["all_cores"] = cpu_all
 
@@ -680,7 +729,9 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl.name, "n": wl.n, "m": wl.m, "batch": n_ins + n_del, "insertions": n_ins,
                        "deletions": n_del, "K": wl.K, "T": wl.T, "s": wl.s, "parallelism": f"replicas{world}",
-                       "l2": "flushed (256 MB write) between timed steps"},
+                       "l2": "flushed (256 MB write) between timed steps",
+                       "stream": f"{L} batches from G(0); timed step k applies batch k mod {L}, each pass on a "
+                                 f"fresh copy ({-(-args.steps // L)} passes)"},
             "walk_steps_per_s": walk_steps_per_s,
             "per_batch": {"walk_steps": steps_done / args.steps,
                           "walked_updates": float(np.mean([p["walked"] for p in phases])),

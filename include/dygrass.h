@@ -442,6 +442,115 @@ typedef struct {
 dg_status dg_walk_estimate_noalloc(dg_ctx* ctx, int32_t graph_id, int64_t nq, const dg_walk_query* d_queries,
                                    dg_walk_estimate* d_out, void* cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Quality of the sparsifier (Section IV: the off-tree density d_H, the
+ * relative condition number kappa(L_G, L_H) of Eqs. 6-10, and PCG on
+ * L_G x = b with L_H as the preconditioner, Table IV).  These calls read G and
+ * H as they stand after the last batch; they run on the context's stream,
+ * hold the graph (no batch of it runs meanwhile) and return when done.  Every
+ * step runs on the device; the host only decides when to stop iterating.
+ * ------------------------------------------------------------------------ */
+
+/* d_H = |E(H)| / |V| - 1 (Section IV), with |E(G)| and |E(H)| (each output
+ * nullable). */
+dg_status dg_sparsifier_density(dg_ctx* ctx, int32_t graph_id, double* d_h_out, int64_t* m_g_out,
+                                int64_t* m_h_out);
+
+#define DG_LAP_G 0
+#define DG_LAP_H 1
+
+/* y = L x for the Laplacian L = D - A of G (which = DG_LAP_G) or H
+ * (DG_LAP_H), Section II-A.  d_x and d_y are device arrays of n doubles owned
+ * by the caller (they may not overlap).  Row x sums its neighbours in
+ * ascending neighbour order; the weighted degree is summed the same way.
+ * cuda_stream: NULL = the context's stream (the call waits for it). */
+dg_status dg_laplacian_apply(dg_ctx* ctx, int32_t graph_id, int32_t which, const double* d_x, double* d_y,
+                             void* cuda_stream);
+
+#define DG_PRECOND_NONE 0
+#define DG_PRECOND_JACOBI 1     /* M = diag(L_G) */
+#define DG_PRECOND_SPARSIFIER 2 /* M = L_H (Section IV, Table IV) */
+
+typedef struct {
+    double tol;             /* stop when ||r_k|| / ||b|| < tol (Section IV uses 1e-8) */
+    int32_t max_iter;       /* outer iterations (> 0) */
+    int32_t precond;        /* DG_PRECOND_* */
+    double inner_tol;       /* DG_PRECOND_SPARSIFIER: each L_H solve runs to this relative residual */
+    int32_t inner_max_iter; /* ... or this many iterations */
+    int32_t reserved;
+} dg_pcg_options;           /* 32 bytes */
+
+typedef struct {
+    int32_t iters;          /* outer iterations run */
+    int32_t converged;      /* 1 when ||r|| / ||b|| < tol was reached */
+    double rel_residual;    /* ||b - L_G x|| / ||b|| recomputed from x at the end */
+    int64_t inner_iters;    /* inner (L_H) iterations over all outer ones */
+    int32_t inner_max;      /* most inner iterations one L_H solve took */
+    int32_t inner_unconverged; /* L_H solves that stopped at inner_max_iter */
+    double ms;              /* device time of the solve */
+} dg_pcg_info;              /* 40 bytes */
+
+/*
+ * Preconditioned conjugate gradients on L_G x = b from x = 0 (Section IV):
+ * alpha = (r, z) / (p, L_G p); x += alpha p; r -= alpha L_G p; stop when
+ * ||r|| / ||b|| < tol; z = M^-1 r; beta = (r_new, z_new) / (r, z);
+ * p = z + beta p.  With DG_PRECOND_SPARSIFIER, z = L_H^+ r is computed by an
+ * inner conjugate-gradient solve on L_H preconditioned by H's maximum-weight
+ * spanning forest F (ties: the smaller edge in lexicographic order), whose
+ * Laplacian is solved exactly through an Euler tour of every tree (subtree
+ * sums of r give the current through each tree edge, root-path sums of
+ * current / weight the potentials), to inner_tol.  b (device, n doubles,
+ * caller-owned) must sum to zero over every connected component of G (else
+ * the singular system has no solution); x (device, n doubles) receives
+ * the solution (defined up to a constant per component).  H must span every
+ * component of G (DG_E_STATE otherwise).  hist (nullable, host, max_iter + 1
+ * doubles) receives ||r_k|| / ||b|| for k = 0..iters.  info (nullable).
+ */
+dg_status dg_pcg_solve(dg_ctx* ctx, int32_t graph_id, const double* d_b, double* d_x, const dg_pcg_options* opt,
+                       dg_pcg_info* info, double* hist);
+
+typedef struct {
+    int32_t max_iter;       /* Lanczos steps (> 0) */
+    int32_t check_every;    /* Ritz values are checked every this many steps (> 0) */
+    double tol;             /* stop when lambda_max moved by less than tol * lambda_max between checks */
+    double inner_tol;       /* each L_H solve runs to this relative residual ... */
+    int32_t inner_max_iter; /* ... or this many iterations */
+    int32_t reserved;
+    const double* d_v0;     /* start vector (device, n doubles; NULL: Philox4x32-10 draws keyed by seed) */
+    uint64_t seed;
+} dg_kappa_options;         /* 48 bytes */
+
+typedef struct {
+    double kappa;           /* lambda_max of the pencil (L_G, L_H) (+inf when H does not span G's components) */
+    double lambda_min;      /* smallest Ritz value (approaches 1 from above for a subgraph H) */
+    int32_t iters;          /* Lanczos steps taken */
+    int32_t converged;
+    int64_t inner_iters;    /* inner (L_H) iterations over all steps */
+    double ms;
+} dg_kappa_info;            /* 40 bytes */
+
+/*
+ * kappa(L_G, L_H) (Eqs. 6-10): for H a subgraph of G the smallest eigenvalue
+ * of the pencil is 1 (Section III-C), so kappa is its largest, found here by
+ * Lanczos in the L_H inner product on L_H^+ L_G: v_1 = v_0 / ||v_0||_H; per
+ * step u = L_G v_j, alpha_j = (v_j, u), w = L_H^+ u - alpha_j v_j -
+ * beta_{j-1} v_{j-1}, beta_j = ||w||_H, v_{j+1} = w / beta_j.  The largest
+ * eigenvalue of the tridiagonal (alpha, beta) is found by multisection on
+ * its Sturm counts.  L_H^+ is the inner solve of dg_pcg_solve.  With
+ * d_v0 == NULL the start vector is x -> 2 u(x) - 1, u(x) the first Philox
+ * word of counter (x, 0, 0, 0) and key (seed low, seed high) scaled by 2^-32.
+ */
+dg_status dg_condition_number(dg_ctx* ctx, int32_t graph_id, const dg_kappa_options* opt, dg_kappa_info* info);
+
+/* Test hooks of the quality calls.  dg_debug_sparsifier_forest writes the
+ * edges (u < v, lexicographic order) of H's maximum-weight spanning forest
+ * into host arrays of cap entries, *nf_out = their count (cap too small:
+ * DG_E_INVALID).  dg_debug_forest_solve sets d_z = L_F^+ d_r up to a
+ * constant per tree (z = 0 at each tree's smallest vertex), F that forest. */
+dg_status dg_debug_sparsifier_forest(dg_ctx* ctx, int32_t graph_id, int64_t cap, int32_t* fu, int32_t* fv,
+                                     int64_t* nf_out);
+dg_status dg_debug_forest_solve(dg_ctx* ctx, int32_t graph_id, const double* d_r, double* d_z);
+
 #ifdef __cplusplus
 }
 #endif

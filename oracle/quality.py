@@ -24,11 +24,17 @@ Each function below is the textbook definition:
   Sparse Linear Systems, Algorithm 9.1): x0 = 0, r0 = b, z0 = M^-1 r0,
   p0 = z0; alpha = (r, z) / (A p, p); x += alpha p; r -= alpha A p;
   stop when ||r|| / ||b|| < tol; z = M^-1 r; beta = (r_new, z_new) / (r, z);
-  p = z + beta p.  M^-1 is exact: for M = L_H it solves the Laplacian system
-  of every component of H grounded at the component's smallest vertex (a
-  sparse LU factorization, scipy's SuperLU), which is L_H^+ r up to a
-  constant per component (constants change neither the residuals nor the
-  iteration count, since r and A p are orthogonal to them).
+  p = z + beta p.  M^-1 is exact: for M = L_H it is the pseudo-inverse
+  L_H^+ = P S P, with S the solve of every component's Laplacian grounded at
+  its smallest vertex (a sparse LU factorization, scipy's SuperLU) and P the
+  projection that removes the mean of every component.
+* ``forest_potentials``: the exact solve of a forest Laplacian, L_F z = r, in
+  its physical reading: with every tree rooted at its smallest vertex
+  (z = 0 there), the current through the edge (parent(y), y) is the sum of r
+  over y's subtree and z_y is the sum of current / weight over the edges of
+  y's root path.  Both sums are taken exactly (rational arithmetic) and
+  rounded once, and the division once, so the result is the correctly
+  rounded potential of the correctly rounded currents.
 """
 from __future__ import annotations
 
@@ -69,8 +75,10 @@ class LaplacianSolver:
         lab = components(n, list(a), list(b))
         self.n = n
         self.parts = []
+        self.comps = []
         for c in np.unique(lab):
             verts = np.flatnonzero(lab == c)  # ascending: verts[0] is the smallest vertex
+            self.comps.append(verts)
             rest = verts[1:]
             if rest.size == 0:
                 continue
@@ -82,6 +90,17 @@ class LaplacianSolver:
         for rest, lu in self.parts:
             z[rest] = lu.solve(r[rest])
         return z
+
+    def pinv_apply(self, r: np.ndarray) -> np.ndarray:
+        """L^+ r: with P the projection that removes the mean of every
+        component and S the grounded solve, L^+ = P S P."""
+        return self._center(self.solve(self._center(np.asarray(r, np.float64))))
+
+    def _center(self, v):
+        y = v.copy()
+        for verts in self.comps:
+            y[verts] -= y[verts].mean()
+        return y
 
 
 def pcg(n, g_edges, b, *, h_edges=None, precond="sparsifier", tol=1e-8, max_iter=10_000):
@@ -101,7 +120,9 @@ def pcg(n, g_edges, b, *, h_edges=None, precond="sparsifier", tol=1e-8, max_iter
             return r / d
     elif precond == "sparsifier":
         S = LaplacianSolver(n, *h_edges)
-        minv = S.solve
+
+        def minv(r):
+            return S.pinv_apply(r)
     else:
         raise ValueError(precond)
     x = np.zeros(n)
@@ -130,6 +151,46 @@ def pcg(n, g_edges, b, *, h_edges=None, precond="sparsifier", tol=1e-8, max_iter
         rz = rz_new
         p = z + beta * p
     return x, it, hist
+
+
+def forest_potentials(n, a, b, w, r) -> np.ndarray:
+    """z with L_F z = r on the forest (a, b, w), z = 0 at each tree's smallest vertex."""
+    from fractions import Fraction
+    adj = [[] for _ in range(n)]
+    for x, y, ww in zip(a, b, w):
+        adj[int(x)].append((int(y), float(ww)))
+        adj[int(y)].append((int(x), float(ww)))
+    parent = [-1] * n
+    pw = [0.0] * n
+    seen = [False] * n
+    order = []  # every vertex after its parent
+    for s in range(n):  # the first vertex met of each tree is its smallest
+        if seen[s]:
+            continue
+        seen[s] = True
+        stack = [s]
+        while stack:
+            x = stack.pop()
+            order.append(x)
+            for y, ww in adj[x]:
+                if not seen[y]:
+                    seen[y] = True
+                    parent[y] = x
+                    pw[y] = ww
+                    stack.append(y)
+    sub = [Fraction(float(v)) for v in r]
+    for x in reversed(order):
+        if parent[x] >= 0:
+            sub[parent[x]] += sub[x]
+    pot = [Fraction(0)] * n
+    z = np.zeros(n)
+    for x in order:
+        p = parent[x]
+        if p >= 0:
+            a_x = float(sub[x]) / pw[x]
+            pot[x] = pot[p] + Fraction(a_x)
+            z[x] = float(pot[x])
+    return z
 
 
 def project_out_constants(n, a, b, x) -> np.ndarray:

@@ -46,7 +46,11 @@ EXPORTS = ("dg_config_default", "dg_create", "dg_destroy", "dg_status_str", "dg_
            "dg_graph_bytes", "dg_launch_count", "dg_set_next_update_id", "dg_get_next_update_id",
            "dg_set_walk_shape", "dg_set_walk_refill", "dg_submit_updates", "dg_wait", "dg_walk_estimate_noalloc",
            "dg_debug_set_wait_limit", "dg_shard_begin", "dg_shard_export", "dg_shard_commit", "dg_wait_ex",
-           "dg_prepare", "dg_init_sparsifier_grass")
+           "dg_prepare", "dg_init_sparsifier_grass", "dg_sparsifier_density", "dg_laplacian_apply",
+           "dg_pcg_solve", "dg_condition_number", "dg_debug_sparsifier_forest", "dg_debug_forest_solve")
+
+LAP_G, LAP_H = 0, 1
+PRECOND = {"none": 0, "jacobi": 1, "sparsifier": 2}
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -73,6 +77,31 @@ class BatchStats(C.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class PcgOptions(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("precond", C.c_int32), ("inner_tol", C.c_double),
+                ("inner_max_iter", C.c_int32), ("reserved", C.c_int32)]
+
+
+class PcgInfo(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("converged", C.c_int32), ("rel_residual", C.c_double),
+                ("inner_iters", C.c_int64), ("inner_max", C.c_int32), ("inner_unconverged", C.c_int32),
+                ("ms", C.c_double)]
+
+
+class KappaOptions(C.Structure):
+    _fields_ = [("max_iter", C.c_int32), ("check_every", C.c_int32), ("tol", C.c_double), ("inner_tol", C.c_double),
+                ("inner_max_iter", C.c_int32), ("reserved", C.c_int32), ("d_v0", C.c_void_p), ("seed", C.c_uint64)]
+
+
+class KappaInfo(C.Structure):
+    _fields_ = [("kappa", C.c_double), ("lambda_min", C.c_double), ("iters", C.c_int32), ("converged", C.c_int32),
+                ("inner_iters", C.c_int64), ("ms", C.c_double)]
+
+
+def _as_dict(st):
+    return {k: getattr(st, k) for k, _ in st._fields_ if not k.startswith("reserved")}
 
 
 class DgError(RuntimeError):
@@ -126,6 +155,12 @@ def load_library(path: str | None = None):
         "dg_wait_ex": (i32, [P, u64, i32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "dg_prepare": (i32, [P, i32, i64]),
         "dg_init_sparsifier_grass": (i32, [P, i32, i64, P, P, i64, P]),
+        "dg_sparsifier_density": (i32, [P, i32, C.POINTER(C.c_double), C.POINTER(i64), C.POINTER(i64)]),
+        "dg_laplacian_apply": (i32, [P, i32, i32, P, P, P]),
+        "dg_pcg_solve": (i32, [P, i32, P, P, C.POINTER(PcgOptions), C.POINTER(PcgInfo), P]),
+        "dg_condition_number": (i32, [P, i32, C.POINTER(KappaOptions), C.POINTER(KappaInfo)]),
+        "dg_debug_sparsifier_forest": (i32, [P, i32, i64, P, P, C.POINTER(i64)]),
+        "dg_debug_forest_solve": (i32, [P, i32, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -410,3 +445,47 @@ class Graph:
     def prepare(self, max_batch: int):
         """Size the workspace and capture the batch steps for batches up to max_batch."""
         _check(self._L.dg_prepare(self.ctx._h, self.gid, int(max_batch)))
+
+    # ---- quality of the sparsifier (Section IV) ------------------------------
+    def density(self):
+        """(d_H, |E(G)|, |E(H)|) with d_H = |E(H)| / |V| - 1."""
+        d, mg, mh = C.c_double(), C.c_int64(), C.c_int64()
+        _check(self._L.dg_sparsifier_density(self.ctx._h, self.gid, C.byref(d), C.byref(mg), C.byref(mh)))
+        return d.value, mg.value, mh.value
+
+    def laplacian_apply(self, which: int, d_x: int, d_y: int, stream=None):
+        """y = L x for G (LAP_G) or H (LAP_H); device pointers to n doubles."""
+        _check(self._L.dg_laplacian_apply(self.ctx._h, self.gid, int(which), d_x, d_y, stream))
+
+    def pcg_solve(self, d_b: int, d_x: int, *, tol=1e-8, max_iter=1000, precond="sparsifier", inner_tol=1e-12,
+                  inner_max_iter=5000, history=True):
+        """PCG on L_G x = b (device pointers); returns (info dict, relative residual history)."""
+        o = PcgOptions(tol=tol, max_iter=int(max_iter), precond=PRECOND[precond], inner_tol=inner_tol,
+                       inner_max_iter=int(inner_max_iter))
+        info = PcgInfo()
+        hist = np.zeros(int(max_iter) + 1) if history else None
+        _check(self._L.dg_pcg_solve(self.ctx._h, self.gid, d_b, d_x, C.byref(o), C.byref(info),
+                                    _ptr(hist) if hist is not None else None))
+        d = _as_dict(info)
+        return d, (hist[: d["iters"] + 1] if hist is not None else None)
+
+    def condition_number(self, *, max_iter=200, check_every=5, tol=1e-10, inner_tol=1e-12, inner_max_iter=5000,
+                         d_v0=None, seed=0):
+        """kappa(L_G, L_H) by Lanczos on the pencil; d_v0: device pointer to a start vector (or None)."""
+        o = KappaOptions(max_iter=int(max_iter), check_every=int(check_every), tol=tol, inner_tol=inner_tol,
+                         inner_max_iter=int(inner_max_iter), d_v0=d_v0, seed=int(seed))
+        info = KappaInfo()
+        _check(self._L.dg_condition_number(self.ctx._h, self.gid, C.byref(o), C.byref(info)))
+        return _as_dict(info)
+
+    def debug_sparsifier_forest(self):
+        """Edges (u < v, lexicographic) of H's maximum-weight spanning forest."""
+        nf = C.c_int64()
+        fu = np.empty(max(self.n, 1), np.int32)
+        fv = np.empty(max(self.n, 1), np.int32)
+        _check(self._L.dg_debug_sparsifier_forest(self.ctx._h, self.gid, fu.size, _ptr(fu), _ptr(fv), C.byref(nf)))
+        return fu[: nf.value].copy(), fv[: nf.value].copy()
+
+    def debug_forest_solve(self, d_r: int, d_z: int):
+        """z = L_F^+ r up to a constant per tree (z = 0 at each tree's smallest vertex)."""
+        _check(self._L.dg_debug_forest_solve(self.ctx._h, self.gid, d_r, d_z))

@@ -57,6 +57,10 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(dg_walk_estimate), offsetof(dg_walk_estimate, status),
          offsetof(dg_walk_estimate, nhits), offsetof(dg_walk_estimate, best_walker),
          offsetof(dg_walk_estimate, steps), offsetof(dg_walk_estimate, r_est), offsetof(dg_walk_estimate, hit));
+  printf("%zu %zu %zu %zu\n", sizeof(dg_pcg_options), sizeof(dg_pcg_info), sizeof(dg_kappa_options),
+         sizeof(dg_kappa_info));
+  printf("%zu %zu %zu %zu %zu\n", offsetof(dg_pcg_options, inner_tol), offsetof(dg_pcg_info, inner_iters),
+         offsetof(dg_pcg_info, ms), offsetof(dg_kappa_options, d_v0), offsetof(dg_kappa_info, inner_iters));
   return 0;
 }
 """
@@ -83,6 +87,11 @@ int main(void) {
     e = vals[16:23]
     assert e[0] == D.ESTIMATE_DTYPE.itemsize == 32
     assert e[1:] == [D.ESTIMATE_DTYPE.fields[f][1] for f in ("status", "nhits", "best_walker", "steps", "r_est", "hit")]
+    qs = vals[23:27]
+    assert qs == [C.sizeof(D.PcgOptions), C.sizeof(D.PcgInfo), C.sizeof(D.KappaOptions), C.sizeof(D.KappaInfo)]
+    assert qs == [32, 40, 48, 40]
+    assert vals[27:32] == [D.PcgOptions.inner_tol.offset, D.PcgInfo.inner_iters.offset, D.PcgInfo.ms.offset,
+                           D.KappaOptions.d_v0.offset, D.KappaInfo.inner_iters.offset]
 
 
 def test_host_only_calls(lib):

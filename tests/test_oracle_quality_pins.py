@@ -191,3 +191,43 @@ def test_smallest_pencil_eigenvalue_is_one_for_a_subgraph():
     ev = checks.pencil_eigs(n, (a, b, w), (a[keep], b[keep], w[keep]))
     assert ev[0] == pytest.approx(1.0, abs=1e-9)
     assert checks.kappa(n, (a, b, w), (a[keep], b[keep], w[keep])) == pytest.approx(ev[-1], rel=1e-9)
+
+
+def test_forest_potentials_on_a_path_and_against_the_grounded_solve():
+    """Unit path: unit current from 0 to n-1 drops the potential by one per
+    edge; on random weighted forests the exact potentials solve L_F z = r and
+    agree with the grounded sparse solve."""
+    n = 9
+    z = Q.forest_potentials(n, *_path(n), np.eye(n)[0] - np.eye(n)[n - 1])
+    assert np.array_equal(z, -np.arange(n, dtype=float))
+    rng = np.random.default_rng(12)
+    for trial in range(3):
+        n = 60
+        a, b, w = _random_graph(n, 90, rng, connected=trial != 1)
+        f = Q.max_spanning_forest(n, a, b, w)
+        fa, fb, fw = a[f], b[f], w[f]
+        r = Q.project_out_constants(n, fa, fb, rng.standard_normal(n))
+        z = Q.forest_potentials(n, fa, fb, fw, r)
+        L = Q.laplacian_csr(n, fa, fb, fw)
+        assert np.abs(L @ z - r).max() < 1e-12
+        zr = Q.LaplacianSolver(n, fa, fb, fw).solve(r)
+        assert np.abs(z - zr).max() < 1e-10 * np.abs(zr).max()
+        lab = checks.components(n, list(fa), list(fb))
+        for c in np.unique(lab):
+            assert z[np.flatnonzero(lab == c)[0]] == 0.0
+
+
+def test_pseudo_inverse_apply_matches_pinv():
+    """P S P (grounded solves between mean projections) is the Moore-Penrose
+    pseudo-inverse, also for right-hand sides with a constant part."""
+    rng = np.random.default_rng(13)
+    a1, b1, w1 = _random_graph(15, 30, rng)
+    a2, b2, w2 = _random_graph(9, 14, rng)
+    a = np.concatenate([a1, a2 + 15])
+    b = np.concatenate([b1, b2 + 15])
+    w = np.concatenate([w1, w2])
+    n = 26  # one isolated vertex
+    r = rng.standard_normal(n)
+    z = Q.LaplacianSolver(n, a, b, w).pinv_apply(r)
+    zp = np.linalg.pinv(checks.laplacian(n, a, b, w), hermitian=True) @ r
+    assert np.abs(z - zp).max() < 1e-10 * np.abs(zp).max()

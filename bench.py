@@ -476,6 +476,85 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_quality(args):
+    """--workload quality: the quality experiment of Section IV (Tables II-IV)
+    on the 3-D mesh: ten insertion batches adding 25 % of |V| edges, then
+    d_H^(0) -> d_H^(10), kappa(G0, H0), kappa(G10, H0) (H left alone),
+    kappa(G10, H10) (dyGRASS updates), and the PCG iterations to a relative
+    residual of 1e-8 with each sparsifier as preconditioner.  The CG
+    iteration without preconditioner is timed for the roofline of the
+    Laplacian-product path."""
+    import torch
+    from paper_2505_02741_b300 import dygrass as D
+    from paper_2505_02741_b300 import workloads as W
+    dims = tuple(int(x) for x in args.quality_mesh.split("x"))
+    wl, st = W.make_mesh3d(*dims, seed=11)
+    n = wl.n
+    per = max(1, int(0.25 * n) // 10)
+    ctx = D.Context(K=wl.K, T=wl.T, s=wl.s)
+    clk = ClockSampler(0).start()
+    g = ctx.load_graph(n, wl.a, wl.b, wl.w)
+    g.init_sparsifier(wl.a[wl.h_ids], wl.b[wl.h_ids])
+    h0 = g.sparsifier()
+    rng = np.random.default_rng(5)
+    b = rng.standard_normal(n)
+    b -= b.mean()  # the mesh is connected
+    db = torch.from_numpy(b).cuda()
+    dx = torch.empty_like(db)
+    kopt = dict(max_iter=args.lanczos_iters, check_every=10, tol=1e-6, inner_tol=1e-10, inner_max_iter=2000)
+    popt = dict(tol=1e-8, max_iter=5000, precond="sparsifier", inner_tol=1e-10, inner_max_iter=2000)
+
+    def measure(gr):
+        k = gr.condition_number(**kopt)
+        info, _ = gr.pcg_solve(db.data_ptr(), dx.data_ptr(), **popt)
+        return k, info
+
+    with clk:
+        d0 = g.density()
+        k00, p00 = measure(g)
+        dens = [d0[0]]
+        upd_ms = []
+        for _ in range(10):
+            bt = st.next_batch(per, 0)
+            t0 = time.perf_counter()
+            g.apply(D.make_updates(bt.u, bt.v, bt.w, bt.op))
+            upd_ms.append(1e3 * (time.perf_counter() - t0))
+            dens.append(g.density()[0])
+        k11, p11 = measure(g)
+        ga, gb, gw = g.edges()
+        g2 = ctx.load_graph(n, ga, gb, gw)
+        g2.init_sparsifier(h0[0], h0[1])
+        k10, p10 = measure(g2)
+        # plain CG: one iteration's Laplacian product and vector updates
+        info_cg, _ = g.pcg_solve(db.data_ptr(), dx.data_ptr(), tol=1e-30, max_iter=args.cg_iters, precond="none")
+    clk.stop()
+    nnz = 2 * ga.size
+    it_ms = info_cg["ms"] / max(1, info_cg["iters"])
+    # algorithmic bytes of one CG iteration: the product (column id 4 B and
+    # weight 8 B per stored entry; row pointer, diagonal, x_i and y_i per row)
+    # and the vector passes (p.q: 2, x/r update: 5 reads+writes, r.r inside,
+    # r.z with z = r: 2, p update: 3, the copy z = r: 2 -> 14 vectors of 8 B)
+    alg = 12 * nnz + 28 * n + 14 * 8 * n
+    peak, peak_kind = measured_peaks()
+    line = {"metric": "sparsifier quality: kappa(L_G, L_H), d_H and PCG iterations (Section IV)", "workload": "quality",
+            "value": p11["iters"], "unit": "PCG iterations to 1e-8 with the updated sparsifier",
+            "higher_is_better": False, "n_gpus": 1, "dtype": "f64", "data": "synthetic",
+            "config": {"graph": f"mesh3d_{args.quality_mesh}", "n": n, "m0": wl.m, "insert_batches": 10,
+                       "per_batch": per, "K": wl.K, "T": wl.T, "s": wl.s},
+            "d_H": dens, "kappa": {"G0_H0": k00["kappa"], "G10_H0": k10["kappa"], "G10_H10": k11["kappa"]},
+            "lanczos": {"G0_H0": k00, "G10_H0": k10, "G10_H10": k11},
+            "pcg_iters": {"G0_H0": p00["iters"], "G10_H0": p10["iters"], "G10_H10": p11["iters"]},
+            "pcg": {"G0_H0": p00, "G10_H0": p10, "G10_H10": p11},
+            "update_ms_per_batch": upd_ms,
+            "cg_iteration": {"ms": it_ms, "iters": info_cg["iters"], "algorithmic_bytes": alg,
+                             "roofline": {"bound": "hbm", "achieved": alg / (it_ms * 1e-3) / 1e9, "peak": peak,
+                                          "unit": "GB/s", "frac": alg / (it_ms * 1e-3) / 1e9 / peak,
+                                          "peak_source": peak_kind}},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -488,8 +567,12 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-full-walks", action="store_true", help="skip the unpruned-walk context line (mesh)")
     ap.add_argument("--walk-shape", default="", help="fixed walk launch shape 'block,ilp' (skips the autotuner)")
-    ap.add_argument("--workload", default="rmat", choices=["rmat", "mesh", "fea", "serve"],
-                    help="rmat (default line), mesh, fea, or serve (several graphs resident, Poisson arrivals)")
+    ap.add_argument("--workload", default="rmat", choices=["rmat", "mesh", "fea", "serve", "quality"],
+                    help="rmat (default line), mesh, fea, serve (several graphs resident, Poisson arrivals) "
+                         "or quality (kappa, d_H and PCG iterations, Section IV)")
+    ap.add_argument("--quality-mesh", default="100x100x100", help="quality: mesh dimensions")
+    ap.add_argument("--lanczos-iters", type=int, default=400, help="quality: Lanczos steps at most")
+    ap.add_argument("--cg-iters", type=int, default=200, help="quality: timed plain CG iterations")
     ap.add_argument("--rmat-scale", type=int, default=22, help="rmat: log2 of the vertex count")
     ap.add_argument("--rmat-edges", type=int, default=64_000_000, help="rmat: distinct undirected edges")
     ap.add_argument("--requests", type=int, default=1000, help="serve: requests per load point")
@@ -497,13 +580,15 @@ def main():
                     help="requests of the serving summary in the default line (0: skip it)")
     args = ap.parse_args()
     if args.impl == "reference":
-        if args.workload == "serve":
+        if args.workload in ("serve", "quality"):
             args.workload = "mesh"
         return run_reference(args)
     if args.warmup < 3:
         raise SystemExit("at least 3 warm-up steps")
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "quality":
+        return run_quality(args)
 
     import torch
     from paper_2505_02741_b300 import dygrass as D

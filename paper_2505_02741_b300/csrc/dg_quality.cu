@@ -16,9 +16,10 @@
 // prefix sums over the Euler tour of the tree: a subtree is a contiguous range
 // of the tour, and a root path is what stays open at y's entry.  The tour is
 // ranked once per call by pointer jumping; every solve is then two prefix sums
-// in double-double arithmetic (Knuth's two-sum), deterministic and accurate
-// to the last bit of the result even where a subtree's sum is small next to
-// the running prefix.
+// of 128-bit fixed-point images of the doubles: integer sums are exact in any
+// order, so each current and each potential is the exact sum rounded once,
+// even where a subtree's sum is small next to the running prefix (and the
+// sums cost integer adds, not the FP64 operations a compensated sum needs).
 //
 // F comes from Boruvka's algorithm with the strict order (weight descending,
 // then (min, max) endpoint pair ascending): every component takes its best
@@ -58,18 +59,79 @@ int dot_blocks() { return device_sms() * 2; }
     } while (0)
 
 // ---------------------------------------------------------------------------
-// double-double arithmetic (Knuth's two-sum; Dekker's fast two-sum)
+// exact sums of doubles in 128-bit fixed point.  A vector is scaled by 2^s,
+// s chosen from its largest exponent so that the sum of all its entries fits
+// in 125 bits; each entry becomes an integer (exact unless its lowest bits lie
+// 2^100 below the largest entry, where it is rounded), every prefix sum is
+// then an exact integer sum in any order, and a difference of two prefixes
+// turns back into a double with one rounding.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double2 dd_add(double2 x, double2 y) {
-    const double s = __dadd_rn(x.x, y.x);
-    const double bb = __dsub_rn(s, x.x);
-    const double e = __dadd_rn(__dsub_rn(x.x, __dsub_rn(s, bb)), __dsub_rn(y.x, bb));
-    const double t = __dadd_rn(e, __dadd_rn(x.y, y.y));
-    const double h = __dadd_rn(s, t);
-    return make_double2(h, __dsub_rn(t, __dsub_rn(h, s)));
+typedef __int128 i128;
+typedef unsigned __int128 u128;
+
+__device__ __forceinline__ uint32_t biased_exp(double v) {
+    return (uint32_t)((__double_as_longlong(v) >> 52) & 0x7FF);
 }
-__device__ __forceinline__ double2 dd_neg(double2 x) { return make_double2(-x.x, -x.y); }
-__device__ __forceinline__ double dd_val(double2 x) { return __dadd_rn(x.x, x.y); }
+
+// the scale 2^s for a vector whose largest biased exponent is e_max (|v| <
+// 2^(e_max - 1022)), summed over at most 2^nbits entries
+__device__ __forceinline__ int fixed_scale(uint32_t e_max, int nbits) {
+    return e_max == 0 ? 0 : 125 - nbits - ((int)e_max - 1022);
+}
+
+__device__ __forceinline__ i128 to_fixed(double v, int s) {
+    const long long bits = __double_as_longlong(v);
+    const int be = (int)((bits >> 52) & 0x7FF);
+    if (be == 0) return 0;  // zero (and subnormals, far below every scale used)
+    const long long man = (bits & 0xFFFFFFFFFFFFFll) | (1ll << 52);  // v = man * 2^(be - 1075)
+    const int sh = be - 1075 + s;
+    i128 q;
+    if (sh >= 0) q = (i128)man << sh;
+    else if (sh > -62) q = (i128)((man + (1ll << (-sh - 1))) >> (-sh));  // nearest, ties away from zero
+    else q = 0;
+    return bits < 0 ? -q : q;
+}
+
+// v * 2^-s, rounded once to nearest even
+__device__ __forceinline__ double from_fixed(i128 v, int s) {
+    const bool neg = v < 0;
+    const u128 m = neg ? (u128)(-v) : (u128)v;
+    const unsigned long long hi = (unsigned long long)(m >> 64);
+    double d;
+    int up = 0;
+    if (hi == 0) {
+        d = __ull2double_rn((unsigned long long)m);
+    } else {
+        const int sh = 64 - __clzll(hi);  // keep the top 64 bits, fold the rest into a sticky bit
+        unsigned long long t = (unsigned long long)(m >> sh);
+        if ((m & (((u128)1 << sh) - 1)) != 0) t |= 1ull;
+        d = __ull2double_rn(t);
+        up = sh;
+    }
+    d = ldexp(d, up - s);
+    return neg ? -d : d;
+}
+
+__device__ __forceinline__ i128 shfl_up_i128(i128 v, int d) {
+    const unsigned long long lo = __shfl_up_sync(0xffffffffu, (unsigned long long)v, d);
+    const long long hi = __shfl_up_sync(0xffffffffu, (long long)(v >> 64), d);
+    return ((i128)hi << 64) | (i128)lo;
+}
+
+// the largest biased exponent of v[0..n) into *e (atomicMax; *e zeroed before)
+__global__ void k_max_exp(const double* __restrict__ v, uint32_t n, uint32_t* e, const uint32_t* skip) {
+    if (skip && *skip) return;
+    uint32_t m = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        m = max(m, biased_exp(v[i]));
+    for (int k = 16; k > 0; k >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, k));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(e, m);
+}
+
+__global__ void k_zero_words(uint32_t* w, int k, const uint32_t* skip) {
+    if (skip && *skip) return;
+    if (threadIdx.x < (unsigned)k) w[threadIdx.x] = 0;
+}
 
 // block-wide sum of one double per thread in a fixed tree
 __device__ double block_sum(double v, double* sh) {
@@ -511,83 +573,93 @@ __global__ void k_fill_u32(uint32_t* p, uint32_t n, uint32_t v) {
 }
 
 // ---------------------------------------------------------------------------
-// exclusive prefix sums in double-double (deterministic: fixed slices and trees)
+// exclusive prefix sums of 128-bit integers (exact, so any grouping gives the
+// same result)
 // ---------------------------------------------------------------------------
-constexpr int DD_ITEMS = 8;
-constexpr int DD_TILE = QT * DD_ITEMS;
+constexpr int IS_ITEMS = 8;
+constexpr int IS_TILE = QT * IS_ITEMS;
 
-// exclusive prefix over the block (Kogge-Stone in a fixed pattern); total = the block's sum
-__device__ double2 block_dd_scan(double2 v, double2* sh, double2* total) {
-    sh[threadIdx.x] = v;
-    __syncthreads();
-    for (int d = 1; d < (int)blockDim.x; d <<= 1) {
-        double2 t = sh[threadIdx.x];
-        if ((int)threadIdx.x >= d) t = dd_add(sh[threadIdx.x - d], t);
-        __syncthreads();
-        sh[threadIdx.x] = t;
-        __syncthreads();
+// exclusive prefix over the block by warp shuffles, then the warp totals;
+// total (nullable) = the block's sum
+__device__ i128 block_i128_scan(i128 v, i128* sh, i128* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    i128 incl = v;
+    for (int d = 1; d < 32; d <<= 1) {
+        const i128 t = shfl_up_i128(incl, d);
+        if (lane >= d) incl += t;
     }
-    const double2 excl = threadIdx.x ? sh[threadIdx.x - 1] : make_double2(0.0, 0.0);
-    if (total) *total = sh[blockDim.x - 1];
+    if (lane == 31) sh[wid] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        i128 run = 0;
+        for (int w = 0; w < nw; ++w) {
+            const i128 t = sh[w];
+            sh[w] = run;
+            run += t;
+        }
+        sh[nw] = run;
+    }
+    __syncthreads();
+    const i128 excl = sh[wid] + incl - v;
+    if (total) *total = sh[nw];
     __syncthreads();
     return excl;
 }
 
-__global__ void __launch_bounds__(QT) k_dd_tile_sums(const double2* __restrict__ in, uint32_t n,
-                                                     double2* __restrict__ tsum, const uint32_t* skip) {
-    __shared__ double2 sh[QT];
+__global__ void __launch_bounds__(QT) k_is_tile_sums(const i128* __restrict__ in, uint32_t n, i128* __restrict__ tsum,
+                                                     const uint32_t* skip) {
+    __shared__ i128 sh[QT / 32 + 1];
     if (skip && *skip) return;
-    const uint64_t base = (uint64_t)blockIdx.x * DD_TILE + (uint64_t)threadIdx.x * DD_ITEMS;
-    double2 s = make_double2(0.0, 0.0);
-    for (int i = 0; i < DD_ITEMS; ++i)
-        if (base + i < n) s = dd_add(s, in[base + i]);
-    double2 tot;
-    block_dd_scan(s, sh, &tot);
+    const uint64_t base = (uint64_t)blockIdx.x * IS_TILE + (uint64_t)threadIdx.x * IS_ITEMS;
+    i128 s = 0;
+    for (int i = 0; i < IS_ITEMS; ++i)
+        if (base + i < n) s += in[base + i];
+    i128 tot;
+    block_i128_scan(s, sh, &tot);
     if (threadIdx.x == 0) tsum[blockIdx.x] = tot;
 }
 
 // exclusive scan of the tile sums by one block (each thread a fixed run of tiles)
-__global__ void __launch_bounds__(1024) k_dd_scan_tiles(double2* tsum, uint32_t tiles, const uint32_t* skip) {
-    __shared__ double2 sh[1024];
+__global__ void __launch_bounds__(1024) k_is_scan_tiles(i128* tsum, uint32_t tiles, const uint32_t* skip) {
+    __shared__ i128 sh[1024 / 32 + 1];
     if (skip && *skip) return;
     const uint32_t per = (tiles + blockDim.x - 1) / blockDim.x;
     const uint32_t lo = threadIdx.x * per, hi = min(tiles, lo + per);
-    double2 s = make_double2(0.0, 0.0);
-    for (uint32_t t = lo; t < hi; ++t) s = dd_add(s, tsum[t]);
-    double2 run = block_dd_scan(s, sh, nullptr);
+    i128 s = 0;
+    for (uint32_t t = lo; t < hi; ++t) s += tsum[t];
+    i128 run = block_i128_scan(s, sh, nullptr);
     for (uint32_t t = lo; t < hi; ++t) {
-        const double2 v = tsum[t];
+        const i128 v = tsum[t];
         tsum[t] = run;
-        run = dd_add(run, v);
+        run += v;
     }
 }
 
-__global__ void __launch_bounds__(QT) k_dd_tile_scan(const double2* __restrict__ in, uint32_t n,
-                                                     const double2* __restrict__ tpre, double2* __restrict__ out,
+__global__ void __launch_bounds__(QT) k_is_tile_scan(const i128* __restrict__ in, uint32_t n,
+                                                     const i128* __restrict__ tpre, i128* __restrict__ out,
                                                      const uint32_t* skip) {
-    __shared__ double2 sh[QT];
+    __shared__ i128 sh[QT / 32 + 1];
     if (skip && *skip) return;
-    const uint64_t base = (uint64_t)blockIdx.x * DD_TILE + (uint64_t)threadIdx.x * DD_ITEMS;
-    double2 loc[DD_ITEMS];
-    double2 s = make_double2(0.0, 0.0);
-    for (int i = 0; i < DD_ITEMS; ++i) {
-        loc[i] = base + i < n ? in[base + i] : make_double2(0.0, 0.0);
-        s = dd_add(s, loc[i]);
+    const uint64_t base = (uint64_t)blockIdx.x * IS_TILE + (uint64_t)threadIdx.x * IS_ITEMS;
+    i128 loc[IS_ITEMS];
+    i128 s = 0;
+    for (int i = 0; i < IS_ITEMS; ++i) {
+        loc[i] = base + i < n ? in[base + i] : (i128)0;
+        s += loc[i];
     }
-    double2 run = dd_add(tpre[blockIdx.x], block_dd_scan(s, sh, nullptr));
-    for (int i = 0; i < DD_ITEMS; ++i) {
+    i128 run = tpre[blockIdx.x] + block_i128_scan(s, sh, nullptr);
+    for (int i = 0; i < IS_ITEMS; ++i) {
         if (base + i < n) out[base + i] = run;
-        run = dd_add(run, loc[i]);
+        run += loc[i];
     }
 }
 
-void dd_scan_exclusive(const double2* in, double2* out, uint32_t n, double2* tsum, cudaStream_t st,
-                       const uint32_t* skip) {
+void i128_scan_exclusive(const i128* in, i128* out, uint32_t n, i128* tsum, cudaStream_t st, const uint32_t* skip) {
     if (!n) return;
-    const uint32_t tiles = (n + DD_TILE - 1) / DD_TILE;
-    QLAUNCH(k_dd_tile_sums, tiles, QT, st, in, n, tsum, skip);
-    QLAUNCH(k_dd_scan_tiles, 1, 1024, st, tsum, tiles, skip);
-    QLAUNCH(k_dd_tile_scan, tiles, QT, st, in, n, tsum, out, skip);
+    const uint32_t tiles = (n + IS_TILE - 1) / IS_TILE;
+    QLAUNCH(k_is_tile_sums, tiles, QT, st, in, n, tsum, skip);
+    QLAUNCH(k_is_scan_tiles, 1, 1024, st, tsum, tiles, skip);
+    QLAUNCH(k_is_tile_scan, tiles, QT, st, in, n, tsum, out, skip);
 }
 
 // ---------------------------------------------------------------------------
@@ -595,66 +667,82 @@ void dd_scan_exclusive(const double2* in, double2* out, uint32_t n, double2* tsu
 // ---------------------------------------------------------------------------
 struct Forest {
     uint32_t n = 0, nf = 0, nh = 0, ntrees = 0;
+    int nbits = 1;  // a tour prefix sum has at most 2^nbits terms
     DBuf<uint32_t> tin, tout, root, toff, tlen, tsz;  // tlen, tsz: tour length and size at each root
-    DBuf<double> tw, mean;
-    DBuf<double2> A, P, tsum;
+    DBuf<uint32_t> ex;                                // largest exponents of the vectors being summed
+    DBuf<double> tw, mean, av;
+    DBuf<i128> A, P, tsum;
     std::vector<unsigned long long> host_edges;  // filled on request (test hook)
     void release(DevAlloc& a, cudaStream_t st) {
-        tin.release(a, st);
-        tout.release(a, st);
-        root.release(a, st);
-        toff.release(a, st);
-        tlen.release(a, st);
-        tsz.release(a, st);
+        for (auto* b : {&tin, &tout, &root, &toff, &tlen, &tsz, &ex}) b->release(a, st);
         tw.release(a, st);
         mean.release(a, st);
+        av.release(a, st);
         A.release(a, st);
         P.release(a, st);
         tsum.release(a, st);
     }
 };
 
-// A[tin_y] = r_y, A[tout_y] = 0 for every non-root y
+// A[tin_y] = r_y, A[tout_y] = 0 for every non-root y, in fixed point
 __global__ void k_fs_scatter(uint32_t n, const uint32_t* __restrict__ tin, const uint32_t* __restrict__ tout,
-                             const double* __restrict__ r, double2* __restrict__ A, const uint32_t* skip) {
+                             const double* __restrict__ r, const uint32_t* ex, int nbits, i128* __restrict__ A,
+                             const uint32_t* skip) {
     if (skip && *skip) return;
+    const int s = fixed_scale(ex[0], nbits);
     for (uint32_t y = blockIdx.x * blockDim.x + threadIdx.x; y < n; y += gridDim.x * blockDim.x) {
         const uint32_t i = tin[y];
         if (i == NONE) continue;
-        A[i] = make_double2(r[y], 0.0);
-        A[tout[y]] = make_double2(0.0, 0.0);
+        A[i] = to_fixed(r[y], s);
+        A[tout[y]] = 0;
     }
 }
 
-// current through y's parent edge = subtree sum; B[tin] = +I/w, B[tout] = -I/w
+// current through y's parent edge = subtree sum (exact, rounded once); a_y = I / w
 __global__ void k_fs_flow(uint32_t n, const uint32_t* __restrict__ tin, const uint32_t* __restrict__ tout,
-                          const double* __restrict__ tw, const double2* __restrict__ P, double2* __restrict__ B,
-                          const uint32_t* skip) {
+                          const double* __restrict__ tw, const i128* __restrict__ P, uint32_t* ex, int nbits,
+                          double* __restrict__ av, const uint32_t* skip) {
     if (skip && *skip) return;
+    const int s = fixed_scale(ex[0], nbits);
+    uint32_t m = 0;
     for (uint32_t y = blockIdx.x * blockDim.x + threadIdx.x; y < n; y += gridDim.x * blockDim.x) {
         const uint32_t i = tin[y];
         if (i == NONE) continue;
-        const double I = dd_val(dd_add(P[tout[y]], dd_neg(P[i])));
+        const double I = from_fixed(P[tout[y]] - P[i], s);
         const double a = __ddiv_rn(I, tw[y]);
-        B[i] = make_double2(a, 0.0);
-        B[tout[y]] = make_double2(-a, 0.0);
+        av[y] = a;
+        m = max(m, biased_exp(a));
+    }
+    for (int k = 16; k > 0; k >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, k));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(&ex[1], m);
+}
+
+// B[tin] = +a, B[tout] = -a in fixed point
+__global__ void k_fs_scatter_a(uint32_t n, const uint32_t* __restrict__ tin, const uint32_t* __restrict__ tout,
+                               const double* __restrict__ av, const uint32_t* ex, int nbits, i128* __restrict__ B,
+                               const uint32_t* skip) {
+    if (skip && *skip) return;
+    const int s = fixed_scale(ex[1], nbits);
+    for (uint32_t y = blockIdx.x * blockDim.x + threadIdx.x; y < n; y += gridDim.x * blockDim.x) {
+        const uint32_t i = tin[y];
+        if (i == NONE) continue;
+        const i128 q = to_fixed(av[y], s);
+        B[i] = q;
+        B[tout[y]] = -q;
     }
 }
 
 // potential: the open edges at y's entry, i.e. the prefix through tin_y minus
-// the prefix at the start of y's tour
+// the prefix at the start of y's tour (exact, rounded once)
 __global__ void k_fs_potential(uint32_t n, const uint32_t* __restrict__ tin, const uint32_t* __restrict__ root,
-                               const uint32_t* __restrict__ toff, const double2* __restrict__ B,
-                               const double2* __restrict__ Q, double* __restrict__ z, const uint32_t* skip) {
+                               const uint32_t* __restrict__ toff, const i128* __restrict__ B,
+                               const i128* __restrict__ Q, const uint32_t* ex, int nbits, double* __restrict__ z,
+                               const uint32_t* skip) {
     if (skip && *skip) return;
+    const int s = fixed_scale(ex[1], nbits);
     for (uint32_t y = blockIdx.x * blockDim.x + threadIdx.x; y < n; y += gridDim.x * blockDim.x) {
         const uint32_t i = tin[y];
-        if (i == NONE) {
-            z[y] = 0.0;
-            continue;
-        }
-        const double2 incl = dd_add(Q[i], B[i]);
-        z[y] = dd_val(dd_add(incl, dd_neg(Q[toff[root[y]]])));
+        z[y] = i == NONE ? 0.0 : from_fixed(Q[i] + B[i] - Q[toff[root[y]]], s);
     }
 }
 
@@ -662,21 +750,27 @@ void forest_solve(Forest& F, const double* r, double* z, cudaStream_t st, const 
     const uint32_t n = F.n;
     if (!n) return;
     if (F.nh) {
-        QLAUNCH(k_fs_scatter, q_grid(n), QT, st, n, F.tin.p, F.tout.p, r, F.A.p, skip);
-        dd_scan_exclusive(F.A.p, F.P.p, F.nh, F.tsum.p, st, skip);
-        QLAUNCH(k_fs_flow, q_grid(n), QT, st, n, F.tin.p, F.tout.p, F.tw.p, F.P.p, F.A.p, skip);
-        dd_scan_exclusive(F.A.p, F.P.p, F.nh, F.tsum.p, st, skip);
+        QLAUNCH(k_zero_words, 1, 32, st, F.ex.p, 2, skip);
+        QLAUNCH(k_max_exp, q_grid(n), QT, st, r, n, F.ex.p, skip);
+        QLAUNCH(k_fs_scatter, q_grid(n), QT, st, n, F.tin.p, F.tout.p, r, F.ex.p, F.nbits, F.A.p, skip);
+        i128_scan_exclusive(F.A.p, F.P.p, F.nh, F.tsum.p, st, skip);
+        QLAUNCH(k_fs_flow, q_grid(n), QT, st, n, F.tin.p, F.tout.p, F.tw.p, F.P.p, F.ex.p, F.nbits, F.av.p, skip);
+        QLAUNCH(k_fs_scatter_a, q_grid(n), QT, st, n, F.tin.p, F.tout.p, F.av.p, F.ex.p, F.nbits, F.A.p, skip);
+        i128_scan_exclusive(F.A.p, F.P.p, F.nh, F.tsum.p, st, skip);
     }
-    QLAUNCH(k_fs_potential, q_grid(n), QT, st, n, F.tin.p, F.root.p, F.toff.p, F.A.p, F.P.p, z, skip);
+    QLAUNCH(k_fs_potential, q_grid(n), QT, st, n, F.tin.p, F.root.p, F.toff.p, F.A.p, F.P.p, F.ex.p, F.nbits, z,
+            skip);
 }
 
 // mean of v over every tree (at the root): the tour prefix at the tree's end
-// minus the prefix at its start covers every vertex but the root
+// minus the prefix at its start covers every vertex but the root (exact sums,
+// rounded once)
 __global__ void k_tree_mean(uint32_t n, const uint32_t* __restrict__ root, const uint32_t* __restrict__ toff,
                             const uint32_t* __restrict__ tlen, const uint32_t* __restrict__ tsz,
-                            const double2* __restrict__ P, const double* __restrict__ v, double* __restrict__ mean,
-                            const uint32_t* skip) {
+                            const i128* __restrict__ P, const double* __restrict__ v, const uint32_t* ex, int nbits,
+                            double* __restrict__ mean, const uint32_t* skip) {
     if (skip && *skip) return;
+    const int s = fixed_scale(ex[0], nbits);
     for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
         if (root[x] != x) continue;
         if (tlen[x] == 0) {
@@ -684,8 +778,7 @@ __global__ void k_tree_mean(uint32_t n, const uint32_t* __restrict__ root, const
             continue;
         }
         const uint32_t o = toff[x];
-        const double2 t = dd_add(dd_add(P[o + tlen[x]], dd_neg(P[o])), make_double2(v[x], 0.0));
-        mean[x] = dd_val(t) / (double)tsz[x];
+        mean[x] = from_fixed(P[o + tlen[x]] - P[o] + to_fixed(v[x], s), s) / (double)tsz[x];
     }
 }
 
@@ -701,11 +794,14 @@ __global__ void k_tree_sub(uint32_t n, const uint32_t* __restrict__ root, const 
 void forest_center(Forest& F, double* v, cudaStream_t st, const uint32_t* skip = nullptr) {
     const uint32_t n = F.n;
     if (!n) return;
+    QLAUNCH(k_zero_words, 1, 32, st, F.ex.p, 2, skip);
+    QLAUNCH(k_max_exp, q_grid(n), QT, st, v, n, F.ex.p, skip);
     if (F.nh) {
-        QLAUNCH(k_fs_scatter, q_grid(n), QT, st, n, F.tin.p, F.tout.p, v, F.A.p, skip);
-        dd_scan_exclusive(F.A.p, F.P.p, F.nh + 1, F.tsum.p, st, skip);
+        QLAUNCH(k_fs_scatter, q_grid(n), QT, st, n, F.tin.p, F.tout.p, v, F.ex.p, F.nbits, F.A.p, skip);
+        i128_scan_exclusive(F.A.p, F.P.p, F.nh + 1, F.tsum.p, st, skip);
     }
-    QLAUNCH(k_tree_mean, q_grid(n), QT, st, n, F.root.p, F.toff.p, F.tlen.p, F.tsz.p, F.P.p, v, F.mean.p, skip);
+    QLAUNCH(k_tree_mean, q_grid(n), QT, st, n, F.root.p, F.toff.p, F.tlen.p, F.tsz.p, F.P.p, v, F.ex.p, F.nbits,
+            F.mean.p, skip);
     QLAUNCH(k_tree_sub, q_grid(n), QT, st, n, F.root.p, F.mean.p, v, skip);
 }
 
@@ -787,8 +883,11 @@ void forest_build(Forest& F, const Lap& H, DevAlloc& a, cudaStream_t st, bool ke
             F.tw.ensure(a, (size_t)n + 1, st);
             F.A.ensure(a, (size_t)nh + 1, st);
             F.P.ensure(a, (size_t)nh + 1, st);
-            DG_CUDA(cudaMemsetAsync(F.A.p + nh, 0, sizeof(double2), st));  // A[nh] = 0: P[nh] is the total
-            F.tsum.ensure(a, ((size_t)nh + 1) / DD_TILE + 2, st);
+            DG_CUDA(cudaMemsetAsync(F.A.p + nh, 0, sizeof(i128), st));  // A[nh] = 0: P[nh] is the total
+            F.av.ensure(a, (size_t)n + 1, st);
+            F.ex.ensure(a, 4, st);
+            F.nbits = std::max(1, bit_length((uint64_t)nh + 1));
+            F.tsum.ensure(a, ((size_t)nh + 1) / IS_TILE + 2, st);
             err.ensure(a, 2, st);
             mn.ensure(a, (size_t)n + 1, st);
             size.ensure(a, (size_t)n + 1, st);
@@ -1175,7 +1274,7 @@ struct Solver {
             launched += c;
             read_scal(k);
             if (host_sc[k].done) break;
-            chunk = pre == Pre::Inner ? 1 : 4;
+            chunk = pre == Pre::Inner ? 1 : (k == 1 ? 4 : 32);
         }
         read_scal(k);
         const uint32_t it = host_sc[k].iters;

@@ -501,8 +501,14 @@ def run_quality(args):
     b -= b.mean()  # the mesh is connected
     db = torch.from_numpy(b).cuda()
     dx = torch.empty_like(db)
-    kopt = dict(max_iter=args.lanczos_iters, check_every=10, tol=1e-6, inner_tol=1e-10, inner_max_iter=2000)
-    popt = dict(tol=1e-8, max_iter=5000, precond="sparsifier", inner_tol=1e-10, inner_max_iter=2000)
+    kopt = dict(max_iter=args.lanczos_iters, check_every=10, tol=1e-6, inner_tol=1e-10,
+                inner_max_iter=args.inner_max_iters)
+    popt = dict(tol=1e-8, max_iter=5000, precond="sparsifier", inner_tol=1e-10, inner_max_iter=args.inner_max_iters)
+    if args.quality_parts == "kappa0":  # one kappa estimate alone (a short run to profile)
+        k = g.condition_number(**dict(kopt, check_every=1))
+        print(json.dumps({"workload": "quality", "part": "kappa0", "n": n, "lanczos": k}), flush=True)
+        ctx.close()
+        return
 
     def measure(gr):
         k = gr.condition_number(**kopt)
@@ -573,6 +579,9 @@ def main():
     ap.add_argument("--quality-mesh", default="100x100x100", help="quality: mesh dimensions")
     ap.add_argument("--lanczos-iters", type=int, default=400, help="quality: Lanczos steps at most")
     ap.add_argument("--cg-iters", type=int, default=200, help="quality: timed plain CG iterations")
+    ap.add_argument("--inner-max-iters", type=int, default=2000, help="quality: iterations of one L_H solve at most")
+    ap.add_argument("--quality-parts", default="all", choices=["all", "kappa0"],
+                    help="quality: the whole experiment, or one kappa estimate of G(0), H(0) (to profile)")
     ap.add_argument("--rmat-scale", type=int, default=22, help="rmat: log2 of the vertex count")
     ap.add_argument("--rmat-edges", type=int, default=64_000_000, help="rmat: distinct undirected edges")
     ap.add_argument("--requests", type=int, default=1000, help="serve: requests per load point")

@@ -442,6 +442,24 @@ typedef struct {
 dg_status dg_walk_estimate_noalloc(dg_ctx* ctx, int32_t graph_id, int64_t nq, const dg_walk_query* d_queries,
                                    dg_walk_estimate* d_out, void* cuda_stream);
 
+/*
+ * The updates applied one at a time, as Algorithm 1 states it: every update
+ * walks the G and H all earlier updates of the stream left, instead of the
+ * snapshot of its batch (Section III-F's deferral).  Results equal applying
+ * each update as a batch of one, in order.  The call cuts the stream into
+ * prefixes whose batched execution provably gives those results -- no walk of
+ * an update of the prefix stands on a vertex whose adjacency another update
+ * of the prefix changes (G: the endpoints of every valid update; H: the
+ * endpoints of kept insertions and deleted H edges, the vertices of a
+ * recovered path), no edge occurs twice, and a deletion whose walkers all
+ * missed ends its prefix -- found by a dry run of each window's walks on the
+ * current G and H, and runs each prefix as a batch.  ups / res: host arrays
+ * of nu records (res nullable).  *prefixes_out (nullable): the number of
+ * prefixes (batches) it took.  Errors as dg_apply_updates.
+ */
+dg_status dg_apply_updates_sequential(dg_ctx* ctx, int32_t graph_id, int64_t nu, const dg_update* ups,
+                                      dg_update_result* res, int64_t* prefixes_out);
+
 /* ------------------------------------------------------------------------
  * Quality of the sparsifier (Section IV: the off-tree density d_H, the
  * relative condition number kappa(L_G, L_H) of Eqs. 6-10, and PCG on

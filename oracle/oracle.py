@@ -226,6 +226,16 @@ class OracleGraph:
             out["paths"] = pbuf.reshape(nu, self.s, self.T + 1)
         return out
 
+    def apply_sequential(self, u, v, w, op, *, prune_bounds=False):
+        """The updates one at a time, as Algorithm 1 states it: each one a batch
+        of its own, so every update sees the G and H all earlier ones left.
+        Returns the per-update arrays of all of them."""
+        outs = [self.apply(u[i:i + 1], v[i:i + 1], w[i:i + 1], op[i:i + 1], prune_bounds=prune_bounds)
+                for i in range(len(u))]
+        if not outs:
+            return self.apply(u, v, w, op, prune_bounds=prune_bounds)
+        return {k: np.concatenate([o[k] for o in outs]) for k in outs[0]}
+
     def edges(self, which="H"):
         """(a, b, w) of H or G, a < b, lexicographic."""
         wh = 1 if which == "H" else 0

@@ -47,7 +47,8 @@ EXPORTS = ("dg_config_default", "dg_create", "dg_destroy", "dg_status_str", "dg_
            "dg_set_walk_shape", "dg_set_walk_refill", "dg_submit_updates", "dg_wait", "dg_walk_estimate_noalloc",
            "dg_debug_set_wait_limit", "dg_shard_begin", "dg_shard_export", "dg_shard_commit", "dg_wait_ex",
            "dg_prepare", "dg_init_sparsifier_grass", "dg_sparsifier_density", "dg_laplacian_apply",
-           "dg_pcg_solve", "dg_condition_number", "dg_debug_sparsifier_forest", "dg_debug_forest_solve")
+           "dg_pcg_solve", "dg_condition_number", "dg_debug_sparsifier_forest", "dg_debug_forest_solve",
+           "dg_apply_updates_sequential")
 
 LAP_G, LAP_H = 0, 1
 PRECOND = {"none": 0, "jacobi": 1, "sparsifier": 2}
@@ -161,6 +162,7 @@ def load_library(path: str | None = None):
         "dg_condition_number": (i32, [P, i32, C.POINTER(KappaOptions), C.POINTER(KappaInfo)]),
         "dg_debug_sparsifier_forest": (i32, [P, i32, i64, P, P, C.POINTER(i64)]),
         "dg_debug_forest_solve": (i32, [P, i32, P, P]),
+        "dg_apply_updates_sequential": (i32, [P, i32, i64, P, P, C.POINTER(i64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -445,6 +447,16 @@ class Graph:
     def prepare(self, max_batch: int):
         """Size the workspace and capture the batch steps for batches up to max_batch."""
         _check(self._L.dg_prepare(self.ctx._h, self.gid, int(max_batch)))
+
+    def apply_sequential(self, ups: np.ndarray):
+        """The updates one at a time (Algorithm 1's order; every update sees all
+        earlier ones).  Returns (results, number of batches it took)."""
+        ups = np.ascontiguousarray(ups, UPDATE_DTYPE)
+        res = np.zeros(ups.size, RESULT_DTYPE)
+        pre = C.c_int64()
+        _check(self._L.dg_apply_updates_sequential(self.ctx._h, self.gid, ups.size, _ptr(ups), _ptr(res),
+                                                   C.byref(pre)))
+        return res, pre.value
 
     # ---- quality of the sparsifier (Section IV) ------------------------------
     def density(self):

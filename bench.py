@@ -26,8 +26,11 @@ roofline : the walk kernel: algorithmic bytes = 20 B per useful walk step (the
            measured HBM copy bandwidth; ``gather`` restates it at the sector
            level (two 32-byte sectors per step).
 Also reported: walk-steps/s, the one-launch-per-update form at identical
-outputs, per-batch latency p50/p99, and the CPU oracle on a bounded sample of
-the same workload, single-threaded and on every host core.
+outputs, the sequential semantics (every update sees all earlier ones,
+Algorithm 1's order), per-batch latency p50/p99, and the CPU oracle on a
+bounded sample of the same workload, single-threaded and on every host core.
+``--workload quality`` runs Section IV's quality experiment (d_H, kappa and
+PCG iterations with and without updates).
 
 Under torchrun each rank runs an independent replica (its own seed); there is
 no collective on the data path; rank 0 prints the whole-job line.
@@ -568,6 +571,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--per-update-steps", type=int, default=2)
+    ap.add_argument("--seq-batches", type=int, default=1,
+                    help="stream batches run in the sequential (one update at a time) semantics")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work per CPU baseline")
     ap.add_argument("--ref-sample", type=int, default=500, help="reference arm: updates per step")
     ap.add_argument("--no-cpu", action="store_true")
@@ -729,6 +734,27 @@ def main():
            "p99_ms": 1e3 * float(np.percentile(e2e_t, 99)), "host_buffers": "pinned",
            "steps": e2e_steps, "batches": "one pass of the stream from G(0) on a fresh copy"}
 
+    # ---- sequential semantics (Algorithm 1's order, one update at a time) ----
+    # the stream's first batches on a fresh copy at G(0), through
+    # dg_apply_updates_sequential (host records); wall clock per batch
+    seq = None
+    if args.seq_batches > 0:
+        gs = fresh_copy()
+        s_t, s_pre, s_nu = [], 0, 0
+        for k in range(min(args.seq_batches, L)):
+            ups, _ = dev_batches[k]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, pre = gs.apply_sequential(ups)
+            s_t.append(time.perf_counter() - t0)
+            s_pre += pre
+            s_nu += len(ups)
+        gs.unload()
+        seq = {"updates_per_s": s_nu / sum(s_t), "batches": len(s_t), "updates": s_nu,
+               "prefixes": s_pre, "mean_prefix": s_nu / max(1, s_pre), "ms_per_batch": 1e3 * float(np.mean(s_t)),
+               "semantics": "every update sees all earlier ones (Algorithm 1); results equal one update per batch",
+               "timing": "host wall clock around dg_apply_updates_sequential, stream batches from G(0)"}
+
     # ---- context (mesh): the same walk kernel without deletion pruning -------
     full = None
     if args.workload == "mesh" and not args.no_full_walks:
@@ -837,6 +863,7 @@ def main():
                           "launches": launches / args.steps, "cuda_graph": bool(phases[-1]["graph_replayed"])},
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
             "per_update_form": pu,
+            "sequential": seq,
             "roofline": roof,
             "roofline_full_walks": full,
             "cpu_baseline": cpu,

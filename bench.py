@@ -58,12 +58,17 @@ os.environ.setdefault("DG_WORKLOAD_CACHE", "/tmp/dg_workload_cache")
 METRIC = "updates/s & walk-steps/s on 1 B300, batched vs per-update; p50/p99 latency"
 ALG_BYTES_PER_STEP = 20      # vertex record (8 B) + neighbour id (4 B) + its resistance (8 B)
 SECTOR_BYTES_PER_STEP = 64   # the same step at DRAM-sector granularity (two 32-byte sectors)
-# DRAM bytes (read + write) of one walk launch of the default workload, from one
-# ncu capture of the current walk kernel, or None while the kernel has changed
-# since its last capture.
-WALK_TRAFFIC_BYTES = 2_231_460_000
-WALK_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_walk_batched<1,1> launch, "
-                       "R-MAT scale 22 default batch: 2.11 GB read + 121.5 MB written")
+# DRAM bytes (read + write) of one walk launch per workload, from one ncu
+# capture of the current walk kernel (None while the kernel has changed since
+# its last capture)
+WALK_TRAFFIC = {
+    "rmat": (2_231_460_000, "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_walk_batched<1,1> launch, "
+                            "R-MAT scale 22 default batch: 2.11 GB read + 121.5 MB written"),
+    "mesh": (252_908_544, "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_walk_batched<1,0> launch, "
+                          "mesh 100^3, first timed batch: 226.9 MB read + 26.0 MB written"),
+    "fea": (574_097_664, "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_walk_batched<1,0> launch, "
+                         "FEA 2048^2, first timed batch: 511.8 MB read + 62.3 MB written"),
+}
 
 BATCH = {"rmat": (30_000, 20_000), "mesh": (10_000, 10_000), "fea": (50_000, 50_000)}
 # batches in one pass of each configuration's update stream (R-MAT: 20 batches of
@@ -814,8 +819,8 @@ def main():
     steps_per_launch = steps_done / args.steps
     achieved = ALG_BYTES_PER_STEP * steps_per_launch / avg_walk_s / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": WALK_TRAFFIC_BYTES if args.workload == "rmat" else None,
-            "traffic_source": WALK_TRAFFIC_SOURCE if args.workload == "rmat" else "not captured for this workload",
+            "traffic": WALK_TRAFFIC.get(args.workload, (None, ""))[0],
+            "traffic_source": WALK_TRAFFIC.get(args.workload, (None, "not captured for this workload"))[1],
             "kernel": "k_walk_batched", "bytes_per_step": ALG_BYTES_PER_STEP, "peak_source": peak_kind,
             "steps_per_launch": steps_per_launch,
             "algorithmic_bytes_per_launch": ALG_BYTES_PER_STEP * steps_per_launch,

@@ -6,8 +6,9 @@ Tolerances (floating point; the integer results -- forests, counts -- are
 compared exactly):
 * Laplacian products: a row sums deg + 1 products in another order than
   scipy, so |y - y_ref| <= 4 (deg + 1) eps * (d |x_i| + sum_j w_ij |x_j|).
-* Forest solve: z = L_F^+ r through two double-double prefix sums (about
-  2^-104 of the running sum each), against the correctly rounded potentials
+* Forest solve: z = L_F^+ r through two exact 128-bit fixed-point prefix
+  sums (each current and potential rounded once; entries 2^100 below the
+  largest are rounded when scaled), against the correctly rounded potentials
   of the correctly rounded currents: within 2 ulp, plus 1e-15 of the largest
   potential where a sum cancels to far below its terms.
 * PCG: the iteration count of conjugate gradients in floating point depends

@@ -635,6 +635,7 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     max_batch = max(len(b.u) for b in batches)
     shape = None
+    coop = (1, 0)
     if args.walk_shape:
         blk, ilp = (int(x) for x in args.walk_shape.split(","))
         shape = (blk, ilp, 0, 0)
@@ -646,6 +647,7 @@ def main():
         gg.init_sparsifier(wl.a[wl.h_ids], wl.b[wl.h_ids])
         if shape is not None:
             gg.set_walk_shape(shape[0], shape[1], shape[2], shape[3])
+            gg.set_walk_coop(*coop)
         gg.prepare(max_batch)
         torch.cuda.synchronize()
         return gg
@@ -667,6 +669,8 @@ def main():
     if shape is None:
         s0 = g.stats()
         shape = (s0["walk_block"], s0["walk_ilp"], s0["walk_blocks_per_sm"], s0["walk_refill"])
+        coop = (s0["walk_lanes"], s0["walk_tile"])
+    tune_log = g.tune_log()
     g.unload()
 
     # ---- timed: device-resident batches -------------------------------------
@@ -864,7 +868,9 @@ def main():
                                        ("mutate_ms", "walk_ms", "reduce_ms", "emit_ms", "commit_ms", "batch_ms")},
                           "walk_shape": {"block": phases[-1]["walk_block"], "ilp": phases[-1]["walk_ilp"],
                                          "blocks_per_sm": phases[-1]["walk_blocks_per_sm"],
-                                         "refill": phases[-1]["walk_refill"], "autotuned": not args.walk_shape},
+                                         "refill": phases[-1]["walk_refill"], "lanes": phases[-1]["walk_lanes"],
+                                         "tile": phases[-1]["walk_tile"], "autotuned": not args.walk_shape,
+                                         "autotuner_trials": [dict(d, ms=round(ms, 4)) for d, ms in tune_log]},
                           "launches": launches / args.steps, "cuda_graph": bool(phases[-1]["graph_replayed"])},
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
             "per_update_form": pu,

@@ -165,6 +165,8 @@ typedef struct {
     int32_t walk_cut;        /* persistent walk launches per batch */
     int32_t autotuned;       /* 1 if this batch ran the walk-shape autotuner */
     int32_t walk_refill;     /* empty walker slots a warp waits for before refilling */
+    int32_t walk_lanes;      /* lanes per walker (1: one walker per lane) */
+    int32_t walk_tile;       /* walked updates per block claim (0: the persistent walker queue) */
     int32_t reserved0;
 } dg_batch_stats;
 
@@ -295,6 +297,27 @@ dg_status dg_set_walk_shape(dg_ctx* ctx, int32_t graph_id, int32_t block, int32_
    several empty slots trades a few idle lanes for fewer stalls.  Outputs never
    depend on it; DG_E_INVALID outside 1..32. */
 dg_status dg_set_walk_refill(dg_ctx* ctx, int32_t graph_id, int32_t refill_min);
+
+/*
+ * The batching engine's other work shapes: lanes per walker (1, 2, 4, 8 or
+ * 32: the lanes of a group draw the Philox words of the next `lanes` steps
+ * side by side and take the walker's steps together) and the frontier tile
+ * (0: the persistent launch's walker queue; 1..16: a block claims that many
+ * walked updates at a time and stages their fields in shared memory; the
+ * walks are then followed by separate reduction and emission kernels).
+ * Outputs never depend on them.  Marks the graph tuned; DG_E_INVALID
+ * outside those values.
+ */
+dg_status dg_set_walk_coop(dg_ctx* ctx, int32_t graph_id, int32_t lanes, int32_t tile);
+
+/*
+ * The autotuner's trials on this graph (from its last run): per trial the
+ * shape {block, walkers per thread, refill, lanes, tile, cut} into shapes
+ * (6 int32 each) and its median walk time (ms) into ms; host arrays of cap
+ * trials; *count_out = the number of trials (cap too small: DG_E_INVALID).
+ */
+dg_status dg_get_tune_log(dg_ctx* ctx, int32_t graph_id, int64_t cap, int32_t* shapes, float* ms,
+                          int64_t* count_out);
 
 /*
  * Sharded batch over replicas (Section III-F: the walked updates of one batch

@@ -506,6 +506,36 @@ dg_status dg_set_walk_refill(dg_ctx* ctx, int32_t gid, int32_t refill_min) {
     });
 }
 
+dg_status dg_set_walk_coop(dg_ctx* ctx, int32_t gid, int32_t lanes, int32_t tile) {
+    return guarded(ctx, [&]() {
+        DGraph& g = C(ctx).graph(gid);
+        std::lock_guard<std::mutex> lk(g.mu);
+        if (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8 && lanes != 32)
+            throw Error(DG_E_INVALID, "lanes must be 1, 2, 4, 8 or 32");
+        if (tile < 0 || tile > 16) throw Error(DG_E_INVALID, "tile must be 0..16");
+        g.shape.lanes = lanes;
+        g.shape.tile = tile;
+        g.tuned = true;
+        ++g.layout_gen;
+    });
+}
+
+dg_status dg_get_tune_log(dg_ctx* ctx, int32_t gid, int64_t cap, int32_t* shapes, float* ms, int64_t* count_out) {
+    return guarded(ctx, [&]() {
+        DGraph& g = C(ctx).graph(gid);
+        std::lock_guard<std::mutex> lk(g.mu);
+        const int64_t n = (int64_t)g.tune_log.size();
+        if (count_out) *count_out = n;
+        if (n > cap || (n && (!shapes || !ms))) throw Error(DG_E_INVALID, "output arrays too small");
+        for (int64_t i = 0; i < n; ++i) {
+            const WalkShape& sh = g.tune_log[i].first;
+            const int32_t v[6] = {sh.block, sh.ilp, sh.refill, sh.lanes, sh.tile, sh.cut};
+            for (int q = 0; q < 6; ++q) shapes[6 * i + q] = v[q];
+            ms[i] = g.tune_log[i].second;
+        }
+    });
+}
+
 dg_status dg_shard_begin(dg_ctx* ctx, int32_t gid, int64_t nu, const dg_update* ups, int32_t rank, int32_t world,
                          void* stream, uint64_t* nrec_out) {
     return guarded(ctx, [&]() {

@@ -1108,16 +1108,22 @@ static bool enqueue_walks(Ctx& c, DGraph& g, cudaStream_t st, int64_t per_update
     const WalkRecs wr = recs_of(c, w);
     const WalkTasks tasks = tasks_of(w);
     const uint32_t cut = g.shape.cut > 1 ? (uint32_t)g.shape.cut : 1u;
-    const bool fused = per_update_W < 0 && cut == 1;
+    const bool tiled = g.shape.lanes > 1 || g.shape.tile > 0;
+    const bool fused = per_update_W < 0 && cut == 1 && !tiled;
     // (the candidate and fallback counts start at zero: cleared with the step's
     // scratch, and again after the autotuner's trial walks)
     DG_CUDA(record_event(g.ev[0], st));
     if (per_update_W < 0) {
-        for (uint32_t c2 = 0; c2 < cut; ++c2)
-            launch_walk_batched(g.H.view(), g.G.view(), tasks, wp, wr, w.hdr.p, w.next.p,
-                                (uint32_t)((uint64_t)w.b_max * c2 / cut),
-                                (uint32_t)((uint64_t)w.b_max * (c2 + 1) / cut), g.shape, fin_of(c, w, fused),
-                                w.err.p, st, g.side, g.fk[5], g.fk[6]);
+        for (uint32_t c2 = 0; c2 < cut; ++c2) {
+            const uint32_t lo = (uint32_t)((uint64_t)w.b_max * c2 / cut);
+            const uint32_t hi = (uint32_t)((uint64_t)w.b_max * (c2 + 1) / cut);
+            if (tiled)
+                launch_walk_tiled(g.H.view(), g.G.view(), tasks, wp, wr, w.hdr.p, w.next.p, lo, hi, g.shape,
+                                  w.err.p, st);
+            else
+                launch_walk_batched(g.H.view(), g.G.view(), tasks, wp, wr, w.hdr.p, w.next.p, lo, hi, g.shape,
+                                    fin_of(c, w, fused), w.err.p, st, g.side, g.fk[5], g.fk[6]);
+        }
     } else {
         for (int64_t j = 0; j < per_update_W; ++j)
             launch_walk_one(g.H.view(), g.G.view(), tasks, wp, wr, w.hdr.p, (uint32_t)j, w.err.p, st);
@@ -1151,11 +1157,15 @@ static void autotune_walks(Ctx& c, DGraph& g, cudaStream_t st) {
         DG_CUDA(cudaMemsetAsync(flush, 0, flush_bytes, st));
         DG_CUDA(cudaMemsetAsync(w.t_kstar.p, 0xFF, 4ull * w.b_max, st));
         DG_CUDA(cudaEventRecord(e0, st));
-        for (int cidx = 0; cidx < sh.cut; ++cidx)
-            launch_walk_batched(g.H.view(), g.G.view(), tasks, wp, wr, w.hdr.p, w.next.p,
-                                (uint32_t)((uint64_t)w.b_max * cidx / sh.cut),
-                                (uint32_t)((uint64_t)w.b_max * (cidx + 1) / sh.cut), sh, fin_of(c, w, false),
-                                w.err.p, st);
+        for (int cidx = 0; cidx < sh.cut; ++cidx) {
+            const uint32_t lo = (uint32_t)((uint64_t)w.b_max * cidx / sh.cut);
+            const uint32_t hi = (uint32_t)((uint64_t)w.b_max * (cidx + 1) / sh.cut);
+            if (sh.lanes > 1 || sh.tile > 0)
+                launch_walk_tiled(g.H.view(), g.G.view(), tasks, wp, wr, w.hdr.p, w.next.p, lo, hi, sh, w.err.p, st);
+            else
+                launch_walk_batched(g.H.view(), g.G.view(), tasks, wp, wr, w.hdr.p, w.next.p, lo, hi, sh,
+                                    fin_of(c, w, false), w.err.p, st);
+        }
         DG_CUDA(cudaEventRecord(e1, st));
         wait_stream(c, st);
         float ms = 0.f;
@@ -1165,9 +1175,12 @@ static void autotune_walks(Ctx& c, DGraph& g, cudaStream_t st) {
     // every trial starts from a flushed L2; a candidate's time is the median of
     // three runs, and it replaces the default shape (256 threads x 2 walkers)
     // only when it is at least 3 % faster
+    g.tune_log.clear();
     auto median3 = [&](const WalkShape& sh) {
         float a0 = trial(sh), a1 = trial(sh), a2 = trial(sh);
-        return std::max(std::min(a0, a1), std::min(std::max(a0, a1), a2));
+        const float m = std::max(std::min(a0, a1), std::min(std::max(a0, a1), a2));
+        g.tune_log.push_back({sh, m});
+        return m;
     };
     WalkShape best;
     best.block = 256;
@@ -1196,6 +1209,22 @@ static void autotune_walks(Ctx& c, DGraph& g, cudaStream_t st) {
         sh.refill = rf;
         const float ms = median3(sh);
         if (ms < best_ms * 0.97f) {
+            best_ms = ms;
+            best = sh;
+        }
+    }
+    // then the tiled launch: lanes per walker and updates per block claim
+    // (its walks are followed by separate reduction and emission kernels, so
+    // it must win by more than the in-kernel finalization it gives up)
+    const int coop[][2] = {{1, 1}, {1, 4}, {2, 1}, {4, 1}, {8, 1}, {32, 1}, {32, 4}};
+    for (const auto& lt : coop) {
+        WalkShape sh;
+        sh.block = 256;
+        sh.ilp = 1;
+        sh.lanes = lt[0];
+        sh.tile = lt[1];
+        const float ms = median3(sh);
+        if (ms < best_ms * 0.85f) {
             best_ms = ms;
             best = sh;
         }
@@ -1524,6 +1553,8 @@ void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_updat
     s.walk_blocks_per_sm = g.shape.blocks_per_sm;
     s.walk_cut = g.shape.cut;
     s.walk_refill = g.shape.refill;
+    s.walk_lanes = g.shape.lanes;
+    s.walk_tile = g.shape.tile;
     s.walk_launches = per_update ? (int64_t)g.hs.counts[0] : 1;
     const uint64_t dl = g_launches - l0;
     s.launches = (int64_t)dl;

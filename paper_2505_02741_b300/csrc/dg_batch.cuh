@@ -124,6 +124,7 @@ struct DGraph {
     HostStage hs;
     WalkShape shape;
     bool tuned = false;
+    std::vector<std::pair<WalkShape, float>> tune_log;  // the autotuner's trials: shape, median walk ms
     uint64_t layout_gen = 1;  // bumped whenever a buffer baked into a captured step moves
     std::map<uint32_t, CapturedStep> steps;  // by batch-size class
     // a sharded batch between its walks and its commit (graph_shard_*)

@@ -1175,6 +1175,145 @@ void launch_walk_batched(const CSRView& H, const CSRView& G, const WalkTasks& t,
     DG_CHECK_LAUNCH();
 }
 
+// ---------------------------------------------------------------------------
+// The batching engine's other work shapes, for the autotuner: a block claims
+// a tile of `tile` walked updates at a time and stages their task fields in
+// shared memory (the frontier tile), and LANES lanes walk one walker
+// together -- the group's lanes compute the Philox words of the next LANES
+// steps side by side, then every lane of the group takes the same steps (the
+// group's loads coincide).  The launch writes the walker records only; the
+// per-update reduction and the emission kernels follow it, as after a cut
+// launch.  Outputs are the same as with any other shape: every walker draws
+// the same words and makes the same picks.
+// ---------------------------------------------------------------------------
+constexpr uint32_t TILE_MAX = 16;
+
+template <int LANES>
+__global__ void __launch_bounds__(256) k_walk_tiled(WalkKernelArgs a, uint32_t tile) {
+    if (walk_aborted(a.d_err)) return;
+    const uint32_t W = min(*a.t.count, a.j_hi);
+    if (W <= a.j_lo) return;
+    __shared__ uint32_t s_u[TILE_MAX], s_v[TILE_MAX], s_idx[TILE_MAX];
+    __shared__ double s_wpq[TILE_MAX];
+    __shared__ uint8_t s_kind[TILE_MAX];
+    __shared__ uint32_t s_j0;
+    const uint64_t id0 = a.hdr->id0;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t gl = lane & (LANES - 1u);  // lane inside the group
+    const uint32_t gmask = LANES == 32 ? 0xffffffffu : (((1u << LANES) - 1u) << (lane & ~(LANES - 1u)));
+    const uint32_t group = threadIdx.x / LANES, ngroups = blockDim.x / LANES;
+    const uint32_t S = a.p.s;
+    for (;;) {
+        if (threadIdx.x == 0) s_j0 = a.j_lo + (uint32_t)atomicAdd(a.next, (unsigned long long)tile);
+        __syncthreads();
+        const uint32_t j0 = s_j0;
+        if (j0 >= W) break;
+        const uint32_t nt = min(tile, W - j0);
+        if (threadIdx.x < nt) {
+            const uint32_t j = j0 + threadIdx.x;
+            s_u[threadIdx.x] = a.t.u[j];
+            s_v[threadIdx.x] = a.t.v[j];
+            s_idx[threadIdx.x] = a.t.idx[j];
+            s_wpq[threadIdx.x] = a.t.wpq[j];
+            s_kind[threadIdx.x] = a.t.kind[j];
+        }
+        __syncthreads();
+        for (uint32_t wl = group; wl < nt * S; wl += ngroups) {
+            const uint32_t jj = wl / S, k = wl - jj * S, j = j0 + jj;
+            const size_t wid = (size_t)j * S + k;
+            const bool ins = s_kind[jj] == WALK_INS;
+            const CSRView& g = ins ? a.H : a.G;
+            const uint32_t u = s_u[jj], q = s_v[jj];
+            const double wpq = s_wpq[jj];
+            const uint64_t id = id0 + s_idx[jj];
+            uint32_t c = u, off = g.off[u], deg = g.deg[u], prev = NONE, steps = 0, reason = R_LEAF;
+            bool pid = false;
+            double R = 0.0;
+            if (a.r.paths && gl == 0) a.r.paths[wid * (a.p.T + 1)] = (int32_t)u;
+            uint32_t wbase = 0;
+            uint32_t word = philox_word0(gl, k, (uint32_t)id, (uint32_t)(id >> 32), a.p.key0, a.p.key1);
+            for (;;) {
+                const uint32_t neff = deg - (prev != NONE ? 1u : 0u);
+                if (neff == 0) {
+                    reason = R_LEAF;
+                    break;
+                }
+                if (ins && a.p.early_exit && __ldcg(&a.t.kstar[j]) <= steps) {
+                    reason = R_CUT;
+                    break;
+                }
+                if (steps - wbase >= LANES) {  // the group draws the words of the next LANES steps
+                    wbase = steps;
+                    word = philox_word0(wbase + gl, k, (uint32_t)id, (uint32_t)(id >> 32), a.p.key0, a.p.key1);
+                }
+                const uint32_t x = LANES == 1 ? word : __shfl_sync(gmask, word, (int)(steps - wbase), LANES);
+                uint4 h;
+                double2 tl;
+                if (nb_step(g, x, c, off, deg, prev, pid, h, tl) <= 0) {
+                    if (gl == 0) atomicOr(a.d_err, (uint32_t)ERR_INTERNAL);
+                    reason = R_LEAF;
+                    break;
+                }
+                R = __dadd_rn(R, tl.x);
+                steps += 1;
+                if (a.r.paths && gl == 0) a.r.paths[wid * (a.p.T + 1) + steps] = (int32_t)c;
+                if (!ins && a.p.del_prune && r_key(R) > __ldcg(&a.t.kstar[j])) {
+                    reason = R_CUT;
+                    break;
+                }
+                if (c == q && (!ins || __dmul_rn(wpq, R) <= a.p.K)) {
+                    if (gl == 0) {
+                        if (ins && a.p.early_exit) atomicMin(&a.t.kstar[j], steps);
+                        if (!ins && a.p.del_prune) atomicMin(&a.t.kstar[j], r_key(R));
+                    }
+                    reason = R_HIT;
+                    break;
+                }
+                if (ins && __dmul_rn(wpq, R) > a.p.K) {
+                    reason = R_OVER_K;
+                    break;
+                }
+                if (steps == a.p.T) {
+                    reason = R_AT_T;
+                    break;
+                }
+            }
+            if (gl == 0) {
+                a.r.meta[wid] = steps | (reason << 16);
+                a.r.R[wid] = R;
+            }
+        }
+        __syncthreads();  // the tile's staged fields are read until here
+    }
+}
+
+void launch_walk_tiled(const CSRView& H, const CSRView& G, const WalkTasks& t, const WalkParams& p,
+                       const WalkRecs& r, const BatchHdr* d_hdr, unsigned long long* d_next, uint32_t j_lo,
+                       uint32_t j_hi, const WalkShape& shape, const uint32_t* d_err, cudaStream_t st) {
+    WalkKernelArgs a = make_args(H, G, t, p, r, d_hdr, d_next, j_lo, j_hi, d_err);
+    const uint32_t tile = (uint32_t)std::min<int>(TILE_MAX, std::max(1, shape.tile));
+    const int block = shape.block;
+    DG_CUDA(cudaMemsetAsync(d_next, 0, sizeof(unsigned long long), st));
+    auto go = [&](auto kern) {
+        int bps = shape.blocks_per_sm;
+        if (bps <= 0) {
+            int occ = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, 0);
+            bps = occ > 0 ? occ : 1;
+        }
+        kern<<<device_sms() * bps, block, 0, st>>>(a, tile);
+    };
+    switch (shape.lanes) {
+        case 2: go(k_walk_tiled<2>); break;
+        case 4: go(k_walk_tiled<4>); break;
+        case 8: go(k_walk_tiled<8>); break;
+        case 32: go(k_walk_tiled<32>); break;
+        default: go(k_walk_tiled<1>); break;
+    }
+    ++g_launches;
+    DG_CHECK_LAUNCH();
+}
+
 void launch_walk_one(const CSRView& H, const CSRView& G, const WalkTasks& t, const WalkParams& p,
                      const WalkRecs& r, const BatchHdr* d_hdr, uint32_t j, const uint32_t* d_err,
                      cudaStream_t st) {

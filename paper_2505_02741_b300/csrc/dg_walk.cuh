@@ -50,7 +50,17 @@ struct WalkShape {
     int blocks_per_sm = 0;  // 0 = occupancy maximum
     int cut = 1;            // persistent launches the walked updates are split over
     int refill = 16;        // empty walker slots a warp with walkers left waits for before refilling
+    int lanes = 1;          // lanes per walker (1, 2, 4, 8, 32); above 1 the tiled launch runs
+    int tile = 0;           // walked updates a block claims at once, staged in shared memory (0: the
+                            // walker queue of the persistent launch; 1..16: the tiled launch)
 };
+
+// the tiled launch over walked updates [j_lo, j_hi): shape.tile updates per
+// block claim, shape.lanes lanes per walker; walker records only (the
+// reduction and emission kernels follow)
+void launch_walk_tiled(const CSRView& H, const CSRView& G, const WalkTasks& t, const WalkParams& p,
+                       const WalkRecs& r, const BatchHdr* d_hdr, unsigned long long* d_next, uint32_t j_lo,
+                       uint32_t j_hi, const WalkShape& shape, const uint32_t* d_err, cudaStream_t st);
 
 // one launch per walked update j (block of s threads), the paper's scheme
 void launch_walk_one(const CSRView& H, const CSRView& G, const WalkTasks& t, const WalkParams& p,

@@ -48,7 +48,7 @@ EXPORTS = ("dg_config_default", "dg_create", "dg_destroy", "dg_status_str", "dg_
            "dg_debug_set_wait_limit", "dg_shard_begin", "dg_shard_export", "dg_shard_commit", "dg_wait_ex",
            "dg_prepare", "dg_init_sparsifier_grass", "dg_sparsifier_density", "dg_laplacian_apply",
            "dg_pcg_solve", "dg_condition_number", "dg_debug_sparsifier_forest", "dg_debug_forest_solve",
-           "dg_apply_updates_sequential")
+           "dg_apply_updates_sequential", "dg_set_walk_coop", "dg_get_tune_log")
 
 LAP_G, LAP_H = 0, 1
 PRECOND = {"none": 0, "jacobi": 1, "sparsifier": 2}
@@ -74,7 +74,8 @@ class BatchStats(C.Structure):
                 ("walk_block", C.c_int32), ("walk_ilp", C.c_int32), ("walk_blocks_per_sm", C.c_int32),
                 ("graph_replayed", C.c_int32), ("mutate_ms", C.c_double), ("reduce_ms", C.c_double),
                 ("emit_ms", C.c_double), ("commit_ms", C.c_double), ("walk_cut", C.c_int32),
-                ("autotuned", C.c_int32), ("walk_refill", C.c_int32), ("reserved0", C.c_int32)]
+                ("autotuned", C.c_int32), ("walk_refill", C.c_int32), ("walk_lanes", C.c_int32),
+                ("walk_tile", C.c_int32), ("reserved0", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -163,6 +164,8 @@ def load_library(path: str | None = None):
         "dg_debug_sparsifier_forest": (i32, [P, i32, i64, P, P, C.POINTER(i64)]),
         "dg_debug_forest_solve": (i32, [P, i32, P, P]),
         "dg_apply_updates_sequential": (i32, [P, i32, i64, P, P, C.POINTER(i64)]),
+        "dg_set_walk_coop": (i32, [P, i32, i32, i32]),
+        "dg_get_tune_log": (i32, [P, i32, i64, P, P, C.POINTER(i64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -384,6 +387,20 @@ class Graph:
         _check(self._L.dg_set_walk_shape(self.ctx._h, self.gid, int(block), int(ilp), int(blocks_per_sm)))
         if refill:
             _check(self._L.dg_set_walk_refill(self.ctx._h, self.gid, int(refill)))
+
+    def set_walk_coop(self, lanes=1, tile=0):
+        """Lanes per walker and the frontier tile (updates per block claim; 0 = walker queue)."""
+        _check(self._L.dg_set_walk_coop(self.ctx._h, self.gid, int(lanes), int(tile)))
+
+    def tune_log(self):
+        """The autotuner's trials: list of (shape dict, median walk ms)."""
+        cnt = C.c_int64()
+        cap = 256
+        shapes = np.zeros(6 * cap, np.int32)
+        ms = np.zeros(cap, np.float32)
+        _check(self._L.dg_get_tune_log(self.ctx._h, self.gid, cap, _ptr(shapes), _ptr(ms), C.byref(cnt)))
+        keys = ("block", "ilp", "refill", "lanes", "tile", "cut")
+        return [(dict(zip(keys, shapes[6 * i:6 * i + 6].tolist())), float(ms[i])) for i in range(cnt.value)]
 
     def walk_estimate_noalloc(self, d_queries_ptr: int, nq: int, d_out_ptr: int, stream=None):
         """Walk estimates for nq device-resident queries; the call allocates no

@@ -300,7 +300,8 @@ def test_random_graphs_many_batches(seed):
 @pytest.mark.parametrize("del_prune", [False, True])
 def test_execution_forms_agree(del_prune):
     """Per-update launches, CUDA-graph replay, eager batched and every walk
-    launch shape give bit-identical outputs, with and without deletion
+    launch shape (threads per block, walkers per thread, lanes per walker,
+    frontier tile) give bit-identical outputs, with and without deletion
     pruning."""
     wl, st = W.make_grid(40, 40)
     batches = [st.next_batch(300, 200) for _ in range(3)]
@@ -320,6 +321,18 @@ def test_execution_forms_agree(del_prune):
         g.init_sparsifier(wl.a[wl.h_ids], wl.b[wl.h_ids])
         g.set_walk_shape(*shape)
         rs = [g.apply(D.make_updates(bt.u, bt.v, bt.w, bt.op)) for bt in batches]
+        outs.append((rs, g.sparsifier()))
+        ctx.close()
+    # lanes per walker and the frontier tile (the tiled launch)
+    for lanes, tile, block in [(1, 1, 256), (2, 4, 128), (4, 16, 256), (8, 1, 64), (32, 3, 256), (32, 1, 32)]:
+        ctx = D.Context(del_prune=del_prune)
+        g = ctx.load_graph(wl.n, wl.a, wl.b, wl.w)
+        g.init_sparsifier(wl.a[wl.h_ids], wl.b[wl.h_ids])
+        g.set_walk_shape(block, 1, 0)
+        g.set_walk_coop(lanes, tile)
+        rs = [g.apply(D.make_updates(bt.u, bt.v, bt.w, bt.op)) for bt in batches]
+        st_ = g.stats()
+        assert (st_["walk_lanes"], st_["walk_tile"]) == (lanes, tile)
         outs.append((rs, g.sparsifier()))
         ctx.close()
     ref_rs, ref_h = outs[0]
@@ -560,3 +573,40 @@ def test_mesh3d_full_size_batch():
         assert (res["status"] == 0).all()
     assert g.stats()["graph_replayed"] == 1
     ctx.close()
+
+
+def test_set_walk_coop_rejects_bad_values():
+    wl, _ = W.make_grid(8, 8)
+    ctx = D.Context()
+    g = ctx.load_graph(wl.n, wl.a, wl.b, wl.w)
+    for lanes, tile in [(3, 0), (0, 0), (64, 1), (1, -1), (1, 17)]:
+        with pytest.raises(D.DgError) as e:
+            g.set_walk_coop(lanes, tile)
+        assert e.value.code == -1
+    ctx.close()
+
+
+def test_autotuner_tries_every_work_shape():
+    """The first large batch runs the autotuner: its trial log covers the
+    threads-per-block / walkers-per-thread shapes, the refill thresholds and
+    the tiled launch's lanes per walker and tiles, and the batch's outputs
+    equal those of a fixed shape."""
+    wl, st = W.make_mesh3d(24, 24, 24, seed=3)
+    bt = st.next_batch(3000, 2000)
+    outs = []
+    for tune in (True, False):
+        ctx = D.Context()
+        g = ctx.load_graph(wl.n, wl.a, wl.b, wl.w)
+        g.init_sparsifier(wl.a[wl.h_ids], wl.b[wl.h_ids])
+        if not tune:
+            g.set_walk_shape(256, 1, 0)
+        outs.append(g.apply(D.make_updates(bt.u, bt.v, bt.w, bt.op)))
+        if tune:
+            assert g.stats()["autotuned"] == 1
+            log = g.tune_log()
+            shapes = {(d["lanes"], d["tile"]) for d, _ in log}
+            assert {(1, 0), (2, 1), (4, 1), (8, 1), (32, 1), (32, 4), (1, 4)} <= shapes
+            assert {d["refill"] for d, _ in log} >= {1, 8, 16, 24, 32}
+            assert all(ms > 0 for _, ms in log)
+        ctx.close()
+    assert_same_outputs(outs[0], outs[1])

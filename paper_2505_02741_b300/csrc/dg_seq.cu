@@ -154,8 +154,8 @@ __global__ void k_seq_walk(SeqArgs a) {
         double R = 0.0;
         bool hit = false;
         path[0] = u;
+        uint32_t off = g.off[u], deg = g.deg[u];
         for (;;) {
-            const uint32_t off = g.off[c], deg = g.deg[c];
             // skipped positions: the previous vertex and, at u, a deletion's own edge
             uint32_t e1 = prev_slot, e2 = c == u ? own : SEQ_NONE;
             if (e1 > e2) {
@@ -169,7 +169,7 @@ __global__ void k_seq_walk(SeqArgs a) {
             uint32_t idx = __umulhi(x, deg - skip);  // the idx-th allowed neighbour in list order
             if (idx >= e1) ++idx;
             if (idx >= e2) ++idx;
-            const Ent& e = g.pool[off + idx];
+            const Ent e = g.pool[off + idx];
             const uint32_t nx = e.nbr;
             R = __dadd_rn(R, e.r);
             ++steps;
@@ -181,7 +181,17 @@ __global__ void k_seq_walk(SeqArgs a) {
             }
             if (ins && __dmul_rn(up.w, R) > a.K) break;
             if (steps == a.T) break;
-            prev_slot = find_nbr(g, nx, c);
+            // the next list and our slot in it: cached in the entry, except for
+            // a hub (whose slot hint is checked, else searched)
+            if (e.noff != HUBREF && e.ndeg != 0) {
+                off = e.noff;
+                deg = e.ndeg;
+                prev_slot = e.rev;
+            } else {
+                off = g.off[nx];
+                deg = g.deg[nx];
+                prev_slot = (e.rev < deg && g.pool[off + e.rev].nbr == c) ? e.rev : find_nbr(g, nx, c);
+            }
             c = nx;
         }
         a.wsteps[wid] = steps;

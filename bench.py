@@ -863,6 +863,7 @@ def main():
                                  f"fresh copy ({-(-args.steps // L)} passes)"},
             "walk_steps_per_s": walk_steps_per_s,
             "per_batch": {"walk_steps": steps_done / args.steps,
+                          "d_H_first_pass": [p["h_edges"] / wl.n - 1.0 for p in phases[:L]],
                           "walked_updates": float(np.mean([p["walked"] for p in phases])),
                           "phase_ms": {k: float(np.mean([p[k] for p in phases])) for k in
                                        ("mutate_ms", "walk_ms", "reduce_ms", "emit_ms", "commit_ms", "batch_ms")},

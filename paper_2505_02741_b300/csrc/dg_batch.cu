@@ -1399,6 +1399,7 @@ static CapturedStep& capture_step(Ctx& c, DGraph& g, uint32_t bucket, bool direc
     DG_CUDA(cudaStreamEndCapture(st, &graph));
     DG_CUDA(cudaGraphInstantiate(&cs.exec, graph, 0));
     cudaGraphDestroy(graph);
+    DG_CUDA(cudaGraphUpload(cs.exec, st));  // its first replay then pays no upload
     cs.layout_gen = g.layout_gen;
     cs.device_io = direct;
     cs.kernels = g_launches - k0;

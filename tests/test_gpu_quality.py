@@ -267,3 +267,28 @@ def test_quality_follows_the_oracle_stream():
         assert g.density()[0] == Q.density(wl.n, o.edges("H")[0].size)
     o.close()
     ctx.close()
+
+
+def test_quality_degenerate_inputs():
+    """A zero right-hand side takes no iteration; a graph with no edges has
+    kappa 1 and density -1; a single-edge graph with H = G has kappa 1."""
+    ctx = D.Context()
+    g = ctx.load_graph(5, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    g.init_sparsifier(np.zeros(0, np.int32), np.zeros(0, np.int32))
+    assert g.density()[0] == -1.0
+    k = g.condition_number(max_iter=5)
+    assert k["kappa"] == 1.0
+    db = torch.zeros(5, dtype=torch.float64, device="cuda")
+    dx = torch.empty_like(db)
+    info, hist = g.pcg_solve(db.data_ptr(), dx.data_ptr(), precond="none")
+    assert info["iters"] == 0 and info["converged"] == 1
+    g2 = ctx.load_graph(2, np.array([0], np.int32), np.array([1], np.int32), np.array([2.0]))
+    g2.init_sparsifier(np.array([0], np.int32), np.array([1], np.int32))
+    assert g2.condition_number(max_iter=5)["kappa"] == pytest.approx(1.0)
+    b = _dev(np.array([1.0, -1.0]))
+    x = torch.empty_like(b)
+    info, _ = g2.pcg_solve(b.data_ptr(), x.data_ptr(), precond="sparsifier")
+    assert info["iters"] == 1
+    xs = x.cpu().numpy()
+    assert (xs[0] - xs[1]) == pytest.approx(0.5)  # unit current through resistance 1/2
+    ctx.close()

@@ -130,3 +130,17 @@ def test_sequential_without_cuts_or_pruning(kw):
     assert_edges_equal(g.sparsifier(), o.edges("H"), "H")
     o.close()
     ctx.close()
+
+
+def test_sequential_empty_and_single_update():
+    wl, st = W.make_grid(10, 10, seed=28)
+    ctx, g, o = _pair(wl)
+    res, pre = g.apply_sequential(D.make_updates([], [], [], []))
+    assert len(res) == 0 and pre == 0
+    bt = st.next_batch(1, 0)
+    res, pre = g.apply_sequential(D.make_updates(bt.u, bt.v, bt.w, bt.op))
+    ref = o.apply_sequential(bt.u, bt.v, bt.w, bt.op, prune_bounds=True)
+    assert pre == 1
+    assert_results_equal(res, ref, "single")
+    o.close()
+    ctx.close()

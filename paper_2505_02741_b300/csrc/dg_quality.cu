@@ -1242,8 +1242,8 @@ struct Solver {
         const uint32_t* done = &s->done;
         QLAUNCH(k_cg_start, np, QT, st, b, x, v.r.p, v.p.p, n, part.p);
         QLAUNCH(k_cg_start_fin, 1, QT, st, s, part.p, np, tol, max_iter, hist_dev);
-        // z0 = M^-1 r0, rz, p = z0
-        auto zstep = [&](bool check_host) {
+        // z = M^-1 r, (r, z), p = z + beta p; false when the outer solve already stopped
+        auto zstep = [&]() {
             if (pre == Pre::Inner) {
                 read_scal(k);
                 if (host_sc[k].done) return false;
@@ -1252,7 +1252,6 @@ struct Solver {
             QLAUNCH(k_dot_part, np, QT, st, v.r.p, v.z.p, n, part.p, done);
             QLAUNCH(k_cg_beta, 1, QT, st, s, part.p, np);
             QLAUNCH(k_cg_p, q_grid(n), QT, st, v.z.p, v.p.p, n, s);
-            (void)check_host;
             return true;
         };
         auto qstep = [&]() {
@@ -1262,14 +1261,14 @@ struct Solver {
             QLAUNCH(k_cg_xr, np, QT, st, x, v.r.p, v.p.p, v.q.p, n, s, part.p);
             QLAUNCH(k_cg_check, 1, QT, st, s, part.p, np, hist_dev);
         };
-        zstep(false);
+        zstep();
         uint32_t launched = 0;
         uint32_t chunk = pre == Pre::Inner ? 1 : std::max<uint32_t>(1, k == 1 ? hint : 8);
         while (launched < max_iter) {
             const uint32_t c = std::min(chunk, max_iter - launched);
             for (uint32_t i = 0; i < c; ++i) {
                 qstep();
-                if (!zstep(true)) break;
+                if (!zstep()) break;
             }
             launched += c;
             read_scal(k);

@@ -610,3 +610,26 @@ def test_autotuner_tries_every_work_shape():
             assert all(ms > 0 for _, ms in log)
         ctx.close()
     assert_same_outputs(outs[0], outs[1])
+
+
+def test_work_shapes_agree_on_a_power_law_graph():
+    """Hubs (HUBREF entries, slot hints) under every work shape: the tiled
+    launch's lanes per walker and tiles give the outputs of the persistent
+    launch, byte for byte, and both match the oracle."""
+    wl, st = W.make_rmat(14, 150_000, seed=9)
+    batches = [st.next_batch(1500, 1000) for _ in range(2)]
+    outs = []
+    for lanes, tile, block in [(1, 0, 256), (1, 4, 256), (4, 1, 128), (32, 2, 256)]:
+        ctx, g, o = pair(wl.n, wl.a, wl.b, wl.w, wl.h_ids)
+        g.set_walk_shape(block, 1, 0)
+        g.set_walk_coop(lanes, tile)
+        rs = []
+        for bt in batches:
+            res, _ = step_both(g, o, bt.u, bt.v, bt.w, bt.op, where=f"lanes {lanes} tile {tile}")
+            rs.append(res)
+        outs.append(rs)
+        o.close()
+        ctx.close()
+    for rs in outs[1:]:
+        for r0, r1 in zip(outs[0], rs):
+            assert_same_outputs(r0, r1)

@@ -478,7 +478,9 @@ dg_status dg_walk_estimate_noalloc(dg_ctx* ctx, int32_t graph_id, int64_t nq, co
  * missed ends its prefix -- found by a dry run of each window's walks on the
  * current G and H, and runs each prefix as a batch.  ups / res: host arrays
  * of nu records (res nullable).  *prefixes_out (nullable): the number of
- * prefixes (batches) it took.  Errors as dg_apply_updates.
+ * prefixes (batches) it took.  Errors as dg_apply_updates; the prefixes run
+ * before an error stay applied (their results are in res, *prefixes_out
+ * counts them, and dg_get_next_update_id tells how far the stream got).
  */
 dg_status dg_apply_updates_sequential(dg_ctx* ctx, int32_t graph_id, int64_t nu, const dg_update* ups,
                                       dg_update_result* res, int64_t* prefixes_out);

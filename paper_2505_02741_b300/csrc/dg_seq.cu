@@ -355,13 +355,14 @@ void graph_apply_sequential(Ctx& c, DGraph& g, int64_t nu64, const dg_update* up
     const uint32_t n = (uint32_t)g.n;
     const uint32_t S = (uint32_t)c.cfg.s, T = (uint32_t)c.cfg.T;
     SeqWS w;
+    uint32_t a0 = 0;  // updates applied so far
+    int64_t prefixes = 0;
     try {
         w.ensure(al, n, SEQ_MAX_WINDOW, S, T, st);
         w.ups.ensure(al, nu, st);
         w.res.ensure(al, nu, st);
         DG_CUDA(cudaMemcpyAsync(w.ups.p, ups_h, sizeof(dg_update) * nu, cudaMemcpyHostToDevice, st));
-        uint32_t a0 = 0, win = 256;
-        int64_t prefixes = 0;
+        uint32_t win = 256;
         while (a0 < nu) {
             const uint32_t m = std::min(win, nu - a0);
             graph_wait_estimates(g, st);
@@ -421,7 +422,12 @@ void graph_apply_sequential(Ctx& c, DGraph& g, int64_t nu64, const dg_update* up
         DG_CUDA(cudaStreamSynchronize(st));
         if (prefixes_out) *prefixes_out = prefixes;
     } catch (...) {
+        // the prefixes already run stay applied: hand back their results
         cudaStreamSynchronize(st);
+        if (res_h && a0 && w.res.p &&
+            cudaMemcpy(res_h, w.res.p, sizeof(dg_update_result) * a0, cudaMemcpyDeviceToHost) != cudaSuccess)
+            cudaGetLastError();
+        if (prefixes_out) *prefixes_out = prefixes;
         w.release(al, st);
         throw;
     }

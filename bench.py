@@ -25,6 +25,9 @@ roofline : the walk kernel: algorithmic bytes = 20 B per useful walk step (the
            vertex record, the neighbour id and its resistance), against the
            measured HBM copy bandwidth; ``gather`` restates it at the sector
            level (two 32-byte sectors per step).
+roofline_merge : the merge of G's touched lists (the largest kernel of the
+           R-MAT step): 32 B per entry read from an old list or written to a
+           new one, over the merge's CUDA-event time inside the step.
 Also reported: walk-steps/s, the one-launch-per-update form at identical
 outputs, the sequential semantics (every update sees all earlier ones,
 Algorithm 1's order), per-batch latency p50/p99, and the CPU oracle on a
@@ -68,6 +71,13 @@ WALK_TRAFFIC = {
                           "mesh 100^3, first timed batch: 226.9 MB read + 26.0 MB written"),
     "fea": (574_097_664, "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_walk_batched<1,0> launch, "
                          "FEA 2048^2, first timed batch: 511.8 MB read + 62.3 MB written"),
+}
+
+# the list merge of G's mutation: one 32-byte entry read (old list) or written (new list)
+MERGE_BYTES_PER_ENTRY = 32
+MERGE_TRAFFIC = {
+    "rmat": (2_910_000_000, "ncu dram__bytes_read.sum + dram__bytes_write.sum of G's k_exec_merge launch, "
+                            "R-MAT scale 22 default batch: 1.51 GB read + 1.40 GB written"),
 }
 
 BATCH = {"rmat": (30_000, 20_000), "mesh": (10_000, 10_000), "fea": (50_000, 50_000)}
@@ -832,6 +842,23 @@ def main():
                        "peak_steps_per_s": peak * 1e9 / SECTOR_BYTES_PER_STEP,
                        "frac": steps_per_launch / avg_walk_s / (peak * 1e9 / SECTOR_BYTES_PER_STEP)}}
 
+    # ---- roofline of the list merge (G's touched lists) ----------------------
+    # every entry of a touched list is read once from the old list and written
+    # once to the new one: 32 B each way; CUDA events around the merge kernel
+    # inside the captured step (G's merge runs beside H's on the second stream)
+    merge = None
+    m_ms = [p["merge_ms"] for p in phases]
+    if all(x > 0 for x in m_ms):
+        m_entries = float(np.mean([p["merge_entries"] for p in phases]))
+        m_s = sum(m_ms) / 1e3 / len(m_ms)
+        m_ach = MERGE_BYTES_PER_ENTRY * m_entries / m_s / 1e9
+        merge = {"bound": "hbm", "achieved": m_ach, "peak": peak, "unit": "GB/s", "frac": m_ach / peak,
+                 "traffic": MERGE_TRAFFIC.get(args.workload, (None, ""))[0],
+                 "traffic_source": MERGE_TRAFFIC.get(args.workload, (None, "not captured for this workload"))[1],
+                 "kernel": "k_exec_merge (G's touched lists)", "bytes_per_entry": MERGE_BYTES_PER_ENTRY,
+                 "entries_per_launch": m_entries, "ms_per_launch": 1e3 * m_s, "peak_source": peak_kind,
+                 "algorithmic_bytes_per_launch": MERGE_BYTES_PER_ENTRY * m_entries}
+
     serving = None
     if rank == 0 and args.serve_requests > 0:
         r = serve_experiment((0.6,), args.serve_requests)
@@ -877,6 +904,7 @@ def main():
             "per_update_form": pu,
             "sequential": seq,
             "roofline": roof,
+            "roofline_merge": merge,
             "roofline_full_walks": full,
             "cpu_baseline": cpu,
             "serving": serving,

@@ -168,6 +168,8 @@ typedef struct {
     int32_t walk_lanes;      /* lanes per walker (1: one walker per lane) */
     int32_t walk_tile;       /* walked updates per block claim (0: the persistent walker queue) */
     int32_t reserved0;
+    double merge_ms;         /* device time of the merge of G's touched lists (-1 when not timed) */
+    int64_t merge_entries;   /* 32-byte entries that merge read (old lists) and wrote (new lists) */
 } dg_batch_stats;
 
 /* default configuration: seed 0, K 100, T 100, s 32, early exit on, batched walks,

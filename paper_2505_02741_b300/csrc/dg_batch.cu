@@ -22,14 +22,7 @@ constexpr int BT = 256;  // threads per block of the small batch kernels
 
 __device__ __forceinline__ bool batch_aborted(const uint32_t* d_err) { return (*d_err & ABORT_MASK) != 0u; }
 
-// timing event: an external event node while the stream is being captured
-static cudaError_t record_event(cudaEvent_t ev, cudaStream_t st) {
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    cudaError_t e = cudaStreamIsCapturing(st, &cs);
-    if (e != cudaSuccess) return e;
-    if (cs == cudaStreamCaptureStatusActive) return cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
-    return cudaEventRecord(ev, st);
-}
+static cudaError_t record_event(cudaEvent_t ev, cudaStream_t st) { return record_timing_event(ev, st); }
 
 static int grid_for(uint64_t items) {
     uint64_t g = (items + BT - 1) / BT;
@@ -524,7 +517,7 @@ static void ensure_ws(Ctx& c, DGraph& g, uint32_t b_max, cudaStream_t st) {
         DG_CUDA(cudaMallocHost(&g.hs.err, sizeof(uint32_t) * 4));
         DG_CUDA(cudaMallocHost(&g.hs.ctr, sizeof(BatchCounters)));
         DG_CUDA(cudaMallocHost(&g.hs.tops, sizeof(unsigned long long) * 2));
-        DG_CUDA(cudaMallocHost(&g.hs.counts, sizeof(uint32_t) * 4));
+        DG_CUDA(cudaMallocHost(&g.hs.counts, sizeof(uint32_t) * 8));
         DG_CUDA(cudaHostGetDevicePointer((void**)&g.hs.d_err, g.hs.err, 0));
         DG_CUDA(cudaHostGetDevicePointer((void**)&g.hs.d_ctr, g.hs.ctr, 0));
         DG_CUDA(cudaHostGetDevicePointer((void**)&g.hs.d_tops, g.hs.tops, 0));
@@ -646,7 +639,7 @@ void graph_load(Ctx& c, DGraph& g, int32_t n, int64_t m, const int32_t* u, const
     csr_build(g.H, a, nullptr, nullptr, nullptr, 0, nullptr, st);
     g.has_h = true;  // empty sparsifier
     g.next_id = 0;
-    for (int i = 0; i < 7; ++i) DG_CUDA(cudaEventCreate(&g.ev[i]));
+    for (int i = 0; i < 9; ++i) DG_CUDA(cudaEventCreate(&g.ev[i]));
     for (int i = 0; i < 7; ++i) DG_CUDA(cudaEventCreateWithFlags(&g.fk[i], cudaEventDisableTiming));
     DG_CUDA(cudaEventCreateWithFlags(&g.ev_mut, cudaEventDisableTiming));
     DG_CUDA(cudaEventCreateWithFlags(&g.ev_est, cudaEventDisableTiming));
@@ -806,7 +799,7 @@ void graph_release(Ctx& c, DGraph& g) {
     if (g.hs.tops) cudaFreeHost(g.hs.tops);
     if (g.hs.counts) cudaFreeHost(g.hs.counts);
     g.hs = HostStage{};
-    for (int i = 0; i < 7; ++i)
+    for (int i = 0; i < 9; ++i)
         if (g.ev[i]) cudaEventDestroy(g.ev[i]);
     for (int i = 0; i < 7; ++i)
         if (g.fk[i]) cudaEventDestroy(g.fk[i]);
@@ -1090,7 +1083,7 @@ static void enqueue_mutate(Ctx& c, DGraph& g, cudaStream_t st) {
     DG_CUDA(cudaEventRecord(g.fk[3], st));
     DG_CUDA(cudaStreamWaitEvent(st, g.fk[2], 0));
     DG_CUDA(cudaStreamWaitEvent(sd, g.fk[3], 0));
-    csr_exec(g.G, clG, w.apG, g.touched.p, w.err.p, st);
+    csr_exec(g.G, clG, w.apG, g.touched.p, w.err.p, st, g.ev[7], g.ev[8]);
     csr_exec(g.H, clH, w.apH, g.touched_h.p, w.err.p, sd);
     DG_CUDA(cudaEventRecord(g.fk[4], sd));
     DG_CUDA(cudaStreamWaitEvent(st, g.fk[4], 0));
@@ -1292,7 +1285,8 @@ static void enqueue_commit(Ctx& c, DGraph& g, cudaStream_t st, bool walk_emitted
 // memory: one node at the end of the captured step instead of six copies
 __global__ void k_readback(const uint32_t* err, const BatchCounters* ctr, const unsigned long long* gtop,
                            const unsigned long long* htop, const uint32_t* t_count, const uint32_t* ccount,
-                           uint32_t* h_err, BatchCounters* h_ctr, unsigned long long* h_tops, uint32_t* h_counts) {
+                           const uint32_t* gtot, const uint32_t* gcount, uint32_t* h_err, BatchCounters* h_ctr,
+                           unsigned long long* h_tops, uint32_t* h_counts) {
     constexpr unsigned CW = sizeof(BatchCounters) / sizeof(unsigned long long);
     static_assert(CW * sizeof(unsigned long long) == sizeof(BatchCounters) && CW <= 8, "counter words");
     const unsigned t = threadIdx.x;
@@ -1303,12 +1297,18 @@ __global__ void k_readback(const uint32_t* err, const BatchCounters* ctr, const 
     if (t == 17) h_tops[1] = *htop;
     if (t == 18) h_counts[0] = *t_count;
     if (t == 19) h_counts[1] = *ccount;
+    // G's list execution: its work items (old entries + changes), net insertions
+    // and deletions, and its change count (the size of the merge)
+    if (t == 20) h_counts[2] = gtot[TOT_WK];
+    if (t == 21) h_counts[3] = gtot[TOT_NI];
+    if (t == 22) h_counts[4] = gtot[TOT_ND];
+    if (t == 23) h_counts[5] = *gcount;
 }
 
 static void enqueue_readback(DGraph& g, cudaStream_t st) {
     BatchWS& w = g.ws;
-    k_readback<<<1, 32, 0, st>>>(w.err.p, w.ctr.p, g.G.top.p, g.H.top.p, w.t_count.p, w.ccount.p, g.hs.d_err,
-                                 g.hs.d_ctr, g.hs.d_tops, g.hs.d_counts);
+    k_readback<<<1, 32, 0, st>>>(w.err.p, w.ctr.p, g.G.top.p, g.H.top.p, w.t_count.p, w.ccount.p,
+                                 w.apG.totals.p, w.gcount.p, g.hs.d_err, g.hs.d_ctr, g.hs.d_tops, g.hs.d_counts);
     ++g_launches;
     DG_CHECK_LAUNCH();
 }
@@ -1546,6 +1546,13 @@ void graph_apply(Ctx& c, DGraph& g, int64_t nu64, const dg_update* ups, dg_updat
     s.reduce_ms = (cudaEventElapsedTime(&ms, g.ev[1], g.ev[5]) == cudaSuccess) ? ms : -1.0;
     s.emit_ms = (cudaEventElapsedTime(&ms, g.ev[5], g.ev[6]) == cudaSuccess) ? ms : -1.0;
     s.commit_ms = (cudaEventElapsedTime(&ms, g.ev[6], g.ev[3]) == cudaSuccess) ? ms : -1.0;
+    s.merge_ms = (cudaEventElapsedTime(&ms, g.ev[7], g.ev[8]) == cudaSuccess) ? ms : -1.0;
+    {
+        // old entries read + new entries written: sum(od) = items - changes,
+        // sum(nd) = sum(od) + insertions - deletions
+        const uint64_t wk = g.hs.counts[2], ni = g.hs.counts[3], nd = g.hs.counts[4], cnt = g.hs.counts[5];
+        s.merge_entries = (wk >= cnt && 2 * (wk - cnt) + ni >= nd) ? (int64_t)(2 * (wk - cnt) + ni - nd) : 0;
+    }
     cudaGetLastError();
     s.retries = retries;
     s.graph_replayed = replayed ? 1 : 0;
@@ -1747,6 +1754,8 @@ void graph_shard_commit(Ctx& c, DGraph& g, const ShardRec* recs, uint64_t nrec, 
     s.reduce_ms = (cudaEventElapsedTime(&ms, g.ev[1], g.ev[5]) == cudaSuccess) ? ms : -1.0;
     s.emit_ms = -1.0;
     s.commit_ms = -1.0;
+    s.merge_ms = -1.0;
+    s.merge_entries = 0;
     cudaGetLastError();
     s.graph_replayed = 0;
     s.launches += (int64_t)(g_launches - l0);

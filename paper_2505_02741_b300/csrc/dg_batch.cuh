@@ -96,7 +96,7 @@ struct HostStage {  // pinned staging for host-API batches
     uint32_t* err = nullptr;
     BatchCounters* ctr = nullptr;
     unsigned long long* tops = nullptr;  // [G top, H top]
-    uint32_t* counts = nullptr;          // [W, ccount]
+    uint32_t* counts = nullptr;          // [W, ccount, G's merge: work items, insertions, deletions, changes]
     // device addresses of err, ctr, tops, counts (pinned, written by k_readback)
     uint32_t* d_err = nullptr;
     BatchCounters* d_ctr = nullptr;
@@ -134,8 +134,9 @@ struct DGraph {
         cudaStream_t st = nullptr;
     } shard;
     cudaStream_t stream = nullptr;           // private stream (serving)
-    // timing events: 0/1 walk, 2/3 batch, 4 end of mutation, 5 end of reduction, 6 end of emission
-    cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    // timing events: 0/1 walk, 2/3 batch, 4 end of mutation, 5 end of reduction, 6 end of emission,
+    // 7/8 the merge of G's touched lists
+    cudaEvent_t ev[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     // second stream of the mutation (H side, walk tasks) and its fork/join events
     cudaStream_t side = nullptr;
     cudaEvent_t fk[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // fork / join of the two streams

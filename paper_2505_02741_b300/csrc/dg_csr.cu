@@ -684,7 +684,7 @@ __global__ void k_exec_fix(ExecArgs a, uint32_t* d_err) {
 }
 
 void csr_exec(CSR& g, const ChangeList& cl, ApplyScratch& s, uint32_t* touched, uint32_t* d_err,
-              cudaStream_t st) {
+              cudaStream_t st, cudaEvent_t merge_t0, cudaEvent_t merge_t1) {
     const int grid = flat_grid();
     ExecArgs a;
     a.cl = cl;
@@ -704,7 +704,9 @@ void csr_exec(CSR& g, const ChangeList& cl, ApplyScratch& s, uint32_t* touched, 
     // space; lists without a twin into the staging buffer); meta then points
     // every touched vertex at its final slots; place copies staged lists back;
     // fix refreshes caches.
+    if (merge_t0) DG_CUDA(record_timing_event(merge_t0, st));
     k_exec_merge<<<grid, FLAT_THREADS, 0, st>>>(a, d_err);
+    if (merge_t1) DG_CUDA(record_timing_event(merge_t1, st));
     k_exec_meta<<<grid, FLAT_THREADS, 0, st>>>(a, d_err);
     k_exec_place<<<grid, FLAT_THREADS, 0, st>>>(a, d_err);
     k_exec_fix<<<grid, FLAT_THREADS, 0, st>>>(a, d_err);

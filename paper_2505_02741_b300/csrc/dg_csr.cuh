@@ -97,9 +97,10 @@ void csr_plan(CSR& g, const ChangeList& cl, ApplyScratch& s, uint32_t* d_err, ui
 // execute: merge, place, refresh cached fields (no-op when *d_err has an abort bit)
 // touched: n + 1 words; entry x = (generation << 2) | bits for the vertices an
 // execution changed, word n = the array's generation (bumped per execution),
-// so marks of earlier executions never match and nothing needs clearing
+// so marks of earlier executions never match and nothing needs clearing.
+// merge_t0 / merge_t1 (nullable): timing events recorded around the merge kernel
 void csr_exec(CSR& g, const ChangeList& cl, ApplyScratch& s, uint32_t* touched, uint32_t* d_err,
-              cudaStream_t st);
+              cudaStream_t st, cudaEvent_t merge_t0 = nullptr, cudaEvent_t merge_t1 = nullptr);
 
 // rebuild every list with fresh slack into a new pool with at least min_free spare entries
 void csr_compact(CSR& g, DevAlloc& a, uint64_t min_free, cudaStream_t st);

@@ -27,6 +27,15 @@ struct Error : std::runtime_error {
 
 #define DG_CHECK_LAUNCH() DG_CUDA(cudaGetLastError())
 
+// timing event: an external event node while the stream is being captured
+inline cudaError_t record_timing_event(cudaEvent_t ev, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return e;
+    if (cs == cudaStreamCaptureStatusActive) return cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+    return cudaEventRecord(ev, st);
+}
+
 // Device memory through the caller's allocator (or cudaMallocAsync/cudaFreeAsync).
 struct DevAlloc {
     void* (*fn_alloc)(size_t, void*, void*) = nullptr;

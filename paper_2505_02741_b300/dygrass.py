@@ -75,7 +75,8 @@ class BatchStats(C.Structure):
                 ("graph_replayed", C.c_int32), ("mutate_ms", C.c_double), ("reduce_ms", C.c_double),
                 ("emit_ms", C.c_double), ("commit_ms", C.c_double), ("walk_cut", C.c_int32),
                 ("autotuned", C.c_int32), ("walk_refill", C.c_int32), ("walk_lanes", C.c_int32),
-                ("walk_tile", C.c_int32), ("reserved0", C.c_int32)]
+                ("walk_tile", C.c_int32), ("reserved0", C.c_int32), ("merge_ms", C.c_double),
+                ("merge_entries", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -633,3 +633,41 @@ def test_work_shapes_agree_on_a_power_law_graph():
     for rs in outs[1:]:
         for r0, r1 in zip(outs[0], rs):
             assert_same_outputs(r0, r1)
+
+
+def test_merge_size_is_the_touched_lists():
+    """The batch statistics report the size of G's list merge: every entry of
+    a touched list read once (old list) and written once (new list).  The
+    count equals the degrees of the vertices whose lists change, from the
+    exported G before and after each batch, and the merge is timed."""
+    rng = np.random.default_rng(11)
+    n, a, b = W.rmat(11, 12000, rng)
+    w = rng.uniform(0.5, 5.0, len(a))
+    h = W.init_sparsifier(n, a, b, w, rng)
+    ctx, g, o = pair(n, a, b, w, h, T=40, s=16, K=60.0)
+    wl = W.Workload("rmat_s11", n, a, b, w, h, K=60.0, T=40, s=16, seed=0)
+    stream = W.UpdateStream(wl, rng, ("uniform",), lambda r, u, v: r.uniform(0.5, 5.0, len(u)))
+
+    def snapshot():
+        ga, gb, _ = g.edges()
+        deg = np.bincount(np.concatenate([ga, gb]), minlength=n)
+        keys = set(zip(np.minimum(ga, gb).tolist(), np.maximum(ga, gb).tolist()))
+        return deg, keys
+
+    for bi in range(3):
+        bt = stream.next_batch(300, 400)
+        deg0, e0 = snapshot()
+        res = g.apply(D.make_updates(bt.u, bt.v, bt.w, bt.op))
+        deg1, e1 = snapshot()
+        st_ = g.stats()
+        touched = set()
+        for i in np.flatnonzero(res["status"] == 0):
+            p = (int(min(bt.u[i], bt.v[i])), int(max(bt.u[i], bt.v[i])))
+            if p in e0 or p in e1:  # absent before and after: no change record
+                touched.update(p)
+        t = np.fromiter(touched, np.int64)
+        expect = int(deg0[t].sum() + deg1[t].sum())
+        assert st_["merge_entries"] == expect, (bi, st_["merge_entries"], expect)
+        assert st_["merge_ms"] > 0.0
+        assert_results_equal(res, o.apply(bt.u, bt.v, bt.w, bt.op, prune_bounds=g.ctx.del_prune), f"batch {bi}")
+    ctx.close()

@@ -606,14 +606,17 @@ __device__ i128 block_i128_scan(i128 v, i128* sh, i128* total) {
     return excl;
 }
 
+// Tile totals.  The sum of a tile is exact whatever the order, so the loads
+// are coalesced (item i * QT + thread of the tile) rather than in runs.
 __global__ void __launch_bounds__(QT) k_is_tile_sums(const i128* __restrict__ in, uint32_t n, i128* __restrict__ tsum,
                                                      const uint32_t* skip) {
     __shared__ i128 sh[QT / 32 + 1];
     if (skip && *skip) return;
-    const uint64_t base = (uint64_t)blockIdx.x * IS_TILE + (uint64_t)threadIdx.x * IS_ITEMS;
+    const uint64_t base = (uint64_t)blockIdx.x * IS_TILE + threadIdx.x;
     i128 s = 0;
+#pragma unroll
     for (int i = 0; i < IS_ITEMS; ++i)
-        if (base + i < n) s += in[base + i];
+        if (base + (uint64_t)i * QT < n) s += in[base + (uint64_t)i * QT];
     i128 tot;
     block_i128_scan(s, sh, &tot);
     if (threadIdx.x == 0) tsum[blockIdx.x] = tot;
@@ -635,22 +638,45 @@ __global__ void __launch_bounds__(1024) k_is_scan_tiles(i128* tsum, uint32_t til
     }
 }
 
+// slot of tile item p in the staging array: one pad slot per IS_ITEMS items, so
+// a thread's run of IS_ITEMS items and the coalesced pattern are both free of
+// shared-memory bank conflicts
+__device__ __forceinline__ uint32_t is_slot(uint32_t p) { return p + p / IS_ITEMS; }
+
+// Exclusive scan of one tile with the tile's prefix: coalesced loads staged in
+// shared memory, each thread scans a run of IS_ITEMS consecutive items, and the
+// results leave through the same staging array as coalesced stores.
 __global__ void __launch_bounds__(QT) k_is_tile_scan(const i128* __restrict__ in, uint32_t n,
                                                      const i128* __restrict__ tpre, i128* __restrict__ out,
                                                      const uint32_t* skip) {
     __shared__ i128 sh[QT / 32 + 1];
+    __shared__ i128 stage[IS_TILE + IS_TILE / IS_ITEMS];
     if (skip && *skip) return;
-    const uint64_t base = (uint64_t)blockIdx.x * IS_TILE + (uint64_t)threadIdx.x * IS_ITEMS;
+    const uint64_t tbase = (uint64_t)blockIdx.x * IS_TILE;
+#pragma unroll
+    for (int i = 0; i < IS_ITEMS; ++i) {
+        const uint32_t p = (uint32_t)i * QT + threadIdx.x;
+        stage[is_slot(p)] = tbase + p < n ? in[tbase + p] : (i128)0;
+    }
+    __syncthreads();
     i128 loc[IS_ITEMS];
     i128 s = 0;
+#pragma unroll
     for (int i = 0; i < IS_ITEMS; ++i) {
-        loc[i] = base + i < n ? in[base + i] : (i128)0;
+        loc[i] = stage[is_slot(threadIdx.x * IS_ITEMS + i)];
         s += loc[i];
     }
-    i128 run = tpre[blockIdx.x] + block_i128_scan(s, sh, nullptr);
+    i128 run = tpre[blockIdx.x] + block_i128_scan(s, sh, nullptr);  // (its barriers order the reads above)
+#pragma unroll
     for (int i = 0; i < IS_ITEMS; ++i) {
-        if (base + i < n) out[base + i] = run;
+        stage[is_slot(threadIdx.x * IS_ITEMS + i)] = run;
         run += loc[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < IS_ITEMS; ++i) {
+        const uint32_t p = (uint32_t)i * QT + threadIdx.x;
+        if (tbase + p < n) out[tbase + p] = stage[is_slot(p)];
     }
 }
 

@@ -759,20 +759,33 @@ __global__ void k_fs_scatter_a(uint32_t n, const uint32_t* __restrict__ tin, con
 }
 
 // potential: the open edges at y's entry, i.e. the prefix through tin_y minus
-// the prefix at the start of y's tour (exact, rounded once)
-__global__ void k_fs_potential(uint32_t n, const uint32_t* __restrict__ tin, const uint32_t* __restrict__ root,
-                               const uint32_t* __restrict__ toff, const i128* __restrict__ B,
-                               const i128* __restrict__ Q, const uint32_t* ex, int nbits, double* __restrict__ z,
-                               const uint32_t* skip) {
+// the prefix at the start of y's tour (exact, rounded once).  With part, also
+// the block's partial sum of dot_r . z (one per block, fixed slices)
+__global__ void __launch_bounds__(QT) k_fs_potential(uint32_t n, const uint32_t* __restrict__ tin,
+                                                     const uint32_t* __restrict__ root,
+                                                     const uint32_t* __restrict__ toff, const i128* __restrict__ B,
+                                                     const i128* __restrict__ Q, const uint32_t* ex, int nbits,
+                                                     double* __restrict__ z, const uint32_t* skip,
+                                                     const double* __restrict__ dot_r, double* __restrict__ part) {
+    __shared__ double sh[QT];
     if (skip && *skip) return;
     const int s = fixed_scale(ex[1], nbits);
+    double acc = 0.0;
     for (uint32_t y = blockIdx.x * blockDim.x + threadIdx.x; y < n; y += gridDim.x * blockDim.x) {
         const uint32_t i = tin[y];
-        z[y] = i == NONE ? 0.0 : from_fixed(Q[i] + B[i] - Q[toff[root[y]]], s);
+        const double zy = i == NONE ? 0.0 : from_fixed(Q[i] + B[i] - Q[toff[root[y]]], s);
+        z[y] = zy;
+        if (part) acc = fma(dot_r[y], zy, acc);
+    }
+    if (part) {
+        acc = block_sum(acc, sh);
+        if (threadIdx.x == 0) part[blockIdx.x] = acc;
     }
 }
 
-void forest_solve(Forest& F, const double* r, double* z, cudaStream_t st, const uint32_t* skip = nullptr) {
+// z = L_F^+ r; with part, also the partial sums of r . z (q_grid(n) of them)
+void forest_solve(Forest& F, const double* r, double* z, cudaStream_t st, const uint32_t* skip = nullptr,
+                  double* part = nullptr) {
     const uint32_t n = F.n;
     if (!n) return;
     if (F.nh) {
@@ -785,7 +798,7 @@ void forest_solve(Forest& F, const double* r, double* z, cudaStream_t st, const 
         i128_scan_exclusive(F.A.p, F.P.p, F.nh, F.tsum.p, st, skip);
     }
     QLAUNCH(k_fs_potential, q_grid(n), QT, st, n, F.tin.p, F.root.p, F.toff.p, F.A.p, F.P.p, F.ex.p, F.nbits, z,
-            skip);
+            skip, r, part);
 }
 
 // mean of v over every tree (at the root): the tour prefix at the tree's end
@@ -1210,7 +1223,8 @@ struct Solver {
         a = &al;
         st = s;
         np = dot_blocks();
-        part.ensure(al, (size_t)np + 1, st);
+        // the forest solve leaves one partial (r, z) per block of its grid
+        part.ensure(al, (size_t)std::max(np, q_grid(n)) + 1, st);
         part2.ensure(al, (size_t)np + 1, st);
         sc.ensure(al, 2, st);
         DG_CUDA(cudaMallocHost(&host_sc, 2 * sizeof(CgScal)));
@@ -1231,18 +1245,22 @@ struct Solver {
         DG_CUDA(cudaStreamSynchronize(st));
     }
 
-    // z = M^-1 r
-    void precond(Pre pre, const double* r, double* z, uint32_t n, const uint32_t* skip) {
+    // z = M^-1 r and the partial sums of (r, z) into part; returns how many
+    int precond(Pre pre, const double* r, double* z, uint32_t n, const uint32_t* skip) {
         switch (pre) {
             case Pre::None: QLAUNCH(k_copy, q_grid(n), QT, st, r, z, n, skip); break;
             case Pre::Jacobi: QLAUNCH(k_jacobi, q_grid(n), QT, st, r, G->diag.p, z, n, skip); break;
-            case Pre::Forest: forest_solve(*F, r, z, st, skip); break;
+            case Pre::Forest:
+                forest_solve(*F, r, z, st, skip, part.p);  // (r, z) in the same pass
+                return q_grid(n);
             case Pre::Inner:
                 // the inner solve runs only when the outer iteration goes on
                 // (the caller checked the flag on the host)
                 hsolve(r, z, n);
                 break;
         }
+        QLAUNCH(k_dot_part, np, QT, st, r, z, n, part.p, skip);
+        return np;
     }
 
     // z = L_H^+ r: the part of r in the range of L_H (r minus its mean over
@@ -1274,9 +1292,8 @@ struct Solver {
                 read_scal(k);
                 if (host_sc[k].done) return false;
             }
-            precond(pre, v.r.p, v.z.p, n, done);
-            QLAUNCH(k_dot_part, np, QT, st, v.r.p, v.z.p, n, part.p, done);
-            QLAUNCH(k_cg_beta, 1, QT, st, s, part.p, np);
+            const int nz = precond(pre, v.r.p, v.z.p, n, done);
+            QLAUNCH(k_cg_beta, 1, QT, st, s, part.p, nz);
             QLAUNCH(k_cg_p, q_grid(n), QT, st, v.z.p, v.p.p, n, s);
             return true;
         };

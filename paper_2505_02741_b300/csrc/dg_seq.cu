@@ -70,6 +70,8 @@ struct SeqArgs {
     uint32_t* paths;       // per walker: T + 1 vertices
     double* pathR;         // per walker: the resistance after each step
     uint32_t* lim;         // per walked insertion: the first hit's step (the batch cuts every walker there)
+    uint32_t* kb;          // per walked update, during the dry run: the least hit step (insertion) or
+                           // the high word of the least hit resistance (deletion) found so far
     double* rbar;          // per walked deletion: the least hit resistance (the batch prunes beyond it)
     uint32_t* wsteps;      // per walker
     uint8_t* whit;
@@ -115,6 +117,7 @@ __global__ void k_seq_classify(SeqArgs a) {
         a.key[j] = key;
         a.best[j] = SEQ_NONE;
         a.accepted[j] = 0;
+        a.kb[j] = SEQ_NONE;
     }
 }
 
@@ -131,7 +134,19 @@ __global__ void k_seq_repeats(SeqArgs a) {
     }
 }
 
-// one thread per walker: the walk the batch would run, every vertex recorded
+// one thread per walker: the walk the batch would run, every vertex recorded.
+// A walker may stop as soon as the batch's own cut of its update is certain
+// to end it (the same rules as the batched walk): an insertion's walker once a
+// walker of its update hit at a step no later than its own, a deletion's once
+// its resistance is above a hit of its update.  Every vertex the batch's
+// walker reads is recorded all the same (the conflict test stops at the
+// update's least hit, which such a bound never undercuts), and the hits
+// that decide the update are unchanged.  The Philox word of the next step is
+// formed while the entry load is in flight.
+__device__ __forceinline__ uint32_t seq_r_key(double R) {
+    return (uint32_t)((unsigned long long)__double_as_longlong(R) >> 32);
+}
+
 __global__ void k_seq_walk(SeqArgs a) {
     const uint32_t total = a.m * a.s;
     for (uint32_t wid = blockIdx.x * blockDim.x + threadIdx.x; wid < total; wid += gridDim.x * blockDim.x) {
@@ -145,31 +160,55 @@ __global__ void k_seq_walk(SeqArgs a) {
             continue;
         }
         const bool ins = kind == WALK_INS;
+        const bool cut = ins ? a.early_exit != 0 : a.del_prune != 0;
         const CSRView& g = ins ? a.H : a.G;
         const dg_update up = a.ups[j];
         const uint32_t u = (uint32_t)up.u, q = (uint32_t)up.v;
         const uint64_t id = a.id0 + j;
         const uint32_t own = ins ? SEQ_NONE : a.qslot[j];
         uint32_t c = u, prev_slot = SEQ_NONE, steps = 0;
+        // after arriving at a hub the previous vertex p is known by id only,
+        // with a hint of its slot (the reference's, possibly drifted)
+        bool pid = false;
+        uint32_t p = SEQ_NONE, hint = 0;
         double R = 0.0;
         bool hit = false;
         path[0] = u;
         uint32_t off = g.off[u], deg = g.deg[u];
+        uint32_t x = philox_word0(0u, k, (uint32_t)id, (uint32_t)(id >> 32), a.key0, a.key1);
         for (;;) {
-            // skipped positions: the previous vertex and, at u, a deletion's own edge
-            uint32_t e1 = prev_slot, e2 = c == u ? own : SEQ_NONE;
-            if (e1 > e2) {
-                const uint32_t t = e1;
-                e1 = e2;
-                e2 = t;
+            if (pid && c == u && own != SEQ_NONE) {  // two skips, one of them by id: find its slot
+                prev_slot = find_nbr(g, c, p);
+                pid = false;
             }
-            const uint32_t skip = (e1 != SEQ_NONE) + (e2 != SEQ_NONE);
-            if (deg <= skip) break;  // a leaf: no neighbour to go to
-            const uint32_t x = philox_word0(steps, k, (uint32_t)id, (uint32_t)(id >> 32), a.key0, a.key1);
-            uint32_t idx = __umulhi(x, deg - skip);  // the idx-th allowed neighbour in list order
-            if (idx >= e1) ++idx;
-            if (idx >= e2) ++idx;
-            const Ent e = g.pool[off + idx];
+            Ent e;
+            if (pid) {
+                // the jj-th neighbour other than p is L[jj] when L[jj] < p and
+                // L[jj + 1] otherwise; the hint picks which to load first
+                if (deg <= 1) break;
+                const uint32_t jj = __umulhi(x, deg - 1);
+                uint32_t idx = jj + (jj >= hint ? 1u : 0u);
+                e = g.pool[off + idx];
+                if (idx == jj ? !(e.nbr < p) : !(e.nbr > p)) {
+                    idx = idx == jj ? jj + 1u : jj;
+                    e = g.pool[off + idx];
+                }
+            } else {
+                // skipped positions: the previous vertex and, at u, a deletion's own edge
+                uint32_t e1 = prev_slot, e2 = c == u ? own : SEQ_NONE;
+                if (e1 > e2) {
+                    const uint32_t t = e1;
+                    e1 = e2;
+                    e2 = t;
+                }
+                const uint32_t skip = (e1 != SEQ_NONE) + (e2 != SEQ_NONE);
+                if (deg <= skip) break;  // a leaf: no neighbour to go to
+                uint32_t idx = __umulhi(x, deg - skip);  // the idx-th allowed neighbour in list order
+                if (idx >= e1) ++idx;
+                if (idx >= e2) ++idx;
+                e = g.pool[off + idx];
+            }
+            x = philox_word0(steps + 1u, k, (uint32_t)id, (uint32_t)(id >> 32), a.key0, a.key1);
             const uint32_t nx = e.nbr;
             R = __dadd_rn(R, e.r);
             ++steps;
@@ -177,20 +216,33 @@ __global__ void k_seq_walk(SeqArgs a) {
             a.pathR[(size_t)wid * (a.T + 1) + steps] = R;
             if (nx == q && (!ins || __dmul_rn(up.w, R) <= a.K)) {
                 hit = true;
+                if (cut) atomicMin(&a.kb[j], ins ? steps : seq_r_key(R));
                 break;
             }
             if (ins && __dmul_rn(up.w, R) > a.K) break;
             if (steps == a.T) break;
-            // the next list and our slot in it: cached in the entry, except for
-            // a hub (whose slot hint is checked, else searched)
+            if (cut) {
+                const uint32_t b = __ldcg(&a.kb[j]);
+                if (ins ? b <= steps : seq_r_key(R) > b) break;
+            }
+            // the next list and our slot in it: cached in the entry; a hub's from
+            // the vertex arrays, our slot there known by id (and a hint)
             if (e.noff != HUBREF && e.ndeg != 0) {
                 off = e.noff;
                 deg = e.ndeg;
                 prev_slot = e.rev;
-            } else {
+                pid = false;
+            } else if (e.noff == HUBREF) {
                 off = g.off[nx];
                 deg = g.deg[nx];
-                prev_slot = (e.rev < deg && g.pool[off + e.rev].nbr == c) ? e.rev : find_nbr(g, nx, c);
+                pid = true;
+                p = c;
+                hint = e.rev;
+            } else {  // an entry whose cache was never filled
+                off = g.off[nx];
+                deg = g.deg[nx];
+                prev_slot = find_nbr(g, nx, c);
+                pid = false;
             }
             c = nx;
         }
@@ -264,10 +316,13 @@ __device__ __forceinline__ uint32_t other(const uint32_t* t1, const uint32_t* t2
 }
 
 // every vertex a walker of update j stands on, and j's endpoints: the first
-// other update changing it ends the prefix before max(j, that update)
+// other update changing it ends the prefix before max(j, that update).  A
+// warp takes a walker: its lanes look at 32 steps of the path at once.
 __global__ void k_seq_conflicts(SeqArgs a) {
     const uint32_t total = a.m * a.s;
-    for (uint32_t wid = blockIdx.x * blockDim.x + threadIdx.x; wid < total; wid += gridDim.x * blockDim.x) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; wid < total; wid += nwarps) {
         const uint32_t j = wid / a.s;
         const uint8_t kind = a.kind[j];
         if (kind != WALK_INS && kind != WALK_DEL) continue;
@@ -280,14 +335,22 @@ __global__ void k_seq_conflicts(SeqArgs a) {
         if (kind == WALK_INS && a.early_exit) steps = min(steps, a.lim[j]);
         const double rb = kind == WALK_DEL && a.del_prune ? a.rbar[j] : INFINITY;
         uint32_t first = SEQ_NONE;
-        for (uint32_t i = 0; i <= steps; ++i) {
-            const uint32_t v = path[i];
-            uint32_t x = other(a.h1, a.h2, v, j);
-            if (kind == WALK_DEL) x = min(x, other(a.g1, a.g2, v, j));
-            first = min(first, x);
-            if (i > 0 && pR[i] > rb) break;
+        for (uint32_t base = 0; base <= steps; base += 32u) {
+            const uint32_t i = base + lane;
+            const bool in = i <= steps;
+            const bool over = in && i > 0 && pR[i] > rb;
+            const uint32_t om = __ballot_sync(0xffffffffu, over);
+            const uint32_t last = om ? base + (uint32_t)(__ffs(om) - 1) : SEQ_NONE;  // included, then stop
+            if (in && i <= last) {
+                const uint32_t v = path[i];
+                uint32_t x = other(a.h1, a.h2, v, j);
+                if (kind == WALK_DEL) x = min(x, other(a.g1, a.g2, v, j));
+                first = min(first, x);
+            }
+            if (om) break;
         }
-        if (first != SEQ_NONE) atomicMin(a.cut, max(j, first));
+        for (int o = 16; o > 0; o >>= 1) first = min(first, __shfl_xor_sync(0xffffffffu, first, o));
+        if (lane == 0 && first != SEQ_NONE) atomicMin(a.cut, max(j, first));
     }
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < a.m; j += gridDim.x * blockDim.x) {
         if (!a.valid[j]) continue;
@@ -301,7 +364,7 @@ __global__ void k_seq_conflicts(SeqArgs a) {
 struct SeqWS {
     uint32_t n = 0, wmax = 0, s = 0, T = 0;
     DBuf<uint8_t> kind, valid, accepted, whit;
-    DBuf<uint32_t> qslot, best, paths, wsteps, tabs, cut, lim;
+    DBuf<uint32_t> qslot, best, paths, wsteps, tabs, cut, lim, kb;
     DBuf<uint64_t> key;
     DBuf<double> wR, pathR, rbar;
     DBuf<dg_update> ups;
@@ -322,6 +385,7 @@ struct SeqWS {
         paths.ensure(a, nw * (TT + 1), st);
         pathR.ensure(a, nw * (TT + 1), st);
         lim.ensure(a, w, st);
+        kb.ensure(a, w, st);
         rbar.ensure(a, w, st);
         wsteps.ensure(a, nw, st);
         wR.ensure(a, nw, st);
@@ -330,7 +394,7 @@ struct SeqWS {
     }
     void release(DevAlloc& a, cudaStream_t st) {
         for (auto* b : {&kind, &valid, &accepted, &whit}) b->release(a, st);
-        for (auto* b : {&qslot, &best, &paths, &wsteps, &tabs, &cut, &lim}) b->release(a, st);
+        for (auto* b : {&qslot, &best, &paths, &wsteps, &tabs, &cut, &lim, &kb}) b->release(a, st);
         key.release(a, st);
         for (auto* b : {&wR, &pathR, &rbar}) b->release(a, st);
         ups.release(a, st);
@@ -388,6 +452,7 @@ void graph_apply_sequential(Ctx& c, DGraph& g, int64_t nu64, const dg_update* up
             A.paths = w.paths.p;
             A.pathR = w.pathR.p;
             A.lim = w.lim.p;
+            A.kb = w.kb.p;
             A.rbar = w.rbar.p;
             A.wsteps = w.wsteps.p;
             A.whit = w.whit.p;
@@ -405,7 +470,7 @@ void graph_apply_sequential(Ctx& c, DGraph& g, int64_t nu64, const dg_update* up
             k_seq_decide<<<s_grid(m), ST, 0, st>>>(A);
             k_seq_edits<1><<<s_grid(m), ST, 0, st>>>(A);
             k_seq_edits<2><<<s_grid(m), ST, 0, st>>>(A);
-            k_seq_conflicts<<<s_grid((uint64_t)m * S), ST, 0, st>>>(A);
+            k_seq_conflicts<<<s_grid((uint64_t)m * S * 32), ST, 0, st>>>(A);
             g_launches += 7;
             uint32_t cnt = 0;
             DG_CUDA(cudaMemcpyAsync(&cnt, w.cut.p, 4, cudaMemcpyDeviceToHost, st));

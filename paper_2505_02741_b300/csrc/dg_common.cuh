@@ -194,6 +194,39 @@ __device__ __forceinline__ uint32_t lower_bound_nbr(const Ent* L, uint32_t d, ui
     return lo;
 }
 
+// The same lower bound, searched outward from position h (a slot that has
+// drifted by a few positions since it was recorded): the probes start next to
+// h and double their distance until they bracket y, then a binary search
+// inside the bracket.  Any h gives the same result as lower_bound_nbr.
+__device__ __forceinline__ uint32_t lower_bound_nbr_near(const Ent* L, uint32_t d, uint32_t y, uint32_t h) {
+    if (d == 0) return 0;
+    if (h >= d) h = d - 1;
+    uint32_t lo, hi, s = 1;  // the bound lies in [lo, hi]
+    if (L[h].nbr < y) {
+        lo = h + 1;
+        hi = lo;
+        while (hi < d && L[hi].nbr < y) {
+            lo = hi + 1;
+            s <<= 1;
+            hi = (d - lo > s) ? lo + s : d;
+        }
+    } else {
+        hi = h;
+        lo = h;
+        while (lo > 0 && !(L[lo - 1].nbr < y)) {
+            hi = lo - 1;
+            s <<= 1;
+            lo = hi > s ? hi - s : 0;
+        }
+    }
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (L[mid].nbr < y) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
 // position of y in x's list or 0xFFFFFFFF
 __device__ __forceinline__ uint32_t find_nbr(const CSRView& g, uint32_t x, uint32_t y) {
     const Ent* L = g.pool + g.off[x];

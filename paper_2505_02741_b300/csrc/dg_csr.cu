@@ -664,6 +664,8 @@ __global__ void k_exec_fix(ExecArgs a, uint32_t* d_err) {
             if (p != 0xFFFFFFFFu) return true;
             if (!fresh && e.y != HUBREF && !(ty & 1u)) {  // a valid copied entry caches the slot
                 p = e.w;
+            } else if (!fresh) {  // the slot it cached (or a hub's hint) is near
+                p = lower_bound_nbr_near(a.g.pool + ly, dy, x, e.w);
             } else {
                 p = lower_bound_nbr(a.g.pool + ly, dy, x);
             }

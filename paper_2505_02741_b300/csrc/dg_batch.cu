@@ -335,13 +335,6 @@ __global__ void k_make_tasks(const dg_update* __restrict__ ups, const uint8_t* _
     }
 }
 
-__global__ void k_flag_hrem(const uint32_t* __restrict__ gvals, const uint8_t* __restrict__ ghrem,
-                            const uint32_t* d_n, uint32_t n_max, uint32_t* __restrict__ flag) {
-    const uint32_t n = min(*d_n, n_max);
-    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
-        flag[c] = ghrem[gvals[c]];
-}
-
 // commit candidates: first of each equal-key run and not already in H'
 __global__ void k_commit_flags(const uint64_t* __restrict__ keys, const uint32_t* d_n, uint32_t n_max, CSRView H,
                                uint32_t* __restrict__ flag, const uint32_t* d_err) {
@@ -365,7 +358,7 @@ uint64_t BatchWS::bytes() const {
     b += vkeys.bytes() + vkeys_alt.bytes() + vvals.bytes() + vvals_alt.bytes() + vhist.bytes() + vscan.bytes();
     b += wkind.bytes() + fin_w.bytes() + wflag.bytes() + wpos.bytes() + wflag2.bytes() + wpos2.bytes();
     b += gkeys.bytes() + gkeys_alt.bytes() + hkeys.bytes() + gvals.bytes() + gvals_alt.bytes() + ghist.bytes();
-    b += gscan.bytes() + gcount.bytes() + hflag.bytes() + hpos.bytes() + hvals.bytes() + hcount.bytes();
+    b += gscan.bytes() + gcount.bytes() + hpos.bytes() + hvals.bytes() + hcount.bytes();
     b += gkind.bytes() + ghrem.bytes() + kind_del.bytes() + gw.bytes() + vtab.bytes();
     b += t_u.bytes() + t_v.bytes() + t_idx.bytes() + t_kstar.bytes() + t_count.bytes() + meta.bytes();
     b += t_fin.bytes() + t_queue.bytes() + qctr.bytes() + cp.bytes() + step_r.bytes() + step_e.bytes();
@@ -440,7 +433,6 @@ static void ensure_ws(Ctx& c, DGraph& g, uint32_t b_max, cudaStream_t st) {
     w.ghist.ensure(a, sort_hist_words(B2), st);
     w.gscan.ensure(a, std::max(sort_scan_tmp_words(B2), scan_tmp_words(B2 + 1)), st);
     w.gcount.ensure(a, 1, st);
-    w.hflag.ensure(a, B2, st);
     w.hpos.ensure(a, B2, st);
     w.hvals.ensure(a, B2, st);
     w.hcount.ensure(a, 1, st);
@@ -828,7 +820,7 @@ void graph_release_ws(Ctx& c, DGraph& g, cudaStream_t st) {
 #define REL(b) w.b.release(c.alloc, st)
     REL(ups); REL(res); REL(hdr); REL(err); REL(ctr); REL(next); REL(vkeys); REL(vtab); REL(vkeys_alt); REL(vvals);
     REL(vvals_alt); REL(vhist); REL(vscan); REL(wkind); REL(fin_w); REL(wflag); REL(wpos); REL(wflag2); REL(wpos2); REL(gkeys);
-    REL(gkeys_alt); REL(hkeys); REL(gvals); REL(gvals_alt); REL(ghist); REL(gscan); REL(gcount); REL(hflag);
+    REL(gkeys_alt); REL(hkeys); REL(gvals); REL(gvals_alt); REL(ghist); REL(gscan); REL(gcount);
     REL(hpos); REL(hvals); REL(hcount); REL(gkind); REL(ghrem); REL(kind_del); REL(gw); REL(t_u); REL(t_v);
     REL(t_idx); REL(t_kstar); REL(t_fin); REL(t_queue); REL(qctr); REL(cp); REL(step_r); REL(step_e); REL(t_count); REL(meta); REL(t_wpq); REL(t_rmax); REL(recR); REL(t_kind); REL(best);
     REL(ckeys); REL(ckeys_alt); REL(ck2); REL(cvals); REL(cvals_alt); REL(chist); REL(cscan); REL(ccount);
@@ -1050,19 +1042,23 @@ static void enqueue_mutate(Ctx& c, DGraph& g, cudaStream_t st) {
     const uint32_t* gv = galt ? w.gvals_alt.p : w.gvals.p;
     DG_CUDA(cudaEventRecord(g.fk[1], st));
     DG_CUDA(cudaStreamWaitEvent(sd, g.fk[1], 0));
-    k_flag_hrem<<<grid_for(B2), BT, 0, sd>>>(gv, w.ghrem.p, w.gcount.p, B2, w.hflag.p);
-    ++g_launches;
     {
+        // H's change list: the G changes that remove an H edge, compacted by
+        // the scan of their flags (generated from the removal marks)
         ScanJob j;
-        j.in[0] = w.hflag.p;
+        j.gen.mode = 2;
+        j.gen.bytes = w.ghrem.p;
+        j.gen.idx = gv;
         j.out[0] = w.hpos.p;
         j.total[0] = w.hcount.p;
         j.k = 1;
         j.err = w.err.p;
+        j.cmp.keys = gk;
+        j.cmp.vals = gv;
+        j.cmp.okeys = w.hkeys.p;
+        j.cmp.ovals = w.hvals.p;
         scan_exclusive(j, w.gcount.p, B2, w.gscan.p, sd, true);
     }
-    k_compact_kv<<<grid_for(B2), BT, 0, sd>>>(gk, gv, w.hflag.p, w.hpos.p, w.gcount.p, B2, w.hkeys.p, w.hvals.p);
-    ++g_launches;
     ChangeList clG;
     clG.keys = gk;
     clG.vals = gv;
@@ -1265,10 +1261,12 @@ static void enqueue_commit(Ctx& c, DGraph& g, cudaStream_t st, bool walk_emitted
         j.total[0] = w.ccount2.p;
         j.k = 1;
         j.err = w.err.p;
+        j.cmp.keys = ck;  // the candidates kept, compacted by the same scan
+        j.cmp.vals = cv;
+        j.cmp.okeys = w.ck2.p;
+        j.cmp.ovals = w.cv2.p;
         scan_exclusive(j, w.ccount.p, CC, w.cscan.p, st, scratch_zeroed);
     }
-    k_compact_kv<<<grid_for(CC), BT, 0, st>>>(ck, cv, w.cflag.p, w.cpos.p, w.ccount.p, CC, w.ck2.p, w.cv2.p);
-    ++g_launches;
     ChangeList clC;
     clC.keys = w.ck2.p;
     clC.vals = w.cv2.p;

@@ -59,7 +59,7 @@ struct BatchWS {
     DBuf<uint32_t> wflag, wpos, wflag2, wpos2;
     // G changes (and the H removals among them)
     DBuf<uint64_t> gkeys, gkeys_alt, hkeys;
-    DBuf<uint32_t> gvals, gvals_alt, ghist, gscan, gcount, hflag, hpos, hvals, hcount;
+    DBuf<uint32_t> gvals, gvals_alt, ghist, gscan, gcount, hpos, hvals, hcount;
     DBuf<uint8_t> gkind, ghrem, kind_del;
     DBuf<double> gw;
     // walks

@@ -31,9 +31,9 @@ __device__ __forceinline__ uint64_t ent_key_u64(uint32_t x, uint32_t y, uint32_t
 // scratch management
 // ---------------------------------------------------------------------------
 void ApplyScratch::ensure(DevAlloc& a, uint32_t changes, uint64_t stage_entries, cudaStream_t st) {
-    if (changes > c_max || !f_head.p) {
+    if (changes > c_max || !p_head.p) {
         uint32_t c = changes < 1024 ? 1024 : changes;
-        DBuf<uint32_t>* bufs[] = {&f_head, &f_ins, &f_del, &p_head, &p_ins, &p_del, &tv, &tstart, &tend,
+        DBuf<uint32_t>* bufs[] = {&p_head, &p_ins, &p_del, &tv, &tstart, &tend,
                                   &odeg, &ndeg, &ooff, &ncap, &rsz, &work, &r_off, &s_off, &w_off,
                                   &fwork, &f_off, &sdeg, &xm, &tdst};
         for (auto* b : bufs) b->ensure(a, (size_t)c + 1, st);
@@ -50,7 +50,7 @@ void ApplyScratch::ensure(DevAlloc& a, uint32_t changes, uint64_t stage_entries,
 }
 
 void ApplyScratch::release(DevAlloc& a, cudaStream_t st) {
-    DBuf<uint32_t>* bufs[] = {&f_head, &f_ins, &f_del, &p_head, &p_ins, &p_del, &tv, &tstart, &tend,
+    DBuf<uint32_t>* bufs[] = {&p_head, &p_ins, &p_del, &tv, &tstart, &tend,
                               &odeg, &ndeg, &ooff, &ncap, &rsz, &work, &r_off, &s_off, &w_off,
                               &fwork, &f_off, &sdeg, &xm, &tdst, &scan_tmp, &totals};
     for (auto* b : bufs) b->release(a, st);
@@ -60,7 +60,7 @@ void ApplyScratch::release(DevAlloc& a, cudaStream_t st) {
 }
 
 uint64_t ApplyScratch::bytes() const {
-    return 23ull * (c_max + 1) * 4 + scan_tmp.bytes() + totals.bytes() + stage.bytes();
+    return 20ull * (c_max + 1) * 4 + scan_tmp.bytes() + totals.bytes() + stage.bytes();
 }
 
 void csr_alloc_vertices(CSR& g, DevAlloc& a, int32_t n, cudaStream_t st) {
@@ -239,19 +239,6 @@ void csr_build(CSR& g, DevAlloc& a, const uint64_t* keys, const uint32_t* vals, 
 // ---------------------------------------------------------------------------
 // plan
 // ---------------------------------------------------------------------------
-__global__ void k_plan_flags(ChangeList cl, uint32_t n, uint32_t* __restrict__ f_head,
-                             uint32_t* __restrict__ f_ins, uint32_t* __restrict__ f_del, const uint32_t* d_err) {
-    if (aborted(d_err)) return;
-    const uint32_t count = count_of(cl.d_count, cl.max_count);
-    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < count; c += gridDim.x * blockDim.x) {
-        const uint32_t x = (uint32_t)(cl.keys[c] / n);
-        f_head[c] = (c == 0 || (uint32_t)(cl.keys[c - 1] / n) != x) ? 1u : 0u;
-        const uint8_t kd = cl.kinds[cl.vals[c]];
-        f_ins[c] = kd == CHG_INS;
-        f_del[c] = kd == CHG_DEL;
-    }
-}
-
 struct PlanArgs {
     ChangeList cl;
     CSRView g;
@@ -340,29 +327,24 @@ __global__ void k_plan_touch(PlanArgs a, const uint32_t* d_err) {
     }
 }
 
-__global__ void k_plan_alloc(CSRView g, uint32_t* totals, uint64_t stage_cap, uint32_t* d_err,
-                             uint32_t pool_bit, uint32_t cap_bit) {
-    if (aborted(d_err)) return;
-    const unsigned long long base = *g.top;
-    const uint64_t R = totals[TOT_R];
-    const uint64_t S = totals[TOT_S];
-    totals[TOT_BASE_LO] = (uint32_t)base;
-    totals[TOT_BASE_HI] = (uint32_t)(base >> 32);
-    if (base + R > g.pool_cap) atomicOr(d_err, pool_bit);
-    else if (S > stage_cap) atomicOr(d_err, cap_bit);
-}
-
 void csr_plan(CSR& g, const ChangeList& cl, ApplyScratch& s, uint32_t* d_err, uint32_t pool_bit,
               uint32_t cap_bit, cudaStream_t st, bool tmp_zeroed) {
     const int grid = flat_grid();
     const uint32_t C = cl.max_count;
     uint32_t* tot = s.totals.p;
-    k_plan_flags<<<grid, FLAT_THREADS, 0, st>>>(cl, (uint32_t)g.n, s.f_head.p, s.f_ins.p, s.f_del.p, d_err);
-    ++g_launches;
+    // run heads, insertions and deletions of the change list, generated inside
+    // the scan (no flag arrays)
     ScanJob j1;
-    j1.in[0] = s.f_head.p; j1.out[0] = s.p_head.p; j1.total[0] = tot + TOT_X;
-    j1.in[1] = s.f_ins.p;  j1.out[1] = s.p_ins.p;  j1.total[1] = tot + TOT_NI;
-    j1.in[2] = s.f_del.p;  j1.out[2] = s.p_del.p;  j1.total[2] = tot + TOT_ND;
+    j1.gen.mode = 1;
+    j1.gen.keys = cl.keys;
+    j1.gen.n_div = (uint64_t)g.n;
+    j1.gen.vals = cl.vals;
+    j1.gen.kinds = cl.kinds;
+    j1.gen.k_ins = CHG_INS;
+    j1.gen.k_del = CHG_DEL;
+    j1.out[0] = s.p_head.p; j1.total[0] = tot + TOT_X;
+    j1.out[1] = s.p_ins.p;  j1.total[1] = tot + TOT_NI;
+    j1.out[2] = s.p_del.p;  j1.total[2] = tot + TOT_ND;
     j1.k = 3;
     j1.err = d_err;
     scan_exclusive(j1, cl.d_count, C, s.scan_tmp.p, st, tmp_zeroed);
@@ -384,9 +366,22 @@ void csr_plan(CSR& g, const ChangeList& cl, ApplyScratch& s, uint32_t* d_err, ui
     j2.in[3] = s.fwork.p; j2.out[3] = s.f_off.p; j2.total[3] = tot + TOT_F;
     j2.k = 4;
     j2.err = d_err;
+    // the pool allocation follows the totals in the same launch: base = the
+    // pool top; the batch aborts (before any list is written) when the new
+    // regions or the staged lists do not fit
+    j2.post.top = g.top.p;
+    j2.post.pool_cap = g.pool_cap;
+    j2.post.stage_cap = s.s_cap;
+    j2.post.totals = tot;
+    j2.post.r_idx = TOT_R;
+    j2.post.s_idx = TOT_S;
+    j2.post.base_lo = TOT_BASE_LO;
+    j2.post.base_hi = TOT_BASE_HI;
+    j2.post.err = d_err;
+    j2.post.abort_mask = ABORT_MASK;
+    j2.post.pool_bit = pool_bit;
+    j2.post.cap_bit = cap_bit;
     scan_exclusive(j2, tot + TOT_X, C, s.scan_tmp.p + s.scan_words, st, tmp_zeroed);
-    k_plan_alloc<<<1, 1, 0, st>>>(g.view(), tot, s.s_cap, d_err, pool_bit, cap_bit);
-    ++g_launches;
     DG_CHECK_LAUNCH();
 }
 
@@ -413,8 +408,8 @@ __device__ __forceinline__ uint32_t dst_off(const ExecArgs& a, uint32_t t) {
     return mode == XM_FRESH ? (uint32_t)(base_of(a.totals) + a.r_off[t]) : mode == XM_TWIN ? a.tdst[t] : a.ooff[t];
 }
 
-__global__ void k_exec_meta(ExecArgs a, const uint32_t* d_err) {
-    if (aborted(d_err)) return;
+// every touched vertex's list fields, hub flag and touched mark
+__device__ __forceinline__ void exec_meta(const ExecArgs& a) {
     const uint32_t X = a.totals[TOT_X];
     if (blockIdx.x == 0 && threadIdx.x == 0)
         *a.g.top = (unsigned long long)(base_of(a.totals) + a.totals[TOT_R]);
@@ -592,8 +587,12 @@ __global__ void k_exec_merge(ExecArgs a, uint32_t* d_err) {
     });
 }
 
-__global__ void k_exec_place(ExecArgs a, const uint32_t* d_err) {
+// meta points every touched vertex at its final slots; place copies the
+// staged lists (those without a twin) back.  Neither reads what the other
+// writes, so one launch does both.
+__global__ void k_exec_meta_place(ExecArgs a, const uint32_t* d_err) {
     if (aborted(d_err)) return;
+    exec_meta(a);
     const uint32_t X = a.totals[TOT_X];
     const uint32_t S = a.totals[TOT_S];
     for_segment_items<16>(a.s_off, X, S, [&](uint32_t item, uint32_t t, uint32_t local) {
@@ -721,16 +720,15 @@ void csr_exec(CSR& g, const ChangeList& cl, ApplyScratch& s, uint32_t* touched, 
     a.stage = s.stage.p;
     a.touched = touched;
     // merge reads the old lists and writes the new ones (into twins or fresh
-    // space; lists without a twin into the staging buffer); meta then points
-    // every touched vertex at its final slots; place copies staged lists back;
-    // fix refreshes caches.
+    // space; lists without a twin into the staging buffer); meta_place then
+    // points every touched vertex at its final slots and copies staged lists
+    // back; fix refreshes caches.
     if (merge_t0) DG_CUDA(record_timing_event(merge_t0, st));
     k_exec_merge<<<grid, FLAT_THREADS, 0, st>>>(a, d_err);
     if (merge_t1) DG_CUDA(record_timing_event(merge_t1, st));
-    k_exec_meta<<<grid, FLAT_THREADS, 0, st>>>(a, d_err);
-    k_exec_place<<<grid, FLAT_THREADS, 0, st>>>(a, d_err);
+    k_exec_meta_place<<<grid, FLAT_THREADS, 0, st>>>(a, d_err);
     k_exec_fix<<<grid, FLAT_THREADS, 0, st>>>(a, d_err);
-    g_launches += 4;
+    g_launches += 3;
     DG_CHECK_LAUNCH();
 }
 

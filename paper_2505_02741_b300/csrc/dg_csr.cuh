@@ -70,7 +70,7 @@ enum { TOT_X = 0, TOT_NI, TOT_ND, TOT_R, TOT_S, TOT_WK, TOT_BASE_LO, TOT_BASE_HI
 struct ApplyScratch {
     uint32_t c_max = 0;
     uint64_t s_cap = 0;  // entries of staging space
-    DBuf<uint32_t> f_head, f_ins, f_del, p_head, p_ins, p_del;
+    DBuf<uint32_t> p_head, p_ins, p_del;  // exclusive run heads, insertions, deletions (the plan's first scan)
     DBuf<uint32_t> tv, tstart, tend, odeg, ndeg, ooff, ncap, rsz, work, r_off, s_off, w_off, fwork, f_off;
     DBuf<uint32_t> sdeg, xm, tdst;  // staged size, placement mode, twin destination (see k_plan_touch)
     DBuf<uint32_t> scan_tmp, totals;  // scan_tmp: one region of scan_words per scan of the plan (2)

@@ -42,7 +42,41 @@ struct ScanArgs {
     uint32_t* total[4];
     int k;
     uint32_t* err;
+    ScanGen gen;
+    ScanCompact cmp;
+    ScanAlloc post;
 };
+
+// element c of input array j (read, or generated: see ScanGen)
+__device__ __forceinline__ uint32_t scan_in(const ScanArgs& a, int j, uint32_t c) {
+    if (a.gen.mode == 1) {
+        if (j == 0) return (c == 0 || a.gen.keys[c - 1] / a.gen.n_div != a.gen.keys[c] / a.gen.n_div) ? 1u : 0u;
+        const uint8_t kd = a.gen.kinds[a.gen.vals[c]];
+        return (j == 1 ? kd == a.gen.k_ins : kd == a.gen.k_del) ? 1u : 0u;
+    }
+    if (a.gen.mode == 2) return a.gen.bytes[a.gen.idx[c]];
+    return a.in[j][c];
+}
+
+// the exclusive prefix of item c of array j is pos: store it, and compact
+__device__ __forceinline__ void scan_out(const ScanArgs& a, int j, uint32_t c, uint32_t pos, uint32_t v) {
+    a.out[j][c] = pos;
+    if (j == 0 && a.cmp.keys && v) {
+        a.cmp.okeys[pos] = a.cmp.keys[c];
+        a.cmp.ovals[pos] = a.cmp.vals[c];
+    }
+}
+
+// the optional step after the totals (see ScanAlloc); one thread
+__device__ __forceinline__ void scan_post(const ScanAlloc& p) {
+    if (!p.top) return;
+    if (*p.err & p.abort_mask) return;
+    const unsigned long long base = *p.top;
+    p.totals[p.base_lo] = (uint32_t)base;
+    p.totals[p.base_hi] = (uint32_t)(base >> 32);
+    if (base + p.totals[p.r_idx] > p.pool_cap) atomicOr(p.err, p.pool_bit);
+    else if ((uint64_t)p.totals[p.s_idx] > p.stage_cap) atomicOr(p.err, p.cap_bit);
+}
 
 constexpr uint32_t SMALL_SCAN_MAX = 16384;
 constexpr int LB_THREADS = 256;
@@ -75,7 +109,7 @@ __global__ void __launch_bounds__(1024) k_scan_single(ScanArgs a, const uint32_t
             if (j < K) {
 #pragma unroll
                 for (int i = 0; i < IT; ++i) {
-                    v[j][i] = (mine + i < n) ? a.in[j][mine + i] : 0u;
+                    v[j][i] = (mine + i < n) ? scan_in(a, j, mine + i) : 0u;
                     s4[j] += v[j][i];
                 }
             }
@@ -106,7 +140,7 @@ __global__ void __launch_bounds__(1024) k_scan_single(ScanArgs a, const uint32_t
             uint32_t run = carry_sh[j] + ((w > 0) ? sh[j][w - 1] : 0u) + x4[j] - s4[j];
 #pragma unroll
             for (int i = 0; i < IT; ++i) {
-                if (mine + i < n) a.out[j][mine + i] = run;
+                if (mine + i < n) scan_out(a, j, mine + i, run, v[j][i]);
                 run += v[j][i];
             }
         }
@@ -119,6 +153,7 @@ __global__ void __launch_bounds__(1024) k_scan_single(ScanArgs a, const uint32_t
         if (K > 1 && a.total[1]) *a.total[1] = carry_sh[1];
         if (K > 2 && a.total[2]) *a.total[2] = carry_sh[2];
         if (K > 3 && a.total[3]) *a.total[3] = carry_sh[3];
+        scan_post(a.post);
     }
 }
 
@@ -151,7 +186,7 @@ __global__ void __launch_bounds__(LB_THREADS) k_scan_lookback(ScanArgs a, const 
         if (j < K) {
 #pragma unroll
             for (int i = 0; i < LB_ITEMS; ++i) {
-                v[j][i] = (mine + i < n) ? a.in[j][mine + i] : 0u;
+                v[j][i] = (mine + i < n) ? scan_in(a, j, mine + i) : 0u;
                 s4[j] += v[j][i];
             }
         }
@@ -216,13 +251,15 @@ __global__ void __launch_bounds__(LB_THREADS) k_scan_lookback(ScanArgs a, const 
         }
     }
     __syncthreads();
+    // the block that wrote the totals (the barrier orders them before this)
+    if (threadIdx.x == 0 && (t + 1 == nt || (nt == 0 && t == 0))) scan_post(a.post);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         if (j >= K) break;
         uint32_t run = s_prefix[j] + ((w > 0) ? sh[j][w - 1] : 0u) + x4[j] - s4[j];
 #pragma unroll
         for (int i = 0; i < LB_ITEMS; ++i) {
-            if (mine + i < n) a.out[j][mine + i] = run;
+            if (mine + i < n) scan_out(a, j, mine + i, run, v[j][i]);
             run += v[j][i];
         }
     }
@@ -238,6 +275,9 @@ void scan_exclusive(const ScanJob& job, const uint32_t* d_n, uint32_t n_max, uin
     }
     a.k = job.k;
     a.err = job.err;
+    a.gen = job.gen;
+    a.cmp = job.cmp;
+    a.post = job.post;
     if (n_max <= SMALL_SCAN_MAX) {
         k_scan_single<<<1, 1024, 0, st>>>(a, d_n, n_max);
         ++g_launches;

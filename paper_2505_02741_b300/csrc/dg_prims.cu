@@ -50,7 +50,11 @@ struct ScanArgs {
 // element c of input array j (read, or generated: see ScanGen)
 __device__ __forceinline__ uint32_t scan_in(const ScanArgs& a, int j, uint32_t c) {
     if (a.gen.mode == 1) {
-        if (j == 0) return (c == 0 || a.gen.keys[c - 1] / a.gen.n_div != a.gen.keys[c] / a.gen.n_div) ? 1u : 0u;
+        if (j == 0) {  // sorted keys: c starts a run iff its predecessor lies below the run's first key
+            if (c == 0) return 1u;
+            const uint64_t k = a.gen.keys[c];
+            return a.gen.keys[c - 1] < k - k % a.gen.n_div ? 1u : 0u;
+        }
         const uint8_t kd = a.gen.kinds[a.gen.vals[c]];
         return (j == 1 ? kd == a.gen.k_ins : kd == a.gen.k_del) ? 1u : 0u;
     }

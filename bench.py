@@ -499,7 +499,9 @@ def run_quality(args):
     on the 3-D mesh: ten insertion batches adding 25 % of |V| edges, then
     d_H^(0) -> d_H^(10), kappa(G0, H0), kappa(G10, H0) (H left alone),
     kappa(G10, H10) (dyGRASS updates), and the PCG iterations to a relative
-    residual of 1e-8 with each sparsifier as preconditioner.  The CG
+    residual of 1e-8 with each sparsifier as preconditioner; beside them the
+    GRASS-like H(0) of the same density (its build time, kappa and PCG
+    iterations).  The CG
     iteration without preconditioner is timed for the roofline of the
     Laplacian-product path."""
     import torch
@@ -533,9 +535,25 @@ def run_quality(args):
         info, _ = gr.pcg_solve(db.data_ptr(), dx.data_ptr(), **popt)
         return k, info
 
+    # the GRASS-like H(0) (reading R20) at the same density: the same spanning
+    # forest plus as many off-tree edges, those of largest stretch
+    tree = W.spanning_forest(n, wl.a, wl.b, wl.w)
+    n_off = int(wl.h_ids.size - tree.size)
     with clk:
         d0 = g.density()
         k00, p00 = measure(g)
+        gg = ctx.load_graph(n, wl.a, wl.b, wl.w)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gg.init_sparsifier_grass(wl.a[tree], wl.b[tree], n_off)
+        grass_ms = 1e3 * (time.perf_counter() - t0)
+        kg, pg = measure(gg)
+        grass = {"init_ms": grass_ms, "init_timing": "host wall clock around dg_init_sparsifier_grass (synchronous)",
+                 "off_tree_edges": n_off, "d_H": gg.density()[0], "kappa": kg["kappa"], "pcg_iters": pg["iters"],
+                 "lanczos": kg, "pcg": pg,
+                 "compare": "H0 = the same forest + a seeded sample of as many off-tree edges: kappa_G0_H0, "
+                            "pcg_iters G0_H0"}
+        gg.unload()
         dens = [d0[0]]
         upd_ms = []
         for _ in range(10):
@@ -570,6 +588,7 @@ def run_quality(args):
             "pcg_iters": {"G0_H0": p00["iters"], "G10_H0": p10["iters"], "G10_H10": p11["iters"]},
             "pcg": {"G0_H0": p00, "G10_H0": p10, "G10_H10": p11},
             "update_ms_per_batch": upd_ms,
+            "grass_init": grass,
             "cg_iteration": {"ms": it_ms, "iters": info_cg["iters"], "algorithmic_bytes": alg,
                              "roofline": {"bound": "hbm", "achieved": alg / (it_ms * 1e-3) / 1e9, "peak": peak,
                                           "unit": "GB/s", "frac": alg / (it_ms * 1e-3) / 1e9 / peak,

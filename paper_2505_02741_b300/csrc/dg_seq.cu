@@ -25,10 +25,13 @@
 // changed vertices.  With, per vertex, the two smallest update indices that
 // change it (in G and in H), each walked vertex v of update j names the first
 // other update x changing v; the pair (j, x) cannot both be in P, so
-// P ends before max(j, x).  The prefix is cut further before the second
-// occurrence of a repeated edge (whose status depends on the first) and after
-// a deletion whose walkers all missed (its fallback edge is not known to the
-// dry run).  A walker counts up to where the batch's walker stops: an
+// P ends before max(j, x).  An update's status depends on its own edge only,
+// and whether a deletion walks on that edge being in H, which another update
+// changes only by recovering a path through both endpoints: a change to the
+// H list of j's endpoint by another update x ends P before max(j, x) as
+// well.  The prefix is cut further before the second occurrence of a
+// repeated edge (whose status depends on the first) and after a deletion
+// whose walkers all missed (its fallback edge is not known to the dry run).  A walker counts up to where the batch's walker stops: an
 // insertion's walkers at its first hit's step, a deletion's once their
 // resistance exceeds the least hit's (the batch reports exactly those counts,
 // whatever its schedule).
@@ -352,11 +355,14 @@ __global__ void k_seq_conflicts(SeqArgs a) {
         for (int o = 16; o > 0; o >>= 1) first = min(first, __shfl_xor_sync(0xffffffffu, first, o));
         if (lane == 0 && first != SEQ_NONE) atomicMin(a.cut, max(j, first));
     }
+    // whether j's edge is in H (which decides whether a deletion walks) can be
+    // changed by another update only through the H lists of j's endpoints (a
+    // recovered path through them); G lists matter only where j's walks read
+    // them, which the walker scan above covers
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < a.m; j += gridDim.x * blockDim.x) {
         if (!a.valid[j]) continue;
         const uint32_t u = (uint32_t)a.ups[j].u, v = (uint32_t)a.ups[j].v;
-        uint32_t x = min(other(a.g1, a.g2, u, j), other(a.g1, a.g2, v, j));
-        x = min(x, min(other(a.h1, a.h2, u, j), other(a.h1, a.h2, v, j)));
+        const uint32_t x = min(other(a.h1, a.h2, u, j), other(a.h1, a.h2, v, j));
         if (x != SEQ_NONE) atomicMin(a.cut, max(j, x));
     }
 }

@@ -78,6 +78,7 @@ struct SeqArgs {
     double* rbar;          // per walked deletion: the least hit resistance (the batch prunes beyond it)
     uint32_t* wsteps;      // per walker
     uint8_t* whit;
+    uint8_t* wleaf;        // per walker: it stopped at a vertex with no neighbour to go to
     double* wR;
     uint32_t* g1;          // per vertex: smallest update index changing its G list
     uint32_t* g2;          // ... the second smallest
@@ -159,6 +160,7 @@ __global__ void k_seq_walk(SeqArgs a) {
         if (kind != WALK_INS && kind != WALK_DEL) {
             a.wsteps[wid] = 0;
             a.whit[wid] = 0;
+            a.wleaf[wid] = 0;
             a.wR[wid] = 0.0;
             continue;
         }
@@ -175,7 +177,7 @@ __global__ void k_seq_walk(SeqArgs a) {
         bool pid = false;
         uint32_t p = SEQ_NONE, hint = 0;
         double R = 0.0;
-        bool hit = false;
+        bool hit = false, leaf = false;
         path[0] = u;
         uint32_t off = g.off[u], deg = g.deg[u];
         uint32_t x = philox_word0(0u, k, (uint32_t)id, (uint32_t)(id >> 32), a.key0, a.key1);
@@ -188,7 +190,10 @@ __global__ void k_seq_walk(SeqArgs a) {
             if (pid) {
                 // the jj-th neighbour other than p is L[jj] when L[jj] < p and
                 // L[jj + 1] otherwise; the hint picks which to load first
-                if (deg <= 1) break;
+                if (deg <= 1) {
+                    leaf = true;
+                    break;
+                }
                 const uint32_t jj = __umulhi(x, deg - 1);
                 uint32_t idx = jj + (jj >= hint ? 1u : 0u);
                 e = g.pool[off + idx];
@@ -205,7 +210,10 @@ __global__ void k_seq_walk(SeqArgs a) {
                     e2 = t;
                 }
                 const uint32_t skip = (e1 != SEQ_NONE) + (e2 != SEQ_NONE);
-                if (deg <= skip) break;  // a leaf: no neighbour to go to
+                if (deg <= skip) {  // a leaf: no neighbour to go to
+                    leaf = true;
+                    break;
+                }
                 uint32_t idx = __umulhi(x, deg - skip);  // the idx-th allowed neighbour in list order
                 if (idx >= e1) ++idx;
                 if (idx >= e2) ++idx;
@@ -251,6 +259,7 @@ __global__ void k_seq_walk(SeqArgs a) {
         }
         a.wsteps[wid] = steps;
         a.whit[wid] = hit;
+        a.wleaf[wid] = leaf;
         a.wR[wid] = R;
     }
 }
@@ -337,6 +346,11 @@ __global__ void k_seq_conflicts(SeqArgs a) {
         uint32_t steps = a.wsteps[wid];
         if (kind == WALK_INS && a.early_exit) steps = min(steps, a.lim[j]);
         const double rb = kind == WALK_DEL && a.del_prune ? a.rbar[j] : INFINITY;
+        // A deletion walker reads the G list of every vertex it leaves, and of
+        // the one it stops on only when it stops there for want of a neighbour:
+        // its arrival at the target, its last step, or its arrival above R~
+        // reads nothing of the vertex reached (the entry it came by holds it).
+        const bool leaf = a.wleaf[wid] != 0 && steps == a.wsteps[wid];
         uint32_t first = SEQ_NONE;
         for (uint32_t base = 0; base <= steps; base += 32u) {
             const uint32_t i = base + lane;
@@ -347,7 +361,8 @@ __global__ void k_seq_conflicts(SeqArgs a) {
             if (in && i <= last) {
                 const uint32_t v = path[i];
                 uint32_t x = other(a.h1, a.h2, v, j);
-                if (kind == WALK_DEL) x = min(x, other(a.g1, a.g2, v, j));
+                const bool stop_here = om ? i == last : i == steps;
+                if (kind == WALK_DEL && (!stop_here || (leaf && !om))) x = min(x, other(a.g1, a.g2, v, j));
                 first = min(first, x);
             }
             if (om) break;
@@ -369,7 +384,7 @@ __global__ void k_seq_conflicts(SeqArgs a) {
 
 struct SeqWS {
     uint32_t n = 0, wmax = 0, s = 0, T = 0;
-    DBuf<uint8_t> kind, valid, accepted, whit;
+    DBuf<uint8_t> kind, valid, accepted, whit, wleaf;
     DBuf<uint32_t> qslot, best, paths, wsteps, tabs, cut, lim, kb;
     DBuf<uint64_t> key;
     DBuf<double> wR, pathR, rbar;
@@ -385,6 +400,7 @@ struct SeqWS {
         valid.ensure(a, w, st);
         accepted.ensure(a, w, st);
         whit.ensure(a, nw, st);
+        wleaf.ensure(a, nw, st);
         qslot.ensure(a, w, st);
         best.ensure(a, w, st);
         key.ensure(a, w, st);
@@ -399,7 +415,7 @@ struct SeqWS {
         cut.ensure(a, 2, st);
     }
     void release(DevAlloc& a, cudaStream_t st) {
-        for (auto* b : {&kind, &valid, &accepted, &whit}) b->release(a, st);
+        for (auto* b : {&kind, &valid, &accepted, &whit, &wleaf}) b->release(a, st);
         for (auto* b : {&qslot, &best, &paths, &wsteps, &tabs, &cut, &lim, &kb}) b->release(a, st);
         key.release(a, st);
         for (auto* b : {&wR, &pathR, &rbar}) b->release(a, st);
@@ -462,6 +478,7 @@ void graph_apply_sequential(Ctx& c, DGraph& g, int64_t nu64, const dg_update* up
             A.rbar = w.rbar.p;
             A.wsteps = w.wsteps.p;
             A.whit = w.whit.p;
+            A.wleaf = w.wleaf.p;
             A.wR = w.wR.p;
             A.g1 = w.tabs.p;
             A.g2 = w.tabs.p + n;

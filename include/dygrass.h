@@ -147,8 +147,8 @@ typedef struct {
     int64_t steps;           /* useful walk steps (sum of dg_update_result.steps) */
     int64_t accepted;        /* kept insertions */
     int64_t recovered;       /* edges returned to H by deletions */
-    int64_t h_edges;         /* |E(H)| after the batch */
-    int64_t g_edges;         /* |E(G)| after the batch */
+    int64_t h_edges;         /* |E(H)| now (after the batch; counted when the statistics are read) */
+    int64_t g_edges;         /* |E(G)| now (after the batch; counted when the statistics are read) */
     double walk_ms;          /* device time of the walk phase (CUDA events on the batch stream) */
     double batch_ms;         /* device time of the whole batch step */
     int64_t walk_launches;   /* kernel launches in the walk phase */

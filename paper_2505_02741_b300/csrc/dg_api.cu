@@ -379,8 +379,10 @@ dg_status dg_get_batch_stats(dg_ctx* ctx, int32_t gid, dg_batch_stats* out) {
         DGraph& g = c.graph(gid);
         std::lock_guard<std::mutex> lk(g.mu);
         *out = g.stats;
-        out->h_edges = -1;
-        out->g_edges = -1;
+        // counted now (one pass over each graph's degrees): the current G and H,
+        // i.e. after the last batch
+        out->g_edges = (int64_t)csr_edge_count(g.G, c.alloc, c.stream);
+        out->h_edges = g.has_h ? (int64_t)csr_edge_count(g.H, c.alloc, c.stream) : 0;
     });
 }
 

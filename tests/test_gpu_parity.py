@@ -669,5 +669,8 @@ def test_merge_size_is_the_touched_lists():
         expect = int(deg0[t].sum() + deg1[t].sum())
         assert st_["merge_entries"] == expect, (bi, st_["merge_entries"], expect)
         assert st_["merge_ms"] > 0.0
+        # the edge counts of the statistics are those of the current G and H
+        assert st_["g_edges"] == len(e1)
+        assert st_["h_edges"] == len(g.sparsifier()[0])
         assert_results_equal(res, o.apply(bt.u, bt.v, bt.w, bt.op, prune_bounds=g.ctx.del_prune), f"batch {bi}")
     ctx.close()

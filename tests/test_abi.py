@@ -61,6 +61,9 @@ int main(void) {
          sizeof(dg_kappa_info));
   printf("%zu %zu %zu %zu %zu\n", offsetof(dg_pcg_options, inner_tol), offsetof(dg_pcg_info, inner_iters),
          offsetof(dg_pcg_info, ms), offsetof(dg_kappa_options, d_v0), offsetof(dg_kappa_info, inner_iters));
+  printf("%zu %zu %zu %zu %zu\n", offsetof(dg_batch_stats, h_edges), offsetof(dg_batch_stats, mutate_ms),
+         offsetof(dg_batch_stats, walk_tile), offsetof(dg_batch_stats, merge_ms),
+         offsetof(dg_batch_stats, merge_entries));
   return 0;
 }
 """
@@ -92,6 +95,8 @@ int main(void) {
     assert qs == [32, 40, 48, 40]
     assert vals[27:32] == [D.PcgOptions.inner_tol.offset, D.PcgInfo.inner_iters.offset, D.PcgInfo.ms.offset,
                            D.KappaOptions.d_v0.offset, D.KappaInfo.inner_iters.offset]
+    assert vals[32:37] == [D.BatchStats.h_edges.offset, D.BatchStats.mutate_ms.offset, D.BatchStats.walk_tile.offset,
+                           D.BatchStats.merge_ms.offset, D.BatchStats.merge_entries.offset]
 
 
 def test_host_only_calls(lib):
